@@ -1,0 +1,153 @@
+"""Algorithm 1 of the paper on the 3-D lattice: initialisation and time loop.
+
+Initialisation (Algorithm 1, steps 2-5):
+  * vessels and cancer cells are seeded from the input maps: a site holds a
+    vessel if u_v < p_vessel, else a cancer cell if u_c < p_cell (u are 24-bit
+    Philox uniforms with distinct purposes);
+  * every cancer cell draws phi ~ U(0, 1) (Section 2.2.4: "all cancer cells");
+  * the initial oxygen solves Eq. (oxygen) with s_K = 0 by the fixed point of
+    the lagged linearisation (Picard iteration from K = K0), standing in for
+    the paper's nonlinear steady solve;
+  * P = Vc = 0 and G_d = 0 (reading: the initial intracellular levels are not
+    given, so they start at zero and evolve from the first step on).
+
+One step n -> n+1 (Algorithm 1, loop body, VEGF/Avastin omitted):
+  1. plasma levels G_{d,0}(t^{n+1}) (closed form);
+  2. oxygen: quasi-steady solve with the consumption linearised about the
+     previous K (Section 2.4.1), x0 = previous K;
+  3. drugs: one implicit-Euler step of Eq. (chemo), x0 = G^n;
+  4. ODEs for phi, P, Vc with the new K;
+  5. the CA update (Section 2.5) with Philox draws keyed by the step index n.
+"""
+
+from __future__ import annotations
+
+import dataclasses
+from typing import List
+
+import numpy as np
+
+from . import params as Pm
+from . import stencil as S
+from .ca import ca_update
+from .odes import ode_update
+from .pcg import SolveInfo, pcg
+from .philox import site_uniform
+from .plasma import plasma_concentration
+
+
+@dataclasses.dataclass
+class StepStats:
+    step: int
+    o2: SolveInfo
+    drugs: List[SolveInfo]
+    committed: int
+    kills: int
+    divisions: int
+    blocked: int
+    counts: np.ndarray          # sites per state code 0..5 after the step
+
+
+def seed_lattice(cfg: Pm.Config, p_cell, p_vessel):
+    """Initial states and cycle clocks from the maps (Algorithm 1, steps 2 and 4)."""
+    sites = np.arange(cfg.n_sites, dtype=np.uint64)
+    u_v = site_uniform(cfg.seed, sites, 0, Pm.PURPOSE_VESSEL).reshape(cfg.shape)
+    u_c = site_uniform(cfg.seed, sites, 0, Pm.PURPOSE_CANCER).reshape(cfg.shape)
+    u_p = site_uniform(cfg.seed, sites, 0, Pm.PURPOSE_PHI).reshape(cfg.shape)
+    pv = np.asarray(p_vessel, dtype=np.float64).reshape(cfg.shape)
+    pc = np.asarray(p_cell, dtype=np.float64).reshape(cfg.shape)
+    state = np.where(u_v < pv, Pm.VESSEL, np.where(u_c < pc, Pm.PROLIF, Pm.EMPTY)).astype(np.uint8)
+    phi = np.where(state == Pm.PROLIF, u_p, 0.0)
+    return state, phi
+
+
+def o2_solve(state, K_prev, cfg: Pm.Config, rtol=None):
+    """One lagged-linearised oxygen solve, x0 = K_prev."""
+    coupling = S.o2_coupling(cfg)
+    reaction = S.o2_reaction(state, K_prev, cfg)
+    diag = S.jacobi_diagonal(state.shape, coupling, reaction)
+    b = S.o2_rhs(state, cfg)
+    return pcg(lambda u: S.apply_operator(u, coupling, reaction), b, K_prev, diag,
+               cfg.rtol_o2 if rtol is None else rtol, cfg.maxit)
+
+
+def o2_initial(state, cfg: Pm.Config):
+    """Picard fixed point of the lagged linearisation, starting from K = K0."""
+    K = np.full(state.shape, cfg.K0, dtype=np.float64)
+    iters = 0
+    for iters in range(1, cfg.picard_maxit + 1):
+        K_new, _ = o2_solve(state, K, cfg)
+        change = float(np.sqrt(np.sum((K_new - K) ** 2)))
+        norm = float(np.sqrt(np.sum(K_new ** 2)))
+        K = K_new
+        if norm == 0.0 or change <= cfg.picard_tol * norm:
+            break
+    return K, iters
+
+
+def drug_solve(state, perf, G_old, G0_next, cfg: Pm.Config, d: int):
+    """One implicit-Euler step of Eq. (chemo) for drug d, x0 = G^n."""
+    coupling = S.drug_coupling(cfg, d)
+    reaction = S.drug_reaction(state, perf, cfg, d)
+    diag = S.jacobi_diagonal(state.shape, coupling, reaction)
+    b = S.drug_rhs(state, perf, G_old, G0_next, cfg, d)
+    return pcg(lambda u: S.apply_operator(u, coupling, reaction), b, G_old, diag,
+               cfg.rtol_drug, cfg.maxit)
+
+
+def plasma_levels(cfg: Pm.Config, t: float):
+    return [plasma_concentration(t, cfg.dose_peak[d], cfg.plasma_decay[d],
+                                 cfg.dose_interval * cfg.dt) for d in range(cfg.n_drugs)]
+
+
+class OracleSim:
+    """The oracle's counterpart of one library handle (one replicate)."""
+
+    def __init__(self, cfg: Pm.Config, p_cell, perf, p_vessel, initial_o2=True):
+        self.cfg = cfg
+        self.perf = np.asarray(perf, dtype=np.float64).reshape(cfg.shape)
+        self.state, self.phi = seed_lattice(cfg, p_cell, p_vessel)
+        self.P = np.zeros(cfg.shape)
+        self.Vc = np.zeros(cfg.shape)
+        self.G = [np.zeros(cfg.shape) for _ in range(cfg.n_drugs)]
+        self.step_index = 0
+        self.history: List[StepStats] = []
+        if initial_o2:
+            self.K, self.picard_iterations = o2_initial(self.state, cfg)
+        else:
+            self.K = np.full(cfg.shape, cfg.K0)
+            self.picard_iterations = 0
+
+    # stages of one step, callable one by one
+    def solve_o2(self):
+        self.K, info = o2_solve(self.state, self.K, self.cfg)
+        return info
+
+    def solve_drugs(self):
+        t_next = (self.step_index + 1) * self.cfg.dt
+        infos = []
+        for d, G0 in enumerate(plasma_levels(self.cfg, t_next)):
+            self.G[d], info = drug_solve(self.state, self.perf, self.G[d], G0, self.cfg, d)
+            infos.append(info)
+        return infos
+
+    def update_odes(self):
+        self.phi, self.P, self.Vc = ode_update(self.state, self.phi, self.P, self.Vc,
+                                               self.K, self.cfg)
+
+    def update_ca(self):
+        self.state, self.phi, self.P, self.Vc, st = ca_update(
+            self.state, self.phi, self.P, self.Vc, self.K, self.G, self.cfg, self.step_index)
+        return st
+
+    def step(self, n_steps: int = 1):
+        for _ in range(n_steps):
+            o2 = self.solve_o2()
+            drugs = self.solve_drugs()
+            self.update_odes()
+            st = self.update_ca()
+            counts = np.bincount(self.state.reshape(-1), minlength=6)[:6]
+            self.history.append(StepStats(self.step_index, o2, drugs, st.committed,
+                                          st.kills, st.divisions, st.blocked, counts))
+            self.step_index += 1
+        return self.history[-1] if self.history else None
