@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Throughput of the coupled HCA step: lattice site-steps/s at 256^3.
+
+Workload (one step = oxygen solve + two drug solves + cell ODEs + CA sweep):
+256^3 lattice, FP32 fields with FP64 reductions, synthetic maps from seeded
+Gaussian random fields (correlation length 8 sites, cell density 0.4, vessel
+density 0.12), bolus every 21 steps, CG to 1e-6 relative residual.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun), every rank advances its
+own independent replicate (seed + rank): replicas only, no collective on the
+data path; the barrier and the max over ranks time the job.
+
+--impl reference times the CPU oracle (the comparison arm: there is no
+reference GPU code) on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "lattice site-steps/s at 256^3 coupled"
+N_EDGE = 256
+SAMPLE_EDGE = 64          # CPU sample lattice
+WORKLOAD = dict(precision="f32", n_drugs=2, seed=1, rtol_o2=1e-6, rtol_drug=1e-6, picard_tol=1e-5,
+                dose_interval=21)
+CORR_LEN = 8.0
+# algorithmic HBM bytes per site of each CG pass (FP32; doubled for FP64):
+#   pass A reads z, p_old, d and writes p_new; pass B reads p, d, x, z and writes x, z
+BYTES_PER_SITE = {"pass_a": 16, "pass_b": 24, "setup": 17, "residual": 13, "ode": 29}
+
+
+def workload_config():
+    return {"workload": f"{N_EDGE}^3 coupled HCA step (O2 quasi-steady CG + 2 implicit-Euler drug CGs + "
+                        f"per-cell ODEs + 27-colour stochastic CA)",
+            "lattice": [N_EDGE] * 3, "precision": "f32 fields, f64 reductions", "n_drugs": 2,
+            "cg_rtol": WORKLOAD["rtol_o2"], "maps": f"seeded GRF, correlation length {CORR_LEN:g} sites",
+            "l2": "working set ~0.9 GB per replicate > 129 MB L2; no flush needed"}
+
+
+# ------------------------------------------------------------- clocks ---
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_record(kernel: str):
+    """ncu DRAM bytes per site for a kernel, if captured for the current source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)[kernel]
+    except Exception:
+        return None
+    if rec.get("source_sha") != kernel_source_sha():
+        return None
+    return rec.get("dram_bytes_per_site")
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for name in ("hca_internal.cuh", "pcg.cu"):
+        with open(os.path.join(ROOT, "paper_2105_00448_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+# ------------------------------------------------------------ oracle ---
+def oracle_sample(steps: int, edge: int = SAMPLE_EDGE):
+    """Time `steps` oracle steps on an edge^3 sample of the workload (seconds)."""
+    from oracle import params as Pm
+    from oracle.model import OracleSim
+    from synth import make_maps
+
+    cfg = Pm.Config(nx=edge, ny=edge, nz=edge, **WORKLOAD)
+    maps = make_maps(edge, edge, edge, corr_len=CORR_LEN, seed=WORKLOAD["seed"])
+    sim = OracleSim(cfg, maps.p_cell, maps.perf, maps.p_vessel)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        sim.step(1)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def cpu_cores_used() -> int:
+    # numpy element-wise kernels and the oracle's Python loops run on one thread
+    return 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    times = oracle_sample(args.warmup + args.steps)
+    timed = times[args.warmup:]
+    sites = SAMPLE_EDGE ** 3
+    total = sum(timed)
+    value = sites * len(timed) / total
+    sample = (f"{len(timed)} coupled steps (after {args.warmup} warm-up) of the FP64 oracle on a {SAMPLE_EDGE}^3 "
+              f"lattice with the 256^3 workload's recipe and parameters")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "site-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(timed),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(),
+            "cpu_baseline": {"value": value, "unit": "site-steps/s", "cores": cpu_cores_used(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "site-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- GPU ---
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2105_00448_gb300 import hca
+    from synth import make_maps
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (no CPU fallback)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n = args.edge
+    sites = n ** 3
+    seed = WORKLOAD["seed"] + rank
+    params = {**WORKLOAD, "seed": seed}
+    maps = make_maps(n, n, n, corr_len=CORR_LEN, seed=seed)
+    stream = torch.cuda.Stream()
+    cfg = hca.make_config(n, n, n, stream=stream.cuda_stream, **params)
+    sim = hca.Sim(cfg, (maps.p_cell, maps.perf, maps.p_vessel))
+    if args.warmup:
+        sim.step(args.warmup, allow_noconv=True)
+    torch.cuda.synchronize()
+    hca.hca_profile_enable(sim.handle, True)
+    launches0 = sim.launches()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    rc = sim.step(args.steps, allow_noconv=True)
+    ev1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if dist:
+        dist.barrier()
+    t_ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    prof = hca.hca_get_profile(sim.handle)
+    hca.hca_profile_enable(sim.handle, False)
+    launches = sim.launches() - launches0
+    stats = sim.stats()
+    sim.close()
+    value = world * sites * args.steps / (t_ms / 1e3)
+
+    # roofline of the dominant kernel class (by summed device time)
+    peak, peak_kind = measured_peak_hbm()
+    dom = max(("pass_a", "pass_b", "setup", "residual", "ode"), key=lambda k: prof[k]["ms"])
+    avg_ms = prof[dom]["ms"] / max(1, prof[dom]["launches"])
+    n_kernels_per_launch = 2 if dom == "residual" else 1
+    bytes_per_launch = BYTES_PER_SITE[dom] * sites * n_kernels_per_launch
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+    tr = traffic_record(dom)
+    roofline = {"bound": "hbm", "kernel": f"k_{dom}<float>", "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": tr * sites if tr is not None else None,
+                "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms}
+    # time share of each kernel class over the timed region
+    total_prof = sum(v["ms"] for v in prof.values())
+    kernel_share = {k: round(v["ms"] / total_prof, 4) for k, v in prof.items() if v["launches"]}
+    line = None
+    if rank == 0:
+        e2e = run_e2e(args, hca, make_maps, np, torch) if not args.skip_e2e else None
+        cpu = None
+        if world == 1 and not args.skip_cpu:
+            times = oracle_sample(args.cpu_steps)
+            cpu_val = SAMPLE_EDGE ** 3 * len(times) / sum(times)
+            cpu = {"value": cpu_val, "unit": "site-steps/s", "cores": cpu_cores_used(), "kind": "oracle",
+                   "sample": f"{len(times)} coupled steps of the FP64 oracle on a {SAMPLE_EDGE}^3 lattice with "
+                             f"the 256^3 workload's recipe and parameters ({sum(times):.1f} s)"}
+        line = {"metric": METRIC, "value": value, "unit": "site-steps/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {**workload_config(), "parallelism": f"replicas{world}" if world > 1 else "single"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clocks,
+                "cg_iterations_per_step": {"total": prof["pass_a"]["launches"] / args.steps},
+                "last_step": {"o2_iterations": stats["o2_iterations"], "drug_iterations": stats["drug_iterations"][:2],
+                              "o2_rel_residual": stats["o2_rel_residual"],
+                              "drug_rel_residual": stats["drug_rel_residual"][:2], "counts": stats["counts"]},
+                "kernel_time_share": kernel_share, "status": int(rc)}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(args, hca, make_maps, np, torch):
+    """Same metric through the public C ABI with host buffers: create from
+    pinned host maps, then per step one hca_step and a read of the states and
+    the oxygen field back to pinned host memory, all inside the timed region."""
+    n = args.edge
+    sites = n ** 3
+    maps = make_maps(n, n, n, corr_len=CORR_LEN, seed=WORKLOAD["seed"])
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    pc, pf, pv = pin(maps.p_cell), pin(maps.perf), pin(maps.p_vessel)
+    states = torch.empty((n, n, n), dtype=torch.uint8).pin_memory()
+    oxy = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
+    steps = args.e2e_steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cfg = hca.make_config(n, n, n, **WORKLOAD)
+    h = hca.hca_create(cfg, pc, pf, pv)
+    for _ in range(steps):
+        rc = hca.hca_step(h, 1)
+        if rc not in (hca.HCA_OK, hca.HCA_ERR_NOCONV):
+            raise hca.HcaError(rc, "hca_step")
+        hca.hca_read_states(h, 0, states)
+        hca.hca_read_fields(h, 0, hca.FIELD_O2, oxy)
+    torch.cuda.synchronize()
+    elapsed = time.perf_counter() - t0
+    hca.hca_destroy(h)
+    return {"value": sites * steps / elapsed, "unit": "site-steps/s",
+            "h2d_bytes_per_step": 3 * 4 * sites / steps, "d2h_bytes_per_step": sites * (1 + 4),
+            "steps": steps, "includes": "create (map upload + initial O2 fixed point) and per-step state/O2 readback"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--edge", type=int, default=N_EDGE, help=argparse.SUPPRESS)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 0 or args.steps < 1:
+        raise SystemExit("need --steps >= 1 and --warmup >= 0")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,276 @@
+/*
+ * hca.h -- C ABI of the GB300 (sm_103a) library for the data-parallel hot path
+ * of one time step of the hybrid cellular automaton (HCA) model of
+ * Lai, Tasken et al., "A scalable solver for a stochastic, hybrid cellular
+ * automaton model of personalized breast cancer therapy" (arXiv:2105.00448).
+ *
+ * One step (Algorithm 1, loop body) on a 3-D lattice of nx*ny*nz sites:
+ *   1. plasma levels G_{d,0}(t^{n+1}) of the drugs (Eq. intrachemo3, closed form);
+ *   2. quasi-steady oxygen K: Eq. (oxygen) with s_K = 0 and the consumption
+ *      linearised about the previous K (Section 2.4.1), 7-point stencil,
+ *      Jacobi-preconditioned CG;
+ *   3. drugs G_d: one implicit-Euler step of Eq. (chemo), 7-point stencil, CG;
+ *   4. per-cell ODEs for phi, P, Vc (Eqs. cellcycle, odep53, odevegf);
+ *   5. the stochastic CA update of committed cancer cells (Sections 2.2.1 and
+ *      2.5): Beta-CDF drug kill (Eq. 1), else division into the free Moore
+ *      neighbour with the highest K, resolved in a fixed 27-colour sweep with
+ *      counter-based Philox4x32-10 draws keyed by (seed, site, step).
+ *
+ * Conventions for every function below:
+ *   - Return value: HCA_OK (0) or a negative HCA_ERR_* code.  No function
+ *     aborts, throws or prints.  hca_status_string() names a code.
+ *   - Site order: linear index x + nx*(y + ny*z) (x fastest); field arrays are
+ *     dense in that order (no padding) on the caller's side.
+ *   - Precision: HCA_FP64 stores every field in double; HCA_FP32 stores fields
+ *     in float and keeps all inner products and residual norms in double.
+ *     Field buffers passed in or out use the handle's precision.
+ *   - Streams: all device work of a handle is ordered on cfg.stream (a
+ *     cudaStream_t; NULL = the legacy default stream).  hca_step and
+ *     hca_stage return once the work is queued; reads, writes and
+ *     hca_get_stats synchronise that stream before they return.
+ *   - Ownership: the library allocates and owns all device state of a handle
+ *     and frees it in hca_destroy.  Caller buffers are only read or written
+ *     during the call and are never retained.
+ *   - "on_device" flags: 1 = the pointer is CUDA device memory of the current
+ *     device, 0 = host memory (pageable or pinned).
+ *   - Thread safety: one handle must not be used by two threads at once.
+ */
+#ifndef HCA_H
+#define HCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HCA_ABI_VERSION 1
+
+/* status codes */
+#define HCA_OK 0
+#define HCA_ERR_ARG (-1)           /* bad argument: size, pointer, index, config value */
+#define HCA_ERR_CUDA (-2)          /* a CUDA runtime call failed */
+#define HCA_ERR_OOM (-3)           /* device allocation failed */
+#define HCA_ERR_NONFINITE (-4)     /* an input map or a field holds NaN/Inf */
+#define HCA_ERR_NOCONV (-5)        /* a CG solve hit maxit; the step completed with its last iterate */
+#define HCA_ERR_TIMEOUT (-6)       /* a bounded device wait gave up */
+#define HCA_ERR_UNIMPLEMENTED (-7)
+#define HCA_ERR_STATE (-8)         /* call not valid in the handle's current state */
+
+/* precision */
+#define HCA_FP64 0
+#define HCA_FP32 1
+
+/* lattice state codes (uint8).  The paper's L(x) in {empty, cancer, stroma}
+ * and vessel indicator G(x) (Sections 2.2.1-2.2.2) merged into one code. */
+#define HCA_EMPTY 0
+#define HCA_PROLIF 1   /* cancer cell, cycling */
+#define HCA_QUIESC 2   /* cancer cell whose last division found no free neighbour */
+#define HCA_DEAD 3     /* killed in the last CA update; acts as EMPTY, cleared next update */
+#define HCA_VESSEL 4   /* functional vessel */
+#define HCA_STROMA 5   /* stroma cell: occupies space, consumes O2, never divides */
+
+/* field selection for hca_read_fields / hca_write_fields; fields are packed
+ * one after another in increasing bit order, each nx*ny*nz elements */
+#define HCA_FIELD_O2 (1u << 0)     /* oxygen K (mmHg) */
+#define HCA_FIELD_DRUG0 (1u << 1)  /* drug concentrations G_0..G_2 (plasma-peak units) */
+#define HCA_FIELD_DRUG1 (1u << 2)
+#define HCA_FIELD_DRUG2 (1u << 3)
+#define HCA_FIELD_PHI (1u << 4)    /* cell-cycle clock phi */
+#define HCA_FIELD_P53 (1u << 5)    /* intracellular p53, P */
+#define HCA_FIELD_VEGFC (1u << 6)  /* intracellular VEGF, Vc */
+#define HCA_FIELD_PERF (1u << 7)   /* perfusion map (the vessel-exchange scale) */
+
+/* stages for hca_stage; HCA_STAGE_ALL runs one full step (as hca_step(h, 1)) */
+#define HCA_STAGE_O2 (1u << 0)
+#define HCA_STAGE_DRUGS (1u << 1)
+#define HCA_STAGE_ODE (1u << 2)
+#define HCA_STAGE_CA (1u << 3)
+#define HCA_STAGE_ADVANCE (1u << 4) /* step counter n -> n+1 */
+#define HCA_STAGE_ALL 0x1Fu
+
+/* warm start of the oxygen CG */
+#define HCA_WS_PREV 0     /* previous step's K */
+#define HCA_WS_LEARNED 1  /* reserved: learned initial guess */
+
+/*
+ * Simulation parameters.  Defaults (hca_config_default) are Table 1 of the
+ * paper plus the readings listed per field.  Units: micrometres, minutes,
+ * mmHg for oxygen, plasma-peak units for drugs.  Arrays of 3 are per drug:
+ * index 0 cyclophosphamide, 1 epirubicin, 2 fluorouracil.
+ */
+typedef struct hca_config {
+  uint32_t struct_size;  /* = sizeof(hca_config); checked */
+  int32_t nx, ny, nz;    /* lattice, each >= 1; nx*ny*nz <= 2^31 - 1 */
+  int32_t precision;     /* HCA_FP64 or HCA_FP32 */
+  int32_t n_drugs;       /* 0..3 */
+  uint64_t seed;         /* Philox key */
+
+  double dx;             /* Table 1 Delta x = 10 um */
+  double dt;             /* CA step, minutes (60) */
+  double rtol_o2;        /* relative residual target of the oxygen solve (1e-8, Section 2.4.1) */
+  double rtol_drug;      /* same for each drug solve (1e-8) */
+  int32_t maxit;         /* CG iteration cap per solve */
+  int32_t ode_substeps;  /* RK4 steps per dt for Vc (60: h = 1 min, Section 2.4.2) */
+  double picard_tol;     /* initial O2 fixed point: stop at ||dK||/||K|| <= tol */
+  int32_t picard_maxit;
+  int32_t dose_interval; /* CA steps between boluses; boluses at steps 0, I, 2I, ... */
+
+  /* Eq. (oxygen), Table 1 */
+  double D_K;    /* 1.05e5 um^2/min */
+  double phi_K;  /* 900, consumption per consuming site (mmHg/min) */
+  double K1;     /* 2.5 mmHg */
+  double K0;     /* 20 mmHg */
+  double r_K;    /* 1.88e4 /min: supply P_K 2 pi r0 / dx^2 per vessel site */
+
+  /* Eq. (chemo), Table 1 and readings */
+  double D_G[3];          /* 9.6e3 um^2/min */
+  double psi_G[3];        /* 1e-2 /min */
+  double kappa_G[3];      /* vessel exchange scale, times the perfusion map (reading: 2.0 /min) */
+  double uptake_G[3];     /* optional uptake at live cancer sites (default 0) */
+  double dose_peak[3];    /* plasma peak per bolus = max G_{d,0} (1.0) */
+  double plasma_decay[3]; /* /min: cl3/u, cl2/w1, v_max/k_m */
+  int32_t kill_b[3];      /* Beta(1, b) sensitivity, positive integers (Eq. 1; default 1) */
+
+  /* Eqs. (cellcycle), (odep53), (odevegf), Table 1 */
+  double T_cycle;  /* 3.74 days in minutes */
+  double K_phi;    /* 1.4 */
+  double k1, k1p, K_p53;         /* 4e-4, 0.01, 0.01 */
+  double k2, k2p, k2pp, J5, K_V; /* 2e-3, 0.01, -2e-4, 0.04, 0.01 */
+
+  /* precision scheme of HCA_FP32 (ignored for HCA_FP64) */
+  double rtol_inner;     /* inner FP32 CG tolerance of the oxygen defect correction (1e-3) */
+  int32_t max_outer;     /* defect-correction sweeps per oxygen solve (8) */
+
+  int32_t warm_start;    /* HCA_WS_PREV */
+  int32_t threads_per_block; /* 0 = library choice; else 128, 256 or 512 (tile autotuning) */
+  void* stream;          /* cudaStream_t, NULL = default stream */
+} hca_config;
+
+/* Per-replicate statistics of the most recent step (or stage). */
+typedef struct hca_stats {
+  int64_t step;                 /* steps completed */
+  int32_t picard_iterations;    /* initial oxygen fixed point */
+  int32_t o2_iterations;        /* CG iterations of the last oxygen solve (all sweeps) */
+  int32_t o2_sweeps;            /* defect-correction sweeps (1 for HCA_FP64) */
+  int32_t drug_iterations[3];
+  double o2_rel_residual;       /* ||b - A K|| / ||b|| recomputed at exit */
+  double drug_rel_residual[3];
+  int32_t not_converged;        /* bit 0: oxygen, bit 1+d: drug d hit maxit */
+  int32_t pad0;
+  int64_t committed, kills, divisions, blocked; /* last CA update */
+  int64_t counts[6];            /* sites per state code after the last update */
+} hca_stats;
+
+typedef struct hca_handle hca_handle;
+
+/* Kernel classes timed by the optional per-launch profiler. */
+#define HCA_KCLASS_SETUP 0      /* solve set-up: r = b - A x0, diagonal */
+#define HCA_KCLASS_PASS_A 1     /* CG pass A: p = z + beta p, p.Ap */
+#define HCA_KCLASS_PASS_B 2     /* CG pass B: x, z update, r.z, |r|^2 */
+#define HCA_KCLASS_RESIDUAL 3   /* true residual at solve exit */
+#define HCA_KCLASS_ODE 4        /* per-cell ODEs */
+#define HCA_KCLASS_CA_COMPACT 5 /* CA commit compaction */
+#define HCA_KCLASS_CA_COLOUR 6  /* CA colour sweeps */
+#define HCA_KCLASS_OTHER 7
+#define HCA_NKCLASS 8
+
+typedef struct hca_profile {
+  int64_t launches[HCA_NKCLASS];
+  double ms[HCA_NKCLASS];      /* summed device time between CUDA events around each launch */
+} hca_profile;
+
+/* Fill *cfg with the defaults above for an nx*ny*nz lattice (FP64, 1 drug,
+ * seed 0).  Returns HCA_ERR_ARG for a NULL pointer. */
+int hca_config_default(hca_config* cfg, int32_t nx, int32_t ny, int32_t nz);
+
+/* Create one simulation (Algorithm 1, steps 2-5): seed vessels and cancer
+ * cells from the maps (vessel if u_v < p_vessel, else cancer if u_c <
+ * p_cell, 24-bit Philox uniforms), phi ~ U(0,1) on cancer cells, P = Vc = 0,
+ * G = 0, and the initial oxygen as the fixed point of the linearised steady
+ * equation.  p_cell, perf, p_vessel: nx*ny*nz float each, site order above;
+ * copied, the caller keeps ownership.  HCA_ERR_NONFINITE if a map holds
+ * NaN/Inf or a probability lies outside [0, 1] or perf < 0. */
+int hca_create(const hca_config* cfg, const float* p_cell, const float* perf,
+               const float* p_vessel, int32_t maps_on_device, hca_handle** out);
+
+/* Create n independent replicates (uneven lattices allowed) that advance
+ * together: every kernel of a step covers all replicates in one launch.
+ * cfgs[i] gives replicate i's lattice, seed and parameters; precision,
+ * n_drugs, dt, threads_per_block and stream must agree across replicates.
+ * Maps are arrays of n pointers. */
+int hca_create_batch(int32_t n, const hca_config* cfgs, const float* const* p_cell,
+                     const float* const* perf, const float* const* p_vessel,
+                     int32_t maps_on_device, hca_handle** out);
+
+/* Advance all replicates by n_steps full steps.  Returns HCA_ERR_NOCONV if
+ * any solve of the last step hit maxit (its last iterate is kept and the
+ * step completed), HCA_ERR_NONFINITE if a residual norm became NaN/Inf. */
+int hca_step(hca_handle* h, int32_t n_steps);
+
+/* Run selected stages of one step (HCA_STAGE_* mask) in their fixed order
+ * O2, DRUGS, ODE, CA, ADVANCE.  The drug stage uses the plasma levels of the
+ * current step index n (at t^{n+1}); the CA stage draws with step index n. */
+int hca_stage(hca_handle* h, uint32_t stage_mask);
+
+/* Copy fields of replicate rep to dst: the selected fields one after another
+ * in increasing mask-bit order, each nx*ny*nz elements of the handle's
+ * precision.  dst_bytes must be at least that size (else HCA_ERR_ARG). */
+int hca_read_fields(hca_handle* h, int32_t rep, uint32_t field_mask, void* dst,
+                    size_t dst_bytes, int32_t dst_on_device);
+
+/* Overwrite fields of replicate rep from src (same packing as reading).
+ * Used to restart from a saved state or to drive stages on given inputs. */
+int hca_write_fields(hca_handle* h, int32_t rep, uint32_t field_mask, const void* src,
+                     size_t src_bytes, int32_t src_on_device);
+
+/* Copy / overwrite the uint8 lattice states (HCA_EMPTY .. HCA_STROMA) of rep. */
+int hca_read_states(hca_handle* h, int32_t rep, uint8_t* dst, size_t dst_bytes,
+                    int32_t dst_on_device);
+int hca_write_states(hca_handle* h, int32_t rep, const uint8_t* src, size_t src_bytes,
+                     int32_t src_on_device);
+
+/* Set / get the step index n (drives plasma levels and the Philox counter). */
+int hca_set_step(hca_handle* h, int64_t step);
+
+/* Statistics of replicate rep after the last step or stage. */
+int hca_get_stats(hca_handle* h, int32_t rep, hca_stats* out);
+
+/* out = A u for replicate rep, where A is the operator of the next solve
+ * (which = 0: oxygen, linearised about the current K; which = 1 + d: drug d's
+ * implicit-Euler operator).  u, out: nx*ny*nz elements of the handle's
+ * precision.  Exposes the 7-point stencil of Eqs. (oxygen)/(chemo) alone. */
+int hca_apply_operator(hca_handle* h, int32_t rep, int32_t which, const void* u, void* out,
+                       int32_t on_device);
+
+/* 24-bit Philox4x32-10 uniforms u = (w0 >> 8) * 2^-24 for sites
+ * site_begin .. site_begin + n - 1 with counter (site lo, site hi, step,
+ * purpose) and key (seed lo, seed hi): the draws of Section 2.6's
+ * per-cell streams.  dst: n floats (device or host). */
+int hca_philox_uniforms(uint64_t seed, uint64_t site_begin, int64_t n, uint32_t step,
+                        uint32_t purpose, float* dst, int32_t dst_on_device);
+
+/* Block until all queued work of h is done. */
+int hca_sync(hca_handle* h);
+
+/* Number of replicates, lattice of replicate rep. */
+int hca_get_shape(hca_handle* h, int32_t rep, int32_t* nx, int32_t* ny, int32_t* nz);
+
+/* Number of this library's kernel launches since creation (for accounting). */
+int64_t hca_launch_count(hca_handle* h);
+
+/* Per-launch device timing: when enabled, every kernel launch of h is
+ * bracketed by CUDA events on the handle's stream and its duration is added
+ * to its class.  Enabling resets the counters.  hca_get_profile synchronises
+ * the stream and returns the sums since the last enable. */
+int hca_profile_enable(hca_handle* h, int32_t enable);
+int hca_get_profile(hca_handle* h, hca_profile* out);
+
+void hca_destroy(hca_handle* h);
+const char* hca_status_string(int32_t status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HCA_H */

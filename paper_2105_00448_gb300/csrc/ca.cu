@@ -1,0 +1,202 @@
+// The stochastic cellular-automaton update (Sections 2.2.1 and 2.5).
+//
+// 1. compaction: DEAD sites become EMPTY; every cancer cell with phi >= 1 is
+//    committed and appended to the list of its colour
+//    c = (x mod 3) + 3 (y mod 3) + 9 (z mod 3);
+// 2. one launch per colour c = 0..26, in order: each committed cell of the
+//    colour is killed with probability 1 - prod_d (1 - x_d)^{b_d},
+//    x_d = clamp(G_d / max G_{d,0}, 0, 1) (Eq. 1 with a = 1), decided by a
+//    Philox draw keyed by (seed, site, step, KILL); otherwise it divides into
+//    the free (EMPTY or DEAD) Moore neighbour with the highest K (first in
+//    dz, dy, dx order on ties), both cells becoming PROLIF with
+//    phi = P = Vc = 0; with no free neighbour it becomes QUIESC with phi = 0.
+//
+// Same-colour sites are at least 3 apart along some axis, so their closed
+// Moore neighbourhoods are disjoint: the cells of one launch never touch the
+// same site and the outcome does not depend on thread order.  Later colours
+// see the daughters and deaths of earlier ones.
+//
+// This translation unit is compiled with -fmad=false and the kill test uses
+// explicit round-to-nearest intrinsics, so the decision is the same IEEE
+// arithmetic as a plain CPU evaluation in the storage precision.
+#include "hca_internal.cuh"
+
+namespace hca {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ float rn_div(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double rn_div(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_ca_compact(Ctx c) {
+  __shared__ unsigned int s_committed;
+  if (threadIdx.x == 0) s_committed = 0;
+  __syncthreads();
+  const int2 ch = c.chunks[blockIdx.x];
+  const int rep = ch.x;
+  const RepDesc& rd = c.reps[rep];
+  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const long long base0 = rd.off + (long long)ch.y * rd.nxp;
+  const int ngroups = nrows * rd.gpr;
+  const int lane = threadIdx.x & 31;
+  int* cnt = c.list_count + rep * 27;
+  unsigned int my_committed = 0;
+  for (int gb = 0; gb < ngroups; gb += blockDim.x) {
+    const int gi = gb + threadIdx.x;
+    const bool ok = gi < ngroups;
+    int rl = 0, g = 0;
+    if (ok) {
+      rl = gi / rd.gpr;
+      g = gi % rd.gpr;
+    }
+    const int j = ch.y + rl;
+    const int y = j % rd.ny, z = j / rd.ny;
+    const long long e = base0 + (long long)rl * rd.nxp + 4LL * g;
+    uchar4 st = ok ? ld_state4(c.state + e) : make_uchar4(0, 0, 0, 0);
+    bool changed = false;
+    bool any_cancer = false;
+    uint8_t sv[4] = {st.x, st.y, st.z, st.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (sv[k] == HCA_DEAD) {
+        sv[k] = HCA_EMPTY;
+        changed = true;
+      }
+      any_cancer |= is_cancer(sv[k]);
+    }
+    V4<T> phi = zero4<T>();
+    if (ok && any_cancer) phi = ld4((const T*)c.phi + e);
+    if (ok && changed) *reinterpret_cast<uchar4*>(c.state + e) = make_uchar4(sv[0], sv[1], sv[2], sv[3]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int x = 4 * g + k;
+      const bool commit = ok && x < rd.nx && is_cancer(sv[k]) && phi.a[k] >= T(1);
+      const int col = commit ? (x % 3) + 3 * (y % 3) + 9 * (z % 3) : -1;
+      const unsigned m = __match_any_sync(FULL, col);
+      const int leader = __ffs(m) - 1;
+      const int rank = __popc(m & ((1u << lane) - 1u));
+      int basev = 0;
+      if (commit && lane == leader) basev = atomicAdd(cnt + col, __popc(m));
+      basev = __shfl_sync(FULL, basev, leader);
+      if (commit) {
+        const unsigned long long site = (unsigned long long)x + (unsigned long long)rd.nx * ((unsigned long long)y + (unsigned long long)rd.ny * z);
+        c.lists[rd.list_off[col] + basev + rank] = (uint32_t)site;
+        my_committed++;
+      }
+    }
+  }
+  if (my_committed) atomicAdd(&s_committed, my_committed);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_committed)
+    atomicAdd((unsigned long long*)&c.stats[rep].committed, (unsigned long long)s_committed);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_ca_colour(Ctx c, int colour) {
+  __shared__ unsigned int s_cnt[3];
+  if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int rep = blockIdx.y;
+  const RepDesc& rd = c.reps[rep];
+  const int n = c.list_count[rep * 27 + colour];
+  const uint32_t step = (uint32_t)(*c.step);
+  T* phi = (T*)c.phi;
+  T* P = (T*)c.P;
+  T* Vc = (T*)c.Vc;
+  const T* K = (const T*)c.K;
+  unsigned int kills = 0, divs = 0, blocked = 0;
+  const long long sy = rd.nxp, sz = (long long)rd.nxp * rd.ny;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t site = c.lists[rd.list_off[colour] + i];
+    const int x = (int)(site % (uint32_t)rd.nx);
+    const int y = (int)((site / (uint32_t)rd.nx) % (uint32_t)rd.ny);
+    const int z = (int)(site / ((uint32_t)rd.nx * (uint32_t)rd.ny));
+    const long long e = rd.off + x + sy * y + sz * z;
+    const T u = (T)site_uniform(rd.seed, site, step, PURPOSE_KILL);
+    T surv = T(1);
+    for (int d = 0; d < rd.n_drugs; ++d) {
+      T xd = rn_div(((const T*)c.G[d])[e], (T)rd.dose_peak[d]);
+      if (xd > T(1)) xd = T(1);
+      if (xd < T(0)) xd = T(0);
+      const T f = rn_sub(T(1), xd);
+      for (int q = 0; q < rd.kill_b[d]; ++q) surv = rn_mul(surv, f);
+    }
+    const T p_kill = rn_sub(T(1), surv);
+    if (u < p_kill) {
+      c.state[e] = HCA_DEAD;
+      phi[e] = T(0);
+      P[e] = T(0);
+      Vc[e] = T(0);
+      kills++;
+      continue;
+    }
+    long long best = -1;
+    T best_K = T(0);
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int zz = z + dz;
+      if (zz < 0 || zz >= rd.nz) continue;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int yy = y + dy;
+        if (yy < 0 || yy >= rd.ny) continue;
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int xx = x + dx;
+          if (xx < 0 || xx >= rd.nx || (dx == 0 && dy == 0 && dz == 0)) continue;
+          const long long nbi = rd.off + xx + sy * yy + sz * zz;
+          if (is_free(c.state[nbi])) {
+            const T kv = K[nbi];
+            if (best < 0 || kv > best_K) {
+              best = nbi;
+              best_K = kv;
+            }
+          }
+        }
+      }
+    }
+    if (best >= 0) {
+      c.state[best] = HCA_PROLIF;
+      c.state[e] = HCA_PROLIF;
+      phi[e] = T(0);
+      P[e] = T(0);
+      Vc[e] = T(0);
+      phi[best] = T(0);
+      P[best] = T(0);
+      Vc[best] = T(0);
+      divs++;
+    } else {
+      c.state[e] = HCA_QUIESC;
+      phi[e] = T(0);
+      blocked++;
+    }
+  }
+  if (kills) atomicAdd(&s_cnt[0], kills);
+  if (divs) atomicAdd(&s_cnt[1], divs);
+  if (blocked) atomicAdd(&s_cnt[2], blocked);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    DevStats& st = c.stats[rep];
+    if (s_cnt[0]) atomicAdd((unsigned long long*)&st.kills, (unsigned long long)s_cnt[0]);
+    if (s_cnt[1]) atomicAdd((unsigned long long*)&st.divisions, (unsigned long long)s_cnt[1]);
+    if (s_cnt[2]) atomicAdd((unsigned long long*)&st.blocked, (unsigned long long)s_cnt[2]);
+  }
+}
+
+}  // namespace
+
+void launch_ca_compact(const Ctx& c, bool fp64) {
+  if (fp64) k_ca_compact<double><<<c.n_chunks, c.threads, 0, c.stream>>>(c);
+  else k_ca_compact<float><<<c.n_chunks, c.threads, 0, c.stream>>>(c);
+}
+
+void launch_ca_colour(const Ctx& c, int colour, int blocks_x, bool fp64) {
+  dim3 grid(blocks_x, c.n_reps);
+  if (fp64) k_ca_colour<double><<<grid, 256, 0, c.stream>>>(c, colour);
+  else k_ca_colour<float><<<grid, 256, 0, c.stream>>>(c, colour);
+}
+
+}  // namespace hca

@@ -1,0 +1,193 @@
+// Lattice initialisation, the per-cell ODEs and small utility kernels.
+//
+// Initialisation (Algorithm 1, steps 2-5): a site holds a vessel if
+// u_v < p_vessel, else a cancer cell if u_c < p_cell; cancer cells draw
+// phi = u_phi ~ U(0, 1).  u are 24-bit Philox uniforms keyed by
+// (seed, site, 0, purpose).  P = Vc = 0, G = 0, K = K0 (start of the initial
+// oxygen fixed point).
+//
+// ODEs over one step dt with K fixed at the cell's site (Section 2.4.2):
+//   phi += dt K / (T (K_phi + K))                         (Eq. cellcycle, exact)
+//   P(s) = P0 e^{-lam s} - k1 expm1(-lam s) / lam,  lam = k1' K/(K_p53 + K)
+//                                                          (Eq. odep53, exact)
+//   Vc: classical RK4 with h = dt / substeps on Eq. (odevegf), P taken from
+//       its exact solution at each stage time.
+// phi is advanced for cancer cells, P and Vc for every cell (cancer, stroma).
+#include "hca_internal.cuh"
+
+namespace hca {
+namespace {
+
+__device__ __forceinline__ float t_exp(float v) { return expf(v); }
+__device__ __forceinline__ double t_exp(double v) { return exp(v); }
+__device__ __forceinline__ float t_expm1(float v) { return expm1f(v); }
+__device__ __forceinline__ double t_expm1(double v) { return expm1(v); }
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_init(Ctx c, const float* __restrict__ pc, const float* __restrict__ pf,
+                                              const float* __restrict__ pv, int* __restrict__ err) {
+  const int2 ch = c.chunks[blockIdx.x];
+  const RepDesc& rd = c.reps[ch.x];
+  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const long long base0 = rd.off + (long long)ch.y * rd.nxp;
+  const int ngroups = nrows * rd.gpr;
+  for (int gi = threadIdx.x; gi < ngroups; gi += blockDim.x) {
+    const int rl = gi / rd.gpr, g = gi % rd.gpr;
+    const int j = ch.y + rl;
+    const int y = j % rd.ny, z = j / rd.ny;
+    const long long e = base0 + (long long)rl * rd.nxp + 4LL * g;
+    uchar4 st = make_uchar4(0, 0, 0, 0);
+    V4<T> phi = zero4<T>(), perf = zero4<T>(), K = zero4<T>();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int x = 4 * g + k;
+      if (x >= rd.nx) continue;
+      const float p_c = pc[e + k], p_f = pf[e + k], p_v = pv[e + k];
+      if (!(p_c >= 0.f && p_c <= 1.f) || !(p_v >= 0.f && p_v <= 1.f) || !(p_f >= 0.f) || !isfinite(p_f))
+        atomicOr(err, 1);
+      const unsigned long long site = (unsigned long long)x + (unsigned long long)rd.nx * ((unsigned long long)y + (unsigned long long)rd.ny * z);
+      const float u_v = site_uniform(rd.seed, site, 0u, PURPOSE_VESSEL);
+      const float u_c = site_uniform(rd.seed, site, 0u, PURPOSE_CANCER);
+      const float u_p = site_uniform(rd.seed, site, 0u, PURPOSE_PHI);
+      uint8_t s = HCA_EMPTY;
+      if (u_v < p_v) s = HCA_VESSEL;
+      else if (u_c < p_c) s = HCA_PROLIF;
+      if (k == 0) st.x = s; else if (k == 1) st.y = s; else if (k == 2) st.z = s; else st.w = s;
+      phi.a[k] = s == HCA_PROLIF ? (T)u_p : T(0);
+      perf.a[k] = (T)p_f;
+      K.a[k] = (T)rd.K0;
+    }
+    *reinterpret_cast<uchar4*>(c.state + e) = st;
+    st4((T*)c.phi + e, phi);
+    st4((T*)c.P + e, zero4<T>());
+    st4((T*)c.Vc + e, zero4<T>());
+    st4((T*)c.perf + e, perf);
+    st4((T*)c.K + e, K);
+    if (c.K_lo) st4((T*)c.K_lo + e, zero4<T>());
+    for (int d = 0; d < rd.n_drugs; ++d) {
+      st4((T*)c.G[d] + e, zero4<T>());
+      if (c.G_lo[d]) st4((T*)c.G_lo[d] + e, zero4<T>());
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T p53_at(T P0, T lam, T s, T k1) {
+  return lam != T(0) ? P0 * t_exp(-lam * s) - k1 * t_expm1(-lam * s) / lam : P0 + k1 * s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_ode(Ctx c) {
+  const int2 ch = c.chunks[blockIdx.x];
+  const RepDesc& rd = c.reps[ch.x];
+  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const long long base0 = rd.off + (long long)ch.y * rd.nxp;
+  const int ngroups = nrows * rd.gpr;
+  const T dt = (T)rd.dt, Tc = (T)rd.T_cycle, Kphi = (T)rd.K_phi;
+  const T k1 = (T)rd.k1, k1p = (T)rd.k1p, Kp53 = (T)rd.K_p53;
+  const T k2 = (T)rd.k2, k2p = (T)rd.k2p, k2pp = (T)rd.k2pp, J5 = (T)rd.J5, KV = (T)rd.K_V;
+  const int nsub = rd.ode_substeps;
+  const T h = (T)(rd.dt / nsub);
+  const T half = T(0.5) * h;
+  const T sixth = h / T(6);
+  for (int gi = threadIdx.x; gi < ngroups; gi += blockDim.x) {
+    const int rl = gi / rd.gpr, g = gi % rd.gpr;
+    const long long e = base0 + (long long)rl * rd.nxp + 4LL * g;
+    const uchar4 st = ld_state4(c.state + e);
+    if (!(is_consumer(st.x) || is_consumer(st.y) || is_consumer(st.z) || is_consumer(st.w))) continue;
+    const V4<T> K = ld4((const T*)c.K + e);
+    V4<T> phi = ld4((const T*)c.phi + e);
+    V4<T> P = ld4((const T*)c.P + e);
+    V4<T> V = ld4((const T*)c.Vc + e);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint8_t s = st_at(st, k);
+      if (!is_consumer(s) || 4 * g + k >= rd.nx) continue;
+      const T Kk = K.a[k];
+      if (is_cancer(s)) phi.a[k] = phi.a[k] + dt * Kk / (Tc * (Kphi + Kk));
+      const T lam = k1p * Kk / (Kp53 + Kk);
+      const T decay = k2p * Kk / (KV + Kk);
+      const T P0 = P.a[k];
+      T v = V.a[k];
+      for (int m = 0; m < nsub; ++m) {
+        const T s0 = (T)m * h;
+        const T Pa = p53_at(P0, lam, s0, k1);
+        const T Pb = p53_at(P0, lam, s0 + half, k1);
+        const T Pc = p53_at(P0, lam, s0 + h, k1);
+        const T f1 = k2 + k2pp * Pa * v / (J5 + v) - decay * v;
+        const T v2 = v + half * f1;
+        const T f2 = k2 + k2pp * Pb * v2 / (J5 + v2) - decay * v2;
+        const T v3 = v + half * f2;
+        const T f3 = k2 + k2pp * Pb * v3 / (J5 + v3) - decay * v3;
+        const T v4 = v + h * f3;
+        const T f4 = k2 + k2pp * Pc * v4 / (J5 + v4) - decay * v4;
+        v = v + sixth * (f1 + T(2) * f2 + T(2) * f3 + f4);
+      }
+      V.a[k] = v;
+      P.a[k] = p53_at(P0, lam, dt, k1);
+    }
+    st4((T*)c.phi + e, phi);
+    st4((T*)c.P + e, P);
+    st4((T*)c.Vc + e, V);
+  }
+}
+
+// Sites per state code, per replicate (into stats[rep].counts).
+__global__ void __launch_bounds__(512) k_histogram(Ctx c) {
+  __shared__ unsigned int h[6];
+  if (threadIdx.x < 6) h[threadIdx.x] = 0;
+  __syncthreads();
+  const int2 ch = c.chunks[blockIdx.x];
+  const RepDesc& rd = c.reps[ch.x];
+  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const long long base0 = rd.off + (long long)ch.y * rd.nxp;
+  unsigned int loc[6] = {0, 0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < nrows * rd.nx; i += blockDim.x) {
+    const int rl = i / rd.nx, x = i % rd.nx;
+    const uint8_t s = c.state[base0 + (long long)rl * rd.nxp + x];
+    if (s < 6) loc[s]++;
+  }
+  for (int k = 0; k < 6; ++k)
+    if (loc[k]) atomicAdd(&h[k], loc[k]);
+  __syncthreads();
+  if (threadIdx.x < 6 && h[threadIdx.x])
+    atomicAdd((unsigned long long*)&c.stats[ch.x].counts[threadIdx.x], (unsigned long long)h[threadIdx.x]);
+}
+
+__global__ void k_philox_uniforms(unsigned long long seed, unsigned long long site0, long long n, uint32_t step,
+                                  uint32_t purpose, float* out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = site_uniform(seed, site0 + (unsigned long long)i, step, purpose);
+}
+
+__global__ void k_advance_step(long long* step, long long by) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *step += by;
+}
+
+}  // namespace
+
+void launch_init(const Ctx& c, const float* pc, const float* pf, const float* pv, int* err, bool fp64) {
+  if (fp64) k_init<double><<<c.n_chunks, c.threads, 0, c.stream>>>(c, pc, pf, pv, err);
+  else k_init<float><<<c.n_chunks, c.threads, 0, c.stream>>>(c, pc, pf, pv, err);
+}
+
+void launch_ode(const Ctx& c, bool fp64) {
+  if (fp64) k_ode<double><<<c.n_chunks, c.threads, 0, c.stream>>>(c);
+  else k_ode<float><<<c.n_chunks, c.threads, 0, c.stream>>>(c);
+}
+
+void launch_histogram(const Ctx& c) { k_histogram<<<c.n_chunks, c.threads, 0, c.stream>>>(c); }
+
+void launch_philox_uniforms(unsigned long long seed, unsigned long long site0, long long n, uint32_t step,
+                            uint32_t purpose, float* out, cudaStream_t stream) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_philox_uniforms<<<(unsigned)blocks, 256, 0, stream>>>(seed, site0, n, step, purpose, out);
+}
+
+void launch_advance_step(long long* step, long long by, cudaStream_t stream) {
+  k_advance_step<<<1, 32, 0, stream>>>(step, by);
+}
+
+}  // namespace hca

@@ -1,0 +1,937 @@
+// Host side of the library: handle set-up, device memory, the step schedule
+// (Algorithm 1 loop body: oxygen, drugs, ODEs, CA) and the C ABI of hca.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hca_internal.cuh"
+
+namespace hca {
+void launch_setup(const Ctx& c, int which, bool fp64);
+void launch_pass_a(const Ctx& c, int which, const void* p_old, void* p_new, bool fp64);
+void launch_pass_b(const Ctx& c, int which, const void* pdir, void* xfield, bool fp64);
+void launch_true_residual(const Ctx& c, int which, void* xfield, bool fp64);
+void launch_apply(const Ctx& c, int which, int rep, const void* u, void* out, bool fp64);
+void launch_diff_norms(const Ctx& c, const void* a, const void* b, bool fp64);
+void launch_dc_residual(const Ctx& c, int which, const void* x_hi, const void* x_lo, bool first);
+void launch_dc_update(const Ctx& c, void* x_hi, void* x_lo);
+void launch_init(const Ctx& c, const float* pc, const float* pf, const float* pv, int* err, bool fp64);
+void launch_ode(const Ctx& c, bool fp64);
+void launch_histogram(const Ctx& c);
+void launch_philox_uniforms(unsigned long long seed, unsigned long long site0, long long n, uint32_t step,
+                            uint32_t purpose, float* out, cudaStream_t stream);
+void launch_advance_step(long long* step, long long by, cudaStream_t stream);
+void launch_ca_compact(const Ctx& c, bool fp64);
+void launch_ca_colour(const Ctx& c, int colour, int blocks_x, bool fp64);
+}  // namespace hca
+
+using hca::Ctx;
+using hca::RepDesc;
+
+// Optional per-launch device timing (hca_profile_enable).
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;   // 2 * kPairs events, created on first enable
+  struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> pending;
+  size_t next = 0;
+  long long launches[HCA_NKCLASS] = {};
+  double ms[HCA_NKCLASS] = {};
+};
+
+struct hca_handle {
+  Profiler prof;
+  int n_reps = 0;
+  bool fp64 = true;
+  int n_drugs = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::vector<hca_config> cfgs;
+  std::vector<RepDesc> reps_h;
+  std::vector<int2> chunks_h;
+  Ctx ctx{};
+  long long total = 0;        // elements per field array
+  long long lists_total = 0;
+  long long step = 0;
+  long long launches = 0;
+  int picard_iterations = 0;
+  int prev_iters[1 + hca::MAX_DRUGS] = {0, 0, 0, 0};
+  int maxit_all = 0;
+  int max_outer = 0;
+  int last_iters = 0;
+  int* h_pinned = nullptr;    // [0] active replicates, [1] error flag
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+constexpr int kFieldAlign = 64;  // elements; keeps every replicate 256-byte aligned
+
+#define HCA_TRY(expr)                              \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) {                       \
+      (void)cudaGetLastError();                    \
+      return e_ == cudaErrorMemoryAllocation ? HCA_ERR_OOM : HCA_ERR_CUDA; \
+    }                                              \
+  } while (0)
+
+
+constexpr size_t kPairs = 4096;
+
+int prof_flush(hca_handle* h) {
+  Profiler& P = h->prof;
+  if (P.pending.empty()) return HCA_OK;
+  HCA_TRY(cudaStreamSynchronize(h->ctx.stream));
+  for (auto& r : P.pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) P.ms[r.cls] += ms;
+    else (void)cudaGetLastError();
+  }
+  P.pending.clear();
+  P.next = 0;
+  return HCA_OK;
+}
+
+cudaEvent_t prof_begin(hca_handle* h) {
+  Profiler& P = h->prof;
+  if (!P.on) return nullptr;
+  if (P.next + 2 > P.pool.size()) prof_flush(h);
+  cudaEvent_t a = P.pool[P.next++];
+  cudaEventRecord(a, h->ctx.stream);
+  return a;
+}
+
+void prof_end(hca_handle* h, int cls, cudaEvent_t a, int n_kernels) {
+  Profiler& P = h->prof;
+  if (!P.on || !a) return;
+  cudaEvent_t b = P.pool[P.next++];
+  cudaEventRecord(b, h->ctx.stream);
+  P.pending.push_back({cls, a, b});
+  P.launches[cls] += n_kernels;
+}
+
+// Launch `call` (n_kernels kernels of class cls), count it, check the launch
+// and, when profiling, bracket it with events.
+#define HCA_LAUNCH(h, cls, n_kernels, call)  \
+  do {                                       \
+    cudaEvent_t a_ = prof_begin(h);          \
+    call;                                    \
+    (h)->launches += (n_kernels);            \
+    cudaError_t e_ = cudaGetLastError();     \
+    if (e_ != cudaSuccess) return HCA_ERR_CUDA; \
+    prof_end(h, cls, a_, n_kernels);         \
+  } while (0)
+
+int colour_count(int n, int r) { return r < n ? (n - r + 2) / 3 : 0; }
+
+int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+size_t elem_size(const hca_handle* h) { return h->fp64 ? sizeof(double) : sizeof(float); }
+
+int validate(const hca_config& c) {
+  if (c.struct_size != sizeof(hca_config)) return HCA_ERR_ARG;
+  if (c.nx < 1 || c.ny < 1 || c.nz < 1) return HCA_ERR_ARG;
+  const long long n = (long long)c.nx * c.ny * c.nz;
+  if (n > 2147483647LL) return HCA_ERR_ARG;
+  if (c.precision != HCA_FP64 && c.precision != HCA_FP32) return HCA_ERR_ARG;
+  if (c.n_drugs < 0 || c.n_drugs > 3) return HCA_ERR_ARG;
+  if (!(c.dx > 0) || !(c.dt > 0) || !(c.rtol_o2 > 0) || !(c.rtol_drug > 0)) return HCA_ERR_ARG;
+  if (c.maxit < 0 || c.ode_substeps < 1 || c.picard_maxit < 0 || !(c.picard_tol >= 0)) return HCA_ERR_ARG;
+  if (c.dose_interval < 1) return HCA_ERR_ARG;
+  for (int d = 0; d < c.n_drugs; ++d) {
+    if (c.kill_b[d] < 1 || c.kill_b[d] > 64 || !(c.dose_peak[d] > 0)) return HCA_ERR_ARG;
+    if (!(c.D_G[d] >= 0) || !(c.psi_G[d] >= 0) || !(c.kappa_G[d] >= 0) || !(c.uptake_G[d] >= 0)) return HCA_ERR_ARG;
+  }
+  if (!(c.D_K > 0) || !(c.phi_K >= 0) || !(c.K1 > 0) || !(c.r_K >= 0) || !(c.K0 >= 0)) return HCA_ERR_ARG;
+  const int t = c.threads_per_block;
+  if (!(t == 0 || t == 64 || t == 128 || t == 256 || t == 512)) return HCA_ERR_ARG;
+  if (c.warm_start != HCA_WS_PREV && c.warm_start != HCA_WS_LEARNED) return HCA_ERR_ARG;
+  return HCA_OK;
+}
+
+RepDesc make_desc(const hca_config& c) {
+  RepDesc r;
+  std::memset(&r, 0, sizeof(r));
+  r.nx = c.nx;
+  r.ny = c.ny;
+  r.nz = c.nz;
+  r.nxp = (c.nx + 3) / 4 * 4;
+  r.gpr = r.nxp / 4;
+  r.lpr = std::min(32, next_pow2(r.gpr));
+  r.seed = c.seed;
+  r.n_drugs = c.n_drugs;
+  r.maxit = c.maxit;
+  r.rtol_o2 = c.rtol_o2;
+  r.rtol_drug = c.rtol_drug;
+  r.rtol_inner = c.rtol_inner;
+  r.max_outer = c.precision == HCA_FP32 ? c.max_outer : 0;
+  const double dx2 = c.dx * c.dx;
+  r.c_o2 = c.D_K / dx2;
+  r.phi_K = c.phi_K;
+  r.K1 = c.K1;
+  r.K0 = c.K0;
+  r.r_K = c.r_K;
+  r.inv_dt = 1.0 / c.dt;
+  for (int d = 0; d < hca::MAX_DRUGS; ++d) {
+    r.c_drug[d] = c.D_G[d] / dx2;
+    r.base_drug[d] = 1.0 / c.dt + c.psi_G[d];
+    r.kappa[d] = c.kappa_G[d];
+    r.uptake[d] = c.uptake_G[d];
+    r.dose_peak[d] = c.dose_peak[d] > 0 ? c.dose_peak[d] : 1.0;
+    r.plasma_decay[d] = c.plasma_decay[d];
+    r.kill_b[d] = c.kill_b[d];
+  }
+  r.dose_interval_min = c.dose_interval * c.dt;
+  r.dt = c.dt;
+  r.T_cycle = c.T_cycle;
+  r.K_phi = c.K_phi;
+  r.k1 = c.k1;
+  r.k1p = c.k1p;
+  r.K_p53 = c.K_p53;
+  r.k2 = c.k2;
+  r.k2p = c.k2p;
+  r.k2pp = c.k2pp;
+  r.J5 = c.J5;
+  r.K_V = c.K_V;
+  r.ode_substeps = c.ode_substeps;
+  return r;
+}
+
+template <typename P>
+int dev_alloc(hca_handle* h, P** out, size_t bytes) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return HCA_ERR_OOM;
+  }
+  h->allocs.push_back(p);
+  *out = (P*)p;
+  return HCA_OK;
+}
+
+void free_all(hca_handle* h) {
+  if (!h) return;
+  for (auto e : h->prof.pool) cudaEventDestroy(e);
+  h->prof.pool.clear();
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  h->h_pinned = nullptr;
+}
+
+void* field_ptr(hca_handle* h, uint32_t bit) {
+  switch (bit) {
+    case HCA_FIELD_O2: return h->ctx.K;
+    case HCA_FIELD_DRUG0: return h->n_drugs > 0 ? h->ctx.G[0] : nullptr;
+    case HCA_FIELD_DRUG1: return h->n_drugs > 1 ? h->ctx.G[1] : nullptr;
+    case HCA_FIELD_DRUG2: return h->n_drugs > 2 ? h->ctx.G[2] : nullptr;
+    case HCA_FIELD_PHI: return h->ctx.phi;
+    case HCA_FIELD_P53: return h->ctx.P;
+    case HCA_FIELD_VEGFC: return h->ctx.Vc;
+    case HCA_FIELD_PERF: return h->ctx.perf;
+    default: return nullptr;
+  }
+}
+
+// CG iterations (pass A, pass B) on operator `which` for every replicate whose
+// solve is active, updating x, until none is active or maxit is reached.
+// The first convergence check comes after about as many iterations as the
+// previous solve of this operator needed; later checks every 4 iterations.
+int pcg_iterate(hca_handle* h, int which, void* x) {
+  Ctx& c = h->ctx;
+  void* p_old = c.p;
+  void* p_new = c.p_alt;
+  int done = 0;
+  int chunk = std::max(2, h->prev_iters[which] - 2);
+  for (;;) {
+    HCA_TRY(cudaMemcpyAsync(h->h_pinned, &c.sync->active_count, 2 * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    HCA_TRY(cudaStreamSynchronize(c.stream));
+    if (h->h_pinned[1]) return HCA_ERR_NONFINITE;
+    if (h->h_pinned[0] == 0 || done >= h->maxit_all) break;
+    const int n = std::min(chunk, h->maxit_all - done);
+    for (int k = 0; k < n; ++k) {
+      HCA_LAUNCH(h, HCA_KCLASS_PASS_A, 1, hca::launch_pass_a(c, which, p_old, p_new, h->fp64));
+      HCA_LAUNCH(h, HCA_KCLASS_PASS_B, 1, hca::launch_pass_b(c, which, p_new, x, h->fp64));
+      std::swap(p_old, p_new);
+    }
+    done += n;
+    chunk = 4;
+  }
+  h->last_iters = done;
+  return HCA_OK;
+}
+
+int record_iters(hca_handle* h, int which) {
+  std::vector<hca::RepSolve> sv(h->n_reps);
+  HCA_TRY(cudaMemcpyAsync(sv.data(), h->ctx.solve, sizeof(hca::RepSolve) * h->n_reps, cudaMemcpyDeviceToHost,
+                          h->ctx.stream));
+  HCA_TRY(cudaStreamSynchronize(h->ctx.stream));
+  int mx = 0;
+  for (auto& s : sv) mx = std::max(mx, s.iters);
+  h->prev_iters[which] = mx;
+  return HCA_OK;
+}
+
+// One Jacobi-PCG solve of operator `which` (0 oxygen, 1 + d drug d) for all
+// replicates, x0 = current field, in place (storage precision arithmetic,
+// FP64 reductions).
+int solve_plain(hca_handle* h, int which) {
+  Ctx& c = h->ctx;
+  void* x = which == 0 ? c.K : c.G[which - 1];
+  HCA_LAUNCH(h, HCA_KCLASS_SETUP, 1, hca::launch_setup(c, which, h->fp64));
+  int rc = pcg_iterate(h, which, x);
+  if (rc) return rc;
+  HCA_LAUNCH(h, HCA_KCLASS_RESIDUAL, 2, hca::launch_true_residual(c, which, x, h->fp64));
+  rc = record_iters(h, which);
+  if (rc) return rc;
+  HCA_TRY(cudaMemcpyAsync(h->h_pinned, &c.sync->active_count, 2 * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  HCA_TRY(cudaStreamSynchronize(c.stream));
+  return h->h_pinned[1] ? HCA_ERR_NONFINITE : HCA_OK;
+}
+
+// FP32 storage with defect correction: FP64 residual of the two-word
+// solution, FP32 inner CG on the correction, two-word update; repeated until
+// the FP64 relative residual meets the tolerance or max_outer sweeps.
+int solve_dc(hca_handle* h, int which) {
+  Ctx& c = h->ctx;
+  void* xh = which == 0 ? c.K : c.G[which - 1];
+  void* xl = which == 0 ? c.K_lo : c.G_lo[which - 1];
+  int inner_total = 0;
+  for (int outer = 0;; ++outer) {
+    HCA_LAUNCH(h, HCA_KCLASS_RESIDUAL, 1, hca::launch_dc_residual(c, which, xh, xl, outer == 0));
+    HCA_TRY(cudaMemcpyAsync(h->h_pinned, &c.sync->active_count, 2 * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    HCA_TRY(cudaStreamSynchronize(c.stream));
+    if (h->h_pinned[1]) return HCA_ERR_NONFINITE;
+    if (h->h_pinned[0] == 0) {
+      // converged everywhere (or max_outer); zero fields whose right-hand side vanished
+      HCA_LAUNCH(h, HCA_KCLASS_OTHER, 1, hca::launch_dc_update(c, xh, xl));
+      break;
+    }
+    int rc = pcg_iterate(h, which, c.dx);
+    if (rc) return rc;
+    inner_total += h->last_iters;
+    HCA_LAUNCH(h, HCA_KCLASS_OTHER, 1, hca::launch_dc_update(c, xh, xl));
+  }
+  h->prev_iters[which] = std::max(4, inner_total / 2);
+  return HCA_OK;
+}
+
+int solve(hca_handle* h, int which) {
+  if (!h->fp64 && h->max_outer > 0) return solve_dc(h, which);
+  return solve_plain(h, which);
+}
+
+int reset_step_stats(hca_handle* h) {
+  HCA_TRY(cudaMemsetAsync(h->ctx.stats, 0, sizeof(hca::DevStats) * h->n_reps, h->ctx.stream));
+  return HCA_OK;
+}
+
+int run_ca(hca_handle* h) {
+  Ctx& c = h->ctx;
+  HCA_TRY(cudaMemsetAsync(c.list_count, 0, sizeof(int) * 27 * h->n_reps, c.stream));
+  HCA_LAUNCH(h, HCA_KCLASS_CA_COMPACT, 1, hca::launch_ca_compact(c, h->fp64));
+  const int bx = std::max(1, std::min(1024, 2 * c.sm_count / std::max(1, h->n_reps)));
+  for (int col = 0; col < 27; ++col) {
+    HCA_LAUNCH(h, HCA_KCLASS_CA_COLOUR, 1, hca::launch_ca_colour(c, col, bx, h->fp64));
+  }
+  return HCA_OK;
+}
+
+int run_stages(hca_handle* h, uint32_t mask) {
+  int rc = reset_step_stats(h);
+  if (rc) return rc;
+  int status = HCA_OK;
+  if (mask & HCA_STAGE_O2) {
+    rc = solve(h, 0);
+    if (rc) return rc;
+  }
+  if (mask & HCA_STAGE_DRUGS) {
+    for (int d = 0; d < h->n_drugs; ++d) {
+      rc = solve(h, 1 + d);
+      if (rc) return rc;
+    }
+  }
+  if (mask & HCA_STAGE_ODE) {
+    HCA_LAUNCH(h, HCA_KCLASS_ODE, 1, hca::launch_ode(h->ctx, h->fp64));
+  }
+  if (mask & HCA_STAGE_CA) {
+    rc = run_ca(h);
+    if (rc) return rc;
+  }
+  if (mask & HCA_STAGE_ADVANCE) {
+    HCA_LAUNCH(h, HCA_KCLASS_OTHER, 1, hca::launch_advance_step(h->ctx.step, 1, h->ctx.stream));
+    h->step += 1;
+  }
+  return status;
+}
+
+int check_convergence(hca_handle* h) {
+  std::vector<hca::DevStats> st(h->n_reps);
+  HCA_TRY(cudaMemcpyAsync(st.data(), h->ctx.stats, sizeof(hca::DevStats) * h->n_reps, cudaMemcpyDeviceToHost,
+                          h->ctx.stream));
+  HCA_TRY(cudaStreamSynchronize(h->ctx.stream));
+  for (auto& s : st) {
+    if (s.nonfinite) return HCA_ERR_NONFINITE;
+  }
+  for (auto& s : st)
+    if (s.not_converged) return HCA_ERR_NOCONV;
+  return HCA_OK;
+}
+
+// Initial oxygen: Picard iteration of the lagged linearisation from K = K0
+// until ||K_new - K_old|| <= picard_tol ||K_new|| for every replicate.
+int initial_oxygen(hca_handle* h) {
+  Ctx& c = h->ctx;
+  double tol = 0;
+  int maxit = 0;
+  for (auto& cf : h->cfgs) {
+    tol = std::max(tol, cf.picard_tol);
+    maxit = std::max(maxit, cf.picard_maxit);
+  }
+  const size_t bytes = (size_t)h->total * elem_size(h);
+  int it = 0;
+  for (it = 1; it <= maxit; ++it) {
+    HCA_TRY(cudaMemcpyAsync(c.aux, c.K, bytes, cudaMemcpyDeviceToDevice, c.stream));
+    int rc = solve(h, 0);
+    if (rc) return rc;
+    HCA_LAUNCH(h, HCA_KCLASS_OTHER, 1, hca::launch_diff_norms(c, c.K, c.aux, h->fp64));
+    std::vector<hca::RepSolve> sv(h->n_reps);
+    HCA_TRY(cudaMemcpyAsync(sv.data(), c.solve, sizeof(hca::RepSolve) * h->n_reps, cudaMemcpyDeviceToHost, c.stream));
+    HCA_TRY(cudaStreamSynchronize(c.stream));
+    bool all = true;
+    for (int r = 0; r < h->n_reps; ++r) {
+      const double change = std::sqrt(sv[r].rnorm2), norm = std::sqrt(sv[r].bnorm2);
+      if (!std::isfinite(change) || !std::isfinite(norm)) return HCA_ERR_NONFINITE;
+      if (!(norm == 0.0 || change <= h->cfgs[r].picard_tol * norm)) all = false;
+    }
+    if (all) break;
+  }
+  h->picard_iterations = std::min(it, maxit);
+  return HCA_OK;
+}
+
+int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const float* const* perf,
+                const float* const* p_vessel, int maps_on_device, hca_handle** out) {
+  if (!out || n < 1 || !cfgs || !p_cell || !perf || !p_vessel) return HCA_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    int rc = validate(cfgs[i]);
+    if (rc) return rc;
+    if (!p_cell[i] || !perf[i] || !p_vessel[i]) return HCA_ERR_ARG;
+    if (cfgs[i].precision != cfgs[0].precision || cfgs[i].n_drugs != cfgs[0].n_drugs ||
+        cfgs[i].dt != cfgs[0].dt || cfgs[i].threads_per_block != cfgs[0].threads_per_block ||
+        cfgs[i].stream != cfgs[0].stream)
+      return HCA_ERR_ARG;
+  }
+  hca_handle* h = new (std::nothrow) hca_handle();
+  if (!h) return HCA_ERR_OOM;
+  h->n_reps = n;
+  h->fp64 = cfgs[0].precision == HCA_FP64;
+  h->n_drugs = cfgs[0].n_drugs;
+  h->stream = (cudaStream_t)cfgs[0].stream;
+  h->cfgs.assign(cfgs, cfgs + n);
+  cudaGetDevice(&h->device);
+  int sm = 0;
+  cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, h->device);
+  h->ctx.sm_count = sm > 0 ? sm : 1;
+
+  // layout
+  long long off = 0, loff = 0;
+  int chunk0 = 0;
+  for (int i = 0; i < n; ++i) {
+    RepDesc r = make_desc(cfgs[i]);
+    r.off = off;
+    off += ((long long)r.nxp * r.ny * r.nz + kFieldAlign - 1) / kFieldAlign * kFieldAlign;
+    const int rows = r.ny * r.nz;
+    r.chunk_begin = chunk0;
+    r.n_chunks = (rows + hca::CHUNK_ROWS - 1) / hca::CHUNK_ROWS;
+    for (int k = 0; k < r.n_chunks; ++k) h->chunks_h.push_back(make_int2(i, k * hca::CHUNK_ROWS));
+    chunk0 += r.n_chunks;
+    for (int col = 0; col < 27; ++col) {
+      const int cap = colour_count(r.nx, col % 3) * colour_count(r.ny, (col / 3) % 3) * colour_count(r.nz, col / 9);
+      r.list_off[col] = loff;
+      r.list_cap[col] = cap;
+      loff += cap;
+    }
+    h->maxit_all = std::max(h->maxit_all, r.maxit);
+    h->max_outer = std::max(h->max_outer, r.max_outer);
+    h->reps_h.push_back(r);
+  }
+  h->total = off;
+  h->lists_total = loff;
+
+  Ctx& c = h->ctx;
+  c.n_reps = n;
+  c.n_chunks = chunk0;
+  c.threads = cfgs[0].threads_per_block ? cfgs[0].threads_per_block : 256;
+  c.stream = h->stream;
+  const size_t es = elem_size(h);
+  const size_t fbytes = (size_t)h->total * es;
+  int rc = HCA_OK;
+#define ALLOC(ptr, bytes) \
+  if ((rc = dev_alloc(h, &(ptr), (bytes))) != HCA_OK) goto fail
+  {
+    RepDesc* reps_d;
+    int2* chunks_d;
+    ALLOC(reps_d, sizeof(RepDesc) * n);
+    ALLOC(chunks_d, sizeof(int2) * chunk0);
+    c.reps = reps_d;
+    c.chunks = chunks_d;
+    ALLOC(c.state, (size_t)h->total + 16);
+    ALLOC(c.K, fbytes);
+    if (!h->fp64) ALLOC(c.K_lo, fbytes);
+    for (int d = 0; d < h->n_drugs; ++d) ALLOC(c.G[d], fbytes);
+    if (!h->fp64) {
+      for (int d = 0; d < h->n_drugs; ++d) ALLOC(c.G_lo[d], fbytes);
+      ALLOC(c.dx, fbytes);
+    }
+    ALLOC(c.phi, fbytes);
+    ALLOC(c.P, fbytes);
+    ALLOC(c.Vc, fbytes);
+    ALLOC(c.perf, fbytes);
+    ALLOC(c.z, fbytes);
+    ALLOC(c.p, fbytes);
+    ALLOC(c.p_alt, fbytes);
+    ALLOC(c.d, fbytes);
+    ALLOC(c.b, fbytes);
+    ALLOC(c.aux, fbytes);
+    ALLOC(c.partial, sizeof(double) * hca::NDOT * chunk0);
+    ALLOC(c.sync, sizeof(hca::PassSync));
+    ALLOC(c.solve, sizeof(hca::RepSolve) * n);
+    ALLOC(c.stats, sizeof(hca::DevStats) * n);
+    ALLOC(c.step, sizeof(long long));
+    ALLOC(c.lists, sizeof(uint32_t) * (size_t)std::max(1LL, h->lists_total));
+    ALLOC(c.list_count, sizeof(int) * 27 * n);
+    if (cudaMallocHost(&h->h_pinned, 4 * sizeof(int)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      rc = HCA_ERR_OOM;
+      goto fail;
+    }
+    h->h_pinned[0] = h->h_pinned[1] = 0;
+    cudaStream_t s = c.stream;
+    if (cudaMemcpyAsync(reps_d, h->reps_h.data(), sizeof(RepDesc) * n, cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(chunks_d, h->chunks_h.data(), sizeof(int2) * chunk0, cudaMemcpyHostToDevice, s)) {
+      rc = HCA_ERR_CUDA;
+      goto fail;
+    }
+    // zero every device array (padding sites must hold 0)
+    void* zero_list[] = {c.K, c.K_lo, c.G[0], c.G[1], c.G[2], c.G_lo[0], c.G_lo[1], c.G_lo[2], c.dx,
+                         c.phi, c.P, c.Vc, c.perf, c.z, c.p, c.p_alt, c.d, c.b, c.aux};
+    for (void* p : zero_list)
+      if (p && cudaMemsetAsync(p, 0, fbytes, s)) {
+        rc = HCA_ERR_CUDA;
+        goto fail;
+      }
+    if (cudaMemsetAsync(c.state, 0, (size_t)h->total + 16, s) || cudaMemsetAsync(c.sync, 0, sizeof(hca::PassSync), s) ||
+        cudaMemsetAsync(c.solve, 0, sizeof(hca::RepSolve) * n, s) ||
+        cudaMemsetAsync(c.stats, 0, sizeof(hca::DevStats) * n, s) || cudaMemsetAsync(c.step, 0, sizeof(long long), s) ||
+        cudaMemsetAsync(c.list_count, 0, sizeof(int) * 27 * n, s)) {
+      rc = HCA_ERR_CUDA;
+      goto fail;
+    }
+    // maps -> padded float staging buffers
+    float *pc_d = nullptr, *pf_d = nullptr, *pv_d = nullptr;
+    int* err_d = nullptr;
+    const size_t mbytes = (size_t)h->total * sizeof(float);
+    if (cudaMalloc(&pc_d, mbytes) || cudaMalloc(&pf_d, mbytes) || cudaMalloc(&pv_d, mbytes) ||
+        cudaMalloc(&err_d, sizeof(int))) {
+      (void)cudaGetLastError();
+      cudaFree(pc_d);
+      cudaFree(pf_d);
+      cudaFree(pv_d);
+      cudaFree(err_d);
+      rc = HCA_ERR_OOM;
+      goto fail;
+    }
+    bool ok = cudaMemsetAsync(pc_d, 0, mbytes, s) == cudaSuccess && cudaMemsetAsync(pf_d, 0, mbytes, s) == cudaSuccess &&
+              cudaMemsetAsync(pv_d, 0, mbytes, s) == cudaSuccess && cudaMemsetAsync(err_d, 0, sizeof(int), s) == cudaSuccess;
+    for (int i = 0; i < n && ok; ++i) {
+      const RepDesc& r = h->reps_h[i];
+      const float* srcs[3] = {p_cell[i], perf[i], p_vessel[i]};
+      float* dsts[3] = {pc_d, pf_d, pv_d};
+      for (int k = 0; k < 3 && ok; ++k)
+        ok = cudaMemcpy2DAsync(dsts[k] + r.off, (size_t)r.nxp * sizeof(float), srcs[k], (size_t)r.nx * sizeof(float),
+                               (size_t)r.nx * sizeof(float), (size_t)r.ny * r.nz, cudaMemcpyDefault, s) == cudaSuccess;
+    }
+    if (ok) {
+      hca::launch_init(c, pc_d, pf_d, pv_d, err_d, h->fp64);
+      h->launches++;
+      ok = cudaGetLastError() == cudaSuccess;
+    }
+    int err_h = 0;
+    if (ok) ok = cudaMemcpyAsync(&err_h, err_d, sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    if (ok) ok = cudaStreamSynchronize(s) == cudaSuccess;
+    cudaFree(pc_d);
+    cudaFree(pf_d);
+    cudaFree(pv_d);
+    cudaFree(err_d);
+    if (!ok) {
+      (void)cudaGetLastError();
+      rc = HCA_ERR_CUDA;
+      goto fail;
+    }
+    if (err_h) {
+      rc = HCA_ERR_NONFINITE;
+      goto fail;
+    }
+    rc = initial_oxygen(h);
+    if (rc) goto fail;
+    rc = reset_step_stats(h);
+    if (rc) goto fail;
+  }
+#undef ALLOC
+  *out = h;
+  return HCA_OK;
+fail:
+  free_all(h);
+  delete h;
+  return rc;
+}
+
+int copy_field(hca_handle* h, int rep, void* field, size_t es, void* host_or_dev, bool to_user, size_t user_offset_elems) {
+  const RepDesc& r = h->reps_h[rep];
+  char* f = (char*)field + (size_t)r.off * es;
+  char* u = (char*)host_or_dev + user_offset_elems * es;
+  cudaError_t e;
+  if (to_user)
+    e = cudaMemcpy2DAsync(u, (size_t)r.nx * es, f, (size_t)r.nxp * es, (size_t)r.nx * es, (size_t)r.ny * r.nz,
+                          cudaMemcpyDefault, h->ctx.stream);
+  else
+    e = cudaMemcpy2DAsync(f, (size_t)r.nxp * es, u, (size_t)r.nx * es, (size_t)r.nx * es, (size_t)r.ny * r.nz,
+                          cudaMemcpyDefault, h->ctx.stream);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return HCA_ERR_CUDA;
+  }
+  return HCA_OK;
+}
+
+int check_rep(hca_handle* h, int rep) { return (h && rep >= 0 && rep < h->n_reps) ? HCA_OK : HCA_ERR_ARG; }
+
+}  // namespace
+
+// ==================================================================== ABI ==
+extern "C" {
+
+int hca_config_default(hca_config* c, int32_t nx, int32_t ny, int32_t nz) {
+  if (!c) return HCA_ERR_ARG;
+  std::memset(c, 0, sizeof(*c));
+  c->struct_size = sizeof(hca_config);
+  c->nx = nx;
+  c->ny = ny;
+  c->nz = nz;
+  c->precision = HCA_FP64;
+  c->n_drugs = 1;
+  c->seed = 0;
+  c->dx = 10.0;
+  c->dt = 60.0;
+  c->rtol_o2 = 1e-8;
+  c->rtol_drug = 1e-8;
+  c->maxit = 20000;
+  c->ode_substeps = 60;
+  c->picard_tol = 1e-8;
+  c->picard_maxit = 100;
+  c->dose_interval = 21;
+  c->D_K = 1.05e5;
+  c->phi_K = 900.0;
+  c->K1 = 2.5;
+  c->K0 = 20.0;
+  c->r_K = 1.88e4;
+  for (int d = 0; d < 3; ++d) {
+    c->D_G[d] = 9.6e3;
+    c->psi_G[d] = 1e-2;
+    c->kappa_G[d] = 2.0;
+    c->uptake_G[d] = 0.0;
+    c->dose_peak[d] = 1.0;
+    c->kill_b[d] = 1;
+  }
+  c->plasma_decay[0] = 3.93e3 / 2430e3;  // cl3 / u, cyclophosphamide
+  c->plasma_decay[1] = 0.983e3 / 18e3;   // cl2 / w1, epirubicin elimination
+  c->plasma_decay[2] = 1.75 / 27.0;      // v_max / k_m, fluorouracil, linear regime
+  c->T_cycle = 3.74 * 24 * 60;
+  c->K_phi = 1.4;
+  c->k1 = 4e-4;
+  c->k1p = 0.01;
+  c->K_p53 = 0.01;
+  c->k2 = 2e-3;
+  c->k2p = 0.01;
+  c->k2pp = -2e-4;
+  c->J5 = 0.04;
+  c->K_V = 0.01;
+  c->rtol_inner = 1e-3;
+  c->max_outer = 8;
+  c->warm_start = HCA_WS_PREV;
+  c->threads_per_block = 0;
+  c->stream = nullptr;
+  return HCA_OK;
+}
+
+int hca_create(const hca_config* cfg, const float* p_cell, const float* perf, const float* p_vessel,
+               int32_t maps_on_device, hca_handle** out) {
+  if (!cfg) return HCA_ERR_ARG;
+  return create_impl(1, cfg, &p_cell, &perf, &p_vessel, maps_on_device, out);
+}
+
+int hca_create_batch(int32_t n, const hca_config* cfgs, const float* const* p_cell, const float* const* perf,
+                     const float* const* p_vessel, int32_t maps_on_device, hca_handle** out) {
+  return create_impl(n, cfgs, p_cell, perf, p_vessel, maps_on_device, out);
+}
+
+int hca_step(hca_handle* h, int32_t n_steps) {
+  if (!h || n_steps < 0) return HCA_ERR_ARG;
+  for (int s = 0; s < n_steps; ++s) {
+    int rc = run_stages(h, HCA_STAGE_ALL);
+    if (rc) return rc;
+  }
+  return n_steps > 0 ? check_convergence(h) : HCA_OK;
+}
+
+int hca_stage(hca_handle* h, uint32_t mask) {
+  if (!h || (mask & ~HCA_STAGE_ALL)) return HCA_ERR_ARG;
+  int rc = run_stages(h, mask);
+  if (rc) return rc;
+  return check_convergence(h);
+}
+
+int hca_read_fields(hca_handle* h, int32_t rep, uint32_t mask, void* dst, size_t dst_bytes, int32_t dst_on_device) {
+  if (check_rep(h, rep) || !dst || (mask & ~0xFFu) || !mask) return HCA_ERR_ARG;
+  const RepDesc& r = h->reps_h[rep];
+  const size_t es = elem_size(h);
+  const size_t per = (size_t)r.nx * r.ny * r.nz;
+  size_t k = 0;
+  for (uint32_t bit = 1; bit <= 0x80u; bit <<= 1)
+    if (mask & bit) {
+      if (!field_ptr(h, bit)) return HCA_ERR_ARG;
+      ++k;
+    }
+  if (dst_bytes < k * per * es) return HCA_ERR_ARG;
+  (void)dst_on_device;
+  size_t slot = 0;
+  for (uint32_t bit = 1; bit <= 0x80u; bit <<= 1) {
+    if (!(mask & bit)) continue;
+    int rc = copy_field(h, rep, field_ptr(h, bit), es, dst, true, slot * per);
+    if (rc) return rc;
+    ++slot;
+  }
+  HCA_TRY(cudaStreamSynchronize(h->ctx.stream));
+  return HCA_OK;
+}
+
+int hca_write_fields(hca_handle* h, int32_t rep, uint32_t mask, const void* src, size_t src_bytes,
+                     int32_t src_on_device) {
+  if (check_rep(h, rep) || !src || (mask & ~0xFFu) || !mask) return HCA_ERR_ARG;
+  const RepDesc& r = h->reps_h[rep];
+  const size_t es = elem_size(h);
+  const size_t per = (size_t)r.nx * r.ny * r.nz;
+  size_t k = 0;
+  for (uint32_t bit = 1; bit <= 0x80u; bit <<= 1)
+    if (mask & bit) {
+      if (!field_ptr(h, bit)) return HCA_ERR_ARG;
+      ++k;
+    }
+  if (src_bytes < k * per * es) return HCA_ERR_ARG;
+  (void)src_on_device;
+  size_t slot = 0;
+  for (uint32_t bit = 1; bit <= 0x80u; bit <<= 1) {
+    if (!(mask & bit)) continue;
+    int rc = copy_field(h, rep, field_ptr(h, bit), es, const_cast<void*>(src), false, slot * per);
+    if (rc) return rc;
+    void* lo = nullptr;
+    if (bit == HCA_FIELD_O2) lo = h->ctx.K_lo;
+    for (int d = 0; d < h->n_drugs; ++d)
+      if (bit == (HCA_FIELD_DRUG0 << d)) lo = h->ctx.G_lo[d];
+    if (lo) {
+      // a written field replaces any low-order correction word
+      const RepDesc& rr = h->reps_h[rep];
+      HCA_TRY(cudaMemsetAsync((char*)lo + (size_t)rr.off * es, 0, (size_t)rr.nxp * rr.ny * rr.nz * es, h->ctx.stream));
+    }
+    ++slot;
+  }
+  HCA_TRY(cudaStreamSynchronize(h->ctx.stream));
+  return HCA_OK;
+}
+
+int hca_read_states(hca_handle* h, int32_t rep, uint8_t* dst, size_t dst_bytes, int32_t dst_on_device) {
+  if (check_rep(h, rep) || !dst) return HCA_ERR_ARG;
+  const RepDesc& r = h->reps_h[rep];
+  if (dst_bytes < (size_t)r.nx * r.ny * r.nz) return HCA_ERR_ARG;
+  (void)dst_on_device;
+  HCA_TRY(cudaMemcpy2DAsync(dst, (size_t)r.nx, h->ctx.state + r.off, (size_t)r.nxp, (size_t)r.nx, (size_t)r.ny * r.nz,
+                            cudaMemcpyDefault, h->ctx.stream));
+  HCA_TRY(cudaStreamSynchronize(h->ctx.stream));
+  return HCA_OK;
+}
+
+int hca_write_states(hca_handle* h, int32_t rep, const uint8_t* src, size_t src_bytes, int32_t src_on_device) {
+  if (check_rep(h, rep) || !src) return HCA_ERR_ARG;
+  const RepDesc& r = h->reps_h[rep];
+  if (src_bytes < (size_t)r.nx * r.ny * r.nz) return HCA_ERR_ARG;
+  (void)src_on_device;
+  HCA_TRY(cudaMemcpy2DAsync(h->ctx.state + r.off, (size_t)r.nxp, src, (size_t)r.nx, (size_t)r.nx, (size_t)r.ny * r.nz,
+                            cudaMemcpyDefault, h->ctx.stream));
+  HCA_TRY(cudaStreamSynchronize(h->ctx.stream));
+  return HCA_OK;
+}
+
+int hca_set_step(hca_handle* h, int64_t step) {
+  if (!h || step < 0) return HCA_ERR_ARG;
+  long long v = step;
+  HCA_TRY(cudaMemcpyAsync(h->ctx.step, &v, sizeof(v), cudaMemcpyHostToDevice, h->ctx.stream));
+  HCA_TRY(cudaStreamSynchronize(h->ctx.stream));
+  h->step = step;
+  return HCA_OK;
+}
+
+int hca_get_stats(hca_handle* h, int32_t rep, hca_stats* out) {
+  if (check_rep(h, rep) || !out) return HCA_ERR_ARG;
+  Ctx& c = h->ctx;
+  for (int r = 0; r < h->n_reps; ++r)
+    HCA_TRY(cudaMemsetAsync(&c.stats[r].counts[0], 0, sizeof(long long) * 6, c.stream));
+  HCA_LAUNCH(h, HCA_KCLASS_OTHER, 1, hca::launch_histogram(c));
+  hca::DevStats st;
+  HCA_TRY(cudaMemcpyAsync(&st, &c.stats[rep], sizeof(st), cudaMemcpyDeviceToHost, c.stream));
+  HCA_TRY(cudaStreamSynchronize(c.stream));
+  std::memset(out, 0, sizeof(*out));
+  out->step = h->step;
+  out->picard_iterations = h->picard_iterations;
+  out->o2_iterations = st.iters[0];
+  out->o2_sweeps = st.sweeps[0];
+  for (int d = 0; d < 3; ++d) {
+    out->drug_iterations[d] = st.iters[1 + d];
+    out->drug_rel_residual[d] = st.rel[1 + d];
+  }
+  out->o2_rel_residual = st.rel[0];
+  out->not_converged = st.not_converged;
+  out->committed = st.committed;
+  out->kills = st.kills;
+  out->divisions = st.divisions;
+  out->blocked = st.blocked;
+  for (int k = 0; k < 6; ++k) out->counts[k] = st.counts[k];
+  return HCA_OK;
+}
+
+int hca_apply_operator(hca_handle* h, int32_t rep, int32_t which, const void* u, void* out, int32_t on_device) {
+  if (check_rep(h, rep) || !u || !out || which < 0 || which > h->n_drugs) return HCA_ERR_ARG;
+  (void)on_device;
+  const size_t es = elem_size(h);
+  int rc = copy_field(h, rep, h->ctx.p, es, const_cast<void*>(u), false, 0);
+  if (rc) return rc;
+  HCA_LAUNCH(h, HCA_KCLASS_OTHER, 1, hca::launch_apply(h->ctx, which, rep, h->ctx.p, h->ctx.z, h->fp64));
+  rc = copy_field(h, rep, h->ctx.z, es, out, true, 0);
+  if (rc) return rc;
+  // restore the invariant that padding holds 0 in p (u had none) and clear p
+  HCA_TRY(cudaMemsetAsync(h->ctx.p, 0, (size_t)h->total * es, h->ctx.stream));
+  HCA_TRY(cudaStreamSynchronize(h->ctx.stream));
+  return HCA_OK;
+}
+
+int hca_philox_uniforms(uint64_t seed, uint64_t site_begin, int64_t n, uint32_t step, uint32_t purpose, float* dst,
+                        int32_t dst_on_device) {
+  if (!dst || n < 0) return HCA_ERR_ARG;
+  if (n == 0) return HCA_OK;
+  float* d = dst;
+  if (!dst_on_device) {
+    if (cudaMalloc(&d, (size_t)n * sizeof(float)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return HCA_ERR_OOM;
+    }
+  }
+  hca::launch_philox_uniforms(seed, site_begin, n, step, purpose, d, 0);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && !dst_on_device) e = cudaMemcpy(dst, d, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (!dst_on_device) cudaFree(d);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return HCA_ERR_CUDA;
+  }
+  return HCA_OK;
+}
+
+int hca_sync(hca_handle* h) {
+  if (!h) return HCA_ERR_ARG;
+  HCA_TRY(cudaStreamSynchronize(h->ctx.stream));
+  return HCA_OK;
+}
+
+int hca_get_shape(hca_handle* h, int32_t rep, int32_t* nx, int32_t* ny, int32_t* nz) {
+  if (!h) return HCA_ERR_ARG;
+  if (rep < 0) return h->n_reps;
+  if (check_rep(h, rep)) return HCA_ERR_ARG;
+  if (nx) *nx = h->reps_h[rep].nx;
+  if (ny) *ny = h->reps_h[rep].ny;
+  if (nz) *nz = h->reps_h[rep].nz;
+  return HCA_OK;
+}
+
+int64_t hca_launch_count(hca_handle* h) { return h ? h->launches : -1; }
+
+int hca_profile_enable(hca_handle* h, int32_t enable) {
+  if (!h) return HCA_ERR_ARG;
+  Profiler& P = h->prof;
+  int rc = prof_flush(h);
+  if (rc) return rc;
+  if (enable && P.pool.empty()) {
+    P.pool.resize(2 * kPairs);
+    for (auto& e : P.pool)
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return HCA_ERR_CUDA;
+      }
+  }
+  for (int k = 0; k < HCA_NKCLASS; ++k) {
+    P.launches[k] = 0;
+    P.ms[k] = 0.0;
+  }
+  P.on = enable != 0;
+  return HCA_OK;
+}
+
+int hca_get_profile(hca_handle* h, hca_profile* out) {
+  if (!h || !out) return HCA_ERR_ARG;
+  int rc = prof_flush(h);
+  if (rc) return rc;
+  for (int k = 0; k < HCA_NKCLASS; ++k) {
+    out->launches[k] = h->prof.launches[k];
+    out->ms[k] = h->prof.ms[k];
+  }
+  return HCA_OK;
+}
+
+void hca_destroy(hca_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->ctx.stream);
+  free_all(h);
+  delete h;
+}
+
+const char* hca_status_string(int32_t s) {
+  switch (s) {
+    case HCA_OK: return "ok";
+    case HCA_ERR_ARG: return "invalid argument";
+    case HCA_ERR_CUDA: return "CUDA runtime error";
+    case HCA_ERR_OOM: return "device memory exhausted";
+    case HCA_ERR_NONFINITE: return "non-finite value in an input or a solver norm";
+    case HCA_ERR_NOCONV: return "a CG solve reached maxit";
+    case HCA_ERR_TIMEOUT: return "a bounded device wait gave up";
+    case HCA_ERR_UNIMPLEMENTED: return "not implemented";
+    case HCA_ERR_STATE: return "call not valid in the current state";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,330 @@
+// Internal device/host definitions shared by the library's translation units.
+//
+// Data layout (HBM): every field of every replicate lives in one array per
+// field.  Replicate r's site (x, y, z) is element off_r + x + nxp_r*(y + ny_r*z)
+// where nxp_r = nx_r rounded up to a multiple of 4, so each row starts on a
+// 16-byte (float) / 32-byte (double) boundary and a thread moves 4 sites with
+// one vector access.  Sites x >= nx are padding: they hold 0 in every field
+// and are masked out of every update and reduction.
+//
+// Work decomposition: the (y, z) rows of a replicate are cut into fixed
+// chunks of CHUNK_ROWS consecutive rows (row j = y + ny*z).  One thread block
+// processes one chunk.  Inner products are summed per row in a fixed lane
+// order, per chunk in a fixed tree, and per replicate over its chunks in a
+// fixed order, so every reduction result is a function of the lattice alone:
+// it does not depend on the block size chosen by the autotuner or on the
+// other replicates of a batch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hca.h"
+
+namespace hca {
+
+constexpr int VEC = 4;          // sites per thread access
+constexpr int CHUNK_ROWS = 32;  // rows per reduction chunk
+constexpr int NDOT = 3;         // inner products carried per pass
+constexpr int MAX_DRUGS = 3;
+constexpr int FINAL_LANES = 256;  // virtual lanes of the per-replicate final reduction
+
+// ---------------------------------------------------------------- params --
+// Per-replicate constants, read-only on the device.
+struct RepDesc {
+  int nx, ny, nz, nxp;
+  long long off;          // element offset of site (0,0,0)
+  int gpr;                // 4-site groups per row = nxp / 4
+  int lpr;                // lanes per row (power of two, <= 32)
+  int chunk_begin;        // first chunk of this replicate in the chunk table
+  int n_chunks;
+  unsigned long long seed;
+  int n_drugs;
+  int maxit;
+  double rtol_o2, rtol_drug, rtol_inner;
+  int max_outer;          // defect-correction sweeps per solve (FP32 storage); 0 = plain FP32 CG
+  // oxygen (Eq. oxygen)
+  double c_o2;            // D_K / dx^2
+  double phi_K, K1, K0, r_K;
+  // drugs (Eq. chemo), implicit Euler
+  double c_drug[MAX_DRUGS];   // D_G / dx^2
+  double base_drug[MAX_DRUGS];// 1/dt + psi_G
+  double inv_dt;
+  double kappa[MAX_DRUGS];
+  double uptake[MAX_DRUGS];
+  double dose_peak[MAX_DRUGS];
+  double plasma_decay[MAX_DRUGS];
+  double dose_interval_min;  // minutes between boluses
+  int kill_b[MAX_DRUGS];
+  // cell ODEs
+  double dt, T_cycle, K_phi, k1, k1p, K_p53, k2, k2p, k2pp, J5, K_V;
+  int ode_substeps;
+  // CA colour lists: capacity offsets per colour (in the replicate's segment)
+  long long list_off[27];
+  int list_cap[27];
+};
+
+// Per-replicate CG scalars, rewritten by each solve.
+struct RepSolve {
+  double rho;      // r.z
+  double alpha, beta;
+  double bnorm2, rnorm2, rtol;
+  double rel_true;
+  int iters;
+  int active;
+  int zero_b;
+  int maxit;
+  int outer;       // defect-correction sweeps done in this solve
+  int dc_apply;    // 1: the last inner solve's correction is to be added
+  int pad[2];
+};
+
+// Per-replicate statistics written by kernels; copied out by hca_get_stats.
+struct DevStats {
+  long long committed, kills, divisions, blocked;
+  long long counts[6];
+  int iters[1 + MAX_DRUGS];
+  int sweeps[1 + MAX_DRUGS];
+  int not_converged;
+  double rel[1 + MAX_DRUGS];
+  int nonfinite;
+  int pad;
+};
+
+// Shared state for the last-block finalisation of a pass.
+struct PassSync {
+  unsigned int ticket;
+  int active_count;     // replicates still iterating after the last pass B
+  int error;            // nonzero: a norm became NaN/Inf
+  int pad;
+};
+
+// ------------------------------------------------------------- vectors ---
+template <typename T> struct V4 { T a[4]; };
+
+__device__ __forceinline__ V4<float> ld4(const float* p) {
+  float4 v = *reinterpret_cast<const float4*>(p);
+  return V4<float>{{v.x, v.y, v.z, v.w}};
+}
+__device__ __forceinline__ V4<double> ld4(const double* p) {
+  double2 u = reinterpret_cast<const double2*>(p)[0];
+  double2 v = reinterpret_cast<const double2*>(p)[1];
+  return V4<double>{{u.x, u.y, v.x, v.y}};
+}
+__device__ __forceinline__ void st4(float* p, const V4<float>& v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v.a[0], v.a[1], v.a[2], v.a[3]);
+}
+__device__ __forceinline__ void st4(double* p, const V4<double>& v) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v.a[0], v.a[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v.a[2], v.a[3]);
+}
+template <typename T> __device__ __forceinline__ V4<T> zero4() { return V4<T>{{T(0), T(0), T(0), T(0)}}; }
+
+__device__ __forceinline__ uchar4 ld_state4(const uint8_t* p) {
+  return *reinterpret_cast<const uchar4*>(p);
+}
+__device__ __forceinline__ uint8_t st_at(const uchar4& s, int k) {
+  return k == 0 ? s.x : (k == 1 ? s.y : (k == 2 ? s.z : s.w));
+}
+
+// state classes
+__device__ __forceinline__ bool is_consumer(uint8_t s) {
+  return s == HCA_PROLIF || s == HCA_QUIESC || s == HCA_STROMA;
+}
+__device__ __forceinline__ bool is_cancer(uint8_t s) { return s == HCA_PROLIF || s == HCA_QUIESC; }
+__device__ __forceinline__ bool is_vessel(uint8_t s) { return s == HCA_VESSEL; }
+__device__ __forceinline__ bool is_free(uint8_t s) { return s == HCA_EMPTY || s == HCA_DEAD; }
+
+// ------------------------------------------------------------- philox ---
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplies with Weyl key increments between rounds.
+struct Philox4 { uint32_t w[4]; };
+
+__host__ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                          uint32_t c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long p0 = 0xD2511F53ull * (unsigned long long)c0;
+    const unsigned long long p1 = 0xCD9E8D57ull * (unsigned long long)c2;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return Philox4{{c0, c1, c2, c3}};
+}
+
+// 24-bit uniform in [0, 1), exact in float: (w0 >> 8) * 2^-24.
+__host__ __device__ __forceinline__ float site_uniform(unsigned long long seed, unsigned long long site,
+                                                       uint32_t step, uint32_t purpose) {
+  Philox4 o = philox4x32_10((uint32_t)site, (uint32_t)(site >> 32), step, purpose, (uint32_t)seed,
+                            (uint32_t)(seed >> 32));
+  return (float)(o.w[0] >> 8) * 5.9604644775390625e-08f;
+}
+
+enum Purpose : uint32_t { PURPOSE_VESSEL = 0, PURPOSE_CANCER = 1, PURPOSE_PHI = 2, PURPOSE_KILL = 3 };
+
+// ------------------------------------------------------ row iteration ---
+// Geometry of one row (y, z) of replicate rd.
+struct RowGeo {
+  long long base;   // element index of (0, y, z)
+  long long sy, sz; // strides to the y and z neighbour rows
+  int y, z;
+  bool ym, yp, zm, zp;  // neighbour rows inside the box
+};
+
+__device__ __forceinline__ RowGeo row_geo(const RepDesc& rd, int j) {
+  RowGeo g;
+  g.y = j % rd.ny;
+  g.z = j / rd.ny;
+  g.sy = rd.nxp;
+  g.sz = (long long)rd.nxp * rd.ny;
+  g.base = rd.off + (long long)j * rd.nxp;
+  g.ym = g.y > 0;
+  g.yp = g.y < rd.ny - 1;
+  g.zm = g.z > 0;
+  g.zp = g.z < rd.nz - 1;
+  return g;
+}
+
+__device__ __forceinline__ int neighbour_count(const RepDesc& rd, const RowGeo& g, int x) {
+  return (x > 0) + (x < rd.nx - 1) + g.ym + g.yp + g.zm + g.zp;
+}
+
+// Sum of a lane-partial double over the `lpr` lanes of a row segment (fixed
+// xor tree; every lane of the warp must call it).
+__device__ __forceinline__ double row_reduce(double v, int lpr) {
+  for (int o = lpr >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 32);
+  return v;
+}
+
+// Fixed-order block epilogue: rows[CHUNK_ROWS][NDOT] (shared) -> one partial
+// per inner product for this chunk, written to partial[chunk * NDOT + k].
+// Then the last block to finish (ticket) reduces every replicate's chunk
+// partials in fixed order and calls `fin(rep, sums)` once per replicate (from
+// one thread); fin returns 1 if the replicate's solve stays active, and the
+// number of active replicates is left in sync->active_count.  `ndot` inner
+// products are carried.
+template <class Fin>
+__device__ __forceinline__ void chunk_epilogue(double (*rows)[NDOT], int ndot, int chunk,
+                                               double* __restrict__ partial, PassSync* sync,
+                                               const RepDesc* __restrict__ reps, int n_reps,
+                                               Fin fin) {
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    for (int k = 0; k < ndot; ++k) {
+      double v = rows[lane][k];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) partial[(long long)chunk * NDOT + k] = v;
+    }
+  }
+  __shared__ unsigned int s_ticket;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_ticket = atomicAdd(&sync->ticket, 1u);
+  }
+  __syncthreads();
+  if (s_ticket != gridDim.x - 1) return;
+  __threadfence();
+  // last block: fixed-order reduction per replicate.  256 virtual lanes
+  // (independent of the block size) each sum chunks v, v + 256, ... in
+  // order; lane sums are then combined by a fixed tree.
+  __shared__ double s_vl[FINAL_LANES][NDOT];
+  const int nthr = blockDim.x;
+  int n_active = 0;
+  for (int r = 0; r < n_reps; ++r) {
+    const RepDesc& rd = reps[r];
+    for (int v = threadIdx.x; v < FINAL_LANES; v += nthr) {
+      double acc[NDOT] = {0.0, 0.0, 0.0};
+      for (int c = v; c < rd.n_chunks; c += FINAL_LANES) {
+        const long long idx = (long long)(rd.chunk_begin + c) * NDOT;
+        for (int k = 0; k < ndot; ++k) acc[k] += __ldcg(partial + idx + k);
+      }
+      for (int k = 0; k < NDOT; ++k) s_vl[v][k] = acc[k];
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double sums[NDOT] = {0.0, 0.0, 0.0};
+      for (int k = 0; k < ndot; ++k) {
+        double v = 0.0;
+        for (int i = lane; i < FINAL_LANES; i += 32) v += s_vl[i][k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        sums[k] = v;
+      }
+      if (lane == 0) n_active += fin(r, sums);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    sync->active_count = n_active;
+    __threadfence();
+    sync->ticket = 0u;
+  }
+}
+
+// -------------------------------------------------------------- launch --
+struct LaunchCfg {
+  int threads;        // block size
+  cudaStream_t stream;
+};
+
+}  // namespace hca
+
+namespace hca {
+
+// Device pointers and launch parameters of one handle, passed by value to
+// every kernel.  Field pointers are typed per precision by the kernels.
+struct Ctx {
+  const RepDesc* reps;
+  int n_reps;
+  const int2* chunks;  // (replicate, first row) per chunk
+  int n_chunks;
+  int threads;
+  int sm_count;
+  cudaStream_t stream;
+  uint8_t* state;
+  void* K;       // oxygen
+  void* K_lo;    // FP32 scheme: low-order words of the solved fields
+  void* G[MAX_DRUGS];
+  void* G_lo[MAX_DRUGS];
+  void* dx;      // FP32 scheme: correction of the inner solve
+  void* aux;     // scratch field (previous iterate of the initial oxygen fixed point)
+  void* phi;
+  void* P;
+  void* Vc;
+  void* perf;
+  void* z;       // preconditioned residual z = r / d
+  void* p;       // search direction (two buffers: pass A reads one, writes the other)
+  void* p_alt;
+  void* d;       // operator diagonal
+  void* b;       // right-hand side (drugs) / defect (oxygen correction solve)
+  double* partial;
+  PassSync* sync;
+  RepSolve* solve;
+  DevStats* stats;
+  long long* step;        // device step counter n
+  uint32_t* lists;
+  int* list_count;        // [rep][27]
+};
+
+// Operator selector: 0 = oxygen, 1 + d = drug d.
+__device__ __forceinline__ double op_coupling(const RepDesc& rd, int which) {
+  return which == 0 ? rd.c_o2 : rd.c_drug[which - 1];
+}
+
+// Plasma level G_{d,0}(t) after boluses at 0, I dt, 2 I dt, ... (closed form
+// of the one-compartment model, doses superposed).
+__device__ __forceinline__ double plasma_level(double t, double peak, double decay, double interval) {
+  if (t < 0.0) return 0.0;
+  double total = 0.0;
+  for (long long n = 0; (double)n * interval <= t; ++n) {
+    total += peak * exp(-decay * (t - (double)n * interval));
+    if (interval <= 0.0) break;
+  }
+  return total;
+}
+
+}  // namespace hca

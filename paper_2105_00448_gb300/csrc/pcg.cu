@@ -1,0 +1,813 @@
+// Matrix-free 7-point operators and the Jacobi-preconditioned CG passes for
+// the oxygen (Eq. oxygen, s_K = 0, consumption linearised about the previous
+// K as in Section 2.4.1) and drug (Eq. chemo, one implicit-Euler step) solves.
+//
+// Operator at site i (Neumann boundaries: out-of-box neighbours are omitted):
+//     (A u)_i = d_i u_i - c * sum_{j in box, |i-j| = 1} u_j,
+//     d_i = c * n_i + a_i,      c = D / dx^2,  n_i = in-box neighbour count,
+//     oxygen: a_i = phi_K / (K1 + K_prev,i) [consumer] + r_K [vessel],  b_i = r_K K0 [vessel]
+//     drug:   a_i = 1/dt + psi + kappa perf_i [vessel] + uptake [cancer],
+//             b_i = G^n_i / dt + kappa perf_i G_0(t^{n+1}) [vessel].
+//
+// CG is carried in the preconditioned residual z = r / d instead of r, so
+// the direction update p = z + beta p needs no division at neighbour sites:
+//   pass A: p = z + beta p;  q = A p (q recomputed, not stored);  sigma = p.q
+//   pass B: q = A p;  x += alpha p;  z -= alpha q / d;  rho = r.z = sum d z^2,
+//           |r|^2 = sum (d z)^2
+// HBM traffic per site and iteration: pass A reads z, p, d and writes p;
+// pass B reads p, d, x, z and writes x, z: 10 values = 40 B (FP32).
+// Neighbour rows are re-read through L1/L2.  Pass A rebuilds the new
+// direction at neighbour sites from the old one, so the old and new
+// directions live in two buffers that swap roles every iteration (an in-place
+// update would let one block read a neighbour row another block has already
+// overwritten).
+#include "hca_internal.cuh"
+
+namespace hca {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename T>
+__device__ __forceinline__ V4<T> ld4_if(const T* p, bool ok) {
+  return ok ? ld4(p) : zero4<T>();
+}
+
+template <typename T>
+__device__ __forceinline__ T sel(const V4<T>& v, int k) {
+  return v.a[k];
+}
+
+// Neighbours of a 4-site group along x.  `v` is this lane's group; lanes of a
+// row segment hold consecutive groups.  carry holds the last site of the
+// previous iteration's last lane.  right_at() loads the site after the group
+// for the segment's last lane.
+template <typename T, class RightAt>
+__device__ __forceinline__ void x_neighbours(const V4<T>& v, int g, int gpr, int sl, int lpr, bool gok,
+                                             T& carry, T& left, T& right, RightAt right_at) {
+  const T up = __shfl_up_sync(FULL, v.a[3], 1, lpr);
+  const T dn = __shfl_down_sync(FULL, v.a[0], 1, lpr);
+  left = sl > 0 ? up : (g > 0 ? carry : T(0));
+  if (sl < lpr - 1) right = dn;
+  else right = (gok && g + 1 < gpr) ? right_at() : T(0);
+  carry = __shfl_sync(FULL, v.a[3], lpr - 1, lpr);
+}
+
+template <typename T>
+__device__ __forceinline__ T nb_sum(const V4<T>& v, int k, T left, T right, const V4<T>& ym, const V4<T>& yp,
+                                    const V4<T>& zm, const V4<T>& zp) {
+  const T l = k == 0 ? left : v.a[k - 1];
+  const T r = k == 3 ? right : v.a[k + 1];
+  return ((l + r) + (ym.a[k] + yp.a[k])) + (zm.a[k] + zp.a[k]);
+}
+
+// Diagonal of the operator at one site.
+template <typename T, int KIND>
+__device__ __forceinline__ T diag_site(const RepDesc& rd, int which, int n_nb, uint8_t s, T K_prev, T pf) {
+  const T cpl = (T)op_coupling(rd, which);
+  T a;
+  if (KIND == 0) {
+    a = is_consumer(s) ? (T)rd.phi_K / ((T)rd.K1 + K_prev) : T(0);
+    if (is_vessel(s)) a += (T)rd.r_K;
+  } else {
+    const int dd = which - 1;
+    a = (T)rd.base_drug[dd];
+    if (is_vessel(s)) a += (T)rd.kappa[dd] * pf;
+    if (is_cancer(s)) a += (T)rd.uptake[dd];
+  }
+  return cpl * (T)n_nb + a;
+}
+
+// Zero the per-row partial sums of the block.
+__device__ __forceinline__ void clear_rows(double (*rows)[NDOT]) {
+  for (int i = threadIdx.x; i < CHUNK_ROWS * NDOT; i += blockDim.x) (&rows[0][0])[i] = 0.0;
+  __syncthreads();
+}
+
+__device__ __forceinline__ void store_row(double (*rows)[NDOT], int rl, bool row_ok, int sl, int lpr,
+                                          double* acc, int ndot) {
+  for (int k = 0; k < ndot; ++k) {
+    const double v = row_reduce(acc[k], lpr);
+    if (row_ok && sl == 0) rows[rl][k] = v;
+  }
+}
+
+struct RowIter {
+  int warp, lane, lpr, rpw, sub, sl, nw, niter;
+};
+__device__ __forceinline__ RowIter row_iter(const RepDesc& rd) {
+  RowIter it;
+  it.warp = threadIdx.x >> 5;
+  it.lane = threadIdx.x & 31;
+  it.lpr = rd.lpr;
+  it.rpw = 32 / rd.lpr;
+  it.sub = it.lane / rd.lpr;
+  it.sl = it.lane % rd.lpr;
+  it.nw = blockDim.x >> 5;
+  it.niter = (rd.gpr + rd.lpr - 1) / rd.lpr;
+  return it;
+}
+
+// ------------------------------------------------------------------ setup --
+// r = b - A x0 with x0 the current field; writes d, z = r/d (and b for drugs);
+// reduces rho = r.z, |r|^2, |b|^2.
+template <typename T, int KIND>
+__global__ void __launch_bounds__(512) k_setup(Ctx c, int which) {
+  __shared__ double rows[CHUNK_ROWS][NDOT];
+  __shared__ double s_G0;
+  const int2 ch = c.chunks[blockIdx.x];
+  const RepDesc& rd = c.reps[ch.x];
+  clear_rows(rows);
+  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const T* __restrict__ x = KIND == 0 ? (const T*)c.K : (const T*)c.G[which - 1];
+  const T* __restrict__ perf = (const T*)c.perf;
+  T* __restrict__ dd = (T*)c.d;
+  T* __restrict__ zz = (T*)c.z;
+  T* __restrict__ bb = (T*)c.b;
+  if (KIND == 1) {
+    if (threadIdx.x == 0) {
+      const int dg = which - 1;
+      const double t_next = ((double)(*c.step) + 1.0) * rd.dt;
+      s_G0 = plasma_level(t_next, rd.dose_peak[dg], rd.plasma_decay[dg], rd.dose_interval_min);
+    }
+    __syncthreads();
+  }
+  const T G0 = KIND == 1 ? (T)s_G0 : T(0);
+  const T cpl = (T)op_coupling(rd, which);
+  const T inv_dt = (T)rd.inv_dt;
+  const T bvessel = (T)(rd.r_K * rd.K0);
+  const RowIter it = row_iter(rd);
+  for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
+    const int rl = rbase + it.sub;
+    const bool row_ok = rl < nrows;
+    const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
+    double acc[NDOT] = {0.0, 0.0, 0.0};
+    T carry = T(0);
+    for (int itn = 0; itn < it.niter; ++itn) {
+      const int g = itn * it.lpr + it.sl;
+      const bool gok = row_ok && g < rd.gpr;
+      const long long e = geo.base + 4LL * g;
+      const V4<T> X = ld4_if(x + e, gok);
+      const V4<T> ym = ld4_if(x + e - geo.sy, gok && geo.ym);
+      const V4<T> yp = ld4_if(x + e + geo.sy, gok && geo.yp);
+      const V4<T> zm = ld4_if(x + e - geo.sz, gok && geo.zm);
+      const V4<T> zp = ld4_if(x + e + geo.sz, gok && geo.zp);
+      T left, right;
+      x_neighbours(X, g, rd.gpr, it.sl, it.lpr, gok, carry, left, right, [&] { return x[e + 4]; });
+      if (gok) {
+        const uchar4 st = ld_state4(c.state + e);
+        V4<T> PF = zero4<T>();
+        if (KIND == 1) PF = ld4(perf + e);
+        V4<T> D, Z, B;
+        T g_rho = 0, g_rr = 0, g_bb = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int xk = 4 * g + k;
+          const uint8_t s = st_at(st, k);
+          T dk = T(0), zk = T(0), bk = T(0);
+          if (xk < rd.nx) {
+            dk = diag_site<T, KIND>(rd, which, neighbour_count(rd, geo, xk), s, X.a[k], PF.a[k]);
+            if (KIND == 0) bk = is_vessel(s) ? bvessel : T(0);
+            else bk = X.a[k] * inv_dt + (is_vessel(s) ? (T)rd.kappa[which - 1] * PF.a[k] * G0 : T(0));
+            const T r = bk - (dk * X.a[k] - cpl * nb_sum(X, k, left, right, ym, yp, zm, zp));
+            zk = dk != T(0) ? r / dk : T(0);   // d = 0 only for an isolated, empty 1-site box
+            g_rho += r * zk;
+            g_rr += r * r;
+            g_bb += bk * bk;
+          }
+          D.a[k] = dk;
+          Z.a[k] = zk;
+          B.a[k] = bk;
+        }
+        st4(dd + e, D);
+        st4(zz + e, Z);
+        if (KIND == 1) st4(bb + e, B);
+        acc[0] += (double)g_rho;
+        acc[1] += (double)g_rr;
+        acc[2] += (double)g_bb;
+      }
+    }
+    store_row(rows, rl, row_ok, it.sl, it.lpr, acc, 3);
+  }
+  const double rtol = KIND == 0 ? rd.rtol_o2 : rd.rtol_drug;
+  (void)rtol;
+  chunk_epilogue(rows, 3, blockIdx.x, c.partial, c.sync, c.reps, c.n_reps,
+                 [&](int r, const double* s3) -> int {
+                   const RepDesc& rr = c.reps[r];
+                   RepSolve& sv = c.solve[r];
+                   const double tol = which == 0 ? rr.rtol_o2 : rr.rtol_drug;
+                   sv.rho = s3[0];
+                   sv.rnorm2 = s3[1];
+                   sv.bnorm2 = s3[2];
+                   sv.alpha = 0.0;
+                   sv.beta = 0.0;
+                   sv.iters = 0;
+                   sv.rtol = tol;
+                   sv.maxit = rr.maxit;
+                   sv.zero_b = s3[2] == 0.0;
+                   const bool fin = isfinite(s3[0]) && isfinite(s3[1]) && isfinite(s3[2]);
+                   if (!fin) c.sync->error = 1;
+                   sv.active = fin && !sv.zero_b && sqrt(s3[1]) > tol * sqrt(s3[2]) && rr.maxit > 0;
+                   return sv.active;
+                 });
+}
+
+// ----------------------------------------------------------------- pass A --
+template <typename T>
+__global__ void __launch_bounds__(512) k_pass_a(Ctx c, int which, const T* __restrict__ p_old,
+                                                T* __restrict__ p_new) {
+  __shared__ double rows[CHUNK_ROWS][NDOT];
+  const int2 ch = c.chunks[blockIdx.x];
+  const RepDesc& rd = c.reps[ch.x];
+  clear_rows(rows);
+  const RepSolve sv = c.solve[ch.x];
+  if (sv.active) {
+    const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+    const T* __restrict__ zz = (const T*)c.z;
+    const T* __restrict__ pp = p_old;
+    const T* __restrict__ dd = (const T*)c.d;
+    const T beta = (T)sv.beta;
+    const bool use_p = sv.beta != 0.0;
+    const T cpl = (T)op_coupling(rd, which);
+    const RowIter it = row_iter(rd);
+    for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
+      const int rl = rbase + it.sub;
+      const bool row_ok = rl < nrows;
+      const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
+      double acc[NDOT] = {0.0, 0.0, 0.0};
+      T carry = T(0);
+      for (int itn = 0; itn < it.niter; ++itn) {
+        const int g = itn * it.lpr + it.sl;
+        const bool gok = row_ok && g < rd.gpr;
+        const long long e = geo.base + 4LL * g;
+        auto pnew = [&](long long o, bool ok) {
+          V4<T> zv = ld4_if(zz + o, ok);
+          if (use_p) {
+            const V4<T> pv = ld4_if(pp + o, ok);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) zv.a[k] += beta * pv.a[k];
+          }
+          return zv;
+        };
+        const V4<T> PN = pnew(e, gok);
+        const V4<T> ym = pnew(e - geo.sy, gok && geo.ym);
+        const V4<T> yp = pnew(e + geo.sy, gok && geo.yp);
+        const V4<T> zm = pnew(e - geo.sz, gok && geo.zm);
+        const V4<T> zp = pnew(e + geo.sz, gok && geo.zp);
+        T left, right;
+        x_neighbours(PN, g, rd.gpr, it.sl, it.lpr, gok, carry, left, right,
+                     [&] { return zz[e + 4] + (use_p ? beta * pp[e + 4] : T(0)); });
+        if (gok) {
+          const V4<T> D = ld4(dd + e);
+          T g_s = 0;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const T q = D.a[k] * PN.a[k] - cpl * nb_sum(PN, k, left, right, ym, yp, zm, zp);
+            g_s += PN.a[k] * q;
+          }
+          st4(p_new + e, PN);
+          acc[0] += (double)g_s;
+        }
+      }
+      store_row(rows, rl, row_ok, it.sl, it.lpr, acc, 1);
+    }
+  }
+  chunk_epilogue(rows, 1, blockIdx.x, c.partial, c.sync, c.reps, c.n_reps,
+                 [&](int r, const double* s1) -> int {
+                   RepSolve& s = c.solve[r];
+                   if (!s.active) return 0;
+                   if (!(s1[0] > 0.0) || !isfinite(s1[0])) {
+                     if (!isfinite(s1[0])) c.sync->error = 1;
+                     s.active = 0;
+                     return 0;
+                   }
+                   s.alpha = s.rho / s1[0];
+                   return 1;
+                 });
+}
+
+// ----------------------------------------------------------------- pass B --
+template <typename T>
+__global__ void __launch_bounds__(512) k_pass_b(Ctx c, int which, const T* __restrict__ pdir, void* xfield) {
+  __shared__ double rows[CHUNK_ROWS][NDOT];
+  const int2 ch = c.chunks[blockIdx.x];
+  const RepDesc& rd = c.reps[ch.x];
+  clear_rows(rows);
+  const RepSolve sv = c.solve[ch.x];
+  if (sv.active) {
+    const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+    T* __restrict__ zz = (T*)c.z;
+    const T* __restrict__ pp = pdir;
+    const T* __restrict__ dd = (const T*)c.d;
+    T* __restrict__ xx = (T*)xfield;
+    const T alpha = (T)sv.alpha;
+    const T cpl = (T)op_coupling(rd, which);
+    const RowIter it = row_iter(rd);
+    for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
+      const int rl = rbase + it.sub;
+      const bool row_ok = rl < nrows;
+      const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
+      double acc[NDOT] = {0.0, 0.0, 0.0};
+      T carry = T(0);
+      for (int itn = 0; itn < it.niter; ++itn) {
+        const int g = itn * it.lpr + it.sl;
+        const bool gok = row_ok && g < rd.gpr;
+        const long long e = geo.base + 4LL * g;
+        const V4<T> P = ld4_if(pp + e, gok);
+        const V4<T> ym = ld4_if(pp + e - geo.sy, gok && geo.ym);
+        const V4<T> yp = ld4_if(pp + e + geo.sy, gok && geo.yp);
+        const V4<T> zm = ld4_if(pp + e - geo.sz, gok && geo.zm);
+        const V4<T> zp = ld4_if(pp + e + geo.sz, gok && geo.zp);
+        T left, right;
+        x_neighbours(P, g, rd.gpr, it.sl, it.lpr, gok, carry, left, right, [&] { return pp[e + 4]; });
+        if (gok) {
+          const V4<T> D = ld4(dd + e);
+          V4<T> X = ld4(xx + e);
+          V4<T> Z = ld4(zz + e);
+          T g_rho = 0, g_rr = 0;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if (4 * g + k < rd.nx) {
+              const T q = D.a[k] * P.a[k] - cpl * nb_sum(P, k, left, right, ym, yp, zm, zp);
+              X.a[k] += alpha * P.a[k];
+              Z.a[k] -= alpha * (q / D.a[k]);
+              const T r = D.a[k] * Z.a[k];
+              g_rho += r * Z.a[k];
+              g_rr += r * r;
+            }
+          }
+          st4(xx + e, X);
+          st4(zz + e, Z);
+          acc[0] += (double)g_rho;
+          acc[1] += (double)g_rr;
+        }
+      }
+      store_row(rows, rl, row_ok, it.sl, it.lpr, acc, 2);
+    }
+  }
+  chunk_epilogue(rows, 2, blockIdx.x, c.partial, c.sync, c.reps, c.n_reps,
+                 [&](int r, const double* s2) -> int {
+                   RepSolve& s = c.solve[r];
+                   if (!s.active) return 0;
+                   s.iters += 1;
+                   if (!isfinite(s2[0]) || !isfinite(s2[1])) {
+                     c.sync->error = 1;
+                     s.active = 0;
+                     return 0;
+                   }
+                   s.beta = s2[0] / s.rho;
+                   s.rho = s2[0];
+                   s.rnorm2 = s2[1];
+                   const bool conv = sqrt(s2[1]) <= s.rtol * sqrt(s.bnorm2);
+                   if (conv || s.iters >= s.maxit) s.active = 0;
+                   return s.active;
+                 });
+}
+
+// ----------------------------------------------------------- true residual --
+// rr = |b - A x|^2 with b rebuilt from the state (oxygen) or read back (drug);
+// zeroes x where b = 0.  Records iterations and the relative residual in the
+// statistics slot `which`.
+template <typename T, int KIND>
+__global__ void __launch_bounds__(512) k_true_residual(Ctx c, int which, void* xfield) {
+  __shared__ double rows[CHUNK_ROWS][NDOT];
+  const int2 ch = c.chunks[blockIdx.x];
+  const RepDesc& rd = c.reps[ch.x];
+  clear_rows(rows);
+  const RepSolve sv = c.solve[ch.x];
+  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  T* __restrict__ xx = (T*)xfield;
+  const T* __restrict__ dd = (const T*)c.d;
+  const T* __restrict__ bb = (const T*)c.b;
+  const T cpl = (T)op_coupling(rd, which);
+  const T bvessel = (T)(rd.r_K * rd.K0);
+  const RowIter it = row_iter(rd);
+  for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
+    const int rl = rbase + it.sub;
+    const bool row_ok = rl < nrows;
+    const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
+    double acc[NDOT] = {0.0, 0.0, 0.0};
+    T carry = T(0);
+    for (int itn = 0; itn < it.niter; ++itn) {
+      const int g = itn * it.lpr + it.sl;
+      const bool gok = row_ok && g < rd.gpr;
+      const long long e = geo.base + 4LL * g;
+      const V4<T> X = ld4_if(xx + e, gok);
+      const V4<T> ym = ld4_if(xx + e - geo.sy, gok && geo.ym);
+      const V4<T> yp = ld4_if(xx + e + geo.sy, gok && geo.yp);
+      const V4<T> zm = ld4_if(xx + e - geo.sz, gok && geo.zm);
+      const V4<T> zp = ld4_if(xx + e + geo.sz, gok && geo.zp);
+      T left, right;
+      x_neighbours(X, g, rd.gpr, it.sl, it.lpr, gok, carry, left, right, [&] { return xx[e + 4]; });
+      if (gok) {
+        const V4<T> D = ld4(dd + e);
+        V4<T> B;
+        if (KIND == 0) {
+          const uchar4 st = ld_state4(c.state + e);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) B.a[k] = is_vessel(st_at(st, k)) ? bvessel : T(0);
+        } else {
+          B = ld4(bb + e);
+        }
+        T g_rr = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (4 * g + k < rd.nx) {
+            const T r = B.a[k] - (D.a[k] * X.a[k] - cpl * nb_sum(X, k, left, right, ym, yp, zm, zp));
+            g_rr += r * r;
+          }
+        }
+        acc[0] += (double)g_rr;
+      }
+    }
+    store_row(rows, rl, row_ok, it.sl, it.lpr, acc, 1);
+  }
+  chunk_epilogue(rows, 1, blockIdx.x, c.partial, c.sync, c.reps, c.n_reps,
+                 [&](int r, const double* s1) -> int {
+                   RepSolve& s = c.solve[r];
+                   DevStats& st = c.stats[r];
+                   s.rel_true = s.zero_b ? 0.0 : sqrt(s1[0] / s.bnorm2);
+                   st.iters[which] += s.iters;
+                   st.rel[which] = s.rel_true;
+                   if (!s.zero_b && !(sqrt(s.rnorm2) <= s.rtol * sqrt(s.bnorm2))) st.not_converged |= 1 << which;
+                   if (!isfinite(s1[0])) {
+                     c.sync->error = 1;
+                     st.nonfinite = 1;
+                   }
+                   return 0;
+                 });
+  (void)sv;
+}
+
+// x = 0 for replicates whose right-hand side vanished.
+template <typename T>
+__global__ void k_zero_if_b_zero(Ctx c, void* xfield) {
+  const int2 ch = c.chunks[blockIdx.x];
+  if (!c.solve[ch.x].zero_b) return;
+  const RepDesc& rd = c.reps[ch.x];
+  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  T* xx = (T*)xfield;
+  const long long base = rd.off + (long long)ch.y * rd.nxp;
+  const long long n = (long long)nrows * rd.nxp;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) xx[base + i] = T(0);
+}
+
+// ---------------------------------------------------------- apply operator --
+// out = A u for one replicate (operator `which`, diagonal rebuilt from the
+// state, the current K and the perfusion map).  Used to expose the stencil.
+template <typename T, int KIND>
+__global__ void __launch_bounds__(512) k_apply(Ctx c, int which, int rep, const T* __restrict__ u,
+                                               T* __restrict__ out) {
+  const int2 ch = c.chunks[blockIdx.x];
+  if (ch.x != rep) return;
+  const RepDesc& rd = c.reps[ch.x];
+  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const T* __restrict__ K = (const T*)c.K;
+  const T* __restrict__ perf = (const T*)c.perf;
+  const T cpl = (T)op_coupling(rd, which);
+  const RowIter it = row_iter(rd);
+  for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
+    const int rl = rbase + it.sub;
+    const bool row_ok = rl < nrows;
+    const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
+    T carry = T(0);
+    for (int itn = 0; itn < it.niter; ++itn) {
+      const int g = itn * it.lpr + it.sl;
+      const bool gok = row_ok && g < rd.gpr;
+      const long long e = geo.base + 4LL * g;
+      const V4<T> U = ld4_if(u + e, gok);
+      const V4<T> ym = ld4_if(u + e - geo.sy, gok && geo.ym);
+      const V4<T> yp = ld4_if(u + e + geo.sy, gok && geo.yp);
+      const V4<T> zm = ld4_if(u + e - geo.sz, gok && geo.zm);
+      const V4<T> zp = ld4_if(u + e + geo.sz, gok && geo.zp);
+      T left, right;
+      x_neighbours(U, g, rd.gpr, it.sl, it.lpr, gok, carry, left, right, [&] { return u[e + 4]; });
+      if (gok) {
+        const uchar4 st = ld_state4(c.state + e);
+        const V4<T> KK = ld4(K + e);
+        const V4<T> PF = ld4(perf + e);
+        V4<T> O;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int xk = 4 * g + k;
+          O.a[k] = T(0);
+          if (xk < rd.nx) {
+            const T dk = diag_site<T, KIND>(rd, which, neighbour_count(rd, geo, xk), st_at(st, k), KK.a[k], PF.a[k]);
+            O.a[k] = dk * U.a[k] - cpl * nb_sum(U, k, left, right, ym, yp, zm, zp);
+          }
+        }
+        st4(out + e, O);
+      }
+    }
+  }
+}
+
+// |a - b|^2 and |a|^2 per replicate (into solve[rep].rnorm2 / bnorm2); used
+// by the fixed-point iteration of the initial oxygen field.
+template <typename T>
+__global__ void __launch_bounds__(512) k_diff_norms(Ctx c, const T* __restrict__ a, const T* __restrict__ b) {
+  __shared__ double rows[CHUNK_ROWS][NDOT];
+  const int2 ch = c.chunks[blockIdx.x];
+  const RepDesc& rd = c.reps[ch.x];
+  clear_rows(rows);
+  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const RowIter it = row_iter(rd);
+  for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
+    const int rl = rbase + it.sub;
+    const bool row_ok = rl < nrows;
+    const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
+    double acc[NDOT] = {0.0, 0.0, 0.0};
+    for (int itn = 0; itn < it.niter; ++itn) {
+      const int g = itn * it.lpr + it.sl;
+      if (row_ok && g < rd.gpr) {
+        const long long e = geo.base + 4LL * g;
+        const V4<T> A = ld4(a + e), B = ld4(b + e);
+        T s0 = 0, s1 = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const T df = A.a[k] - B.a[k];
+          s0 += df * df;
+          s1 += A.a[k] * A.a[k];
+        }
+        acc[0] += (double)s0;
+        acc[1] += (double)s1;
+      }
+    }
+    store_row(rows, rl, row_ok, it.sl, it.lpr, acc, 2);
+  }
+  chunk_epilogue(rows, 2, blockIdx.x, c.partial, c.sync, c.reps, c.n_reps,
+                 [&](int r, const double* s2) -> int {
+                   c.solve[r].rnorm2 = s2[0];
+                   c.solve[r].bnorm2 = s2[1];
+                   return 0;
+                 });
+}
+
+// --------------------------------------------------- defect correction ---
+// FP32 storage scheme.  The solution is kept as two FP32 words, x = x_hi +
+// x_lo.  Each sweep evaluates the residual r = b - A x in FP64 from the FP32
+// operator coefficients (d, c) and the two-word solution, stops the solve when
+// |r| <= rtol |b| (FP64 norms), and otherwise starts an FP32 inner CG on the
+// correction: A dx = fl32(r), dx0 = 0, to the inner tolerance.  The first
+// sweep of a solve also builds and stores d (and b for a drug).
+template <int KIND>
+__global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const float* __restrict__ x_hi,
+                                                     const float* __restrict__ x_lo, int first) {
+  __shared__ double rows[CHUNK_ROWS][NDOT];
+  __shared__ double s_G0;
+  const int2 ch = c.chunks[blockIdx.x];
+  const RepDesc& rd = c.reps[ch.x];
+  clear_rows(rows);
+  const RepSolve sv = c.solve[ch.x];
+  const bool live = first || sv.active || sv.dc_apply;
+  if (KIND == 1 && first) {
+    if (threadIdx.x == 0) {
+      const int dg = which - 1;
+      const double t_next = ((double)(*c.step) + 1.0) * rd.dt;
+      s_G0 = plasma_level(t_next, rd.dose_peak[dg], rd.plasma_decay[dg], rd.dose_interval_min);
+    }
+    __syncthreads();
+  }
+  if (live) {
+    const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+    float* __restrict__ dd = (float*)c.d;
+    float* __restrict__ zz = (float*)c.z;
+    float* __restrict__ bb = (float*)c.b;
+    float* __restrict__ dxv = (float*)c.dx;
+    const float* __restrict__ perf = (const float*)c.perf;
+    const double cpl = (double)(float)op_coupling(rd, which);
+    const float G0 = KIND == 1 && first ? (float)s_G0 : 0.f;
+    const float bvessel = (float)(rd.r_K * rd.K0);
+    const RowIter it = row_iter(rd);
+    auto ldx = [&](long long o, bool ok) {
+      const V4<float> h = ld4_if(x_hi + o, ok), l = ld4_if(x_lo + o, ok);
+      V4<double> r;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) r.a[k] = (double)h.a[k] + (double)l.a[k];
+      return r;
+    };
+    for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
+      const int rl = rbase + it.sub;
+      const bool row_ok = rl < nrows;
+      const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
+      double acc[NDOT] = {0.0, 0.0, 0.0};
+      double carry = 0.0;
+      for (int itn = 0; itn < it.niter; ++itn) {
+        const int g = itn * it.lpr + it.sl;
+        const bool gok = row_ok && g < rd.gpr;
+        const long long e = geo.base + 4LL * g;
+        const V4<double> X = ldx(e, gok);
+        const V4<double> ym = ldx(e - geo.sy, gok && geo.ym);
+        const V4<double> yp = ldx(e + geo.sy, gok && geo.yp);
+        const V4<double> zm = ldx(e - geo.sz, gok && geo.zm);
+        const V4<double> zp = ldx(e + geo.sz, gok && geo.zp);
+        double left, right;
+        x_neighbours(X, g, rd.gpr, it.sl, it.lpr, gok, carry, left, right,
+                     [&] { return (double)x_hi[e + 4] + (double)x_lo[e + 4]; });
+        if (gok) {
+          V4<float> D, B;
+          if (first) {
+            const uchar4 st = ld_state4(c.state + e);
+            V4<float> PF = zero4<float>();
+            if (KIND == 1) PF = ld4(perf + e);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const int xk = 4 * g + k;
+              const uint8_t s = st_at(st, k);
+              D.a[k] = 0.f;
+              B.a[k] = 0.f;
+              if (xk < rd.nx) {
+                // the operator is linearised about the solution at the start of the solve
+                D.a[k] = diag_site<float, KIND>(rd, which, neighbour_count(rd, geo, xk), s, (float)X.a[k], PF.a[k]);
+                if (KIND == 0) B.a[k] = is_vessel(s) ? bvessel : 0.f;
+                else B.a[k] = (float)(X.a[k] * rd.inv_dt) + (is_vessel(s) ? (float)rd.kappa[which - 1] * PF.a[k] * G0 : 0.f);
+              }
+            }
+            st4(dd + e, D);
+            st4(bb + e, B);
+          } else {
+            D = ld4(dd + e);
+            B = ld4(bb + e);
+          }
+          V4<float> Z;
+          double g_rr = 0.0, g_bb = 0.0;
+          float g_rho = 0.f;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            Z.a[k] = 0.f;
+            if (4 * g + k < rd.nx) {
+              const double r = (double)B.a[k] - ((double)D.a[k] * X.a[k] - cpl * nb_sum(X, k, left, right, ym, yp, zm, zp));
+              const float r32 = (float)r;
+              const float zk = D.a[k] != 0.f ? r32 / D.a[k] : 0.f;
+              Z.a[k] = zk;
+              g_rr += r * r;
+              g_bb += (double)B.a[k] * (double)B.a[k];
+              g_rho += r32 * zk;
+            }
+          }
+          st4(zz + e, Z);
+          st4(dxv + e, zero4<float>());
+          acc[0] += g_rr;
+          acc[1] += g_bb;
+          acc[2] += (double)g_rho;
+        }
+      }
+      store_row(rows, rl, row_ok, it.sl, it.lpr, acc, 3);
+    }
+  }
+  chunk_epilogue(rows, 3, blockIdx.x, c.partial, c.sync, c.reps, c.n_reps,
+                 [&](int r, const double* s3) -> int {
+                   const RepDesc& rr = c.reps[r];
+                   RepSolve& s = c.solve[r];
+                   DevStats& st = c.stats[r];
+                   if (first) {
+                     s.outer = 0;
+                     s.zero_b = 0;
+                     s.dc_apply = 0;
+                     s.active = 0;
+                     s.iters = 0;
+                   } else if (!s.dc_apply) {
+                     return 0;        // this replicate finished in an earlier sweep
+                   }
+                   st.iters[which] += s.iters;
+                   st.sweeps[which] += 1;
+                   if (!isfinite(s3[0]) || !isfinite(s3[1]) || !isfinite(s3[2])) {
+                     c.sync->error = 1;
+                     st.nonfinite = 1;
+                     s.active = 0;
+                     s.dc_apply = 0;
+                     return 0;
+                   }
+                   const double tol = which == 0 ? rr.rtol_o2 : rr.rtol_drug;
+                   if (s3[1] == 0.0) {
+                     s.zero_b = 1;
+                     s.rel_true = 0.0;
+                     st.rel[which] = 0.0;
+                     s.active = 0;
+                     s.dc_apply = 0;
+                     return 0;
+                   }
+                   const double rel = sqrt(s3[0] / s3[1]);
+                   s.rel_true = rel;
+                   st.rel[which] = rel;
+                   if (rel <= tol || s.outer >= rr.max_outer) {
+                     if (rel > tol) st.not_converged |= 1 << which;
+                     s.active = 0;
+                     s.dc_apply = 0;
+                     return 0;
+                   }
+                   // start the inner FP32 solve A dx = fl32(r)
+                   s.outer += 1;
+                   s.rho = s3[2];
+                   s.rnorm2 = s3[0];
+                   s.bnorm2 = s3[0];
+                   s.rtol = rr.rtol_inner;
+                   s.maxit = rr.maxit;
+                   s.iters = 0;
+                   s.alpha = 0.0;
+                   s.beta = 0.0;
+                   s.dc_apply = 1;
+                   s.active = s3[2] > 0.0 ? 1 : 0;
+                   return s.active;
+                 });
+}
+
+// x_hi + x_lo += dx (two-word sum), or x = 0 for a vanishing right-hand side.
+__global__ void __launch_bounds__(512) k_dc_update(Ctx c, float* __restrict__ x_hi, float* __restrict__ x_lo) {
+  const int2 ch = c.chunks[blockIdx.x];
+  const RepSolve sv = c.solve[ch.x];
+  if (!sv.dc_apply && !sv.zero_b) return;
+  const RepDesc& rd = c.reps[ch.x];
+  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const long long base0 = rd.off + (long long)ch.y * rd.nxp;
+  const int ngroups = nrows * rd.gpr;
+  const float* __restrict__ dxv = (const float*)c.dx;
+  for (int gi = threadIdx.x; gi < ngroups; gi += blockDim.x) {
+    const int rl = gi / rd.gpr, g = gi % rd.gpr;
+    const long long e = base0 + (long long)rl * rd.nxp + 4LL * g;
+    if (sv.zero_b) {
+      st4(x_hi + e, zero4<float>());
+      st4(x_lo + e, zero4<float>());
+      continue;
+    }
+    V4<float> H = ld4(x_hi + e), L = ld4(x_lo + e);
+    const V4<float> D = ld4(dxv + e);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      // two-sum of hi and dx, then renormalise with the low word
+      const float s = __fadd_rn(H.a[k], D.a[k]);
+      const float bv = __fsub_rn(s, H.a[k]);
+      const float err = __fadd_rn(__fsub_rn(H.a[k], __fsub_rn(s, bv)), __fsub_rn(D.a[k], bv));
+      const float lo = __fadd_rn(L.a[k], err);
+      const float hi = __fadd_rn(s, lo);
+      L.a[k] = __fsub_rn(lo, __fsub_rn(hi, s));
+      H.a[k] = hi;
+    }
+    st4(x_hi + e, H);
+    st4(x_lo + e, L);
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- launchers --
+void launch_dc_residual(const Ctx& c, int which, const void* x_hi, const void* x_lo, bool first) {
+  if (which == 0)
+    k_dc_residual<0><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, (const float*)x_hi, (const float*)x_lo, first);
+  else
+    k_dc_residual<1><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, (const float*)x_hi, (const float*)x_lo, first);
+}
+
+void launch_dc_update(const Ctx& c, void* x_hi, void* x_lo) {
+  k_dc_update<<<c.n_chunks, c.threads, 0, c.stream>>>(c, (float*)x_hi, (float*)x_lo);
+}
+
+void launch_diff_norms(const Ctx& c, const void* a, const void* b, bool fp64) {
+  if (fp64) k_diff_norms<double><<<c.n_chunks, c.threads, 0, c.stream>>>(c, (const double*)a, (const double*)b);
+  else k_diff_norms<float><<<c.n_chunks, c.threads, 0, c.stream>>>(c, (const float*)a, (const float*)b);
+}
+
+template <typename T>
+static void launch_setup_t(const Ctx& c, int which) {
+  if (which == 0) k_setup<T, 0><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which);
+  else k_setup<T, 1><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which);
+}
+
+void launch_setup(const Ctx& c, int which, bool fp64) {
+  if (fp64) launch_setup_t<double>(c, which);
+  else launch_setup_t<float>(c, which);
+}
+
+void launch_pass_a(const Ctx& c, int which, const void* p_old, void* p_new, bool fp64) {
+  if (fp64) k_pass_a<double><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, (const double*)p_old, (double*)p_new);
+  else k_pass_a<float><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, (const float*)p_old, (float*)p_new);
+}
+
+void launch_pass_b(const Ctx& c, int which, const void* pdir, void* xfield, bool fp64) {
+  if (fp64) k_pass_b<double><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, (const double*)pdir, xfield);
+  else k_pass_b<float><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, (const float*)pdir, xfield);
+}
+
+void launch_true_residual(const Ctx& c, int which, void* xfield, bool fp64) {
+  if (fp64) {
+    if (which == 0) k_true_residual<double, 0><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, xfield);
+    else k_true_residual<double, 1><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, xfield);
+    k_zero_if_b_zero<double><<<c.n_chunks, c.threads, 0, c.stream>>>(c, xfield);
+  } else {
+    if (which == 0) k_true_residual<float, 0><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, xfield);
+    else k_true_residual<float, 1><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, xfield);
+    k_zero_if_b_zero<float><<<c.n_chunks, c.threads, 0, c.stream>>>(c, xfield);
+  }
+}
+
+void launch_apply(const Ctx& c, int which, int rep, const void* u, void* out, bool fp64) {
+  if (fp64) {
+    if (which == 0) k_apply<double, 0><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, rep, (const double*)u, (double*)out);
+    else k_apply<double, 1><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, rep, (const double*)u, (double*)out);
+  } else {
+    if (which == 0) k_apply<float, 0><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, rep, (const float*)u, (float*)out);
+    else k_apply<float, 1><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, rep, (const float*)u, (float*)out);
+  }
+}
+
+}  // namespace hca

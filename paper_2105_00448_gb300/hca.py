@@ -1,0 +1,426 @@
+"""Thin ctypes binding of libhca.so (include/hca.h).
+
+Only argument marshalling lives here: every step of the hot path runs in the
+library's CUDA kernels.  Host buffers are numpy arrays; device buffers are
+torch CUDA tensors (PyTorch supplies device memory and streams only).  There
+is no CPU fallback: if libhca.so cannot be loaded, every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+
+from . import _build
+
+# status codes (hca.h)
+HCA_OK = 0
+HCA_ERR_ARG = -1
+HCA_ERR_CUDA = -2
+HCA_ERR_OOM = -3
+HCA_ERR_NONFINITE = -4
+HCA_ERR_NOCONV = -5
+HCA_ERR_TIMEOUT = -6
+HCA_ERR_UNIMPLEMENTED = -7
+HCA_ERR_STATE = -8
+
+HCA_FP64 = 0
+HCA_FP32 = 1
+
+EMPTY, PROLIF, QUIESC, DEAD, VESSEL, STROMA = range(6)
+
+FIELD_O2 = 1 << 0
+FIELD_DRUG0 = 1 << 1
+FIELD_DRUG1 = 1 << 2
+FIELD_DRUG2 = 1 << 3
+FIELD_PHI = 1 << 4
+FIELD_P53 = 1 << 5
+FIELD_VEGFC = 1 << 6
+FIELD_PERF = 1 << 7
+FIELD_DRUG = (FIELD_DRUG0, FIELD_DRUG1, FIELD_DRUG2)
+
+STAGE_O2 = 1 << 0
+STAGE_DRUGS = 1 << 1
+STAGE_ODE = 1 << 2
+STAGE_CA = 1 << 3
+STAGE_ADVANCE = 1 << 4
+STAGE_ALL = 0x1F
+
+_d3 = ctypes.c_double * 3
+_i3 = ctypes.c_int32 * 3
+
+
+class hca_config(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32),
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("n_drugs", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("dx", ctypes.c_double), ("dt", ctypes.c_double),
+        ("rtol_o2", ctypes.c_double), ("rtol_drug", ctypes.c_double),
+        ("maxit", ctypes.c_int32), ("ode_substeps", ctypes.c_int32),
+        ("picard_tol", ctypes.c_double), ("picard_maxit", ctypes.c_int32),
+        ("dose_interval", ctypes.c_int32),
+        ("D_K", ctypes.c_double), ("phi_K", ctypes.c_double), ("K1", ctypes.c_double),
+        ("K0", ctypes.c_double), ("r_K", ctypes.c_double),
+        ("D_G", _d3), ("psi_G", _d3), ("kappa_G", _d3), ("uptake_G", _d3),
+        ("dose_peak", _d3), ("plasma_decay", _d3), ("kill_b", _i3),
+        ("T_cycle", ctypes.c_double), ("K_phi", ctypes.c_double),
+        ("k1", ctypes.c_double), ("k1p", ctypes.c_double), ("K_p53", ctypes.c_double),
+        ("k2", ctypes.c_double), ("k2p", ctypes.c_double), ("k2pp", ctypes.c_double),
+        ("J5", ctypes.c_double), ("K_V", ctypes.c_double),
+        ("rtol_inner", ctypes.c_double), ("max_outer", ctypes.c_int32),
+        ("warm_start", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class hca_stats(ctypes.Structure):
+    _fields_ = [
+        ("step", ctypes.c_int64),
+        ("picard_iterations", ctypes.c_int32),
+        ("o2_iterations", ctypes.c_int32),
+        ("o2_sweeps", ctypes.c_int32),
+        ("drug_iterations", _i3),
+        ("o2_rel_residual", ctypes.c_double),
+        ("drug_rel_residual", _d3),
+        ("not_converged", ctypes.c_int32),
+        ("pad0", ctypes.c_int32),
+        ("committed", ctypes.c_int64), ("kills", ctypes.c_int64),
+        ("divisions", ctypes.c_int64), ("blocked", ctypes.c_int64),
+        ("counts", ctypes.c_int64 * 6),
+    ]
+
+    def as_dict(self) -> Dict:
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = list(v) if hasattr(v, "__len__") else v
+        return d
+
+
+NKCLASS = 8
+KCLASS_NAMES = ("setup", "pass_a", "pass_b", "residual", "ode", "ca_compact", "ca_colour", "other")
+
+
+class hca_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * NKCLASS), ("ms", ctypes.c_double * NKCLASS)]
+
+    def as_dict(self) -> Dict:
+        return {name: {"launches": int(self.launches[i]), "ms": float(self.ms[i])}
+                for i, name in enumerate(KCLASS_NAMES)}
+
+
+EXPORTS = [
+    "hca_config_default", "hca_create", "hca_create_batch", "hca_step", "hca_stage",
+    "hca_read_fields", "hca_write_fields", "hca_read_states", "hca_write_states",
+    "hca_set_step", "hca_get_stats", "hca_apply_operator", "hca_philox_uniforms",
+    "hca_sync", "hca_get_shape", "hca_launch_count", "hca_profile_enable", "hca_get_profile",
+    "hca_destroy", "hca_status_string",
+]
+
+_lib = None
+
+
+class HcaError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        msg = _lib.hca_status_string(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{what}: {msg} ({status})" if what else f"{msg} ({status})")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libhca.so (building it first if absent).  Raises if it cannot load."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"libhca.so not built at {path}")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    I32, I64, U32, U64, SZ = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t
+    cfgp = ctypes.POINTER(hca_config)
+    sig = {
+        "hca_config_default": (ctypes.c_int, [cfgp, I32, I32, I32]),
+        "hca_create": (ctypes.c_int, [cfgp, P, P, P, I32, ctypes.POINTER(P)]),
+        "hca_create_batch": (ctypes.c_int, [I32, cfgp, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
+                                            I32, ctypes.POINTER(P)]),
+        "hca_step": (ctypes.c_int, [P, I32]),
+        "hca_stage": (ctypes.c_int, [P, U32]),
+        "hca_read_fields": (ctypes.c_int, [P, I32, U32, P, SZ, I32]),
+        "hca_write_fields": (ctypes.c_int, [P, I32, U32, P, SZ, I32]),
+        "hca_read_states": (ctypes.c_int, [P, I32, P, SZ, I32]),
+        "hca_write_states": (ctypes.c_int, [P, I32, P, SZ, I32]),
+        "hca_set_step": (ctypes.c_int, [P, I64]),
+        "hca_get_stats": (ctypes.c_int, [P, I32, ctypes.POINTER(hca_stats)]),
+        "hca_apply_operator": (ctypes.c_int, [P, I32, I32, P, P, I32]),
+        "hca_philox_uniforms": (ctypes.c_int, [U64, U64, I64, U32, U32, P, I32]),
+        "hca_sync": (ctypes.c_int, [P]),
+        "hca_get_shape": (ctypes.c_int, [P, I32, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)]),
+        "hca_launch_count": (I64, [P]),
+        "hca_profile_enable": (ctypes.c_int, [P, I32]),
+        "hca_get_profile": (ctypes.c_int, [P, ctypes.POINTER(hca_profile)]),
+        "hca_destroy": (None, [P]),
+        "hca_status_string": (ctypes.c_char_p, [I32]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, what: str):
+    if rc != HCA_OK:
+        raise HcaError(rc, what)
+
+
+# ------------------------------------------------------------ config ---
+_ARRAY3 = {"D_G", "psi_G", "kappa_G", "uptake_G", "dose_peak", "plasma_decay", "kill_b"}
+
+
+def make_config(nx: int, ny: int, nz: int, precision="f64", stream=None, **params) -> hca_config:
+    """hca_config from the library defaults plus overrides (names as in hca.h)."""
+    lib = load()
+    cfg = hca_config()
+    _check(lib.hca_config_default(ctypes.byref(cfg), nx, ny, nz), "hca_config_default")
+    cfg.precision = HCA_FP32 if precision in ("f32", HCA_FP32) else HCA_FP64
+    for k, v in params.items():
+        if k in _ARRAY3:
+            arr = getattr(cfg, k)
+            vals = list(v)
+            for i in range(min(3, len(vals))):
+                arr[i] = vals[i]
+        elif k == "seed":
+            cfg.seed = int(v) & 0xFFFFFFFFFFFFFFFF
+        elif hasattr(cfg, k):
+            setattr(cfg, k, v)
+        else:
+            raise KeyError(f"unknown hca_config field {k!r}")
+    if stream is not None:
+        cfg.stream = ctypes.c_void_p(int(stream))
+    return cfg
+
+
+# ---------------------------------------------------------- buffers ---
+def _ptr(buf):
+    """(pointer, nbytes, on_device) for a numpy array or torch tensor."""
+    if isinstance(buf, np.ndarray):
+        if not buf.flags.c_contiguous:
+            raise ValueError("host buffers must be C-contiguous")
+        return buf.ctypes.data, buf.nbytes, 0
+    # torch tensor
+    if not buf.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return buf.data_ptr(), buf.numel() * buf.element_size(), 1 if buf.is_cuda else 0
+
+
+# --------------------------------------------------------------- API ---
+def hca_config_default(nx, ny, nz) -> hca_config:
+    return make_config(nx, ny, nz)
+
+
+def hca_create(cfg: hca_config, p_cell, perf, p_vessel):
+    lib = load()
+    ptrs = [_ptr(m) for m in (p_cell, perf, p_vessel)]
+    on_dev = ptrs[0][2]
+    if any(p[2] != on_dev for p in ptrs):
+        raise ValueError("maps must all be on the host or all on the device")
+    n = cfg.nx * cfg.ny * cfg.nz
+    for m, p in zip((p_cell, perf, p_vessel), ptrs):
+        if p[1] < 4 * n:
+            raise ValueError("map too small")
+    h = ctypes.c_void_p()
+    _check(lib.hca_create(ctypes.byref(cfg), ptrs[0][0], ptrs[1][0], ptrs[2][0], on_dev, ctypes.byref(h)),
+           "hca_create")
+    return h
+
+
+def hca_create_batch(cfgs: Sequence[hca_config], p_cell, perf, p_vessel):
+    lib = load()
+    n = len(cfgs)
+    arr = (hca_config * n)(*cfgs)
+    pc = [_ptr(m) for m in p_cell]
+    pf = [_ptr(m) for m in perf]
+    pv = [_ptr(m) for m in p_vessel]
+    on_dev = pc[0][2]
+    mk = lambda lst: (ctypes.c_void_p * n)(*[p[0] for p in lst])
+    h = ctypes.c_void_p()
+    _check(lib.hca_create_batch(n, arr, mk(pc), mk(pf), mk(pv), on_dev, ctypes.byref(h)), "hca_create_batch")
+    return h
+
+
+def hca_step(h, n_steps: int = 1) -> int:
+    return load().hca_step(h, n_steps)
+
+
+def hca_stage(h, mask: int) -> int:
+    return load().hca_stage(h, mask)
+
+
+def hca_read_fields(h, rep: int, mask: int, dst) -> None:
+    p, nb, dev = _ptr(dst)
+    _check(load().hca_read_fields(h, rep, mask, p, nb, dev), "hca_read_fields")
+
+
+def hca_write_fields(h, rep: int, mask: int, src) -> None:
+    p, nb, dev = _ptr(src)
+    _check(load().hca_write_fields(h, rep, mask, p, nb, dev), "hca_write_fields")
+
+
+def hca_read_states(h, rep: int, dst) -> None:
+    p, nb, dev = _ptr(dst)
+    _check(load().hca_read_states(h, rep, p, nb, dev), "hca_read_states")
+
+
+def hca_write_states(h, rep: int, src) -> None:
+    p, nb, dev = _ptr(src)
+    _check(load().hca_write_states(h, rep, p, nb, dev), "hca_write_states")
+
+
+def hca_set_step(h, step: int) -> None:
+    _check(load().hca_set_step(h, step), "hca_set_step")
+
+
+def hca_get_stats(h, rep: int = 0) -> hca_stats:
+    st = hca_stats()
+    _check(load().hca_get_stats(h, rep, ctypes.byref(st)), "hca_get_stats")
+    return st
+
+
+def hca_apply_operator(h, rep: int, which: int, u, out) -> None:
+    pu, nu, du = _ptr(u)
+    po, no, do = _ptr(out)
+    if du != do or nu != no:
+        raise ValueError("u and out must match in size and location")
+    _check(load().hca_apply_operator(h, rep, which, pu, po, du), "hca_apply_operator")
+
+
+def hca_philox_uniforms(seed: int, site_begin: int, n: int, step: int, purpose: int, dst=None):
+    if dst is None:
+        dst = np.empty(n, dtype=np.float32)
+    p, nb, dev = _ptr(dst)
+    if nb < 4 * n:
+        raise ValueError("dst too small")
+    _check(load().hca_philox_uniforms(seed & 0xFFFFFFFFFFFFFFFF, site_begin, n, step, purpose, p, dev),
+           "hca_philox_uniforms")
+    return dst
+
+
+def hca_sync(h) -> None:
+    _check(load().hca_sync(h), "hca_sync")
+
+
+def hca_launch_count(h) -> int:
+    return int(load().hca_launch_count(h))
+
+
+def hca_profile_enable(h, enable: bool = True) -> None:
+    _check(load().hca_profile_enable(h, 1 if enable else 0), "hca_profile_enable")
+
+
+def hca_get_profile(h) -> Dict:
+    out = hca_profile()
+    _check(load().hca_get_profile(h, ctypes.byref(out)), "hca_get_profile")
+    return out.as_dict()
+
+
+def hca_destroy(h) -> None:
+    if h:
+        load().hca_destroy(h)
+
+
+# ------------------------------------------------------ convenience ---
+class Sim:
+    """One handle (one replicate or a batch) with numpy-friendly helpers."""
+
+    def __init__(self, cfgs, maps, batch: bool = False):
+        if batch:
+            self.cfgs = list(cfgs)
+            self.handle = hca_create_batch(self.cfgs, [m[0] for m in maps], [m[1] for m in maps],
+                                           [m[2] for m in maps])
+        else:
+            self.cfgs = [cfgs]
+            self.handle = hca_create(cfgs, *maps)
+        self.fp64 = self.cfgs[0].precision == HCA_FP64
+        self.dtype = np.float64 if self.fp64 else np.float32
+
+    @classmethod
+    def create(cls, nx, ny, nz, p_cell, perf, p_vessel, precision="f64", **params):
+        return cls(make_config(nx, ny, nz, precision=precision, **params), (p_cell, perf, p_vessel))
+
+    def shape(self, rep: int = 0):
+        c = self.cfgs[rep]
+        return (c.nz, c.ny, c.nx)
+
+    def step(self, n: int = 1, allow_noconv: bool = False) -> int:
+        rc = hca_step(self.handle, n)
+        if rc != HCA_OK and not (allow_noconv and rc == HCA_ERR_NOCONV):
+            raise HcaError(rc, "hca_step")
+        return rc
+
+    def stage(self, mask: int, allow_noconv: bool = False) -> int:
+        rc = hca_stage(self.handle, mask)
+        if rc != HCA_OK and not (allow_noconv and rc == HCA_ERR_NOCONV):
+            raise HcaError(rc, "hca_stage")
+        return rc
+
+    def field(self, bit: int, rep: int = 0) -> np.ndarray:
+        out = np.empty(self.shape(rep), dtype=self.dtype)
+        hca_read_fields(self.handle, rep, bit, out)
+        return out
+
+    def set_field(self, bit: int, values, rep: int = 0) -> None:
+        arr = np.ascontiguousarray(np.asarray(values, dtype=self.dtype).reshape(self.shape(rep)))
+        hca_write_fields(self.handle, rep, bit, arr)
+
+    def states(self, rep: int = 0) -> np.ndarray:
+        out = np.empty(self.shape(rep), dtype=np.uint8)
+        hca_read_states(self.handle, rep, out)
+        return out
+
+    def set_states(self, values, rep: int = 0) -> None:
+        hca_write_states(self.handle, rep, np.ascontiguousarray(np.asarray(values, dtype=np.uint8)))
+
+    def stats(self, rep: int = 0) -> Dict:
+        return hca_get_stats(self.handle, rep).as_dict()
+
+    def apply_operator(self, which: int, u, rep: int = 0) -> np.ndarray:
+        u = np.ascontiguousarray(np.asarray(u, dtype=self.dtype).reshape(self.shape(rep)))
+        out = np.empty_like(u)
+        hca_apply_operator(self.handle, rep, which, u, out)
+        return out
+
+    def set_step(self, n: int) -> None:
+        hca_set_step(self.handle, n)
+
+    def launches(self) -> int:
+        return hca_launch_count(self.handle)
+
+    def close(self) -> None:
+        if self.handle:
+            hca_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
