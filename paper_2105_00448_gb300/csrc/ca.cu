@@ -35,6 +35,7 @@ __device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(
 
 template <typename T>
 __global__ void __launch_bounds__(512) k_ca_compact(Ctx c) {
+  HCA_COUNT_KERNEL(c);
   __shared__ unsigned int s_committed;
   if (threadIdx.x == 0) s_committed = 0;
   __syncthreads();
@@ -99,6 +100,7 @@ __global__ void __launch_bounds__(512) k_ca_compact(Ctx c) {
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_ca_colour(Ctx c, int colour) {
+  HCA_COUNT_KERNEL(c);
   __shared__ unsigned int s_cnt[3];
   if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0;
   __syncthreads();

@@ -26,6 +26,7 @@ __device__ __forceinline__ double t_expm1(double v) { return expm1(v); }
 template <typename T>
 __global__ void __launch_bounds__(512) k_init(Ctx c, const float* __restrict__ pc, const float* __restrict__ pf,
                                               const float* __restrict__ pv, int* __restrict__ err) {
+  HCA_COUNT_KERNEL(c);
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
   const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
@@ -78,6 +79,7 @@ __device__ __forceinline__ T p53_at(T P0, T lam, T s, T k1) {
 
 template <typename T>
 __global__ void __launch_bounds__(512) k_ode(Ctx c) {
+  HCA_COUNT_KERNEL(c);
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
   const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
@@ -134,6 +136,7 @@ __global__ void __launch_bounds__(512) k_ode(Ctx c) {
 
 // Sites per state code, per replicate (into stats[rep].counts).
 __global__ void __launch_bounds__(512) k_histogram(Ctx c) {
+  HCA_COUNT_KERNEL(c);
   __shared__ unsigned int h[6];
   if (threadIdx.x < 6) h[threadIdx.x] = 0;
   __syncthreads();
@@ -160,8 +163,11 @@ __global__ void k_philox_uniforms(unsigned long long seed, unsigned long long si
     out[i] = site_uniform(seed, site0 + (unsigned long long)i, step, purpose);
 }
 
-__global__ void k_advance_step(long long* step, long long by) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *step += by;
+__global__ void k_advance_step(long long* step, long long by, unsigned long long* n_kernels) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *step += by;
+    atomicAdd(n_kernels, 1ull);
+  }
 }
 
 }  // namespace
@@ -186,8 +192,6 @@ void launch_philox_uniforms(unsigned long long seed, unsigned long long site0, l
   k_philox_uniforms<<<(unsigned)blocks, 256, 0, stream>>>(seed, site0, n, step, purpose, out);
 }
 
-void launch_advance_step(long long* step, long long by, cudaStream_t stream) {
-  k_advance_step<<<1, 32, 0, stream>>>(step, by);
-}
+void launch_advance_step(const Ctx& c, long long by) { k_advance_step<<<1, 32, 0, c.stream>>>(c.step, by, c.n_kernels); }
 
 }  // namespace hca

@@ -12,20 +12,21 @@
 #include "hca_internal.cuh"
 
 namespace hca {
-void launch_setup(const Ctx& c, int which, bool fp64);
-void launch_pass_a(const Ctx& c, int which, const void* p_old, void* p_new, bool fp64);
-void launch_pass_b(const Ctx& c, int which, const void* pdir, void* xfield, bool fp64);
+void launch_setup(const Ctx& c, int which, bool fp64, CondArg cnd);
+void launch_pass_a(const Ctx& c, int which, bool fp64);
+void launch_pass_b(const Ctx& c, int which, void* xfield, bool fp64, CondArg cnd);
 void launch_true_residual(const Ctx& c, int which, void* xfield, bool fp64);
 void launch_apply(const Ctx& c, int which, int rep, const void* u, void* out, bool fp64);
 void launch_diff_norms(const Ctx& c, const void* a, const void* b, bool fp64);
-void launch_dc_residual(const Ctx& c, int which, const void* x_hi, const void* x_lo, bool first);
+void launch_dc_residual(const Ctx& c, int which, const void* x_hi, const void* x_lo, bool first, CondArg outer,
+                        CondArg inner);
 void launch_dc_update(const Ctx& c, void* x_hi, void* x_lo);
 void launch_init(const Ctx& c, const float* pc, const float* pf, const float* pv, int* err, bool fp64);
 void launch_ode(const Ctx& c, bool fp64);
 void launch_histogram(const Ctx& c);
 void launch_philox_uniforms(unsigned long long seed, unsigned long long site0, long long n, uint32_t step,
                             uint32_t purpose, float* out, cudaStream_t stream);
-void launch_advance_step(long long* step, long long by, cudaStream_t stream);
+void launch_advance_step(const Ctx& c, long long by);
 void launch_ca_compact(const Ctx& c, bool fp64);
 void launch_ca_colour(const Ctx& c, int colour, int blocks_x, bool fp64);
 }  // namespace hca
@@ -67,6 +68,15 @@ struct hca_handle {
   int maxit_all = 0;
   int max_outer = 0;
   int last_iters = 0;
+  int prev_inner[1 + hca::MAX_DRUGS][16] = {};
+  // step graphs (one per stage mask), built on first use
+  struct Graph {
+    uint32_t mask;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+  cudaStream_t cap[3] = {nullptr, nullptr, nullptr};
+  bool graphs_ok = true;
   int* h_pinned = nullptr;    // [0] active replicates, [1] error flag
   std::vector<void*> allocs;
 };
@@ -225,6 +235,13 @@ int dev_alloc(hca_handle* h, P** out, size_t bytes) {
 
 void free_all(hca_handle* h) {
   if (!h) return;
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+  for (auto& s : h->cap)
+    if (s) {
+      cudaStreamDestroy(s);
+      s = nullptr;
+    }
   for (auto e : h->prof.pool) cudaEventDestroy(e);
   h->prof.pool.clear();
   for (void* p : h->allocs) cudaFree(p);
@@ -247,16 +264,17 @@ void* field_ptr(hca_handle* h, uint32_t bit) {
   }
 }
 
+constexpr hca::CondArg kNoCond{0ull, 0};
+
 // CG iterations (pass A, pass B) on operator `which` for every replicate whose
-// solve is active, updating x, until none is active or maxit is reached.
-// The first convergence check comes after about as many iterations as the
-// previous solve of this operator needed; later checks every 4 iterations.
-int pcg_iterate(hca_handle* h, int which, void* x) {
+// solve is active, updating x, until none is active or maxit is reached.  The
+// first convergence check comes after about as many iterations as the same
+// solve needed last time (`predict`), later ones every 4 iterations; with
+// the profiler on, after every iteration (so no launch runs empty).
+int pcg_iterate(hca_handle* h, int which, void* x, int predict) {
   Ctx& c = h->ctx;
-  void* p_old = c.p;
-  void* p_new = c.p_alt;
   int done = 0;
-  int chunk = std::max(2, h->prev_iters[which] - 2);
+  int chunk = h->prof.on ? 1 : std::max(1, predict - 2);
   for (;;) {
     HCA_TRY(cudaMemcpyAsync(h->h_pinned, &c.sync->active_count, 2 * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     HCA_TRY(cudaStreamSynchronize(c.stream));
@@ -264,25 +282,13 @@ int pcg_iterate(hca_handle* h, int which, void* x) {
     if (h->h_pinned[0] == 0 || done >= h->maxit_all) break;
     const int n = std::min(chunk, h->maxit_all - done);
     for (int k = 0; k < n; ++k) {
-      HCA_LAUNCH(h, HCA_KCLASS_PASS_A, 1, hca::launch_pass_a(c, which, p_old, p_new, h->fp64));
-      HCA_LAUNCH(h, HCA_KCLASS_PASS_B, 1, hca::launch_pass_b(c, which, p_new, x, h->fp64));
-      std::swap(p_old, p_new);
+      HCA_LAUNCH(h, HCA_KCLASS_PASS_A, 1, hca::launch_pass_a(c, which, h->fp64));
+      HCA_LAUNCH(h, HCA_KCLASS_PASS_B, 1, hca::launch_pass_b(c, which, x, h->fp64, kNoCond));
     }
     done += n;
-    chunk = 4;
+    chunk = h->prof.on ? 1 : 4;
   }
   h->last_iters = done;
-  return HCA_OK;
-}
-
-int record_iters(hca_handle* h, int which) {
-  std::vector<hca::RepSolve> sv(h->n_reps);
-  HCA_TRY(cudaMemcpyAsync(sv.data(), h->ctx.solve, sizeof(hca::RepSolve) * h->n_reps, cudaMemcpyDeviceToHost,
-                          h->ctx.stream));
-  HCA_TRY(cudaStreamSynchronize(h->ctx.stream));
-  int mx = 0;
-  for (auto& s : sv) mx = std::max(mx, s.iters);
-  h->prev_iters[which] = mx;
   return HCA_OK;
 }
 
@@ -292,12 +298,11 @@ int record_iters(hca_handle* h, int which) {
 int solve_plain(hca_handle* h, int which) {
   Ctx& c = h->ctx;
   void* x = which == 0 ? c.K : c.G[which - 1];
-  HCA_LAUNCH(h, HCA_KCLASS_SETUP, 1, hca::launch_setup(c, which, h->fp64));
-  int rc = pcg_iterate(h, which, x);
+  HCA_LAUNCH(h, HCA_KCLASS_SETUP, 1, hca::launch_setup(c, which, h->fp64, kNoCond));
+  int rc = pcg_iterate(h, which, x, h->prev_inner[which][0]);
   if (rc) return rc;
+  h->prev_inner[which][0] = h->last_iters;
   HCA_LAUNCH(h, HCA_KCLASS_RESIDUAL, 2, hca::launch_true_residual(c, which, x, h->fp64));
-  rc = record_iters(h, which);
-  if (rc) return rc;
   HCA_TRY(cudaMemcpyAsync(h->h_pinned, &c.sync->active_count, 2 * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
   HCA_TRY(cudaStreamSynchronize(c.stream));
   return h->h_pinned[1] ? HCA_ERR_NONFINITE : HCA_OK;
@@ -310,9 +315,9 @@ int solve_dc(hca_handle* h, int which) {
   Ctx& c = h->ctx;
   void* xh = which == 0 ? c.K : c.G[which - 1];
   void* xl = which == 0 ? c.K_lo : c.G_lo[which - 1];
-  int inner_total = 0;
   for (int outer = 0;; ++outer) {
-    HCA_LAUNCH(h, HCA_KCLASS_RESIDUAL, 1, hca::launch_dc_residual(c, which, xh, xl, outer == 0));
+    HCA_LAUNCH(h, HCA_KCLASS_RESIDUAL, 1,
+               hca::launch_dc_residual(c, which, xh, xl, outer == 0, kNoCond, kNoCond));
     HCA_TRY(cudaMemcpyAsync(h->h_pinned, &c.sync->active_count, 2 * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     HCA_TRY(cudaStreamSynchronize(c.stream));
     if (h->h_pinned[1]) return HCA_ERR_NONFINITE;
@@ -321,12 +326,12 @@ int solve_dc(hca_handle* h, int which) {
       HCA_LAUNCH(h, HCA_KCLASS_OTHER, 1, hca::launch_dc_update(c, xh, xl));
       break;
     }
-    int rc = pcg_iterate(h, which, c.dx);
+    const int slot = std::min(outer, 15);
+    int rc = pcg_iterate(h, which, c.dx, h->prev_inner[which][slot]);
     if (rc) return rc;
-    inner_total += h->last_iters;
+    h->prev_inner[which][slot] = h->last_iters;
     HCA_LAUNCH(h, HCA_KCLASS_OTHER, 1, hca::launch_dc_update(c, xh, xl));
   }
-  h->prev_iters[which] = std::max(4, inner_total / 2);
   return HCA_OK;
 }
 
@@ -335,8 +340,175 @@ int solve(hca_handle* h, int which) {
   return solve_plain(h, which);
 }
 
+// ------------------------------------------------------------ step graph --
+// The whole step (or a subset of its stages) captured once into a CUDA graph.
+// Each CG loop is a WHILE conditional node whose body is [pass A, pass B];
+// the last block of the set-up / pass B / defect-correction residual kernels
+// sets the loop condition on the device, so a step runs without any host
+// round trip.  Loop exit is guaranteed by maxit / max_outer, with a device
+// guard counter as a second stop.
+int add_while(cudaStream_t s, cudaGraphConditionalHandle hnd, cudaGraph_t* body) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  HCA_TRY(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd));
+  if (st != cudaStreamCaptureStatusActive) return HCA_ERR_CUDA;
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = hnd;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  HCA_TRY(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+  HCA_TRY(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  *body = p.conditional.phGraph_out[0];
+  return HCA_OK;
+}
+
+int cap_solve(hca_handle* h, int which, cudaGraph_t G) {
+  Ctx& c = h->ctx;
+  cudaStream_t S = h->cap[0], S2 = h->cap[1], S3 = h->cap[2];
+  const bool dc = !h->fp64 && h->max_outer > 0;
+  int rc;
+  if (!dc) {
+    void* x = which == 0 ? c.K : c.G[which - 1];
+    cudaGraphConditionalHandle H;
+    HCA_TRY(cudaGraphConditionalHandleCreate(&H, G, 0, cudaGraphCondAssignDefault));
+    const hca::CondArg cnd{H, 1};
+    c.stream = S;
+    hca::launch_setup(c, which, h->fp64, cnd);
+    HCA_TRY(cudaGetLastError());
+    cudaGraph_t body;
+    if ((rc = add_while(S, H, &body))) return rc;
+    HCA_TRY(cudaStreamBeginCaptureToGraph(S2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    c.stream = S2;
+    hca::launch_pass_a(c, which, h->fp64);
+    hca::launch_pass_b(c, which, x, h->fp64, cnd);
+    HCA_TRY(cudaGetLastError());
+    HCA_TRY(cudaStreamEndCapture(S2, &body));
+    c.stream = S;
+    hca::launch_true_residual(c, which, x, h->fp64);
+    HCA_TRY(cudaGetLastError());
+    return HCA_OK;
+  }
+  void* xh = which == 0 ? c.K : c.G[which - 1];
+  void* xl = which == 0 ? c.K_lo : c.G_lo[which - 1];
+  cudaGraphConditionalHandle Ho, Hi;
+  HCA_TRY(cudaGraphConditionalHandleCreate(&Ho, G, 0, cudaGraphCondAssignDefault));
+  HCA_TRY(cudaGraphConditionalHandleCreate(&Hi, G, 0, cudaGraphCondAssignDefault));
+  const hca::CondArg co{Ho, 1}, ci{Hi, 1};
+  c.stream = S;
+  hca::launch_dc_residual(c, which, xh, xl, true, co, ci);
+  HCA_TRY(cudaGetLastError());
+  cudaGraph_t bo, bi;
+  if ((rc = add_while(S, Ho, &bo))) return rc;
+  HCA_TRY(cudaStreamBeginCaptureToGraph(S2, bo, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  if ((rc = add_while(S2, Hi, &bi))) return rc;
+  HCA_TRY(cudaStreamBeginCaptureToGraph(S3, bi, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  c.stream = S3;
+  hca::launch_pass_a(c, which, h->fp64);
+  hca::launch_pass_b(c, which, c.dx, h->fp64, ci);
+  HCA_TRY(cudaGetLastError());
+  HCA_TRY(cudaStreamEndCapture(S3, &bi));
+  c.stream = S2;
+  hca::launch_dc_update(c, xh, xl);
+  hca::launch_dc_residual(c, which, xh, xl, false, co, ci);
+  HCA_TRY(cudaGetLastError());
+  HCA_TRY(cudaStreamEndCapture(S2, &bo));
+  c.stream = S;
+  hca::launch_dc_update(c, xh, xl);
+  HCA_TRY(cudaGetLastError());
+  return HCA_OK;
+}
+
+int cap_stages(hca_handle* h, uint32_t mask, cudaGraph_t G) {
+  Ctx& c = h->ctx;
+  c.stream = h->cap[0];
+  HCA_TRY(cudaMemsetAsync(c.stats, 0, sizeof(hca::DevStats) * h->n_reps, c.stream));
+  HCA_TRY(cudaMemsetAsync(&c.sync->error, 0, sizeof(int), c.stream));
+  int rc;
+  if (mask & HCA_STAGE_O2)
+    if ((rc = cap_solve(h, 0, G))) return rc;
+  if (mask & HCA_STAGE_DRUGS)
+    for (int d = 0; d < h->n_drugs; ++d)
+      if ((rc = cap_solve(h, 1 + d, G))) return rc;
+  c.stream = h->cap[0];
+  if (mask & HCA_STAGE_ODE) hca::launch_ode(c, h->fp64);
+  if (mask & HCA_STAGE_CA) {
+    HCA_TRY(cudaMemsetAsync(c.list_count, 0, sizeof(int) * 27 * h->n_reps, c.stream));
+    hca::launch_ca_compact(c, h->fp64);
+    const int bx = std::max(1, std::min(1024, 2 * c.sm_count / std::max(1, h->n_reps)));
+    for (int col = 0; col < 27; ++col) hca::launch_ca_colour(c, col, bx, h->fp64);
+  }
+  if (mask & HCA_STAGE_ADVANCE) hca::launch_advance_step(c, 1);
+  HCA_TRY(cudaGetLastError());
+  return HCA_OK;
+}
+
+int build_graph(hca_handle* h, uint32_t mask, cudaGraphExec_t* out) {
+  for (int k = 0; k < 3; ++k)
+    if (!h->cap[k]) HCA_TRY(cudaStreamCreateWithFlags(&h->cap[k], cudaStreamNonBlocking));
+  cudaGraph_t G;
+  HCA_TRY(cudaGraphCreate(&G, 0));
+  const cudaStream_t user = h->ctx.stream;
+  int rc = HCA_OK;
+  if (cudaStreamBeginCaptureToGraph(h->cap[0], G, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    (void)cudaGetLastError();
+    cudaGraphDestroy(G);
+    return HCA_ERR_CUDA;
+  }
+  rc = cap_stages(h, mask, G);
+  cudaGraph_t done = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->cap[0], &done);
+  h->ctx.stream = user;
+  if (rc || e != cudaSuccess) {
+    (void)cudaGetLastError();
+    // leave any nested capture
+    for (int k = 1; k < 3; ++k) {
+      cudaStreamCaptureStatus st;
+      if (cudaStreamIsCapturing(h->cap[k], &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+        cudaGraph_t tmp;
+        cudaStreamEndCapture(h->cap[k], &tmp);
+      }
+    }
+    (void)cudaGetLastError();
+    cudaGraphDestroy(G);
+    return rc ? rc : HCA_ERR_CUDA;
+  }
+  e = cudaGraphInstantiate(out, G, 0);
+  cudaGraphDestroy(G);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return HCA_ERR_CUDA;
+  }
+  return HCA_OK;
+}
+
+// Run one step's stages `mask` through its cached graph; returns HCA_ERR_CUDA
+// (and disables graphs for the handle) if a graph cannot be built.
+int run_graph(hca_handle* h, uint32_t mask, int times) {
+  cudaGraphExec_t exec = nullptr;
+  for (auto& g : h->graphs)
+    if (g.mask == mask) exec = g.exec;
+  if (!exec) {
+    int rc = build_graph(h, mask, &exec);
+    if (rc) {
+      h->graphs_ok = false;
+      return rc;
+    }
+    h->graphs.push_back({mask, exec});
+  }
+  for (int i = 0; i < times; ++i) {
+    HCA_TRY(cudaGraphLaunch(exec, h->ctx.stream));
+    if (mask & HCA_STAGE_ADVANCE) h->step += 1;
+  }
+  return HCA_OK;
+}
+
 int reset_step_stats(hca_handle* h) {
   HCA_TRY(cudaMemsetAsync(h->ctx.stats, 0, sizeof(hca::DevStats) * h->n_reps, h->ctx.stream));
+  HCA_TRY(cudaMemsetAsync(&h->ctx.sync->error, 0, sizeof(int), h->ctx.stream));
   return HCA_OK;
 }
 
@@ -373,7 +545,7 @@ int run_stages(hca_handle* h, uint32_t mask) {
     if (rc) return rc;
   }
   if (mask & HCA_STAGE_ADVANCE) {
-    HCA_LAUNCH(h, HCA_KCLASS_OTHER, 1, hca::launch_advance_step(h->ctx.step, 1, h->ctx.stream));
+    HCA_LAUNCH(h, HCA_KCLASS_OTHER, 1, hca::launch_advance_step(h->ctx, 1));
     h->step += 1;
   }
   return status;
@@ -383,7 +555,11 @@ int check_convergence(hca_handle* h) {
   std::vector<hca::DevStats> st(h->n_reps);
   HCA_TRY(cudaMemcpyAsync(st.data(), h->ctx.stats, sizeof(hca::DevStats) * h->n_reps, cudaMemcpyDeviceToHost,
                           h->ctx.stream));
+  HCA_TRY(cudaMemcpyAsync(h->h_pinned, &h->ctx.sync->active_count, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                          h->ctx.stream));
   HCA_TRY(cudaStreamSynchronize(h->ctx.stream));
+  if (h->h_pinned[1] == 1) return HCA_ERR_NONFINITE;
+  if (h->h_pinned[1] == 2) return HCA_ERR_NOCONV;
   for (auto& s : st) {
     if (s.nonfinite) return HCA_ERR_NONFINITE;
   }
@@ -498,6 +674,7 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     if (!h->fp64) {
       for (int d = 0; d < h->n_drugs; ++d) ALLOC(c.G_lo[d], fbytes);
       ALLOC(c.dx, fbytes);
+      ALLOC(c.reac, fbytes);
     }
     ALLOC(c.phi, fbytes);
     ALLOC(c.P, fbytes);
@@ -516,6 +693,7 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     ALLOC(c.step, sizeof(long long));
     ALLOC(c.lists, sizeof(uint32_t) * (size_t)std::max(1LL, h->lists_total));
     ALLOC(c.list_count, sizeof(int) * 27 * n);
+    ALLOC(c.n_kernels, sizeof(unsigned long long));
     if (cudaMallocHost(&h->h_pinned, 4 * sizeof(int)) != cudaSuccess) {
       (void)cudaGetLastError();
       rc = HCA_ERR_OOM;
@@ -530,7 +708,7 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     }
     // zero every device array (padding sites must hold 0)
     void* zero_list[] = {c.K, c.K_lo, c.G[0], c.G[1], c.G[2], c.G_lo[0], c.G_lo[1], c.G_lo[2], c.dx,
-                         c.phi, c.P, c.Vc, c.perf, c.z, c.p, c.p_alt, c.d, c.b, c.aux};
+                         c.phi, c.P, c.Vc, c.perf, c.z, c.p, c.p_alt, c.d, c.b, c.aux, c.reac};
     for (void* p : zero_list)
       if (p && cudaMemsetAsync(p, 0, fbytes, s)) {
         rc = HCA_ERR_CUDA;
@@ -539,9 +717,19 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     if (cudaMemsetAsync(c.state, 0, (size_t)h->total + 16, s) || cudaMemsetAsync(c.sync, 0, sizeof(hca::PassSync), s) ||
         cudaMemsetAsync(c.solve, 0, sizeof(hca::RepSolve) * n, s) ||
         cudaMemsetAsync(c.stats, 0, sizeof(hca::DevStats) * n, s) || cudaMemsetAsync(c.step, 0, sizeof(long long), s) ||
-        cudaMemsetAsync(c.list_count, 0, sizeof(int) * 27 * n, s)) {
+        cudaMemsetAsync(c.list_count, 0, sizeof(int) * 27 * n, s) ||
+        cudaMemsetAsync(c.n_kernels, 0, sizeof(unsigned long long), s)) {
       rc = HCA_ERR_CUDA;
       goto fail;
+    }
+    {
+      hca::PassSync ps{};
+      ps.guard_limit = h->maxit_all + 4;
+      ps.guard_outer_limit = h->max_outer + 2;
+      if (cudaMemcpyAsync(c.sync, &ps, sizeof(ps), cudaMemcpyHostToDevice, s) || cudaStreamSynchronize(s)) {
+        rc = HCA_ERR_CUDA;
+        goto fail;
+      }
     }
     // maps -> padded float staging buffers
     float *pc_d = nullptr, *pf_d = nullptr, *pv_d = nullptr;
@@ -693,15 +881,19 @@ int hca_create_batch(int32_t n, const hca_config* cfgs, const float* const* p_ce
 
 int hca_step(hca_handle* h, int32_t n_steps) {
   if (!h || n_steps < 0) return HCA_ERR_ARG;
+  if (n_steps == 0) return HCA_OK;
+  if (h->graphs_ok && !h->prof.on && run_graph(h, HCA_STAGE_ALL, n_steps) == HCA_OK) return check_convergence(h);
   for (int s = 0; s < n_steps; ++s) {
     int rc = run_stages(h, HCA_STAGE_ALL);
     if (rc) return rc;
   }
-  return n_steps > 0 ? check_convergence(h) : HCA_OK;
+  return check_convergence(h);
 }
 
 int hca_stage(hca_handle* h, uint32_t mask) {
   if (!h || (mask & ~HCA_STAGE_ALL)) return HCA_ERR_ARG;
+  if (!mask) return HCA_OK;
+  if (h->graphs_ok && !h->prof.on && run_graph(h, mask, 1) == HCA_OK) return check_convergence(h);
   int rc = run_stages(h, mask);
   if (rc) return rc;
   return check_convergence(h);
@@ -878,7 +1070,16 @@ int hca_get_shape(hca_handle* h, int32_t rep, int32_t* nx, int32_t* ny, int32_t*
   return HCA_OK;
 }
 
-int64_t hca_launch_count(hca_handle* h) { return h ? h->launches : -1; }
+int64_t hca_launch_count(hca_handle* h) {
+  if (!h) return -1;
+  unsigned long long n = 0;
+  if (cudaMemcpyAsync(&n, h->ctx.n_kernels, sizeof(n), cudaMemcpyDeviceToHost, h->ctx.stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->ctx.stream) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return -1;
+  }
+  return (int64_t)n;
+}
 
 int hca_profile_enable(hca_handle* h, int32_t enable) {
   if (!h) return HCA_ERR_ARG;

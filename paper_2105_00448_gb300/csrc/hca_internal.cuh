@@ -96,7 +96,18 @@ struct PassSync {
   unsigned int ticket;
   int active_count;     // replicates still iterating after the last pass B
   int error;            // nonzero: a norm became NaN/Inf
-  int pad;
+  int parity;           // which direction buffer holds the current p (0: p, 1: p_alt)
+  int guard;            // CG passes since the solve's set-up (loop insurance)
+  int guard_outer;      // defect-correction sweeps since the solve's first sweep
+  int guard_limit;      // passes after which a graph loop is forced to stop
+  int guard_outer_limit;
+};
+
+// A conditional-node handle of the step graph that a kernel's last block sets
+// (valid = 0 outside graph execution).
+struct CondArg {
+  unsigned long long h;
+  int valid;
 };
 
 // ------------------------------------------------------------- vectors ---
@@ -207,11 +218,11 @@ __device__ __forceinline__ double row_reduce(double v, int lpr) {
 // one thread); fin returns 1 if the replicate's solve stays active, and the
 // number of active replicates is left in sync->active_count.  `ndot` inner
 // products are carried.
-template <class Fin>
+template <class Fin, class Post>
 __device__ __forceinline__ void chunk_epilogue(double (*rows)[NDOT], int ndot, int chunk,
                                                double* __restrict__ partial, PassSync* sync,
                                                const RepDesc* __restrict__ reps, int n_reps,
-                                               Fin fin) {
+                                               Fin fin, Post post) {
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0) {
@@ -260,9 +271,21 @@ __device__ __forceinline__ void chunk_epilogue(double (*rows)[NDOT], int ndot, i
   }
   if (threadIdx.x == 0) {
     sync->active_count = n_active;
+    post(n_active);
     __threadfence();
     sync->ticket = 0u;
   }
+}
+
+template <class Fin>
+__device__ __forceinline__ void chunk_epilogue(double (*rows)[NDOT], int ndot, int chunk,
+                                               double* __restrict__ partial, PassSync* sync,
+                                               const RepDesc* __restrict__ reps, int n_reps, Fin fin) {
+  chunk_epilogue(rows, ndot, chunk, partial, sync, reps, n_reps, fin, [](int) {});
+}
+
+__device__ __forceinline__ void set_cond(const CondArg& c, bool v) {
+  if (c.valid) cudaGraphSetConditional((cudaGraphConditionalHandle)c.h, v ? 1u : 0u);
 }
 
 // -------------------------------------------------------------- launch --
@@ -292,6 +315,7 @@ struct Ctx {
   void* G_lo[MAX_DRUGS];
   void* dx;      // FP32 scheme: correction of the inner solve
   void* aux;     // scratch field (previous iterate of the initial oxygen fixed point)
+  void* reac;    // FP32 scheme: reaction part a of the diagonal d = c n + a
   void* phi;
   void* P;
   void* Vc;
@@ -308,7 +332,14 @@ struct Ctx {
   long long* step;        // device step counter n
   uint32_t* lists;
   int* list_count;        // [rep][27]
+  unsigned long long* n_kernels;  // kernels that ran (counted by block 0 of each)
 };
+
+// Count this kernel launch (call once, at kernel entry).
+#define HCA_COUNT_KERNEL(c)                                                  \
+  do {                                                                       \
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) atomicAdd((c).n_kernels, 1ull); \
+  } while (0)
 
 // Operator selector: 0 = oxygen, 1 + d = drug d.
 __device__ __forceinline__ double op_coupling(const RepDesc& rd, int which) {

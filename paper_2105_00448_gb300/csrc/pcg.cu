@@ -20,7 +20,8 @@
 // direction at neighbour sites from the old one, so the old and new
 // directions live in two buffers that swap roles every iteration (an in-place
 // update would let one block read a neighbour row another block has already
-// overwritten).
+// overwritten); a parity bit in device memory, flipped by pass B, names the
+// current buffer, so the same two kernels form the body of a graph loop.
 #include "hca_internal.cuh"
 
 namespace hca {
@@ -59,6 +60,22 @@ __device__ __forceinline__ T nb_sum(const V4<T>& v, int k, T left, T right, cons
   const T l = k == 0 ? left : v.a[k - 1];
   const T r = k == 3 ? right : v.a[k + 1];
   return ((l + r) + (ym.a[k] + yp.a[k])) + (zm.a[k] + zp.a[k]);
+}
+
+// Reaction coefficient a of the operator at one site (d = c n + a).
+template <typename T, int KIND>
+__device__ __forceinline__ T reaction_site(const RepDesc& rd, int which, uint8_t s, T K_prev, T pf) {
+  T a;
+  if (KIND == 0) {
+    a = is_consumer(s) ? (T)rd.phi_K / ((T)rd.K1 + K_prev) : T(0);
+    if (is_vessel(s)) a += (T)rd.r_K;
+  } else {
+    const int dd = which - 1;
+    a = (T)rd.base_drug[dd];
+    if (is_vessel(s)) a += (T)rd.kappa[dd] * pf;
+    if (is_cancer(s)) a += (T)rd.uptake[dd];
+  }
+  return a;
 }
 
 // Diagonal of the operator at one site.
@@ -112,7 +129,8 @@ __device__ __forceinline__ RowIter row_iter(const RepDesc& rd) {
 // r = b - A x0 with x0 the current field; writes d, z = r/d (and b for drugs);
 // reduces rho = r.z, |r|^2, |b|^2.
 template <typename T, int KIND>
-__global__ void __launch_bounds__(512) k_setup(Ctx c, int which) {
+__global__ void __launch_bounds__(512) k_setup(Ctx c, int which, CondArg cnd) {
+  HCA_COUNT_KERNEL(c);
   __shared__ double rows[CHUNK_ROWS][NDOT];
   __shared__ double s_G0;
   const int2 ch = c.chunks[blockIdx.x];
@@ -209,13 +227,20 @@ __global__ void __launch_bounds__(512) k_setup(Ctx c, int which) {
                    if (!fin) c.sync->error = 1;
                    sv.active = fin && !sv.zero_b && sqrt(s3[1]) > tol * sqrt(s3[2]) && rr.maxit > 0;
                    return sv.active;
+                 },
+                 [&](int n_active) {
+                   c.sync->parity = 0;
+                   c.sync->guard = 0;
+                   set_cond(cnd, n_active > 0);
                  });
 }
 
 // ----------------------------------------------------------------- pass A --
+// All loads of a group (own site and the four neighbour rows) are issued
+// before any value is used, so a group costs one memory round trip.
 template <typename T>
-__global__ void __launch_bounds__(512) k_pass_a(Ctx c, int which, const T* __restrict__ p_old,
-                                                T* __restrict__ p_new) {
+__global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) k_pass_a(Ctx c, int which) {
+  HCA_COUNT_KERNEL(c);
   __shared__ double rows[CHUNK_ROWS][NDOT];
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
@@ -223,8 +248,11 @@ __global__ void __launch_bounds__(512) k_pass_a(Ctx c, int which, const T* __res
   const RepSolve sv = c.solve[ch.x];
   if (sv.active) {
     const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+    const int gpr = rd.gpr;
+    const int par = c.sync->parity;
+    const T* __restrict__ pp = (const T*)(par ? c.p_alt : c.p);
+    T* __restrict__ p_new = (T*)(par ? c.p : c.p_alt);
     const T* __restrict__ zz = (const T*)c.z;
-    const T* __restrict__ pp = p_old;
     const T* __restrict__ dd = (const T*)c.d;
     const T beta = (T)sv.beta;
     const bool use_p = sv.beta != 0.0;
@@ -234,31 +262,45 @@ __global__ void __launch_bounds__(512) k_pass_a(Ctx c, int which, const T* __res
       const int rl = rbase + it.sub;
       const bool row_ok = rl < nrows;
       const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
-      double acc[NDOT] = {0.0, 0.0, 0.0};
+      double acc = 0.0;
       T carry = T(0);
       for (int itn = 0; itn < it.niter; ++itn) {
         const int g = itn * it.lpr + it.sl;
-        const bool gok = row_ok && g < rd.gpr;
+        const bool gok = row_ok && g < gpr;
         const long long e = geo.base + 4LL * g;
-        auto pnew = [&](long long o, bool ok) {
-          V4<T> zv = ld4_if(zz + o, ok);
-          if (use_p) {
-            const V4<T> pv = ld4_if(pp + o, ok);
+        const bool last_lane = it.sl == it.lpr - 1 && gok && g + 1 < gpr;
+        // issue every load of this group
+        const V4<T> z0 = ld4_if(zz + e, gok);
+        const V4<T> zym = ld4_if(zz + e - geo.sy, gok && geo.ym);
+        const V4<T> zyp = ld4_if(zz + e + geo.sy, gok && geo.yp);
+        const V4<T> zzm = ld4_if(zz + e - geo.sz, gok && geo.zm);
+        const V4<T> zzp = ld4_if(zz + e + geo.sz, gok && geo.zp);
+        const V4<T> D = ld4_if(dd + e, gok);
+        const T zr = last_lane ? zz[e + 4] : T(0);
+        V4<T> p0 = zero4<T>(), pym = zero4<T>(), pyp = zero4<T>(), pzm = zero4<T>(), pzp = zero4<T>();
+        T pr = T(0);
+        if (use_p) {
+          p0 = ld4_if(pp + e, gok);
+          pym = ld4_if(pp + e - geo.sy, gok && geo.ym);
+          pyp = ld4_if(pp + e + geo.sy, gok && geo.yp);
+          pzm = ld4_if(pp + e - geo.sz, gok && geo.zm);
+          pzp = ld4_if(pp + e + geo.sz, gok && geo.zp);
+          pr = last_lane ? pp[e + 4] : T(0);
+        }
+        // new direction at the site and at its neighbours: p = z + beta p_old
+        V4<T> PN, ym, yp, zm, zp;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) zv.a[k] += beta * pv.a[k];
-          }
-          return zv;
-        };
-        const V4<T> PN = pnew(e, gok);
-        const V4<T> ym = pnew(e - geo.sy, gok && geo.ym);
-        const V4<T> yp = pnew(e + geo.sy, gok && geo.yp);
-        const V4<T> zm = pnew(e - geo.sz, gok && geo.zm);
-        const V4<T> zp = pnew(e + geo.sz, gok && geo.zp);
+        for (int k = 0; k < 4; ++k) {
+          PN.a[k] = z0.a[k] + beta * p0.a[k];
+          ym.a[k] = zym.a[k] + beta * pym.a[k];
+          yp.a[k] = zyp.a[k] + beta * pyp.a[k];
+          zm.a[k] = zzm.a[k] + beta * pzm.a[k];
+          zp.a[k] = zzp.a[k] + beta * pzp.a[k];
+        }
+        const T right_next = zr + beta * pr;
         T left, right;
-        x_neighbours(PN, g, rd.gpr, it.sl, it.lpr, gok, carry, left, right,
-                     [&] { return zz[e + 4] + (use_p ? beta * pp[e + 4] : T(0)); });
+        x_neighbours(PN, g, gpr, it.sl, it.lpr, gok, carry, left, right, [&] { return right_next; });
         if (gok) {
-          const V4<T> D = ld4(dd + e);
           T g_s = 0;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
@@ -266,10 +308,10 @@ __global__ void __launch_bounds__(512) k_pass_a(Ctx c, int which, const T* __res
             g_s += PN.a[k] * q;
           }
           st4(p_new + e, PN);
-          acc[0] += (double)g_s;
+          acc += (double)g_s;
         }
       }
-      store_row(rows, rl, row_ok, it.sl, it.lpr, acc, 1);
+      store_row(rows, rl, row_ok, it.sl, it.lpr, &acc, 1);
     }
   }
   chunk_epilogue(rows, 1, blockIdx.x, c.partial, c.sync, c.reps, c.n_reps,
@@ -288,7 +330,8 @@ __global__ void __launch_bounds__(512) k_pass_a(Ctx c, int which, const T* __res
 
 // ----------------------------------------------------------------- pass B --
 template <typename T>
-__global__ void __launch_bounds__(512) k_pass_b(Ctx c, int which, const T* __restrict__ pdir, void* xfield) {
+__global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) k_pass_b(Ctx c, int which, void* xfield, CondArg cnd) {
+  HCA_COUNT_KERNEL(c);
   __shared__ double rows[CHUNK_ROWS][NDOT];
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
@@ -296,8 +339,9 @@ __global__ void __launch_bounds__(512) k_pass_b(Ctx c, int which, const T* __res
   const RepSolve sv = c.solve[ch.x];
   if (sv.active) {
     const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+    const int gpr = rd.gpr, nx = rd.nx;
     T* __restrict__ zz = (T*)c.z;
-    const T* __restrict__ pp = pdir;
+    const T* __restrict__ pp = (const T*)(c.sync->parity ? c.p : c.p_alt);
     const T* __restrict__ dd = (const T*)c.d;
     T* __restrict__ xx = (T*)xfield;
     const T alpha = (T)sv.alpha;
@@ -307,27 +351,30 @@ __global__ void __launch_bounds__(512) k_pass_b(Ctx c, int which, const T* __res
       const int rl = rbase + it.sub;
       const bool row_ok = rl < nrows;
       const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
-      double acc[NDOT] = {0.0, 0.0, 0.0};
+      double acc[2] = {0.0, 0.0};
       T carry = T(0);
       for (int itn = 0; itn < it.niter; ++itn) {
         const int g = itn * it.lpr + it.sl;
-        const bool gok = row_ok && g < rd.gpr;
+        const bool gok = row_ok && g < gpr;
         const long long e = geo.base + 4LL * g;
+        const bool last_lane = it.sl == it.lpr - 1 && gok && g + 1 < gpr;
+        // issue every load of this group
         const V4<T> P = ld4_if(pp + e, gok);
         const V4<T> ym = ld4_if(pp + e - geo.sy, gok && geo.ym);
         const V4<T> yp = ld4_if(pp + e + geo.sy, gok && geo.yp);
         const V4<T> zm = ld4_if(pp + e - geo.sz, gok && geo.zm);
         const V4<T> zp = ld4_if(pp + e + geo.sz, gok && geo.zp);
+        const V4<T> D = ld4_if(dd + e, gok);
+        V4<T> X = ld4_if(xx + e, gok);
+        V4<T> Z = ld4_if(zz + e, gok);
+        const T pr = last_lane ? pp[e + 4] : T(0);
         T left, right;
-        x_neighbours(P, g, rd.gpr, it.sl, it.lpr, gok, carry, left, right, [&] { return pp[e + 4]; });
+        x_neighbours(P, g, gpr, it.sl, it.lpr, gok, carry, left, right, [&] { return pr; });
         if (gok) {
-          const V4<T> D = ld4(dd + e);
-          V4<T> X = ld4(xx + e);
-          V4<T> Z = ld4(zz + e);
           T g_rho = 0, g_rr = 0;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            if (4 * g + k < rd.nx) {
+            if (4 * g + k < nx) {
               const T q = D.a[k] * P.a[k] - cpl * nb_sum(P, k, left, right, ym, yp, zm, zp);
               X.a[k] += alpha * P.a[k];
               Z.a[k] -= alpha * (q / D.a[k]);
@@ -361,6 +408,17 @@ __global__ void __launch_bounds__(512) k_pass_b(Ctx c, int which, const T* __res
                    const bool conv = sqrt(s2[1]) <= s.rtol * sqrt(s.bnorm2);
                    if (conv || s.iters >= s.maxit) s.active = 0;
                    return s.active;
+                 },
+                 [&](int n_active) {
+                   c.sync->parity ^= 1;
+                   const int g = ++c.sync->guard;
+                   bool go = n_active > 0;
+                   if (go && g >= c.sync->guard_limit) {
+                     // every replicate stops at maxit; this only guards the graph loop
+                     c.sync->error = 2;
+                     go = false;
+                   }
+                   set_cond(cnd, go);
                  });
 }
 
@@ -370,6 +428,7 @@ __global__ void __launch_bounds__(512) k_pass_b(Ctx c, int which, const T* __res
 // statistics slot `which`.
 template <typename T, int KIND>
 __global__ void __launch_bounds__(512) k_true_residual(Ctx c, int which, void* xfield) {
+  HCA_COUNT_KERNEL(c);
   __shared__ double rows[CHUNK_ROWS][NDOT];
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
@@ -442,6 +501,7 @@ __global__ void __launch_bounds__(512) k_true_residual(Ctx c, int which, void* x
 // x = 0 for replicates whose right-hand side vanished.
 template <typename T>
 __global__ void k_zero_if_b_zero(Ctx c, void* xfield) {
+  HCA_COUNT_KERNEL(c);
   const int2 ch = c.chunks[blockIdx.x];
   if (!c.solve[ch.x].zero_b) return;
   const RepDesc& rd = c.reps[ch.x];
@@ -458,6 +518,7 @@ __global__ void k_zero_if_b_zero(Ctx c, void* xfield) {
 template <typename T, int KIND>
 __global__ void __launch_bounds__(512) k_apply(Ctx c, int which, int rep, const T* __restrict__ u,
                                                T* __restrict__ out) {
+  HCA_COUNT_KERNEL(c);
   const int2 ch = c.chunks[blockIdx.x];
   if (ch.x != rep) return;
   const RepDesc& rd = c.reps[ch.x];
@@ -506,6 +567,7 @@ __global__ void __launch_bounds__(512) k_apply(Ctx c, int which, int rep, const 
 // by the fixed-point iteration of the initial oxygen field.
 template <typename T>
 __global__ void __launch_bounds__(512) k_diff_norms(Ctx c, const T* __restrict__ a, const T* __restrict__ b) {
+  HCA_COUNT_KERNEL(c);
   __shared__ double rows[CHUNK_ROWS][NDOT];
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
@@ -545,14 +607,19 @@ __global__ void __launch_bounds__(512) k_diff_norms(Ctx c, const T* __restrict__
 
 // --------------------------------------------------- defect correction ---
 // FP32 storage scheme.  The solution is kept as two FP32 words, x = x_hi +
-// x_lo.  Each sweep evaluates the residual r = b - A x in FP64 from the FP32
-// operator coefficients (d, c) and the two-word solution, stops the solve when
-// |r| <= rtol |b| (FP64 norms), and otherwise starts an FP32 inner CG on the
-// correction: A dx = fl32(r), dx0 = 0, to the inner tolerance.  The first
-// sweep of a solve also builds and stores d (and b for a drug).
+// x_lo.  Each sweep evaluates the residual r = b - A x in FP64 from the
+// two-word solution, with the diagonal rebuilt in FP64 as c n + a from the
+// stored FP32 reaction coefficient a (storing d = c n + a itself in FP32 would
+// round away most digits of the small reaction part: 1/dt + psi ~ 0.03 next to
+// c n ~ 600 for a drug).  It stops the solve when |r| <= rtol |b| (FP64 norms)
+// and otherwise starts an FP32 inner CG on the correction, A32 dx = fl32(r),
+// dx0 = 0, to the inner tolerance, where A32 uses the FP32 diagonal.  The first
+// sweep of a solve also builds and stores a, d (and b for a drug).
 template <int KIND>
 __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const float* __restrict__ x_hi,
-                                                     const float* __restrict__ x_lo, int first) {
+                                                     const float* __restrict__ x_lo, int first, CondArg outer,
+                                                     CondArg inner) {
+  HCA_COUNT_KERNEL(c);
   __shared__ double rows[CHUNK_ROWS][NDOT];
   __shared__ double s_G0;
   const int2 ch = c.chunks[blockIdx.x];
@@ -571,6 +638,7 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
   if (live) {
     const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
     float* __restrict__ dd = (float*)c.d;
+    float* __restrict__ aa = (float*)c.reac;
     float* __restrict__ zz = (float*)c.z;
     float* __restrict__ bb = (float*)c.b;
     float* __restrict__ dxv = (float*)c.dx;
@@ -605,7 +673,7 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
         x_neighbours(X, g, rd.gpr, it.sl, it.lpr, gok, carry, left, right,
                      [&] { return (double)x_hi[e + 4] + (double)x_lo[e + 4]; });
         if (gok) {
-          V4<float> D, B;
+          V4<float> D, B, AR;
           if (first) {
             const uchar4 st = ld_state4(c.state + e);
             V4<float> PF = zero4<float>();
@@ -616,17 +684,21 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
               const uint8_t s = st_at(st, k);
               D.a[k] = 0.f;
               B.a[k] = 0.f;
+              AR.a[k] = 0.f;
               if (xk < rd.nx) {
                 // the operator is linearised about the solution at the start of the solve
-                D.a[k] = diag_site<float, KIND>(rd, which, neighbour_count(rd, geo, xk), s, (float)X.a[k], PF.a[k]);
+                AR.a[k] = reaction_site<float, KIND>(rd, which, s, (float)X.a[k], PF.a[k]);
+                D.a[k] = (float)cpl * (float)neighbour_count(rd, geo, xk) + AR.a[k];
                 if (KIND == 0) B.a[k] = is_vessel(s) ? bvessel : 0.f;
                 else B.a[k] = (float)(X.a[k] * rd.inv_dt) + (is_vessel(s) ? (float)rd.kappa[which - 1] * PF.a[k] * G0 : 0.f);
               }
             }
             st4(dd + e, D);
+            st4(aa + e, AR);
             st4(bb + e, B);
           } else {
             D = ld4(dd + e);
+            AR = ld4(aa + e);
             B = ld4(bb + e);
           }
           V4<float> Z;
@@ -636,7 +708,8 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
           for (int k = 0; k < 4; ++k) {
             Z.a[k] = 0.f;
             if (4 * g + k < rd.nx) {
-              const double r = (double)B.a[k] - ((double)D.a[k] * X.a[k] - cpl * nb_sum(X, k, left, right, ym, yp, zm, zp));
+              const double d64 = cpl * (double)neighbour_count(rd, geo, 4 * g + k) + (double)AR.a[k];
+              const double r = (double)B.a[k] - (d64 * X.a[k] - cpl * nb_sum(X, k, left, right, ym, yp, zm, zp));
               const float r32 = (float)r;
               const float zk = D.a[k] != 0.f ? r32 / D.a[k] : 0.f;
               Z.a[k] = zk;
@@ -709,11 +782,24 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
                    s.dc_apply = 1;
                    s.active = s3[2] > 0.0 ? 1 : 0;
                    return s.active;
+                 },
+                 [&](int n_active) {
+                   c.sync->parity = 0;
+                   c.sync->guard = 0;
+                   const int g = first ? (c.sync->guard_outer = 0) : ++c.sync->guard_outer;
+                   bool go = n_active > 0;
+                   if (go && g >= c.sync->guard_outer_limit) {
+                     c.sync->error = 2;
+                     go = false;
+                   }
+                   set_cond(outer, go);
+                   set_cond(inner, go);
                  });
 }
 
 // x_hi + x_lo += dx (two-word sum), or x = 0 for a vanishing right-hand side.
 __global__ void __launch_bounds__(512) k_dc_update(Ctx c, float* __restrict__ x_hi, float* __restrict__ x_lo) {
+  HCA_COUNT_KERNEL(c);
   const int2 ch = c.chunks[blockIdx.x];
   const RepSolve sv = c.solve[ch.x];
   if (!sv.dc_apply && !sv.zero_b) return;
@@ -751,11 +837,14 @@ __global__ void __launch_bounds__(512) k_dc_update(Ctx c, float* __restrict__ x_
 }  // namespace
 
 // ------------------------------------------------------------- launchers --
-void launch_dc_residual(const Ctx& c, int which, const void* x_hi, const void* x_lo, bool first) {
+void launch_dc_residual(const Ctx& c, int which, const void* x_hi, const void* x_lo, bool first, CondArg outer,
+                        CondArg inner) {
   if (which == 0)
-    k_dc_residual<0><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, (const float*)x_hi, (const float*)x_lo, first);
+    k_dc_residual<0><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, (const float*)x_hi, (const float*)x_lo, first,
+                                                              outer, inner);
   else
-    k_dc_residual<1><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, (const float*)x_hi, (const float*)x_lo, first);
+    k_dc_residual<1><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, (const float*)x_hi, (const float*)x_lo, first,
+                                                              outer, inner);
 }
 
 void launch_dc_update(const Ctx& c, void* x_hi, void* x_lo) {
@@ -768,24 +857,24 @@ void launch_diff_norms(const Ctx& c, const void* a, const void* b, bool fp64) {
 }
 
 template <typename T>
-static void launch_setup_t(const Ctx& c, int which) {
-  if (which == 0) k_setup<T, 0><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which);
-  else k_setup<T, 1><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which);
+static void launch_setup_t(const Ctx& c, int which, CondArg cnd) {
+  if (which == 0) k_setup<T, 0><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, cnd);
+  else k_setup<T, 1><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, cnd);
 }
 
-void launch_setup(const Ctx& c, int which, bool fp64) {
-  if (fp64) launch_setup_t<double>(c, which);
-  else launch_setup_t<float>(c, which);
+void launch_setup(const Ctx& c, int which, bool fp64, CondArg cnd) {
+  if (fp64) launch_setup_t<double>(c, which, cnd);
+  else launch_setup_t<float>(c, which, cnd);
 }
 
-void launch_pass_a(const Ctx& c, int which, const void* p_old, void* p_new, bool fp64) {
-  if (fp64) k_pass_a<double><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, (const double*)p_old, (double*)p_new);
-  else k_pass_a<float><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, (const float*)p_old, (float*)p_new);
+void launch_pass_a(const Ctx& c, int which, bool fp64) {
+  if (fp64) k_pass_a<double><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which);
+  else k_pass_a<float><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which);
 }
 
-void launch_pass_b(const Ctx& c, int which, const void* pdir, void* xfield, bool fp64) {
-  if (fp64) k_pass_b<double><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, (const double*)pdir, xfield);
-  else k_pass_b<float><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, (const float*)pdir, xfield);
+void launch_pass_b(const Ctx& c, int which, void* xfield, bool fp64, CondArg cnd) {
+  if (fp64) k_pass_b<double><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, xfield, cnd);
+  else k_pass_b<float><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, xfield, cnd);
 }
 
 void launch_true_residual(const Ctx& c, int which, void* xfield, bool fp64) {
