@@ -620,6 +620,11 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
   h->n_drugs = cfgs[0].n_drugs;
   h->stream = (cudaStream_t)cfgs[0].stream;
   h->cfgs.assign(cfgs, cfgs + n);
+  {
+    // HCA_NO_GRAPH=1 runs steps from a host loop instead of the step graph
+    const char* ng = std::getenv("HCA_NO_GRAPH");
+    if (ng && ng[0] == '1') h->graphs_ok = false;
+  }
   cudaGetDevice(&h->device);
   int sm = 0;
   cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, h->device);

@@ -77,6 +77,7 @@ struct RepSolve {
   int outer;       // defect-correction sweeps done in this solve
   int dc_apply;    // 1: the last inner solve's correction is to be added
   int pad[2];
+  double scale;    // power of two applied to the inner problem (1 for plain solves)
 };
 
 // Per-replicate statistics written by kernels; copied out by hca_get_stats.

@@ -219,6 +219,7 @@ __global__ void __launch_bounds__(512) k_setup(Ctx c, int which, CondArg cnd) {
                    sv.bnorm2 = s3[2];
                    sv.alpha = 0.0;
                    sv.beta = 0.0;
+                   sv.scale = 1.0;
                    sv.iters = 0;
                    sv.rtol = tol;
                    sv.maxit = rr.maxit;
@@ -256,6 +257,8 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) k_pass_a(Ctx c, int which
     const T* __restrict__ dd = (const T*)c.d;
     const T beta = (T)sv.beta;
     const bool use_p = sv.beta != 0.0;
+    // the first iteration of a rescaled inner solve starts from scale * z
+    const T zs = sv.iters == 0 ? (T)sv.scale : T(1);
     const T cpl = (T)op_coupling(rd, which);
     const RowIter it = row_iter(rd);
     for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
@@ -291,13 +294,13 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) k_pass_a(Ctx c, int which
         V4<T> PN, ym, yp, zm, zp;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          PN.a[k] = z0.a[k] + beta * p0.a[k];
-          ym.a[k] = zym.a[k] + beta * pym.a[k];
-          yp.a[k] = zyp.a[k] + beta * pyp.a[k];
-          zm.a[k] = zzm.a[k] + beta * pzm.a[k];
-          zp.a[k] = zzp.a[k] + beta * pzp.a[k];
+          PN.a[k] = zs * z0.a[k] + beta * p0.a[k];
+          ym.a[k] = zs * zym.a[k] + beta * pym.a[k];
+          yp.a[k] = zs * zyp.a[k] + beta * pyp.a[k];
+          zm.a[k] = zs * zzm.a[k] + beta * pzm.a[k];
+          zp.a[k] = zs * zzp.a[k] + beta * pzp.a[k];
         }
-        const T right_next = zr + beta * pr;
+        const T right_next = zs * zr + beta * pr;
         T left, right;
         x_neighbours(PN, g, gpr, it.sl, it.lpr, gok, carry, left, right, [&] { return right_next; });
         if (gok) {
@@ -345,6 +348,7 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) k_pass_b(Ctx c, int which
     const T* __restrict__ dd = (const T*)c.d;
     T* __restrict__ xx = (T*)xfield;
     const T alpha = (T)sv.alpha;
+    const T zs = sv.iters == 0 ? (T)sv.scale : T(1);
     const T cpl = (T)op_coupling(rd, which);
     const RowIter it = row_iter(rd);
     for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
@@ -377,7 +381,7 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) k_pass_b(Ctx c, int which
             if (4 * g + k < nx) {
               const T q = D.a[k] * P.a[k] - cpl * nb_sum(P, k, left, right, ym, yp, zm, zp);
               X.a[k] += alpha * P.a[k];
-              Z.a[k] -= alpha * (q / D.a[k]);
+              Z.a[k] = zs * Z.a[k] - alpha * (q / D.a[k]);
               const T r = D.a[k] * Z.a[k];
               g_rho += r * Z.a[k];
               g_rr += r * r;
@@ -702,8 +706,7 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
             B = ld4(bb + e);
           }
           V4<float> Z;
-          double g_rr = 0.0, g_bb = 0.0;
-          float g_rho = 0.f;
+          double g_rr = 0.0, g_bb = 0.0, g_rho = 0.0;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             Z.a[k] = 0.f;
@@ -715,14 +718,14 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
               Z.a[k] = zk;
               g_rr += r * r;
               g_bb += (double)B.a[k] * (double)B.a[k];
-              g_rho += r32 * zk;
+              g_rho += r * (double)zk;     // FP64: FP32 products of a tiny residual underflow
             }
           }
           st4(zz + e, Z);
           st4(dxv + e, zero4<float>());
           acc[0] += g_rr;
           acc[1] += g_bb;
-          acc[2] += (double)g_rho;
+          acc[2] += g_rho;
         }
       }
       store_row(rows, rl, row_ok, it.sl, it.lpr, acc, 3);
@@ -769,11 +772,20 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
                      s.dc_apply = 0;
                      return 0;
                    }
-                   // start the inner FP32 solve A dx = fl32(r)
+                   // start the inner FP32 solve A dx = fl32(r), rescaled by a
+                   // power of two so that its values are O(1) per site (the
+                   // residual of a decayed field can be ~1e-22, whose FP32
+                   // squares underflow); the update divides the scale out
                    s.outer += 1;
-                   s.rho = s3[2];
-                   s.rnorm2 = s3[0];
-                   s.bnorm2 = s3[0];
+                   const double n_sites = (double)rr.nx * rr.ny * rr.nz;
+                   const double rms = sqrt(s3[0] / n_sites);
+                   int e = rms > 0.0 ? -ilogb(rms) : 0;
+                   e = e < -120 ? -120 : (e > 120 ? 120 : e);
+                   const double sc = ldexp(1.0, e);
+                   s.scale = sc;
+                   s.rho = s3[2] * sc * sc;
+                   s.rnorm2 = s3[0] * sc * sc;
+                   s.bnorm2 = s3[0] * sc * sc;
                    s.rtol = rr.rtol_inner;
                    s.maxit = rr.maxit;
                    s.iters = 0;
@@ -808,6 +820,7 @@ __global__ void __launch_bounds__(512) k_dc_update(Ctx c, float* __restrict__ x_
   const long long base0 = rd.off + (long long)ch.y * rd.nxp;
   const int ngroups = nrows * rd.gpr;
   const float* __restrict__ dxv = (const float*)c.dx;
+  const float inv_s = (float)(1.0 / sv.scale);   // a power of two: exact
   for (int gi = threadIdx.x; gi < ngroups; gi += blockDim.x) {
     const int rl = gi / rd.gpr, g = gi % rd.gpr;
     const long long e = base0 + (long long)rl * rd.nxp + 4LL * g;
@@ -817,7 +830,9 @@ __global__ void __launch_bounds__(512) k_dc_update(Ctx c, float* __restrict__ x_
       continue;
     }
     V4<float> H = ld4(x_hi + e), L = ld4(x_lo + e);
-    const V4<float> D = ld4(dxv + e);
+    V4<float> D = ld4(dxv + e);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) D.a[k] = __fmul_rn(D.a[k], inv_s);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       // two-sum of hi and dx, then renormalise with the low word

@@ -168,6 +168,30 @@ def test_fp32_defect_correction_reaches_fp64_tolerance(shape, rng):
     assert errK <= 1e-6 and errG <= 1e-6
 
 
+@pytest.mark.parametrize("shape", SHAPES[1:3])
+def test_fp32_defect_correction_decayed_field(shape, rng):
+    # a drug washed out to ~1e-10 of its peak (epirubicin a day after a bolus):
+    # the inner problem's residual is ~1e-22, so it must be rescaled to stay
+    # clear of FP32 underflow
+    sim, cfg, _ = make_pair(shape, "f32", seed=9, n_drugs=2, picard_maxit=1, rtol_drug=1e-8, max_outer=10)
+    st = random_states(shape, rng)
+    sim.set_states(st)
+    sim.set_step(30)
+    G_old = (rng.random(shape) * 1e-10).astype(np.float32)
+    sim.set_field(hca.FIELD_DRUG1, G_old)
+    rc = sim.stage(hca.STAGE_DRUGS)
+    s = sim.stats()
+    assert rc == hca.HCA_OK and s["drug_rel_residual"][1] <= 1e-8
+    assert s["drug_iterations"][1] < 2000, s["drug_iterations"]
+    from oracle.model import plasma_levels
+    perf = sim.field(hca.FIELD_PERF).astype(np.float64)
+    cfg64 = cfg.replace(precision="f64", rtol_drug=1e-11)
+    ref, _ = drug_solve(st, perf, G_old.astype(np.float64), plasma_levels(cfg, 31 * cfg.dt)[1], cfg64, 1)
+    got = sim.field(hca.FIELD_DRUG1).astype(np.float64)
+    assert np.max(np.abs(got - ref)) <= 1e-6 * np.max(np.abs(ref))
+    sim.close()
+
+
 @pytest.mark.parametrize("shape", SHAPES[:3])
 def test_fp32_plain_cg_error(shape, rng):
     # plain FP32 CG (no defect correction): the stored-FP32 residual floor of
