@@ -29,6 +29,7 @@ UNITS = {
     "cell.cu": [],
     "ca.cu": ["-fmad=false"],
     "engine.cu": [],
+    "noalloc.cu": [],
 }
 
 

@@ -119,7 +119,7 @@ EXPORTS = [
     "hca_read_fields", "hca_write_fields", "hca_read_states", "hca_write_states",
     "hca_set_step", "hca_get_stats", "hca_apply_operator", "hca_philox_uniforms",
     "hca_sync", "hca_get_shape", "hca_launch_count", "hca_profile_enable", "hca_get_profile",
-    "hca_destroy", "hca_status_string",
+    "hca_o2_residual_noalloc", "hca_destroy", "hca_status_string",
 ]
 
 _lib = None
@@ -170,6 +170,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "hca_launch_count": (I64, [P]),
         "hca_profile_enable": (ctypes.c_int, [P, I32]),
         "hca_get_profile": (ctypes.c_int, [P, ctypes.POINTER(hca_profile)]),
+        "hca_o2_residual_noalloc": (ctypes.c_int, [cfgp, P, P, P, ctypes.POINTER(ctypes.c_double), P]),
         "hca_destroy": (None, [P]),
         "hca_status_string": (ctypes.c_char_p, [I32]),
     }
@@ -334,6 +335,21 @@ def hca_get_profile(h) -> Dict:
     out = hca_profile()
     _check(load().hca_get_profile(h, ctypes.byref(out)), "hca_get_profile")
     return out.as_dict()
+
+
+def hca_o2_residual_noalloc(cfg: hca_config, state, K_prev, K, stream=None) -> float:
+    """||b - A(K_prev) K|| / ||b|| on caller-owned device tensors, with no device
+    allocation (for callers that may not allocate; see include/hca.h)."""
+    ptrs = [_ptr(t) for t in (state, K_prev, K)]
+    if not all(p[2] for p in ptrs):
+        raise ValueError("state, K_prev and K must be device tensors")
+    n = cfg.nx * cfg.ny * cfg.nz
+    if ptrs[0][1] < n or ptrs[1][1] < 8 * n or ptrs[2][1] < 8 * n:
+        raise ValueError("arrays too small for the lattice")
+    out = ctypes.c_double()
+    _check(load().hca_o2_residual_noalloc(ctypes.byref(cfg), ptrs[0][0], ptrs[1][0], ptrs[2][0], ctypes.byref(out),
+                                          ctypes.c_void_p(int(stream) if stream else 0)), "hca_o2_residual_noalloc")
+    return out.value
 
 
 def hca_destroy(h) -> None:
