@@ -144,7 +144,7 @@ typedef struct hca_config {
   int32_t max_outer;     /* defect-correction sweeps per oxygen solve (8) */
 
   int32_t warm_start;    /* HCA_WS_PREV */
-  int32_t threads_per_block; /* 0 = library choice; else 128, 256 or 512 (tile autotuning) */
+  int32_t threads_per_block; /* 0 = library choice (128); else 64, 128, 256 or 512; results do not depend on it */
   void* stream;          /* cudaStream_t, NULL = default stream */
 } hca_config;
 

@@ -29,6 +29,8 @@ void launch_philox_uniforms(unsigned long long seed, unsigned long long site0, l
 void launch_advance_step(const Ctx& c, long long by);
 void launch_ca_compact(const Ctx& c, bool fp64);
 void launch_ca_colour(const Ctx& c, int colour, int blocks_x, bool fp64);
+void set_pass_regs(int r);
+void set_pass_ni(int ni);
 }  // namespace hca
 
 using hca::Ctx;
@@ -266,6 +268,12 @@ void* field_ptr(hca_handle* h, uint32_t bit) {
 
 constexpr hca::CondArg kNoCond{0ull, 0};
 
+void pass_a(hca_handle* h, int which) { hca::launch_pass_a(h->ctx, which, h->fp64); }
+
+void pass_b(hca_handle* h, int which, void* x, hca::CondArg cnd) {
+  hca::launch_pass_b(h->ctx, which, x, h->fp64, cnd);
+}
+
 // CG iterations (pass A, pass B) on operator `which` for every replicate whose
 // solve is active, updating x, until none is active or maxit is reached.  The
 // first convergence check comes after about as many iterations as the same
@@ -282,8 +290,8 @@ int pcg_iterate(hca_handle* h, int which, void* x, int predict) {
     if (h->h_pinned[0] == 0 || done >= h->maxit_all) break;
     const int n = std::min(chunk, h->maxit_all - done);
     for (int k = 0; k < n; ++k) {
-      HCA_LAUNCH(h, HCA_KCLASS_PASS_A, 1, hca::launch_pass_a(c, which, h->fp64));
-      HCA_LAUNCH(h, HCA_KCLASS_PASS_B, 1, hca::launch_pass_b(c, which, x, h->fp64, kNoCond));
+      HCA_LAUNCH(h, HCA_KCLASS_PASS_A, 1, pass_a(h, which));
+      HCA_LAUNCH(h, HCA_KCLASS_PASS_B, 1, pass_b(h, which, x, kNoCond));
     }
     done += n;
     chunk = h->prof.on ? 1 : 4;
@@ -383,8 +391,8 @@ int cap_solve(hca_handle* h, int which, cudaGraph_t G) {
     if ((rc = add_while(S, H, &body))) return rc;
     HCA_TRY(cudaStreamBeginCaptureToGraph(S2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     c.stream = S2;
-    hca::launch_pass_a(c, which, h->fp64);
-    hca::launch_pass_b(c, which, x, h->fp64, cnd);
+    pass_a(h, which);
+    pass_b(h, which, x, cnd);
     HCA_TRY(cudaGetLastError());
     HCA_TRY(cudaStreamEndCapture(S2, &body));
     c.stream = S;
@@ -407,8 +415,8 @@ int cap_solve(hca_handle* h, int which, cudaGraph_t G) {
   if ((rc = add_while(S2, Hi, &bi))) return rc;
   HCA_TRY(cudaStreamBeginCaptureToGraph(S3, bi, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   c.stream = S3;
-  hca::launch_pass_a(c, which, h->fp64);
-  hca::launch_pass_b(c, which, c.dx, h->fp64, ci);
+  pass_a(h, which);
+  pass_b(h, which, c.dx, ci);
   HCA_TRY(cudaGetLastError());
   HCA_TRY(cudaStreamEndCapture(S3, &bi));
   c.stream = S2;
@@ -579,6 +587,9 @@ int initial_oxygen(hca_handle* h) {
     maxit = std::max(maxit, cf.picard_maxit);
   }
   const size_t bytes = (size_t)h->total * elem_size(h);
+  // a replicate that has converged is frozen, so a batch gives every
+  // replicate exactly the iterations it would get alone
+  std::vector<int> frozen(h->n_reps, 0);
   int it = 0;
   for (it = 1; it <= maxit; ++it) {
     HCA_TRY(cudaMemcpyAsync(c.aux, c.K, bytes, cudaMemcpyDeviceToDevice, c.stream));
@@ -590,12 +601,17 @@ int initial_oxygen(hca_handle* h) {
     HCA_TRY(cudaStreamSynchronize(c.stream));
     bool all = true;
     for (int r = 0; r < h->n_reps; ++r) {
+      if (frozen[r]) continue;
       const double change = std::sqrt(sv[r].rnorm2), norm = std::sqrt(sv[r].bnorm2);
       if (!std::isfinite(change) || !std::isfinite(norm)) return HCA_ERR_NONFINITE;
-      if (!(norm == 0.0 || change <= h->cfgs[r].picard_tol * norm)) all = false;
+      if (norm == 0.0 || change <= h->cfgs[r].picard_tol * norm || it >= h->cfgs[r].picard_maxit) frozen[r] = 1;
+      else all = false;
     }
     if (all) break;
+    HCA_TRY(cudaMemcpyAsync(c.frozen, frozen.data(), sizeof(int) * h->n_reps, cudaMemcpyHostToDevice, c.stream));
   }
+  HCA_TRY(cudaMemsetAsync(c.frozen, 0, sizeof(int) * h->n_reps, c.stream));
+  HCA_TRY(cudaStreamSynchronize(c.stream));
   h->picard_iterations = std::min(it, maxit);
   return HCA_OK;
 }
@@ -624,6 +640,9 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     // HCA_NO_GRAPH=1 runs steps from a host loop instead of the step graph
     const char* ng = std::getenv("HCA_NO_GRAPH");
     if (ng && ng[0] == '1') h->graphs_ok = false;
+    // HCA_PASS_REGS=64|80|96|128 overrides the CG passes' register cap (tuning)
+    const char* pr = std::getenv("HCA_PASS_REGS");
+    if (pr) hca::set_pass_regs(std::atoi(pr));
   }
   cudaGetDevice(&h->device);
   int sm = 0;
@@ -632,7 +651,7 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
 
   // layout
   long long off = 0, loff = 0;
-  int chunk0 = 0;
+  int chunk0 = 0, super0 = 0;
   for (int i = 0; i < n; ++i) {
     RepDesc r = make_desc(cfgs[i]);
     r.off = off;
@@ -640,6 +659,9 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     const int rows = r.ny * r.nz;
     r.chunk_begin = chunk0;
     r.n_chunks = (rows + hca::CHUNK_ROWS - 1) / hca::CHUNK_ROWS;
+    r.super_begin = super0;
+    r.n_supers = (r.n_chunks + hca::SUPER_CHUNKS - 1) / hca::SUPER_CHUNKS;
+    super0 += r.n_supers;
     for (int k = 0; k < r.n_chunks; ++k) h->chunks_h.push_back(make_int2(i, k * hca::CHUNK_ROWS));
     chunk0 += r.n_chunks;
     for (int col = 0; col < 27; ++col) {
@@ -658,7 +680,9 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
   Ctx& c = h->ctx;
   c.n_reps = n;
   c.n_chunks = chunk0;
-  c.threads = cfgs[0].threads_per_block ? cfgs[0].threads_per_block : 256;
+  c.n_supers = super0;
+  // 128 threads per block measured fastest for the CG passes on GB300
+  c.threads = cfgs[0].threads_per_block ? cfgs[0].threads_per_block : 128;
   c.stream = h->stream;
   const size_t es = elem_size(h);
   const size_t fbytes = (size_t)h->total * es;
@@ -699,6 +723,11 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     ALLOC(c.lists, sizeof(uint32_t) * (size_t)std::max(1LL, h->lists_total));
     ALLOC(c.list_count, sizeof(int) * 27 * n);
     ALLOC(c.n_kernels, sizeof(unsigned long long));
+    ALLOC(c.frozen, sizeof(int) * n);
+    ALLOC(c.rowp, sizeof(double) * hca::NDOT * hca::CHUNK_ROWS * (size_t)chunk0);
+    ALLOC(c.chunk_cnt, sizeof(int) * (size_t)chunk0);
+    ALLOC(c.superp, sizeof(double) * hca::NDOT * (size_t)super0);
+    ALLOC(c.super_cnt, sizeof(int) * (size_t)super0);
     if (cudaMallocHost(&h->h_pinned, 4 * sizeof(int)) != cudaSuccess) {
       (void)cudaGetLastError();
       rc = HCA_ERR_OOM;
@@ -723,7 +752,10 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
         cudaMemsetAsync(c.solve, 0, sizeof(hca::RepSolve) * n, s) ||
         cudaMemsetAsync(c.stats, 0, sizeof(hca::DevStats) * n, s) || cudaMemsetAsync(c.step, 0, sizeof(long long), s) ||
         cudaMemsetAsync(c.list_count, 0, sizeof(int) * 27 * n, s) ||
-        cudaMemsetAsync(c.n_kernels, 0, sizeof(unsigned long long), s)) {
+        cudaMemsetAsync(c.n_kernels, 0, sizeof(unsigned long long), s) ||
+        cudaMemsetAsync(c.frozen, 0, sizeof(int) * n, s) ||
+        cudaMemsetAsync(c.chunk_cnt, 0, sizeof(int) * (size_t)chunk0, s) ||
+        cudaMemsetAsync(c.super_cnt, 0, sizeof(int) * (size_t)super0, s)) {
       rc = HCA_ERR_CUDA;
       goto fail;
     }
@@ -780,6 +812,15 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     if (err_h) {
       rc = HCA_ERR_NONFINITE;
       goto fail;
+    }
+    {
+      // a common groups-per-lane count lets the passes use a compile-time trip count
+      int ni = -1;
+      for (auto& r : h->reps_h) {
+        const int v = (r.gpr + r.lpr - 1) / r.lpr;
+        ni = (ni < 0 || ni == v) ? v : 0;
+      }
+      hca::set_pass_ni(ni == 1 || ni == 2 || ni == 4 ? ni : 0);
     }
     rc = initial_oxygen(h);
     if (rc) goto fail;

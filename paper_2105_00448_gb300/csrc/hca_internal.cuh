@@ -27,7 +27,7 @@ constexpr int VEC = 4;          // sites per thread access
 constexpr int CHUNK_ROWS = 32;  // rows per reduction chunk
 constexpr int NDOT = 3;         // inner products carried per pass
 constexpr int MAX_DRUGS = 3;
-constexpr int FINAL_LANES = 256;  // virtual lanes of the per-replicate final reduction
+constexpr int SUPER_CHUNKS = 64;  // chunks per second-level reduction group
 
 // ---------------------------------------------------------------- params --
 // Per-replicate constants, read-only on the device.
@@ -38,6 +38,8 @@ struct RepDesc {
   int lpr;                // lanes per row (power of two, <= 32)
   int chunk_begin;        // first chunk of this replicate in the chunk table
   int n_chunks;
+  int super_begin;        // first group of SUPER_CHUNKS chunks of this replicate
+  int n_supers;
   unsigned long long seed;
   int n_drugs;
   int maxit;
@@ -212,88 +214,9 @@ __device__ __forceinline__ double row_reduce(double v, int lpr) {
   return v;
 }
 
-// Fixed-order block epilogue: rows[CHUNK_ROWS][NDOT] (shared) -> one partial
-// per inner product for this chunk, written to partial[chunk * NDOT + k].
-// Then the last block to finish (ticket) reduces every replicate's chunk
-// partials in fixed order and calls `fin(rep, sums)` once per replicate (from
-// one thread); fin returns 1 if the replicate's solve stays active, and the
-// number of active replicates is left in sync->active_count.  `ndot` inner
-// products are carried.
-template <class Fin, class Post>
-__device__ __forceinline__ void chunk_epilogue(double (*rows)[NDOT], int ndot, int chunk,
-                                               double* __restrict__ partial, PassSync* sync,
-                                               const RepDesc* __restrict__ reps, int n_reps,
-                                               Fin fin, Post post) {
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp == 0) {
-    for (int k = 0; k < ndot; ++k) {
-      double v = rows[lane][k];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) partial[(long long)chunk * NDOT + k] = v;
-    }
-  }
-  __shared__ unsigned int s_ticket;
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_ticket = atomicAdd(&sync->ticket, 1u);
-  }
-  __syncthreads();
-  if (s_ticket != gridDim.x - 1) return;
-  __threadfence();
-  // last block: fixed-order reduction per replicate.  256 virtual lanes
-  // (independent of the block size) each sum chunks v, v + 256, ... in
-  // order; lane sums are then combined by a fixed tree.
-  __shared__ double s_vl[FINAL_LANES][NDOT];
-  const int nthr = blockDim.x;
-  int n_active = 0;
-  for (int r = 0; r < n_reps; ++r) {
-    const RepDesc& rd = reps[r];
-    for (int v = threadIdx.x; v < FINAL_LANES; v += nthr) {
-      double acc[NDOT] = {0.0, 0.0, 0.0};
-      for (int c = v; c < rd.n_chunks; c += FINAL_LANES) {
-        const long long idx = (long long)(rd.chunk_begin + c) * NDOT;
-        for (int k = 0; k < ndot; ++k) acc[k] += __ldcg(partial + idx + k);
-      }
-      for (int k = 0; k < NDOT; ++k) s_vl[v][k] = acc[k];
-    }
-    __syncthreads();
-    if (warp == 0) {
-      double sums[NDOT] = {0.0, 0.0, 0.0};
-      for (int k = 0; k < ndot; ++k) {
-        double v = 0.0;
-        for (int i = lane; i < FINAL_LANES; i += 32) v += s_vl[i][k];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        sums[k] = v;
-      }
-      if (lane == 0) n_active += fin(r, sums);
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    sync->active_count = n_active;
-    post(n_active);
-    __threadfence();
-    sync->ticket = 0u;
-  }
-}
-
-template <class Fin>
-__device__ __forceinline__ void chunk_epilogue(double (*rows)[NDOT], int ndot, int chunk,
-                                               double* __restrict__ partial, PassSync* sync,
-                                               const RepDesc* __restrict__ reps, int n_reps, Fin fin) {
-  chunk_epilogue(rows, ndot, chunk, partial, sync, reps, n_reps, fin, [](int) {});
-}
-
 __device__ __forceinline__ void set_cond(const CondArg& c, bool v) {
   if (c.valid) cudaGraphSetConditional((cudaGraphConditionalHandle)c.h, v ? 1u : 0u);
 }
-
-// -------------------------------------------------------------- launch --
-struct LaunchCfg {
-  int threads;        // block size
-  cudaStream_t stream;
-};
 
 }  // namespace hca
 
@@ -334,7 +257,149 @@ struct Ctx {
   uint32_t* lists;
   int* list_count;        // [rep][27]
   unsigned long long* n_kernels;  // kernels that ran (counted by block 0 of each)
+  int* frozen;            // [rep] 1: solves leave this replicate's field untouched
+  // fixed-order reductions: row sums -> chunk sums -> group sums -> replicate
+  double* rowp;           // [chunk][CHUNK_ROWS][NDOT]
+  int* chunk_cnt;         // [chunk] warps done
+  double* superp;         // [group][NDOT]
+  int* super_cnt;         // [group] chunks done
+  int n_supers;
 };
+
+// Float-float accumulator: an unevaluated sum hi + lo of two FP32 words,
+// updated with Knuth's error-free TwoSum, so sums keep ~48 significant bits
+// while running on the FP32 pipes (GB300's FP64 rate is a small fraction of
+// its FP32 rate; the CG inner products would otherwise be FP64-ALU bound).
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_add(FF a, float b) {
+  const float s = __fadd_rn(a.hi, b);
+  const float bb = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return FF{s, __fadd_rn(a.lo, err)};
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  FF r = ff_add(a, b.hi);
+  r.lo = __fadd_rn(r.lo, b.lo);
+  return r;
+}
+
+// Row sum of float-float lane partials over the row's lane segment (fixed
+// xor tree), as a double.
+__device__ __forceinline__ double row_reduce_ff(FF v, int lpr) {
+  for (int o = lpr >> 1; o > 0; o >>= 1) {
+    FF w;
+    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o, 32);
+    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o, 32);
+    v = ff_add(v, w);
+  }
+  return (double)v.hi + (double)v.lo;
+}
+
+__device__ __forceinline__ void store_row_ff(const Ctx& c, int chunk, int rl, bool row_ok, int sl, int lpr,
+                                             const FF* acc, int ndot) {
+  for (int k = 0; k < ndot; ++k) {
+    const double v = row_reduce_ff(acc[k], lpr);
+    if (row_ok && sl == 0) c.rowp[((long long)chunk * CHUNK_ROWS + rl) * NDOT + k] = v;
+  }
+}
+
+// Row sum of a lane-partial over the row's lane segment, written to the
+// row slot of the chunk (by the segment's first lane).
+__device__ __forceinline__ void store_row(const Ctx& c, int chunk, int rl, bool row_ok, int sl, int lpr,
+                                          const double* acc, int ndot) {
+  for (int k = 0; k < ndot; ++k) {
+    const double v = row_reduce(acc[k], lpr);
+    if (row_ok && sl == 0) c.rowp[((long long)chunk * CHUNK_ROWS + rl) * NDOT + k] = v;
+  }
+}
+
+// Every warp of a block calls this after its rows (no block barrier).  The
+// last warp to finish a chunk sums the chunk's 32 row slots (fixed xor tree);
+// the last chunk to finish a group of SUPER_CHUNKS chunks sums the group's
+// chunk sums (fixed lane order); the last group to finish sums, per
+// replicate, its groups (fixed lane order) and calls fin(rep, sums) from one
+// lane; fin returns 1 if the replicate's solve stays active.  The number of
+// active replicates goes to sync->active_count and to post(n_active).  The
+// summation order depends on the lattice only, not on the block size, on the
+// other replicates of a batch or on which warp performs it.
+template <class Fin, class Post>
+__device__ __forceinline__ void warp_epilogue(const Ctx& c, int ndot, int chunk, Fin fin, Post post) {
+  const unsigned FULLM = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  __syncwarp();
+  int t = 0;
+  if (lane == 0) {
+    __threadfence();
+    t = atomicAdd(&c.chunk_cnt[chunk], 1);
+  }
+  t = __shfl_sync(FULLM, t, 0);
+  if (t != nw - 1) return;
+  __threadfence();
+  const int2 ch = c.chunks[chunk];
+  const RepDesc& rd = c.reps[ch.x];
+  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  for (int k = 0; k < ndot; ++k) {
+    double v = lane < nrows ? __ldcg(&c.rowp[((long long)chunk * CHUNK_ROWS + lane) * NDOT + k]) : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULLM, v, o);
+    if (lane == 0) c.partial[(long long)chunk * NDOT + k] = v;
+  }
+  // group of chunks
+  const int lc = chunk - rd.chunk_begin;
+  const int gi = lc / SUPER_CHUNKS;
+  const int sg = rd.super_begin + gi;
+  const int g0 = rd.chunk_begin + gi * SUPER_CHUNKS;
+  const int n_in = min(SUPER_CHUNKS, rd.n_chunks - gi * SUPER_CHUNKS);
+  if (lane == 0) {
+    c.chunk_cnt[chunk] = 0;
+    __threadfence();
+    t = atomicAdd(&c.super_cnt[sg], 1);
+  }
+  t = __shfl_sync(FULLM, t, 0);
+  if (t != n_in - 1) return;
+  __threadfence();
+  for (int k = 0; k < ndot; ++k) {
+    double v = 0.0;
+    for (int i = lane; i < n_in; i += 32) v += __ldcg(&c.partial[(long long)(g0 + i) * NDOT + k]);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULLM, v, o);
+    if (lane == 0) c.superp[(long long)sg * NDOT + k] = v;
+  }
+  if (lane == 0) {
+    c.super_cnt[sg] = 0;
+    __threadfence();
+    t = (int)atomicAdd(&c.sync->ticket, 1u);
+  }
+  t = __shfl_sync(FULLM, t, 0);
+  if (t != c.n_supers - 1) return;
+  __threadfence();
+  int n_active = 0;
+  for (int r = 0; r < c.n_reps; ++r) {
+    const RepDesc& rr = c.reps[r];
+    double sums[NDOT] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < ndot; ++k) {
+      double v = 0.0;
+      for (int i = lane; i < rr.n_supers; i += 32) v += __ldcg(&c.superp[(long long)(rr.super_begin + i) * NDOT + k]);
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULLM, v, o);
+      sums[k] = v;
+    }
+    if (lane == 0) n_active += fin(r, sums);
+  }
+  if (lane == 0) {
+    c.sync->active_count = n_active;
+    post(n_active);
+    __threadfence();
+    c.sync->ticket = 0u;
+  }
+}
+
+template <class Fin>
+__device__ __forceinline__ void warp_epilogue(const Ctx& c, int ndot, int chunk, Fin fin) {
+  warp_epilogue(c, ndot, chunk, fin, [](int) {});
+}
 
 // Count this kernel launch (call once, at kernel entry).
 #define HCA_COUNT_KERNEL(c)                                                  \

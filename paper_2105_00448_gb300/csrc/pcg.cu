@@ -95,20 +95,6 @@ __device__ __forceinline__ T diag_site(const RepDesc& rd, int which, int n_nb, u
   return cpl * (T)n_nb + a;
 }
 
-// Zero the per-row partial sums of the block.
-__device__ __forceinline__ void clear_rows(double (*rows)[NDOT]) {
-  for (int i = threadIdx.x; i < CHUNK_ROWS * NDOT; i += blockDim.x) (&rows[0][0])[i] = 0.0;
-  __syncthreads();
-}
-
-__device__ __forceinline__ void store_row(double (*rows)[NDOT], int rl, bool row_ok, int sl, int lpr,
-                                          double* acc, int ndot) {
-  for (int k = 0; k < ndot; ++k) {
-    const double v = row_reduce(acc[k], lpr);
-    if (row_ok && sl == 0) rows[rl][k] = v;
-  }
-}
-
 struct RowIter {
   int warp, lane, lpr, rpw, sub, sl, nw, niter;
 };
@@ -131,11 +117,9 @@ __device__ __forceinline__ RowIter row_iter(const RepDesc& rd) {
 template <typename T, int KIND>
 __global__ void __launch_bounds__(512) k_setup(Ctx c, int which, CondArg cnd) {
   HCA_COUNT_KERNEL(c);
-  __shared__ double rows[CHUNK_ROWS][NDOT];
   __shared__ double s_G0;
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
-  clear_rows(rows);
   const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
   const T* __restrict__ x = KIND == 0 ? (const T*)c.K : (const T*)c.G[which - 1];
   const T* __restrict__ perf = (const T*)c.perf;
@@ -205,15 +189,24 @@ __global__ void __launch_bounds__(512) k_setup(Ctx c, int which, CondArg cnd) {
         acc[2] += (double)g_bb;
       }
     }
-    store_row(rows, rl, row_ok, it.sl, it.lpr, acc, 3);
+    store_row(c, blockIdx.x, rl, row_ok, it.sl, it.lpr, acc, 3);
   }
   const double rtol = KIND == 0 ? rd.rtol_o2 : rd.rtol_drug;
   (void)rtol;
-  chunk_epilogue(rows, 3, blockIdx.x, c.partial, c.sync, c.reps, c.n_reps,
+  warp_epilogue(c, 3, blockIdx.x,
                  [&](int r, const double* s3) -> int {
                    const RepDesc& rr = c.reps[r];
                    RepSolve& sv = c.solve[r];
                    const double tol = which == 0 ? rr.rtol_o2 : rr.rtol_drug;
+                   if (c.frozen[r]) {
+                     sv.active = 0;
+                     sv.zero_b = 0;
+                     sv.iters = 0;
+                     sv.rnorm2 = 0.0;
+                     sv.bnorm2 = 1.0;
+                     sv.scale = 1.0;
+                     return 0;
+                   }
                    sv.rho = s3[0];
                    sv.rnorm2 = s3[1];
                    sv.bnorm2 = s3[2];
@@ -236,16 +229,38 @@ __global__ void __launch_bounds__(512) k_setup(Ctx c, int which, CondArg cnd) {
                  });
 }
 
+// Per-lane accumulator of a pass: float-float for FP32 fields, double for FP64.
+template <typename T> struct LaneAcc;
+template <> struct LaneAcc<float> {
+  FF v{0.f, 0.f};
+  __device__ __forceinline__ void add(float x) { v = ff_add(v, x); }
+};
+template <> struct LaneAcc<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+};
+
+__device__ __forceinline__ void store_rows_acc(const Ctx& c, int chunk, int rl, bool row_ok, int sl, int lpr,
+                                               const LaneAcc<float>* acc, int ndot) {
+  FF a[NDOT];
+  for (int k = 0; k < ndot; ++k) a[k] = acc[k].v;
+  store_row_ff(c, chunk, rl, row_ok, sl, lpr, a, ndot);
+}
+__device__ __forceinline__ void store_rows_acc(const Ctx& c, int chunk, int rl, bool row_ok, int sl, int lpr,
+                                               const LaneAcc<double>* acc, int ndot) {
+  double a[NDOT];
+  for (int k = 0; k < ndot; ++k) a[k] = acc[k].v;
+  store_row(c, chunk, rl, row_ok, sl, lpr, a, ndot);
+}
+
 // ----------------------------------------------------------------- pass A --
 // All loads of a group (own site and the four neighbour rows) are issued
 // before any value is used, so a group costs one memory round trip.
-template <typename T>
-__global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) k_pass_a(Ctx c, int which) {
+template <typename T, int REGS, int NI>
+__global__ void __maxnreg__(REGS) k_pass_a(Ctx c, int which) {
   HCA_COUNT_KERNEL(c);
-  __shared__ double rows[CHUNK_ROWS][NDOT];
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
-  clear_rows(rows);
   const RepSolve sv = c.solve[ch.x];
   if (sv.active) {
     const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
@@ -265,9 +280,13 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) k_pass_a(Ctx c, int which
       const int rl = rbase + it.sub;
       const bool row_ok = rl < nrows;
       const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
-      double acc = 0.0;
+      LaneAcc<T> acc[1];
       T carry = T(0);
-      for (int itn = 0; itn < it.niter; ++itn) {
+      // groups per lane in a row: a compile-time count (NI > 0) lets the
+      // compiler issue the loads of all of them before the first is used
+      const int niter = NI > 0 ? NI : it.niter;
+#pragma unroll
+      for (int itn = 0; itn < niter; ++itn) {
         const int g = itn * it.lpr + it.sl;
         const bool gok = row_ok && g < gpr;
         const long long e = geo.base + 4LL * g;
@@ -311,13 +330,13 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) k_pass_a(Ctx c, int which
             g_s += PN.a[k] * q;
           }
           st4(p_new + e, PN);
-          acc += (double)g_s;
+          acc[0].add(g_s);
         }
       }
-      store_row(rows, rl, row_ok, it.sl, it.lpr, &acc, 1);
+      store_rows_acc(c, blockIdx.x, rl, row_ok, it.sl, it.lpr, acc, 1);
     }
   }
-  chunk_epilogue(rows, 1, blockIdx.x, c.partial, c.sync, c.reps, c.n_reps,
+  warp_epilogue(c, 1, blockIdx.x,
                  [&](int r, const double* s1) -> int {
                    RepSolve& s = c.solve[r];
                    if (!s.active) return 0;
@@ -332,13 +351,11 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) k_pass_a(Ctx c, int which
 }
 
 // ----------------------------------------------------------------- pass B --
-template <typename T>
-__global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) k_pass_b(Ctx c, int which, void* xfield, CondArg cnd) {
+template <typename T, int REGS, int NI>
+__global__ void __maxnreg__(REGS) k_pass_b(Ctx c, int which, void* xfield, CondArg cnd) {
   HCA_COUNT_KERNEL(c);
-  __shared__ double rows[CHUNK_ROWS][NDOT];
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
-  clear_rows(rows);
   const RepSolve sv = c.solve[ch.x];
   if (sv.active) {
     const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
@@ -355,9 +372,13 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) k_pass_b(Ctx c, int which
       const int rl = rbase + it.sub;
       const bool row_ok = rl < nrows;
       const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
-      double acc[2] = {0.0, 0.0};
+      LaneAcc<T> acc[2];
       T carry = T(0);
-      for (int itn = 0; itn < it.niter; ++itn) {
+      // groups per lane in a row: a compile-time count (NI > 0) lets the
+      // compiler issue the loads of all of them before the first is used
+      const int niter = NI > 0 ? NI : it.niter;
+#pragma unroll
+      for (int itn = 0; itn < niter; ++itn) {
         const int g = itn * it.lpr + it.sl;
         const bool gok = row_ok && g < gpr;
         const long long e = geo.base + 4LL * g;
@@ -389,14 +410,14 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) k_pass_b(Ctx c, int which
           }
           st4(xx + e, X);
           st4(zz + e, Z);
-          acc[0] += (double)g_rho;
-          acc[1] += (double)g_rr;
+          acc[0].add(g_rho);
+          acc[1].add(g_rr);
         }
       }
-      store_row(rows, rl, row_ok, it.sl, it.lpr, acc, 2);
+      store_rows_acc(c, blockIdx.x, rl, row_ok, it.sl, it.lpr, acc, 2);
     }
   }
-  chunk_epilogue(rows, 2, blockIdx.x, c.partial, c.sync, c.reps, c.n_reps,
+  warp_epilogue(c, 2, blockIdx.x,
                  [&](int r, const double* s2) -> int {
                    RepSolve& s = c.solve[r];
                    if (!s.active) return 0;
@@ -433,10 +454,8 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) k_pass_b(Ctx c, int which
 template <typename T, int KIND>
 __global__ void __launch_bounds__(512) k_true_residual(Ctx c, int which, void* xfield) {
   HCA_COUNT_KERNEL(c);
-  __shared__ double rows[CHUNK_ROWS][NDOT];
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
-  clear_rows(rows);
   const RepSolve sv = c.solve[ch.x];
   const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
   T* __restrict__ xx = (T*)xfield;
@@ -483,9 +502,9 @@ __global__ void __launch_bounds__(512) k_true_residual(Ctx c, int which, void* x
         acc[0] += (double)g_rr;
       }
     }
-    store_row(rows, rl, row_ok, it.sl, it.lpr, acc, 1);
+    store_row(c, blockIdx.x, rl, row_ok, it.sl, it.lpr, acc, 1);
   }
-  chunk_epilogue(rows, 1, blockIdx.x, c.partial, c.sync, c.reps, c.n_reps,
+  warp_epilogue(c, 1, blockIdx.x,
                  [&](int r, const double* s1) -> int {
                    RepSolve& s = c.solve[r];
                    DevStats& st = c.stats[r];
@@ -572,10 +591,8 @@ __global__ void __launch_bounds__(512) k_apply(Ctx c, int which, int rep, const 
 template <typename T>
 __global__ void __launch_bounds__(512) k_diff_norms(Ctx c, const T* __restrict__ a, const T* __restrict__ b) {
   HCA_COUNT_KERNEL(c);
-  __shared__ double rows[CHUNK_ROWS][NDOT];
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
-  clear_rows(rows);
   const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
   const RowIter it = row_iter(rd);
   for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
@@ -599,9 +616,9 @@ __global__ void __launch_bounds__(512) k_diff_norms(Ctx c, const T* __restrict__
         acc[1] += (double)s1;
       }
     }
-    store_row(rows, rl, row_ok, it.sl, it.lpr, acc, 2);
+    store_row(c, blockIdx.x, rl, row_ok, it.sl, it.lpr, acc, 2);
   }
-  chunk_epilogue(rows, 2, blockIdx.x, c.partial, c.sync, c.reps, c.n_reps,
+  warp_epilogue(c, 2, blockIdx.x,
                  [&](int r, const double* s2) -> int {
                    c.solve[r].rnorm2 = s2[0];
                    c.solve[r].bnorm2 = s2[1];
@@ -624,11 +641,9 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
                                                      const float* __restrict__ x_lo, int first, CondArg outer,
                                                      CondArg inner) {
   HCA_COUNT_KERNEL(c);
-  __shared__ double rows[CHUNK_ROWS][NDOT];
   __shared__ double s_G0;
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
-  clear_rows(rows);
   const RepSolve sv = c.solve[ch.x];
   const bool live = first || sv.active || sv.dc_apply;
   if (KIND == 1 && first) {
@@ -728,10 +743,10 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
           acc[2] += g_rho;
         }
       }
-      store_row(rows, rl, row_ok, it.sl, it.lpr, acc, 3);
+      store_row(c, blockIdx.x, rl, row_ok, it.sl, it.lpr, acc, 3);
     }
   }
-  chunk_epilogue(rows, 3, blockIdx.x, c.partial, c.sync, c.reps, c.n_reps,
+  warp_epilogue(c, 3, blockIdx.x,
                  [&](int r, const double* s3) -> int {
                    const RepDesc& rr = c.reps[r];
                    RepSolve& s = c.solve[r];
@@ -742,6 +757,7 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
                      s.dc_apply = 0;
                      s.active = 0;
                      s.iters = 0;
+                     if (c.frozen[r]) return 0;
                    } else if (!s.dc_apply) {
                      return 0;        // this replicate finished in an earlier sweep
                    }
@@ -882,14 +898,46 @@ void launch_setup(const Ctx& c, int which, bool fp64, CondArg cnd) {
   else launch_setup_t<float>(c, which, cnd);
 }
 
-void launch_pass_a(const Ctx& c, int which, bool fp64) {
-  if (fp64) k_pass_a<double><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which);
-  else k_pass_a<float><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which);
+int g_pass_regs = 96;   // register cap of the FP32 passes (measured best at 128 threads)
+int g_pass_ni = 0;      // groups per lane in a row, shared by all replicates (0: differs)
+
+void set_pass_regs(int r) { g_pass_regs = r; }
+void set_pass_ni(int ni) { g_pass_ni = ni; }
+
+template <int REGS, int NI>
+static void launch_ab_f32(const Ctx& c, int which, bool a, void* xfield, CondArg cnd) {
+  if (a) k_pass_a<float, REGS, NI><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which);
+  else k_pass_b<float, REGS, NI><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, xfield, cnd);
 }
 
+template <int REGS>
+static void launch_ab_f32_ni(const Ctx& c, int which, bool a, void* xfield, CondArg cnd) {
+  switch (g_pass_ni) {
+    case 1: launch_ab_f32<REGS, 1>(c, which, a, xfield, cnd); break;
+    case 2: launch_ab_f32<REGS, 2>(c, which, a, xfield, cnd); break;
+    case 4: launch_ab_f32<REGS, 4>(c, which, a, xfield, cnd); break;
+    default: launch_ab_f32<REGS, 0>(c, which, a, xfield, cnd); break;
+  }
+}
+
+static void launch_ab(const Ctx& c, int which, bool fp64, bool a, void* xfield, CondArg cnd) {
+  if (fp64) {
+    if (a) k_pass_a<double, 128, 0><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which);
+    else k_pass_b<double, 128, 0><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, xfield, cnd);
+    return;
+  }
+  switch (g_pass_regs) {
+    case 64: launch_ab_f32_ni<64>(c, which, a, xfield, cnd); break;
+    case 96: launch_ab_f32_ni<96>(c, which, a, xfield, cnd); break;
+    case 128: launch_ab_f32_ni<128>(c, which, a, xfield, cnd); break;
+    default: launch_ab_f32_ni<80>(c, which, a, xfield, cnd); break;
+  }
+}
+
+void launch_pass_a(const Ctx& c, int which, bool fp64) { launch_ab(c, which, fp64, true, nullptr, CondArg{0ull, 0}); }
+
 void launch_pass_b(const Ctx& c, int which, void* xfield, bool fp64, CondArg cnd) {
-  if (fp64) k_pass_b<double><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, xfield, cnd);
-  else k_pass_b<float><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, xfield, cnd);
+  launch_ab(c, which, fp64, false, xfield, cnd);
 }
 
 void launch_true_residual(const Ctx& c, int which, void* xfield, bool fp64) {

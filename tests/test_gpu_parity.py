@@ -353,3 +353,28 @@ def test_errors_are_reported():
     with pytest.raises(hca.HcaError):
         hca.hca_read_fields(sim.handle, 0, hca.FIELD_O2, short)
     sim.close()
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_batch_equals_single_replicates(precision):
+    # uneven lattices, distinct seeds and maps, one launch per kernel for all
+    shapes = [(12, 16, 20), (8, 9, 13), (16, 16, 16)]
+    params = dict(n_drugs=2, rtol_o2=1e-8, rtol_drug=1e-8, picard_tol=1e-7)
+    cfgs, maps = [], []
+    for r, (nz, ny, nx) in enumerate(shapes):
+        m = make_maps(nx, ny, nz, corr_len=3.0, seed=100 + r)
+        maps.append((m.p_cell, m.perf, m.p_vessel))
+        cfgs.append(hca.make_config(nx, ny, nz, precision=precision, seed=100 + r, **params))
+    batch = hca.Sim(cfgs, maps, batch=True)
+    batch.step(3)
+    for r, (nz, ny, nx) in enumerate(shapes):
+        single = hca.Sim(hca.make_config(nx, ny, nz, precision=precision, seed=100 + r, **params), maps[r])
+        single.step(3)
+        assert np.array_equal(batch.states(r), single.states())
+        for bit in (hca.FIELD_O2, hca.FIELD_DRUG0, hca.FIELD_DRUG1, hca.FIELD_PHI, hca.FIELD_P53, hca.FIELD_VEGFC):
+            assert np.array_equal(batch.field(bit, r), single.field(bit)), (r, bit)
+        sb, ss = batch.stats(r), single.stats()
+        for key in ("o2_iterations", "drug_iterations", "kills", "divisions", "counts"):
+            assert sb[key] == ss[key], (r, key)
+        single.close()
+    batch.close()
