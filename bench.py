@@ -99,6 +99,21 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
 
 
+def measured_peak_bf16():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (cuBLAS bf16 burst)"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+# FLOPs of one forward pass of the warm-start network per level-0 site:
+# 2 * 27 * C_in * C_out per output site of each 3x3x3 convolution, levels 0..3
+NET_FLOPS_PER_SITE = 2 * 27 * (16 * 16 + 32 * 16 + (16 * 32 + 64 * 32) / 8 + (32 * 64 + 64 * 64) / 64
+                               + 64 * 64 / 512) + 2 * 16
+
+
 def measured_peak_hbm():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -273,11 +288,104 @@ def run_gpu(args):
                               "o2_rel_residual": stats["o2_rel_residual"],
                               "drug_rel_residual": stats["drug_rel_residual"][:2], "counts": stats["counts"]},
                 "kernel_time_share": kernel_share, "status": int(rc)}
+        if args.ws_learned and world == 1:
+            line["warm_start_learned"] = run_ws_learned(args, hca, make_maps, np, torch)
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def run_ws_learned(args, hca, make_maps, np, torch):
+    """The learned oxygen warm start on the 256^3 workload at rtol 1e-6: train
+    the network on the oxygen solves of two 128^3 runs (seeds 2000, 2001),
+    then run the 256^3 workload (seed 1) from the previous-step guess and from
+    the network's guess, and time the network's forward pass alone."""
+    from paper_2105_00448_gb300 import warmstart
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n, m = args.edge, args.edge // 2
+    ev = {**WORKLOAD, "rtol_o2": 1e-6}
+    t0 = time.perf_counter()
+    samples = []
+    for seed in (2000, 2001):
+        mp = make_maps(m, m, m, corr_len=CORR_LEN, seed=seed)
+        sim = hca.Sim(hca.make_config(m, m, m, **{**WORKLOAD, "seed": seed}), (mp.p_cell, mp.perf, mp.p_vessel))
+        sim.step(1, allow_noconv=True)
+        samples += warmstart.collect_samples(sim, args.ws_samples // 2, dev)
+        sim.close()
+    t_collect = time.perf_counter() - t0
+    net_t = hca.Net(m, m, m, trainable=True)
+    net_t.set_params(warmstart.init_params(0))
+    t0 = time.perf_counter()
+    losses = warmstart.train(net_t, hca.make_config(m, m, m), samples, args.ws_iters, 3e-3, seed=1, lr_final=1.5e-4,
+                             w_res=0.03)
+    t_train = time.perf_counter() - t0
+    params = net_t.params()
+    net_t.close()
+    del samples
+    stream = torch.cuda.Stream()
+    net = hca.Net(n, n, n, stream=stream.cuda_stream)
+    net.set_params(params)
+    # forward alone (features already in place): CUDA events on the network's stream
+    x = torch.zeros(n * n * n * 16, dtype=torch.bfloat16, device=dev)
+    out = torch.empty(n * n * n, dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            hca.hca_net_forward_x(net.handle, x, out)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record(stream)
+        for _ in range(reps):
+            hca.hca_net_forward_x(net.handle, x, out)
+        e1.record(stream)
+    stream.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / reps
+    del x, out
+    runs = {}
+    maps = make_maps(n, n, n, corr_len=CORR_LEN, seed=WORKLOAD["seed"])
+    for mode in (hca.HCA_WS_PREV, hca.HCA_WS_LEARNED):
+        cfg = hca.make_config(n, n, n, stream=stream.cuda_stream, warm_start=mode, **ev)
+        sim = hca.Sim(cfg, (maps.p_cell, maps.perf, maps.p_vessel))
+        if mode == hca.HCA_WS_LEARNED:
+            sim.set_warm_start_net(net)
+        sim.step(args.warmup, allow_noconv=True)
+        its, used, ms, r0 = [], 0, 0.0, [0.0, 0.0]
+        for _ in range(args.ws_steps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sim.step(1, allow_noconv=True)
+            b.record(stream)
+            stream.synchronize()
+            ms += a.elapsed_time(b)
+            st = sim.stats()
+            its.append(st["o2_iterations"])
+            used += st["ws_used"]
+            r0[0] += st["ws_r0_prev"] / args.ws_steps
+            r0[1] += st["ws_r0_learned"] / args.ws_steps
+        sim.close()
+        runs[mode] = {"o2_iterations_per_step": sum(its) / len(its), "ms_per_step": ms / args.ws_steps,
+                      "guess_used_steps": used}
+        if mode == hca.HCA_WS_LEARNED:
+            runs[mode]["mean_rel_r0"] = {"previous_field": r0[0], "network_guess": r0[1]}
+    net.close()
+    peak, kind = measured_peak_bf16()
+    achieved = NET_FLOPS_PER_SITE * n ** 3 / (fwd_ms * 1e-3) / 1e12
+    prev, lrn = runs[hca.HCA_WS_PREV], runs[hca.HCA_WS_LEARNED]
+    return {"workload": f"{n}^3 workload, oxygen rtol 1e-6, {args.ws_steps} steps after {args.warmup} warm-up",
+            "training": f"{args.ws_iters} Adam steps (MSE + 0.03 residual) on {args.ws_samples} oxygen solves of two {m}^3 runs "
+                        f"(seeds 2000, 2001); collect {t_collect:.1f} s, train {t_train:.1f} s; "
+                        f"loss {float(np.mean(losses[:20])):.2e} -> {float(np.mean(losses[-50:])):.2e}",
+            "previous_step_start": prev, "learned_start": lrn,
+            "o2_iteration_ratio": lrn["o2_iterations_per_step"] / max(1e-9, prev["o2_iterations_per_step"]),
+            "step_time_ratio": lrn["ms_per_step"] / max(1e-9, prev["ms_per_step"]),
+            "net_forward": {"ms": fwd_ms, "flops": NET_FLOPS_PER_SITE * n ** 3},
+            "roofline": {"bound": "tensor", "kernel": "network forward (7 conv launches + pools)",
+                         "achieved": achieved, "peak": peak, "peak_kind": kind, "unit": "TFLOP/s",
+                         "frac": achieved / peak}}
 
 
 def run_e2e(args, hca, make_maps, np, torch):
@@ -322,6 +430,11 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=2)
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--ws-learned", action="store_true",
+                    help="also train and measure the learned oxygen warm start (about a minute)")
+    ap.add_argument("--ws-samples", type=int, default=48)
+    ap.add_argument("--ws-iters", type=int, default=4000)
+    ap.add_argument("--ws-steps", type=int, default=10)
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         raise SystemExit("need --steps >= 1 and --warmup >= 0")

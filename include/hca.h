@@ -92,7 +92,8 @@ extern "C" {
 
 /* warm start of the oxygen CG */
 #define HCA_WS_PREV 0     /* previous step's K */
-#define HCA_WS_LEARNED 1  /* reserved: learned initial guess */
+#define HCA_WS_LEARNED 1  /* network guess (hca_set_warm_start_net), residual-checked */
+#define HCA_WS_LEARNED_ALWAYS 2  /* network guess without the residual check (for measurement) */
 
 /*
  * Simulation parameters.  Defaults (hca_config_default) are Table 1 of the
@@ -140,7 +141,10 @@ typedef struct hca_config {
   double k2, k2p, k2pp, J5, K_V; /* 2e-3, 0.01, -2e-4, 0.04, 0.01 */
 
   /* precision scheme of HCA_FP32 (ignored for HCA_FP64) */
-  double rtol_inner;     /* inner FP32 CG tolerance of the oxygen defect correction (1e-3) */
+  double rtol_inner;     /* inner FP32 CG tolerance of a defect-correction sweep,
+                            relative to its defect (1e-3); a sweep aims at half
+                            the outer target instead when that is looser or at
+                            most 8x tighter */
   int32_t max_outer;     /* defect-correction sweeps per oxygen solve (8) */
 
   int32_t warm_start;    /* HCA_WS_PREV */
@@ -161,6 +165,10 @@ typedef struct hca_stats {
   int32_t pad0;
   int64_t committed, kills, divisions, blocked; /* last CA update */
   int64_t counts[6];            /* sites per state code after the last update */
+  int32_t ws_used;              /* HCA_WS_LEARNED: 1 if the last oxygen solve started from the network's guess */
+  int32_t pad1;
+  double ws_r0_prev;            /* HCA_WS_LEARNED: ||b - A K_prev|| / ||b|| before the last oxygen solve */
+  double ws_r0_learned;         /* HCA_WS_LEARNED: the same for the network's guess */
 } hca_stats;
 
 typedef struct hca_handle hca_handle;
@@ -296,6 +304,98 @@ int hca_o2_residual_noalloc(const hca_config* cfg, const uint8_t* state, const d
 
 void hca_destroy(hca_handle* h);
 const char* hca_status_string(int32_t status);
+
+/* ------------------------------------------------ learned warm start ---
+ * The paper has no counterpart: it starts every solve from the previous
+ * step's field.  A small 3-D convolutional encoder-decoder predicts the
+ * change of the oxygen field over one step from the lattice the solve sees;
+ * the oxygen CG of Eq. (oxygen) then starts from K_prev + (K0 / HCA_NET_SCALE)
+ * f(x) whenever that guess has a smaller residual than K_prev (checked on the
+ * device every step, so a poor network never slows a solve beyond its own
+ * cost).  The consumption term stays linearised about K_prev.
+ *
+ * Network (levels 0..3, channels 16, 32, 64, 64; every lattice extent a
+ * multiple of 8): e0 = relu(conv(x)+b), e_l = relu(conv(pool(e_{l-1}))+b),
+ * d2 = relu(conv(up(e3))+b+e2), d1 = relu(conv(up(d2))+b+e1),
+ * d0 = relu(conv(up(d1))+b+e0), f = d0 . w_head + b_head; conv = 3x3x3 'same'
+ * with zero padding, pool = 2x2x2 mean, up = 2x nearest.  BF16 weights and
+ * activations, FP32 accumulation (tensor cores), FP32 master parameters.
+ * Input channels of x (dense (D, H, W, 16) BF16, channels innermost): one-hot
+ * state code 0..5, perf, K_prev / K0, HCA_NET_SCALE (b - A K_prev) /
+ * (diag(A) K0), zeros.  Parameters: one FP32 array, per conv layer (order
+ * enc0, enc1, enc2, enc3, dec2, dec1, dec0) the weights (27, C_out, C_in),
+ * tap 9(dz+1)+3(dy+1)+(dx+1), then the biases; then 16 head weights and the
+ * head bias.  Training minimises the loss below with Adam.  All arrays below are caller-owned DEVICE arrays unless
+ * a flag says otherwise; lattices are dense (D, H, W) = (nz, ny, nx) with x
+ * fastest.  Work runs on the stream given at creation; functions that read
+ * results back synchronise it.  Errors: HCA_ERR_ARG (bad argument or
+ * lattice), HCA_ERR_OOM, HCA_ERR_CUDA. */
+#define HCA_NET_IN_CH 16
+#define HCA_NET_SCALE 64.0
+
+typedef struct hca_net hca_net;
+
+/* Number of FP32 parameters. */
+int hca_net_param_count(int64_t* n_out);
+
+/* A network for D x H x W lattices (multiples of 8); trainable != 0 also
+ * allocates the gradient, Adam and backward buffers.  Parameters start at 0. */
+int hca_net_create(int32_t D, int32_t H, int32_t W, int32_t trainable, void* stream, hca_net** out);
+
+/* Copy the FP32 parameters in (resets Adam's moments and step count) / out. */
+int hca_net_set_params(hca_net* n, const float* params, int32_t on_device);
+int hca_net_get_params(hca_net* n, float* params, int32_t on_device);
+
+/* Features of (state uint8, perf float, K_prev float) under cfg's oxygen
+ * parameters (D_K, dx, phi_K, K1, r_K, K0), then f into out (D*H*W floats).
+ * x_out (optional, D*H*W*16 BF16) receives the features. */
+int hca_net_forward(hca_net* n, const hca_config* cfg, const uint8_t* state, const float* perf, const float* K_prev,
+                    float* out, void* x_out);
+
+/* f of a given BF16 input x (D*H*W*16) into out. */
+int hca_net_forward_x(hca_net* n, const void* x, float* out);
+
+/* Copy a stored activation of the last forward pass (BF16, dense, channels
+ * innermost) into dst: which = 0 x, 1 e0, 2 pool(e0), 3 e1, 4 pool(e1),
+ * 5 e2, 6 pool(e2), 7 e3, 8 d2, 9 d1, 10 d0 (d0: trainable networks only).
+ * For inspection and per-layer checks. */
+int hca_net_read_activation(hca_net* n, int32_t which, void* dst);
+
+/* Forward and backward on input x and target t (D*H*W floats): gradients of
+ * mean((f - t)^2) into grads (param_count floats, optional) and the loss
+ * into *loss (optional); both device pointers.  Needs trainable. */
+int hca_net_gradients_x(hca_net* n, const void* x, const float* target, float* grads, float* loss);
+
+/* One Adam step (Kingma & Ba 2015) on the gradients of the last backward pass. */
+int hca_net_adam(hca_net* n, double lr, double beta1, double beta2, double eps);
+
+/* Training loss L = w_mse mean((f - t)^2) + w_res mean((A e)^2) / c^2 with
+ * t = HCA_NET_SCALE (K_new - K_prev) / K0, e = f - t, A the oxygen operator
+ * linearised about K_prev and c = D_K / dx^2 (the second term is the
+ * residual of the guess up to scale).  Weights >= 0, not both 0. */
+
+/* Features, forward and backward for one oxygen solve (state uint8, perf,
+ * K_prev, K_new float): gradients into grads (param_count floats, optional)
+ * and the loss into *loss (optional), device pointers.  Asynchronous. */
+int hca_net_gradients(hca_net* n, const hca_config* cfg, const uint8_t* state, const float* perf,
+                      const float* K_prev, const float* K_new, double w_mse, double w_res, float* grads,
+                      float* loss);
+
+/* hca_net_gradients followed by one Adam step (beta = (0.9, 0.999),
+ * eps = 1e-8); *loss (device, optional) receives the loss before the
+ * update.  Asynchronous. */
+int hca_net_train_step(hca_net* n, const hca_config* cfg, const uint8_t* state, const float* perf,
+                       const float* K_prev, const float* K_new, double w_mse, double w_res, double lr,
+                       float* loss);
+
+int hca_net_sync(hca_net* n);
+int hca_net_destroy(hca_net* n);
+
+/* Attach a network (not owned; must outlive its use) to a single-replicate
+ * handle created with warm_start = HCA_WS_LEARNED(_ALWAYS) and an nz x ny x nx
+ * lattice equal to the network's.  NULL detaches (the solve then starts
+ * from K_prev).  Rebuilds the captured step graph on the next step. */
+int hca_set_warm_start_net(hca_handle* h, hca_net* n);
 
 #ifdef __cplusplus
 }

@@ -196,6 +196,21 @@ def mse_grad(out, target):
     return float(np.mean((out - target) ** 2)), 2.0 * (out - target) / n
 
 
+def residual_loss(out, target, state, K_prev, cfg):
+    """Loss mean((A e)^2) / c^2 and its gradient with respect to out, where
+    e = out - target, A is the oxygen operator of Eq. (oxygen) linearised
+    about K_prev (the operator of the solve the guess starts) and
+    c = D_K / dx^2.  Since A K_new = b, A e is the residual of the guess up
+    to the output scale: the loss trains the quantity the solver's fallback
+    test compares."""
+    cpl = S.o2_coupling(cfg)
+    reac = S.o2_reaction(state, K_prev, cfg)
+    e = np.asarray(out, dtype=np.float64) - target
+    u = S.apply_operator(e, cpl, reac) / cpl
+    n = e.size
+    return float(np.mean(u * u)), 2.0 * S.apply_operator(u, cpl, reac) / (cpl * n)
+
+
 def adam(w, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam update (Kingma & Ba 2015, Algorithm 1) at step t >= 1; returns (w, m, v)."""
     m = beta1 * m + (1.0 - beta1) * g

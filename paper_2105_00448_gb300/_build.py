@@ -1,6 +1,6 @@
 """Build libhca.so in-tree with nvcc for sm_103a (GB300).
 
-The four translation units compile in parallel; the CA unit is compiled with
+The translation units compile in parallel; the CA unit is compiled with
 -fmad=false so its decision arithmetic is plain IEEE operations.  The result
 lands in ``paper_2105_00448_gb300/_lib/libhca.so``; a stamp of the source
 hashes and flags skips rebuilds that would produce the same library.
@@ -30,6 +30,7 @@ UNITS = {
     "ca.cu": ["-fmad=false"],
     "engine.cu": [],
     "noalloc.cu": [],
+    "net.cu": [],
 }
 
 

@@ -36,6 +36,8 @@ void set_pass_ni(int ni);
 using hca::Ctx;
 using hca::RepDesc;
 
+#include "net_internal.cuh"
+
 // Optional per-launch device timing (hca_profile_enable).
 struct Profiler {
   bool on = false;
@@ -81,6 +83,12 @@ struct hca_handle {
   bool graphs_ok = true;
   int* h_pinned = nullptr;    // [0] active replicates, [1] error flag
   std::vector<void*> allocs;
+  // learned warm start of the oxygen solve (single replicate)
+  bool learned = false;
+  hca_net* net = nullptr;
+  double* ws_cand = nullptr;
+  double* ws_part = nullptr;
+  hcanet::WsResult* ws_res = nullptr;
 };
 
 namespace {
@@ -170,7 +178,8 @@ int validate(const hca_config& c) {
   if (!(c.D_K > 0) || !(c.phi_K >= 0) || !(c.K1 > 0) || !(c.r_K >= 0) || !(c.K0 >= 0)) return HCA_ERR_ARG;
   const int t = c.threads_per_block;
   if (!(t == 0 || t == 64 || t == 128 || t == 256 || t == 512)) return HCA_ERR_ARG;
-  if (c.warm_start != HCA_WS_PREV && c.warm_start != HCA_WS_LEARNED) return HCA_ERR_ARG;
+  if (c.warm_start != HCA_WS_PREV && c.warm_start != HCA_WS_LEARNED && c.warm_start != HCA_WS_LEARNED_ALWAYS)
+    return HCA_ERR_ARG;
   return HCA_OK;
 }
 
@@ -355,6 +364,37 @@ int solve(hca_handle* h, int which) {
 // sets the loop condition on the device, so a step runs without any host
 // round trip.  Loop exit is guaranteed by maxit / max_outer, with a device
 // guard counter as a second stop.
+// Learned warm start: replace K by the network's guess when its residual is
+// smaller and point the oxygen set-up at K_prev (c.aux) for the linearisation.
+int ws_before_o2(hca_handle* h, cudaStream_t s) {
+  Ctx& c = h->ctx;
+  c.lag = nullptr;
+  if (!h->learned || !h->net) return HCA_OK;
+  const RepDesc& r = h->reps_h[0];
+  const hca_config& g = h->cfgs[0];
+  hcanet::FeatureArgs f;
+  f.state = c.state;
+  f.perf = c.perf;
+  f.nx = r.nx;
+  f.ny = r.ny;
+  f.nz = r.nz;
+  f.pitch = r.nxp;
+  f.base = r.off;
+  f.D_K = g.D_K;
+  f.dx = g.dx;
+  f.phi_K = g.phi_K;
+  f.K1 = g.K1;
+  f.r_K = g.r_K;
+  f.K0 = g.K0;
+  const bool dc = !h->fp64 && h->max_outer > 0;
+  const bool always = g.warm_start == HCA_WS_LEARNED_ALWAYS;
+  const int rc = hcanet::ws_o2(h->net, f, h->fp64, always, c.K, dc ? static_cast<float*>(c.K_lo) : nullptr, c.aux,
+                               h->ws_cand, h->ws_part, h->ws_res, s);
+  if (rc) return rc;
+  c.lag = c.aux;
+  return HCA_OK;
+}
+
 int add_while(cudaStream_t s, cudaGraphConditionalHandle hnd, cudaGraph_t* body) {
   cudaStreamCaptureStatus st;
   cudaGraph_t g = nullptr;
@@ -436,8 +476,12 @@ int cap_stages(hca_handle* h, uint32_t mask, cudaGraph_t G) {
   HCA_TRY(cudaMemsetAsync(c.stats, 0, sizeof(hca::DevStats) * h->n_reps, c.stream));
   HCA_TRY(cudaMemsetAsync(&c.sync->error, 0, sizeof(int), c.stream));
   int rc;
-  if (mask & HCA_STAGE_O2)
-    if ((rc = cap_solve(h, 0, G))) return rc;
+  if (mask & HCA_STAGE_O2) {
+    rc = ws_before_o2(h, c.stream);
+    if (!rc) rc = cap_solve(h, 0, G);
+    c.lag = nullptr;
+    if (rc) return rc;
+  }
   if (mask & HCA_STAGE_DRUGS)
     for (int d = 0; d < h->n_drugs; ++d)
       if ((rc = cap_solve(h, 1 + d, G))) return rc;
@@ -536,7 +580,9 @@ int run_stages(hca_handle* h, uint32_t mask) {
   if (rc) return rc;
   int status = HCA_OK;
   if (mask & HCA_STAGE_O2) {
-    rc = solve(h, 0);
+    rc = ws_before_o2(h, h->ctx.stream);
+    if (!rc) rc = solve(h, 0);
+    h->ctx.lag = nullptr;
     if (rc) return rc;
   }
   if (mask & HCA_STAGE_DRUGS) {
@@ -628,6 +674,8 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
         cfgs[i].dt != cfgs[0].dt || cfgs[i].threads_per_block != cfgs[0].threads_per_block ||
         cfgs[i].stream != cfgs[0].stream)
       return HCA_ERR_ARG;
+    // the learned warm start runs one network on one lattice
+    if (cfgs[i].warm_start != HCA_WS_PREV && n > 1) return HCA_ERR_UNIMPLEMENTED;
   }
   hca_handle* h = new (std::nothrow) hca_handle();
   if (!h) return HCA_ERR_OOM;
@@ -636,6 +684,7 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
   h->n_drugs = cfgs[0].n_drugs;
   h->stream = (cudaStream_t)cfgs[0].stream;
   h->cfgs.assign(cfgs, cfgs + n);
+  h->learned = cfgs[0].warm_start != HCA_WS_PREV;
   {
     // HCA_NO_GRAPH=1 runs steps from a host loop instead of the step graph
     const char* ng = std::getenv("HCA_NO_GRAPH");
@@ -715,6 +764,11 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     ALLOC(c.d, fbytes);
     ALLOC(c.b, fbytes);
     ALLOC(c.aux, fbytes);
+    if (h->learned) {
+      ALLOC(h->ws_cand, sizeof(double) * (size_t)h->total);
+      ALLOC(h->ws_part, sizeof(double) * 3 * hcanet::kWsNormBlocks);
+      ALLOC(h->ws_res, sizeof(hcanet::WsResult));
+    }
     ALLOC(c.partial, sizeof(double) * hca::NDOT * chunk0);
     ALLOC(c.sync, sizeof(hca::PassSync));
     ALLOC(c.solve, sizeof(hca::RepSolve) * n);
@@ -755,7 +809,8 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
         cudaMemsetAsync(c.n_kernels, 0, sizeof(unsigned long long), s) ||
         cudaMemsetAsync(c.frozen, 0, sizeof(int) * n, s) ||
         cudaMemsetAsync(c.chunk_cnt, 0, sizeof(int) * (size_t)chunk0, s) ||
-        cudaMemsetAsync(c.super_cnt, 0, sizeof(int) * (size_t)super0, s)) {
+        cudaMemsetAsync(c.super_cnt, 0, sizeof(int) * (size_t)super0, s) ||
+        (h->ws_res && cudaMemsetAsync(h->ws_res, 0, sizeof(hcanet::WsResult), s))) {
       rc = HCA_ERR_CUDA;
       goto fail;
     }
@@ -1059,6 +1114,23 @@ int hca_get_stats(hca_handle* h, int32_t rep, hca_stats* out) {
   out->divisions = st.divisions;
   out->blocked = st.blocked;
   for (int k = 0; k < 6; ++k) out->counts[k] = st.counts[k];
+  if (h->learned && h->net) {
+    hcanet::WsResult w;
+    HCA_TRY(cudaMemcpy(&w, h->ws_res, sizeof(w), cudaMemcpyDeviceToHost));
+    out->ws_used = w.used;
+    out->ws_r0_prev = w.r0_prev;
+    out->ws_r0_learned = w.r0_learned;
+  }
+  return HCA_OK;
+}
+
+int hca_set_warm_start_net(hca_handle* h, hca_net* n) {
+  if (!h) return HCA_ERR_ARG;
+  if (n && (!h->learned || !hcanet::ws_fits(n, h->reps_h[0].nx, h->reps_h[0].ny, h->reps_h[0].nz))) return HCA_ERR_ARG;
+  HCA_TRY(cudaStreamSynchronize(h->ctx.stream));
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+  h->net = n;
   return HCA_OK;
 }
 

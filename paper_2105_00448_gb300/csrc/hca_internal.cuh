@@ -239,6 +239,7 @@ struct Ctx {
   void* G_lo[MAX_DRUGS];
   void* dx;      // FP32 scheme: correction of the inner solve
   void* aux;     // scratch field (previous iterate of the initial oxygen fixed point)
+  const void* lag;  // oxygen linearisation point (K_prev) when the solve starts elsewhere; null: the start field
   void* reac;    // FP32 scheme: reaction part a of the diagonal d = c n + a
   void* phi;
   void* P;

@@ -160,6 +160,7 @@ __global__ void __launch_bounds__(512) k_setup(Ctx c, int which, CondArg cnd) {
         const uchar4 st = ld_state4(c.state + e);
         V4<T> PF = zero4<T>();
         if (KIND == 1) PF = ld4(perf + e);
+        const V4<T> LG = (KIND == 0 && c.lag) ? ld4((const T*)c.lag + e) : X;
         V4<T> D, Z, B;
         T g_rho = 0, g_rr = 0, g_bb = 0;
 #pragma unroll
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(512) k_setup(Ctx c, int which, CondArg cnd) {
           const uint8_t s = st_at(st, k);
           T dk = T(0), zk = T(0), bk = T(0);
           if (xk < rd.nx) {
-            dk = diag_site<T, KIND>(rd, which, neighbour_count(rd, geo, xk), s, X.a[k], PF.a[k]);
+            dk = diag_site<T, KIND>(rd, which, neighbour_count(rd, geo, xk), s, LG.a[k], PF.a[k]);
             if (KIND == 0) bk = is_vessel(s) ? bvessel : T(0);
             else bk = X.a[k] * inv_dt + (is_vessel(s) ? (T)rd.kappa[which - 1] * PF.a[k] * G0 : T(0));
             const T r = bk - (dk * X.a[k] - cpl * nb_sum(X, k, left, right, ym, yp, zm, zp));
@@ -705,8 +706,9 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
               B.a[k] = 0.f;
               AR.a[k] = 0.f;
               if (xk < rd.nx) {
-                // the operator is linearised about the solution at the start of the solve
-                AR.a[k] = reaction_site<float, KIND>(rd, which, s, (float)X.a[k], PF.a[k]);
+                // the operator is linearised about K_prev: the start field, or c.lag when the solve starts from another guess
+                const float lag = (KIND == 0 && c.lag) ? ((const float*)c.lag)[e + k] : (float)X.a[k];
+                AR.a[k] = reaction_site<float, KIND>(rd, which, s, lag, PF.a[k]);
                 D.a[k] = (float)cpl * (float)neighbour_count(rd, geo, xk) + AR.a[k];
                 if (KIND == 0) B.a[k] = is_vessel(s) ? bvessel : 0.f;
                 else B.a[k] = (float)(X.a[k] * rd.inv_dt) + (is_vessel(s) ? (float)rd.kappa[which - 1] * PF.a[k] * G0 : 0.f);
@@ -802,7 +804,13 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
                    s.rho = s3[2] * sc * sc;
                    s.rnorm2 = s3[0] * sc * sc;
                    s.bnorm2 = s3[0] * sc * sc;
-                   s.rtol = rr.rtol_inner;
+                   // inner tolerance: rtol_inner relative to this sweep's
+                   // defect, or, when the outer target is within a factor 8
+                   // of that (or looser), the reduction that reaches half the
+                   // outer target, so the last sweep neither over-solves nor
+                   // falls just short and costs another sweep
+                   const double q = 0.5 * tol / rel;
+                   s.rtol = q >= 0.125 * rr.rtol_inner ? q : rr.rtol_inner;
                    s.maxit = rr.maxit;
                    s.iters = 0;
                    s.alpha = 0.0;

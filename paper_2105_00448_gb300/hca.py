@@ -29,6 +29,9 @@ HCA_ERR_STATE = -8
 
 HCA_FP64 = 0
 HCA_FP32 = 1
+HCA_WS_PREV = 0
+HCA_WS_LEARNED = 1
+HCA_WS_LEARNED_ALWAYS = 2
 
 EMPTY, PROLIF, QUIESC, DEAD, VESSEL, STROMA = range(6)
 
@@ -92,6 +95,10 @@ class hca_stats(ctypes.Structure):
         ("committed", ctypes.c_int64), ("kills", ctypes.c_int64),
         ("divisions", ctypes.c_int64), ("blocked", ctypes.c_int64),
         ("counts", ctypes.c_int64 * 6),
+        ("ws_used", ctypes.c_int32),
+        ("pad1", ctypes.c_int32),
+        ("ws_r0_prev", ctypes.c_double),
+        ("ws_r0_learned", ctypes.c_double),
     ]
 
     def as_dict(self) -> Dict:
@@ -120,7 +127,14 @@ EXPORTS = [
     "hca_set_step", "hca_get_stats", "hca_apply_operator", "hca_philox_uniforms",
     "hca_sync", "hca_get_shape", "hca_launch_count", "hca_profile_enable", "hca_get_profile",
     "hca_o2_residual_noalloc", "hca_destroy", "hca_status_string",
+    "hca_net_param_count", "hca_net_create", "hca_net_set_params", "hca_net_get_params", "hca_net_forward",
+    "hca_net_forward_x", "hca_net_read_activation", "hca_net_gradients_x", "hca_net_gradients", "hca_net_adam", "hca_net_train_step", "hca_net_sync",
+    "hca_net_destroy", "hca_set_warm_start_net",
 ]
+
+NET_IN_CH = 16
+NET_SCALE = 64.0
+
 
 _lib = None
 
@@ -173,6 +187,21 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "hca_o2_residual_noalloc": (ctypes.c_int, [cfgp, P, P, P, ctypes.POINTER(ctypes.c_double), P]),
         "hca_destroy": (None, [P]),
         "hca_status_string": (ctypes.c_char_p, [I32]),
+        "hca_net_param_count": (ctypes.c_int, [ctypes.POINTER(I64)]),
+        "hca_net_create": (ctypes.c_int, [I32, I32, I32, I32, P, ctypes.POINTER(P)]),
+        "hca_net_set_params": (ctypes.c_int, [P, P, I32]),
+        "hca_net_get_params": (ctypes.c_int, [P, P, I32]),
+        "hca_net_forward": (ctypes.c_int, [P, cfgp, P, P, P, P, P]),
+        "hca_net_forward_x": (ctypes.c_int, [P, P, P]),
+        "hca_net_read_activation": (ctypes.c_int, [P, I32, P]),
+        "hca_net_gradients_x": (ctypes.c_int, [P, P, P, P, P]),
+        "hca_net_adam": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+        "hca_net_gradients": (ctypes.c_int, [P, cfgp, P, P, P, P, ctypes.c_double, ctypes.c_double, P, P]),
+        "hca_net_train_step": (ctypes.c_int, [P, cfgp, P, P, P, P, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_double, P]),
+        "hca_net_sync": (ctypes.c_int, [P]),
+        "hca_net_destroy": (ctypes.c_int, [P]),
+        "hca_set_warm_start_net": (ctypes.c_int, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -357,6 +386,130 @@ def hca_destroy(h) -> None:
         load().hca_destroy(h)
 
 
+# ------------------------------------------- learned warm start (net) ---
+def _dev(t, what, nbytes=None):
+    p, nb, on_dev = _ptr(t)
+    if not on_dev:
+        raise ValueError(f"{what} must be a device tensor")
+    if nbytes is not None and nb < nbytes:
+        raise ValueError(f"{what} too small ({nb} < {nbytes} bytes)")
+    return p
+
+
+def hca_net_param_count() -> int:
+    n = ctypes.c_int64()
+    _check(load().hca_net_param_count(ctypes.byref(n)), "hca_net_param_count")
+    return n.value
+
+
+def hca_net_create(D: int, H: int, W: int, trainable: bool = False, stream=None):
+    h = ctypes.c_void_p()
+    _check(load().hca_net_create(D, H, W, 1 if trainable else 0, ctypes.c_void_p(int(stream) if stream else 0),
+                                 ctypes.byref(h)), "hca_net_create")
+    return h
+
+
+def hca_net_set_params(net, params) -> None:
+    n = hca_net_param_count()
+    if isinstance(params, np.ndarray):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+    p, nb, on_dev = _ptr(params)
+    if nb < 4 * n:
+        raise ValueError("parameter array too small")
+    _check(load().hca_net_set_params(net, p, on_dev), "hca_net_set_params")
+
+
+def hca_net_get_params(net) -> np.ndarray:
+    out = np.empty(hca_net_param_count(), dtype=np.float32)
+    _check(load().hca_net_get_params(net, out.ctypes.data, 0), "hca_net_get_params")
+    return out
+
+
+def hca_net_forward(net, cfg: hca_config, state, perf, K_prev, out, x_out=None) -> None:
+    n = cfg.nx * cfg.ny * cfg.nz
+    _check(load().hca_net_forward(net, ctypes.byref(cfg), _dev(state, "state", n), _dev(perf, "perf", 4 * n),
+                                  _dev(K_prev, "K_prev", 4 * n), _dev(out, "out", 4 * n),
+                                  _dev(x_out, "x_out", 32 * n) if x_out is not None else None), "hca_net_forward")
+
+
+def hca_net_forward_x(net, x, out) -> None:
+    _check(load().hca_net_forward_x(net, _dev(x, "x"), _dev(out, "out")), "hca_net_forward_x")
+
+
+# stored activations: (name, level, channels) in hca_net_read_activation order
+NET_ACTIVATIONS = (("x", 0, 16), ("e0", 0, 16), ("p0", 1, 16), ("e1", 1, 32), ("p1", 2, 32), ("e2", 2, 64),
+                   ("p2", 3, 64), ("e3", 3, 64), ("d2", 2, 64), ("d1", 1, 32), ("d0", 0, 16))
+
+
+def hca_net_read_activation(net, which: int, dst) -> None:
+    _check(load().hca_net_read_activation(net, which, _dev(dst, "dst")), "hca_net_read_activation")
+
+
+def hca_net_gradients_x(net, x, target, grads=None, loss=None) -> None:
+    _check(load().hca_net_gradients_x(net, _dev(x, "x"), _dev(target, "target"),
+                                      _dev(grads, "grads", 4 * hca_net_param_count()) if grads is not None else None,
+                                      _dev(loss, "loss", 4) if loss is not None else None), "hca_net_gradients_x")
+
+
+def hca_net_adam(net, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8) -> None:
+    _check(load().hca_net_adam(net, lr, beta1, beta2, eps), "hca_net_adam")
+
+
+def hca_net_gradients(net, cfg: hca_config, state, perf, K_prev, K_new, w_mse: float = 1.0, w_res: float = 0.0,
+                      grads=None, loss=None) -> None:
+    n = cfg.nx * cfg.ny * cfg.nz
+    _check(load().hca_net_gradients(net, ctypes.byref(cfg), _dev(state, "state", n), _dev(perf, "perf", 4 * n),
+                                    _dev(K_prev, "K_prev", 4 * n), _dev(K_new, "K_new", 4 * n), w_mse, w_res,
+                                    _dev(grads, "grads", 4 * hca_net_param_count()) if grads is not None else None,
+                                    _dev(loss, "loss", 4) if loss is not None else None), "hca_net_gradients")
+
+
+def hca_net_train_step(net, cfg: hca_config, state, perf, K_prev, K_new, lr: float, loss=None,
+                       w_mse: float = 1.0, w_res: float = 0.0) -> None:
+    n = cfg.nx * cfg.ny * cfg.nz
+    _check(load().hca_net_train_step(net, ctypes.byref(cfg), _dev(state, "state", n), _dev(perf, "perf", 4 * n),
+                                     _dev(K_prev, "K_prev", 4 * n), _dev(K_new, "K_new", 4 * n), w_mse, w_res, lr,
+                                     _dev(loss, "loss", 4) if loss is not None else None), "hca_net_train_step")
+
+
+def hca_net_sync(net) -> None:
+    _check(load().hca_net_sync(net), "hca_net_sync")
+
+
+def hca_net_destroy(net) -> None:
+    if net:
+        load().hca_net_destroy(net)
+
+
+def hca_set_warm_start_net(h, net) -> None:
+    _check(load().hca_set_warm_start_net(h, net if net else None), "hca_set_warm_start_net")
+
+
+class Net:
+    """The warm-start network for one D x H x W lattice (device tensors in and out)."""
+
+    def __init__(self, D: int, H: int, W: int, trainable: bool = False, stream=None):
+        self.shape = (D, H, W)
+        self.handle = hca_net_create(D, H, W, trainable, stream)
+
+    def set_params(self, params) -> None:
+        hca_net_set_params(self.handle, params)
+
+    def params(self) -> np.ndarray:
+        return hca_net_get_params(self.handle)
+
+    def close(self) -> None:
+        if self.handle:
+            hca_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ------------------------------------------------------ convenience ---
 class Sim:
     """One handle (one replicate or a batch) with numpy-friendly helpers."""
@@ -423,6 +576,9 @@ class Sim:
 
     def launches(self) -> int:
         return hca_launch_count(self.handle)
+
+    def set_warm_start_net(self, net) -> None:
+        hca_set_warm_start_net(self.handle, net.handle if isinstance(net, Net) else net)
 
     def close(self) -> None:
         if self.handle:

@@ -1,0 +1,450 @@
+"""GPU parity of the learned warm-start network (libhca's net kernels) with
+the FP64 oracle in oracle/convnet.py: features, forward, gradients, Adam,
+training, and its use as the oxygen solve's initial guess.
+
+Tolerances: the GPU stores activations and activation gradients in BF16 and
+accumulates in FP32; the oracle rounds the same activations to BF16
+(forward(bf16=True)) and keeps everything else in FP64.  What remains is
+FP32-vs-FP64 summation order, which now and then moves a stored activation
+by one BF16 unit (2^-8 relative), plus the BF16 storage of the gradients
+(2^-9 relative per element, averaged over the sums of the weight gradient).
+"""
+
+import numpy as np
+import pytest
+
+from gpu_helpers import make_pair
+from oracle import convnet as C
+from oracle import params as Pm
+from paper_2105_00448_gb300 import hca, warmstart
+
+pytestmark = pytest.mark.gpu
+
+CONVS = C.CONVS
+
+
+def unflatten(flat):
+    """The flat FP32 parameter layout of include/hca.h as a dict."""
+    p, o = {}, 0
+    for name, ci, co in CONVS:
+        n = 27 * co * ci
+        p[name + ".w"] = flat[o:o + n].astype(np.float64).reshape(27, co, ci)
+        o += n
+        p[name + ".b"] = flat[o:o + co].astype(np.float64)
+        o += co
+    p["head.w"] = flat[o:o + 16].astype(np.float64)
+    p["head.b"] = flat[o + 16:o + 17].astype(np.float64)
+    assert o + 17 == flat.size
+    return p
+
+
+def flatten(p):
+    parts = []
+    for name, _, _ in CONVS:
+        parts += [p[name + ".w"].reshape(-1), p[name + ".b"]]
+    parts += [p["head.w"], p["head.b"]]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def random_params(seed):
+    rng = np.random.default_rng(seed)
+    p = C.init_params(rng)
+    for k in p:
+        if k.endswith(".b"):
+            p[k] = rng.standard_normal(p[k].shape) * 0.1
+    return flatten(p)
+
+
+def dev():
+    import torch
+
+    return torch.device("cuda", 0)
+
+
+def to_bf16_dev(x):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(dev()).to(torch.bfloat16).contiguous()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+SHAPES = [(8, 8, 8), (16, 24, 40), (24, 16, 32)]
+
+
+def test_param_count():
+    assert hca.hca_net_param_count() == flatten(C.init_params(np.random.default_rng(0))).size
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_forward_matches_oracle(shape):
+    import torch
+
+    D, H, W = shape
+    rng = np.random.default_rng(1)
+    flat = random_params(2)
+    x = C.bf16_round(rng.standard_normal((D, H, W, 16)) * 0.7)
+    net = hca.Net(D, H, W)
+    net.set_params(flat)
+    out = torch.empty(D * H * W, dtype=torch.float32, device=dev())
+    hca.hca_net_forward_x(net.handle, to_bf16_dev(x), out)
+    got = out.cpu().numpy().reshape(D, H, W).astype(np.float64)
+    ref, _ = C.forward(unflatten(flat), x, bf16=True)
+    net.close()
+    e = rel(got, ref)
+    print(f"forward {shape}: rel L2 {e:.2e}, max abs {np.max(np.abs(got - ref)):.2e}, |ref| {np.max(np.abs(ref)):.2e}")
+    # rounding flips of stored activations propagate: loose end to end (the
+    # per-layer test below is the sharp check)
+    assert e < 1e-2
+    assert np.max(np.abs(got - ref)) < 5e-2 * np.max(np.abs(ref))
+
+
+def _bf16_close(got, ref):
+    """Elements equal, or (rarely) one BF16 unit apart from a rounding tie the
+    FP32 and FP64 sums resolve differently."""
+    diff = np.abs(got - ref)
+    unit = np.maximum(np.abs(ref), np.abs(got)) * 2.0 ** -7 + 1e-30
+    frac = np.mean(diff > 0)
+    return bool(np.all(diff <= unit * 1.01 + 1e-6)) and frac < 5e-3, frac, float(np.max(diff / unit))
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_each_layer_matches_oracle_on_gpu_inputs(shape):
+    """Every stored activation equals the oracle's layer applied to the GPU's
+    own stored inputs (so rounding differences cannot accumulate)."""
+    import torch
+
+    D, H, W = shape
+    rng = np.random.default_rng(12)
+    flat = random_params(13)
+    x = C.bf16_round(rng.standard_normal((D, H, W, 16)) * 0.7)
+    net = hca.Net(D, H, W, trainable=True)
+    net.set_params(flat)
+    out = torch.empty(D * H * W, dtype=torch.float32, device=dev())
+    hca.hca_net_forward_x(net.handle, to_bf16_dev(x), out)
+    act = {}
+    for i, (name, lvl, ch) in enumerate(hca.NET_ACTIVATIONS):
+        t = torch.empty((D >> lvl) * (H >> lvl) * (W >> lvl) * ch, dtype=torch.bfloat16, device=dev())
+        hca.hca_net_read_activation(net.handle, i, t)
+        act[name] = t.float().cpu().numpy().astype(np.float64).reshape(D >> lvl, H >> lvl, W >> lvl, ch)
+    net.close()
+    P = unflatten(flat)
+    Wb = {k: C.bf16_round(v) for k, v in P.items() if k.endswith(".w") and k != "head.w"}
+    r = C.bf16_round
+    relu = lambda v: r(np.maximum(v, 0.0))
+    ref = {
+        "e0": relu(C.conv3(act["x"], Wb["enc0.w"]) + P["enc0.b"]),
+        "p0": r(C.pool(act["e0"])),
+        "e1": relu(C.conv3(act["p0"], Wb["enc1.w"]) + P["enc1.b"]),
+        "p1": r(C.pool(act["e1"])),
+        "e2": relu(C.conv3(act["p1"], Wb["enc2.w"]) + P["enc2.b"]),
+        "p2": r(C.pool(act["e2"])),
+        "e3": relu(C.conv3(act["p2"], Wb["enc3.w"]) + P["enc3.b"]),
+        "d2": relu(C.conv3(C.up(act["e3"]), Wb["dec2.w"]) + P["dec2.b"] + act["e2"]),
+        "d1": relu(C.conv3(C.up(act["d2"]), Wb["dec1.w"]) + P["dec1.b"] + act["e1"]),
+        "d0": relu(C.conv3(C.up(act["d1"]), Wb["dec0.w"]) + P["dec0.b"] + act["e0"]),
+    }
+    assert np.array_equal(act["x"], x)
+    for k, v in ref.items():
+        ok, frac, worst = _bf16_close(act[k], v)
+        print(f"{shape} {k}: differing {frac:.1e}, worst {worst:.2f} units")
+        assert ok, k
+    head = act["d0"] @ P["head.w"] + P["head.b"][0]
+    got = out.cpu().numpy().reshape(D, H, W)
+    assert np.max(np.abs(got - head)) <= 1e-5 * max(1.0, np.max(np.abs(head)))
+
+
+def test_forward_is_deterministic_and_tile_independent():
+    import torch
+
+    D, H, W = 16, 16, 48
+    rng = np.random.default_rng(4)
+    flat = random_params(5)
+    x = C.bf16_round(rng.standard_normal((D, H, W, 16)))
+    net = hca.Net(D, H, W)
+    net.set_params(flat)
+    xd = to_bf16_dev(x)
+    o1 = torch.empty(D * H * W, dtype=torch.float32, device=dev())
+    o2 = torch.empty_like(o1)
+    hca.hca_net_forward_x(net.handle, xd, o1)
+    hca.hca_net_forward_x(net.handle, xd, o2)
+    assert torch.equal(o1, o2)
+    net.close()
+
+
+def test_features_match_oracle():
+    import torch
+
+    shape = (16, 16, 24)
+    sim, cfg, maps = make_pair(shape, "f64", seed=3, n_drugs=1)
+    sim.step(2)
+    st = sim.states()
+    K = sim.field(hca.FIELD_O2).astype(np.float32)
+    perf = maps.perf.astype(np.float32)
+    sim.close()
+    D, H, W = shape
+    net = hca.Net(D, H, W)
+    c = hca.make_config(W, H, D)
+    out = torch.empty(D * H * W, dtype=torch.float32, device=dev())
+    xo = torch.empty(D * H * W * 16, dtype=torch.bfloat16, device=dev())
+    tt = lambda a: torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).to(dev())
+    hca.hca_net_forward(net.handle, c, tt(st), tt(perf), tt(K), out, xo)
+    net.close()
+    got = xo.float().cpu().numpy().astype(np.float64).reshape(D, H, W, 16)
+    ref = C.bf16_round(C.make_input(st, perf.astype(np.float64), K.astype(np.float64), cfg))
+    assert np.array_equal(got[..., :7], ref[..., :7])      # one-hot and perf: exact
+    assert np.all(got[..., 9:] == 0)
+    ulp = lambda v: np.maximum(np.abs(v), 1e-30) * 2.0 ** -7
+    assert np.all(np.abs(got[..., 7] - ref[..., 7]) <= ulp(ref[..., 7]))
+    # the residual channel: float arithmetic with cancellation vs FP64, then BF16
+    assert np.all(np.abs(got[..., 8] - ref[..., 8]) <= ulp(ref[..., 8]) + 2e-3)
+
+
+@pytest.mark.parametrize("shape", [(8, 8, 8), (16, 16, 32)])
+def test_gradients_match_oracle(shape):
+    import torch
+
+    D, H, W = shape
+    rng = np.random.default_rng(7)
+    flat = random_params(8)
+    x = C.bf16_round(rng.standard_normal((D, H, W, 16)) * 0.7)
+    tgt = rng.standard_normal((D, H, W)).astype(np.float32)
+    net = hca.Net(D, H, W, trainable=True)
+    net.set_params(flat)
+    n = hca.hca_net_param_count()
+    g = torch.empty(n, dtype=torch.float32, device=dev())
+    loss = torch.empty(1, dtype=torch.float32, device=dev())
+    hca.hca_net_gradients_x(net.handle, to_bf16_dev(x), torch.from_numpy(tgt.reshape(-1)).to(dev()), g, loss)
+    gg = unflatten(g.cpu().numpy())
+    net.close()
+    P = unflatten(flat)
+    out, cache = C.forward(P, x, bf16=True)
+    L, gout = C.mse_grad(out, tgt.astype(np.float64))
+    ref = C.backward(P, cache, gout)
+    assert abs(float(loss.item()) - L) <= 1e-4 * L
+    for k in ref:
+        e = rel(gg[k], ref[k])
+        print(f"grad {k}: rel {e:.2e}")
+        assert e < 3e-2, k
+
+
+def test_combined_loss_gradients_match_oracle():
+    """Gradients of 0.5 MSE + 0.25 residual loss for one solver field, oracle
+    fed with the GPU's own (BF16) features."""
+    import torch
+
+    shape = (16, 16, 24)
+    sim, cfg, maps = make_pair(shape, "f64", seed=6, n_drugs=0)
+    sim.step(1)
+    st = sim.states()
+    Kp = sim.field(hca.FIELD_O2).astype(np.float32)
+    sim.stage(hca.STAGE_O2)
+    Kn = sim.field(hca.FIELD_O2).astype(np.float32)
+    sim.close()
+    D, H, W = shape
+    flat = random_params(14)
+    net = hca.Net(D, H, W, trainable=True)
+    net.set_params(flat)
+    tt = lambda a: torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).to(dev())
+    n = hca.hca_net_param_count()
+    g = torch.empty(n, dtype=torch.float32, device=dev())
+    loss = torch.empty(1, dtype=torch.float32, device=dev())
+    c = hca.make_config(W, H, D)
+    hca.hca_net_gradients(net.handle, c, tt(st), tt(maps.perf.astype(np.float32)), tt(Kp), tt(Kn),
+                          0.5, 0.25, g, loss)
+    xg = torch.empty(D * H * W * 16, dtype=torch.bfloat16, device=dev())
+    hca.hca_net_read_activation(net.handle, 0, xg)
+    x = xg.float().cpu().numpy().astype(np.float64).reshape(D, H, W, 16)
+    gg = unflatten(g.cpu().numpy())
+    net.close()
+    P = unflatten(flat)
+    out, cache = C.forward(P, x, bf16=True)
+    tgt = C.target(Kp.astype(np.float64), Kn.astype(np.float64), cfg)
+    Lr, gr = C.residual_loss(out, tgt, st, Kp.astype(np.float64), cfg)
+    Lm, gm = C.mse_grad(out, tgt)
+    L, gout = 0.5 * Lm + 0.25 * Lr, 0.5 * gm + 0.25 * gr
+    ref = C.backward(P, cache, gout)
+    assert abs(float(loss.item()) - L) <= 1e-3 * L
+    for k in ref:
+        e = rel(gg[k], ref[k])
+        print(f"residual-loss grad {k}: rel {e:.2e}")
+        assert e < 3e-2, k
+
+
+def test_adam_step_matches_formula():
+    import torch
+
+    D = H = W = 8
+    rng = np.random.default_rng(9)
+    flat = random_params(10)
+    x = C.bf16_round(rng.standard_normal((D, H, W, 16)))
+    tgt = torch.from_numpy(rng.standard_normal(D * H * W).astype(np.float32)).to(dev())
+    net = hca.Net(D, H, W, trainable=True)
+    net.set_params(flat)
+    n = hca.hca_net_param_count()
+    g = torch.empty(n, dtype=torch.float32, device=dev())
+    w = flat.astype(np.float64)
+    m = np.zeros(n)
+    v = np.zeros(n)
+    for t in (1, 2, 3):
+        hca.hca_net_gradients_x(net.handle, to_bf16_dev(x), tgt, g, None)
+        gh = g.cpu().numpy().astype(np.float64)
+        hca.hca_net_adam(net.handle, 1e-3)
+        w, m, v = C.adam(w, gh, m, v, t, 1e-3)
+        got = net.params().astype(np.float64)
+        assert np.max(np.abs(got - w)) <= 1e-6, t
+        w = got    # follow the GPU's FP32 weights into the next step
+    net.close()
+
+
+def _sim_samples(shape, seed, n_steps, precision="f32"):
+    import torch
+
+    nz, ny, nx = shape
+    sim, cfg, maps = make_pair(shape, precision, seed=seed, n_drugs=1, rtol_o2=1e-8, corr_len=4.0)
+    sim.step(1)
+    samples = warmstart.collect_samples(sim, n_steps, dev())
+    sim.close()
+    return samples, hca.make_config(nx, ny, nz)
+
+
+def test_training_reduces_the_loss_on_solver_fields():
+    shape = (16, 32, 32)
+    samples, c = _sim_samples(shape, 11, 4)
+    net = hca.Net(*shape, trainable=True)
+    net.set_params(warmstart.init_params(0))
+    losses = warmstart.train(net, c, samples, 400, 3e-3, seed=1, lr_final=2e-4)
+    net.close()
+    first, last = losses[:10].mean(), losses[-10:].mean()
+    print(f"loss {first:.3e} -> {last:.3e}")
+    assert np.all(np.isfinite(losses)) and last < 0.5 * first
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_learned_start_keeps_the_solution_and_cuts_iterations(precision):
+    """Overfit one oxygen solve, then start the same solve from the network's
+    guess: the solver must reach the same field (linearised about K_prev, not
+    about the guess) in fewer iterations."""
+    import torch
+
+    shape = (16, 32, 32)
+    nz, ny, nx = shape
+    rtol = 1e-10 if precision == "f64" else 1e-8
+    common = dict(seed=21, n_drugs=1, rtol_o2=rtol, corr_len=4.0)
+    ref, _, _ = make_pair(shape, precision, **common)
+    ref.step(2)
+    st, Kp = ref.states(), ref.field(hca.FIELD_O2)
+    perf = ref.field(hca.FIELD_PERF)
+    ref.stage(hca.STAGE_O2)
+    K_ref = ref.field(hca.FIELD_O2)
+    it_prev = ref.stats()["o2_iterations"]
+    ref.close()
+
+    tt = lambda a: torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).to(dev())
+    s = warmstart.Sample(tt(st), tt(perf.astype(np.float32)), tt(Kp.astype(np.float32)), tt(K_ref.astype(np.float32)))
+    net = hca.Net(*shape, trainable=True)
+    net.set_params(warmstart.init_params(3))
+    warmstart.train(net, hca.make_config(nx, ny, nz), [s], 1500, 3e-3, lr_final=1.5e-4)
+
+    sim, _, _ = make_pair(shape, precision, warm_start=hca.HCA_WS_LEARNED, **common)
+    sim.set_states(st)
+    sim.set_field(hca.FIELD_O2, Kp)
+    sim.set_warm_start_net(net)
+    sim.stage(hca.STAGE_O2)
+    K = sim.field(hca.FIELD_O2)
+    stt = sim.stats()
+    sim.close()
+    net.close()
+    print(precision, "iterations", it_prev, "->", stt["o2_iterations"], "r0", stt["ws_r0_prev"], stt["ws_r0_learned"])
+    assert stt["ws_used"] == 1 and stt["ws_r0_learned"] < stt["ws_r0_prev"]
+    assert stt["o2_iterations"] < it_prev
+    tol = 1e-8 if precision == "f64" else 2e-6
+    assert np.max(np.abs(K - K_ref)) <= tol * np.max(np.abs(K_ref))
+
+
+def test_poor_guess_falls_back_to_previous_field():
+    shape = (16, 16, 16)
+    common = dict(seed=5, n_drugs=0, rtol_o2=1e-10)
+    ref, _, _ = make_pair(shape, "f64", **common)
+    ref.step(1)
+    it_ref_state = (ref.states(), ref.field(hca.FIELD_O2))
+    ref.stage(hca.STAGE_O2)
+    it_prev, K_ref = ref.stats()["o2_iterations"], ref.field(hca.FIELD_O2)
+    ref.close()
+    flat = np.zeros(hca.hca_net_param_count(), dtype=np.float32)
+    flat[-1] = 50.0                      # head bias: guess = K_prev + K0 * 50 / 64 everywhere
+    net = hca.Net(*shape)
+    net.set_params(flat)
+    sim, _, _ = make_pair(shape, "f64", warm_start=hca.HCA_WS_LEARNED, **common)
+    sim.set_states(it_ref_state[0])
+    sim.set_field(hca.FIELD_O2, it_ref_state[1])
+    sim.set_warm_start_net(net)
+    sim.stage(hca.STAGE_O2)
+    stt = sim.stats()
+    K = sim.field(hca.FIELD_O2)
+    sim.close()
+    net.close()
+    assert stt["ws_used"] == 0 and stt["ws_r0_learned"] > stt["ws_r0_prev"]
+    assert stt["o2_iterations"] == it_prev and np.array_equal(K, K_ref)
+
+
+def test_learned_mode_argument_errors():
+    with pytest.raises(hca.HcaError):
+        hca.Net(12, 16, 16)                      # not a multiple of 8
+    sim, _, _ = make_pair((16, 16, 16), "f64", seed=1, n_drugs=0)
+    net = hca.Net(16, 16, 16)
+    with pytest.raises(hca.HcaError):            # handle not created with HCA_WS_LEARNED
+        sim.set_warm_start_net(net)
+    sim.close()
+    sim, _, _ = make_pair((16, 16, 16), "f64", seed=1, n_drugs=0, warm_start=hca.HCA_WS_LEARNED)
+    other = hca.Net(16, 16, 24)
+    with pytest.raises(hca.HcaError):            # lattice mismatch
+        sim.set_warm_start_net(other)
+    sim.step(1)                                  # no network attached: plain warm start
+    assert sim.stats()["ws_used"] == 0
+    sim.close()
+    net.close()
+    other.close()
+
+
+def test_trained_network_cuts_oxygen_iterations_on_held_out_solves():
+    """The gain over the plain warm start: train on the oxygen solves of two
+    runs (seeds 2000, 2001), then start held-out solves of another run
+    (seed 1) from the network's guess (residual-checked); FP32 with defect
+    correction to rtol 1e-6, 32 x 64 x 64 lattice."""
+    shape = (32, 64, 64)
+    nz, ny, nx = shape
+    common = dict(n_drugs=1, rtol_o2=1e-6, corr_len=4.0)
+
+    def collect(seed, warm, n):
+        sim, _, _ = make_pair(shape, "f32", seed=seed, **common)
+        sim.step(warm)
+        s = warmstart.collect_samples(sim, n, dev())
+        sim.close()
+        return s
+
+    train_s = collect(2000, 1, 24) + collect(2001, 1, 24)
+    test_s = collect(1, 3, 4)
+    net = hca.Net(*shape, trainable=True)
+    net.set_params(warmstart.init_params(0))
+    warmstart.train(net, hca.make_config(nx, ny, nz), train_s, 4000, 3e-3, seed=1, lr_final=1.5e-4,
+                    w_res=0.03)
+    it = {0: 0, 1: 0}
+    for s in test_s:
+        K_prev = s.K_prev.cpu().numpy().reshape(shape)
+        for mode in (0, 1):
+            sim, _, _ = make_pair(shape, "f32", seed=1, warm_start=mode, **common)
+            sim.set_states(s.state.cpu().numpy().reshape(shape))
+            sim.set_field(hca.FIELD_O2, K_prev)
+            if mode:
+                sim.set_warm_start_net(net)
+            sim.stage(hca.STAGE_O2)
+            st = sim.stats()
+            assert st["o2_rel_residual"] <= 1e-6
+            it[mode] += st["o2_iterations"]
+            sim.close()
+    net.close()
+    print("held-out oxygen CG iterations: previous-step start", it[0], "learned start", it[1])
+    assert it[1] <= 0.9 * it[0]

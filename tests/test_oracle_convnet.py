@@ -145,3 +145,32 @@ def test_input_features():
     assert np.max(np.abs(xf[..., 8])) < 1e-9
     Kn = rng.uniform(5, 20, size=st.shape)
     assert np.allclose(C.guess(K, C.target(K, Kn, cfg), cfg), Kn)
+
+
+def test_residual_loss_gradient_and_special_cases():
+    cfg = Pm.Config(5, 4, 3)
+    rng = np.random.default_rng(8)
+    st = rng.integers(0, 6, size=(3, 4, 5)).astype(np.uint8)
+    Kp = rng.uniform(5, 20, size=st.shape)
+    out = rng.standard_normal(st.shape)
+    tgt = rng.standard_normal(st.shape)
+    L, g = C.residual_loss(out, tgt, st, Kp, cfg)
+    h = 1e-6
+    for idx in [(0, 0, 0), (1, 2, 3), (2, 3, 4), (1, 0, 2)]:
+        o = out.copy()
+        o[idx] += h
+        lp = C.residual_loss(o, tgt, st, Kp, cfg)[0]
+        o[idx] -= 2 * h
+        lm = C.residual_loss(o, tgt, st, Kp, cfg)[0]
+        assert abs((lp - lm) / (2 * h) - g[idx]) <= 1e-6 * max(1.0, abs(g[idx]))
+    # a constant error on a lattice without consumers or vessels lies in the
+    # Neumann Laplacian's null space: zero loss
+    st0 = np.zeros_like(st)
+    assert C.residual_loss(tgt + 0.3, tgt, st0, Kp, cfg)[0] < 1e-24
+    # a single-site error e at an isolated interior empty site: (A e)/c has
+    # 6 e at the site and -e at each of its 6 neighbours -> mean = 42 e^2 / n
+    st1 = np.zeros((3, 3, 3), dtype=np.uint8)
+    e = np.zeros((3, 3, 3))
+    e[1, 1, 1] = 0.5
+    L1, _ = C.residual_loss(e, np.zeros_like(e), st1, np.ones_like(e), Pm.Config(3, 3, 3))
+    assert L1 == pytest.approx(42 * 0.25 / 27)
