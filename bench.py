@@ -319,7 +319,7 @@ def run_ws_learned(args, hca, make_maps, np, torch):
     net_t = hca.Net(m, m, m, trainable=True)
     net_t.set_params(warmstart.init_params(0))
     t0 = time.perf_counter()
-    losses = warmstart.train(net_t, hca.make_config(m, m, m), samples, args.ws_iters, 3e-3, seed=1, lr_final=1.5e-4,
+    losses = warmstart.train(net_t, hca.make_config(m, m, m), samples, args.ws_iters, 1e-3, seed=1, lr_final=5e-5,
                              w_res=0.03)
     t_train = time.perf_counter() - t0
     params = net_t.params()
@@ -376,7 +376,7 @@ def run_ws_learned(args, hca, make_maps, np, torch):
     achieved = NET_FLOPS_PER_SITE * n ** 3 / (fwd_ms * 1e-3) / 1e12
     prev, lrn = runs[hca.HCA_WS_PREV], runs[hca.HCA_WS_LEARNED]
     return {"workload": f"{n}^3 workload, oxygen rtol 1e-6, {args.ws_steps} steps after {args.warmup} warm-up",
-            "training": f"{args.ws_iters} Adam steps (MSE + 0.03 residual) on {args.ws_samples} oxygen solves of two {m}^3 runs "
+            "training": f"{args.ws_iters} Adam steps (MSE + 0.03 residual, lr 1e-3 -> 5e-5) on {args.ws_samples} oxygen solves of two {m}^3 runs "
                         f"(seeds 2000, 2001); collect {t_collect:.1f} s, train {t_train:.1f} s; "
                         f"loss {float(np.mean(losses[:20])):.2e} -> {float(np.mean(losses[-50:])):.2e}",
             "previous_step_start": prev, "learned_start": lrn,
