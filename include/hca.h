@@ -90,6 +90,16 @@ extern "C" {
 #define HCA_STAGE_ADVANCE (1u << 4) /* step counter n -> n+1 */
 #define HCA_STAGE_ALL 0x1Fu
 
+/* CG preconditioner.  HCA_PC_JACOBI: diag(A), the textbook PCG of the
+ * reference solver.  HCA_PC_MG: one symmetric geometric-multigrid V-cycle
+ * per iteration (the lattice counterpart of the paper's algebraic-multigrid
+ * preconditioned CG, Section 2.4): 2x2x2 agglomeration, coupling doubled per
+ * level, reaction summed over the children, sum restriction, copy
+ * prolongation, one weighted-Jacobi sweep (weight 0.8) before and after the
+ * coarse correction, 16 sweeps on the coarsest level (<= 512 sites). */
+#define HCA_PC_JACOBI 0
+#define HCA_PC_MG 1
+
 /* warm start of the oxygen CG */
 #define HCA_WS_PREV 0     /* previous step's K */
 #define HCA_WS_LEARNED 1  /* network guess (hca_set_warm_start_net), residual-checked */
@@ -148,7 +158,9 @@ typedef struct hca_config {
   int32_t max_outer;     /* defect-correction sweeps per oxygen solve (8) */
 
   int32_t warm_start;    /* HCA_WS_PREV */
+  int32_t preconditioner; /* HCA_PC_JACOBI (default) or HCA_PC_MG (single-replicate handles) */
   int32_t threads_per_block; /* 0 = library choice (128); else 64, 128, 256 or 512; results do not depend on it */
+  int32_t pad2;
   void* stream;          /* cudaStream_t, NULL = default stream */
 } hca_config;
 
@@ -182,7 +194,8 @@ typedef struct hca_handle hca_handle;
 #define HCA_KCLASS_CA_COMPACT 5 /* CA commit compaction */
 #define HCA_KCLASS_CA_COLOUR 6  /* CA colour sweeps */
 #define HCA_KCLASS_OTHER 7
-#define HCA_NKCLASS 8
+#define HCA_KCLASS_MG 8         /* multigrid V-cycle (all its kernels) */
+#define HCA_NKCLASS 9
 
 typedef struct hca_profile {
   int64_t launches[HCA_NKCLASS];
@@ -251,6 +264,13 @@ int hca_get_stats(hca_handle* h, int32_t rep, hca_stats* out);
  * precision.  Exposes the 7-point stencil of Eqs. (oxygen)/(chemo) alone. */
 int hca_apply_operator(hca_handle* h, int32_t rep, int32_t which, const void* u, void* out,
                        int32_t on_device);
+
+/* z = M r for replicate rep, with M the multigrid V-cycle (HCA_PC_MG) built
+ * on the operator of the next solve of `which` (as hca_apply_operator).
+ * r, z: nx*ny*nz elements of the handle's precision.  HCA_ERR_STATE unless
+ * the handle was created with HCA_PC_MG.  Exposes the preconditioner alone. */
+int hca_apply_preconditioner(hca_handle* h, int32_t rep, int32_t which, const void* r, void* z,
+                             int32_t on_device);
 
 /* 24-bit Philox4x32-10 uniforms u = (w0 >> 8) * 2^-24 for sites
  * site_begin .. site_begin + n - 1 with counter (site lo, site hi, step,

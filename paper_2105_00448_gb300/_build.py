@@ -31,6 +31,7 @@ UNITS = {
     "engine.cu": [],
     "noalloc.cu": [],
     "net.cu": [],
+    "mg.cu": [],
 }
 
 

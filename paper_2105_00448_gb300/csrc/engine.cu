@@ -31,6 +31,8 @@ void launch_ca_compact(const Ctx& c, bool fp64);
 void launch_ca_colour(const Ctx& c, int colour, int blocks_x, bool fp64);
 void set_pass_regs(int r);
 void set_pass_ni(int ni);
+void launch_mg_setup(const Ctx& c, int which, bool fp64, const MGHost& H);
+void launch_vcycle(const Ctx& c, int which, bool fp64, const MGHost& H);
 }  // namespace hca
 
 using hca::Ctx;
@@ -83,6 +85,9 @@ struct hca_handle {
   bool graphs_ok = true;
   int* h_pinned = nullptr;    // [0] active replicates, [1] error flag
   std::vector<void*> allocs;
+  // multigrid preconditioner (single replicate)
+  bool mg = false;
+  hca::MGHost mgh;
   // learned warm start of the oxygen solve (single replicate)
   bool learned = false;
   hca_net* net = nullptr;
@@ -180,6 +185,7 @@ int validate(const hca_config& c) {
   if (!(t == 0 || t == 64 || t == 128 || t == 256 || t == 512)) return HCA_ERR_ARG;
   if (c.warm_start != HCA_WS_PREV && c.warm_start != HCA_WS_LEARNED && c.warm_start != HCA_WS_LEARNED_ALWAYS)
     return HCA_ERR_ARG;
+  if (c.preconditioner != HCA_PC_JACOBI && c.preconditioner != HCA_PC_MG) return HCA_ERR_ARG;
   return HCA_OK;
 }
 
@@ -283,6 +289,12 @@ void pass_b(hca_handle* h, int which, void* x, hca::CondArg cnd) {
   hca::launch_pass_b(h->ctx, which, x, h->fp64, cnd);
 }
 
+// z = M r (V-cycle); also sets rho and beta for the next pass A
+void vcycle(hca_handle* h, int which) { hca::launch_vcycle(h->ctx, which, h->fp64, h->mgh); }
+
+// coarse diagonals of the current operator (after its set-up stored d)
+void mg_setup(hca_handle* h, int which) { hca::launch_mg_setup(h->ctx, which, h->fp64, h->mgh); }
+
 // CG iterations (pass A, pass B) on operator `which` for every replicate whose
 // solve is active, updating x, until none is active or maxit is reached.  The
 // first convergence check comes after about as many iterations as the same
@@ -301,6 +313,7 @@ int pcg_iterate(hca_handle* h, int which, void* x, int predict) {
     for (int k = 0; k < n; ++k) {
       HCA_LAUNCH(h, HCA_KCLASS_PASS_A, 1, pass_a(h, which));
       HCA_LAUNCH(h, HCA_KCLASS_PASS_B, 1, pass_b(h, which, x, kNoCond));
+      if (h->mg) HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.launches, vcycle(h, which));
     }
     done += n;
     chunk = h->prof.on ? 1 : 4;
@@ -316,6 +329,10 @@ int solve_plain(hca_handle* h, int which) {
   Ctx& c = h->ctx;
   void* x = which == 0 ? c.K : c.G[which - 1];
   HCA_LAUNCH(h, HCA_KCLASS_SETUP, 1, hca::launch_setup(c, which, h->fp64, kNoCond));
+  if (h->mg) {
+    HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.nlev - 1, mg_setup(h, which));
+    HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.launches, vcycle(h, which));
+  }
   int rc = pcg_iterate(h, which, x, h->prev_inner[which][0]);
   if (rc) return rc;
   h->prev_inner[which][0] = h->last_iters;
@@ -335,6 +352,10 @@ int solve_dc(hca_handle* h, int which) {
   for (int outer = 0;; ++outer) {
     HCA_LAUNCH(h, HCA_KCLASS_RESIDUAL, 1,
                hca::launch_dc_residual(c, which, xh, xl, outer == 0, kNoCond, kNoCond));
+    if (h->mg) {
+      if (outer == 0) HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.nlev - 1, mg_setup(h, which));
+      HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.launches, vcycle(h, which));
+    }
     HCA_TRY(cudaMemcpyAsync(h->h_pinned, &c.sync->active_count, 2 * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     HCA_TRY(cudaStreamSynchronize(c.stream));
     if (h->h_pinned[1]) return HCA_ERR_NONFINITE;
@@ -426,6 +447,10 @@ int cap_solve(hca_handle* h, int which, cudaGraph_t G) {
     const hca::CondArg cnd{H, 1};
     c.stream = S;
     hca::launch_setup(c, which, h->fp64, cnd);
+    if (h->mg) {
+      mg_setup(h, which);
+      vcycle(h, which);
+    }
     HCA_TRY(cudaGetLastError());
     cudaGraph_t body;
     if ((rc = add_while(S, H, &body))) return rc;
@@ -433,6 +458,7 @@ int cap_solve(hca_handle* h, int which, cudaGraph_t G) {
     c.stream = S2;
     pass_a(h, which);
     pass_b(h, which, x, cnd);
+    if (h->mg) vcycle(h, which);
     HCA_TRY(cudaGetLastError());
     HCA_TRY(cudaStreamEndCapture(S2, &body));
     c.stream = S;
@@ -448,6 +474,10 @@ int cap_solve(hca_handle* h, int which, cudaGraph_t G) {
   const hca::CondArg co{Ho, 1}, ci{Hi, 1};
   c.stream = S;
   hca::launch_dc_residual(c, which, xh, xl, true, co, ci);
+  if (h->mg) {
+    mg_setup(h, which);
+    vcycle(h, which);
+  }
   HCA_TRY(cudaGetLastError());
   cudaGraph_t bo, bi;
   if ((rc = add_while(S, Ho, &bo))) return rc;
@@ -457,11 +487,13 @@ int cap_solve(hca_handle* h, int which, cudaGraph_t G) {
   c.stream = S3;
   pass_a(h, which);
   pass_b(h, which, c.dx, ci);
+  if (h->mg) vcycle(h, which);
   HCA_TRY(cudaGetLastError());
   HCA_TRY(cudaStreamEndCapture(S3, &bi));
   c.stream = S2;
   hca::launch_dc_update(c, xh, xl);
   hca::launch_dc_residual(c, which, xh, xl, false, co, ci);
+  if (h->mg) vcycle(h, which);
   HCA_TRY(cudaGetLastError());
   HCA_TRY(cudaStreamEndCapture(S2, &bo));
   c.stream = S;
@@ -674,8 +706,9 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
         cfgs[i].dt != cfgs[0].dt || cfgs[i].threads_per_block != cfgs[0].threads_per_block ||
         cfgs[i].stream != cfgs[0].stream)
       return HCA_ERR_ARG;
-    // the learned warm start runs one network on one lattice
-    if (cfgs[i].warm_start != HCA_WS_PREV && n > 1) return HCA_ERR_UNIMPLEMENTED;
+    // the learned warm start and the multigrid hierarchy serve one lattice
+    if ((cfgs[i].warm_start != HCA_WS_PREV || cfgs[i].preconditioner != HCA_PC_JACOBI) && n > 1)
+      return HCA_ERR_UNIMPLEMENTED;
   }
   hca_handle* h = new (std::nothrow) hca_handle();
   if (!h) return HCA_ERR_OOM;
@@ -685,6 +718,7 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
   h->stream = (cudaStream_t)cfgs[0].stream;
   h->cfgs.assign(cfgs, cfgs + n);
   h->learned = cfgs[0].warm_start != HCA_WS_PREV;
+  h->mg = cfgs[0].preconditioner == HCA_PC_MG;
   {
     // HCA_NO_GRAPH=1 runs steps from a host loop instead of the step graph
     const char* ng = std::getenv("HCA_NO_GRAPH");
@@ -764,6 +798,46 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     ALLOC(c.d, fbytes);
     ALLOC(c.b, fbytes);
     ALLOC(c.aux, fbytes);
+    if (h->mg) {
+      hca::MGHost& H = h->mgh;
+      const RepDesc& r0 = h->reps_h[0];
+      int nx = r0.nx, ny = r0.ny, nz = r0.nz;
+      long long nn = (long long)nx * ny * nz;
+      H.n0 = nn;
+      H.nlev = 1;
+      while (nn > hca::MG_MIN_SITES && std::min(nx, std::min(ny, nz)) > 1 && H.nlev < 16) {
+        nx = (nx + 1) / 2;
+        ny = (ny + 1) / 2;
+        nz = (nz + 1) / 2;
+        nn = (long long)nx * ny * nz;
+        hca::MGLevel& L = H.lv[H.nlev];
+        L.nx = nx;
+        L.ny = ny;
+        L.nz = nz;
+        L.n = nn;
+        L.cscale = std::ldexp(1.0, H.nlev);
+        ALLOC(L.x, es * (size_t)nn);
+        ALLOC(L.t, es * (size_t)nn);
+        ALLOC(L.rhs, es * (size_t)nn);
+        ALLOC(L.d, es * (size_t)nn);
+        H.nlev += 1;
+      }
+      H.small = H.nlev - 1;
+      for (int l = 1; l < H.nlev; ++l)
+        if (H.lv[l].n <= hca::MG_SMALL_SITES) {
+          H.small = l;
+          break;
+        }
+      H.launches = H.nlev == 1 ? hca::MG_NU_COARSE : 5 + 4 * (H.small - 1);
+      ALLOC(c.r, fbytes);
+      ALLOC(c.mg_t0, fbytes);
+      hca::MGLevel* lv_d;
+      ALLOC(lv_d, sizeof(hca::MGLevel) * H.nlev);
+      c.mg_lv = lv_d;
+      c.mg = 1;
+      c.mg_nlev = H.nlev;
+      c.mg_small = H.small;
+    }
     if (h->learned) {
       ALLOC(h->ws_cand, sizeof(double) * (size_t)h->total);
       ALLOC(h->ws_part, sizeof(double) * 3 * hcanet::kWsNormBlocks);
@@ -796,12 +870,27 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     }
     // zero every device array (padding sites must hold 0)
     void* zero_list[] = {c.K, c.K_lo, c.G[0], c.G[1], c.G[2], c.G_lo[0], c.G_lo[1], c.G_lo[2], c.dx,
-                         c.phi, c.P, c.Vc, c.perf, c.z, c.p, c.p_alt, c.d, c.b, c.aux, c.reac};
+                         c.phi, c.P, c.Vc, c.perf, c.z, c.p, c.p_alt, c.d, c.b, c.aux, c.reac, c.r, c.mg_t0};
     for (void* p : zero_list)
       if (p && cudaMemsetAsync(p, 0, fbytes, s)) {
         rc = HCA_ERR_CUDA;
         goto fail;
       }
+    if (h->mg) {
+      const hca::MGHost& H = h->mgh;
+      for (int l = 1; l < H.nlev; ++l) {
+        void* arr[4] = {H.lv[l].x, H.lv[l].t, H.lv[l].rhs, H.lv[l].d};
+        for (void* p : arr)
+          if (cudaMemsetAsync(p, 0, es * (size_t)H.lv[l].n, s)) {
+            rc = HCA_ERR_CUDA;
+            goto fail;
+          }
+      }
+      if (cudaMemcpyAsync(const_cast<void*>(c.mg_lv), H.lv, sizeof(hca::MGLevel) * H.nlev, cudaMemcpyHostToDevice, s)) {
+        rc = HCA_ERR_CUDA;
+        goto fail;
+      }
+    }
     if (cudaMemsetAsync(c.state, 0, (size_t)h->total + 16, s) || cudaMemsetAsync(c.sync, 0, sizeof(hca::PassSync), s) ||
         cudaMemsetAsync(c.solve, 0, sizeof(hca::RepSolve) * n, s) ||
         cudaMemsetAsync(c.stats, 0, sizeof(hca::DevStats) * n, s) || cudaMemsetAsync(c.step, 0, sizeof(long long), s) ||
@@ -964,6 +1053,7 @@ int hca_config_default(hca_config* c, int32_t nx, int32_t ny, int32_t nz) {
   c->rtol_inner = 1e-3;
   c->max_outer = 8;
   c->warm_start = HCA_WS_PREV;
+  c->preconditioner = HCA_PC_JACOBI;
   c->threads_per_block = 0;
   c->stream = nullptr;
   return HCA_OK;
@@ -1131,6 +1221,25 @@ int hca_set_warm_start_net(hca_handle* h, hca_net* n) {
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
   h->graphs.clear();
   h->net = n;
+  return HCA_OK;
+}
+
+int hca_apply_preconditioner(hca_handle* h, int32_t rep, int32_t which, const void* r, void* z, int32_t on_device) {
+  if (check_rep(h, rep) || !r || !z || which < 0 || which > h->n_drugs) return HCA_ERR_ARG;
+  if (!h->mg) return HCA_ERR_STATE;
+  (void)on_device;
+  const size_t es = elem_size(h);
+  Ctx& c = h->ctx;
+  // the set-up of a solve of `which` writes the diagonal (its other outputs
+  // are rewritten by the next solve)
+  HCA_LAUNCH(h, HCA_KCLASS_SETUP, 1, hca::launch_setup(c, which, h->fp64, kNoCond));
+  HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.nlev - 1, mg_setup(h, which));
+  int rc = copy_field(h, rep, c.r, es, const_cast<void*>(r), false, 0);
+  if (rc) return rc;
+  HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.launches, vcycle(h, which));
+  rc = copy_field(h, rep, c.z, es, z, true, 0);
+  if (rc) return rc;
+  HCA_TRY(cudaStreamSynchronize(c.stream));
   return HCA_OK;
 }
 

@@ -224,6 +224,29 @@ namespace hca {
 
 // Device pointers and launch parameters of one handle, passed by value to
 // every kernel.  Field pointers are typed per precision by the kernels.
+// One coarse level of the multigrid hierarchy (dense, x fastest).
+struct MGLevel {
+  int nx, ny, nz, pad;
+  long long n;
+  void *x, *t, *rhs, *d;   // iterate, second iterate, right-hand side, diagonal
+  double cscale;            // coupling of this level / coupling of the lattice (2^level)
+};
+
+// multigrid constants (the FP64 reference uses the same)
+constexpr double MG_OMEGA = 0.8;
+constexpr int MG_NU_COARSE = 16;
+constexpr long long MG_MIN_SITES = 512;     // coarsening stops at or below this size
+constexpr long long MG_SMALL_SITES = 4096;  // levels this small run inside one block
+
+// Host copy of the hierarchy (launch geometry and pointers).
+struct MGHost {
+  int nlev = 0;
+  int small = 0;
+  long long n0 = 0;
+  MGLevel lv[16] = {};
+  int launches = 0;   // kernels per V-cycle
+};
+
 struct Ctx {
   const RepDesc* reps;
   int n_reps;
@@ -240,6 +263,14 @@ struct Ctx {
   void* dx;      // FP32 scheme: correction of the inner solve
   void* aux;     // scratch field (previous iterate of the initial oxygen fixed point)
   const void* lag;  // oxygen linearisation point (K_prev) when the solve starts elsewhere; null: the start field
+  // multigrid preconditioner (single replicate): residual r (the Jacobi form
+  // carries z = r / d instead), level-0 scratch, coarse level table
+  int mg;           // 0: Jacobi (z = r / d), 1: V-cycle (z = M r)
+  int mg_nlev;      // levels including the lattice itself
+  int mg_small;     // first level handled by the single-block kernel
+  void* r;
+  void* mg_t0;
+  const void* mg_lv;  // device MGLevel[mg_nlev] (entry 0 unused)
   void* reac;    // FP32 scheme: reaction part a of the diagonal d = c n + a
   void* phi;
   void* P;

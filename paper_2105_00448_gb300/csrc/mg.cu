@@ -1,0 +1,375 @@
+// Geometric-multigrid V-cycle preconditioner for the CG solves of
+// Eqs. (oxygen) and (chemo): z = M r with M one symmetric V-cycle.
+//
+// The paper preconditions CG with algebraic multigrid (BoomerAMG,
+// Section 2.4); on the uniform lattice the geometric counterpart needs no
+// setup beyond summing reaction coefficients.  Level l+1 halves every extent
+// (ceil); its site owns the existing children 2I + {0,1}^3.  Coupling
+// c_{l+1} = 2 c_l (the Laplacian at twice the spacing, scaled by the 8x
+// volume); reaction a_{l+1} = sum of the children's a_l; diagonal
+// d_l = c_l n_l + a_l with n_l the in-box neighbour count (Neumann).
+// Restriction sums over the children, prolongation copies to them, the
+// smoother is weighted Jacobi (one sweep before and one after the coarse
+// correction, MG_NU_COARSE sweeps on the coarsest level), so M is symmetric.
+//
+// Level 0 is the solver's padded field layout (replicate 0): rhs = r,
+// iterate = mg_t0, diagonal = d; coarser levels are dense arrays.  Levels of
+// at most MG_SMALL_SITES sites run inside one block (block barriers between
+// sweeps).  The last kernel, the post-smoothing sweep on level 0, also forms
+// rho = r.z with the fixed-order reductions of the CG passes and sets beta.
+
+#include "hca_internal.cuh"
+#include "row_ops.cuh"
+
+namespace hca {
+namespace {
+
+constexpr int kMgThreads = 256;
+constexpr int kSmallThreads = 1024;
+
+template <typename T>
+struct View {
+  int nx, ny, nz;
+  long long off, sy, sz;
+  T *x, *t, *rhs, *d;
+  T c;
+  __device__ __forceinline__ long long n() const { return (long long)nx * ny * nz; }
+  __device__ __forceinline__ long long at(int X, int Y, int Z) const { return off + X + sy * Y + sz * Z; }
+  __device__ __forceinline__ void coords(long long s, int& X, int& Y, int& Z) const {
+    X = (int)(s % nx);
+    Y = (int)((s / nx) % ny);
+    Z = (int)(s / ((long long)nx * ny));
+  }
+  __device__ __forceinline__ int nbcount(int X, int Y, int Z) const {
+    return (X > 0) + (X < nx - 1) + (Y > 0) + (Y < ny - 1) + (Z > 0) + (Z < nz - 1);
+  }
+  // (A u)_e
+  __device__ __forceinline__ T apply(const T* __restrict__ u, int X, int Y, int Z, long long e) const {
+    T nb = T(0);
+    if (X > 0) nb += u[e - 1];
+    if (X < nx - 1) nb += u[e + 1];
+    if (Y > 0) nb += u[e - sy];
+    if (Y < ny - 1) nb += u[e + sy];
+    if (Z > 0) nb += u[e - sz];
+    if (Z < nz - 1) nb += u[e + sz];
+    return d[e] * u[e] - c * nb;
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ View<T> view(const Ctx& c, int which, int l) {
+  const RepDesc& rd = c.reps[0];
+  View<T> v;
+  const T c0 = (T)op_coupling(rd, which);
+  if (l == 0) {
+    v.nx = rd.nx;
+    v.ny = rd.ny;
+    v.nz = rd.nz;
+    v.off = rd.off;
+    v.sy = rd.nxp;
+    v.sz = (long long)rd.nxp * rd.ny;
+    v.x = (T*)c.mg_t0;
+    v.t = (T*)c.mg_t0;   // level 0 prolongs in place
+    v.rhs = (T*)c.r;
+    v.d = (T*)c.d;
+    v.c = c0;
+    return v;
+  }
+  const MGLevel& L = ((const MGLevel*)c.mg_lv)[l];
+  v.nx = L.nx;
+  v.ny = L.ny;
+  v.nz = L.nz;
+  v.off = 0;
+  v.sy = L.nx;
+  v.sz = (long long)L.nx * L.ny;
+  v.x = (T*)L.x;
+  v.t = (T*)L.t;
+  v.rhs = (T*)L.rhs;
+  v.d = (T*)L.d;
+  v.c = c0 * (T)L.cscale;
+  return v;
+}
+
+// ------------------------------------------------------ per-site steps --
+// d_C(I) = c_C n_C(I) + sum over children of max(0, d_F - c_F n_F)
+template <typename T>
+__device__ void coarse_diag(const View<T>& F, const View<T>& C, long long s0, long long step) {
+  for (long long S = s0; S < C.n(); S += step) {
+    int X, Y, Z;
+    C.coords(S, X, Y, Z);
+    double a = 0.0;
+    for (int k = 0; k < 8; ++k) {
+      const int x = 2 * X + (k & 1), y = 2 * Y + ((k >> 1) & 1), z = 2 * Z + (k >> 2);
+      if (x < F.nx && y < F.ny && z < F.nz)
+        a += fmax(0.0, (double)F.d[F.at(x, y, z)] - (double)F.c * F.nbcount(x, y, z));
+    }
+    C.d[C.at(X, Y, Z)] = (T)((double)C.c * C.nbcount(X, Y, Z) + a);
+  }
+}
+
+// x = omega rhs / d
+template <typename T>
+__device__ void sweep_first(const View<T>& V, long long s0, long long step) {
+  for (long long s = s0; s < V.n(); s += step) {
+    int X, Y, Z;
+    V.coords(s, X, Y, Z);
+    const long long e = V.at(X, Y, Z);
+    const T d = V.d[e];
+    V.x[e] = d != T(0) ? (T)MG_OMEGA * V.rhs[e] / d : T(0);
+  }
+}
+
+// dst = src + omega (rhs - A src) / d
+template <typename T>
+__device__ void sweep(const View<T>& V, const T* __restrict__ src, T* __restrict__ dst, long long s0, long long step) {
+  for (long long s = s0; s < V.n(); s += step) {
+    int X, Y, Z;
+    V.coords(s, X, Y, Z);
+    const long long e = V.at(X, Y, Z);
+    const T d = V.d[e];
+    const T r = V.rhs[e] - V.apply(src, X, Y, Z, e);
+    dst[e] = d != T(0) ? src[e] + (T)MG_OMEGA * r / d : T(0);
+  }
+}
+
+// rhs_C(I) = sum over children of (rhs_F - A_F x_F)
+template <typename T>
+__device__ void restrict_residual(const View<T>& F, const View<T>& C, long long s0, long long step) {
+  for (long long S = s0; S < C.n(); S += step) {
+    int X, Y, Z;
+    C.coords(S, X, Y, Z);
+    T acc = T(0);
+    for (int k = 0; k < 8; ++k) {
+      const int x = 2 * X + (k & 1), y = 2 * Y + ((k >> 1) & 1), z = 2 * Z + (k >> 2);
+      if (x < F.nx && y < F.ny && z < F.nz) {
+        const long long e = F.at(x, y, z);
+        acc += F.rhs[e] - F.apply(F.x, x, y, z, e);
+      }
+    }
+    C.rhs[C.at(X, Y, Z)] = acc;
+  }
+}
+
+// t_F = x_F + P x_C
+template <typename T>
+__device__ void prolong(const View<T>& F, const View<T>& C, long long s0, long long step) {
+  for (long long s = s0; s < F.n(); s += step) {
+    int X, Y, Z;
+    F.coords(s, X, Y, Z);
+    const long long e = F.at(X, Y, Z);
+    F.t[e] = F.x[e] + C.x[C.at(X >> 1, Y >> 1, Z >> 1)];
+  }
+}
+
+#define HCA_GRID_STRIDE (blockIdx.x * (long long)blockDim.x + threadIdx.x), ((long long)gridDim.x * blockDim.x)
+
+// ------------------------------------------------------- grid kernels ---
+template <typename T>
+__global__ void __launch_bounds__(kMgThreads) k_mg_diag(Ctx c, int which, int l) {
+  HCA_COUNT_KERNEL(c);
+  coarse_diag<T>(view<T>(c, which, l - 1), view<T>(c, which, l), HCA_GRID_STRIDE);
+}
+
+// level 0, first sweep: scale r on the first application of a rescaled inner
+// solve (the defect-correction residual is stored unscaled), then t0 = omega r / d
+template <typename T>
+__global__ void __launch_bounds__(kMgThreads) k_mg_first0(Ctx c, int which) {
+  HCA_COUNT_KERNEL(c);
+  const RepSolve sv = c.solve[0];
+  const View<T> V = view<T>(c, which, 0);
+  const T s = sv.iters == 0 ? (T)sv.scale : T(1);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < V.n(); q += (long long)gridDim.x * blockDim.x) {
+    int X, Y, Z;
+    V.coords(q, X, Y, Z);
+    const long long e = V.at(X, Y, Z);
+    T r = V.rhs[e];
+    if (s != T(1)) {
+      r *= s;
+      V.rhs[e] = r;
+    }
+    const T d = V.d[e];
+    V.x[e] = d != T(0) ? (T)MG_OMEGA * r / d : T(0);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kMgThreads) k_mg_first(Ctx c, int which, int l) {
+  HCA_COUNT_KERNEL(c);
+  sweep_first<T>(view<T>(c, which, l), HCA_GRID_STRIDE);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kMgThreads) k_mg_sweep(Ctx c, int which, int l, const T* src, T* dst) {
+  HCA_COUNT_KERNEL(c);
+  sweep<T>(view<T>(c, which, l), src, dst, HCA_GRID_STRIDE);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kMgThreads) k_mg_restrict(Ctx c, int which, int l) {
+  HCA_COUNT_KERNEL(c);
+  restrict_residual<T>(view<T>(c, which, l), view<T>(c, which, l + 1), HCA_GRID_STRIDE);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kMgThreads) k_mg_prolong(Ctx c, int which, int l) {
+  HCA_COUNT_KERNEL(c);
+  prolong<T>(view<T>(c, which, l), view<T>(c, which, l + 1), HCA_GRID_STRIDE);
+}
+
+// The whole sub-cycle of levels l0 .. nlev-1 in one block.
+template <typename T>
+__global__ void __launch_bounds__(kSmallThreads) k_mg_small(Ctx c, int which, int l0) {
+  HCA_COUNT_KERNEL(c);
+  const int last = c.mg_nlev - 1;
+  const long long s0 = threadIdx.x, st = blockDim.x;
+  for (int l = l0; l < last; ++l) {
+    const View<T> V = view<T>(c, which, l);
+    sweep_first<T>(V, s0, st);
+    __syncthreads();
+    restrict_residual<T>(V, view<T>(c, which, l + 1), s0, st);
+    __syncthreads();
+  }
+  {
+    const View<T> V = view<T>(c, which, last);
+    sweep_first<T>(V, s0, st);
+    __syncthreads();
+    for (int k = 1; k < MG_NU_COARSE; ++k) {
+      const bool odd = k & 1;
+      sweep<T>(V, odd ? V.x : V.t, odd ? V.t : V.x, s0, st);
+      __syncthreads();
+    }
+    if ((MG_NU_COARSE & 1) == 0) {   // the last sweep wrote t
+      for (long long s = s0; s < V.n(); s += st) V.x[s] = V.t[s];
+      __syncthreads();
+    }
+  }
+  for (int l = last - 1; l >= l0; --l) {
+    const View<T> V = view<T>(c, which, l);
+    prolong<T>(V, view<T>(c, which, l + 1), s0, st);
+    __syncthreads();
+    sweep<T>(V, V.t, V.x, s0, st);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------ level-0 post-smoothing + rho --
+// z = t0 + omega (r - A t0) / d over the chunk's rows; rho = r.z (fixed-order
+// sums); beta = rho / rho_old (0 on the first application of a solve).
+template <typename T>
+__global__ void __launch_bounds__(512) k_mg_post0(Ctx c, int which, const T* __restrict__ src) {
+  HCA_COUNT_KERNEL(c);
+  const int2 ch = c.chunks[blockIdx.x];
+  const RepDesc& rd = c.reps[ch.x];
+  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const T* __restrict__ rr = (const T*)c.r;
+  const T* __restrict__ dd = (const T*)c.d;
+  T* __restrict__ zz = (T*)c.z;
+  const T cpl = (T)op_coupling(rd, which);
+  const T om = (T)MG_OMEGA;
+  const RowIter it = row_iter(rd);
+  for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
+    const int rl = rbase + it.sub;
+    const bool row_ok = rl < nrows;
+    const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
+    double acc[NDOT] = {0.0, 0.0, 0.0};
+    T carry = T(0);
+    for (int itn = 0; itn < it.niter; ++itn) {
+      const int g = itn * it.lpr + it.sl;
+      const bool gok = row_ok && g < rd.gpr;
+      const long long e = geo.base + 4LL * g;
+      const V4<T> U = ld4_if(src + e, gok);
+      const V4<T> ym = ld4_if(src + e - geo.sy, gok && geo.ym);
+      const V4<T> yp = ld4_if(src + e + geo.sy, gok && geo.yp);
+      const V4<T> zm = ld4_if(src + e - geo.sz, gok && geo.zm);
+      const V4<T> zp = ld4_if(src + e + geo.sz, gok && geo.zp);
+      const V4<T> R = ld4_if(rr + e, gok);
+      const V4<T> D = ld4_if(dd + e, gok);
+      T left, right;
+      x_neighbours(U, g, rd.gpr, it.sl, it.lpr, gok, carry, left, right, [&] { return src[e + 4]; });
+      if (gok) {
+        V4<T> Zo;
+        double rz = 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          Zo.a[k] = T(0);
+          if (4 * g + k < rd.nx && D.a[k] != T(0)) {
+            const T q = D.a[k] * U.a[k] - cpl * nb_sum(U, k, left, right, ym, yp, zm, zp);
+            Zo.a[k] = U.a[k] + om * (R.a[k] - q) / D.a[k];
+            rz += (double)R.a[k] * (double)Zo.a[k];
+          }
+        }
+        st4(zz + e, Zo);
+        acc[0] += rz;
+      }
+    }
+    store_row(c, blockIdx.x, rl, row_ok, it.sl, it.lpr, acc, 1);
+  }
+  warp_epilogue(c, 1, blockIdx.x, [&](int r, const double* s1) -> int {
+    RepSolve& s = c.solve[r];
+    if (!s.active) return 0;
+    if (!(s1[0] > 0.0) || !isfinite(s1[0])) {
+      if (!isfinite(s1[0])) c.sync->error = 1;
+      s.active = 0;
+      return 0;
+    }
+    s.beta = s.iters == 0 ? 0.0 : s1[0] / s.rho;
+    s.rho = s1[0];
+    return 1;
+  });
+}
+
+int grid_for(long long n) {
+  const long long b = (n + kMgThreads - 1) / kMgThreads;
+  return (int)std::max(1LL, std::min(b, 152LL * 16));
+}
+
+template <typename T>
+void vcycle_t(const Ctx& c, int which, const MGHost& H) {
+  cudaStream_t s = c.stream;
+  const int nlev = H.nlev;
+  T* t0 = (T*)c.mg_t0;
+  T* z = (T*)c.z;
+  const long long n0 = H.n0;
+  k_mg_first0<T><<<grid_for(n0), kMgThreads, 0, s>>>(c, which);
+  if (nlev == 1) {
+    // the lattice is the coarsest level: MG_NU_COARSE sweeps, the last one in post0
+    for (int k = 1; k < MG_NU_COARSE - 1; ++k) {
+      const bool odd = k & 1;
+      k_mg_sweep<T><<<grid_for(n0), kMgThreads, 0, s>>>(c, which, 0, odd ? t0 : z, odd ? z : t0);
+    }
+    const T* src = ((MG_NU_COARSE - 2) & 1) ? z : t0;
+    k_mg_post0<T><<<c.n_chunks, c.threads, 0, s>>>(c, which, src);
+    return;
+  }
+  k_mg_restrict<T><<<grid_for(H.lv[1].n), kMgThreads, 0, s>>>(c, which, 0);
+  for (int l = 1; l < H.small; ++l) {
+    k_mg_first<T><<<grid_for(H.lv[l].n), kMgThreads, 0, s>>>(c, which, l);
+    k_mg_restrict<T><<<grid_for(H.lv[l + 1].n), kMgThreads, 0, s>>>(c, which, l);
+  }
+  k_mg_small<T><<<1, kSmallThreads, 0, s>>>(c, which, H.small);
+  for (int l = H.small - 1; l >= 1; --l) {
+    k_mg_prolong<T><<<grid_for(H.lv[l].n), kMgThreads, 0, s>>>(c, which, l);
+    k_mg_sweep<T><<<grid_for(H.lv[l].n), kMgThreads, 0, s>>>(c, which, l, (const T*)H.lv[l].t, (T*)H.lv[l].x);
+  }
+  k_mg_prolong<T><<<grid_for(n0), kMgThreads, 0, s>>>(c, which, 0);
+  k_mg_post0<T><<<c.n_chunks, c.threads, 0, s>>>(c, which, t0);
+}
+
+template <typename T>
+void mg_setup_t(const Ctx& c, int which, const MGHost& H) {
+  for (int l = 1; l < H.nlev; ++l) k_mg_diag<T><<<grid_for(H.lv[l].n), kMgThreads, 0, c.stream>>>(c, which, l);
+}
+
+}  // namespace
+
+void launch_mg_setup(const Ctx& c, int which, bool fp64, const MGHost& H) {
+  if (fp64) mg_setup_t<double>(c, which, H);
+  else mg_setup_t<float>(c, which, H);
+}
+
+void launch_vcycle(const Ctx& c, int which, bool fp64, const MGHost& H) {
+  if (fp64) vcycle_t<double>(c, which, H);
+  else vcycle_t<float>(c, which, H);
+}
+
+}  // namespace hca

@@ -23,44 +23,10 @@
 // overwritten); a parity bit in device memory, flipped by pass B, names the
 // current buffer, so the same two kernels form the body of a graph loop.
 #include "hca_internal.cuh"
+#include "row_ops.cuh"
 
 namespace hca {
 namespace {
-
-constexpr unsigned FULL = 0xffffffffu;
-
-template <typename T>
-__device__ __forceinline__ V4<T> ld4_if(const T* p, bool ok) {
-  return ok ? ld4(p) : zero4<T>();
-}
-
-template <typename T>
-__device__ __forceinline__ T sel(const V4<T>& v, int k) {
-  return v.a[k];
-}
-
-// Neighbours of a 4-site group along x.  `v` is this lane's group; lanes of a
-// row segment hold consecutive groups.  carry holds the last site of the
-// previous iteration's last lane.  right_at() loads the site after the group
-// for the segment's last lane.
-template <typename T, class RightAt>
-__device__ __forceinline__ void x_neighbours(const V4<T>& v, int g, int gpr, int sl, int lpr, bool gok,
-                                             T& carry, T& left, T& right, RightAt right_at) {
-  const T up = __shfl_up_sync(FULL, v.a[3], 1, lpr);
-  const T dn = __shfl_down_sync(FULL, v.a[0], 1, lpr);
-  left = sl > 0 ? up : (g > 0 ? carry : T(0));
-  if (sl < lpr - 1) right = dn;
-  else right = (gok && g + 1 < gpr) ? right_at() : T(0);
-  carry = __shfl_sync(FULL, v.a[3], lpr - 1, lpr);
-}
-
-template <typename T>
-__device__ __forceinline__ T nb_sum(const V4<T>& v, int k, T left, T right, const V4<T>& ym, const V4<T>& yp,
-                                    const V4<T>& zm, const V4<T>& zp) {
-  const T l = k == 0 ? left : v.a[k - 1];
-  const T r = k == 3 ? right : v.a[k + 1];
-  return ((l + r) + (ym.a[k] + yp.a[k])) + (zm.a[k] + zp.a[k]);
-}
 
 // Reaction coefficient a of the operator at one site (d = c n + a).
 template <typename T, int KIND>
@@ -93,22 +59,6 @@ __device__ __forceinline__ T diag_site(const RepDesc& rd, int which, int n_nb, u
     if (is_cancer(s)) a += (T)rd.uptake[dd];
   }
   return cpl * (T)n_nb + a;
-}
-
-struct RowIter {
-  int warp, lane, lpr, rpw, sub, sl, nw, niter;
-};
-__device__ __forceinline__ RowIter row_iter(const RepDesc& rd) {
-  RowIter it;
-  it.warp = threadIdx.x >> 5;
-  it.lane = threadIdx.x & 31;
-  it.lpr = rd.lpr;
-  it.rpw = 32 / rd.lpr;
-  it.sub = it.lane / rd.lpr;
-  it.sl = it.lane % rd.lpr;
-  it.nw = blockDim.x >> 5;
-  it.niter = (rd.gpr + rd.lpr - 1) / rd.lpr;
-  return it;
 }
 
 // ------------------------------------------------------------------ setup --
@@ -161,7 +111,7 @@ __global__ void __launch_bounds__(512) k_setup(Ctx c, int which, CondArg cnd) {
         V4<T> PF = zero4<T>();
         if (KIND == 1) PF = ld4(perf + e);
         const V4<T> LG = (KIND == 0 && c.lag) ? ld4((const T*)c.lag + e) : X;
-        V4<T> D, Z, B;
+        V4<T> D, Z, B, RR = zero4<T>();
         T g_rho = 0, g_rr = 0, g_bb = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -173,6 +123,7 @@ __global__ void __launch_bounds__(512) k_setup(Ctx c, int which, CondArg cnd) {
             if (KIND == 0) bk = is_vessel(s) ? bvessel : T(0);
             else bk = X.a[k] * inv_dt + (is_vessel(s) ? (T)rd.kappa[which - 1] * PF.a[k] * G0 : T(0));
             const T r = bk - (dk * X.a[k] - cpl * nb_sum(X, k, left, right, ym, yp, zm, zp));
+            RR.a[k] = r;
             zk = dk != T(0) ? r / dk : T(0);   // d = 0 only for an isolated, empty 1-site box
             g_rho += r * zk;
             g_rr += r * r;
@@ -184,6 +135,7 @@ __global__ void __launch_bounds__(512) k_setup(Ctx c, int which, CondArg cnd) {
         }
         st4(dd + e, D);
         st4(zz + e, Z);
+        if (c.mg) st4((T*)c.r + e, RR);
         if (KIND == 1) st4(bb + e, B);
         acc[0] += (double)g_rho;
         acc[1] += (double)g_rr;
@@ -274,7 +226,8 @@ __global__ void __maxnreg__(REGS) k_pass_a(Ctx c, int which) {
     const T beta = (T)sv.beta;
     const bool use_p = sv.beta != 0.0;
     // the first iteration of a rescaled inner solve starts from scale * z
-    const T zs = sv.iters == 0 ? (T)sv.scale : T(1);
+    // (the V-cycle scales r itself before it forms z)
+    const T zs = (sv.iters == 0 && !c.mg) ? (T)sv.scale : T(1);
     const T cpl = (T)op_coupling(rd, which);
     const RowIter it = row_iter(rd);
     for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
@@ -361,12 +314,14 @@ __global__ void __maxnreg__(REGS) k_pass_b(Ctx c, int which, void* xfield, CondA
   if (sv.active) {
     const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
     const int gpr = rd.gpr, nx = rd.nx;
-    T* __restrict__ zz = (T*)c.z;
+    // Jacobi form: z = r / d is carried; V-cycle form: r itself (already scaled)
+    const bool mg = c.mg != 0;
+    T* __restrict__ zz = (T*)(mg ? c.r : c.z);
     const T* __restrict__ pp = (const T*)(c.sync->parity ? c.p : c.p_alt);
     const T* __restrict__ dd = (const T*)c.d;
     T* __restrict__ xx = (T*)xfield;
     const T alpha = (T)sv.alpha;
-    const T zs = sv.iters == 0 ? (T)sv.scale : T(1);
+    const T zs = (sv.iters == 0 && !mg) ? (T)sv.scale : T(1);
     const T cpl = (T)op_coupling(rd, which);
     const RowIter it = row_iter(rd);
     for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
@@ -403,10 +358,15 @@ __global__ void __maxnreg__(REGS) k_pass_b(Ctx c, int which, void* xfield, CondA
             if (4 * g + k < nx) {
               const T q = D.a[k] * P.a[k] - cpl * nb_sum(P, k, left, right, ym, yp, zm, zp);
               X.a[k] += alpha * P.a[k];
-              Z.a[k] = zs * Z.a[k] - alpha * (q / D.a[k]);
-              const T r = D.a[k] * Z.a[k];
-              g_rho += r * Z.a[k];
-              g_rr += r * r;
+              if (mg) {
+                Z.a[k] -= alpha * q;
+                g_rr += Z.a[k] * Z.a[k];
+              } else {
+                Z.a[k] = zs * Z.a[k] - alpha * (q / D.a[k]);
+                const T r = D.a[k] * Z.a[k];
+                g_rho += r * Z.a[k];
+                g_rr += r * r;
+              }
             }
           }
           st4(xx + e, X);
@@ -428,8 +388,10 @@ __global__ void __maxnreg__(REGS) k_pass_b(Ctx c, int which, void* xfield, CondA
                      s.active = 0;
                      return 0;
                    }
-                   s.beta = s2[0] / s.rho;
-                   s.rho = s2[0];
+                   if (!c.mg) {   // the V-cycle form sets beta and rho after z = M r
+                     s.beta = s2[0] / s.rho;
+                     s.rho = s2[0];
+                   }
                    s.rnorm2 = s2[1];
                    const bool conv = sqrt(s2[1]) <= s.rtol * sqrt(s.bnorm2);
                    if (conv || s.iters >= s.maxit) s.active = 0;
@@ -722,7 +684,7 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
             AR = ld4(aa + e);
             B = ld4(bb + e);
           }
-          V4<float> Z;
+          V4<float> Z, R32 = zero4<float>();
           double g_rr = 0.0, g_bb = 0.0, g_rho = 0.0;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
@@ -733,12 +695,14 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
               const float r32 = (float)r;
               const float zk = D.a[k] != 0.f ? r32 / D.a[k] : 0.f;
               Z.a[k] = zk;
+              R32.a[k] = r32;
               g_rr += r * r;
               g_bb += (double)B.a[k] * (double)B.a[k];
               g_rho += r * (double)zk;     // FP64: FP32 products of a tiny residual underflow
             }
           }
           st4(zz + e, Z);
+          if (c.mg) st4((float*)c.r + e, R32);
           st4(dxv + e, zero4<float>());
           acc[0] += g_rr;
           acc[1] += g_bb;

@@ -1,0 +1,61 @@
+// Row-segment helpers shared by the kernels that sweep the padded field
+// layout: a warp's lanes hold consecutive 4-site groups of one x-row; the x
+// neighbours of a group come from lane shuffles.
+#pragma once
+
+#include "hca_internal.cuh"
+
+namespace hca {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename T>
+__device__ __forceinline__ V4<T> ld4_if(const T* p, bool ok) {
+  return ok ? ld4(p) : zero4<T>();
+}
+
+template <typename T>
+__device__ __forceinline__ T sel(const V4<T>& v, int k) {
+  return v.a[k];
+}
+
+// Neighbours of a 4-site group along x.  `v` is this lane's group; lanes of a
+// row segment hold consecutive groups.  carry holds the last site of the
+// previous iteration's last lane.  right_at() loads the site after the group
+// for the segment's last lane.
+template <typename T, class RightAt>
+__device__ __forceinline__ void x_neighbours(const V4<T>& v, int g, int gpr, int sl, int lpr, bool gok,
+                                             T& carry, T& left, T& right, RightAt right_at) {
+  const T up = __shfl_up_sync(FULL, v.a[3], 1, lpr);
+  const T dn = __shfl_down_sync(FULL, v.a[0], 1, lpr);
+  left = sl > 0 ? up : (g > 0 ? carry : T(0));
+  if (sl < lpr - 1) right = dn;
+  else right = (gok && g + 1 < gpr) ? right_at() : T(0);
+  carry = __shfl_sync(FULL, v.a[3], lpr - 1, lpr);
+}
+
+template <typename T>
+__device__ __forceinline__ T nb_sum(const V4<T>& v, int k, T left, T right, const V4<T>& ym, const V4<T>& yp,
+                                    const V4<T>& zm, const V4<T>& zp) {
+  const T l = k == 0 ? left : v.a[k - 1];
+  const T r = k == 3 ? right : v.a[k + 1];
+  return ((l + r) + (ym.a[k] + yp.a[k])) + (zm.a[k] + zp.a[k]);
+}
+
+struct RowIter {
+  int warp, lane, lpr, rpw, sub, sl, nw, niter;
+};
+__device__ __forceinline__ RowIter row_iter(const RepDesc& rd) {
+  RowIter it;
+  it.warp = threadIdx.x >> 5;
+  it.lane = threadIdx.x & 31;
+  it.lpr = rd.lpr;
+  it.rpw = 32 / rd.lpr;
+  it.sub = it.lane / rd.lpr;
+  it.sl = it.lane % rd.lpr;
+  it.nw = blockDim.x >> 5;
+  it.niter = (rd.gpr + rd.lpr - 1) / rd.lpr;
+  return it;
+}
+
+}  // namespace hca

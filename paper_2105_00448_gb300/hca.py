@@ -32,6 +32,8 @@ HCA_FP32 = 1
 HCA_WS_PREV = 0
 HCA_WS_LEARNED = 1
 HCA_WS_LEARNED_ALWAYS = 2
+HCA_PC_JACOBI = 0
+HCA_PC_MG = 1
 
 EMPTY, PROLIF, QUIESC, DEAD, VESSEL, STROMA = range(6)
 
@@ -76,7 +78,8 @@ class hca_config(ctypes.Structure):
         ("k2", ctypes.c_double), ("k2p", ctypes.c_double), ("k2pp", ctypes.c_double),
         ("J5", ctypes.c_double), ("K_V", ctypes.c_double),
         ("rtol_inner", ctypes.c_double), ("max_outer", ctypes.c_int32),
-        ("warm_start", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
+        ("warm_start", ctypes.c_int32), ("preconditioner", ctypes.c_int32),
+        ("threads_per_block", ctypes.c_int32), ("pad2", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -109,8 +112,8 @@ class hca_stats(ctypes.Structure):
         return d
 
 
-NKCLASS = 8
-KCLASS_NAMES = ("setup", "pass_a", "pass_b", "residual", "ode", "ca_compact", "ca_colour", "other")
+NKCLASS = 9
+KCLASS_NAMES = ("setup", "pass_a", "pass_b", "residual", "ode", "ca_compact", "ca_colour", "other", "mg")
 
 
 class hca_profile(ctypes.Structure):
@@ -124,7 +127,7 @@ class hca_profile(ctypes.Structure):
 EXPORTS = [
     "hca_config_default", "hca_create", "hca_create_batch", "hca_step", "hca_stage",
     "hca_read_fields", "hca_write_fields", "hca_read_states", "hca_write_states",
-    "hca_set_step", "hca_get_stats", "hca_apply_operator", "hca_philox_uniforms",
+    "hca_set_step", "hca_get_stats", "hca_apply_operator", "hca_apply_preconditioner", "hca_philox_uniforms",
     "hca_sync", "hca_get_shape", "hca_launch_count", "hca_profile_enable", "hca_get_profile",
     "hca_o2_residual_noalloc", "hca_destroy", "hca_status_string",
     "hca_net_param_count", "hca_net_create", "hca_net_set_params", "hca_net_get_params", "hca_net_forward",
@@ -178,6 +181,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "hca_set_step": (ctypes.c_int, [P, I64]),
         "hca_get_stats": (ctypes.c_int, [P, I32, ctypes.POINTER(hca_stats)]),
         "hca_apply_operator": (ctypes.c_int, [P, I32, I32, P, P, I32]),
+        "hca_apply_preconditioner": (ctypes.c_int, [P, I32, I32, P, P, I32]),
         "hca_philox_uniforms": (ctypes.c_int, [U64, U64, I64, U32, U32, P, I32]),
         "hca_sync": (ctypes.c_int, [P]),
         "hca_get_shape": (ctypes.c_int, [P, I32, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)]),
@@ -335,6 +339,14 @@ def hca_apply_operator(h, rep: int, which: int, u, out) -> None:
     if du != do or nu != no:
         raise ValueError("u and out must match in size and location")
     _check(load().hca_apply_operator(h, rep, which, pu, po, du), "hca_apply_operator")
+
+
+def hca_apply_preconditioner(h, rep: int, which: int, r, z) -> None:
+    pr, nr, dr = _ptr(r)
+    pz, nz, dz = _ptr(z)
+    if dr != dz or nr != nz:
+        raise ValueError("r and z must match in size and location")
+    _check(load().hca_apply_preconditioner(h, rep, which, pr, pz, dr), "hca_apply_preconditioner")
 
 
 def hca_philox_uniforms(seed: int, site_begin: int, n: int, step: int, purpose: int, dst=None):
@@ -570,6 +582,12 @@ class Sim:
         out = np.empty_like(u)
         hca_apply_operator(self.handle, rep, which, u, out)
         return out
+
+    def apply_preconditioner(self, which: int, r, rep: int = 0) -> np.ndarray:
+        r = np.ascontiguousarray(np.asarray(r, dtype=self.dtype).reshape(self.shape(rep)))
+        z = np.empty_like(r)
+        hca_apply_preconditioner(self.handle, rep, which, r, z)
+        return z
 
     def set_step(self, n: int) -> None:
         hca_set_step(self.handle, n)

@@ -1,0 +1,104 @@
+"""Pins of the FP64 multigrid oracle (oracle/multigrid.py): transfer
+adjointness, symmetry and definiteness of the V-cycle, the coarsest-level
+sweeps against their closed-form matrix polynomial, and MG-preconditioned CG
+against a dense direct solve and against Jacobi-preconditioned CG."""
+
+import numpy as np
+import pytest
+
+from oracle import multigrid as MG
+from oracle import pcg as PCG
+from oracle import stencil as S
+
+
+def dense(op, shape):
+    n = int(np.prod(shape))
+    M = np.zeros((n, n))
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        M[:, i] = op(e.reshape(shape)).reshape(-1)
+    return M
+
+
+def test_transfers_are_adjoint_on_odd_lattices(rng):
+    u = rng.standard_normal((5, 6, 7))
+    v = rng.standard_normal(MG.coarse_shape(u.shape))
+    assert MG.coarse_shape((5, 6, 7)) == (3, 3, 4)
+    assert np.isclose(np.sum(MG.restrict(u) * v), np.sum(u * MG.prolong(v, u.shape)))
+    # restriction sums, so it preserves the total
+    assert np.isclose(MG.restrict(u).sum(), u.sum())
+
+
+def test_coarse_operator_coefficients():
+    a = np.full((4, 4, 4), 0.5)
+    lv = MG.hierarchy(3.0, a)
+    assert len(lv) == 1                       # 64 sites <= MIN_SITES: one level
+    a = np.full((16, 16, 16), 0.5)
+    lv = MG.hierarchy(3.0, a)
+    assert [l.a.shape for l in lv] == [(16, 16, 16), (8, 8, 8)]
+    assert lv[1].c == 6.0 and np.all(lv[1].a == 4.0)
+
+
+@pytest.fixture
+def small_levels(monkeypatch):
+    monkeypatch.setattr(MG, "MIN_SITES", 8)
+
+
+def test_vcycle_is_symmetric_positive_definite(rng, small_levels):
+    shape = (5, 6, 7)
+    a = rng.uniform(0.0, 3.0, shape) * (rng.random(shape) < 0.5) + 0.01
+    levels = MG.hierarchy(2.0, a)
+    assert len(levels) >= 3
+    M = dense(lambda r: MG.vcycle(levels, r), shape)
+    assert np.allclose(M, M.T, atol=1e-12 * np.abs(M).max())
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0.0
+
+
+def test_single_level_is_the_jacobi_polynomial(rng):
+    shape = (3, 4, 5)
+    a = rng.uniform(0.1, 2.0, shape)
+    levels = MG.hierarchy(1.5, a)
+    assert len(levels) == 1
+    A = dense(levels[0].apply, shape)
+    Dinv = np.diag(1.0 / levels[0].d.reshape(-1))
+    G = np.eye(A.shape[0]) - MG.OMEGA * Dinv @ A
+    # M = sum_{k < nu} G^k omega D^-1
+    M = np.zeros_like(A)
+    Gk = np.eye(A.shape[0])
+    for _ in range(MG.NU_COARSE):
+        M += Gk @ (MG.OMEGA * Dinv)
+        Gk = Gk @ G
+    r = rng.standard_normal(shape)
+    assert np.allclose(MG.vcycle(levels, r).reshape(-1), M @ r.reshape(-1), rtol=1e-12, atol=1e-14)
+
+
+def _drug_like(shape, rng):
+    """Implicit-Euler drug operator: c = D/dx^2 = 96, a = 1/dt + psi (+ vessel exchange)."""
+    c = 9.6e3 / 100.0
+    a = np.full(shape, 1.0 / 60.0 + 0.01)
+    vessel = rng.random(shape) < 0.1
+    a[vessel] += 2.0 * rng.uniform(0.5, 1.5, vessel.sum())
+    b = rng.uniform(0.0, 1.0, shape) / 60.0 + np.where(vessel, 2.0, 0.0)
+    return c, a, b
+
+
+def test_mg_pcg_matches_direct_solve(rng, small_levels):
+    shape = (6, 7, 9)
+    c, a, b = _drug_like(shape, rng)
+    x, info = MG.mg_pcg(c, a, b, np.zeros(shape), 1e-12, 500)
+    A = dense(lambda u: c * S.laplacian_sum(u) + a * u, shape)
+    xs = np.linalg.solve(A, b.reshape(-1)).reshape(shape)
+    assert info.converged
+    assert np.max(np.abs(x - xs)) <= 1e-8 * np.max(np.abs(xs))
+
+
+def test_mg_pcg_needs_far_fewer_iterations_than_jacobi(rng):
+    shape = (32, 32, 32)
+    c, a, b = _drug_like(shape, rng)
+    x_mg, i_mg = MG.mg_pcg(c, a, b, np.zeros(shape), 1e-8, 2000)
+    d = S.jacobi_diagonal(shape, c, a)
+    x_j, i_j = PCG.pcg(lambda u: c * S.laplacian_sum(u) + a * u, b, np.zeros(shape), d, 1e-8, 5000)
+    assert i_mg.converged and i_j.converged
+    assert i_mg.iterations * 5 < i_j.iterations
+    assert np.max(np.abs(x_mg - x_j)) <= 1e-6 * np.max(np.abs(x_j))
