@@ -4,7 +4,8 @@
 Workload (one step = oxygen solve + two drug solves + cell ODEs + CA sweep):
 256^3 lattice, FP32 fields with FP64 reductions, synthetic maps from seeded
 Gaussian random fields (correlation length 8 sites, cell density 0.4, vessel
-density 0.12), bolus every 21 steps, CG to 1e-8 relative residual (FP64-measured, defect correction).
+density 0.12), bolus every 21 steps, CG to 1e-8 relative residual (FP64-measured, defect correction),
+each CG iteration preconditioned by one geometric-multigrid V-cycle.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -36,16 +37,23 @@ METRIC = "lattice site-steps/s at 256^3 coupled"
 N_EDGE = 256
 SAMPLE_EDGE = 64          # CPU sample lattice
 WORKLOAD = dict(precision="f32", n_drugs=2, seed=1, rtol_o2=1e-8, rtol_drug=1e-8, picard_tol=1e-6,
-                dose_interval=21)
+                dose_interval=21, preconditioner=1)     # 1 = HCA_PC_MG
 CORR_LEN = 8.0
-# algorithmic HBM bytes per site of each CG pass (FP32; doubled for FP64):
-#   pass A reads z, p_old, d and writes p_new; pass B reads p, d, x, z and writes x, z
-BYTES_PER_SITE = {"pass_a": 16, "pass_b": 24, "setup": 17, "residual": 13, "ode": 29}
+# algorithmic HBM bytes per site of each kernel class (FP32):
+#   pass A reads z, p_old, d and writes p_new; pass B reads p, d, x, r and writes x, r;
+#   defect-correction residual (later sweeps) reads x_hi, x_lo, d, a, b and writes z, dx, r;
+#   multigrid on the lattice: the first sweep + restriction reads r, omega/d, d and writes the
+#   1/8-size coarse right-hand side; the prolongation + last sweep reads r, omega/d, d and the
+#   1/8-size coarse correction and writes z; ODE reads state, K and updates phi, P, Vc
+BYTES_PER_SITE = {"pass_a": 16, "pass_b": 24, "setup": 17, "residual": 32, "ode": 29,
+                  "mg_restrict0": 12.5, "mg_post0": 16.5}
 
 
 def workload_config():
     return {"workload": f"{N_EDGE}^3 coupled HCA step (O2 quasi-steady CG + 2 implicit-Euler drug CGs + "
                         f"per-cell ODEs + 27-colour stochastic CA)",
+            "solver": "CG preconditioned by one geometric-multigrid V-cycle per iteration; FP32 inner solves "
+                      "with FP64-residual defect correction",
             "lattice": [N_EDGE] * 3, "precision": "f32 fields, f64 reductions", "n_drugs": 2,
             "cg_rtol": WORKLOAD["rtol_o2"], "maps": f"seeded GRF, correlation length {CORR_LEN:g} sites",
             "l2": "working set ~0.9 GB per replicate > 129 MB L2; no flush needed"}
@@ -138,7 +146,7 @@ def traffic_record(kernel: str):
 
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
-    for name in ("hca_internal.cuh", "pcg.cu"):
+    for name in ("hca_internal.cuh", "row_ops.cuh", "pcg.cu", "mg.cu"):
         with open(os.path.join(ROOT, "paper_2105_00448_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -151,7 +159,10 @@ def oracle_sample(steps: int, edge: int = SAMPLE_EDGE):
     from oracle.model import OracleSim
     from synth import make_maps
 
-    cfg = Pm.Config(nx=edge, ny=edge, nz=edge, **WORKLOAD)
+    # the oracle's own solver (Jacobi-preconditioned textbook CG); the
+    # library-only settings (preconditioner) have no oracle counterpart
+    params = {k: v for k, v in WORKLOAD.items() if k in Pm.Config.__dataclass_fields__}
+    cfg = Pm.Config(nx=edge, ny=edge, nz=edge, **params)
     maps = make_maps(edge, edge, edge, corr_len=CORR_LEN, seed=WORKLOAD["seed"])
     sim = OracleSim(cfg, maps.p_cell, maps.perf, maps.p_vessel)
     times = []
@@ -252,13 +263,15 @@ def run_gpu(args):
 
     # roofline of the dominant kernel class (by summed device time)
     peak, peak_kind = measured_peak_hbm()
-    dom = max(("pass_a", "pass_b", "setup", "residual", "ode"), key=lambda k: prof[k]["ms"])
+    dom = max(BYTES_PER_SITE, key=lambda k: prof[k]["ms"])
     avg_ms = prof[dom]["ms"] / max(1, prof[dom]["launches"])
-    n_kernels_per_launch = 2 if dom == "residual" else 1
-    bytes_per_launch = BYTES_PER_SITE[dom] * sites * n_kernels_per_launch
+    bytes_per_launch = BYTES_PER_SITE[dom] * sites
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
     tr = traffic_record(dom)
-    roofline = {"bound": "hbm", "kernel": f"k_{dom}<float>", "achieved": achieved, "peak": peak,
+    kernel_names = {"pass_a": "k_pass_a<float>", "pass_b": "k_pass_b<float>", "setup": "k_setup<float>",
+                    "residual": "k_dc_residual", "ode": "k_ode<float>", "mg_restrict0": "k_mg_restrict<float> (level 0)",
+                    "mg_post0": "k_mg_post0<float, true>"}
+    roofline = {"bound": "hbm", "kernel": kernel_names[dom], "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": tr * sites if tr is not None else None,
                 "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,

@@ -194,8 +194,10 @@ typedef struct hca_handle hca_handle;
 #define HCA_KCLASS_CA_COMPACT 5 /* CA commit compaction */
 #define HCA_KCLASS_CA_COLOUR 6  /* CA colour sweeps */
 #define HCA_KCLASS_OTHER 7
-#define HCA_KCLASS_MG 8         /* multigrid V-cycle (all its kernels) */
-#define HCA_NKCLASS 9
+#define HCA_KCLASS_MG 8         /* multigrid: coarse levels, r scaling, level diagonals */
+#define HCA_KCLASS_MG_RESTRICT0 9 /* multigrid: first sweep + restriction on the lattice */
+#define HCA_KCLASS_MG_POST0 10  /* multigrid: prolongation + last sweep on the lattice, r.z */
+#define HCA_NKCLASS 11
 
 typedef struct hca_profile {
   int64_t launches[HCA_NKCLASS];

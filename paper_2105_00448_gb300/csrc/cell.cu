@@ -110,12 +110,18 @@ __global__ void __launch_bounds__(512) k_ode(Ctx c) {
       const T lam = k1p * Kk / (Kp53 + Kk);
       const T decay = k2p * Kk / (KV + Kk);
       const T P0 = P.a[k];
+      // P(s) = P0 e^{-lam s} + k1 (1 - e^{-lam s}) / lam = P0 + expm1(-lam s) (P0 - k1 / lam):
+      // one transcendental per stage time; the end of a substep is the start
+      // of the next, so two evaluations per substep
+      const bool has_lam = lam != T(0);
+      const T A0 = has_lam ? P0 - k1 / lam : T(0);
+      auto P_at = [&](T s) { return has_lam ? P0 + t_expm1(-lam * s) * A0 : P0 + k1 * s; };
       T v = V.a[k];
+      T Pa = P0;
       for (int m = 0; m < nsub; ++m) {
         const T s0 = (T)m * h;
-        const T Pa = p53_at(P0, lam, s0, k1);
-        const T Pb = p53_at(P0, lam, s0 + half, k1);
-        const T Pc = p53_at(P0, lam, s0 + h, k1);
+        const T Pb = P_at(s0 + half);
+        const T Pc = P_at(s0 + h);
         const T f1 = k2 + k2pp * Pa * v / (J5 + v) - decay * v;
         const T v2 = v + half * f1;
         const T f2 = k2 + k2pp * Pb * v2 / (J5 + v2) - decay * v2;
@@ -124,6 +130,7 @@ __global__ void __launch_bounds__(512) k_ode(Ctx c) {
         const T v4 = v + h * f3;
         const T f4 = k2 + k2pp * Pc * v4 / (J5 + v4) - decay * v4;
         v = v + sixth * (f1 + T(2) * f2 + T(2) * f3 + f4);
+        Pa = Pc;
       }
       V.a[k] = v;
       P.a[k] = p53_at(P0, lam, dt, k1);

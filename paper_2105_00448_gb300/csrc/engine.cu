@@ -32,7 +32,9 @@ void launch_ca_colour(const Ctx& c, int colour, int blocks_x, bool fp64);
 void set_pass_regs(int r);
 void set_pass_ni(int ni);
 void launch_mg_setup(const Ctx& c, int which, bool fp64, const MGHost& H);
-void launch_vcycle(const Ctx& c, int which, bool fp64, const MGHost& H);
+void launch_vcycle(const Ctx& c, int which, bool fp64, const MGHost& H, int part);
+int vcycle_launches(const MGHost& H);
+int vcycle_part_launches(const MGHost& H, int part);
 }  // namespace hca
 
 using hca::Ctx;
@@ -290,7 +292,23 @@ void pass_b(hca_handle* h, int which, void* x, hca::CondArg cnd) {
 }
 
 // z = M r (V-cycle); also sets rho and beta for the next pass A
-void vcycle(hca_handle* h, int which) { hca::launch_vcycle(h->ctx, which, h->fp64, h->mgh); }
+void vcycle(hca_handle* h, int which) { hca::launch_vcycle(h->ctx, which, h->fp64, h->mgh, -1); }
+
+// The V-cycle from the host loop: with the profiler on, its lattice-level
+// kernels are timed as classes of their own.
+int vcycle_host(hca_handle* h, int which) {
+  if (!h->prof.on) {
+    HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.launches, vcycle(h, which));
+    return HCA_OK;
+  }
+  const hca::MGHost& H = h->mgh;
+  const int cls[3] = {HCA_KCLASS_MG_RESTRICT0, HCA_KCLASS_MG, HCA_KCLASS_MG_POST0};
+  for (int part = 0; part < 3; ++part) {
+    const int n = hca::vcycle_part_launches(H, part);
+    if (n) HCA_LAUNCH(h, cls[part], n, hca::launch_vcycle(h->ctx, which, h->fp64, H, part));
+  }
+  return HCA_OK;
+}
 
 // coarse diagonals of the current operator (after its set-up stored d)
 void mg_setup(hca_handle* h, int which) { hca::launch_mg_setup(h->ctx, which, h->fp64, h->mgh); }
@@ -313,7 +331,10 @@ int pcg_iterate(hca_handle* h, int which, void* x, int predict) {
     for (int k = 0; k < n; ++k) {
       HCA_LAUNCH(h, HCA_KCLASS_PASS_A, 1, pass_a(h, which));
       HCA_LAUNCH(h, HCA_KCLASS_PASS_B, 1, pass_b(h, which, x, kNoCond));
-      if (h->mg) HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.launches, vcycle(h, which));
+      if (h->mg) {
+        const int rc = vcycle_host(h, which);
+        if (rc) return rc;
+      }
     }
     done += n;
     chunk = h->prof.on ? 1 : 4;
@@ -330,8 +351,9 @@ int solve_plain(hca_handle* h, int which) {
   void* x = which == 0 ? c.K : c.G[which - 1];
   HCA_LAUNCH(h, HCA_KCLASS_SETUP, 1, hca::launch_setup(c, which, h->fp64, kNoCond));
   if (h->mg) {
-    HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.nlev - 1, mg_setup(h, which));
-    HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.launches, vcycle(h, which));
+    HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.nlev, mg_setup(h, which));
+    const int rv = vcycle_host(h, which);
+    if (rv) return rv;
   }
   int rc = pcg_iterate(h, which, x, h->prev_inner[which][0]);
   if (rc) return rc;
@@ -353,8 +375,9 @@ int solve_dc(hca_handle* h, int which) {
     HCA_LAUNCH(h, HCA_KCLASS_RESIDUAL, 1,
                hca::launch_dc_residual(c, which, xh, xl, outer == 0, kNoCond, kNoCond));
     if (h->mg) {
-      if (outer == 0) HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.nlev - 1, mg_setup(h, which));
-      HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.launches, vcycle(h, which));
+      if (outer == 0) HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.nlev, mg_setup(h, which));
+      const int rv = vcycle_host(h, which);
+      if (rv) return rv;
     }
     HCA_TRY(cudaMemcpyAsync(h->h_pinned, &c.sync->active_count, 2 * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     HCA_TRY(cudaStreamSynchronize(c.stream));
@@ -820,6 +843,7 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
         ALLOC(L.t, es * (size_t)nn);
         ALLOC(L.rhs, es * (size_t)nn);
         ALLOC(L.d, es * (size_t)nn);
+        ALLOC(L.w, es * (size_t)nn);
         H.nlev += 1;
       }
       H.small = H.nlev - 1;
@@ -828,9 +852,10 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
           H.small = l;
           break;
         }
-      H.launches = H.nlev == 1 ? hca::MG_NU_COARSE : 5 + 4 * (H.small - 1);
+      H.launches = hca::vcycle_launches(H);
       ALLOC(c.r, fbytes);
       ALLOC(c.mg_t0, fbytes);
+      ALLOC(c.mg_w, fbytes);
       hca::MGLevel* lv_d;
       ALLOC(lv_d, sizeof(hca::MGLevel) * H.nlev);
       c.mg_lv = lv_d;
@@ -870,7 +895,7 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     }
     // zero every device array (padding sites must hold 0)
     void* zero_list[] = {c.K, c.K_lo, c.G[0], c.G[1], c.G[2], c.G_lo[0], c.G_lo[1], c.G_lo[2], c.dx,
-                         c.phi, c.P, c.Vc, c.perf, c.z, c.p, c.p_alt, c.d, c.b, c.aux, c.reac, c.r, c.mg_t0};
+                         c.phi, c.P, c.Vc, c.perf, c.z, c.p, c.p_alt, c.d, c.b, c.aux, c.reac, c.r, c.mg_t0, c.mg_w};
     for (void* p : zero_list)
       if (p && cudaMemsetAsync(p, 0, fbytes, s)) {
         rc = HCA_ERR_CUDA;
@@ -879,7 +904,7 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     if (h->mg) {
       const hca::MGHost& H = h->mgh;
       for (int l = 1; l < H.nlev; ++l) {
-        void* arr[4] = {H.lv[l].x, H.lv[l].t, H.lv[l].rhs, H.lv[l].d};
+        void* arr[5] = {H.lv[l].x, H.lv[l].t, H.lv[l].rhs, H.lv[l].d, H.lv[l].w};
         for (void* p : arr)
           if (cudaMemsetAsync(p, 0, es * (size_t)H.lv[l].n, s)) {
             rc = HCA_ERR_CUDA;
@@ -1233,7 +1258,7 @@ int hca_apply_preconditioner(hca_handle* h, int32_t rep, int32_t which, const vo
   // the set-up of a solve of `which` writes the diagonal (its other outputs
   // are rewritten by the next solve)
   HCA_LAUNCH(h, HCA_KCLASS_SETUP, 1, hca::launch_setup(c, which, h->fp64, kNoCond));
-  HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.nlev - 1, mg_setup(h, which));
+  HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.nlev, mg_setup(h, which));
   int rc = copy_field(h, rep, c.r, es, const_cast<void*>(r), false, 0);
   if (rc) return rc;
   HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.launches, vcycle(h, which));

@@ -78,7 +78,7 @@ struct RepSolve {
   int maxit;
   int outer;       // defect-correction sweeps done in this solve
   int dc_apply;    // 1: the last inner solve's correction is to be added
-  int pad[2];
+  double bb_outer; // |b|^2 of the defect-corrected system (from its first sweep)
   double scale;    // power of two applied to the inner problem (1 for plain solves)
 };
 
@@ -228,7 +228,7 @@ namespace hca {
 struct MGLevel {
   int nx, ny, nz, pad;
   long long n;
-  void *x, *t, *rhs, *d;   // iterate, second iterate, right-hand side, diagonal
+  void *x, *t, *rhs, *d, *w;   // iterate, second iterate, right-hand side, diagonal, omega / diagonal
   double cscale;            // coupling of this level / coupling of the lattice (2^level)
 };
 
@@ -270,6 +270,7 @@ struct Ctx {
   int mg_small;     // first level handled by the single-block kernel
   void* r;
   void* mg_t0;
+  void* mg_w;         // omega / d on the lattice (0 where d = 0)
   const void* mg_lv;  // device MGLevel[mg_nlev] (entry 0 unused)
   void* reac;    // FP32 scheme: reaction part a of the diagonal d = c n + a
   void* phi;
@@ -318,6 +319,28 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
   r.lo = __fadd_rn(r.lo, b.lo);
   return r;
 }
+
+// Exact product a*b = hi + lo (one FMA recovers the rounding error).
+__device__ __forceinline__ FF ff_two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return FF{p, __fmaf_rn(a, b, -p)};
+}
+
+// (x.hi + x.lo) * b to ~48 bits
+__device__ __forceinline__ FF ff_mul(FF x, float b) {
+  FF p = ff_two_prod(x.hi, b);
+  p.lo = __fmaf_rn(x.lo, b, p.lo);
+  return p;
+}
+
+// (x.hi + x.lo) * (y.hi + y.lo) to ~48 bits
+__device__ __forceinline__ FF ff_mul(FF x, FF y) {
+  FF p = ff_two_prod(x.hi, y.hi);
+  p.lo = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, p.lo));
+  return p;
+}
+
+__device__ __forceinline__ FF ff_neg(FF x) { return FF{-x.hi, -x.lo}; }
 
 // Row sum of float-float lane partials over the row's lane segment (fixed
 // xor tree), as a double.

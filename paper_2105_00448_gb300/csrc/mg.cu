@@ -31,7 +31,7 @@ template <typename T>
 struct View {
   int nx, ny, nz;
   long long off, sy, sz;
-  T *x, *t, *rhs, *d;
+  T *x, *t, *rhs, *d, *w;   // w = omega / d (0 where d = 0): the sweeps divide nowhere
   T c;
   __device__ __forceinline__ long long n() const { return (long long)nx * ny * nz; }
   __device__ __forceinline__ long long at(int X, int Y, int Z) const { return off + X + sy * Y + sz * Z; }
@@ -72,6 +72,7 @@ __device__ __forceinline__ View<T> view(const Ctx& c, int which, int l) {
     v.t = (T*)c.mg_t0;   // level 0 prolongs in place
     v.rhs = (T*)c.r;
     v.d = (T*)c.d;
+    v.w = (T*)c.mg_w;
     v.c = c0;
     return v;
   }
@@ -86,6 +87,7 @@ __device__ __forceinline__ View<T> view(const Ctx& c, int which, int l) {
   v.t = (T*)L.t;
   v.rhs = (T*)L.rhs;
   v.d = (T*)L.d;
+  v.w = (T*)L.w;
   v.c = c0 * (T)L.cscale;
   return v;
 }
@@ -103,7 +105,21 @@ __device__ void coarse_diag(const View<T>& F, const View<T>& C, long long s0, lo
       if (x < F.nx && y < F.ny && z < F.nz)
         a += fmax(0.0, (double)F.d[F.at(x, y, z)] - (double)F.c * F.nbcount(x, y, z));
     }
-    C.d[C.at(X, Y, Z)] = (T)((double)C.c * C.nbcount(X, Y, Z) + a);
+    const double dc = (double)C.c * C.nbcount(X, Y, Z) + a;
+    C.d[C.at(X, Y, Z)] = (T)dc;
+    C.w[C.at(X, Y, Z)] = dc != 0.0 ? (T)(MG_OMEGA / dc) : T(0);
+  }
+}
+
+// w = omega / d on the lattice
+template <typename T>
+__device__ void lattice_w(const View<T>& V, long long s0, long long step) {
+  for (long long s = s0; s < V.n(); s += step) {
+    int X, Y, Z;
+    V.coords(s, X, Y, Z);
+    const long long e = V.at(X, Y, Z);
+    const T d = V.d[e];
+    V.w[e] = d != T(0) ? (T)MG_OMEGA / d : T(0);
   }
 }
 
@@ -114,8 +130,7 @@ __device__ void sweep_first(const View<T>& V, long long s0, long long step) {
     int X, Y, Z;
     V.coords(s, X, Y, Z);
     const long long e = V.at(X, Y, Z);
-    const T d = V.d[e];
-    V.x[e] = d != T(0) ? (T)MG_OMEGA * V.rhs[e] / d : T(0);
+    V.x[e] = V.w[e] * V.rhs[e];
   }
 }
 
@@ -126,9 +141,8 @@ __device__ void sweep(const View<T>& V, const T* __restrict__ src, T* __restrict
     int X, Y, Z;
     V.coords(s, X, Y, Z);
     const long long e = V.at(X, Y, Z);
-    const T d = V.d[e];
     const T r = V.rhs[e] - V.apply(src, X, Y, Z, e);
-    dst[e] = d != T(0) ? src[e] + (T)MG_OMEGA * r / d : T(0);
+    dst[e] = src[e] + V.w[e] * r;
   }
 }
 
@@ -161,41 +175,100 @@ __device__ void prolong(const View<T>& F, const View<T>& C, long long s0, long l
   }
 }
 
+// First sweep from zero, evaluated where it is needed: u = omega rhs / d
+template <typename T>
+__device__ __forceinline__ T u_first(const View<T>& V, long long e) {
+  return V.w[e] * V.rhs[e];
+}
+
+// rhs_C(I) = sum over children of (rhs_F - A_F u), u = omega rhs_F / d_F
+// (the pre-smoothing sweep fused into the restriction; u is not stored)
+template <typename T>
+__device__ void restrict_fused(const View<T>& F, const View<T>& C, long long s0, long long step) {
+  for (long long S = s0; S < C.n(); S += step) {
+    int X, Y, Z;
+    C.coords(S, X, Y, Z);
+    T acc = T(0);
+    for (int k = 0; k < 8; ++k) {
+      const int x = 2 * X + (k & 1), y = 2 * Y + ((k >> 1) & 1), z = 2 * Z + (k >> 2);
+      if (x < F.nx && y < F.ny && z < F.nz) {
+        const long long e = F.at(x, y, z);
+        T nb = T(0);
+        if (x > 0) nb += u_first(F, e - 1);
+        if (x < F.nx - 1) nb += u_first(F, e + 1);
+        if (y > 0) nb += u_first(F, e - F.sy);
+        if (y < F.ny - 1) nb += u_first(F, e + F.sy);
+        if (z > 0) nb += u_first(F, e - F.sz);
+        if (z < F.nz - 1) nb += u_first(F, e + F.sz);
+        acc += F.rhs[e] - (F.d[e] * u_first(F, e) - F.c * nb);
+      }
+    }
+    C.rhs[C.at(X, Y, Z)] = acc;
+  }
+}
+
+// x_F = u + omega (rhs_F - A_F u) / d_F with u = omega rhs_F / d_F + P x_C
+// (prolongation fused into the post-smoothing sweep; u is not stored)
+template <typename T>
+__device__ void post_fused(const View<T>& F, const View<T>& C, long long s0, long long step) {
+  auto u = [&](int x, int y, int z) {
+    return u_first(F, F.at(x, y, z)) + C.x[C.at(x >> 1, y >> 1, z >> 1)];
+  };
+  for (long long s = s0; s < F.n(); s += step) {
+    int X, Y, Z;
+    F.coords(s, X, Y, Z);
+    const long long e = F.at(X, Y, Z);
+    const T d = F.d[e];
+    const T w = F.w[e];
+    T nb = T(0);
+    if (X > 0) nb += u(X - 1, Y, Z);
+    if (X < F.nx - 1) nb += u(X + 1, Y, Z);
+    if (Y > 0) nb += u(X, Y - 1, Z);
+    if (Y < F.ny - 1) nb += u(X, Y + 1, Z);
+    if (Z > 0) nb += u(X, Y, Z - 1);
+    if (Z < F.nz - 1) nb += u(X, Y, Z + 1);
+    const T uc = u(X, Y, Z);
+    F.x[e] = uc + w * (F.rhs[e] - (d * uc - F.c * nb));
+  }
+}
+
 #define HCA_GRID_STRIDE (blockIdx.x * (long long)blockDim.x + threadIdx.x), ((long long)gridDim.x * blockDim.x)
 
 // ------------------------------------------------------- grid kernels ---
+template <typename T>
+__global__ void __launch_bounds__(kMgThreads) k_mg_w0(Ctx c, int which) {
+  HCA_COUNT_KERNEL(c);
+  lattice_w<T>(view<T>(c, which, 0), HCA_GRID_STRIDE);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kMgThreads) k_mg_diag(Ctx c, int which, int l) {
   HCA_COUNT_KERNEL(c);
   coarse_diag<T>(view<T>(c, which, l - 1), view<T>(c, which, l), HCA_GRID_STRIDE);
 }
 
-// level 0, first sweep: scale r on the first application of a rescaled inner
-// solve (the defect-correction residual is stored unscaled), then t0 = omega r / d
+// The defect-correction residual is stored unscaled: on the first
+// application of a rescaled inner solve, r *= scale (elementwise, in place);
+// otherwise the kernel returns at once.
 template <typename T>
-__global__ void __launch_bounds__(kMgThreads) k_mg_first0(Ctx c, int which) {
+__global__ void __launch_bounds__(kMgThreads) k_mg_scale0(Ctx c, int which) {
   HCA_COUNT_KERNEL(c);
-  const RepSolve sv = c.solve[0];
+  const RepSolve& sv = c.solve[0];
+  if (sv.iters != 0 || sv.scale == 1.0) return;
+  const T sc = (T)sv.scale;
   const View<T> V = view<T>(c, which, 0);
-  const T s = sv.iters == 0 ? (T)sv.scale : T(1);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < V.n(); q += (long long)gridDim.x * blockDim.x) {
     int X, Y, Z;
     V.coords(q, X, Y, Z);
-    const long long e = V.at(X, Y, Z);
-    T r = V.rhs[e];
-    if (s != T(1)) {
-      r *= s;
-      V.rhs[e] = r;
-    }
-    const T d = V.d[e];
-    V.x[e] = d != T(0) ? (T)MG_OMEGA * r / d : T(0);
+    V.rhs[V.at(X, Y, Z)] *= sc;
   }
 }
 
+// level 0 as the coarsest level: t0 = omega r / d
 template <typename T>
-__global__ void __launch_bounds__(kMgThreads) k_mg_first(Ctx c, int which, int l) {
+__global__ void __launch_bounds__(kMgThreads) k_mg_first0(Ctx c, int which) {
   HCA_COUNT_KERNEL(c);
-  sweep_first<T>(view<T>(c, which, l), HCA_GRID_STRIDE);
+  sweep_first<T>(view<T>(c, which, 0), HCA_GRID_STRIDE);
 }
 
 template <typename T>
@@ -207,13 +280,13 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_sweep(Ctx c, int which, int l
 template <typename T>
 __global__ void __launch_bounds__(kMgThreads) k_mg_restrict(Ctx c, int which, int l) {
   HCA_COUNT_KERNEL(c);
-  restrict_residual<T>(view<T>(c, which, l), view<T>(c, which, l + 1), HCA_GRID_STRIDE);
+  restrict_fused<T>(view<T>(c, which, l), view<T>(c, which, l + 1), HCA_GRID_STRIDE);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kMgThreads) k_mg_prolong(Ctx c, int which, int l) {
+__global__ void __launch_bounds__(kMgThreads) k_mg_post(Ctx c, int which, int l) {
   HCA_COUNT_KERNEL(c);
-  prolong<T>(view<T>(c, which, l), view<T>(c, which, l + 1), HCA_GRID_STRIDE);
+  post_fused<T>(view<T>(c, which, l), view<T>(c, which, l + 1), HCA_GRID_STRIDE);
 }
 
 // The whole sub-cycle of levels l0 .. nlev-1 in one block.
@@ -253,9 +326,12 @@ __global__ void __launch_bounds__(kSmallThreads) k_mg_small(Ctx c, int which, in
 }
 
 // ------------------------------------------ level-0 post-smoothing + rho --
-// z = t0 + omega (r - A t0) / d over the chunk's rows; rho = r.z (fixed-order
-// sums); beta = rho / rho_old (0 on the first application of a solve).
-template <typename T>
+// z = u + omega (r - A u) / d over the chunk's rows, with u = omega r / d +
+// P x_1 (PROLONG: the first sweep and the coarse correction evaluated where
+// they are needed) or u = src (the lattice is the coarsest level);
+// rho = r.z (fixed-order sums); beta = rho / rho_old (0 on the first
+// application of a solve).
+template <typename T, bool PROLONG>
 __global__ void __launch_bounds__(512) k_mg_post0(Ctx c, int which, const T* __restrict__ src) {
   HCA_COUNT_KERNEL(c);
   const int2 ch = c.chunks[blockIdx.x];
@@ -263,29 +339,59 @@ __global__ void __launch_bounds__(512) k_mg_post0(Ctx c, int which, const T* __r
   const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
   const T* __restrict__ rr = (const T*)c.r;
   const T* __restrict__ dd = (const T*)c.d;
+  const T* __restrict__ ww = (const T*)c.mg_w;
   T* __restrict__ zz = (T*)c.z;
   const T cpl = (T)op_coupling(rd, which);
-  const T om = (T)MG_OMEGA;
+  const T* __restrict__ x1 = nullptr;
+  int nx1 = 0, ny1 = 0;
+  if (PROLONG) {
+    const MGLevel& L1 = ((const MGLevel*)c.mg_lv)[1];
+    x1 = (const T*)L1.x;
+    nx1 = L1.nx;
+    ny1 = L1.ny;
+  }
   const RowIter it = row_iter(rd);
   for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
     const int rl = rbase + it.sub;
     const bool row_ok = rl < nrows;
-    const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
+    const int j = ch.y + (row_ok ? rl : 0);
+    const RowGeo geo = row_geo(rd, j);
+    const int y = j % rd.ny, z = j / rd.ny;
     double acc[NDOT] = {0.0, 0.0, 0.0};
     T carry = T(0);
     for (int itn = 0; itn < it.niter; ++itn) {
       const int g = itn * it.lpr + it.sl;
       const bool gok = row_ok && g < rd.gpr;
       const long long e = geo.base + 4LL * g;
-      const V4<T> U = ld4_if(src + e, gok);
-      const V4<T> ym = ld4_if(src + e - geo.sy, gok && geo.ym);
-      const V4<T> yp = ld4_if(src + e + geo.sy, gok && geo.yp);
-      const V4<T> zm = ld4_if(src + e - geo.sz, gok && geo.zm);
-      const V4<T> zp = ld4_if(src + e + geo.sz, gok && geo.zp);
+      // u on the 4-site group of row (yy, zq) that starts at element er
+      auto urow = [&](long long er, bool ok, int yy, int zq) {
+        if (!PROLONG) return ld4_if(src + er, ok);
+        V4<T> u = zero4<T>();
+        if (!ok) return u;
+        const V4<T> R = ld4(rr + er), W = ld4(ww + er);
+        const long long cb = ((long long)(zq >> 1) * ny1 + (yy >> 1)) * nx1 + 2LL * g;
+        const T c0 = x1[cb];
+        const T c1 = 4 * g + 2 < rd.nx ? x1[cb + 1] : T(0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (4 * g + k < rd.nx && W.a[k] != T(0)) u.a[k] = W.a[k] * R.a[k] + (k < 2 ? c0 : c1);
+        return u;
+      };
+      const V4<T> U = urow(e, gok, y, z);
+      const V4<T> ym = urow(e - geo.sy, gok && geo.ym, y - 1, z);
+      const V4<T> yp = urow(e + geo.sy, gok && geo.yp, y + 1, z);
+      const V4<T> zm = urow(e - geo.sz, gok && geo.zm, y, z - 1);
+      const V4<T> zp = urow(e + geo.sz, gok && geo.zp, y, z + 1);
       const V4<T> R = ld4_if(rr + e, gok);
       const V4<T> D = ld4_if(dd + e, gok);
+      const V4<T> W = ld4_if(ww + e, gok);
       T left, right;
-      x_neighbours(U, g, rd.gpr, it.sl, it.lpr, gok, carry, left, right, [&] { return src[e + 4]; });
+      x_neighbours(U, g, rd.gpr, it.sl, it.lpr, gok, carry, left, right, [&] {
+        if (!PROLONG) return src[e + 4];
+        const T wn = ww[e + 4];
+        const long long cb = ((long long)(z >> 1) * ny1 + (y >> 1)) * nx1 + 2LL * g + 2;
+        return wn != T(0) ? wn * rr[e + 4] + x1[cb] : T(0);
+      });
       if (gok) {
         V4<T> Zo;
         double rz = 0.0;
@@ -294,7 +400,7 @@ __global__ void __launch_bounds__(512) k_mg_post0(Ctx c, int which, const T* __r
           Zo.a[k] = T(0);
           if (4 * g + k < rd.nx && D.a[k] != T(0)) {
             const T q = D.a[k] * U.a[k] - cpl * nb_sum(U, k, left, right, ym, yp, zm, zp);
-            Zo.a[k] = U.a[k] + om * (R.a[k] - q) / D.a[k];
+            Zo.a[k] = U.a[k] + W.a[k] * (R.a[k] - q);
             rz += (double)R.a[k] * (double)Zo.a[k];
           }
         }
@@ -323,53 +429,64 @@ int grid_for(long long n) {
   return (int)std::max(1LL, std::min(b, 152LL * 16));
 }
 
+// part: -1 = whole cycle; 0 = r scaling and the lattice's first sweep +
+// restriction; 1 = coarse levels; 2 = the lattice's prolongation + last sweep
 template <typename T>
-void vcycle_t(const Ctx& c, int which, const MGHost& H) {
+void vcycle_t(const Ctx& c, int which, const MGHost& H, int part) {
   cudaStream_t s = c.stream;
-  const int nlev = H.nlev;
   T* t0 = (T*)c.mg_t0;
   T* z = (T*)c.z;
   const long long n0 = H.n0;
-  k_mg_first0<T><<<grid_for(n0), kMgThreads, 0, s>>>(c, which);
-  if (nlev == 1) {
+  const bool all = part < 0;
+  if (H.nlev == 1) {
+    if (!all && part != 0) return;
     // the lattice is the coarsest level: MG_NU_COARSE sweeps, the last one in post0
+    k_mg_scale0<T><<<grid_for(n0), kMgThreads, 0, s>>>(c, which);
+    k_mg_first0<T><<<grid_for(n0), kMgThreads, 0, s>>>(c, which);
     for (int k = 1; k < MG_NU_COARSE - 1; ++k) {
       const bool odd = k & 1;
       k_mg_sweep<T><<<grid_for(n0), kMgThreads, 0, s>>>(c, which, 0, odd ? t0 : z, odd ? z : t0);
     }
     const T* src = ((MG_NU_COARSE - 2) & 1) ? z : t0;
-    k_mg_post0<T><<<c.n_chunks, c.threads, 0, s>>>(c, which, src);
+    k_mg_post0<T, false><<<c.n_chunks, c.threads, 0, s>>>(c, which, src);
     return;
   }
-  k_mg_restrict<T><<<grid_for(H.lv[1].n), kMgThreads, 0, s>>>(c, which, 0);
-  for (int l = 1; l < H.small; ++l) {
-    k_mg_first<T><<<grid_for(H.lv[l].n), kMgThreads, 0, s>>>(c, which, l);
-    k_mg_restrict<T><<<grid_for(H.lv[l + 1].n), kMgThreads, 0, s>>>(c, which, l);
+  if (all || part == 0) {
+    k_mg_scale0<T><<<grid_for(n0), kMgThreads, 0, s>>>(c, which);
+    k_mg_restrict<T><<<grid_for(H.lv[1].n), kMgThreads, 0, s>>>(c, which, 0);
   }
-  k_mg_small<T><<<1, kSmallThreads, 0, s>>>(c, which, H.small);
-  for (int l = H.small - 1; l >= 1; --l) {
-    k_mg_prolong<T><<<grid_for(H.lv[l].n), kMgThreads, 0, s>>>(c, which, l);
-    k_mg_sweep<T><<<grid_for(H.lv[l].n), kMgThreads, 0, s>>>(c, which, l, (const T*)H.lv[l].t, (T*)H.lv[l].x);
+  if (all || part == 1) {
+    for (int l = 1; l < H.small; ++l)
+      k_mg_restrict<T><<<grid_for(H.lv[l + 1].n), kMgThreads, 0, s>>>(c, which, l);
+    k_mg_small<T><<<1, kSmallThreads, 0, s>>>(c, which, H.small);
+    for (int l = H.small - 1; l >= 1; --l) k_mg_post<T><<<grid_for(H.lv[l].n), kMgThreads, 0, s>>>(c, which, l);
   }
-  k_mg_prolong<T><<<grid_for(n0), kMgThreads, 0, s>>>(c, which, 0);
-  k_mg_post0<T><<<c.n_chunks, c.threads, 0, s>>>(c, which, t0);
+  if (all || part == 2) k_mg_post0<T, true><<<c.n_chunks, c.threads, 0, s>>>(c, which, nullptr);
 }
 
 template <typename T>
 void mg_setup_t(const Ctx& c, int which, const MGHost& H) {
+  k_mg_w0<T><<<grid_for(H.n0), kMgThreads, 0, c.stream>>>(c, which);
   for (int l = 1; l < H.nlev; ++l) k_mg_diag<T><<<grid_for(H.lv[l].n), kMgThreads, 0, c.stream>>>(c, which, l);
 }
 
 }  // namespace
+
+int vcycle_launches(const MGHost& H) { return H.nlev == 1 ? MG_NU_COARSE + 1 : 2 * H.small + 2; }
 
 void launch_mg_setup(const Ctx& c, int which, bool fp64, const MGHost& H) {
   if (fp64) mg_setup_t<double>(c, which, H);
   else mg_setup_t<float>(c, which, H);
 }
 
-void launch_vcycle(const Ctx& c, int which, bool fp64, const MGHost& H) {
-  if (fp64) vcycle_t<double>(c, which, H);
-  else vcycle_t<float>(c, which, H);
+void launch_vcycle(const Ctx& c, int which, bool fp64, const MGHost& H, int part) {
+  if (fp64) vcycle_t<double>(c, which, H, part);
+  else vcycle_t<float>(c, which, H, part);
+}
+
+int vcycle_part_launches(const MGHost& H, int part) {
+  if (H.nlev == 1) return part == 0 ? MG_NU_COARSE + 1 : 0;
+  return part == 0 ? 2 : part == 1 ? 2 * (H.small - 1) + 1 : 1;
 }
 
 }  // namespace hca

@@ -629,31 +629,26 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
     const float G0 = KIND == 1 && first ? (float)s_G0 : 0.f;
     const float bvessel = (float)(rd.r_K * rd.K0);
     const RowIter it = row_iter(rd);
-    auto ldx = [&](long long o, bool ok) {
-      const V4<float> h = ld4_if(x_hi + o, ok), l = ld4_if(x_lo + o, ok);
-      V4<double> r;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) r.a[k] = (double)h.a[k] + (double)l.a[k];
-      return r;
-    };
+    const float cpl32 = (float)cpl;
     for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
       const int rl = rbase + it.sub;
       const bool row_ok = rl < nrows;
       const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
       double acc[NDOT] = {0.0, 0.0, 0.0};
-      double carry = 0.0;
+      float carry_h = 0.f, carry_l = 0.f;
       for (int itn = 0; itn < it.niter; ++itn) {
         const int g = itn * it.lpr + it.sl;
         const bool gok = row_ok && g < rd.gpr;
         const long long e = geo.base + 4LL * g;
-        const V4<double> X = ldx(e, gok);
-        const V4<double> ym = ldx(e - geo.sy, gok && geo.ym);
-        const V4<double> yp = ldx(e + geo.sy, gok && geo.yp);
-        const V4<double> zm = ldx(e - geo.sz, gok && geo.zm);
-        const V4<double> zp = ldx(e + geo.sz, gok && geo.zp);
-        double left, right;
-        x_neighbours(X, g, rd.gpr, it.sl, it.lpr, gok, carry, left, right,
-                     [&] { return (double)x_hi[e + 4] + (double)x_lo[e + 4]; });
+        // the two-word solution x_hi + x_lo at the group and its neighbour rows
+        const V4<float> Xh = ld4_if(x_hi + e, gok), Xl = ld4_if(x_lo + e, gok);
+        const V4<float> ymh = ld4_if(x_hi + e - geo.sy, gok && geo.ym), yml = ld4_if(x_lo + e - geo.sy, gok && geo.ym);
+        const V4<float> yph = ld4_if(x_hi + e + geo.sy, gok && geo.yp), ypl = ld4_if(x_lo + e + geo.sy, gok && geo.yp);
+        const V4<float> zmh = ld4_if(x_hi + e - geo.sz, gok && geo.zm), zml = ld4_if(x_lo + e - geo.sz, gok && geo.zm);
+        const V4<float> zph = ld4_if(x_hi + e + geo.sz, gok && geo.zp), zpl = ld4_if(x_lo + e + geo.sz, gok && geo.zp);
+        float lh, rh, ll, rlo;
+        x_neighbours(Xh, g, rd.gpr, it.sl, it.lpr, gok, carry_h, lh, rh, [&] { return x_hi[e + 4]; });
+        x_neighbours(Xl, g, rd.gpr, it.sl, it.lpr, gok, carry_l, ll, rlo, [&] { return x_lo[e + 4]; });
         if (gok) {
           V4<float> D, B, AR;
           if (first) {
@@ -668,12 +663,14 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
               B.a[k] = 0.f;
               AR.a[k] = 0.f;
               if (xk < rd.nx) {
+                const double xk64 = (double)Xh.a[k] + (double)Xl.a[k];
+                const float xk32 = (float)xk64;
                 // the operator is linearised about K_prev: the start field, or c.lag when the solve starts from another guess
-                const float lag = (KIND == 0 && c.lag) ? ((const float*)c.lag)[e + k] : (float)X.a[k];
+                const float lag = (KIND == 0 && c.lag) ? ((const float*)c.lag)[e + k] : xk32;
                 AR.a[k] = reaction_site<float, KIND>(rd, which, s, lag, PF.a[k]);
-                D.a[k] = (float)cpl * (float)neighbour_count(rd, geo, xk) + AR.a[k];
+                D.a[k] = cpl32 * (float)neighbour_count(rd, geo, xk) + AR.a[k];
                 if (KIND == 0) B.a[k] = is_vessel(s) ? bvessel : 0.f;
-                else B.a[k] = (float)(X.a[k] * rd.inv_dt) + (is_vessel(s) ? (float)rd.kappa[which - 1] * PF.a[k] * G0 : 0.f);
+                else B.a[k] = (float)(xk64 * rd.inv_dt) + (is_vessel(s) ? (float)rd.kappa[which - 1] * PF.a[k] * G0 : 0.f);
               }
             }
             st4(dd + e, D);
@@ -690,15 +687,25 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
           for (int k = 0; k < 4; ++k) {
             Z.a[k] = 0.f;
             if (4 * g + k < rd.nx) {
-              const double d64 = cpl * (double)neighbour_count(rd, geo, 4 * g + k) + (double)AR.a[k];
-              const double r = (double)B.a[k] - (d64 * X.a[k] - cpl * nb_sum(X, k, left, right, ym, yp, zm, zp));
+              // r = b - (d x - c sum_nb x) in float-float (~48 bits): the
+              // operator's terms cancel to the small defect; d = c n + a is
+              // formed exactly from the stored reaction a
+              const FF xv{Xh.a[k], Xl.a[k]};
+              const FF L{k == 0 ? lh : Xh.a[k - 1], k == 0 ? ll : Xl.a[k - 1]};
+              const FF Rr{k == 3 ? rh : Xh.a[k + 1], k == 3 ? rlo : Xl.a[k + 1]};
+              const FF nb = ff_add(ff_add(ff_add(L, Rr), ff_add(FF{ymh.a[k], yml.a[k]}, FF{yph.a[k], ypl.a[k]})),
+                                   ff_add(FF{zmh.a[k], zml.a[k]}, FF{zph.a[k], zpl.a[k]}));
+              const FF d = ff_add(ff_two_prod(cpl32, (float)neighbour_count(rd, geo, 4 * g + k)), AR.a[k]);
+              const FF t = ff_add(ff_mul(d, xv), ff_neg(ff_mul(nb, cpl32)));
+              const FF rf = ff_add(ff_neg(t), B.a[k]);
+              const double r = (double)rf.hi + (double)rf.lo;
               const float r32 = (float)r;
               const float zk = D.a[k] != 0.f ? r32 / D.a[k] : 0.f;
               Z.a[k] = zk;
               R32.a[k] = r32;
               g_rr += r * r;
-              g_bb += (double)B.a[k] * (double)B.a[k];
-              g_rho += r * (double)zk;     // FP64: FP32 products of a tiny residual underflow
+              if (first) g_bb += (double)B.a[k] * (double)B.a[k];
+              if (!c.mg) g_rho += r * (double)zk;  // FP64: FP32 products of a tiny residual underflow
             }
           }
           st4(zz + e, Z);
@@ -729,7 +736,10 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
                    }
                    st.iters[which] += s.iters;
                    st.sweeps[which] += 1;
-                   if (!isfinite(s3[0]) || !isfinite(s3[1]) || !isfinite(s3[2])) {
+                   // |b|^2 is summed on the first sweep only (b does not change)
+                   if (first) s.bb_outer = s3[1];
+                   const double bb = s.bb_outer;
+                   if (!isfinite(s3[0]) || !isfinite(bb) || !isfinite(s3[2])) {
                      c.sync->error = 1;
                      st.nonfinite = 1;
                      s.active = 0;
@@ -737,7 +747,7 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
                      return 0;
                    }
                    const double tol = which == 0 ? rr.rtol_o2 : rr.rtol_drug;
-                   if (s3[1] == 0.0) {
+                   if (bb == 0.0) {
                      s.zero_b = 1;
                      s.rel_true = 0.0;
                      st.rel[which] = 0.0;
@@ -745,7 +755,7 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
                      s.dc_apply = 0;
                      return 0;
                    }
-                   const double rel = sqrt(s3[0] / s3[1]);
+                   const double rel = sqrt(s3[0] / bb);
                    s.rel_true = rel;
                    st.rel[which] = rel;
                    if (rel <= tol || s.outer >= rr.max_outer) {
@@ -780,7 +790,8 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
                    s.alpha = 0.0;
                    s.beta = 0.0;
                    s.dc_apply = 1;
-                   s.active = s3[2] > 0.0 ? 1 : 0;
+                   // the multigrid form leaves rho to the V-cycle (s3[2] = 0)
+                   s.active = (c.mg ? s3[0] > 0.0 : s3[2] > 0.0) ? 1 : 0;
                    return s.active;
                  },
                  [&](int n_active) {

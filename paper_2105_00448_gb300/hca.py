@@ -112,8 +112,9 @@ class hca_stats(ctypes.Structure):
         return d
 
 
-NKCLASS = 9
-KCLASS_NAMES = ("setup", "pass_a", "pass_b", "residual", "ode", "ca_compact", "ca_colour", "other", "mg")
+NKCLASS = 11
+KCLASS_NAMES = ("setup", "pass_a", "pass_b", "residual", "ode", "ca_compact", "ca_colour", "other", "mg",
+                "mg_restrict0", "mg_post0")
 
 
 class hca_profile(ctypes.Structure):
