@@ -990,6 +990,7 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
         ni = (ni < 0 || ni == v) ? v : 0;
       }
       hca::set_pass_ni(ni == 1 || ni == 2 || ni == 4 ? ni : 0);
+      h->mgh.ni = ni == 1 || ni == 2 || ni == 4 ? ni : 0;
     }
     rc = initial_oxygen(h);
     if (rc) goto fail;

@@ -245,6 +245,7 @@ struct MGHost {
   long long n0 = 0;
   MGLevel lv[16] = {};
   int launches = 0;   // kernels per V-cycle
+  int ni = 0;         // groups per lane in a row of the lattice (1, 2, 4; 0 = other)
 };
 
 struct Ctx {

@@ -35,10 +35,13 @@ struct View {
   T c;
   __device__ __forceinline__ long long n() const { return (long long)nx * ny * nz; }
   __device__ __forceinline__ long long at(int X, int Y, int Z) const { return off + X + sy * Y + sz * Z; }
+  // 32-bit arithmetic: lattices hold fewer than 2^31 sites (64-bit division
+  // would dominate these kernels' instruction count)
   __device__ __forceinline__ void coords(long long s, int& X, int& Y, int& Z) const {
-    X = (int)(s % nx);
-    Y = (int)((s / nx) % ny);
-    Z = (int)(s / ((long long)nx * ny));
+    const unsigned u = (unsigned)s, q = u / (unsigned)nx;
+    X = (int)(u - q * (unsigned)nx);
+    Z = (int)(q / (unsigned)ny);
+    Y = (int)(q - (unsigned)Z * (unsigned)ny);
   }
   __device__ __forceinline__ int nbcount(int X, int Y, int Z) const {
     return (X > 0) + (X < nx - 1) + (Y > 0) + (Y < ny - 1) + (Z > 0) + (Z < nz - 1);
@@ -331,8 +334,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_mg_small(Ctx c, int which, in
 // they are needed) or u = src (the lattice is the coarsest level);
 // rho = r.z (fixed-order sums); beta = rho / rho_old (0 on the first
 // application of a solve).
-template <typename T, bool PROLONG>
-__global__ void __launch_bounds__(512) k_mg_post0(Ctx c, int which, const T* __restrict__ src) {
+template <typename T, bool PROLONG, int NI>
+__global__ void __maxnreg__(96) k_mg_post0(Ctx c, int which, const T* __restrict__ src) {
   HCA_COUNT_KERNEL(c);
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
@@ -357,9 +360,13 @@ __global__ void __launch_bounds__(512) k_mg_post0(Ctx c, int which, const T* __r
     const int j = ch.y + (row_ok ? rl : 0);
     const RowGeo geo = row_geo(rd, j);
     const int y = j % rd.ny, z = j / rd.ny;
-    double acc[NDOT] = {0.0, 0.0, 0.0};
+    LaneAcc<T> acc[1];
     T carry = T(0);
-    for (int itn = 0; itn < it.niter; ++itn) {
+    // groups per lane in a row: a compile-time count (NI > 0) lets the
+    // compiler issue the loads of all of them before the first is used
+    const int niter = NI > 0 ? NI : it.niter;
+#pragma unroll
+    for (int itn = 0; itn < niter; ++itn) {
       const int g = itn * it.lpr + it.sl;
       const bool gok = row_ok && g < rd.gpr;
       const long long e = geo.base + 4LL * g;
@@ -385,30 +392,38 @@ __global__ void __launch_bounds__(512) k_mg_post0(Ctx c, int which, const T* __r
       const V4<T> R = ld4_if(rr + e, gok);
       const V4<T> D = ld4_if(dd + e, gok);
       const V4<T> W = ld4_if(ww + e, gok);
+      // u at the site after the group, for the segment's last lane, loaded
+      // with the rest of the group's values
+      const bool last_lane = it.sl == it.lpr - 1 && gok && g + 1 < rd.gpr;
+      T un = T(0);
+      if (last_lane) {
+        if (!PROLONG) {
+          un = src[e + 4];
+        } else {
+          const T wn = ww[e + 4];
+          const long long cb = ((long long)(z >> 1) * ny1 + (y >> 1)) * nx1 + 2LL * g + 2;
+          un = wn != T(0) ? wn * rr[e + 4] + x1[cb] : T(0);
+        }
+      }
       T left, right;
-      x_neighbours(U, g, rd.gpr, it.sl, it.lpr, gok, carry, left, right, [&] {
-        if (!PROLONG) return src[e + 4];
-        const T wn = ww[e + 4];
-        const long long cb = ((long long)(z >> 1) * ny1 + (y >> 1)) * nx1 + 2LL * g + 2;
-        return wn != T(0) ? wn * rr[e + 4] + x1[cb] : T(0);
-      });
+      x_neighbours(U, g, rd.gpr, it.sl, it.lpr, gok, carry, left, right, [&] { return un; });
       if (gok) {
         V4<T> Zo;
-        double rz = 0.0;
+        T rz = T(0);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           Zo.a[k] = T(0);
           if (4 * g + k < rd.nx && D.a[k] != T(0)) {
             const T q = D.a[k] * U.a[k] - cpl * nb_sum(U, k, left, right, ym, yp, zm, zp);
             Zo.a[k] = U.a[k] + W.a[k] * (R.a[k] - q);
-            rz += (double)R.a[k] * (double)Zo.a[k];
+            rz += R.a[k] * Zo.a[k];
           }
         }
         st4(zz + e, Zo);
-        acc[0] += rz;
+        acc[0].add(rz);   // float-float lane sums for FP32 (r is scaled to O(1))
       }
     }
-    store_row(c, blockIdx.x, rl, row_ok, it.sl, it.lpr, acc, 1);
+    store_rows_acc(c, blockIdx.x, rl, row_ok, it.sl, it.lpr, acc, 1);
   }
   warp_epilogue(c, 1, blockIdx.x, [&](int r, const double* s1) -> int {
     RepSolve& s = c.solve[r];
@@ -448,7 +463,7 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part) {
       k_mg_sweep<T><<<grid_for(n0), kMgThreads, 0, s>>>(c, which, 0, odd ? t0 : z, odd ? z : t0);
     }
     const T* src = ((MG_NU_COARSE - 2) & 1) ? z : t0;
-    k_mg_post0<T, false><<<c.n_chunks, c.threads, 0, s>>>(c, which, src);
+    k_mg_post0<T, false, 0><<<c.n_chunks, c.threads, 0, s>>>(c, which, src);
     return;
   }
   if (all || part == 0) {
@@ -461,7 +476,14 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part) {
     k_mg_small<T><<<1, kSmallThreads, 0, s>>>(c, which, H.small);
     for (int l = H.small - 1; l >= 1; --l) k_mg_post<T><<<grid_for(H.lv[l].n), kMgThreads, 0, s>>>(c, which, l);
   }
-  if (all || part == 2) k_mg_post0<T, true><<<c.n_chunks, c.threads, 0, s>>>(c, which, nullptr);
+  if (all || part == 2) {
+    switch (H.ni) {
+      case 1: k_mg_post0<T, true, 1><<<c.n_chunks, c.threads, 0, s>>>(c, which, nullptr); break;
+      case 2: k_mg_post0<T, true, 2><<<c.n_chunks, c.threads, 0, s>>>(c, which, nullptr); break;
+      case 4: k_mg_post0<T, true, 4><<<c.n_chunks, c.threads, 0, s>>>(c, which, nullptr); break;
+      default: k_mg_post0<T, true, 0><<<c.n_chunks, c.threads, 0, s>>>(c, which, nullptr); break;
+    }
+  }
 }
 
 template <typename T>

@@ -58,4 +58,28 @@ __device__ __forceinline__ RowIter row_iter(const RepDesc& rd) {
   return it;
 }
 
+// Per-lane accumulator of a pass: float-float for FP32 fields, double for FP64.
+template <typename T> struct LaneAcc;
+template <> struct LaneAcc<float> {
+  FF v{0.f, 0.f};
+  __device__ __forceinline__ void add(float x) { v = ff_add(v, x); }
+};
+template <> struct LaneAcc<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+};
+
+__device__ __forceinline__ void store_rows_acc(const Ctx& c, int chunk, int rl, bool row_ok, int sl, int lpr,
+                                               const LaneAcc<float>* acc, int ndot) {
+  FF a[NDOT];
+  for (int k = 0; k < ndot; ++k) a[k] = acc[k].v;
+  store_row_ff(c, chunk, rl, row_ok, sl, lpr, a, ndot);
+}
+__device__ __forceinline__ void store_rows_acc(const Ctx& c, int chunk, int rl, bool row_ok, int sl, int lpr,
+                                               const LaneAcc<double>* acc, int ndot) {
+  double a[NDOT];
+  for (int k = 0; k < ndot; ++k) a[k] = acc[k].v;
+  store_row(c, chunk, rl, row_ok, sl, lpr, a, ndot);
+}
+
 }  // namespace hca
