@@ -35,3 +35,19 @@ def random_states(shape, rng, p_vessel=0.1, p_cancer=0.45, p_stroma=0.03, p_dead
 def operator_scale(coupling, reaction, u):
     """Size of the terms of (A u)_i, the yardstick for rounding differences."""
     return float(np.max(np.abs(reaction) * np.abs(u)) + coupling * 7.0 * np.max(np.abs(u)))
+
+
+def oracle_counts(args):
+    """One oracle replicate of the coupled run (for a spawn process pool):
+    (seed, edge, steps, corr_len, params) -> (final counts per state code,
+    kills, divisions summed over the steps)."""
+    seed, edge, steps, corr_len, params = args
+    from oracle.model import OracleSim
+
+    cfg = Pm.Config(nx=edge, ny=edge, nz=edge, seed=seed, **params)
+    maps = make_maps(edge, edge, edge, corr_len=corr_len, seed=seed)
+    sim = OracleSim(cfg, maps.p_cell, maps.perf, maps.p_vessel)
+    sim.step(steps)
+    kills = sum(h.kills for h in sim.history)
+    divisions = sum(h.divisions for h in sim.history)
+    return np.bincount(sim.state.reshape(-1), minlength=6).astype(np.int64), kills, divisions
