@@ -159,7 +159,7 @@ typedef struct hca_config {
 
   int32_t warm_start;    /* HCA_WS_PREV */
   int32_t preconditioner; /* HCA_PC_JACOBI (default) or HCA_PC_MG (single-replicate handles) */
-  int32_t threads_per_block; /* 0 = library choice (128); else 64, 128, 256 or 512; results do not depend on it */
+  int32_t threads_per_block; /* 0 = library choice (autotuned at creation); else 64, 128, 256 or 512; results do not depend on it */
   int32_t pad2;
   void* stream;          /* cudaStream_t, NULL = default stream */
 } hca_config;
@@ -266,6 +266,13 @@ int hca_get_stats(hca_handle* h, int32_t rep, hca_stats* out);
  * precision.  Exposes the 7-point stencil of Eqs. (oxygen)/(chemo) alone. */
 int hca_apply_operator(hca_handle* h, int32_t rep, int32_t which, const void* u, void* out,
                        int32_t on_device);
+
+/* The launch shape the handle uses: threads per block of the sweep kernels
+ * and the register cap of the FP32 CG passes.  With threads_per_block = 0
+ * in the config the library picks both at creation by timing the oxygen CG
+ * passes on the handle's own lattices (set HCA_NO_TUNE=1 to keep 128 / 96).
+ * Results do not depend on the choice. */
+int hca_get_launch_config(hca_handle* h, int32_t* threads_per_block, int32_t* pass_regs);
 
 /* z = M r for replicate rep, with M the multigrid V-cycle (HCA_PC_MG) built
  * on the operator of the next solve of `which` (as hca_apply_operator).

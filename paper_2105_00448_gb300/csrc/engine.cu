@@ -29,8 +29,6 @@ void launch_philox_uniforms(unsigned long long seed, unsigned long long site0, l
 void launch_advance_step(const Ctx& c, long long by);
 void launch_ca_compact(const Ctx& c, bool fp64);
 void launch_ca_colour(const Ctx& c, int colour, int blocks_x, bool fp64);
-void set_pass_regs(int r);
-void set_pass_ni(int ni);
 void launch_mg_setup(const Ctx& c, int which, bool fp64, const MGHost& H);
 void launch_vcycle(const Ctx& c, int which, bool fp64, const MGHost& H, int part);
 int vcycle_launches(const MGHost& H);
@@ -679,6 +677,65 @@ int check_convergence(hca_handle* h) {
 
 // Initial oxygen: Picard iteration of the lagged linearisation from K = K0
 // until ||K_new - K_old|| <= picard_tol ||K_new|| for every replicate.
+// Launch-shape autotuner: times the oxygen CG passes (the hot pair) for each
+// candidate block size (and register cap of the FP32 passes) on the handle's
+// own lattices and keeps the fastest.  It runs at creation, on the solver's
+// scratch vectors (x = aux), before anything depends on them; the reductions
+// sum by rows in a fixed order, so results do not depend on the choice.
+int autotune(hca_handle* h, bool tune_regs) {
+  Ctx& c = h->ctx;
+  const int cand_t[3] = {128, 256, 512};
+  const int cand_r[3] = {80, 96, 128};
+  const int nr = (tune_regs && !h->fp64) ? 3 : 1;
+  constexpr int kIters = 6;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  HCA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return HCA_ERR_CUDA;
+  }
+  float best = 1e30f;
+  int bt = c.threads, br = c.pass_regs;
+  int rc = HCA_OK;
+  for (int ti = 0; ti < 3 && !rc; ++ti)
+    for (int ri = 0; ri < nr && !rc; ++ri) {
+      c.threads = cand_t[ti];
+      if (nr > 1) c.pass_regs = cand_r[ri];
+      hca::launch_setup(c, 0, h->fp64, kNoCond);
+      for (int k = 0; k < 2; ++k) {   // warm-up
+        pass_a(h, 0);
+        pass_b(h, 0, c.aux, kNoCond);
+      }
+      cudaEventRecord(e0, c.stream);
+      for (int k = 0; k < kIters; ++k) {
+        pass_a(h, 0);
+        pass_b(h, 0, c.aux, kNoCond);
+      }
+      cudaEventRecord(e1, c.stream);
+      float ms = 0.f;
+      if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        rc = HCA_ERR_CUDA;
+        break;
+      }
+      h->launches += 1 + 2 * (kIters + 2);
+      if (ms < best) {
+        best = ms;
+        bt = c.threads;
+        br = c.pass_regs;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c.threads = bt;
+  c.pass_regs = br;
+  if (rc) return rc;
+  // the timed passes may have left solver flags set; the solves reset the rest
+  HCA_TRY(cudaMemsetAsync(&c.sync->error, 0, sizeof(int), c.stream));
+  HCA_TRY(cudaStreamSynchronize(c.stream));
+  return HCA_OK;
+}
+
 int initial_oxygen(hca_handle* h) {
   Ctx& c = h->ctx;
   double tol = 0;
@@ -746,9 +803,6 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     // HCA_NO_GRAPH=1 runs steps from a host loop instead of the step graph
     const char* ng = std::getenv("HCA_NO_GRAPH");
     if (ng && ng[0] == '1') h->graphs_ok = false;
-    // HCA_PASS_REGS=64|80|96|128 overrides the CG passes' register cap (tuning)
-    const char* pr = std::getenv("HCA_PASS_REGS");
-    if (pr) hca::set_pass_regs(std::atoi(pr));
   }
   cudaGetDevice(&h->device);
   int sm = 0;
@@ -789,6 +843,12 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
   c.n_supers = super0;
   // 128 threads per block measured fastest for the CG passes on GB300
   c.threads = cfgs[0].threads_per_block ? cfgs[0].threads_per_block : 128;
+  c.pass_regs = 96;   // measured best at 128 threads; the autotuner may change both
+  {
+    // HCA_PASS_REGS=64|80|96|128 fixes the CG passes' register cap
+    const char* pr = std::getenv("HCA_PASS_REGS");
+    if (pr) c.pass_regs = std::atoi(pr);
+  }
   c.stream = h->stream;
   const size_t es = elem_size(h);
   const size_t fbytes = (size_t)h->total * es;
@@ -989,8 +1049,15 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
         const int v = (r.gpr + r.lpr - 1) / r.lpr;
         ni = (ni < 0 || ni == v) ? v : 0;
       }
-      hca::set_pass_ni(ni == 1 || ni == 2 || ni == 4 ? ni : 0);
-      h->mgh.ni = ni == 1 || ni == 2 || ni == 4 ? ni : 0;
+      c.pass_ni = ni == 1 || ni == 2 || ni == 4 ? ni : 0;
+      h->mgh.ni = c.pass_ni;
+    }
+    if (!cfgs[0].threads_per_block) {
+      const char* nt = std::getenv("HCA_NO_TUNE");
+      if (!(nt && nt[0] == '1')) {
+        rc = autotune(h, std::getenv("HCA_PASS_REGS") == nullptr);
+        if (rc) goto fail;
+      }
     }
     rc = initial_oxygen(h);
     if (rc) goto fail;
@@ -1237,6 +1304,13 @@ int hca_get_stats(hca_handle* h, int32_t rep, hca_stats* out) {
     out->ws_r0_prev = w.r0_prev;
     out->ws_r0_learned = w.r0_learned;
   }
+  return HCA_OK;
+}
+
+int hca_get_launch_config(hca_handle* h, int32_t* threads_per_block, int32_t* pass_regs) {
+  if (!h || !threads_per_block || !pass_regs) return HCA_ERR_ARG;
+  *threads_per_block = h->ctx.threads;
+  *pass_regs = h->fp64 ? 128 : h->ctx.pass_regs;
   return HCA_OK;
 }
 

@@ -266,6 +266,8 @@ struct Ctx {
   const void* lag;  // oxygen linearisation point (K_prev) when the solve starts elsewhere; null: the start field
   // multigrid preconditioner (single replicate): residual r (the Jacobi form
   // carries z = r / d instead), level-0 scratch, coarse level table
+  int pass_regs;    // register cap of the FP32 CG passes (64, 80, 96, 128)
+  int pass_ni;      // groups per lane in a row shared by all replicates (1, 2, 4; 0 = differs)
   int mg;           // 0: Jacobi (z = r / d), 1: V-cycle (z = M r)
   int mg_nlev;      // levels including the lattice itself
   int mg_small;     // first level handled by the single-block kernel

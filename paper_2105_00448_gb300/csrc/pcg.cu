@@ -857,12 +857,6 @@ void launch_setup(const Ctx& c, int which, bool fp64, CondArg cnd) {
   else launch_setup_t<float>(c, which, cnd);
 }
 
-int g_pass_regs = 96;   // register cap of the FP32 passes (measured best at 128 threads)
-int g_pass_ni = 0;      // groups per lane in a row, shared by all replicates (0: differs)
-
-void set_pass_regs(int r) { g_pass_regs = r; }
-void set_pass_ni(int ni) { g_pass_ni = ni; }
-
 template <int REGS, int NI>
 static void launch_ab_f32(const Ctx& c, int which, bool a, void* xfield, CondArg cnd) {
   if (a) k_pass_a<float, REGS, NI><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which);
@@ -871,7 +865,7 @@ static void launch_ab_f32(const Ctx& c, int which, bool a, void* xfield, CondArg
 
 template <int REGS>
 static void launch_ab_f32_ni(const Ctx& c, int which, bool a, void* xfield, CondArg cnd) {
-  switch (g_pass_ni) {
+  switch (c.pass_ni) {
     case 1: launch_ab_f32<REGS, 1>(c, which, a, xfield, cnd); break;
     case 2: launch_ab_f32<REGS, 2>(c, which, a, xfield, cnd); break;
     case 4: launch_ab_f32<REGS, 4>(c, which, a, xfield, cnd); break;
@@ -885,7 +879,7 @@ static void launch_ab(const Ctx& c, int which, bool fp64, bool a, void* xfield, 
     else k_pass_b<double, 128, 0><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, xfield, cnd);
     return;
   }
-  switch (g_pass_regs) {
+  switch (c.pass_regs) {
     case 64: launch_ab_f32_ni<64>(c, which, a, xfield, cnd); break;
     case 96: launch_ab_f32_ni<96>(c, which, a, xfield, cnd); break;
     case 128: launch_ab_f32_ni<128>(c, which, a, xfield, cnd); break;

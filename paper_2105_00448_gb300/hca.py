@@ -129,6 +129,7 @@ EXPORTS = [
     "hca_config_default", "hca_create", "hca_create_batch", "hca_step", "hca_stage",
     "hca_read_fields", "hca_write_fields", "hca_read_states", "hca_write_states",
     "hca_set_step", "hca_get_stats", "hca_apply_operator", "hca_apply_preconditioner", "hca_philox_uniforms",
+    "hca_get_launch_config",
     "hca_sync", "hca_get_shape", "hca_launch_count", "hca_profile_enable", "hca_get_profile",
     "hca_o2_residual_noalloc", "hca_destroy", "hca_status_string",
     "hca_net_param_count", "hca_net_create", "hca_net_set_params", "hca_net_get_params", "hca_net_forward",
@@ -183,6 +184,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "hca_get_stats": (ctypes.c_int, [P, I32, ctypes.POINTER(hca_stats)]),
         "hca_apply_operator": (ctypes.c_int, [P, I32, I32, P, P, I32]),
         "hca_apply_preconditioner": (ctypes.c_int, [P, I32, I32, P, P, I32]),
+        "hca_get_launch_config": (ctypes.c_int, [P, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
         "hca_philox_uniforms": (ctypes.c_int, [U64, U64, I64, U32, U32, P, I32]),
         "hca_sync": (ctypes.c_int, [P]),
         "hca_get_shape": (ctypes.c_int, [P, I32, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)]),
@@ -340,6 +342,12 @@ def hca_apply_operator(h, rep: int, which: int, u, out) -> None:
     if du != do or nu != no:
         raise ValueError("u and out must match in size and location")
     _check(load().hca_apply_operator(h, rep, which, pu, po, du), "hca_apply_operator")
+
+
+def hca_get_launch_config(h):
+    t, r = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().hca_get_launch_config(h, ctypes.byref(t), ctypes.byref(r)), "hca_get_launch_config")
+    return t.value, r.value
 
 
 def hca_apply_preconditioner(h, rep: int, which: int, r, z) -> None:

@@ -382,3 +382,24 @@ def test_batch_equals_single_replicates(precision):
             assert sb[key] == ss[key], (r, key)
         single.close()
     batch.close()
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_autotuned_launch_shape_gives_identical_results(precision, monkeypatch):
+    """threads_per_block = 0: the library times candidate launch shapes at
+    creation; the steps must be bit-identical to a fixed 128-thread handle."""
+    shape = (24, 40, 64)
+    runs = []
+    for threads, tune in ((0, "0"), (128, "1")):
+        monkeypatch.setenv("HCA_NO_TUNE", tune)
+        sim, _, _ = make_pair(shape, precision, seed=12, n_drugs=1, threads=threads)
+        t, r = hca.hca_get_launch_config(sim.handle)
+        assert t in (64, 128, 256, 512) and r in (64, 80, 96, 128)
+        if threads:
+            assert t == 128
+        sim.step(2)
+        runs.append((sim.states(), sim.field(hca.FIELD_O2), sim.field(hca.FIELD_DRUG0), sim.stats()))
+        sim.close()
+    (s0, K0, G0, st0), (s1, K1, G1, st1) = runs
+    assert np.array_equal(s0, s1) and np.array_equal(K0, K1) and np.array_equal(G0, G1)
+    assert st0["o2_iterations"] == st1["o2_iterations"] and st0["drug_iterations"] == st1["drug_iterations"]
