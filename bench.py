@@ -303,6 +303,8 @@ def run_gpu(args):
                 "kernel_time_share": kernel_share, "status": int(rc)}
         if args.ws_learned and world == 1:
             line["warm_start_learned"] = run_ws_learned(args, hca, make_maps, np, torch)
+        if args.batch and world == 1:
+            line["batched"] = run_batch(args, hca, torch)
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -401,6 +403,39 @@ def run_ws_learned(args, hca, make_maps, np, torch):
                          "frac": achieved / peak}}
 
 
+def run_batch(args, hca, torch):
+    """Batched replicates of uneven size in one handle (one launch per kernel
+    for the whole batch): sizes drawn from {64, 96, 128, 192}^3, seeds 1000 + r,
+    the workload's physics; batches use the Jacobi preconditioner."""
+    from synth import make_maps, replicate_sizes
+
+    sizes = replicate_sizes(args.batch)
+    stream = torch.cuda.Stream()
+    params = {**WORKLOAD, "preconditioner": 0}
+    cfgs, maps = [], []
+    for r, n in enumerate(sizes):
+        m = make_maps(n, n, n, corr_len=CORR_LEN, seed=1000 + r)
+        maps.append((m.p_cell, m.perf, m.p_vessel))
+        cfgs.append(hca.make_config(n, n, n, stream=stream.cuda_stream, **{**params, "seed": 1000 + r}))
+    sim = hca.Sim(cfgs, maps, batch=True)
+    sim.step(args.warmup, allow_noconv=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.batch_steps, allow_noconv=True)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1) / args.batch_steps
+    its = [sim.stats(r) for r in range(len(sizes))]
+    sim.close()
+    total = sum(n ** 3 for n in sizes)
+    return {"workload": f"{len(sizes)} replicates, edges {sorted(set(sizes))} "
+                        f"(counts {[sizes.count(v) for v in sorted(set(sizes))]}), one handle",
+            "sites": total, "ms_per_step": ms, "value": total / (ms / 1e3), "unit": "site-steps/s",
+            "per_replicate_site_steps_s": {str(n): n ** 3 / (ms / 1e3) for n in sorted(set(sizes))},
+            "steps": args.batch_steps, "preconditioner": "jacobi",
+            "max_cg_iterations_last_step": max(s["o2_iterations"] + sum(s["drug_iterations"]) for s in its)}
+
+
 def run_e2e(args, hca, make_maps, np, torch):
     """Same metric through the public C ABI with host buffers: create from
     pinned host maps, then per step one hca_step and a read of the states and
@@ -448,6 +483,9 @@ def main():
     ap.add_argument("--ws-samples", type=int, default=48)
     ap.add_argument("--ws-iters", type=int, default=4000)
     ap.add_argument("--ws-steps", type=int, default=10)
+    ap.add_argument("--batch", type=int, default=0,
+                    help="also time N batched replicates of uneven size (e.g. 64)")
+    ap.add_argument("--batch-steps", type=int, default=5)
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         raise SystemExit("need --steps >= 1 and --warmup >= 0")
