@@ -406,12 +406,13 @@ def run_ws_learned(args, hca, make_maps, np, torch):
 def run_batch(args, hca, torch):
     """Batched replicates of uneven size in one handle (one launch per kernel
     for the whole batch): sizes drawn from {64, 96, 128, 192}^3, seeds 1000 + r,
-    the workload's physics; batches use the Jacobi preconditioner."""
+    the workload's physics and solver (each replicate its own multigrid
+    hierarchy)."""
     from synth import make_maps, replicate_sizes
 
     sizes = replicate_sizes(args.batch)
     stream = torch.cuda.Stream()
-    params = {**WORKLOAD, "preconditioner": 0}
+    params = dict(WORKLOAD)
     cfgs, maps = [], []
     for r, n in enumerate(sizes):
         m = make_maps(n, n, n, corr_len=CORR_LEN, seed=1000 + r)
@@ -432,7 +433,7 @@ def run_batch(args, hca, torch):
                         f"(counts {[sizes.count(v) for v in sorted(set(sizes))]}), one handle",
             "sites": total, "ms_per_step": ms, "value": total / (ms / 1e3), "unit": "site-steps/s",
             "per_replicate_site_steps_s": {str(n): n ** 3 / (ms / 1e3) for n in sorted(set(sizes))},
-            "steps": args.batch_steps, "preconditioner": "jacobi",
+            "steps": args.batch_steps, "preconditioner": "multigrid",
             "max_cg_iterations_last_step": max(s["o2_iterations"] + sum(s["drug_iterations"]) for s in its)}
 
 

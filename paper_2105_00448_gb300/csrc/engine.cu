@@ -787,8 +787,8 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
         cfgs[i].stream != cfgs[0].stream)
       return HCA_ERR_ARG;
     // the learned warm start and the multigrid hierarchy serve one lattice
-    if ((cfgs[i].warm_start != HCA_WS_PREV || cfgs[i].preconditioner != HCA_PC_JACOBI) && n > 1)
-      return HCA_ERR_UNIMPLEMENTED;
+    if (cfgs[i].warm_start != HCA_WS_PREV && n > 1) return HCA_ERR_UNIMPLEMENTED;
+    if (cfgs[i].preconditioner != cfgs[0].preconditioner) return HCA_ERR_ARG;
   }
   hca_handle* h = new (std::nothrow) hca_handle();
   if (!h) return HCA_ERR_OOM;
@@ -882,46 +882,96 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     ALLOC(c.b, fbytes);
     ALLOC(c.aux, fbytes);
     if (h->mg) {
+      // one hierarchy per replicate; each coarse level's arrays hold all
+      // replicates back to back
       hca::MGHost& H = h->mgh;
-      const RepDesc& r0 = h->reps_h[0];
-      int nx = r0.nx, ny = r0.ny, nz = r0.nz;
-      long long nn = (long long)nx * ny * nz;
-      H.n0 = nn;
-      H.nlev = 1;
-      while (nn > hca::MG_MIN_SITES && std::min(nx, std::min(ny, nz)) > 1 && H.nlev < 16) {
-        nx = (nx + 1) / 2;
-        ny = (ny + 1) / 2;
-        nz = (nz + 1) / 2;
-        nn = (long long)nx * ny * nz;
-        hca::MGLevel& L = H.lv[H.nlev];
-        L.nx = nx;
-        L.ny = ny;
-        L.nz = nz;
-        L.n = nn;
-        L.cscale = std::ldexp(1.0, H.nlev);
-        ALLOC(L.x, es * (size_t)nn);
-        ALLOC(L.t, es * (size_t)nn);
-        ALLOC(L.rhs, es * (size_t)nn);
-        ALLOC(L.d, es * (size_t)nn);
-        ALLOC(L.w, es * (size_t)nn);
-        H.nlev += 1;
-      }
-      H.small = H.nlev - 1;
-      for (int l = 1; l < H.nlev; ++l)
-        if (H.lv[l].n <= hca::MG_SMALL_SITES) {
-          H.small = l;
-          break;
+      std::vector<hca::MGLevel> lv((size_t)n * hca::MG_MAXLEV);
+      std::vector<int2> rep(n);
+      std::vector<long long> start((size_t)hca::MG_MAXLEV * (n + 1), 0);
+      for (int i = 0; i < n; ++i) {
+        const RepDesc& r0 = h->reps_h[i];
+        int nx = r0.nx, ny = r0.ny, nz = r0.nz;
+        long long nn = (long long)nx * ny * nz;
+        int nl = 1;
+        start[i + 1] = start[i] + nn;   // level 0 (the lattices)
+        while (nn > hca::MG_MIN_SITES && std::min(nx, std::min(ny, nz)) > 1 && nl < hca::MG_MAXLEV) {
+          nx = (nx + 1) / 2;
+          ny = (ny + 1) / 2;
+          nz = (nz + 1) / 2;
+          nn = (long long)nx * ny * nz;
+          hca::MGLevel& L = lv[(size_t)i * hca::MG_MAXLEV + nl];
+          L.nx = nx;
+          L.ny = ny;
+          L.nz = nz;
+          L.n = nn;
+          L.cscale = std::ldexp(1.0, nl);
+          nl += 1;
         }
+        int small = nl - 1;
+        for (int l = 1; l < nl; ++l)
+          if (lv[(size_t)i * hca::MG_MAXLEV + l].n <= hca::MG_SMALL_SITES) {
+            small = l;
+            break;
+          }
+        rep[i] = make_int2(nl, small);
+        H.nlev = std::max(H.nlev, nl);
+        H.small = std::max(H.small, small);
+      }
+      if (n > 1 && H.nlev > 0)
+        for (int i = 0; i < n; ++i)
+          if (rep[i].x == 1) {   // a batch needs a coarse level in every replicate
+            rc = HCA_ERR_UNIMPLEMENTED;
+            goto fail;
+          }
+      for (int l = 1; l < H.nlev; ++l) {
+        long long tot = 0;
+        for (int i = 0; i < n; ++i) {
+          start[(size_t)l * (n + 1) + i] = tot;
+          if (l < rep[i].x) tot += lv[(size_t)i * hca::MG_MAXLEV + l].n;
+        }
+        start[(size_t)l * (n + 1) + n] = tot;
+        H.ntot[l] = tot;
+        char* arr[5];
+        for (int k = 0; k < 5; ++k) ALLOC(arr[k], es * (size_t)std::max(1LL, tot));
+        for (int k = 0; k < 5; ++k)
+          if (cudaMemsetAsync(arr[k], 0, es * (size_t)std::max(1LL, tot), c.stream)) {
+            rc = HCA_ERR_CUDA;
+            goto fail;
+          }
+        for (int i = 0; i < n; ++i) {
+          if (l >= rep[i].x) continue;
+          hca::MGLevel& L = lv[(size_t)i * hca::MG_MAXLEV + l];
+          const size_t o = es * (size_t)start[(size_t)l * (n + 1) + i];
+          L.x = arr[0] + o;
+          L.t = arr[1] + o;
+          L.rhs = arr[2] + o;
+          L.d = arr[3] + o;
+          L.w = arr[4] + o;
+        }
+      }
+      H.ntot[0] = start[n];
       H.launches = hca::vcycle_launches(H);
       ALLOC(c.r, fbytes);
       ALLOC(c.mg_t0, fbytes);
       ALLOC(c.mg_w, fbytes);
       hca::MGLevel* lv_d;
-      ALLOC(lv_d, sizeof(hca::MGLevel) * H.nlev);
+      long long* start_d;
+      int2* rep_d;
+      ALLOC(lv_d, sizeof(hca::MGLevel) * lv.size());
+      ALLOC(start_d, sizeof(long long) * start.size());
+      ALLOC(rep_d, sizeof(int2) * n);
+      if (cudaMemcpyAsync(lv_d, lv.data(), sizeof(hca::MGLevel) * lv.size(), cudaMemcpyHostToDevice, c.stream) ||
+          cudaMemcpyAsync(start_d, start.data(), sizeof(long long) * start.size(), cudaMemcpyHostToDevice,
+                          c.stream) ||
+          cudaMemcpyAsync(rep_d, rep.data(), sizeof(int2) * n, cudaMemcpyHostToDevice, c.stream) ||
+          cudaStreamSynchronize(c.stream)) {
+        rc = HCA_ERR_CUDA;
+        goto fail;
+      }
       c.mg_lv = lv_d;
+      c.mg_start = start_d;
+      c.mg_rep = rep_d;
       c.mg = 1;
-      c.mg_nlev = H.nlev;
-      c.mg_small = H.small;
     }
     if (h->learned) {
       ALLOC(h->ws_cand, sizeof(double) * (size_t)h->total);
@@ -961,21 +1011,6 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
         rc = HCA_ERR_CUDA;
         goto fail;
       }
-    if (h->mg) {
-      const hca::MGHost& H = h->mgh;
-      for (int l = 1; l < H.nlev; ++l) {
-        void* arr[5] = {H.lv[l].x, H.lv[l].t, H.lv[l].rhs, H.lv[l].d, H.lv[l].w};
-        for (void* p : arr)
-          if (cudaMemsetAsync(p, 0, es * (size_t)H.lv[l].n, s)) {
-            rc = HCA_ERR_CUDA;
-            goto fail;
-          }
-      }
-      if (cudaMemcpyAsync(const_cast<void*>(c.mg_lv), H.lv, sizeof(hca::MGLevel) * H.nlev, cudaMemcpyHostToDevice, s)) {
-        rc = HCA_ERR_CUDA;
-        goto fail;
-      }
-    }
     if (cudaMemsetAsync(c.state, 0, (size_t)h->total + 16, s) || cudaMemsetAsync(c.sync, 0, sizeof(hca::PassSync), s) ||
         cudaMemsetAsync(c.solve, 0, sizeof(hca::RepSolve) * n, s) ||
         cudaMemsetAsync(c.stats, 0, sizeof(hca::DevStats) * n, s) || cudaMemsetAsync(c.step, 0, sizeof(long long), s) ||

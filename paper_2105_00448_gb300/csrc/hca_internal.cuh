@@ -238,14 +238,15 @@ constexpr int MG_NU_COARSE = 16;
 constexpr long long MG_MIN_SITES = 512;     // coarsening stops at or below this size
 constexpr long long MG_SMALL_SITES = 4096;  // levels this small run inside one block
 
-// Host copy of the hierarchy (launch geometry and pointers).
+constexpr int MG_MAXLEV = 16;
+
+// Host summary of the hierarchies of a handle's replicates (launch geometry).
 struct MGHost {
-  int nlev = 0;
-  int small = 0;
-  long long n0 = 0;
-  MGLevel lv[16] = {};
-  int launches = 0;   // kernels per V-cycle
-  int ni = 0;         // groups per lane in a row of the lattice (1, 2, 4; 0 = other)
+  int nlev = 0;                  // most levels of any replicate
+  int small = 0;                 // 1 + deepest grid-kernel level of any replicate
+  long long ntot[MG_MAXLEV] = {};  // sites of level l summed over the replicates
+  int launches = 0;              // kernels per V-cycle
+  int ni = 0;                    // groups per lane in a row of the lattice (1, 2, 4; 0 = other)
 };
 
 struct Ctx {
@@ -269,12 +270,12 @@ struct Ctx {
   int pass_regs;    // register cap of the FP32 CG passes (64, 80, 96, 128)
   int pass_ni;      // groups per lane in a row shared by all replicates (1, 2, 4; 0 = differs)
   int mg;           // 0: Jacobi (z = r / d), 1: V-cycle (z = M r)
-  int mg_nlev;      // levels including the lattice itself
-  int mg_small;     // first level handled by the single-block kernel
   void* r;
   void* mg_t0;
   void* mg_w;         // omega / d on the lattice (0 where d = 0)
-  const void* mg_lv;  // device MGLevel[mg_nlev] (entry 0 unused)
+  const void* mg_lv;  // device MGLevel[n_reps][MG_MAXLEV] (level 0 unused)
+  const long long* mg_start;  // [MG_MAXLEV][n_reps + 1] prefix sums of each level's sites over the replicates
+  const int2* mg_rep;         // per replicate: (levels, first single-block level)
   void* reac;    // FP32 scheme: reaction part a of the diagonal d = c n + a
   void* phi;
   void* P;

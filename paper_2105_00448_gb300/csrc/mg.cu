@@ -12,11 +12,14 @@
 // smoother is weighted Jacobi (one sweep before and one after the coarse
 // correction, MG_NU_COARSE sweeps on the coarsest level), so M is symmetric.
 //
-// Level 0 is the solver's padded field layout (replicate 0): rhs = r,
-// iterate = mg_t0, diagonal = d; coarser levels are dense arrays.  Levels of
-// at most MG_SMALL_SITES sites run inside one block (block barriers between
-// sweeps).  The last kernel, the post-smoothing sweep on level 0, also forms
-// rho = r.z with the fixed-order reductions of the CG passes and sets beta.
+// Level 0 is the solver's padded field layout: rhs = r, iterate = mg_t0,
+// diagonal = d; coarser levels are dense arrays, the replicates of a batch
+// concatenated per level (each replicate has its own hierarchy; a per-level
+// prefix table maps a flattened site index to its replicate).  Levels of at
+// most MG_SMALL_SITES sites run inside one block per replicate (block
+// barriers between sweeps).  The last kernel, the post-smoothing sweep on
+// level 0, also forms rho = r.z with the fixed-order reductions of the CG
+// passes and sets beta, per replicate.
 
 #include "hca_internal.cuh"
 #include "row_ops.cuh"
@@ -60,8 +63,8 @@ struct View {
 };
 
 template <typename T>
-__device__ __forceinline__ View<T> view(const Ctx& c, int which, int l) {
-  const RepDesc& rd = c.reps[0];
+__device__ __forceinline__ View<T> view(const Ctx& c, int which, int r, int l) {
+  const RepDesc& rd = c.reps[r];
   View<T> v;
   const T c0 = (T)op_coupling(rd, which);
   if (l == 0) {
@@ -79,7 +82,7 @@ __device__ __forceinline__ View<T> view(const Ctx& c, int which, int l) {
     v.c = c0;
     return v;
   }
-  const MGLevel& L = ((const MGLevel*)c.mg_lv)[l];
+  const MGLevel& L = ((const MGLevel*)c.mg_lv)[r * MG_MAXLEV + l];
   v.nx = L.nx;
   v.ny = L.ny;
   v.nz = L.nz;
@@ -95,87 +98,92 @@ __device__ __forceinline__ View<T> view(const Ctx& c, int which, int l) {
   return v;
 }
 
-// ------------------------------------------------------ per-site steps --
-// d_C(I) = c_C n_C(I) + sum over children of max(0, d_F - c_F n_F)
-template <typename T>
-__device__ void coarse_diag(const View<T>& F, const View<T>& C, long long s0, long long step) {
-  for (long long S = s0; S < C.n(); S += step) {
-    int X, Y, Z;
-    C.coords(S, X, Y, Z);
-    double a = 0.0;
-    for (int k = 0; k < 8; ++k) {
-      const int x = 2 * X + (k & 1), y = 2 * Y + ((k >> 1) & 1), z = 2 * Z + (k >> 2);
-      if (x < F.nx && y < F.ny && z < F.nz)
-        a += fmax(0.0, (double)F.d[F.at(x, y, z)] - (double)F.c * F.nbcount(x, y, z));
-    }
-    const double dc = (double)C.c * C.nbcount(X, Y, Z) + a;
-    C.d[C.at(X, Y, Z)] = (T)dc;
-    C.w[C.at(X, Y, Z)] = dc != 0.0 ? (T)(MG_OMEGA / dc) : T(0);
+// Replicate that owns flattened site q of level l: the last r with
+// start[l][r] <= q (replicates without level l have empty ranges).
+__device__ __forceinline__ int rep_of(const Ctx& c, int l, long long q) {
+  const long long* st = c.mg_start + (long long)l * (c.n_reps + 1);
+  int lo = 0, hi = c.n_reps;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (st[mid] <= q) lo = mid;
+    else hi = mid;
   }
+  return lo;
+}
+
+__device__ __forceinline__ long long rep_start(const Ctx& c, int l, int r) {
+  return c.mg_start[(long long)l * (c.n_reps + 1) + r];
+}
+
+// ------------------------------------------------------ per-site steps --
+// d_C(I) = c_C n_C(I) + sum over children of max(0, d_F - c_F n_F); w_C = omega / d_C
+template <typename T>
+__device__ void coarse_diag_at(const View<T>& F, const View<T>& C, long long S) {
+  int X, Y, Z;
+  C.coords(S, X, Y, Z);
+  double a = 0.0;
+  for (int k = 0; k < 8; ++k) {
+    const int x = 2 * X + (k & 1), y = 2 * Y + ((k >> 1) & 1), z = 2 * Z + (k >> 2);
+    if (x < F.nx && y < F.ny && z < F.nz)
+      a += fmax(0.0, (double)F.d[F.at(x, y, z)] - (double)F.c * F.nbcount(x, y, z));
+  }
+  const double dc = (double)C.c * C.nbcount(X, Y, Z) + a;
+  C.d[C.at(X, Y, Z)] = (T)dc;
+  C.w[C.at(X, Y, Z)] = dc != 0.0 ? (T)(MG_OMEGA / dc) : T(0);
 }
 
 // w = omega / d on the lattice
 template <typename T>
-__device__ void lattice_w(const View<T>& V, long long s0, long long step) {
-  for (long long s = s0; s < V.n(); s += step) {
-    int X, Y, Z;
-    V.coords(s, X, Y, Z);
-    const long long e = V.at(X, Y, Z);
-    const T d = V.d[e];
-    V.w[e] = d != T(0) ? (T)MG_OMEGA / d : T(0);
-  }
+__device__ void lattice_w_at(const View<T>& V, long long s) {
+  int X, Y, Z;
+  V.coords(s, X, Y, Z);
+  const long long e = V.at(X, Y, Z);
+  const T d = V.d[e];
+  V.w[e] = d != T(0) ? (T)MG_OMEGA / d : T(0);
 }
 
 // x = omega rhs / d
 template <typename T>
-__device__ void sweep_first(const View<T>& V, long long s0, long long step) {
-  for (long long s = s0; s < V.n(); s += step) {
-    int X, Y, Z;
-    V.coords(s, X, Y, Z);
-    const long long e = V.at(X, Y, Z);
-    V.x[e] = V.w[e] * V.rhs[e];
-  }
+__device__ void sweep_first_at(const View<T>& V, long long s) {
+  int X, Y, Z;
+  V.coords(s, X, Y, Z);
+  const long long e = V.at(X, Y, Z);
+  V.x[e] = V.w[e] * V.rhs[e];
 }
 
 // dst = src + omega (rhs - A src) / d
 template <typename T>
-__device__ void sweep(const View<T>& V, const T* __restrict__ src, T* __restrict__ dst, long long s0, long long step) {
-  for (long long s = s0; s < V.n(); s += step) {
-    int X, Y, Z;
-    V.coords(s, X, Y, Z);
-    const long long e = V.at(X, Y, Z);
-    const T r = V.rhs[e] - V.apply(src, X, Y, Z, e);
-    dst[e] = src[e] + V.w[e] * r;
-  }
+__device__ void sweep_at(const View<T>& V, const T* __restrict__ src, T* __restrict__ dst, long long s) {
+  int X, Y, Z;
+  V.coords(s, X, Y, Z);
+  const long long e = V.at(X, Y, Z);
+  const T r = V.rhs[e] - V.apply(src, X, Y, Z, e);
+  dst[e] = src[e] + V.w[e] * r;
 }
 
 // rhs_C(I) = sum over children of (rhs_F - A_F x_F)
 template <typename T>
-__device__ void restrict_residual(const View<T>& F, const View<T>& C, long long s0, long long step) {
-  for (long long S = s0; S < C.n(); S += step) {
-    int X, Y, Z;
-    C.coords(S, X, Y, Z);
-    T acc = T(0);
-    for (int k = 0; k < 8; ++k) {
-      const int x = 2 * X + (k & 1), y = 2 * Y + ((k >> 1) & 1), z = 2 * Z + (k >> 2);
-      if (x < F.nx && y < F.ny && z < F.nz) {
-        const long long e = F.at(x, y, z);
-        acc += F.rhs[e] - F.apply(F.x, x, y, z, e);
-      }
+__device__ void restrict_residual_at(const View<T>& F, const View<T>& C, long long S) {
+  int X, Y, Z;
+  C.coords(S, X, Y, Z);
+  T acc = T(0);
+  for (int k = 0; k < 8; ++k) {
+    const int x = 2 * X + (k & 1), y = 2 * Y + ((k >> 1) & 1), z = 2 * Z + (k >> 2);
+    if (x < F.nx && y < F.ny && z < F.nz) {
+      const long long e = F.at(x, y, z);
+      acc += F.rhs[e] - F.apply(F.x, x, y, z, e);
     }
-    C.rhs[C.at(X, Y, Z)] = acc;
   }
+  C.rhs[C.at(X, Y, Z)] = acc;
 }
 
 // t_F = x_F + P x_C
 template <typename T>
-__device__ void prolong(const View<T>& F, const View<T>& C, long long s0, long long step) {
-  for (long long s = s0; s < F.n(); s += step) {
-    int X, Y, Z;
-    F.coords(s, X, Y, Z);
-    const long long e = F.at(X, Y, Z);
-    F.t[e] = F.x[e] + C.x[C.at(X >> 1, Y >> 1, Z >> 1)];
-  }
+__device__ void prolong_at(const View<T>& F, const View<T>& C, long long s) {
+  int X, Y, Z;
+  F.coords(s, X, Y, Z);
+  const long long e = F.at(X, Y, Z);
+  F.t[e] = F.x[e] + C.x[C.at(X >> 1, Y >> 1, Z >> 1)];
 }
 
 // First sweep from zero, evaluated where it is needed: u = omega rhs / d
@@ -187,131 +195,152 @@ __device__ __forceinline__ T u_first(const View<T>& V, long long e) {
 // rhs_C(I) = sum over children of (rhs_F - A_F u), u = omega rhs_F / d_F
 // (the pre-smoothing sweep fused into the restriction; u is not stored)
 template <typename T>
-__device__ void restrict_fused(const View<T>& F, const View<T>& C, long long s0, long long step) {
-  for (long long S = s0; S < C.n(); S += step) {
-    int X, Y, Z;
-    C.coords(S, X, Y, Z);
-    T acc = T(0);
-    for (int k = 0; k < 8; ++k) {
-      const int x = 2 * X + (k & 1), y = 2 * Y + ((k >> 1) & 1), z = 2 * Z + (k >> 2);
-      if (x < F.nx && y < F.ny && z < F.nz) {
-        const long long e = F.at(x, y, z);
-        T nb = T(0);
-        if (x > 0) nb += u_first(F, e - 1);
-        if (x < F.nx - 1) nb += u_first(F, e + 1);
-        if (y > 0) nb += u_first(F, e - F.sy);
-        if (y < F.ny - 1) nb += u_first(F, e + F.sy);
-        if (z > 0) nb += u_first(F, e - F.sz);
-        if (z < F.nz - 1) nb += u_first(F, e + F.sz);
-        acc += F.rhs[e] - (F.d[e] * u_first(F, e) - F.c * nb);
-      }
+__device__ void restrict_fused_at(const View<T>& F, const View<T>& C, long long S) {
+  int X, Y, Z;
+  C.coords(S, X, Y, Z);
+  T acc = T(0);
+  for (int k = 0; k < 8; ++k) {
+    const int x = 2 * X + (k & 1), y = 2 * Y + ((k >> 1) & 1), z = 2 * Z + (k >> 2);
+    if (x < F.nx && y < F.ny && z < F.nz) {
+      const long long e = F.at(x, y, z);
+      T nb = T(0);
+      if (x > 0) nb += u_first(F, e - 1);
+      if (x < F.nx - 1) nb += u_first(F, e + 1);
+      if (y > 0) nb += u_first(F, e - F.sy);
+      if (y < F.ny - 1) nb += u_first(F, e + F.sy);
+      if (z > 0) nb += u_first(F, e - F.sz);
+      if (z < F.nz - 1) nb += u_first(F, e + F.sz);
+      acc += F.rhs[e] - (F.d[e] * u_first(F, e) - F.c * nb);
     }
-    C.rhs[C.at(X, Y, Z)] = acc;
   }
+  C.rhs[C.at(X, Y, Z)] = acc;
 }
 
 // x_F = u + omega (rhs_F - A_F u) / d_F with u = omega rhs_F / d_F + P x_C
 // (prolongation fused into the post-smoothing sweep; u is not stored)
 template <typename T>
-__device__ void post_fused(const View<T>& F, const View<T>& C, long long s0, long long step) {
-  auto u = [&](int x, int y, int z) {
-    return u_first(F, F.at(x, y, z)) + C.x[C.at(x >> 1, y >> 1, z >> 1)];
-  };
-  for (long long s = s0; s < F.n(); s += step) {
-    int X, Y, Z;
-    F.coords(s, X, Y, Z);
-    const long long e = F.at(X, Y, Z);
-    const T d = F.d[e];
-    const T w = F.w[e];
-    T nb = T(0);
-    if (X > 0) nb += u(X - 1, Y, Z);
-    if (X < F.nx - 1) nb += u(X + 1, Y, Z);
-    if (Y > 0) nb += u(X, Y - 1, Z);
-    if (Y < F.ny - 1) nb += u(X, Y + 1, Z);
-    if (Z > 0) nb += u(X, Y, Z - 1);
-    if (Z < F.nz - 1) nb += u(X, Y, Z + 1);
-    const T uc = u(X, Y, Z);
-    F.x[e] = uc + w * (F.rhs[e] - (d * uc - F.c * nb));
-  }
+__device__ void post_fused_at(const View<T>& F, const View<T>& C, long long s) {
+  auto u = [&](int x, int y, int z) { return u_first(F, F.at(x, y, z)) + C.x[C.at(x >> 1, y >> 1, z >> 1)]; };
+  int X, Y, Z;
+  F.coords(s, X, Y, Z);
+  const long long e = F.at(X, Y, Z);
+  const T d = F.d[e];
+  const T w = F.w[e];
+  T nb = T(0);
+  if (X > 0) nb += u(X - 1, Y, Z);
+  if (X < F.nx - 1) nb += u(X + 1, Y, Z);
+  if (Y > 0) nb += u(X, Y - 1, Z);
+  if (Y < F.ny - 1) nb += u(X, Y + 1, Z);
+  if (Z > 0) nb += u(X, Y, Z - 1);
+  if (Z < F.nz - 1) nb += u(X, Y, Z + 1);
+  const T uc = u(X, Y, Z);
+  F.x[e] = uc + w * (F.rhs[e] - (d * uc - F.c * nb));
 }
 
-#define HCA_GRID_STRIDE (blockIdx.x * (long long)blockDim.x + threadIdx.x), ((long long)gridDim.x * blockDim.x)
+// Grid-stride loop over the flattened sites of level l of every replicate
+// (a per-site lookup of the owning replicate in the level's prefix table).
+#define HCA_MG_FOR_SITES(l)                                                                           \
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;                               \
+       q < c.mg_start[(long long)(l) * (c.n_reps + 1) + c.n_reps]; q += (long long)gridDim.x * blockDim.x)
 
 // ------------------------------------------------------- grid kernels ---
 template <typename T>
 __global__ void __launch_bounds__(kMgThreads) k_mg_w0(Ctx c, int which) {
   HCA_COUNT_KERNEL(c);
-  lattice_w<T>(view<T>(c, which, 0), HCA_GRID_STRIDE);
+  HCA_MG_FOR_SITES(0) {
+    const int r = rep_of(c, 0, q);
+    lattice_w_at<T>(view<T>(c, which, r, 0), q - rep_start(c, 0, r));
+  }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kMgThreads) k_mg_diag(Ctx c, int which, int l) {
   HCA_COUNT_KERNEL(c);
-  coarse_diag<T>(view<T>(c, which, l - 1), view<T>(c, which, l), HCA_GRID_STRIDE);
+  HCA_MG_FOR_SITES(l) {
+    const int r = rep_of(c, l, q);
+    coarse_diag_at<T>(view<T>(c, which, r, l - 1), view<T>(c, which, r, l), q - rep_start(c, l, r));
+  }
 }
 
 // The defect-correction residual is stored unscaled: on the first
 // application of a rescaled inner solve, r *= scale (elementwise, in place);
-// otherwise the kernel returns at once.
+// replicates past that return at once.
 template <typename T>
 __global__ void __launch_bounds__(kMgThreads) k_mg_scale0(Ctx c, int which) {
   HCA_COUNT_KERNEL(c);
-  const RepSolve& sv = c.solve[0];
-  if (sv.iters != 0 || sv.scale == 1.0) return;
-  const T sc = (T)sv.scale;
-  const View<T> V = view<T>(c, which, 0);
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < V.n(); q += (long long)gridDim.x * blockDim.x) {
+  HCA_MG_FOR_SITES(0) {
+    const int r = rep_of(c, 0, q);
+    const RepSolve& sv = c.solve[r];
+    if (sv.iters != 0 || sv.scale == 1.0) continue;
+    const View<T> V = view<T>(c, which, r, 0);
     int X, Y, Z;
-    V.coords(q, X, Y, Z);
-    V.rhs[V.at(X, Y, Z)] *= sc;
+    V.coords(q - rep_start(c, 0, r), X, Y, Z);
+    V.rhs[V.at(X, Y, Z)] *= (T)sv.scale;
   }
 }
 
-// level 0 as the coarsest level: t0 = omega r / d
+// The lattice as the coarsest level (single replicate): t0 = omega r / d
 template <typename T>
 __global__ void __launch_bounds__(kMgThreads) k_mg_first0(Ctx c, int which) {
   HCA_COUNT_KERNEL(c);
-  sweep_first<T>(view<T>(c, which, 0), HCA_GRID_STRIDE);
+  const View<T> V = view<T>(c, which, 0, 0);
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < V.n(); s += (long long)gridDim.x * blockDim.x)
+    sweep_first_at<T>(V, s);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kMgThreads) k_mg_sweep(Ctx c, int which, int l, const T* src, T* dst) {
+__global__ void __launch_bounds__(kMgThreads) k_mg_sweep0(Ctx c, int which, const T* src, T* dst) {
   HCA_COUNT_KERNEL(c);
-  sweep<T>(view<T>(c, which, l), src, dst, HCA_GRID_STRIDE);
+  const View<T> V = view<T>(c, which, 0, 0);
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < V.n(); s += (long long)gridDim.x * blockDim.x)
+    sweep_at<T>(V, src, dst, s);
 }
 
+// Restriction from level l to l + 1 for the replicates whose level l is
+// swept by grid kernels (l < their first single-block level)
 template <typename T>
 __global__ void __launch_bounds__(kMgThreads) k_mg_restrict(Ctx c, int which, int l) {
   HCA_COUNT_KERNEL(c);
-  restrict_fused<T>(view<T>(c, which, l), view<T>(c, which, l + 1), HCA_GRID_STRIDE);
+  HCA_MG_FOR_SITES(l + 1) {
+    const int r = rep_of(c, l + 1, q);
+    if (l >= c.mg_rep[r].y) continue;
+    restrict_fused_at<T>(view<T>(c, which, r, l), view<T>(c, which, r, l + 1), q - rep_start(c, l + 1, r));
+  }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kMgThreads) k_mg_post(Ctx c, int which, int l) {
   HCA_COUNT_KERNEL(c);
-  post_fused<T>(view<T>(c, which, l), view<T>(c, which, l + 1), HCA_GRID_STRIDE);
+  HCA_MG_FOR_SITES(l) {
+    const int r = rep_of(c, l, q);
+    if (l >= c.mg_rep[r].y) continue;
+    post_fused_at<T>(view<T>(c, which, r, l), view<T>(c, which, r, l + 1), q - rep_start(c, l, r));
+  }
 }
 
-// The whole sub-cycle of levels l0 .. nlev-1 in one block.
+// The whole sub-cycle of one replicate's levels small .. nlev-1 in one block
+// (block r = replicate r).
 template <typename T>
-__global__ void __launch_bounds__(kSmallThreads) k_mg_small(Ctx c, int which, int l0) {
+__global__ void __launch_bounds__(kSmallThreads) k_mg_small(Ctx c, int which) {
   HCA_COUNT_KERNEL(c);
-  const int last = c.mg_nlev - 1;
+  const int r = blockIdx.x;
+  const int l0 = c.mg_rep[r].y, last = c.mg_rep[r].x - 1;
   const long long s0 = threadIdx.x, st = blockDim.x;
   for (int l = l0; l < last; ++l) {
-    const View<T> V = view<T>(c, which, l);
-    sweep_first<T>(V, s0, st);
+    const View<T> V = view<T>(c, which, r, l);
+    for (long long s = s0; s < V.n(); s += st) sweep_first_at<T>(V, s);
     __syncthreads();
-    restrict_residual<T>(V, view<T>(c, which, l + 1), s0, st);
+    const View<T> C = view<T>(c, which, r, l + 1);
+    for (long long s = s0; s < C.n(); s += st) restrict_residual_at<T>(V, C, s);
     __syncthreads();
   }
   {
-    const View<T> V = view<T>(c, which, last);
-    sweep_first<T>(V, s0, st);
+    const View<T> V = view<T>(c, which, r, last);
+    for (long long s = s0; s < V.n(); s += st) sweep_first_at<T>(V, s);
     __syncthreads();
     for (int k = 1; k < MG_NU_COARSE; ++k) {
       const bool odd = k & 1;
-      sweep<T>(V, odd ? V.x : V.t, odd ? V.t : V.x, s0, st);
+      for (long long s = s0; s < V.n(); s += st) sweep_at<T>(V, odd ? V.x : V.t, odd ? V.t : V.x, s);
       __syncthreads();
     }
     if ((MG_NU_COARSE & 1) == 0) {   // the last sweep wrote t
@@ -320,10 +349,11 @@ __global__ void __launch_bounds__(kSmallThreads) k_mg_small(Ctx c, int which, in
     }
   }
   for (int l = last - 1; l >= l0; --l) {
-    const View<T> V = view<T>(c, which, l);
-    prolong<T>(V, view<T>(c, which, l + 1), s0, st);
+    const View<T> V = view<T>(c, which, r, l);
+    const View<T> C = view<T>(c, which, r, l + 1);
+    for (long long s = s0; s < V.n(); s += st) prolong_at<T>(V, C, s);
     __syncthreads();
-    sweep<T>(V, V.t, V.x, s0, st);
+    for (long long s = s0; s < V.n(); s += st) sweep_at<T>(V, V.t, V.x, s);
     __syncthreads();
   }
 }
@@ -348,7 +378,7 @@ __global__ void __maxnreg__(96) k_mg_post0(Ctx c, int which, const T* __restrict
   const T* __restrict__ x1 = nullptr;
   int nx1 = 0, ny1 = 0;
   if (PROLONG) {
-    const MGLevel& L1 = ((const MGLevel*)c.mg_lv)[1];
+    const MGLevel& L1 = ((const MGLevel*)c.mg_lv)[ch.x * MG_MAXLEV + 1];
     x1 = (const T*)L1.x;
     nx1 = L1.nx;
     ny1 = L1.ny;
@@ -451,30 +481,30 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part) {
   cudaStream_t s = c.stream;
   T* t0 = (T*)c.mg_t0;
   T* z = (T*)c.z;
-  const long long n0 = H.n0;
   const bool all = part < 0;
   if (H.nlev == 1) {
     if (!all && part != 0) return;
-    // the lattice is the coarsest level: MG_NU_COARSE sweeps, the last one in post0
-    k_mg_scale0<T><<<grid_for(n0), kMgThreads, 0, s>>>(c, which);
-    k_mg_first0<T><<<grid_for(n0), kMgThreads, 0, s>>>(c, which);
+    // the lattice is the coarsest level (single replicate): MG_NU_COARSE
+    // sweeps, the last one in post0
+    k_mg_scale0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, s>>>(c, which);
+    k_mg_first0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, s>>>(c, which);
     for (int k = 1; k < MG_NU_COARSE - 1; ++k) {
       const bool odd = k & 1;
-      k_mg_sweep<T><<<grid_for(n0), kMgThreads, 0, s>>>(c, which, 0, odd ? t0 : z, odd ? z : t0);
+      k_mg_sweep0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, s>>>(c, which, odd ? t0 : z, odd ? z : t0);
     }
     const T* src = ((MG_NU_COARSE - 2) & 1) ? z : t0;
     k_mg_post0<T, false, 0><<<c.n_chunks, c.threads, 0, s>>>(c, which, src);
     return;
   }
   if (all || part == 0) {
-    k_mg_scale0<T><<<grid_for(n0), kMgThreads, 0, s>>>(c, which);
-    k_mg_restrict<T><<<grid_for(H.lv[1].n), kMgThreads, 0, s>>>(c, which, 0);
+    k_mg_scale0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, s>>>(c, which);
+    k_mg_restrict<T><<<grid_for(H.ntot[1]), kMgThreads, 0, s>>>(c, which, 0);
   }
   if (all || part == 1) {
     for (int l = 1; l < H.small; ++l)
-      k_mg_restrict<T><<<grid_for(H.lv[l + 1].n), kMgThreads, 0, s>>>(c, which, l);
-    k_mg_small<T><<<1, kSmallThreads, 0, s>>>(c, which, H.small);
-    for (int l = H.small - 1; l >= 1; --l) k_mg_post<T><<<grid_for(H.lv[l].n), kMgThreads, 0, s>>>(c, which, l);
+      k_mg_restrict<T><<<grid_for(H.ntot[l + 1]), kMgThreads, 0, s>>>(c, which, l);
+    k_mg_small<T><<<c.n_reps, kSmallThreads, 0, s>>>(c, which);
+    for (int l = H.small - 1; l >= 1; --l) k_mg_post<T><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
   }
   if (all || part == 2) {
     switch (H.ni) {
@@ -488,13 +518,14 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part) {
 
 template <typename T>
 void mg_setup_t(const Ctx& c, int which, const MGHost& H) {
-  k_mg_w0<T><<<grid_for(H.n0), kMgThreads, 0, c.stream>>>(c, which);
-  for (int l = 1; l < H.nlev; ++l) k_mg_diag<T><<<grid_for(H.lv[l].n), kMgThreads, 0, c.stream>>>(c, which, l);
+  k_mg_w0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, c.stream>>>(c, which);
+  for (int l = 1; l < H.nlev; ++l) k_mg_diag<T><<<grid_for(H.ntot[l]), kMgThreads, 0, c.stream>>>(c, which, l);
 }
 
 }  // namespace
 
 int vcycle_launches(const MGHost& H) { return H.nlev == 1 ? MG_NU_COARSE + 1 : 2 * H.small + 2; }
+// (H.small: the deepest grid-kernel level + 1 over the batch)
 
 void launch_mg_setup(const Ctx& c, int which, bool fp64, const MGHost& H) {
   if (fp64) mg_setup_t<double>(c, which, H);

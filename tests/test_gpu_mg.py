@@ -185,7 +185,16 @@ def test_mg_edge_cases():
     sim.step(1)
     assert sim.stats()["o2_rel_residual"] <= 2e-10
     sim.close()
-    # batches and the Jacobi-only entry point
+    # a batch needs a coarse level in every replicate (a 6x6x6 lattice has none)
+    cfgs, maps = [], []
+    for n in (16, 6):
+        m = [np.full((n, n, n), 0.5, dtype=np.float32)] * 3
+        maps.append(m)
+        cfgs.append(hca.make_config(n, n, n, preconditioner=hca.HCA_PC_MG))
+    with pytest.raises(hca.HcaError) as e:
+        hca.Sim(cfgs, maps, batch=True)
+    assert e.value.status == hca.HCA_ERR_UNIMPLEMENTED
+    # an invalid preconditioner and the Jacobi-only entry point
     with pytest.raises(hca.HcaError) as e:
         sim = hca.Sim.create(8, 8, 8, *[np.full((8, 8, 8), 0.5, dtype=np.float32)] * 3, preconditioner=7)
     assert e.value.status == hca.HCA_ERR_ARG

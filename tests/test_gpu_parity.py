@@ -359,11 +359,13 @@ def test_errors_are_reported():
     sim.close()
 
 
+@pytest.mark.parametrize("pc", [0, 1])
 @pytest.mark.parametrize("precision", ["f64", "f32"])
-def test_batch_equals_single_replicates(precision):
-    # uneven lattices, distinct seeds and maps, one launch per kernel for all
+def test_batch_equals_single_replicates(precision, pc):
+    # uneven lattices, distinct seeds and maps, one launch per kernel for all;
+    # pc = 1: every replicate has its own multigrid hierarchy
     shapes = [(12, 16, 20), (8, 9, 13), (16, 16, 16)]
-    params = dict(n_drugs=2, rtol_o2=1e-8, rtol_drug=1e-8, picard_tol=1e-7)
+    params = dict(n_drugs=2, rtol_o2=1e-8, rtol_drug=1e-8, picard_tol=1e-7, preconditioner=pc)
     cfgs, maps = [], []
     for r, (nz, ny, nx) in enumerate(shapes):
         m = make_maps(nx, ny, nz, corr_len=3.0, seed=100 + r)
