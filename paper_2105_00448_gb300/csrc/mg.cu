@@ -115,6 +115,25 @@ __device__ __forceinline__ long long rep_start(const Ctx& c, int l, int r) {
   return c.mg_start[(long long)l * (c.n_reps + 1) + r];
 }
 
+// The replicate of the flattened sites a thread visits, with its views on
+// levels l and l + 1, refreshed only when a site falls outside the cached
+// replicate's range (a thread's consecutive sites nearly always share one).
+template <typename T>
+struct RepCursor {
+  int r = -1;
+  long long lo = 0, hi = 0;
+  View<T> F, C;
+  __device__ __forceinline__ bool at(const Ctx& c, int which, int l, long long q, bool coarse) {
+    if (q >= lo && q < hi) return false;
+    r = rep_of(c, l, q);
+    lo = rep_start(c, l, r);
+    hi = rep_start(c, l, r + 1);
+    F = view<T>(c, which, r, l);
+    if (coarse) C = view<T>(c, which, r, l + 1);
+    return true;
+  }
+};
+
 // ------------------------------------------------------ per-site steps --
 // d_C(I) = c_C n_C(I) + sum over children of max(0, d_F - c_F n_F); w_C = omega / d_C
 template <typename T>
@@ -247,18 +266,21 @@ __device__ void post_fused_at(const View<T>& F, const View<T>& C, long long s) {
 template <typename T>
 __global__ void __launch_bounds__(kMgThreads) k_mg_w0(Ctx c, int which) {
   HCA_COUNT_KERNEL(c);
+  RepCursor<T> k;
   HCA_MG_FOR_SITES(0) {
-    const int r = rep_of(c, 0, q);
-    lattice_w_at<T>(view<T>(c, which, r, 0), q - rep_start(c, 0, r));
+    k.at(c, which, 0, q, false);
+    lattice_w_at<T>(k.F, q - k.lo);
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kMgThreads) k_mg_diag(Ctx c, int which, int l) {
   HCA_COUNT_KERNEL(c);
+  RepCursor<T> k;
+  View<T> Fm;
   HCA_MG_FOR_SITES(l) {
-    const int r = rep_of(c, l, q);
-    coarse_diag_at<T>(view<T>(c, which, r, l - 1), view<T>(c, which, r, l), q - rep_start(c, l, r));
+    if (k.at(c, which, l, q, false)) Fm = view<T>(c, which, k.r, l - 1);
+    coarse_diag_at<T>(Fm, k.F, q - k.lo);
   }
 }
 
@@ -268,14 +290,19 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_diag(Ctx c, int which, int l)
 template <typename T>
 __global__ void __launch_bounds__(kMgThreads) k_mg_scale0(Ctx c, int which) {
   HCA_COUNT_KERNEL(c);
+  RepCursor<T> k;
+  bool skip = true;
+  T sc = T(1);
   HCA_MG_FOR_SITES(0) {
-    const int r = rep_of(c, 0, q);
-    const RepSolve& sv = c.solve[r];
-    if (sv.iters != 0 || sv.scale == 1.0) continue;
-    const View<T> V = view<T>(c, which, r, 0);
+    if (k.at(c, which, 0, q, false)) {
+      const RepSolve& sv = c.solve[k.r];
+      skip = sv.iters != 0 || sv.scale == 1.0;
+      sc = (T)sv.scale;
+    }
+    if (skip) continue;
     int X, Y, Z;
-    V.coords(q - rep_start(c, 0, r), X, Y, Z);
-    V.rhs[V.at(X, Y, Z)] *= (T)sv.scale;
+    k.F.coords(q - k.lo, X, Y, Z);
+    k.F.rhs[k.F.at(X, Y, Z)] *= sc;
   }
 }
 
@@ -297,24 +324,45 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_sweep0(Ctx c, int which, cons
 }
 
 // Restriction from level l to l + 1 for the replicates whose level l is
-// swept by grid kernels (l < their first single-block level)
-template <typename T>
+// swept by grid kernels (l < their first single-block level).  MULTI = false:
+// one replicate, whose views are fixed for the whole kernel (fewer registers).
+template <typename T, bool MULTI>
 __global__ void __launch_bounds__(kMgThreads) k_mg_restrict(Ctx c, int which, int l) {
   HCA_COUNT_KERNEL(c);
+  if (!MULTI) {
+    const View<T> F = view<T>(c, which, 0, l), C = view<T>(c, which, 0, l + 1);
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < C.n(); s += (long long)gridDim.x * blockDim.x)
+      restrict_fused_at<T>(F, C, s);
+    return;
+  }
+  RepCursor<T> k;   // cursor on level l + 1 (its F is the coarse view)
+  View<T> Ff;
+  bool skip = true;
   HCA_MG_FOR_SITES(l + 1) {
-    const int r = rep_of(c, l + 1, q);
-    if (l >= c.mg_rep[r].y) continue;
-    restrict_fused_at<T>(view<T>(c, which, r, l), view<T>(c, which, r, l + 1), q - rep_start(c, l + 1, r));
+    if (k.at(c, which, l + 1, q, false)) {
+      skip = l >= c.mg_rep[k.r].y;
+      Ff = view<T>(c, which, k.r, l);
+    }
+    if (skip) continue;
+    restrict_fused_at<T>(Ff, k.F, q - k.lo);
   }
 }
 
-template <typename T>
+template <typename T, bool MULTI>
 __global__ void __launch_bounds__(kMgThreads) k_mg_post(Ctx c, int which, int l) {
   HCA_COUNT_KERNEL(c);
+  if (!MULTI) {
+    const View<T> F = view<T>(c, which, 0, l), C = view<T>(c, which, 0, l + 1);
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < F.n(); s += (long long)gridDim.x * blockDim.x)
+      post_fused_at<T>(F, C, s);
+    return;
+  }
+  RepCursor<T> k;
+  bool skip = true;
   HCA_MG_FOR_SITES(l) {
-    const int r = rep_of(c, l, q);
-    if (l >= c.mg_rep[r].y) continue;
-    post_fused_at<T>(view<T>(c, which, r, l), view<T>(c, which, r, l + 1), q - rep_start(c, l, r));
+    if (k.at(c, which, l, q, true)) skip = l >= c.mg_rep[k.r].y;
+    if (skip) continue;
+    post_fused_at<T>(k.F, k.C, q - k.lo);
   }
 }
 
@@ -482,6 +530,7 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part) {
   T* t0 = (T*)c.mg_t0;
   T* z = (T*)c.z;
   const bool all = part < 0;
+  const bool multi = c.n_reps > 1;
   if (H.nlev == 1) {
     if (!all && part != 0) return;
     // the lattice is the coarsest level (single replicate): MG_NU_COARSE
@@ -498,13 +547,19 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part) {
   }
   if (all || part == 0) {
     k_mg_scale0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, s>>>(c, which);
-    k_mg_restrict<T><<<grid_for(H.ntot[1]), kMgThreads, 0, s>>>(c, which, 0);
+    if (multi) k_mg_restrict<T, true><<<grid_for(H.ntot[1]), kMgThreads, 0, s>>>(c, which, 0);
+    else k_mg_restrict<T, false><<<grid_for(H.ntot[1]), kMgThreads, 0, s>>>(c, which, 0);
   }
   if (all || part == 1) {
-    for (int l = 1; l < H.small; ++l)
-      k_mg_restrict<T><<<grid_for(H.ntot[l + 1]), kMgThreads, 0, s>>>(c, which, l);
+    for (int l = 1; l < H.small; ++l) {
+      if (multi) k_mg_restrict<T, true><<<grid_for(H.ntot[l + 1]), kMgThreads, 0, s>>>(c, which, l);
+      else k_mg_restrict<T, false><<<grid_for(H.ntot[l + 1]), kMgThreads, 0, s>>>(c, which, l);
+    }
     k_mg_small<T><<<c.n_reps, kSmallThreads, 0, s>>>(c, which);
-    for (int l = H.small - 1; l >= 1; --l) k_mg_post<T><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
+    for (int l = H.small - 1; l >= 1; --l) {
+      if (multi) k_mg_post<T, true><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
+      else k_mg_post<T, false><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
+    }
   }
   if (all || part == 2) {
     switch (H.ni) {
