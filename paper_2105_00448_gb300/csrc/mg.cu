@@ -448,41 +448,58 @@ __global__ void __maxnreg__(96) k_mg_post0(Ctx c, int which, const T* __restrict
       const int g = itn * it.lpr + it.sl;
       const bool gok = row_ok && g < rd.gpr;
       const long long e = geo.base + 4LL * g;
-      // u on the 4-site group of row (yy, zq) that starts at element er
-      auto urow = [&](long long er, bool ok, int yy, int zq) {
-        if (!PROLONG) return ld4_if(src + er, ok);
-        V4<T> u = zero4<T>();
-        if (!ok) return u;
-        const V4<T> R = ld4(rr + er), W = ld4(ww + er);
-        const long long cb = ((long long)(zq >> 1) * ny1 + (yy >> 1)) * nx1 + 2LL * g;
-        const T c0 = x1[cb];
-        const T c1 = 4 * g + 2 < rd.nx ? x1[cb + 1] : T(0);
+      // u on the group and on the same group of the four neighbour rows.  All
+      // loads of the group are issued (predicated) before any value is used,
+      // so a group costs one memory round trip
+      const bool rok[5] = {gok, gok && geo.ym, gok && geo.yp, gok && geo.zm, gok && geo.zp};
+      const long long roff[5] = {0, -geo.sy, geo.sy, -geo.sz, geo.sz};
+      const int ry[5] = {y, y - 1, y + 1, y, y};
+      const int rz[5] = {z, z, z, z - 1, z + 1};
+      V4<T> RR[5], WW[5];
+      T C0[5], C1[5];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (4 * g + k < rd.nx && W.a[k] != T(0)) u.a[k] = W.a[k] * R.a[k] + (k < 2 ? c0 : c1);
-        return u;
-      };
-      const V4<T> U = urow(e, gok, y, z);
-      const V4<T> ym = urow(e - geo.sy, gok && geo.ym, y - 1, z);
-      const V4<T> yp = urow(e + geo.sy, gok && geo.yp, y + 1, z);
-      const V4<T> zm = urow(e - geo.sz, gok && geo.zm, y, z - 1);
-      const V4<T> zp = urow(e + geo.sz, gok && geo.zp, y, z + 1);
-      const V4<T> R = ld4_if(rr + e, gok);
-      const V4<T> D = ld4_if(dd + e, gok);
-      const V4<T> W = ld4_if(ww + e, gok);
-      // u at the site after the group, for the segment's last lane, loaded
-      // with the rest of the group's values
-      const bool last_lane = it.sl == it.lpr - 1 && gok && g + 1 < rd.gpr;
-      T un = T(0);
-      if (last_lane) {
-        if (!PROLONG) {
-          un = src[e + 4];
+      for (int q = 0; q < 5; ++q) {
+        if (PROLONG) {
+          RR[q] = ld4_if(rr + e + roff[q], rok[q]);
+          WW[q] = ld4_if(ww + e + roff[q], rok[q]);
+          const long long cb = rok[q] ? ((long long)(rz[q] >> 1) * ny1 + (ry[q] >> 1)) * nx1 + 2LL * g : 0;
+          C0[q] = rok[q] ? x1[cb] : T(0);
+          C1[q] = (rok[q] && 4 * g + 2 < rd.nx) ? x1[cb + 1] : T(0);
         } else {
-          const T wn = ww[e + 4];
-          const long long cb = ((long long)(z >> 1) * ny1 + (y >> 1)) * nx1 + 2LL * g + 2;
-          un = wn != T(0) ? wn * rr[e + 4] + x1[cb] : T(0);
+          RR[q] = ld4_if(src + e + roff[q], rok[q]);
         }
       }
+      const V4<T> D = ld4_if(dd + e, gok);
+      // u at the site after the group, for the segment's last lane
+      const bool last_lane = it.sl == it.lpr - 1 && gok && g + 1 < rd.gpr;
+      T un = T(0);
+      if (PROLONG) {
+        const T wn = last_lane ? ww[e + 4] : T(0);
+        const T rn = last_lane ? rr[e + 4] : T(0);
+        const T cn = last_lane ? x1[((long long)(z >> 1) * ny1 + (y >> 1)) * nx1 + 2LL * g + 2] : T(0);
+        un = wn != T(0) ? wn * rn + cn : T(0);
+      } else {
+        un = last_lane ? src[e + 4] : T(0);
+      }
+      V4<T> UU[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        if (PROLONG) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            UU[q].a[k] = (4 * g + k < rd.nx && WW[q].a[k] != T(0)) ? WW[q].a[k] * RR[q].a[k] + (k < 2 ? C0[q] : C1[q])
+                                                                    : T(0);
+        } else {
+          UU[q] = RR[q];
+        }
+      }
+      const V4<T>& U = UU[0];
+      const V4<T>& ym = UU[1];
+      const V4<T>& yp = UU[2];
+      const V4<T>& zm = UU[3];
+      const V4<T>& zp = UU[4];
+      const V4<T> R = PROLONG ? RR[0] : ld4_if(rr + e, gok);
+      const V4<T> W = PROLONG ? WW[0] : ld4_if(ww + e, gok);
       T left, right;
       x_neighbours(U, g, rd.gpr, it.sl, it.lpr, gok, carry, left, right, [&] { return un; });
       if (gok) {
