@@ -77,9 +77,16 @@ __device__ __forceinline__ T p53_at(T P0, T lam, T s, T k1) {
   return lam != T(0) ? P0 * t_exp(-lam * s) - k1 * t_expm1(-lam * s) / lam : P0 + k1 * s;
 }
 
+// Per-cell ODEs over one chunk of rows.  A warp packs the consuming sites of
+// its 32 four-site groups into a shared-memory list and its lanes take the
+// list's entries in turn, so the 60-substep RK4 keeps every lane busy
+// whatever the mix of cells and empty sites (each site's arithmetic is
+// unchanged).
 template <typename T>
 __global__ void __launch_bounds__(512) k_ode(Ctx c) {
   HCA_COUNT_KERNEL(c);
+  constexpr int kMaxWarps = 16;
+  __shared__ long long s_site[kMaxWarps][128];
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
   const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
@@ -92,31 +99,52 @@ __global__ void __launch_bounds__(512) k_ode(Ctx c) {
   const T h = (T)(rd.dt / nsub);
   const T half = T(0.5) * h;
   const T sixth = h / T(6);
-  for (int gi = threadIdx.x; gi < ngroups; gi += blockDim.x) {
-    const int rl = gi / rd.gpr, g = gi % rd.gpr;
-    const long long e = base0 + (long long)rl * rd.nxp + 4LL * g;
-    const uchar4 st = ld_state4(c.state + e);
-    if (!(is_consumer(st.x) || is_consumer(st.y) || is_consumer(st.z) || is_consumer(st.w))) continue;
-    const V4<T> K = ld4((const T*)c.K + e);
-    V4<T> phi = ld4((const T*)c.phi + e);
-    V4<T> P = ld4((const T*)c.P + e);
-    V4<T> V = ld4((const T*)c.Vc + e);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const T* __restrict__ KK = (const T*)c.K;
+  T* __restrict__ PHI = (T*)c.phi;
+  T* __restrict__ PP = (T*)c.P;
+  T* __restrict__ VV = (T*)c.Vc;
+  for (int gbase = 0; gbase < ngroups; gbase += blockDim.x) {
+    const int gi = gbase + threadIdx.x;
+    unsigned live = 0;
+    long long e = 0;
+    if (gi < ngroups) {
+      const int rl = gi / rd.gpr, g = gi % rd.gpr;
+      e = base0 + (long long)rl * rd.nxp + 4LL * g;
+      const uchar4 st = ld_state4(c.state + e);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const uint8_t s = st_at(st, k);
-      if (!is_consumer(s) || 4 * g + k >= rd.nx) continue;
-      const T Kk = K.a[k];
-      if (is_cancer(s)) phi.a[k] = phi.a[k] + dt * Kk / (Tc * (Kphi + Kk));
+      for (int k = 0; k < 4; ++k)
+        if (is_consumer(st_at(st, k)) && 4 * g + k < rd.nx) live |= 1u << k;
+    }
+    // exclusive prefix of the live counts over the warp's lanes
+    const int cnt = __popc(live);
+    int pre = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, pre, o);
+      if (lane >= o) pre += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, pre, 31);
+    pre -= cnt;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (live >> k & 1u) s_site[wid][pre++] = e + k;
+    __syncwarp();
+    for (int j = lane; j < total; j += 32) {
+      const long long q = s_site[wid][j];
+      const uint8_t s = c.state[q];
+      const T Kk = KK[q];
+      if (is_cancer(s)) PHI[q] = PHI[q] + dt * Kk / (Tc * (Kphi + Kk));
       const T lam = k1p * Kk / (Kp53 + Kk);
       const T decay = k2p * Kk / (KV + Kk);
-      const T P0 = P.a[k];
+      const T P0 = PP[q];
       // P(s) = P0 e^{-lam s} + k1 (1 - e^{-lam s}) / lam = P0 + expm1(-lam s) (P0 - k1 / lam):
       // one transcendental per stage time; the end of a substep is the start
       // of the next, so two evaluations per substep
       const bool has_lam = lam != T(0);
       const T A0 = has_lam ? P0 - k1 / lam : T(0);
-      auto P_at = [&](T s) { return has_lam ? P0 + t_expm1(-lam * s) * A0 : P0 + k1 * s; };
-      T v = V.a[k];
+      auto P_at = [&](T t) { return has_lam ? P0 + t_expm1(-lam * t) * A0 : P0 + k1 * t; };
+      T v = VV[q];
       T Pa = P0;
       for (int m = 0; m < nsub; ++m) {
         const T s0 = (T)m * h;
@@ -132,12 +160,10 @@ __global__ void __launch_bounds__(512) k_ode(Ctx c) {
         v = v + sixth * (f1 + T(2) * f2 + T(2) * f3 + f4);
         Pa = Pc;
       }
-      V.a[k] = v;
-      P.a[k] = p53_at(P0, lam, dt, k1);
+      VV[q] = v;
+      PP[q] = p53_at(P0, lam, dt, k1);
     }
-    st4((T*)c.phi + e, phi);
-    st4((T*)c.P + e, P);
-    st4((T*)c.Vc + e, V);
+    __syncwarp();
   }
 }
 

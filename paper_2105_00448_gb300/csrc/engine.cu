@@ -30,9 +30,9 @@ void launch_advance_step(const Ctx& c, long long by);
 void launch_ca_compact(const Ctx& c, bool fp64);
 void launch_ca_colour(const Ctx& c, int colour, int blocks_x, bool fp64);
 void launch_mg_setup(const Ctx& c, int which, bool fp64, const MGHost& H);
-void launch_vcycle(const Ctx& c, int which, bool fp64, const MGHost& H, int part);
-int vcycle_launches(const MGHost& H);
-int vcycle_part_launches(const MGHost& H, int part);
+void launch_vcycle(const Ctx& c, int which, bool fp64, const MGHost& H, int part, bool scale);
+int vcycle_launches(const MGHost& H, bool scale);
+int vcycle_part_launches(const MGHost& H, int part, bool scale);
 }  // namespace hca
 
 using hca::Ctx;
@@ -289,21 +289,25 @@ void pass_b(hca_handle* h, int which, void* x, hca::CondArg cnd) {
   hca::launch_pass_b(h->ctx, which, x, h->fp64, cnd);
 }
 
-// z = M r (V-cycle); also sets rho and beta for the next pass A
-void vcycle(hca_handle* h, int which) { hca::launch_vcycle(h->ctx, which, h->fp64, h->mgh, -1); }
+// z = M r (V-cycle); also sets rho and beta for the next pass A.  first: the
+// residual was just formed (start of a solve or a defect-correction sweep),
+// so it may still need its power-of-two scaling.
+void vcycle(hca_handle* h, int which, bool first) {
+  hca::launch_vcycle(h->ctx, which, h->fp64, h->mgh, -1, first);
+}
 
 // The V-cycle from the host loop: with the profiler on, its lattice-level
 // kernels are timed as classes of their own.
-int vcycle_host(hca_handle* h, int which) {
+int vcycle_host(hca_handle* h, int which, bool first) {
   if (!h->prof.on) {
-    HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.launches, vcycle(h, which));
+    HCA_LAUNCH(h, HCA_KCLASS_MG, hca::vcycle_launches(h->mgh, first), vcycle(h, which, first));
     return HCA_OK;
   }
   const hca::MGHost& H = h->mgh;
   const int cls[3] = {HCA_KCLASS_MG_RESTRICT0, HCA_KCLASS_MG, HCA_KCLASS_MG_POST0};
   for (int part = 0; part < 3; ++part) {
-    const int n = hca::vcycle_part_launches(H, part);
-    if (n) HCA_LAUNCH(h, cls[part], n, hca::launch_vcycle(h->ctx, which, h->fp64, H, part));
+    const int n = hca::vcycle_part_launches(H, part, first);
+    if (n) HCA_LAUNCH(h, cls[part], n, hca::launch_vcycle(h->ctx, which, h->fp64, H, part, first));
   }
   return HCA_OK;
 }
@@ -330,7 +334,7 @@ int pcg_iterate(hca_handle* h, int which, void* x, int predict) {
       HCA_LAUNCH(h, HCA_KCLASS_PASS_A, 1, pass_a(h, which));
       HCA_LAUNCH(h, HCA_KCLASS_PASS_B, 1, pass_b(h, which, x, kNoCond));
       if (h->mg) {
-        const int rc = vcycle_host(h, which);
+        const int rc = vcycle_host(h, which, false);
         if (rc) return rc;
       }
     }
@@ -350,7 +354,7 @@ int solve_plain(hca_handle* h, int which) {
   HCA_LAUNCH(h, HCA_KCLASS_SETUP, 1, hca::launch_setup(c, which, h->fp64, kNoCond));
   if (h->mg) {
     HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.nlev, mg_setup(h, which));
-    const int rv = vcycle_host(h, which);
+    const int rv = vcycle_host(h, which, true);
     if (rv) return rv;
   }
   int rc = pcg_iterate(h, which, x, h->prev_inner[which][0]);
@@ -374,7 +378,7 @@ int solve_dc(hca_handle* h, int which) {
                hca::launch_dc_residual(c, which, xh, xl, outer == 0, kNoCond, kNoCond));
     if (h->mg) {
       if (outer == 0) HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.nlev, mg_setup(h, which));
-      const int rv = vcycle_host(h, which);
+      const int rv = vcycle_host(h, which, true);
       if (rv) return rv;
     }
     HCA_TRY(cudaMemcpyAsync(h->h_pinned, &c.sync->active_count, 2 * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
@@ -470,7 +474,7 @@ int cap_solve(hca_handle* h, int which, cudaGraph_t G) {
     hca::launch_setup(c, which, h->fp64, cnd);
     if (h->mg) {
       mg_setup(h, which);
-      vcycle(h, which);
+      vcycle(h, which, true);
     }
     HCA_TRY(cudaGetLastError());
     cudaGraph_t body;
@@ -479,7 +483,7 @@ int cap_solve(hca_handle* h, int which, cudaGraph_t G) {
     c.stream = S2;
     pass_a(h, which);
     pass_b(h, which, x, cnd);
-    if (h->mg) vcycle(h, which);
+    if (h->mg) vcycle(h, which, false);
     HCA_TRY(cudaGetLastError());
     HCA_TRY(cudaStreamEndCapture(S2, &body));
     c.stream = S;
@@ -497,7 +501,7 @@ int cap_solve(hca_handle* h, int which, cudaGraph_t G) {
   hca::launch_dc_residual(c, which, xh, xl, true, co, ci);
   if (h->mg) {
     mg_setup(h, which);
-    vcycle(h, which);
+    vcycle(h, which, true);
   }
   HCA_TRY(cudaGetLastError());
   cudaGraph_t bo, bi;
@@ -508,13 +512,13 @@ int cap_solve(hca_handle* h, int which, cudaGraph_t G) {
   c.stream = S3;
   pass_a(h, which);
   pass_b(h, which, c.dx, ci);
-  if (h->mg) vcycle(h, which);
+  if (h->mg) vcycle(h, which, false);
   HCA_TRY(cudaGetLastError());
   HCA_TRY(cudaStreamEndCapture(S3, &bi));
   c.stream = S2;
   hca::launch_dc_update(c, xh, xl);
   hca::launch_dc_residual(c, which, xh, xl, false, co, ci);
-  if (h->mg) vcycle(h, which);
+  if (h->mg) vcycle(h, which, true);
   HCA_TRY(cudaGetLastError());
   HCA_TRY(cudaStreamEndCapture(S2, &bo));
   c.stream = S;
@@ -950,7 +954,7 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
         }
       }
       H.ntot[0] = start[n];
-      H.launches = hca::vcycle_launches(H);
+      H.launches = hca::vcycle_launches(H, false);
       ALLOC(c.r, fbytes);
       ALLOC(c.mg_t0, fbytes);
       ALLOC(c.mg_w, fbytes);
@@ -1371,7 +1375,7 @@ int hca_apply_preconditioner(hca_handle* h, int32_t rep, int32_t which, const vo
   HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.nlev, mg_setup(h, which));
   int rc = copy_field(h, rep, c.r, es, const_cast<void*>(r), false, 0);
   if (rc) return rc;
-  HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.launches, vcycle(h, which));
+  HCA_LAUNCH(h, HCA_KCLASS_MG, hca::vcycle_launches(h->mgh, true), vcycle(h, which, true));
   rc = copy_field(h, rep, c.z, es, z, true, 0);
   if (rc) return rc;
   HCA_TRY(cudaStreamSynchronize(c.stream));

@@ -540,9 +540,11 @@ int grid_for(long long n) {
 }
 
 // part: -1 = whole cycle; 0 = r scaling and the lattice's first sweep +
-// restriction; 1 = coarse levels; 2 = the lattice's prolongation + last sweep
+// restriction; 1 = coarse levels; 2 = the lattice's prolongation + last sweep.
+// scale: launch the r-scaling kernel (needed only right after a residual was
+// formed, i.e. at the start of a solve or a defect-correction sweep).
 template <typename T>
-void vcycle_t(const Ctx& c, int which, const MGHost& H, int part) {
+void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
   cudaStream_t s = c.stream;
   T* t0 = (T*)c.mg_t0;
   T* z = (T*)c.z;
@@ -552,7 +554,7 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part) {
     if (!all && part != 0) return;
     // the lattice is the coarsest level (single replicate): MG_NU_COARSE
     // sweeps, the last one in post0
-    k_mg_scale0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, s>>>(c, which);
+    if (scale) k_mg_scale0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, s>>>(c, which);
     k_mg_first0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, s>>>(c, which);
     for (int k = 1; k < MG_NU_COARSE - 1; ++k) {
       const bool odd = k & 1;
@@ -563,7 +565,7 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part) {
     return;
   }
   if (all || part == 0) {
-    k_mg_scale0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, s>>>(c, which);
+    if (scale) k_mg_scale0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, s>>>(c, which);
     if (multi) k_mg_restrict<T, true><<<grid_for(H.ntot[1]), kMgThreads, 0, s>>>(c, which, 0);
     else k_mg_restrict<T, false><<<grid_for(H.ntot[1]), kMgThreads, 0, s>>>(c, which, 0);
   }
@@ -596,7 +598,9 @@ void mg_setup_t(const Ctx& c, int which, const MGHost& H) {
 
 }  // namespace
 
-int vcycle_launches(const MGHost& H) { return H.nlev == 1 ? MG_NU_COARSE + 1 : 2 * H.small + 2; }
+int vcycle_launches(const MGHost& H, bool scale) {
+  return (H.nlev == 1 ? MG_NU_COARSE : 2 * H.small + 1) + (scale ? 1 : 0);
+}
 // (H.small: the deepest grid-kernel level + 1 over the batch)
 
 void launch_mg_setup(const Ctx& c, int which, bool fp64, const MGHost& H) {
@@ -604,14 +608,14 @@ void launch_mg_setup(const Ctx& c, int which, bool fp64, const MGHost& H) {
   else mg_setup_t<float>(c, which, H);
 }
 
-void launch_vcycle(const Ctx& c, int which, bool fp64, const MGHost& H, int part) {
-  if (fp64) vcycle_t<double>(c, which, H, part);
-  else vcycle_t<float>(c, which, H, part);
+void launch_vcycle(const Ctx& c, int which, bool fp64, const MGHost& H, int part, bool scale) {
+  if (fp64) vcycle_t<double>(c, which, H, part, scale);
+  else vcycle_t<float>(c, which, H, part, scale);
 }
 
-int vcycle_part_launches(const MGHost& H, int part) {
-  if (H.nlev == 1) return part == 0 ? MG_NU_COARSE + 1 : 0;
-  return part == 0 ? 2 : part == 1 ? 2 * (H.small - 1) + 1 : 1;
+int vcycle_part_launches(const MGHost& H, int part, bool scale) {
+  if (H.nlev == 1) return part == 0 ? MG_NU_COARSE + (scale ? 1 : 0) : 0;
+  return part == 0 ? 1 + (scale ? 1 : 0) : part == 1 ? 2 * (H.small - 1) + 1 : 1;
 }
 
 }  // namespace hca
