@@ -658,7 +658,6 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
             B = ld4(bb + e);
           }
           V4<float> Z, R32 = zero4<float>();
-          double g_rr = 0.0, g_bb = 0.0, g_rho = 0.0;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             Z.a[k] = 0.f;
@@ -674,14 +673,47 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
               const FF d = ff_add(ff_two_prod(cpl32, (float)neighbour_count(rd, geo, 4 * g + k)), AR.a[k]);
               const FF t = ff_add(ff_mul(d, xv), ff_neg(ff_mul(nb, cpl32)));
               const FF rf = ff_add(ff_neg(t), B.a[k]);
-              const double r = (double)rf.hi + (double)rf.lo;
-              const float r32 = (float)r;
-              const float zk = D.a[k] != 0.f ? r32 / D.a[k] : 0.f;
-              Z.a[k] = zk;
+              const float r32 = __fadd_rn(rf.hi, rf.lo);
+              Z.a[k] = D.a[k] != 0.f ? r32 / D.a[k] : 0.f;
               R32.a[k] = r32;
-              g_rr += r * r;
-              if (first) g_bb += (double)B.a[k] * (double)B.a[k];
-              if (!c.mg) g_rho += r * (double)zk;  // FP64: FP32 products of a tiny residual underflow
+            }
+          }
+          // the group's |r|^2, r.z and |b|^2: each 4-term sum is taken in
+          // FP32 after an exact power-of-two scaling by the group's largest
+          // magnitude (a decayed field's residual, ~1e-22, would underflow
+          // when squared unscaled) and enters the FP64 row sums once
+          auto scaled_sum = [](const V4<float>& v, const V4<float>* w) -> double {
+            float m = 0.f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) m = fmaxf(m, fabsf(v.a[k]));
+            if (m == 0.f) return 0.0;
+            const int ex = ilogbf(m);
+            float s2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const float u = scalbnf(v.a[k], -ex);
+              s2 += w ? u * scalbnf(w->a[k], -ex) : u * u;
+            }
+            return ldexp((double)s2, 2 * ex);
+          };
+          const double g_rr = scaled_sum(R32, nullptr);
+          const double g_bb = first ? scaled_sum(B, nullptr) : 0.0;
+          double g_rho = 0.0;
+          if (!c.mg) {
+            // r.z with z = r / d: scale r and z by the same power (|z| may be
+            // far from |r|, so each is scaled by its own group maximum)
+            float mr = 0.f, mz = 0.f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              mr = fmaxf(mr, fabsf(R32.a[k]));
+              mz = fmaxf(mz, fabsf(Z.a[k]));
+            }
+            if (mr > 0.f && mz > 0.f) {
+              const int er = ilogbf(mr), ez = ilogbf(mz);
+              float s = 0.f;
+#pragma unroll
+              for (int k = 0; k < 4; ++k) s += scalbnf(R32.a[k], -er) * scalbnf(Z.a[k], -ez);
+              g_rho = ldexp((double)s, er + ez);
             }
           }
           st4(zz + e, Z);
