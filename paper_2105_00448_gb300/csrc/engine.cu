@@ -954,13 +954,21 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
         }
       }
       H.ntot[0] = start[n];
+      std::vector<long long> rowstart(n + 1, 0);
+      for (int i = 0; i < n; ++i) {
+        const hca::MGLevel& L1 = lv[(size_t)i * hca::MG_MAXLEV + 1];
+        rowstart[i + 1] = rowstart[i] + (rep[i].x > 1 ? (long long)L1.ny * L1.nz * h->reps_h[i].gpr : 0);
+      }
+      H.nrowitems = rowstart[n];
       H.launches = hca::vcycle_launches(H, false);
       ALLOC(c.r, fbytes);
       ALLOC(c.mg_t0, fbytes);
       ALLOC(c.mg_w, fbytes);
       hca::MGLevel* lv_d;
       long long* start_d;
+      long long* rowstart_d;
       int2* rep_d;
+      ALLOC(rowstart_d, sizeof(long long) * (n + 1));
       ALLOC(lv_d, sizeof(hca::MGLevel) * lv.size());
       ALLOC(start_d, sizeof(long long) * start.size());
       ALLOC(rep_d, sizeof(int2) * n);
@@ -968,6 +976,8 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
           cudaMemcpyAsync(start_d, start.data(), sizeof(long long) * start.size(), cudaMemcpyHostToDevice,
                           c.stream) ||
           cudaMemcpyAsync(rep_d, rep.data(), sizeof(int2) * n, cudaMemcpyHostToDevice, c.stream) ||
+          cudaMemcpyAsync(rowstart_d, rowstart.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice,
+                          c.stream) ||
           cudaStreamSynchronize(c.stream)) {
         rc = HCA_ERR_CUDA;
         goto fail;
@@ -975,6 +985,7 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
       c.mg_lv = lv_d;
       c.mg_start = start_d;
       c.mg_rep = rep_d;
+      c.mg_rowstart = rowstart_d;
       c.mg = 1;
     }
     if (h->learned) {

@@ -245,6 +245,7 @@ struct MGHost {
   int nlev = 0;                  // most levels of any replicate
   int small = 0;                 // 1 + deepest grid-kernel level of any replicate
   long long ntot[MG_MAXLEV] = {};  // sites of level l summed over the replicates
+  long long nrowitems = 0;         // (level-1 row, lattice 4-site group) items over the replicates
   int launches = 0;              // kernels per V-cycle
   int ni = 0;                    // groups per lane in a row of the lattice (1, 2, 4; 0 = other)
 };
@@ -276,6 +277,7 @@ struct Ctx {
   const void* mg_lv;  // device MGLevel[n_reps][MG_MAXLEV] (level 0 unused)
   const long long* mg_start;  // [MG_MAXLEV][n_reps + 1] prefix sums of each level's sites over the replicates
   const int2* mg_rep;         // per replicate: (levels, first single-block level)
+  const long long* mg_rowstart;  // [n_reps + 1] prefix of level-1 rows x lattice groups per row
   void* reac;    // FP32 scheme: reaction part a of the diagonal d = c n + a
   void* phi;
   void* P;

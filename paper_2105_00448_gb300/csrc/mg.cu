@@ -366,6 +366,123 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_post(Ctx c, int which, int l)
   }
 }
 
+// Restriction from the lattice to level 1 in row-vector form: one thread per
+// 4-site group of the fine rows 2Y, 2Y+1 x 2Z, 2Z+1 under coarse row (Y, Z),
+// producing coarse sites X = 2j, 2j+1.  Every load of the item (the four own
+// rows, their eight outer neighbour rows, the x neighbours at the group's
+// ends) is issued before u = (omega/d) r is formed, so an item costs one
+// memory round trip.  Same arithmetic as restrict_fused_at.
+template <typename T>
+__global__ void __launch_bounds__(128) k_mg_restrict0_rows(Ctx c, int which) {
+  HCA_COUNT_KERNEL(c);
+  const T* __restrict__ rr = (const T*)c.r;
+  const T* __restrict__ ww = (const T*)c.mg_w;
+  const T* __restrict__ dd = (const T*)c.d;
+  const MGLevel* LV = (const MGLevel*)c.mg_lv;
+  const long long total = c.mg_rowstart[c.n_reps];
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    // replicate of item q (prefix over replicates of coarse rows x groups)
+    int r = 0;
+    {
+      int lo = 0, hi = c.n_reps;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (c.mg_rowstart[mid] <= q) lo = mid;
+        else hi = mid;
+      }
+      r = lo;
+    }
+    const RepDesc& rd = c.reps[r];
+    const MGLevel& L1 = LV[r * MG_MAXLEV + 1];
+    const long long it = q - c.mg_rowstart[r];
+    const int gpr = rd.gpr;
+    const int j = (int)(it % gpr);
+    const long long R = it / gpr;
+    const int Y = (int)(R % L1.ny), Z = (int)(R / L1.ny);
+    const long long sy = rd.nxp, sz = (long long)rd.nxp * rd.ny;
+    const int y0 = 2 * Y, z0 = 2 * Z, x0 = 4 * j;
+    const long long eb = rd.off + (long long)x0 + sy * y0 + sz * z0;   // fine (x0, y0, z0)
+    const T cpl = (T)op_coupling(rd, which);
+    // rows: own (a, b) = (y0 + a, z0 + b); outer: y0 - 1, y0 + 2 (for b = 0, 1), z0 - 1, z0 + 2 (for a = 0, 1)
+    bool ok[12];
+    long long off[12];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        ok[2 * a + b] = (y0 + a < rd.ny) && (z0 + b < rd.nz);
+        off[2 * a + b] = sy * a + sz * b;
+      }
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      ok[4 + b] = y0 > 0 && z0 + b < rd.nz;
+      off[4 + b] = -sy + sz * b;
+      ok[6 + b] = y0 + 2 < rd.ny && z0 + b < rd.nz;
+      off[6 + b] = 2 * sy + sz * b;
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      ok[8 + a] = z0 > 0 && y0 + a < rd.ny;
+      off[8 + a] = sy * a - sz;
+      ok[10 + a] = z0 + 2 < rd.nz && y0 + a < rd.ny;
+      off[10 + a] = sy * a + 2 * sz;
+    }
+    V4<T> RV[12], WV[12], DV[4];
+#pragma unroll
+    for (int t = 0; t < 12; ++t) {
+      RV[t] = ld4_if(rr + eb + off[t], ok[t]);
+      WV[t] = ld4_if(ww + eb + off[t], ok[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) DV[t] = ld4_if(dd + eb + off[t], ok[t]);
+    // x neighbours of the own rows at the group's ends
+    T lr[4], lw[4], rrr[4], rw[4];
+    const bool hasl = x0 > 0, hasr = x0 + 4 < rd.nx;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      lr[t] = (ok[t] && hasl) ? rr[eb + off[t] - 1] : T(0);
+      lw[t] = (ok[t] && hasl) ? ww[eb + off[t] - 1] : T(0);
+      rrr[t] = (ok[t] && hasr) ? rr[eb + off[t] + 4] : T(0);
+      rw[t] = (ok[t] && hasr) ? ww[eb + off[t] + 4] : T(0);
+    }
+    // u = (omega/d) r (zero outside the lattice: w = 0 on padding and missing rows)
+    V4<T> U[12];
+#pragma unroll
+    for (int t = 0; t < 12; ++t)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) U[t].a[e] = (x0 + e < rd.nx) ? WV[t].a[e] * RV[t].a[e] : T(0);
+    T acc0 = T(0), acc1 = T(0);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const int t = 2 * a + b;
+        if (!ok[t]) continue;
+        const V4<T>& ymr = a ? U[b] : U[4 + b];           // row y - 1
+        const V4<T>& ypr = a ? U[6 + b] : U[2 + b];       // row y + 1
+        const V4<T>& zmr = b ? U[2 * a] : U[8 + a];       // row z - 1
+        const V4<T>& zpr = b ? U[10 + a] : U[2 * a + 1];  // row z + 1
+        const T ul = lw[t] * lr[t], ur = rw[t] * rrr[t];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int x = x0 + e;
+          if (x >= rd.nx) continue;
+          const T left = e == 0 ? ul : U[t].a[e - 1];
+          const T right = e == 3 ? ur : U[t].a[e + 1];
+          const T nb = (x > 0 ? left : T(0)) + (x < rd.nx - 1 ? right : T(0)) + ymr.a[e] + ypr.a[e] + zmr.a[e] + zpr.a[e];
+          const T res = RV[t].a[e] - (DV[t].a[e] * U[t].a[e] - cpl * nb);
+          if (e < 2) acc0 += res;
+          else acc1 += res;
+        }
+      }
+    T* rhs1 = (T*)L1.rhs;
+    const long long cb = ((long long)Z * L1.ny + Y) * L1.nx + 2 * j;
+    if (2 * j < L1.nx) rhs1[cb] = acc0;
+    if (2 * j + 1 < L1.nx) rhs1[cb + 1] = acc1;
+  }
+}
+
 // The whole sub-cycle of one replicate's levels small .. nlev-1 in one block
 // (block r = replicate r).
 template <typename T>
@@ -566,8 +683,9 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
   }
   if (all || part == 0) {
     if (scale) k_mg_scale0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, s>>>(c, which);
-    if (multi) k_mg_restrict<T, true><<<grid_for(H.ntot[1]), kMgThreads, 0, s>>>(c, which, 0);
-    else k_mg_restrict<T, false><<<grid_for(H.ntot[1]), kMgThreads, 0, s>>>(c, which, 0);
+    // 128 threads: the kernel keeps ~28 vector loads per thread in flight
+    const int nb = (int)std::max(1LL, std::min((H.nrowitems + 127) / 128, 152LL * 16));
+    k_mg_restrict0_rows<T><<<nb, 128, 0, s>>>(c, which);
   }
   if (all || part == 1) {
     for (int l = 1; l < H.small; ++l) {
