@@ -305,6 +305,8 @@ def run_gpu(args):
             line["warm_start_learned"] = run_ws_learned(args, hca, make_maps, np, torch)
         if args.batch and world == 1:
             line["batched"] = run_batch(args, hca, torch)
+        if args.nonlinear and world == 1:
+            line["o2_nonlinear"] = run_nonlinear(args, hca, make_maps, np, torch)
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -437,6 +439,59 @@ def run_batch(args, hca, torch):
             "max_cg_iterations_last_step": max(s["o2_iterations"] + sum(s["drug_iterations"]) for s in its)}
 
 
+def run_nonlinear(args, hca, make_maps, np, torch):
+    """The linearisation of the oxygen equation (Section 2.4.1) against its
+    nonlinear solution on the workload: each step, from the same lattice and
+    previous K, one handle takes the lagged-linearised solve and a second
+    handle (o2_nonlinear) iterates it to the fixed point; the relative L2
+    difference of the two fields is the linearisation error the paper bounds
+    by 0.03 %.  Both O2 solves are timed with CUDA events."""
+    n = args.edge
+    maps = make_maps(n, n, n, corr_len=CORR_LEN, seed=WORKLOAD["seed"])
+    stream = torch.cuda.Stream()
+    args3 = (n, n, n, maps.p_cell, maps.perf, maps.p_vessel)
+    lin = hca.Sim(hca.make_config(n, n, n, stream=stream.cuda_stream, **WORKLOAD), args3[3:])
+    nl = hca.Sim(hca.make_config(n, n, n, stream=stream.cuda_stream, **{**WORKLOAD, "o2_nonlinear": 1}), args3[3:])
+    lin.step(args.warmup, allow_noconv=True)
+    st = torch.empty((n, n, n), dtype=torch.uint8, device="cuda")
+    K = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+    Kn = torch.empty_like(K)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    rel, mx, t_lin, t_nl, picard = [], [], [], [], []
+    for _ in range(args.nl_steps):
+        hca.hca_read_states(lin.handle, 0, st)
+        hca.hca_read_fields(lin.handle, 0, hca.FIELD_O2, K)
+        torch.cuda.synchronize()
+        hca.hca_write_states(nl.handle, 0, st)
+        hca.hca_write_fields(nl.handle, 0, hca.FIELD_O2, K)
+        ev[0].record(stream)
+        nl.stage(hca.STAGE_O2, allow_noconv=True)
+        ev[1].record(stream)
+        lin.stage(hca.STAGE_O2, allow_noconv=True)
+        ev[2].record(stream)
+        stream.synchronize()
+        t_nl.append(ev[0].elapsed_time(ev[1]))
+        t_lin.append(ev[1].elapsed_time(ev[2]))
+        picard.append(nl.stats()["picard_iterations"])
+        hca.hca_read_fields(lin.handle, 0, hca.FIELD_O2, K)
+        hca.hca_read_fields(nl.handle, 0, hca.FIELD_O2, Kn)
+        torch.cuda.synchronize()
+        d = (K.double() - Kn.double())
+        rel.append(float(d.norm() / Kn.double().norm()))
+        mx.append(float(d.abs().max() / Kn.double().abs().max()))
+        lin.stage(hca.STAGE_DRUGS | hca.STAGE_ODE | hca.STAGE_CA | hca.STAGE_ADVANCE, allow_noconv=True)
+    stream.synchronize()
+    lin.close()
+    nl.close()
+    return {"workload": f"{n}^3 workload, {args.nl_steps} steps after {args.warmup} warm-up; nonlinear: Picard "
+                        f"iteration of the linearisation to ||dK||/||K|| <= {WORKLOAD['picard_tol']:g} "
+                        f"(FP32 fields)",
+            "linearisation_rel_l2": {"max": max(rel), "mean": sum(rel) / len(rel)},
+            "linearisation_rel_max_norm": max(mx), "paper_bound_rel": 3e-4,
+            "o2_ms_linearised": sum(t_lin) / len(t_lin), "o2_ms_nonlinear": sum(t_nl) / len(t_nl),
+            "picard_iterations_mean": sum(picard) / len(picard)}
+
+
 def run_e2e(args, hca, make_maps, np, torch):
     """Same metric through the public C ABI with host buffers: create from
     pinned host maps, then per step one hca_step and a read of the states and
@@ -487,6 +542,9 @@ def main():
     ap.add_argument("--batch", type=int, default=0,
                     help="also time N batched replicates of uneven size (e.g. 64)")
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--nonlinear", action="store_true",
+                    help="also measure the oxygen linearisation error against the nonlinear solve")
+    ap.add_argument("--nl-steps", type=int, default=4)
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         raise SystemExit("need --steps >= 1 and --warmup >= 0")

@@ -124,7 +124,8 @@ typedef struct hca_config {
   double rtol_drug;      /* same for each drug solve (1e-8) */
   int32_t maxit;         /* CG iteration cap per solve */
   int32_t ode_substeps;  /* RK4 steps per dt for Vc (60: h = 1 min, Section 2.4.2) */
-  double picard_tol;     /* initial O2 fixed point: stop at ||dK||/||K|| <= tol */
+  double picard_tol;     /* O2 fixed point (initial field; every step with o2_nonlinear):
+                            stop at ||dK||/||K|| <= tol */
   int32_t picard_maxit;
   int32_t dose_interval; /* CA steps between boluses; boluses at steps 0, I, 2I, ... */
 
@@ -160,14 +161,19 @@ typedef struct hca_config {
   int32_t warm_start;    /* HCA_WS_PREV */
   int32_t preconditioner; /* HCA_PC_JACOBI (default) or HCA_PC_MG (single-replicate handles) */
   int32_t threads_per_block; /* 0 = library choice (autotuned at creation); else 64, 128, 256 or 512; results do not depend on it */
-  int32_t pad2;
+  int32_t o2_nonlinear;  /* 0: one lagged-linearised oxygen solve per step (Section 2.4.1);
+                            1: iterate that linearisation from the previous K to its fixed
+                            point every step (picard_tol, picard_maxit), i.e. solve the
+                            nonlinear quasi-steady Eq. (oxygen); steps then run from a host
+                            loop (one convergence check per Picard iterate), not a graph.
+                            Must match across a batch; not with HCA_WS_LEARNED*. */
   void* stream;          /* cudaStream_t, NULL = default stream */
 } hca_config;
 
 /* Per-replicate statistics of the most recent step (or stage). */
 typedef struct hca_stats {
   int64_t step;                 /* steps completed */
-  int32_t picard_iterations;    /* initial oxygen fixed point */
+  int32_t picard_iterations;    /* oxygen fixed point: of the last step with o2_nonlinear, else of the initial field */
   int32_t o2_iterations;        /* CG iterations of the last oxygen solve (all sweeps) */
   int32_t o2_sweeps;            /* defect-correction sweeps (1 for HCA_FP64) */
   int32_t drug_iterations[3];

@@ -14,7 +14,9 @@ Initialisation (Algorithm 1, steps 2-5):
 One step n -> n+1 (Algorithm 1, loop body, VEGF/Avastin omitted):
   1. plasma levels G_{d,0}(t^{n+1}) (closed form);
   2. oxygen: quasi-steady solve with the consumption linearised about the
-     previous K (Section 2.4.1), x0 = previous K;
+     previous K (Section 2.4.1), x0 = previous K; with o2_nonlinear set, the
+     linearisation is iterated to its fixed point from the previous K instead
+     (the nonlinear quasi-steady equation, solved exactly);
   3. drugs: one implicit-Euler step of Eq. (chemo), x0 = G^n;
   4. ODEs for phi, P, Vc with the new K;
   5. the CA update (Section 2.5) with Philox draws keyed by the step index n.
@@ -39,7 +41,7 @@ from .plasma import plasma_concentration
 @dataclasses.dataclass
 class StepStats:
     step: int
-    o2: SolveInfo
+    o2: SolveInfo               # None when the O2 solve is the Picard iteration
     drugs: List[SolveInfo]
     committed: int
     kills: int
@@ -71,9 +73,21 @@ def o2_solve(state, K_prev, cfg: Pm.Config, rtol=None):
                cfg.rtol_o2 if rtol is None else rtol, cfg.maxit)
 
 
-def o2_initial(state, cfg: Pm.Config):
-    """Picard fixed point of the lagged linearisation, starting from K = K0."""
-    K = np.full(state.shape, cfg.K0, dtype=np.float64)
+def o2_residual_nonlinear(state, K, cfg: Pm.Config):
+    """F(K) of Eq. (oxygen) with s_K = 0 and the consumption kept nonlinear:
+    D_K/dx^2 S(K) + phi_K K/(K1 + K) [consumer] + r_K (K - K0) [vessel]
+    (its zero is the quasi-steady oxygen field)."""
+    K = np.asarray(K, dtype=np.float64)
+    cons = np.where(S.is_consumer(state), cfg.phi_K * K / (cfg.K1 + K), 0.0)
+    ves = np.where(S.is_vessel(state), cfg.r_K * (K - cfg.K0), 0.0)
+    return S.o2_coupling(cfg) * S.laplacian_sum(K) + cons + ves
+
+
+def o2_picard(state, K_start, cfg: Pm.Config):
+    """Fixed point of the lagged linearisation K -> A(K)^{-1} b iterated from
+    K_start until ||dK|| <= picard_tol ||K|| (or picard_maxit): the solution
+    of the nonlinear quasi-steady oxygen equation.  Returns (K, iterations)."""
+    K = np.array(K_start, dtype=np.float64)
     iters = 0
     for iters in range(1, cfg.picard_maxit + 1):
         K_new, _ = o2_solve(state, K, cfg)
@@ -83,6 +97,11 @@ def o2_initial(state, cfg: Pm.Config):
         if norm == 0.0 or change <= cfg.picard_tol * norm:
             break
     return K, iters
+
+
+def o2_initial(state, cfg: Pm.Config):
+    """Picard fixed point of the lagged linearisation, starting from K = K0."""
+    return o2_picard(state, np.full(state.shape, cfg.K0, dtype=np.float64), cfg)
 
 
 def drug_solve(state, perf, G_old, G0_next, cfg: Pm.Config, d: int):
@@ -120,6 +139,9 @@ class OracleSim:
 
     # stages of one step, callable one by one
     def solve_o2(self):
+        if self.cfg.o2_nonlinear:
+            self.K, self.picard_iterations = o2_picard(self.state, self.K, self.cfg)
+            return None
         self.K, info = o2_solve(self.state, self.K, self.cfg)
         return info
 

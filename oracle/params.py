@@ -52,8 +52,12 @@ class Config:
     rtol_o2: float = 1e-8           # Section 2.4: relative tolerance 1e-8
     rtol_drug: float = 1e-8
     maxit: int = 20000
-    picard_tol: float = 1e-8        # initial oxygen fixed point, ||dK||/||K||
+    picard_tol: float = 1e-8        # oxygen fixed point, ||dK||/||K||
     picard_maxit: int = 100
+    # 0: one solve of the lagged linearisation per step (Section 2.4.1,
+    # "linear approximation"); 1: the nonlinear quasi-steady equation, as the
+    # fixed point of that linearisation iterated from K_prev each step
+    o2_nonlinear: int = 0
     ode_substeps: int = 60          # RK4 step h = dt / ode_substeps = 1 min (Section 2.4.2)
 
     # oxygen, Eq. (oxygen) and Table 1

@@ -70,6 +70,7 @@ struct hca_handle {
   long long step = 0;
   long long launches = 0;
   int picard_iterations = 0;
+  bool nonlinear = false;     // o2_nonlinear: a Picard solve of the oxygen equation every step
   int prev_iters[1 + hca::MAX_DRUGS] = {0, 0, 0, 0};
   int maxit_all = 0;
   int max_outer = 0;
@@ -175,6 +176,9 @@ int validate(const hca_config& c) {
   if (c.n_drugs < 0 || c.n_drugs > 3) return HCA_ERR_ARG;
   if (!(c.dx > 0) || !(c.dt > 0) || !(c.rtol_o2 > 0) || !(c.rtol_drug > 0)) return HCA_ERR_ARG;
   if (c.maxit < 0 || c.ode_substeps < 1 || c.picard_maxit < 0 || !(c.picard_tol >= 0)) return HCA_ERR_ARG;
+  if (c.o2_nonlinear != 0 && c.o2_nonlinear != 1) return HCA_ERR_ARG;
+  if (c.o2_nonlinear && c.picard_maxit < 1) return HCA_ERR_ARG;
+  if (c.o2_nonlinear && c.warm_start != HCA_WS_PREV) return HCA_ERR_UNIMPLEMENTED;
   if (c.dose_interval < 1) return HCA_ERR_ARG;
   for (int d = 0; d < c.n_drugs; ++d) {
     if (c.kill_b[d] < 1 || c.kill_b[d] > 64 || !(c.dose_peak[d] > 0)) return HCA_ERR_ARG;
@@ -632,11 +636,16 @@ int run_ca(hca_handle* h) {
   return HCA_OK;
 }
 
+int picard_oxygen(hca_handle* h);
+
 int run_stages(hca_handle* h, uint32_t mask) {
   int rc = reset_step_stats(h);
   if (rc) return rc;
   int status = HCA_OK;
-  if (mask & HCA_STAGE_O2) {
+  if ((mask & HCA_STAGE_O2) && h->nonlinear) {
+    rc = picard_oxygen(h);
+    if (rc) return rc;
+  } else if (mask & HCA_STAGE_O2) {
     rc = ws_before_o2(h, h->ctx.stream);
     if (!rc) rc = solve(h, 0);
     h->ctx.lag = nullptr;
@@ -679,8 +688,6 @@ int check_convergence(hca_handle* h) {
   return HCA_OK;
 }
 
-// Initial oxygen: Picard iteration of the lagged linearisation from K = K0
-// until ||K_new - K_old|| <= picard_tol ||K_new|| for every replicate.
 // Launch-shape autotuner: times the oxygen CG passes (the hot pair) for each
 // candidate block size (and register cap of the FP32 passes) on the handle's
 // own lattices and keeps the fastest.  It runs at creation, on the solver's
@@ -740,7 +747,10 @@ int autotune(hca_handle* h, bool tune_regs) {
   return HCA_OK;
 }
 
-int initial_oxygen(hca_handle* h) {
+// Oxygen fixed point: Picard iteration of the lagged linearisation from the
+// current K (K0 at creation) until ||K_new - K_old|| <= picard_tol ||K_new||
+// for every replicate; its limit solves the nonlinear quasi-steady Eq. (oxygen).
+int picard_oxygen(hca_handle* h) {
   Ctx& c = h->ctx;
   double tol = 0;
   int maxit = 0;
@@ -788,7 +798,7 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     if (!p_cell[i] || !perf[i] || !p_vessel[i]) return HCA_ERR_ARG;
     if (cfgs[i].precision != cfgs[0].precision || cfgs[i].n_drugs != cfgs[0].n_drugs ||
         cfgs[i].dt != cfgs[0].dt || cfgs[i].threads_per_block != cfgs[0].threads_per_block ||
-        cfgs[i].stream != cfgs[0].stream)
+        cfgs[i].stream != cfgs[0].stream || cfgs[i].o2_nonlinear != cfgs[0].o2_nonlinear)
       return HCA_ERR_ARG;
     // the learned warm start and the multigrid hierarchy serve one lattice
     if (cfgs[i].warm_start != HCA_WS_PREV && n > 1) return HCA_ERR_UNIMPLEMENTED;
@@ -803,6 +813,8 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
   h->cfgs.assign(cfgs, cfgs + n);
   h->learned = cfgs[0].warm_start != HCA_WS_PREV;
   h->mg = cfgs[0].preconditioner == HCA_PC_MG;
+  h->nonlinear = cfgs[0].o2_nonlinear != 0;
+  if (h->nonlinear) h->graphs_ok = false;   // each Picard iterate is checked on the host
   {
     // HCA_NO_GRAPH=1 runs steps from a host loop instead of the step graph
     const char* ng = std::getenv("HCA_NO_GRAPH");
@@ -1109,7 +1121,7 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
         if (rc) goto fail;
       }
     }
-    rc = initial_oxygen(h);
+    rc = picard_oxygen(h);
     if (rc) goto fail;
     rc = reset_step_stats(h);
     if (rc) goto fail;

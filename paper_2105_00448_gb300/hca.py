@@ -79,7 +79,7 @@ class hca_config(ctypes.Structure):
         ("J5", ctypes.c_double), ("K_V", ctypes.c_double),
         ("rtol_inner", ctypes.c_double), ("max_outer", ctypes.c_int32),
         ("warm_start", ctypes.c_int32), ("preconditioner", ctypes.c_int32),
-        ("threads_per_block", ctypes.c_int32), ("pad2", ctypes.c_int32),
+        ("threads_per_block", ctypes.c_int32), ("o2_nonlinear", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
     ]
 
