@@ -17,7 +17,9 @@ One step n -> n+1 (Algorithm 1, loop body, VEGF/Avastin omitted):
      previous K (Section 2.4.1), x0 = previous K; with o2_nonlinear set, the
      linearisation is iterated to its fixed point from the previous K instead
      (the nonlinear quasi-steady equation, solved exactly);
-  3. drugs: one implicit-Euler step of Eq. (chemo), x0 = G^n;
+  3. drugs: one implicit-Euler step of Eq. (chemo), x0 = G^n (or sub-steps,
+     implicit Euler or Crank-Nicolson, per drug_scheme/drug_substeps); with
+     o2_scheme set, step 2 is the time-dependent oxygen equation instead;
   4. ODEs for phi, P, Vc with the new K;
   5. the CA update (Section 2.5) with Philox draws keyed by the step index n.
 """
@@ -114,6 +116,56 @@ def drug_solve(state, perf, G_old, G0_next, cfg: Pm.Config, d: int):
                cfg.rtol_drug, cfg.maxit)
 
 
+def drug_step(state, perf, G_old, step_index: int, cfg: Pm.Config, d: int):
+    """Eq. (chemo) over one CA step as drug_substeps sub-steps of h = dt/m,
+    each by implicit Euler (drug_scheme 0) or Crank-Nicolson (1), the plasma
+    level taken at the sub-step's end (and start, for Crank-Nicolson); each
+    solve starts from the previous sub-step's field.  Returns (G, infos)."""
+    m = cfg.drug_substeps
+    h = cfg.dt / m
+    scheme = 1 if cfg.drug_scheme == 0 else 2
+    coupling = S.drug_coupling(cfg, d)
+    a0 = S.drug_reaction0(state, perf, cfg, d)
+    kappa = S.drug_kappa(state, perf, cfg, d)
+    reaction = S.drug_reaction(state, perf, cfg, d, mass=S.time_mass(scheme, h))
+    diag = S.jacobi_diagonal(state.shape, coupling, reaction)
+    period = cfg.dose_interval * cfg.dt
+    G = np.asarray(G_old, dtype=np.float64)
+    infos = []
+    for j in range(m):
+        t_old = (step_index + j / m) * cfg.dt
+        t_new = (step_index + (j + 1) / m) * cfg.dt
+        f_old = kappa * plasma_concentration(t_old, cfg.dose_peak[d], cfg.plasma_decay[d], period)
+        f_new = kappa * plasma_concentration(t_new, cfg.dose_peak[d], cfg.plasma_decay[d], period)
+        b = S.time_rhs(scheme, h, G, coupling, a0, f_old, f_new)
+        G, info = pcg(lambda u: S.apply_operator(u, coupling, reaction), b, G, diag, cfg.rtol_drug, cfg.maxit)
+        infos.append(info)
+    return G, infos
+
+
+def o2_transient_step(state, K_old, cfg: Pm.Config):
+    """Time-dependent Eq. (oxygen) (s_K = 1) over one CA step as o2_substeps
+    sub-steps of h = dt/m by implicit Euler (o2_scheme 1) or Crank-Nicolson
+    (2), the consumption of each sub-step linearised about its starting field
+    (Section 2.4.1's linear approximation).  Returns (K, infos)."""
+    if cfg.o2_nonlinear:
+        raise ValueError("the nonlinear oxygen solve is the quasi-steady form only")
+    m = cfg.o2_substeps
+    h = cfg.dt / m
+    coupling = S.o2_coupling(cfg)
+    f = S.o2_rhs(state, cfg)
+    K = np.asarray(K_old, dtype=np.float64)
+    infos = []
+    for _ in range(m):
+        a0 = S.o2_reaction(state, K, cfg)
+        reaction = a0 + S.time_mass(cfg.o2_scheme, h)
+        diag = S.jacobi_diagonal(state.shape, coupling, reaction)
+        b = S.time_rhs(cfg.o2_scheme, h, K, coupling, a0, f, f)
+        K, info = pcg(lambda u: S.apply_operator(u, coupling, reaction), b, K, diag, cfg.rtol_o2, cfg.maxit)
+        infos.append(info)
+    return K, infos
+
+
 def plasma_levels(cfg: Pm.Config, t: float):
     return [plasma_concentration(t, cfg.dose_peak[d], cfg.plasma_decay[d],
                                  cfg.dose_interval * cfg.dt) for d in range(cfg.n_drugs)]
@@ -139,6 +191,9 @@ class OracleSim:
 
     # stages of one step, callable one by one
     def solve_o2(self):
+        if self.cfg.o2_scheme:
+            self.K, infos = o2_transient_step(self.state, self.K, self.cfg)
+            return infos[-1]
         if self.cfg.o2_nonlinear:
             self.K, self.picard_iterations = o2_picard(self.state, self.K, self.cfg)
             return None
@@ -146,11 +201,10 @@ class OracleSim:
         return info
 
     def solve_drugs(self):
-        t_next = (self.step_index + 1) * self.cfg.dt
         infos = []
-        for d, G0 in enumerate(plasma_levels(self.cfg, t_next)):
-            self.G[d], info = drug_solve(self.state, self.perf, self.G[d], G0, self.cfg, d)
-            infos.append(info)
+        for d in range(self.cfg.n_drugs):
+            self.G[d], sub = drug_step(self.state, self.perf, self.G[d], self.step_index, self.cfg, d)
+            infos.append(sub[-1])
         return infos
 
     def update_odes(self):

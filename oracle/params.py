@@ -58,6 +58,15 @@ class Config:
     # "linear approximation"); 1: the nonlinear quasi-steady equation, as the
     # fixed point of that linearisation iterated from K_prev each step
     o2_nonlinear: int = 0
+    # time discretisation (Section 2.4.1).  Drugs: 0 implicit Euler, 1
+    # Crank-Nicolson, over drug_substeps equal sub-steps of dt.  Oxygen: 0
+    # quasi-steady (s_K = 0); 1 implicit Euler, 2 Crank-Nicolson in time
+    # (s_K = 1) over o2_substeps sub-steps, consumption linearised about the
+    # field at the start of each sub-step
+    drug_scheme: int = 0
+    drug_substeps: int = 1
+    o2_scheme: int = 0
+    o2_substeps: int = 1
     ode_substeps: int = 60          # RK4 step h = dt / ode_substeps = 1 min (Section 2.4.2)
 
     # oxygen, Eq. (oxygen) and Table 1

@@ -91,6 +91,27 @@ def o2_rhs(state, cfg: P.Config) -> np.ndarray:
     return np.where(is_vessel(state), cfg.r_K * cfg.K0, 0.0)
 
 
+# ------------------------------------------------- time discretisation ---
+# With the spatial operator A_0 u = coupling S(u) + a u and source f, the
+# semi-discrete equation du/dt = -A_0 u + f (s = 1 in Eq. oxygen, Eq. chemo)
+# over a sub-step h becomes
+#   implicit Euler:   (1/h + A_0) u^k = u^{k-1}/h + f^k
+#   Crank-Nicolson:   (2/h + A_0) u^k = (2/h - A_0) u^{k-1} + f^{k-1} + f^k
+# (the Crank-Nicolson form is the average of the two time levels, times 2).
+def time_mass(scheme: int, h: float) -> float:
+    """Coefficient added to the reaction: 1/h (implicit Euler), 2/h
+    (Crank-Nicolson)."""
+    return {1: 1.0 / h, 2: 2.0 / h}[scheme]
+
+
+def time_rhs(scheme: int, h: float, u_old, coupling: float, reaction0, f_old, f_new) -> np.ndarray:
+    """Right-hand side of one sub-step; reaction0 is a of A_0 (no mass term)."""
+    u_old = np.asarray(u_old, dtype=np.float64)
+    if scheme == 1:
+        return u_old / h + f_new
+    return 2.0 * u_old / h - apply_operator(u_old, coupling, reaction0) + f_old + f_new
+
+
 # ----------------------------------------------------------------- drugs ---
 def drug_coupling(cfg: P.Config, d: int) -> float:
     return cfg.D_G[d] / cfg.dx ** 2
@@ -107,11 +128,20 @@ def drug_kappa(state, perf, cfg: P.Config, d: int) -> np.ndarray:
     return np.where(is_vessel(state), cfg.kappa_G[d] * perf, 0.0)
 
 
-def drug_reaction(state, perf, cfg: P.Config, d: int) -> np.ndarray:
-    """Implicit-Euler reaction: 1/dt + psi + kappa_i [+ uptake at live cancer sites]."""
+def drug_reaction0(state, perf, cfg: P.Config, d: int) -> np.ndarray:
+    """Reaction of the spatial operator: psi + kappa_i [+ uptake at live cancer sites]."""
     kappa = drug_kappa(state, perf, cfg, d)
     uptake = np.where(is_live_cancer(state), cfg.uptake_G[d], 0.0)
-    return 1.0 / cfg.dt + cfg.psi_G[d] + kappa + uptake
+    return cfg.psi_G[d] + kappa + uptake
+
+
+def drug_reaction(state, perf, cfg: P.Config, d: int, mass=None) -> np.ndarray:
+    """Reaction of the solved operator: mass + psi + kappa_i [+ uptake at live
+    cancer sites], mass = 1/dt (one implicit-Euler step) unless given."""
+    kappa = drug_kappa(state, perf, cfg, d)
+    uptake = np.where(is_live_cancer(state), cfg.uptake_G[d], 0.0)
+    m = 1.0 / cfg.dt if mass is None else mass
+    return m + cfg.psi_G[d] + kappa + uptake
 
 
 def drug_rhs(state, perf, G_old, G0_next: float, cfg: P.Config, d: int) -> np.ndarray:
