@@ -305,6 +305,8 @@ def run_gpu(args):
             line["warm_start_learned"] = run_ws_learned(args, hca, make_maps, np, torch)
         if args.batch and world == 1:
             line["batched"] = run_batch(args, hca, torch)
+        if args.paper_time and world == 1:
+            line["paper_time_stepping"] = run_paper_time(args, hca, make_maps, np, torch)
         if args.nonlinear and world == 1:
             line["o2_nonlinear"] = run_nonlinear(args, hca, make_maps, np, torch)
         print(json.dumps(line), flush=True)
@@ -439,6 +441,33 @@ def run_batch(args, hca, torch):
             "max_cg_iterations_last_step": max(s["o2_iterations"] + sum(s["drug_iterations"]) for s in its)}
 
 
+def run_paper_time(args, hca, make_maps, np, torch):
+    """The paper's time stepping for the drugs (Section 2.4.1): Crank-Nicolson
+    with a 1-minute step, i.e. 60 sub-steps per hourly CA step, against the
+    workload's one implicit-Euler step; the rest of the step unchanged."""
+    n = args.edge
+    maps = make_maps(n, n, n, corr_len=CORR_LEN, seed=WORKLOAD["seed"])
+    stream = torch.cuda.Stream()
+    out = {}
+    for name, extra in (("implicit_euler_1", {}), ("crank_nicolson_60", {"drug_scheme": 1, "drug_substeps": 60})):
+        sim = hca.Sim(hca.make_config(n, n, n, stream=stream.cuda_stream, **{**WORKLOAD, **extra}),
+                      (maps.p_cell, maps.perf, maps.p_vessel))
+        sim.step(args.warmup, allow_noconv=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(args.paper_time_steps, allow_noconv=True)
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1) / args.paper_time_steps
+        st = sim.stats()
+        sim.close()
+        out[name] = {"ms_per_step": ms, "value": n ** 3 / (ms / 1e3), "unit": "site-steps/s",
+                     "drug_cg_iterations_last_step": st["drug_iterations"][:2]}
+    out["workload"] = (f"{n}^3 workload, {args.paper_time_steps} steps after {args.warmup} warm-up; drugs by one "
+                       f"implicit-Euler step of 60 min vs Crank-Nicolson at 1 min (60 sub-steps)")
+    return out
+
+
 def run_nonlinear(args, hca, make_maps, np, torch):
     """The linearisation of the oxygen equation (Section 2.4.1) against its
     nonlinear solution on the workload: each step, from the same lattice and
@@ -545,6 +574,9 @@ def main():
     ap.add_argument("--nonlinear", action="store_true",
                     help="also measure the oxygen linearisation error against the nonlinear solve")
     ap.add_argument("--nl-steps", type=int, default=4)
+    ap.add_argument("--paper-time", action="store_true",
+                    help="also time the drugs with Crank-Nicolson at 1-minute sub-steps")
+    ap.add_argument("--paper-time-steps", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         raise SystemExit("need --steps >= 1 and --warmup >= 0")

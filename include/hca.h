@@ -167,6 +167,18 @@ typedef struct hca_config {
                             nonlinear quasi-steady Eq. (oxygen); steps then run from a host
                             loop (one convergence check per Picard iterate), not a graph.
                             Must match across a batch; not with HCA_WS_LEARNED*. */
+  /* Time discretisation (Section 2.4.1).  With the spatial operator A_0 and
+     source f, one sub-step of h = dt / substeps solves
+       implicit Euler:   (1/h + A_0) u^k = u^{k-1}/h + f^k
+       Crank-Nicolson:   (2/h + A_0) u^k = (2/h - A_0) u^{k-1} + f^{k-1} + f^k,
+     each from x0 = u^{k-1}; the drugs' f is kappa perf G_{d,0}(t) at the
+     sub-step's ends.  All four must match across a batch. */
+  int32_t drug_scheme;   /* 0 implicit Euler (default), 1 Crank-Nicolson */
+  int32_t drug_substeps; /* sub-steps per CA step (1) */
+  int32_t o2_scheme;     /* 0 quasi-steady, s_K = 0 (default); 1 implicit Euler, 2 Crank-Nicolson
+                            in time (s_K = 1), consumption linearised about each sub-step's
+                            starting field; not with o2_nonlinear or HCA_WS_LEARNED* */
+  int32_t o2_substeps;   /* sub-steps per CA step for o2_scheme 1, 2 (1) */
   void* stream;          /* cudaStream_t, NULL = default stream */
 } hca_config;
 
@@ -174,7 +186,7 @@ typedef struct hca_config {
 typedef struct hca_stats {
   int64_t step;                 /* steps completed */
   int32_t picard_iterations;    /* oxygen fixed point: of the last step with o2_nonlinear, else of the initial field */
-  int32_t o2_iterations;        /* CG iterations of the last oxygen solve (all sweeps) */
+  int32_t o2_iterations;        /* CG iterations of the last step's oxygen solves (all sweeps and sub-steps) */
   int32_t o2_sweeps;            /* defect-correction sweeps (1 for HCA_FP64) */
   int32_t drug_iterations[3];
   double o2_rel_residual;       /* ||b - A K|| / ||b|| recomputed at exit */

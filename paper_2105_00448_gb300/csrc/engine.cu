@@ -63,6 +63,10 @@ struct hca_handle {
   int device = 0;
   std::vector<hca_config> cfgs;
   std::vector<RepDesc> reps_h;
+  // the descriptors with the quasi-steady oxygen form, for the initial oxygen
+  // fixed point of a handle whose oxygen equation is time-dependent
+  std::vector<RepDesc> reps_qs_h;
+  RepDesc* reps_qs = nullptr;
   std::vector<int2> chunks_h;
   Ctx ctx{};
   long long total = 0;        // elements per field array
@@ -179,6 +183,11 @@ int validate(const hca_config& c) {
   if (c.o2_nonlinear != 0 && c.o2_nonlinear != 1) return HCA_ERR_ARG;
   if (c.o2_nonlinear && c.picard_maxit < 1) return HCA_ERR_ARG;
   if (c.o2_nonlinear && c.warm_start != HCA_WS_PREV) return HCA_ERR_UNIMPLEMENTED;
+  if (c.drug_scheme != 0 && c.drug_scheme != 1) return HCA_ERR_ARG;
+  if (c.o2_scheme < 0 || c.o2_scheme > 2) return HCA_ERR_ARG;
+  if (c.drug_substeps < 1 || c.drug_substeps > 100000 || c.o2_substeps < 1 || c.o2_substeps > 100000)
+    return HCA_ERR_ARG;
+  if (c.o2_scheme && (c.o2_nonlinear || c.warm_start != HCA_WS_PREV)) return HCA_ERR_UNIMPLEMENTED;
   if (c.dose_interval < 1) return HCA_ERR_ARG;
   for (int d = 0; d < c.n_drugs; ++d) {
     if (c.kill_b[d] < 1 || c.kill_b[d] > 64 || !(c.dose_peak[d] > 0)) return HCA_ERR_ARG;
@@ -216,9 +225,21 @@ RepDesc make_desc(const hca_config& c) {
   r.K0 = c.K0;
   r.r_K = c.r_K;
   r.inv_dt = 1.0 / c.dt;
+  // time discretisation: sub-step h, mass term 1/h (implicit Euler) or 2/h
+  // (Crank-Nicolson), b = bx x0 [- A x0] + source
+  const double ho = c.dt / c.o2_substeps, hd = c.dt / c.drug_substeps;
+  r.o2_mass = c.o2_scheme == 1 ? 1.0 / ho : c.o2_scheme == 2 ? 2.0 / ho : 0.0;
+  r.bx[0] = c.o2_scheme == 1 ? 1.0 / ho : c.o2_scheme == 2 ? 4.0 / ho : 0.0;
+  r.bax[0] = c.o2_scheme == 2;
+  r.nsub[0] = c.o2_scheme ? c.o2_substeps : 1;
+  for (int d = 0; d < hca::MAX_DRUGS; ++d) {
+    r.bx[1 + d] = c.drug_scheme ? 4.0 / hd : 1.0 / hd;
+    r.bax[1 + d] = c.drug_scheme == 1;
+    r.nsub[1 + d] = c.drug_substeps;
+  }
   for (int d = 0; d < hca::MAX_DRUGS; ++d) {
     r.c_drug[d] = c.D_G[d] / dx2;
-    r.base_drug[d] = 1.0 / c.dt + c.psi_G[d];
+    r.base_drug[d] = (c.drug_scheme ? 2.0 / hd : 1.0 / hd) + c.psi_G[d];
     r.kappa[d] = c.kappa_G[d];
     r.uptake[d] = c.uptake_G[d];
     r.dose_peak[d] = c.dose_peak[d] > 0 ? c.dose_peak[d] : 1.0;
@@ -539,13 +560,22 @@ int cap_stages(hca_handle* h, uint32_t mask, cudaGraph_t G) {
   int rc;
   if (mask & HCA_STAGE_O2) {
     rc = ws_before_o2(h, c.stream);
-    if (!rc) rc = cap_solve(h, 0, G);
+    for (int j = 0; j < h->cfgs[0].o2_substeps && !rc && (j == 0 || h->cfgs[0].o2_scheme); ++j) {
+      c.sub = j;
+      rc = cap_solve(h, 0, G);
+    }
     c.lag = nullptr;
+    c.sub = 0;
     if (rc) return rc;
   }
   if (mask & HCA_STAGE_DRUGS)
     for (int d = 0; d < h->n_drugs; ++d)
-      if ((rc = cap_solve(h, 1 + d, G))) return rc;
+      for (int j = 0; j < h->cfgs[0].drug_substeps; ++j) {
+        c.sub = j;
+        rc = cap_solve(h, 1 + d, G);
+        c.sub = 0;
+        if (rc) return rc;
+      }
   c.stream = h->cap[0];
   if (mask & HCA_STAGE_ODE) hca::launch_ode(c, h->fp64);
   if (mask & HCA_STAGE_CA) {
@@ -647,15 +677,23 @@ int run_stages(hca_handle* h, uint32_t mask) {
     if (rc) return rc;
   } else if (mask & HCA_STAGE_O2) {
     rc = ws_before_o2(h, h->ctx.stream);
-    if (!rc) rc = solve(h, 0);
+    for (int j = 0; j < h->cfgs[0].o2_substeps && !rc && (j == 0 || h->cfgs[0].o2_scheme); ++j) {
+      h->ctx.sub = j;
+      rc = solve(h, 0);
+    }
     h->ctx.lag = nullptr;
+    h->ctx.sub = 0;
     if (rc) return rc;
   }
   if (mask & HCA_STAGE_DRUGS) {
-    for (int d = 0; d < h->n_drugs; ++d) {
-      rc = solve(h, 1 + d);
-      if (rc) return rc;
-    }
+    for (int d = 0; d < h->n_drugs; ++d)
+      for (int j = 0; j < h->cfgs[0].drug_substeps; ++j) {
+        h->ctx.sub = j;
+        rc = solve(h, 1 + d);
+        if (rc) break;
+      }
+    h->ctx.sub = 0;
+    if (rc) return rc;
   }
   if (mask & HCA_STAGE_ODE) {
     HCA_LAUNCH(h, HCA_KCLASS_ODE, 1, hca::launch_ode(h->ctx, h->fp64));
@@ -750,7 +788,18 @@ int autotune(hca_handle* h, bool tune_regs) {
 // Oxygen fixed point: Picard iteration of the lagged linearisation from the
 // current K (K0 at creation) until ||K_new - K_old|| <= picard_tol ||K_new||
 // for every replicate; its limit solves the nonlinear quasi-steady Eq. (oxygen).
+int picard_oxygen_impl(hca_handle* h);
+
 int picard_oxygen(hca_handle* h) {
+  // the fixed point is that of the quasi-steady form, whatever the time scheme
+  const RepDesc* reps = h->ctx.reps;
+  if (h->reps_qs) h->ctx.reps = h->reps_qs;
+  const int rc = picard_oxygen_impl(h);
+  h->ctx.reps = reps;
+  return rc;
+}
+
+int picard_oxygen_impl(hca_handle* h) {
   Ctx& c = h->ctx;
   double tol = 0;
   int maxit = 0;
@@ -798,7 +847,9 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     if (!p_cell[i] || !perf[i] || !p_vessel[i]) return HCA_ERR_ARG;
     if (cfgs[i].precision != cfgs[0].precision || cfgs[i].n_drugs != cfgs[0].n_drugs ||
         cfgs[i].dt != cfgs[0].dt || cfgs[i].threads_per_block != cfgs[0].threads_per_block ||
-        cfgs[i].stream != cfgs[0].stream || cfgs[i].o2_nonlinear != cfgs[0].o2_nonlinear)
+        cfgs[i].stream != cfgs[0].stream || cfgs[i].o2_nonlinear != cfgs[0].o2_nonlinear ||
+        cfgs[i].drug_scheme != cfgs[0].drug_scheme || cfgs[i].drug_substeps != cfgs[0].drug_substeps ||
+        cfgs[i].o2_scheme != cfgs[0].o2_scheme || cfgs[i].o2_substeps != cfgs[0].o2_substeps)
       return HCA_ERR_ARG;
     // the learned warm start and the multigrid hierarchy serve one lattice
     if (cfgs[i].warm_start != HCA_WS_PREV && n > 1) return HCA_ERR_UNIMPLEMENTED;
@@ -878,6 +929,16 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     ALLOC(chunks_d, sizeof(int2) * chunk0);
     c.reps = reps_d;
     c.chunks = chunks_d;
+    if (cfgs[0].o2_scheme) {
+      h->reps_qs_h = h->reps_h;
+      for (auto& r : h->reps_qs_h) {
+        r.o2_mass = 0.0;
+        r.bx[0] = 0.0;
+        r.bax[0] = 0;
+        r.nsub[0] = 1;
+      }
+      ALLOC(h->reps_qs, sizeof(RepDesc) * n);
+    }
     ALLOC(c.state, (size_t)h->total + 16);
     ALLOC(c.K, fbytes);
     if (!h->fp64) ALLOC(c.K_lo, fbytes);
@@ -1025,7 +1086,9 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     }
     h->h_pinned[0] = h->h_pinned[1] = 0;
     cudaStream_t s = c.stream;
-    if (cudaMemcpyAsync(reps_d, h->reps_h.data(), sizeof(RepDesc) * n, cudaMemcpyHostToDevice, s) ||
+    if ((h->reps_qs &&
+         cudaMemcpyAsync(h->reps_qs, h->reps_qs_h.data(), sizeof(RepDesc) * n, cudaMemcpyHostToDevice, s)) ||
+        cudaMemcpyAsync(reps_d, h->reps_h.data(), sizeof(RepDesc) * n, cudaMemcpyHostToDevice, s) ||
         cudaMemcpyAsync(chunks_d, h->chunks_h.data(), sizeof(int2) * chunk0, cudaMemcpyHostToDevice, s)) {
       rc = HCA_ERR_CUDA;
       goto fail;
@@ -1178,6 +1241,8 @@ int hca_config_default(hca_config* c, int32_t nx, int32_t ny, int32_t nz) {
   c->ode_substeps = 60;
   c->picard_tol = 1e-8;
   c->picard_maxit = 100;
+  c->drug_substeps = 1;
+  c->o2_substeps = 1;
   c->dose_interval = 21;
   c->D_K = 1.05e5;
   c->phi_K = 900.0;

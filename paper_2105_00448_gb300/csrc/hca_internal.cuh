@@ -52,6 +52,14 @@ struct RepDesc {
   double c_drug[MAX_DRUGS];   // D_G / dx^2
   double base_drug[MAX_DRUGS];// 1/dt + psi_G
   double inv_dt;
+  // time discretisation per operator (0 oxygen, 1 + d drug d): the reaction
+  // carries the mass term (o2_mass; inside base_drug), the right-hand side is
+  // b = bx x0 - (bax ? A x0 : 0) + source, with the oxygen source doubled and
+  // the drug source taken at both ends of the sub-step when bax (Crank-Nicolson)
+  double o2_mass;
+  double bx[1 + MAX_DRUGS];
+  int bax[1 + MAX_DRUGS];
+  int nsub[1 + MAX_DRUGS];   // sub-steps per CA step
   double kappa[MAX_DRUGS];
   double uptake[MAX_DRUGS];
   double dose_peak[MAX_DRUGS];
@@ -265,6 +273,7 @@ struct Ctx {
   void* G_lo[MAX_DRUGS];
   void* dx;      // FP32 scheme: correction of the inner solve
   void* aux;     // scratch field (previous iterate of the initial oxygen fixed point)
+  int sub;          // sub-step of the current solve within the CA step (plasma times)
   const void* lag;  // oxygen linearisation point (K_prev) when the solve starts elsewhere; null: the start field
   // multigrid preconditioner (single replicate): residual r (the Jacobi form
   // carries z = r / d instead), level-0 scratch, coarse level table
@@ -483,6 +492,19 @@ __device__ __forceinline__ double plasma_level(double t, double peak, double dec
     if (interval <= 0.0) break;
   }
   return total;
+}
+
+// Plasma level seen by a drug sub-step: G_{d,0} at its end (t_k), plus at its
+// start (t_{k-1}) under Crank-Nicolson; t_k = (step + (sub + 1) / m) dt.
+__device__ __forceinline__ double substep_plasma(const RepDesc& rd, int which, long long step, int sub) {
+  const int dg = which - 1;
+  const double m = (double)rd.nsub[which];
+  const double t_new = ((double)step + (double)(sub + 1) / m) * rd.dt;
+  double g = plasma_level(t_new, rd.dose_peak[dg], rd.plasma_decay[dg], rd.dose_interval_min);
+  if (rd.bax[which])
+    g += plasma_level(((double)step + (double)sub / m) * rd.dt, rd.dose_peak[dg], rd.plasma_decay[dg],
+                      rd.dose_interval_min);
+  return g;
 }
 
 }  // namespace hca

@@ -35,6 +35,7 @@ __device__ __forceinline__ T reaction_site(const RepDesc& rd, int which, uint8_t
   if (KIND == 0) {
     a = is_consumer(s) ? (T)rd.phi_K / ((T)rd.K1 + K_prev) : T(0);
     if (is_vessel(s)) a += (T)rd.r_K;
+    a += (T)rd.o2_mass;   // 0 for the quasi-steady form
   } else {
     const int dd = which - 1;
     a = (T)rd.base_drug[dd];
@@ -52,6 +53,7 @@ __device__ __forceinline__ T diag_site(const RepDesc& rd, int which, int n_nb, u
   if (KIND == 0) {
     a = is_consumer(s) ? (T)rd.phi_K / ((T)rd.K1 + K_prev) : T(0);
     if (is_vessel(s)) a += (T)rd.r_K;
+    a += (T)rd.o2_mass;
   } else {
     const int dd = which - 1;
     a = (T)rd.base_drug[dd];
@@ -62,8 +64,8 @@ __device__ __forceinline__ T diag_site(const RepDesc& rd, int which, int n_nb, u
 }
 
 // ------------------------------------------------------------------ setup --
-// r = b - A x0 with x0 the current field; writes d, z = r/d (and b for drugs);
-// reduces rho = r.z, |r|^2, |b|^2.
+// r = b - A x0 with x0 the current field; writes d, z = r/d (and b for drugs
+// and the time-dependent oxygen form); reduces rho = r.z, |r|^2, |b|^2.
 template <typename T, int KIND>
 __global__ void __launch_bounds__(512) k_setup(Ctx c, int which, CondArg cnd) {
   HCA_COUNT_KERNEL(c);
@@ -77,17 +79,15 @@ __global__ void __launch_bounds__(512) k_setup(Ctx c, int which, CondArg cnd) {
   T* __restrict__ zz = (T*)c.z;
   T* __restrict__ bb = (T*)c.b;
   if (KIND == 1) {
-    if (threadIdx.x == 0) {
-      const int dg = which - 1;
-      const double t_next = ((double)(*c.step) + 1.0) * rd.dt;
-      s_G0 = plasma_level(t_next, rd.dose_peak[dg], rd.plasma_decay[dg], rd.dose_interval_min);
-    }
+    if (threadIdx.x == 0) s_G0 = substep_plasma(rd, which, *c.step, c.sub);
     __syncthreads();
   }
   const T G0 = KIND == 1 ? (T)s_G0 : T(0);
   const T cpl = (T)op_coupling(rd, which);
-  const T inv_dt = (T)rd.inv_dt;
-  const T bvessel = (T)(rd.r_K * rd.K0);
+  const T bx = (T)rd.bx[which];
+  const bool bax = rd.bax[which] != 0;
+  const bool o2t = KIND == 0 && rd.bx[0] != 0.0;   // time-dependent oxygen: b depends on x0
+  const T bvessel = (T)(bax ? 2.0 * rd.r_K * rd.K0 : rd.r_K * rd.K0);
   const RowIter it = row_iter(rd);
   for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
     const int rl = rbase + it.sub;
@@ -120,9 +120,11 @@ __global__ void __launch_bounds__(512) k_setup(Ctx c, int which, CondArg cnd) {
           T dk = T(0), zk = T(0), bk = T(0);
           if (xk < rd.nx) {
             dk = diag_site<T, KIND>(rd, which, neighbour_count(rd, geo, xk), s, LG.a[k], PF.a[k]);
-            if (KIND == 0) bk = is_vessel(s) ? bvessel : T(0);
-            else bk = X.a[k] * inv_dt + (is_vessel(s) ? (T)rd.kappa[which - 1] * PF.a[k] * G0 : T(0));
-            const T r = bk - (dk * X.a[k] - cpl * nb_sum(X, k, left, right, ym, yp, zm, zp));
+            if (KIND == 0) bk = (is_vessel(s) ? bvessel : T(0)) + (o2t ? X.a[k] * bx : T(0));
+            else bk = X.a[k] * bx + (is_vessel(s) ? (T)rd.kappa[which - 1] * PF.a[k] * G0 : T(0));
+            const T ax = dk * X.a[k] - cpl * nb_sum(X, k, left, right, ym, yp, zm, zp);
+            if (bax) bk -= ax;   // Crank-Nicolson: b = (4/h) x0 - A x0 + f^{k-1} + f^k
+            const T r = bk - ax;
             RR.a[k] = r;
             zk = dk != T(0) ? r / dk : T(0);   // d = 0 only for an isolated, empty 1-site box
             g_rho += r * zk;
@@ -136,7 +138,7 @@ __global__ void __launch_bounds__(512) k_setup(Ctx c, int which, CondArg cnd) {
         st4(dd + e, D);
         st4(zz + e, Z);
         if (c.mg) st4((T*)c.r + e, RR);
-        if (KIND == 1) st4(bb + e, B);
+        if (KIND == 1 || o2t) st4(bb + e, B);
         acc[0] += (double)g_rho;
         acc[1] += (double)g_rr;
         acc[2] += (double)g_bb;
@@ -423,7 +425,9 @@ __global__ void __launch_bounds__(512) k_true_residual(Ctx c, int which, void* x
       if (gok) {
         const V4<T> D = ld4(dd + e);
         V4<T> B;
-        if (KIND == 0) {
+        if (KIND == 0 && rd.bx[0] != 0.0) {
+          B = ld4(bb + e);
+        } else if (KIND == 0) {
           const uchar4 st = ld_state4(c.state + e);
 #pragma unroll
           for (int k = 0; k < 4; ++k) B.a[k] = is_vessel(st_at(st, k)) ? bvessel : T(0);
@@ -586,11 +590,7 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
   const RepSolve sv = c.solve[ch.x];
   const bool live = first || sv.active || sv.dc_apply;
   if (KIND == 1 && first) {
-    if (threadIdx.x == 0) {
-      const int dg = which - 1;
-      const double t_next = ((double)(*c.step) + 1.0) * rd.dt;
-      s_G0 = plasma_level(t_next, rd.dose_peak[dg], rd.plasma_decay[dg], rd.dose_interval_min);
-    }
+    if (threadIdx.x == 0) s_G0 = substep_plasma(rd, which, *c.step, c.sub);
     __syncthreads();
   }
   if (live) {
@@ -603,7 +603,10 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
     const float* __restrict__ perf = (const float*)c.perf;
     const double cpl = (double)(float)op_coupling(rd, which);
     const float G0 = KIND == 1 && first ? (float)s_G0 : 0.f;
-    const float bvessel = (float)(rd.r_K * rd.K0);
+    const bool bax = rd.bax[which] != 0;
+    const bool o2t = KIND == 0 && rd.bx[0] != 0.0;
+    const double bx = rd.bx[which];
+    const float bvessel = (float)(bax ? 2.0 * rd.r_K * rd.K0 : rd.r_K * rd.K0);
     const RowIter it = row_iter(rd);
     const float cpl32 = (float)cpl;
     for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
@@ -626,7 +629,7 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
         x_neighbours(Xh, g, rd.gpr, it.sl, it.lpr, gok, carry_h, lh, rh, [&] { return x_hi[e + 4]; });
         x_neighbours(Xl, g, rd.gpr, it.sl, it.lpr, gok, carry_l, ll, rlo, [&] { return x_lo[e + 4]; });
         if (gok) {
-          V4<float> D, B, AR;
+          V4<float> D, B, AR, SRC;
           if (first) {
             const uchar4 st = ld_state4(c.state + e);
             V4<float> PF = zero4<float>();
@@ -638,6 +641,7 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
               D.a[k] = 0.f;
               B.a[k] = 0.f;
               AR.a[k] = 0.f;
+              SRC.a[k] = 0.f;
               if (xk < rd.nx) {
                 const double xk64 = (double)Xh.a[k] + (double)Xl.a[k];
                 const float xk32 = (float)xk64;
@@ -645,13 +649,17 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
                 const float lag = (KIND == 0 && c.lag) ? ((const float*)c.lag)[e + k] : xk32;
                 AR.a[k] = reaction_site<float, KIND>(rd, which, s, lag, PF.a[k]);
                 D.a[k] = cpl32 * (float)neighbour_count(rd, geo, xk) + AR.a[k];
-                if (KIND == 0) B.a[k] = is_vessel(s) ? bvessel : 0.f;
-                else B.a[k] = (float)(xk64 * rd.inv_dt) + (is_vessel(s) ? (float)rd.kappa[which - 1] * PF.a[k] * G0 : 0.f);
+                if (KIND == 0) {
+                  SRC.a[k] = is_vessel(s) ? bvessel : 0.f;
+                  B.a[k] = SRC.a[k] + (o2t ? (float)(xk64 * bx) : 0.f);
+                } else {
+                  SRC.a[k] = is_vessel(s) ? (float)rd.kappa[which - 1] * PF.a[k] * G0 : 0.f;
+                  B.a[k] = (float)(xk64 * bx) + SRC.a[k];
+                }
               }
             }
             st4(dd + e, D);
             st4(aa + e, AR);
-            st4(bb + e, B);
           } else {
             D = ld4(dd + e);
             AR = ld4(aa + e);
@@ -672,12 +680,16 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
                                    ff_add(FF{zmh.a[k], zml.a[k]}, FF{zph.a[k], zpl.a[k]}));
               const FF d = ff_add(ff_two_prod(cpl32, (float)neighbour_count(rd, geo, 4 * g + k)), AR.a[k]);
               const FF t = ff_add(ff_mul(d, xv), ff_neg(ff_mul(nb, cpl32)));
+              // Crank-Nicolson: b = (4/h) x0 - A x0 + source, formed once from the start field
+              if (first && bax)
+                B.a[k] = (float)(((double)xv.hi + (double)xv.lo) * bx + (double)SRC.a[k] - ((double)t.hi + (double)t.lo));
               const FF rf = ff_add(ff_neg(t), B.a[k]);
               const float r32 = __fadd_rn(rf.hi, rf.lo);
               Z.a[k] = D.a[k] != 0.f ? r32 / D.a[k] : 0.f;
               R32.a[k] = r32;
             }
           }
+          if (first) st4(bb + e, B);
           // the group's |r|^2, r.z and |b|^2: each 4-term sum is taken in
           // FP32 after an exact power-of-two scaling by the group's largest
           // magnitude (a decayed field's residual, ~1e-22, would underflow
