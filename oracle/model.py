@@ -21,7 +21,9 @@ One step n -> n+1 (Algorithm 1, loop body, VEGF/Avastin omitted):
      implicit Euler or Crank-Nicolson, per drug_scheme/drug_substeps); with
      o2_scheme set, step 2 is the time-dependent oxygen equation instead;
   4. ODEs for phi, P, Vc with the new K;
-  5. the CA update (Section 2.5) with Philox draws keyed by the step index n.
+  5. the CA update (Section 2.5) with Philox draws keyed by the step index n:
+     the 27-colour sweep, or with ca_mode 1 the synchronous update with
+     Algorithm 2's higher-phi rule.
 """
 
 from __future__ import annotations
@@ -34,6 +36,7 @@ import numpy as np
 from . import params as Pm
 from . import stencil as S
 from .ca import ca_update
+from .ca_sync import ca_update_sync
 from .odes import ode_update
 from .pcg import SolveInfo, pcg
 from .philox import site_uniform
@@ -212,7 +215,8 @@ class OracleSim:
                                                self.K, self.cfg)
 
     def update_ca(self):
-        self.state, self.phi, self.P, self.Vc, st = ca_update(
+        update = ca_update_sync if self.cfg.ca_mode == 1 else ca_update
+        self.state, self.phi, self.P, self.Vc, st = update(
             self.state, self.phi, self.P, self.Vc, self.K, self.G, self.cfg, self.step_index)
         return st
 

@@ -67,6 +67,9 @@ class Config:
     drug_substeps: int = 1
     o2_scheme: int = 0
     o2_substeps: int = 1
+    # CA update: 0 the 27-colour Gauss-Seidel sweep (ca.py); 1 synchronous,
+    # a contested site going to the higher phi (Algorithm 2; ca_sync.py)
+    ca_mode: int = 0
     ode_substeps: int = 60          # RK4 step h = dt / ode_substeps = 1 min (Section 2.4.2)
 
     # oxygen, Eq. (oxygen) and Table 1
