@@ -307,6 +307,8 @@ def run_gpu(args):
             line["batched"] = run_batch(args, hca, torch)
         if args.paper_time and world == 1:
             line["paper_time_stepping"] = run_paper_time(args, hca, make_maps, np, torch)
+        if args.biopsy2d and world == 1:
+            line["biopsy_2d"] = run_biopsy2d(args, hca, torch)
         if args.nonlinear and world == 1:
             line["o2_nonlinear"] = run_nonlinear(args, hca, make_maps, np, torch)
         print(json.dumps(line), flush=True)
@@ -468,6 +470,42 @@ def run_paper_time(args, hca, make_maps, np, torch):
     return out
 
 
+def run_biopsy2d(args, hca, torch):
+    """The paper's 2-D digital biopsy (Section 3.4): 2 x 10 voxels of
+    100 x 100 sites (a 200 x 1000 lattice, nz = 1), piecewise-constant voxel
+    maps (synth.biopsy_maps), one week = 168 hourly steps, timed with CUDA
+    events; both CA update rules, FP64 and FP32 storage, Jacobi-PCG (a flat
+    lattice has no coarse multigrid level)."""
+    import numpy as np
+    from synth import biopsy_maps
+
+    m = biopsy_maps(seed=11)
+    _, ny, nx = m.shape
+    stream = torch.cuda.Stream()
+    out = {}
+    for prec in ("f64", "f32"):
+        for mode in (0, 1):
+            params = {**WORKLOAD, "precision": prec, "preconditioner": 0, "ca_mode": mode, "seed": 11}
+            sim = hca.Sim(hca.make_config(nx, ny, 1, stream=stream.cuda_stream, **params), (m.p_cell, m.perf, m.p_vessel))
+            c0 = np.bincount(sim.states().reshape(-1), minlength=6)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(args.biopsy_steps, allow_noconv=True)
+            e1.record(stream)
+            stream.synchronize()
+            ms = e0.elapsed_time(e1)
+            st = sim.stats()
+            sim.close()
+            out[f"{prec}_{'sync' if mode else 'colour'}"] = {
+                "seconds": ms / 1e3, "ms_per_step": ms / args.biopsy_steps,
+                "site_steps_per_s": nx * ny * args.biopsy_steps / (ms / 1e3),
+                "cancer_cells_start": int(c0[1] + c0[2]), "cancer_cells_end": int(st["counts"][1] + st["counts"][2])}
+    out["workload"] = (f"2-D digital biopsy {ny} x {nx} sites (2 x 10 voxels of 100 x 100), {args.biopsy_steps} hourly "
+                       f"steps after creation (initial O2 fixed point not timed), O2 + 2 drugs, Jacobi-PCG rtol 1e-8")
+    out["paper_context"] = "the paper reports about 18 h on 80 CPU cores for one week of this problem (Section 3.4)"
+    return out
+
+
 def run_nonlinear(args, hca, make_maps, np, torch):
     """The linearisation of the oxygen equation (Section 2.4.1) against its
     nonlinear solution on the workload: each step, from the same lattice and
@@ -577,6 +615,9 @@ def main():
     ap.add_argument("--paper-time", action="store_true",
                     help="also time the drugs with Crank-Nicolson at 1-minute sub-steps")
     ap.add_argument("--paper-time-steps", type=int, default=3)
+    ap.add_argument("--biopsy2d", action="store_true",
+                    help="also time one week of the 2-D digital biopsy (200 x 1000 lattice)")
+    ap.add_argument("--biopsy-steps", type=int, default=168)
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         raise SystemExit("need --steps >= 1 and --warmup >= 0")

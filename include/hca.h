@@ -179,6 +179,11 @@ typedef struct hca_config {
                             in time (s_K = 1), consumption linearised about each sub-step's
                             starting field; not with o2_nonlinear or HCA_WS_LEARNED* */
   int32_t o2_substeps;   /* sub-steps per CA step for o2_scheme 1, 2 (1) */
+  int32_t ca_mode;       /* 0: 27-colour Gauss-Seidel sweep (default; later colours see earlier
+                            daughters and deaths); 1: synchronous update (Section 2.5), every
+                            committed cell decides on the lattice before the update and a site
+                            picked by several parents goes to the highest phi, then the lowest
+                            site index (Algorithm 2); must match across a batch */
   void* stream;          /* cudaStream_t, NULL = default stream */
 } hca_config;
 

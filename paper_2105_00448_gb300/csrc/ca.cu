@@ -11,6 +11,8 @@
 //    dz, dy, dx order on ties), both cells becoming PROLIF with
 //    phi = P = Vc = 0; with no free neighbour it becomes QUIESC with phi = 0.
 //
+// (ca_mode 1 replaces step 2 by the synchronous update further below.)
+//
 // Same-colour sites are at least 3 apart along some axis, so their closed
 // Moore neighbourhoods are disjoint: the cells of one launch never touch the
 // same site and the outcome does not depend on thread order.  Later colours
@@ -32,6 +34,54 @@ __device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, 
 __device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+
+// The drug kill test of a committed cell (Eq. 1 with a = 1), in round-to-
+// nearest arithmetic of the storage precision.
+template <typename T>
+__device__ __forceinline__ bool killed(const Ctx& c, const RepDesc& rd, long long e, uint32_t site, uint32_t step) {
+  const T u = (T)site_uniform(rd.seed, site, step, PURPOSE_KILL);
+  T surv = T(1);
+  for (int d = 0; d < rd.n_drugs; ++d) {
+    T xd = rn_div(((const T*)c.G[d])[e], (T)rd.dose_peak[d]);
+    if (xd > T(1)) xd = T(1);
+    if (xd < T(0)) xd = T(0);
+    const T f = rn_sub(T(1), xd);
+    for (int q = 0; q < rd.kill_b[d]; ++q) surv = rn_mul(surv, f);
+  }
+  const T p_kill = rn_sub(T(1), surv);
+  return u < p_kill;
+}
+
+// The free Moore neighbour of (x, y, z) with the highest K (first in dz, dy,
+// dx order on ties), as a field element, or -1.
+template <typename T>
+__device__ __forceinline__ long long best_free(const Ctx& c, const RepDesc& rd, int x, int y, int z) {
+  const T* K = (const T*)c.K;
+  const long long sy = rd.nxp, sz = (long long)rd.nxp * rd.ny;
+  long long best = -1;
+  T best_K = T(0);
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int zz = z + dz;
+    if (zz < 0 || zz >= rd.nz) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int yy = y + dy;
+      if (yy < 0 || yy >= rd.ny) continue;
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int xx = x + dx;
+        if (xx < 0 || xx >= rd.nx || (dx == 0 && dy == 0 && dz == 0)) continue;
+        const long long nbi = rd.off + xx + sy * yy + sz * zz;
+        if (is_free(c.state[nbi])) {
+          const T kv = K[nbi];
+          if (best < 0 || kv > best_K) {
+            best = nbi;
+            best_K = kv;
+          }
+        }
+      }
+    }
+  }
+  return best;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(512) k_ca_compact(Ctx c) {
@@ -111,7 +161,6 @@ __global__ void __launch_bounds__(256) k_ca_colour(Ctx c, int colour) {
   T* phi = (T*)c.phi;
   T* P = (T*)c.P;
   T* Vc = (T*)c.Vc;
-  const T* K = (const T*)c.K;
   unsigned int kills = 0, divs = 0, blocked = 0;
   const long long sy = rd.nxp, sz = (long long)rd.nxp * rd.ny;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -120,17 +169,7 @@ __global__ void __launch_bounds__(256) k_ca_colour(Ctx c, int colour) {
     const int y = (int)((site / (uint32_t)rd.nx) % (uint32_t)rd.ny);
     const int z = (int)(site / ((uint32_t)rd.nx * (uint32_t)rd.ny));
     const long long e = rd.off + x + sy * y + sz * z;
-    const T u = (T)site_uniform(rd.seed, site, step, PURPOSE_KILL);
-    T surv = T(1);
-    for (int d = 0; d < rd.n_drugs; ++d) {
-      T xd = rn_div(((const T*)c.G[d])[e], (T)rd.dose_peak[d]);
-      if (xd > T(1)) xd = T(1);
-      if (xd < T(0)) xd = T(0);
-      const T f = rn_sub(T(1), xd);
-      for (int q = 0; q < rd.kill_b[d]; ++q) surv = rn_mul(surv, f);
-    }
-    const T p_kill = rn_sub(T(1), surv);
-    if (u < p_kill) {
+    if (killed<T>(c, rd, e, site, step)) {
       c.state[e] = HCA_DEAD;
       phi[e] = T(0);
       P[e] = T(0);
@@ -138,28 +177,7 @@ __global__ void __launch_bounds__(256) k_ca_colour(Ctx c, int colour) {
       kills++;
       continue;
     }
-    long long best = -1;
-    T best_K = T(0);
-    for (int dz = -1; dz <= 1; ++dz) {
-      const int zz = z + dz;
-      if (zz < 0 || zz >= rd.nz) continue;
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int yy = y + dy;
-        if (yy < 0 || yy >= rd.ny) continue;
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int xx = x + dx;
-          if (xx < 0 || xx >= rd.nx || (dx == 0 && dy == 0 && dz == 0)) continue;
-          const long long nbi = rd.off + xx + sy * yy + sz * zz;
-          if (is_free(c.state[nbi])) {
-            const T kv = K[nbi];
-            if (best < 0 || kv > best_K) {
-              best = nbi;
-              best_K = kv;
-            }
-          }
-        }
-      }
-    }
+    const long long best = best_free<T>(c, rd, x, y, z);
     if (best >= 0) {
       c.state[best] = HCA_PROLIF;
       c.state[e] = HCA_PROLIF;
@@ -169,6 +187,148 @@ __global__ void __launch_bounds__(256) k_ca_colour(Ctx c, int colour) {
       phi[best] = T(0);
       P[best] = T(0);
       Vc[best] = T(0);
+      divs++;
+    } else {
+      c.state[e] = HCA_QUIESC;
+      phi[e] = T(0);
+      blocked++;
+    }
+  }
+  if (kills) atomicAdd(&s_cnt[0], kills);
+  if (divs) atomicAdd(&s_cnt[1], divs);
+  if (blocked) atomicAdd(&s_cnt[2], blocked);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    DevStats& st = c.stats[rep];
+    if (s_cnt[0]) atomicAdd((unsigned long long*)&st.kills, (unsigned long long)s_cnt[0]);
+    if (s_cnt[1]) atomicAdd((unsigned long long*)&st.divisions, (unsigned long long)s_cnt[1]);
+    if (s_cnt[2]) atomicAdd((unsigned long long*)&st.blocked, (unsigned long long)s_cnt[2]);
+  }
+}
+
+// ------------------------------------------------- synchronous update ---
+// ca_mode 1 (Section 2.5 read with Algorithm 2's rule): every committed cell
+// decides against the lattice as it was before the update, and a site picked
+// by several parents goes to the highest phi, then the lowest site index.
+// Four launches over all 27 colour lists of a replicate:
+//   decide: kill test and target (best free neighbour), claim slots reset;
+//   claim_phi: atomicMax of phi's bits at the target (phi >= 1 > 0, so the
+//              bit patterns order like the values);
+//   claim_idx: atomicMin of the site among the claims with the winning phi;
+//   apply: kills, divisions of the winners, the rest blocked.
+// Nothing the first three write is read by a decision, so thread order does
+// not matter.
+
+// Slot of the i-th committed cell of a replicate, taking the colour lists in
+// order; -1 past the end.
+__device__ __forceinline__ long long slot_of(const Ctx& c, const RepDesc& rd, int rep, int i) {
+  const int* cnt = c.list_count + rep * 27;
+  for (int col = 0; col < 27; ++col) {
+    const int n = cnt[col];
+    if (i < n) return rd.list_off[col] + i;
+    i -= n;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ int committed_total(const Ctx& c, int rep) {
+  int t = 0;
+  for (int col = 0; col < 27; ++col) t += c.list_count[rep * 27 + col];
+  return t;
+}
+
+template <typename T>
+__device__ __forceinline__ unsigned long long phi_bits(T v) {
+  if constexpr (sizeof(T) == 4) return (unsigned long long)__float_as_uint((float)v);
+  else return (unsigned long long)__double_as_longlong((double)v);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_ca_sync_decide(Ctx c) {
+  HCA_COUNT_KERNEL(c);
+  const int rep = blockIdx.y;
+  const RepDesc& rd = c.reps[rep];
+  const int n = committed_total(c, rep);
+  const uint32_t step = (uint32_t)(*c.step);
+  const long long sy = rd.nxp, sz = (long long)rd.nxp * rd.ny;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const long long slot = slot_of(c, rd, rep, i);
+    const uint32_t site = c.lists[slot];
+    const int x = (int)(site % (uint32_t)rd.nx);
+    const int y = (int)((site / (uint32_t)rd.nx) % (uint32_t)rd.ny);
+    const int z = (int)(site / ((uint32_t)rd.nx * (uint32_t)rd.ny));
+    const long long e = rd.off + x + sy * y + sz * z;
+    long long dec = -2;
+    if (!killed<T>(c, rd, e, site, step)) {
+      dec = best_free<T>(c, rd, x, y, z);
+      if (dec >= 0) {
+        c.claim_phi[dec] = 0ull;
+        c.claim_idx[dec] = 0xffffffffu;
+      }
+    }
+    c.ca_dec[slot] = dec;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_ca_sync_claim(Ctx c, int pass) {
+  HCA_COUNT_KERNEL(c);
+  const int rep = blockIdx.y;
+  const RepDesc& rd = c.reps[rep];
+  const int n = committed_total(c, rep);
+  const T* phi = (const T*)c.phi;
+  const long long sy = rd.nxp, sz = (long long)rd.nxp * rd.ny;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const long long slot = slot_of(c, rd, rep, i);
+    const long long t = c.ca_dec[slot];
+    if (t < 0) continue;
+    const uint32_t site = c.lists[slot];
+    const int x = (int)(site % (uint32_t)rd.nx);
+    const int y = (int)((site / (uint32_t)rd.nx) % (uint32_t)rd.ny);
+    const int z = (int)(site / ((uint32_t)rd.nx * (uint32_t)rd.ny));
+    const unsigned long long b = phi_bits<T>(phi[rd.off + x + sy * y + sz * z]);
+    if (pass == 0) atomicMax(c.claim_phi + t, b);
+    else if (c.claim_phi[t] == b) atomicMin(c.claim_idx + t, site);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_ca_sync_apply(Ctx c) {
+  HCA_COUNT_KERNEL(c);
+  __shared__ unsigned int s_cnt[3];
+  if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int rep = blockIdx.y;
+  const RepDesc& rd = c.reps[rep];
+  const int n = committed_total(c, rep);
+  T* phi = (T*)c.phi;
+  T* P = (T*)c.P;
+  T* Vc = (T*)c.Vc;
+  unsigned int kills = 0, divs = 0, blocked = 0;
+  const long long sy = rd.nxp, sz = (long long)rd.nxp * rd.ny;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const long long slot = slot_of(c, rd, rep, i);
+    const long long t = c.ca_dec[slot];
+    const uint32_t site = c.lists[slot];
+    const int x = (int)(site % (uint32_t)rd.nx);
+    const int y = (int)((site / (uint32_t)rd.nx) % (uint32_t)rd.ny);
+    const int z = (int)(site / ((uint32_t)rd.nx * (uint32_t)rd.ny));
+    const long long e = rd.off + x + sy * y + sz * z;
+    if (t == -2) {
+      c.state[e] = HCA_DEAD;
+      phi[e] = T(0);
+      P[e] = T(0);
+      Vc[e] = T(0);
+      kills++;
+    } else if (t >= 0 && c.claim_idx[t] == site) {
+      c.state[t] = HCA_PROLIF;
+      c.state[e] = HCA_PROLIF;
+      phi[e] = T(0);
+      P[e] = T(0);
+      Vc[e] = T(0);
+      phi[t] = T(0);
+      P[t] = T(0);
+      Vc[t] = T(0);
       divs++;
     } else {
       c.state[e] = HCA_QUIESC;
@@ -199,6 +359,21 @@ void launch_ca_colour(const Ctx& c, int colour, int blocks_x, bool fp64) {
   dim3 grid(blocks_x, c.n_reps);
   if (fp64) k_ca_colour<double><<<grid, 256, 0, c.stream>>>(c, colour);
   else k_ca_colour<float><<<grid, 256, 0, c.stream>>>(c, colour);
+}
+
+void launch_ca_sync(const Ctx& c, int blocks_x, bool fp64) {
+  dim3 grid(blocks_x, c.n_reps);
+  if (fp64) {
+    k_ca_sync_decide<double><<<grid, 256, 0, c.stream>>>(c);
+    k_ca_sync_claim<double><<<grid, 256, 0, c.stream>>>(c, 0);
+    k_ca_sync_claim<double><<<grid, 256, 0, c.stream>>>(c, 1);
+    k_ca_sync_apply<double><<<grid, 256, 0, c.stream>>>(c);
+  } else {
+    k_ca_sync_decide<float><<<grid, 256, 0, c.stream>>>(c);
+    k_ca_sync_claim<float><<<grid, 256, 0, c.stream>>>(c, 0);
+    k_ca_sync_claim<float><<<grid, 256, 0, c.stream>>>(c, 1);
+    k_ca_sync_apply<float><<<grid, 256, 0, c.stream>>>(c);
+  }
 }
 
 }  // namespace hca

@@ -29,6 +29,7 @@ void launch_philox_uniforms(unsigned long long seed, unsigned long long site0, l
 void launch_advance_step(const Ctx& c, long long by);
 void launch_ca_compact(const Ctx& c, bool fp64);
 void launch_ca_colour(const Ctx& c, int colour, int blocks_x, bool fp64);
+void launch_ca_sync(const Ctx& c, int blocks_x, bool fp64);
 void launch_mg_setup(const Ctx& c, int which, bool fp64, const MGHost& H);
 void launch_vcycle(const Ctx& c, int which, bool fp64, const MGHost& H, int part, bool scale);
 int vcycle_launches(const MGHost& H, bool scale);
@@ -74,7 +75,8 @@ struct hca_handle {
   long long step = 0;
   long long launches = 0;
   int picard_iterations = 0;
-  bool nonlinear = false;     // o2_nonlinear: a Picard solve of the oxygen equation every step
+  bool nonlinear = false;
+  bool ca_sync = false;       // ca_mode 1: synchronous CA update, higher phi wins     // o2_nonlinear: a Picard solve of the oxygen equation every step
   int prev_iters[1 + hca::MAX_DRUGS] = {0, 0, 0, 0};
   int maxit_all = 0;
   int max_outer = 0;
@@ -184,6 +186,7 @@ int validate(const hca_config& c) {
   if (c.o2_nonlinear && c.picard_maxit < 1) return HCA_ERR_ARG;
   if (c.o2_nonlinear && c.warm_start != HCA_WS_PREV) return HCA_ERR_UNIMPLEMENTED;
   if (c.drug_scheme != 0 && c.drug_scheme != 1) return HCA_ERR_ARG;
+  if (c.ca_mode != 0 && c.ca_mode != 1) return HCA_ERR_ARG;
   if (c.o2_scheme < 0 || c.o2_scheme > 2) return HCA_ERR_ARG;
   if (c.drug_substeps < 1 || c.drug_substeps > 100000 || c.o2_substeps < 1 || c.o2_substeps > 100000)
     return HCA_ERR_ARG;
@@ -552,6 +555,12 @@ int cap_solve(hca_handle* h, int which, cudaGraph_t G) {
   return HCA_OK;
 }
 
+// Blocks per replicate of the synchronous CA launches (all committed cells of
+// a replicate in one grid-stride launch).
+int ca_sync_blocks(const hca_handle* h) {
+  return std::max(1, std::min(4096, 8 * h->ctx.sm_count / std::max(1, h->n_reps)));
+}
+
 int cap_stages(hca_handle* h, uint32_t mask, cudaGraph_t G) {
   Ctx& c = h->ctx;
   c.stream = h->cap[0];
@@ -581,8 +590,12 @@ int cap_stages(hca_handle* h, uint32_t mask, cudaGraph_t G) {
   if (mask & HCA_STAGE_CA) {
     HCA_TRY(cudaMemsetAsync(c.list_count, 0, sizeof(int) * 27 * h->n_reps, c.stream));
     hca::launch_ca_compact(c, h->fp64);
-    const int bx = std::max(1, std::min(1024, 2 * c.sm_count / std::max(1, h->n_reps)));
-    for (int col = 0; col < 27; ++col) hca::launch_ca_colour(c, col, bx, h->fp64);
+    if (h->ca_sync) {
+      hca::launch_ca_sync(c, ca_sync_blocks(h), h->fp64);
+    } else {
+      const int bx = std::max(1, std::min(1024, 2 * c.sm_count / std::max(1, h->n_reps)));
+      for (int col = 0; col < 27; ++col) hca::launch_ca_colour(c, col, bx, h->fp64);
+    }
   }
   if (mask & HCA_STAGE_ADVANCE) hca::launch_advance_step(c, 1);
   HCA_TRY(cudaGetLastError());
@@ -659,6 +672,10 @@ int run_ca(hca_handle* h) {
   Ctx& c = h->ctx;
   HCA_TRY(cudaMemsetAsync(c.list_count, 0, sizeof(int) * 27 * h->n_reps, c.stream));
   HCA_LAUNCH(h, HCA_KCLASS_CA_COMPACT, 1, hca::launch_ca_compact(c, h->fp64));
+  if (h->ca_sync) {
+    HCA_LAUNCH(h, HCA_KCLASS_CA_COLOUR, 4, hca::launch_ca_sync(c, ca_sync_blocks(h), h->fp64));
+    return HCA_OK;
+  }
   const int bx = std::max(1, std::min(1024, 2 * c.sm_count / std::max(1, h->n_reps)));
   for (int col = 0; col < 27; ++col) {
     HCA_LAUNCH(h, HCA_KCLASS_CA_COLOUR, 1, hca::launch_ca_colour(c, col, bx, h->fp64));
@@ -849,7 +866,8 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
         cfgs[i].dt != cfgs[0].dt || cfgs[i].threads_per_block != cfgs[0].threads_per_block ||
         cfgs[i].stream != cfgs[0].stream || cfgs[i].o2_nonlinear != cfgs[0].o2_nonlinear ||
         cfgs[i].drug_scheme != cfgs[0].drug_scheme || cfgs[i].drug_substeps != cfgs[0].drug_substeps ||
-        cfgs[i].o2_scheme != cfgs[0].o2_scheme || cfgs[i].o2_substeps != cfgs[0].o2_substeps)
+        cfgs[i].o2_scheme != cfgs[0].o2_scheme || cfgs[i].o2_substeps != cfgs[0].o2_substeps ||
+        cfgs[i].ca_mode != cfgs[0].ca_mode)
       return HCA_ERR_ARG;
     // the learned warm start and the multigrid hierarchy serve one lattice
     if (cfgs[i].warm_start != HCA_WS_PREV && n > 1) return HCA_ERR_UNIMPLEMENTED;
@@ -865,6 +883,7 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
   h->learned = cfgs[0].warm_start != HCA_WS_PREV;
   h->mg = cfgs[0].preconditioner == HCA_PC_MG;
   h->nonlinear = cfgs[0].o2_nonlinear != 0;
+  h->ca_sync = cfgs[0].ca_mode == 1;
   if (h->nonlinear) h->graphs_ok = false;   // each Picard iterate is checked on the host
   {
     // HCA_NO_GRAPH=1 runs steps from a host loop instead of the step graph
@@ -1072,6 +1091,11 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     ALLOC(c.stats, sizeof(hca::DevStats) * n);
     ALLOC(c.step, sizeof(long long));
     ALLOC(c.lists, sizeof(uint32_t) * (size_t)std::max(1LL, h->lists_total));
+    if (h->ca_sync) {
+      ALLOC(c.ca_dec, sizeof(long long) * (size_t)std::max(1LL, h->lists_total));
+      ALLOC(c.claim_phi, sizeof(unsigned long long) * (size_t)h->total);
+      ALLOC(c.claim_idx, sizeof(unsigned int) * (size_t)h->total);
+    }
     ALLOC(c.list_count, sizeof(int) * 27 * n);
     ALLOC(c.n_kernels, sizeof(unsigned long long));
     ALLOC(c.frozen, sizeof(int) * n);

@@ -304,6 +304,12 @@ struct Ctx {
   long long* step;        // device step counter n
   uint32_t* lists;
   int* list_count;        // [rep][27]
+  // synchronous CA update (ca_mode 1): per list slot the decision (target
+  // element, -1 blocked, -2 killed); per field element the highest claiming
+  // phi (its bits) and the lowest claiming site among those
+  long long* ca_dec;
+  unsigned long long* claim_phi;
+  unsigned int* claim_idx;
   unsigned long long* n_kernels;  // kernels that ran (counted by block 0 of each)
   int* frozen;            // [rep] 1: solves leave this replicate's field untouched
   // fixed-order reductions: row sums -> chunk sums -> group sums -> replicate

@@ -81,7 +81,7 @@ class hca_config(ctypes.Structure):
         ("warm_start", ctypes.c_int32), ("preconditioner", ctypes.c_int32),
         ("threads_per_block", ctypes.c_int32), ("o2_nonlinear", ctypes.c_int32),
         ("drug_scheme", ctypes.c_int32), ("drug_substeps", ctypes.c_int32),
-        ("o2_scheme", ctypes.c_int32), ("o2_substeps", ctypes.c_int32),
+        ("o2_scheme", ctypes.c_int32), ("o2_substeps", ctypes.c_int32), ("ca_mode", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
     ]
 

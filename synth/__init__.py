@@ -6,6 +6,6 @@ no ODE, no automaton rule), so both sides may use it without sharing method
 code.
 """
 
-from .maps import MapSet, gaussian_random_field, make_maps, replicate_sizes
+from .maps import MapSet, biopsy_maps, gaussian_random_field, make_maps, replicate_sizes
 
-__all__ = ["MapSet", "gaussian_random_field", "make_maps", "replicate_sizes"]
+__all__ = ["MapSet", "biopsy_maps", "gaussian_random_field", "make_maps", "replicate_sizes"]

@@ -104,3 +104,33 @@ def replicate_sizes(n_replicates: int, choices=(64, 96, 128, 192), seed: int = 7
     rng = np.random.default_rng(seed)
     idx = rng.integers(0, len(choices), size=n_replicates)
     return [int(choices[i]) for i in idx]
+
+
+def biopsy_maps(vox_y: int = 2, vox_x: int = 10, vox_edge: int = 100, seed: int = 0) -> MapSet:
+    """Piecewise-constant maps of a 2-D digital biopsy: vox_y x vox_x MRI
+    voxels of vox_edge x vox_edge sites each (nz = 1), the layout of the
+    paper's biopsy cross-section (Section 3.4: 2 x 10 voxels of 100 x 100
+    grid points, the first half of each row in the poorly perfused tumour
+    core, the second half at the better perfused edge).
+
+    Per voxel, drawn with numpy's PCG64 generator seeded with ``seed`` (free
+    parameters of this stand-in; the paper's per-voxel Tofts estimates are
+    patient data):
+      core: perf ~ U(0.1, 0.5), vessel fraction ~ U(0.005, 0.02), cell density ~ U(0.5, 0.8)
+      edge: perf ~ U(1.0, 2.0), vessel fraction ~ U(0.03, 0.08), cell density ~ U(0.3, 0.6)
+    The lattice seeding then places vessels and cells at random inside each
+    voxel with those probabilities.
+    """
+    rng = np.random.default_rng(seed)
+    shape = (1, vox_y * vox_edge, vox_x * vox_edge)
+    p_cell = np.empty(shape, dtype=np.float32)
+    perf = np.empty(shape, dtype=np.float32)
+    p_vessel = np.empty(shape, dtype=np.float32)
+    for vy in range(vox_y):
+        for vx in range(vox_x):
+            edge = vx >= vox_x // 2
+            lo_hi = ((1.0, 2.0), (0.03, 0.08), (0.3, 0.6)) if edge else ((0.1, 0.5), (0.005, 0.02), (0.5, 0.8))
+            pf, pv, pc = (rng.uniform(a, b) for a, b in lo_hi)
+            sl = (0, slice(vy * vox_edge, (vy + 1) * vox_edge), slice(vx * vox_edge, (vx + 1) * vox_edge))
+            perf[sl], p_vessel[sl], p_cell[sl] = pf, pv, pc
+    return MapSet(p_cell, perf, p_vessel)
