@@ -21,6 +21,9 @@ One step n -> n+1 (Algorithm 1, loop body, VEGF/Avastin omitted):
      implicit Euler or Crank-Nicolson, per drug_scheme/drug_substeps); with
      o2_scheme set, step 2 is the time-dependent oxygen equation instead;
   4. ODEs for phi, P, Vc with the new K;
+  (with vegf = 1 the VEGF field of Eq. (vac_v), A = 0, is solved after
+  oxygen; with vessel_interval set the vascular automaton runs after the cell
+  update every vessel_interval steps; the plasma levels follow pk_model)
   5. the CA update (Section 2.5) with Philox draws keyed by the step index n:
      the 27-colour sweep, or with ca_mode 1 the synchronous update with
      Algorithm 2's higher-phi rule.
@@ -40,7 +43,8 @@ from .ca_sync import ca_update_sync
 from .odes import ode_update
 from .pcg import SolveInfo, pcg
 from .philox import site_uniform
-from .plasma import plasma_concentration
+from .pk import plasma_level
+from .vascular import VascularStats, vascular_update
 
 
 @dataclasses.dataclass
@@ -53,6 +57,9 @@ class StepStats:
     divisions: int
     blocked: int
     counts: np.ndarray          # sites per state code 0..5 after the step
+    vegf: SolveInfo = None      # the VEGF solve (vegf = 1)
+    vessel_births: int = 0
+    vessel_deaths: int = 0
 
 
 def seed_lattice(cfg: Pm.Config, p_cell, p_vessel):
@@ -132,18 +139,38 @@ def drug_step(state, perf, G_old, step_index: int, cfg: Pm.Config, d: int):
     kappa = S.drug_kappa(state, perf, cfg, d)
     reaction = S.drug_reaction(state, perf, cfg, d, mass=S.time_mass(scheme, h))
     diag = S.jacobi_diagonal(state.shape, coupling, reaction)
-    period = cfg.dose_interval * cfg.dt
     G = np.asarray(G_old, dtype=np.float64)
     infos = []
     for j in range(m):
         t_old = (step_index + j / m) * cfg.dt
         t_new = (step_index + (j + 1) / m) * cfg.dt
-        f_old = kappa * plasma_concentration(t_old, cfg.dose_peak[d], cfg.plasma_decay[d], period)
-        f_new = kappa * plasma_concentration(t_new, cfg.dose_peak[d], cfg.plasma_decay[d], period)
+        f_old = kappa * plasma_level(cfg, d, t_old)
+        f_new = kappa * plasma_level(cfg, d, t_new)
         b = S.time_rhs(scheme, h, G, coupling, a0, f_old, f_new)
         G, info = pcg(lambda u: S.apply_operator(u, coupling, reaction), b, G, diag, cfg.rtol_drug, cfg.maxit)
         infos.append(info)
     return G, infos
+
+
+def vegf_step(state, V_old, Vc, cfg: Pm.Config):
+    """Eq. (vac_v) with A = 0 over one CA step, stepped like the drugs
+    (drug_scheme, drug_substeps): reaction psi_V, source a_V Vc at cells
+    (constant over the step: Vc is the previous step's).  Returns (V, infos)."""
+    m = cfg.drug_substeps
+    h = cfg.dt / m
+    scheme = 1 if cfg.drug_scheme == 0 else 2
+    coupling = cfg.D_V / cfg.dx ** 2
+    a0 = np.full(state.shape, cfg.psi_V)
+    reaction = S.time_mass(scheme, h) + a0
+    diag = S.jacobi_diagonal(state.shape, coupling, reaction)
+    f = np.where(S.is_consumer(state), cfg.a_V * np.asarray(Vc, dtype=np.float64), 0.0)
+    V = np.asarray(V_old, dtype=np.float64)
+    infos = []
+    for _ in range(m):
+        b = S.time_rhs(scheme, h, V, coupling, a0, f, f)
+        V, info = pcg(lambda u: S.apply_operator(u, coupling, reaction), b, V, diag, cfg.rtol_drug, cfg.maxit)
+        infos.append(info)
+    return V, infos
 
 
 def o2_transient_step(state, K_old, cfg: Pm.Config):
@@ -170,8 +197,7 @@ def o2_transient_step(state, K_old, cfg: Pm.Config):
 
 
 def plasma_levels(cfg: Pm.Config, t: float):
-    return [plasma_concentration(t, cfg.dose_peak[d], cfg.plasma_decay[d],
-                                 cfg.dose_interval * cfg.dt) for d in range(cfg.n_drugs)]
+    return [plasma_level(cfg, d, t) for d in range(cfg.n_drugs)]
 
 
 class OracleSim:
@@ -184,6 +210,7 @@ class OracleSim:
         self.P = np.zeros(cfg.shape)
         self.Vc = np.zeros(cfg.shape)
         self.G = [np.zeros(cfg.shape) for _ in range(cfg.n_drugs)]
+        self.V = np.zeros(cfg.shape)
         self.step_index = 0
         self.history: List[StepStats] = []
         if initial_o2:
@@ -202,6 +229,18 @@ class OracleSim:
             return None
         self.K, info = o2_solve(self.state, self.K, self.cfg)
         return info
+
+    def solve_vegf(self):
+        self.V, infos = vegf_step(self.state, self.V, self.Vc, self.cfg)
+        return infos[-1]
+
+    def update_vessels(self):
+        """The vascular automaton after the cell update of steps n with
+        (n + 1) % vessel_interval == 0."""
+        if not self.cfg.vessel_interval or (self.step_index + 1) % self.cfg.vessel_interval:
+            return VascularStats()
+        self.state, vs = vascular_update(self.state, self.V, self.cfg, self.step_index)
+        return vs
 
     def solve_drugs(self):
         infos = []
@@ -223,11 +262,14 @@ class OracleSim:
     def step(self, n_steps: int = 1):
         for _ in range(n_steps):
             o2 = self.solve_o2()
+            vegf = self.solve_vegf() if self.cfg.vegf else None
             drugs = self.solve_drugs()
             self.update_odes()
             st = self.update_ca()
+            vs = self.update_vessels()
             counts = np.bincount(self.state.reshape(-1), minlength=6)[:6]
             self.history.append(StepStats(self.step_index, o2, drugs, st.committed,
-                                          st.kills, st.divisions, st.blocked, counts))
+                                          st.kills, st.divisions, st.blocked, counts, vegf,
+                                          vs.births, vs.deaths))
             self.step_index += 1
         return self.history[-1] if self.history else None

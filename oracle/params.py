@@ -29,6 +29,7 @@ PURPOSE_VESSEL = 0
 PURPOSE_CANCER = 1
 PURPOSE_PHI = 2
 PURPOSE_KILL = 3
+PURPOSE_VASCULAR = 4
 
 
 def _three(v):
@@ -70,6 +71,32 @@ class Config:
     # CA update: 0 the 27-colour Gauss-Seidel sweep (ca.py); 1 synchronous,
     # a contested site going to the higher phi (Algorithm 2; ca_sync.py)
     ca_mode: int = 0
+
+    # VEGF field, Eq. (vac_v) without Avastin (A = 0), Table 1: solved every
+    # step after oxygen when vegf = 1, stepped like the drugs (drug_scheme,
+    # drug_substeps); released by cells at rate a_V * Vc
+    vegf: int = 0
+    D_V: float = 3.52e3             # um^2/min
+    psi_V: float = 1e-2             # 1/min
+    a_V: float = 6.66e-6            # 1/min, VEGF secretion slope
+    # vascular birth-death CA (Eq. vascular_module) every vessel_interval steps
+    # (0 = off; 12 = Delta v of 720 min at hourly steps)
+    vessel_interval: int = 0
+    V_low: float = 1e-6             # Table 1
+    V_high: float = 1e-3            # reading: not published
+    p_death: float = 0.1            # reading: not published
+    beta_birth: float = 0.05        # reading: Pr_sprout 2 pi r0 h_c Delta v lumped (not published)
+    V_sprout: float = 1e-4          # reading: not published
+    # plasma pharmacokinetics per drug: 0 one-compartment exponential
+    # (plasma_decay), 1 Michaelis-Menten (mm_vmax, mm_km; Eq. for fluorouracil),
+    # 2 three-compartment (epi_*; Eq. for epirubicin)
+    pk_model: Tuple[int, int, int] = (0, 0, 0)
+    mm_vmax: float = 1.75           # ug/mL/min, Table 1
+    mm_km: float = 27.0             # ug/mL, Table 1
+    epi_w: Tuple[float, float, float] = (18e3, 957e3, 25e3)   # mL, Table 1
+    epi_q2: float = 0.918e3         # mL/min, Table 1
+    epi_q3: float = 0.25e3
+    epi_cl2: float = 0.983e3
     ode_substeps: int = 60          # RK4 step h = dt / ode_substeps = 1 min (Section 2.4.2)
 
     # oxygen, Eq. (oxygen) and Table 1
