@@ -81,6 +81,7 @@ extern "C" {
 #define HCA_FIELD_P53 (1u << 5)    /* intracellular p53, P */
 #define HCA_FIELD_VEGFC (1u << 6)  /* intracellular VEGF, Vc */
 #define HCA_FIELD_PERF (1u << 7)   /* perfusion map (the vessel-exchange scale) */
+#define HCA_FIELD_VEGF (1u << 8)   /* extracellular VEGF, V (ug/mL; vegf = 1) */
 
 /* stages for hca_stage; HCA_STAGE_ALL runs one full step (as hca_step(h, 1)) */
 #define HCA_STAGE_O2 (1u << 0)
@@ -184,6 +185,31 @@ typedef struct hca_config {
                             committed cell decides on the lattice before the update and a site
                             picked by several parents goes to the highest phi, then the lowest
                             site index (Algorithm 2); must match across a batch */
+  /* VEGF field and vascular automaton (Sections 2.2.2, 2.3), without Avastin:
+     with vegf = 1, Eq. (vac_v) with A = 0, dV/dt = D_V lap V + a_V Vc [cell]
+     - psi_V V, is solved every step after oxygen, stepped like the drugs
+     (drug_scheme, drug_substeps; Vc of the previous step).  With
+     vessel_interval > 0 the vascular birth-death automaton (Eq.
+     vascular_module) runs after the cell update of every step n with
+     (n + 1) % vessel_interval == 0: a vessel with V outside [V_low, V_high]
+     is removed with probability p_death; a free site with V inside becomes a
+     vessel with probability min(1, E V / sum_candidates V), E = beta_birth
+     sum_vessels V / (V_sprout + V) (both sums in 2^-32 fixed point, exact).
+     Needs vegf = 1. */
+  int32_t vegf;
+  int32_t vessel_interval;
+  /* plasma pharmacokinetics per drug (Section 2.2.3): 0 one-compartment
+     exponential (plasma_decay); 1 Michaelis-Menten, dG/dt = -mm_vmax G /
+     (mm_km + G), each dose adding dose_peak to the level before it; 2 three
+     compartments (epi_w, epi_q2, epi_q3, epi_cl2), doses superposed */
+  int32_t pk_model[3];
+  int32_t pad3;
+  double D_V, psi_V, a_V;        /* 3.52e3 um^2/min, 1e-2 /min, 6.66e-6 /min (Table 1) */
+  double V_low, V_high;          /* 1e-6 (Table 1), 1e-3 ug/mL */
+  double p_death, beta_birth, V_sprout; /* 0.1, 0.05, 1e-4 ug/mL */
+  double mm_vmax, mm_km;         /* 1.75 ug/mL/min, 27 ug/mL (Table 1) */
+  double epi_w[3];               /* 18e3, 957e3, 25e3 mL (Table 1) */
+  double epi_q2, epi_q3, epi_cl2; /* 0.918e3, 0.25e3, 0.983e3 mL/min (Table 1) */
   void* stream;          /* cudaStream_t, NULL = default stream */
 } hca_config;
 
@@ -204,6 +230,10 @@ typedef struct hca_stats {
   int32_t pad1;
   double ws_r0_prev;            /* HCA_WS_LEARNED: ||b - A K_prev|| / ||b|| before the last oxygen solve */
   double ws_r0_learned;         /* HCA_WS_LEARNED: the same for the network's guess */
+  int32_t vegf_iterations;      /* vegf = 1: CG iterations of the last step's VEGF solves */
+  int32_t pad2;
+  double vegf_rel_residual;
+  int64_t vessel_births, vessel_deaths; /* last vascular update (0 on other steps) */
 } hca_stats;
 
 typedef struct hca_handle hca_handle;

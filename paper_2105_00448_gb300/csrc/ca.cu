@@ -348,6 +348,110 @@ __global__ void __launch_bounds__(256) k_ca_sync_apply(Ctx c) {
   }
 }
 
+// --------------------------------------------------- vascular automaton ---
+// Every vessel_interval steps, after the cell update (Eq. vascular_module,
+// Section 2.2.2, A = 0): one Philox draw u per site keyed (seed, site, step,
+// VASCULAR).  A vessel with V outside [V_low, V_high] is removed if
+// u < p_death; a free site with V inside becomes a vessel if
+// u < min(1, (beta_birth S1 (V / V_high)) / S2), where S1 = sum over vessels of
+// floor(2^32 V / (V_sprout + V)) and S2 = sum over candidate sites of
+// floor(2^32 V / V_high): exact integer sums, so the probability does not
+// depend on summation order.  Two launches: the sums (atomic 64-bit integer
+// adds), then the update.
+
+__device__ __forceinline__ bool vessel_step(const Ctx& c, const RepDesc& rd) {
+  return rd.vessel_interval > 0 && ((*c.step) + 1) % rd.vessel_interval == 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_vessel_sums(Ctx c) {
+  HCA_COUNT_KERNEL(c);
+  __shared__ unsigned long long s_sum[2];
+  const int2 ch = c.chunks[blockIdx.x];
+  const int rep = ch.x;
+  const RepDesc& rd = c.reps[rep];
+  if (!vessel_step(c, rd)) return;
+  if (threadIdx.x < 2) s_sum[threadIdx.x] = 0ull;
+  __syncthreads();
+  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const long long base0 = rd.off + (long long)ch.y * rd.nxp;
+  const T* V = (const T*)c.G[VEGF_SLOT];
+  unsigned long long a1 = 0ull, a2 = 0ull;
+  for (int i = threadIdx.x; i < nrows * rd.nxp; i += blockDim.x) {
+    const int rl = i / rd.nxp, x = i - rl * rd.nxp;
+    if (x >= rd.nx) continue;
+    const long long e = base0 + (long long)rl * rd.nxp + x;
+    const uint8_t s = c.state[e];
+    const double v = (double)V[e];
+    if (s == HCA_VESSEL) a1 += (unsigned long long)floor(v / (rd.V_sprout + v) * 4294967296.0);
+    else if (is_free(s) && v >= rd.V_low && v <= rd.V_high)
+      a2 += (unsigned long long)floor(v / rd.V_high * 4294967296.0);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a1 += __shfl_xor_sync(FULL, a1, o);
+    a2 += __shfl_xor_sync(FULL, a2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&s_sum[0], a1);
+    atomicAdd(&s_sum[1], a2);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicAdd(&c.vsum[2 * rep], s_sum[0]);
+    atomicAdd(&c.vsum[2 * rep + 1], s_sum[1]);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_vessel_update(Ctx c) {
+  HCA_COUNT_KERNEL(c);
+  __shared__ unsigned int s_cnt[2];
+  const int2 ch = c.chunks[blockIdx.x];
+  const int rep = ch.x;
+  const RepDesc& rd = c.reps[rep];
+  if (!vessel_step(c, rd)) return;
+  if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0u;
+  __syncthreads();
+  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const long long base0 = rd.off + (long long)ch.y * rd.nxp;
+  const T* V = (const T*)c.G[VEGF_SLOT];
+  const double S1 = (double)c.vsum[2 * rep], S2 = (double)c.vsum[2 * rep + 1];
+  const uint32_t step = (uint32_t)(*c.step);
+  unsigned int births = 0, deaths = 0;
+  for (int i = threadIdx.x; i < nrows * rd.nxp; i += blockDim.x) {
+    const int rl = i / rd.nxp, x = i - rl * rd.nxp;
+    if (x >= rd.nx) continue;
+    const long long e = base0 + (long long)rl * rd.nxp + x;
+    const uint8_t s = c.state[e];
+    const double v = (double)V[e];
+    const bool in_range = v >= rd.V_low && v <= rd.V_high;
+    const bool vessel = s == HCA_VESSEL;
+    if (!(vessel && !in_range) && !(is_free(s) && in_range && S2 > 0.0)) continue;
+    const int j = ch.y + rl;
+    const unsigned long long site = (unsigned long long)x + (unsigned long long)rd.nx * (unsigned long long)j;
+    const double u = (double)site_uniform(rd.seed, site, step, PURPOSE_VASCULAR);
+    if (vessel) {
+      if (u < rd.p_death) {
+        c.state[e] = HCA_EMPTY;
+        deaths++;
+      }
+    } else {
+      const double p = fmin(1.0, __ddiv_rn(__dmul_rn(__dmul_rn(rd.beta_birth, S1), __ddiv_rn(v, rd.V_high)), S2));
+      if (u < p) {
+        c.state[e] = HCA_VESSEL;
+        births++;
+      }
+    }
+  }
+  if (births) atomicAdd(&s_cnt[0], births);
+  if (deaths) atomicAdd(&s_cnt[1], deaths);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_cnt[0]) atomicAdd((unsigned long long*)&c.stats[rep].vessel_births, (unsigned long long)s_cnt[0]);
+    if (s_cnt[1]) atomicAdd((unsigned long long*)&c.stats[rep].vessel_deaths, (unsigned long long)s_cnt[1]);
+  }
+}
+
 }  // namespace
 
 void launch_ca_compact(const Ctx& c, bool fp64) {
@@ -373,6 +477,16 @@ void launch_ca_sync(const Ctx& c, int blocks_x, bool fp64) {
     k_ca_sync_claim<float><<<grid, 256, 0, c.stream>>>(c, 0);
     k_ca_sync_claim<float><<<grid, 256, 0, c.stream>>>(c, 1);
     k_ca_sync_apply<float><<<grid, 256, 0, c.stream>>>(c);
+  }
+}
+
+void launch_vessels(const Ctx& c, bool fp64) {
+  if (fp64) {
+    k_vessel_sums<double><<<c.n_chunks, c.threads, 0, c.stream>>>(c);
+    k_vessel_update<double><<<c.n_chunks, c.threads, 0, c.stream>>>(c);
+  } else {
+    k_vessel_sums<float><<<c.n_chunks, c.threads, 0, c.stream>>>(c);
+    k_vessel_update<float><<<c.n_chunks, c.threads, 0, c.stream>>>(c);
   }
 }
 

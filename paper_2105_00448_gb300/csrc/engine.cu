@@ -30,6 +30,7 @@ void launch_advance_step(const Ctx& c, long long by);
 void launch_ca_compact(const Ctx& c, bool fp64);
 void launch_ca_colour(const Ctx& c, int colour, int blocks_x, bool fp64);
 void launch_ca_sync(const Ctx& c, int blocks_x, bool fp64);
+void launch_vessels(const Ctx& c, bool fp64);
 void launch_mg_setup(const Ctx& c, int which, bool fp64, const MGHost& H);
 void launch_vcycle(const Ctx& c, int which, bool fp64, const MGHost& H, int part, bool scale);
 int vcycle_launches(const MGHost& H, bool scale);
@@ -76,12 +77,14 @@ struct hca_handle {
   long long launches = 0;
   int picard_iterations = 0;
   bool nonlinear = false;
-  bool ca_sync = false;       // ca_mode 1: synchronous CA update, higher phi wins     // o2_nonlinear: a Picard solve of the oxygen equation every step
-  int prev_iters[1 + hca::MAX_DRUGS] = {0, 0, 0, 0};
+  bool ca_sync = false;       // ca_mode 1: synchronous CA update, higher phi wins
+  bool vegf = false;          // the VEGF field (slot 3) is solved every step
+  bool vessels = false;       // some replicate runs the vascular automaton     // o2_nonlinear: a Picard solve of the oxygen equation every step
+  int prev_iters[1 + hca::MAX_FIELDS] = {0, 0, 0, 0, 0};
   int maxit_all = 0;
   int max_outer = 0;
   int last_iters = 0;
-  int prev_inner[1 + hca::MAX_DRUGS][16] = {};
+  int prev_inner[1 + hca::MAX_FIELDS][16] = {};
   // step graphs (one per stage mask), built on first use
   struct Graph {
     uint32_t mask;
@@ -187,6 +190,20 @@ int validate(const hca_config& c) {
   if (c.o2_nonlinear && c.warm_start != HCA_WS_PREV) return HCA_ERR_UNIMPLEMENTED;
   if (c.drug_scheme != 0 && c.drug_scheme != 1) return HCA_ERR_ARG;
   if (c.ca_mode != 0 && c.ca_mode != 1) return HCA_ERR_ARG;
+  if (c.vegf != 0 && c.vegf != 1) return HCA_ERR_ARG;
+  if (c.vessel_interval < 0 || (c.vessel_interval > 0 && !c.vegf)) return HCA_ERR_ARG;
+  if (!(c.D_V >= 0) || !(c.psi_V >= 0) || !(c.a_V >= 0)) return HCA_ERR_ARG;
+  if (c.vessel_interval > 0 && (!(c.V_low >= 0) || !(c.V_high > c.V_low) || !(c.p_death >= 0 && c.p_death <= 1) ||
+                                !(c.beta_birth >= 0) || !(c.V_sprout > 0)))
+    return HCA_ERR_ARG;
+  for (int d = 0; d < 3; ++d) {
+    if (c.pk_model[d] < 0 || c.pk_model[d] > 2) return HCA_ERR_ARG;
+    if (d < c.n_drugs && c.pk_model[d] == 1 && (!(c.mm_vmax > 0) || !(c.mm_km > 0))) return HCA_ERR_ARG;
+    if (d < c.n_drugs && c.pk_model[d] == 2 &&
+        (!(c.epi_w[0] > 0) || !(c.epi_w[1] > 0) || !(c.epi_w[2] > 0) || !(c.epi_q2 > 0) || !(c.epi_q3 > 0) ||
+         !(c.epi_cl2 > 0)))
+      return HCA_ERR_ARG;
+  }
   if (c.o2_scheme < 0 || c.o2_scheme > 2) return HCA_ERR_ARG;
   if (c.drug_substeps < 1 || c.drug_substeps > 100000 || c.o2_substeps < 1 || c.o2_substeps > 100000)
     return HCA_ERR_ARG;
@@ -203,6 +220,50 @@ int validate(const hca_config& c) {
     return HCA_ERR_ARG;
   if (c.preconditioner != HCA_PC_JACOBI && c.preconditioner != HCA_PC_MG) return HCA_ERR_ARG;
   return HCA_OK;
+}
+
+// Plasma response of the three-compartment model to a unit bolus,
+// [exp(M t)]_00 = sum_i coef_i exp(lam_i t), with M the rate matrix of the
+// compartment amounts.  D M D^-1 with D = diag(w)^(-1/2) is symmetric and has
+// the same (0,0) entry of its exponential, so lam_i are its eigenvalues and
+// coef_i the squared first components of its unit eigenvectors (cyclic
+// Jacobi rotations, FP64).
+void three_compartment_response(const hca_config& c, double lam[3], double coef[3]) {
+  const double w1 = c.epi_w[0], w2 = c.epi_w[1], w3 = c.epi_w[2];
+  double S[3][3] = {{-(c.epi_cl2 + c.epi_q2 + c.epi_q3) / w1, c.epi_q2 / std::sqrt(w1 * w2), c.epi_q3 / std::sqrt(w1 * w3)},
+                    {c.epi_q2 / std::sqrt(w1 * w2), -c.epi_q2 / w2, 0.0},
+                    {c.epi_q3 / std::sqrt(w1 * w3), 0.0, -c.epi_q3 / w3}};
+  double V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  for (int sweep = 0; sweep < 64; ++sweep) {
+    const double off = std::fabs(S[0][1]) + std::fabs(S[0][2]) + std::fabs(S[1][2]);
+    if (off == 0.0) break;
+    for (int p = 0; p < 2; ++p)
+      for (int q = p + 1; q < 3; ++q) {
+        if (S[p][q] == 0.0) continue;
+        const double theta = (S[q][q] - S[p][p]) / (2.0 * S[p][q]);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+        for (int k = 0; k < 3; ++k) {   // S <- S J (columns p, q)
+          const double a = S[k][p], b = S[k][q];
+          S[k][p] = cs * a - sn * b;
+          S[k][q] = sn * a + cs * b;
+        }
+        for (int k = 0; k < 3; ++k) {   // S <- J^T S (rows p, q)
+          const double a = S[p][k], b = S[q][k];
+          S[p][k] = cs * a - sn * b;
+          S[q][k] = sn * a + cs * b;
+        }
+        for (int k = 0; k < 3; ++k) {   // V <- V J
+          const double a = V[k][p], b = V[k][q];
+          V[k][p] = cs * a - sn * b;
+          V[k][q] = sn * a + cs * b;
+        }
+      }
+  }
+  for (int i = 0; i < 3; ++i) {
+    lam[i] = S[i][i];
+    coef[i] = V[0][i] * V[0][i];
+  }
 }
 
 RepDesc make_desc(const hca_config& c) {
@@ -249,6 +310,28 @@ RepDesc make_desc(const hca_config& c) {
     r.plasma_decay[d] = c.plasma_decay[d];
     r.kill_b[d] = c.kill_b[d];
   }
+  // the VEGF field (Eq. vac_v, A = 0) in slot 3: stepped like the drugs, no
+  // vessel exchange, released by the cells
+  r.bx[hca::WHICH_VEGF] = c.drug_scheme ? 4.0 / hd : 1.0 / hd;
+  r.bax[hca::WHICH_VEGF] = c.drug_scheme == 1;
+  r.nsub[hca::WHICH_VEGF] = c.drug_substeps;
+  r.c_drug[hca::VEGF_SLOT] = c.D_V / dx2;
+  r.base_drug[hca::VEGF_SLOT] = (c.drug_scheme ? 2.0 / hd : 1.0 / hd) + c.psi_V;
+  r.kappa[hca::VEGF_SLOT] = 0.0;
+  r.uptake[hca::VEGF_SLOT] = 0.0;
+  r.a_vegf = c.a_V;
+  for (int d = 0; d < hca::MAX_DRUGS; ++d) {
+    r.pk_model[d] = c.pk_model[d];
+    if (c.pk_model[d] == 2) three_compartment_response(c, r.pk_lam[d], r.pk_coef[d]);
+  }
+  r.mm_vmax = c.mm_vmax;
+  r.mm_km = c.mm_km;
+  r.vessel_interval = c.vessel_interval;
+  r.V_low = c.V_low;
+  r.V_high = c.V_high;
+  r.p_death = c.p_death;
+  r.beta_birth = c.beta_birth;
+  r.V_sprout = c.V_sprout;
   r.dose_interval_min = c.dose_interval * c.dt;
   r.dt = c.dt;
   r.T_cycle = c.T_cycle;
@@ -305,6 +388,7 @@ void* field_ptr(hca_handle* h, uint32_t bit) {
     case HCA_FIELD_P53: return h->ctx.P;
     case HCA_FIELD_VEGFC: return h->ctx.Vc;
     case HCA_FIELD_PERF: return h->ctx.perf;
+    case HCA_FIELD_VEGF: return h->vegf ? h->ctx.G[hca::VEGF_SLOT] : nullptr;
     default: return nullptr;
   }
 }
@@ -577,6 +661,13 @@ int cap_stages(hca_handle* h, uint32_t mask, cudaGraph_t G) {
     c.sub = 0;
     if (rc) return rc;
   }
+  if ((mask & HCA_STAGE_O2) && h->vegf)
+    for (int j = 0; j < h->cfgs[0].drug_substeps; ++j) {
+      c.sub = j;
+      rc = cap_solve(h, hca::WHICH_VEGF, G);
+      c.sub = 0;
+      if (rc) return rc;
+    }
   if (mask & HCA_STAGE_DRUGS)
     for (int d = 0; d < h->n_drugs; ++d)
       for (int j = 0; j < h->cfgs[0].drug_substeps; ++j) {
@@ -595,6 +686,10 @@ int cap_stages(hca_handle* h, uint32_t mask, cudaGraph_t G) {
     } else {
       const int bx = std::max(1, std::min(1024, 2 * c.sm_count / std::max(1, h->n_reps)));
       for (int col = 0; col < 27; ++col) hca::launch_ca_colour(c, col, bx, h->fp64);
+    }
+    if (h->vessels) {
+      HCA_TRY(cudaMemsetAsync(c.vsum, 0, sizeof(unsigned long long) * 2 * h->n_reps, c.stream));
+      hca::launch_vessels(c, h->fp64);
     }
   }
   if (mask & HCA_STAGE_ADVANCE) hca::launch_advance_step(c, 1);
@@ -702,6 +797,14 @@ int run_stages(hca_handle* h, uint32_t mask) {
     h->ctx.sub = 0;
     if (rc) return rc;
   }
+  if ((mask & HCA_STAGE_O2) && h->vegf) {
+    for (int j = 0; j < h->cfgs[0].drug_substeps && !rc; ++j) {
+      h->ctx.sub = j;
+      rc = solve(h, hca::WHICH_VEGF);
+    }
+    h->ctx.sub = 0;
+    if (rc) return rc;
+  }
   if (mask & HCA_STAGE_DRUGS) {
     for (int d = 0; d < h->n_drugs; ++d)
       for (int j = 0; j < h->cfgs[0].drug_substeps; ++j) {
@@ -718,6 +821,10 @@ int run_stages(hca_handle* h, uint32_t mask) {
   if (mask & HCA_STAGE_CA) {
     rc = run_ca(h);
     if (rc) return rc;
+    if (h->vessels) {
+      HCA_TRY(cudaMemsetAsync(h->ctx.vsum, 0, sizeof(unsigned long long) * 2 * h->n_reps, h->ctx.stream));
+      HCA_LAUNCH(h, HCA_KCLASS_CA_COLOUR, 2, hca::launch_vessels(h->ctx, h->fp64));
+    }
   }
   if (mask & HCA_STAGE_ADVANCE) {
     HCA_LAUNCH(h, HCA_KCLASS_OTHER, 1, hca::launch_advance_step(h->ctx, 1));
@@ -867,7 +974,7 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
         cfgs[i].stream != cfgs[0].stream || cfgs[i].o2_nonlinear != cfgs[0].o2_nonlinear ||
         cfgs[i].drug_scheme != cfgs[0].drug_scheme || cfgs[i].drug_substeps != cfgs[0].drug_substeps ||
         cfgs[i].o2_scheme != cfgs[0].o2_scheme || cfgs[i].o2_substeps != cfgs[0].o2_substeps ||
-        cfgs[i].ca_mode != cfgs[0].ca_mode)
+        cfgs[i].ca_mode != cfgs[0].ca_mode || cfgs[i].vegf != cfgs[0].vegf)
       return HCA_ERR_ARG;
     // the learned warm start and the multigrid hierarchy serve one lattice
     if (cfgs[i].warm_start != HCA_WS_PREV && n > 1) return HCA_ERR_UNIMPLEMENTED;
@@ -884,6 +991,8 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
   h->mg = cfgs[0].preconditioner == HCA_PC_MG;
   h->nonlinear = cfgs[0].o2_nonlinear != 0;
   h->ca_sync = cfgs[0].ca_mode == 1;
+  h->vegf = cfgs[0].vegf != 0;
+  for (int i = 0; i < n; ++i) h->vessels = h->vessels || cfgs[i].vessel_interval > 0;
   if (h->nonlinear) h->graphs_ok = false;   // each Picard iterate is checked on the host
   {
     // HCA_NO_GRAPH=1 runs steps from a host loop instead of the step graph
@@ -962,8 +1071,11 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     ALLOC(c.K, fbytes);
     if (!h->fp64) ALLOC(c.K_lo, fbytes);
     for (int d = 0; d < h->n_drugs; ++d) ALLOC(c.G[d], fbytes);
+    if (h->vegf) ALLOC(c.G[hca::VEGF_SLOT], fbytes);
+    if (h->vessels) ALLOC(c.vsum, sizeof(unsigned long long) * 2 * (size_t)n);
     if (!h->fp64) {
       for (int d = 0; d < h->n_drugs; ++d) ALLOC(c.G_lo[d], fbytes);
+      if (h->vegf) ALLOC(c.G_lo[hca::VEGF_SLOT], fbytes);
       ALLOC(c.dx, fbytes);
       ALLOC(c.reac, fbytes);
     }
@@ -1118,7 +1230,7 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
       goto fail;
     }
     // zero every device array (padding sites must hold 0)
-    void* zero_list[] = {c.K, c.K_lo, c.G[0], c.G[1], c.G[2], c.G_lo[0], c.G_lo[1], c.G_lo[2], c.dx,
+    void* zero_list[] = {c.K, c.K_lo, c.G[0], c.G[1], c.G[2], c.G[3], c.G_lo[0], c.G_lo[1], c.G_lo[2], c.G_lo[3], c.dx,
                          c.phi, c.P, c.Vc, c.perf, c.z, c.p, c.p_alt, c.d, c.b, c.aux, c.reac, c.r, c.mg_t0, c.mg_w};
     for (void* p : zero_list)
       if (p && cudaMemsetAsync(p, 0, fbytes, s)) {
@@ -1267,6 +1379,22 @@ int hca_config_default(hca_config* c, int32_t nx, int32_t ny, int32_t nz) {
   c->picard_maxit = 100;
   c->drug_substeps = 1;
   c->o2_substeps = 1;
+  c->D_V = 3.52e3;
+  c->psi_V = 1e-2;
+  c->a_V = 6.66e-6;
+  c->V_low = 1e-6;
+  c->V_high = 1e-3;
+  c->p_death = 0.1;
+  c->beta_birth = 0.05;
+  c->V_sprout = 1e-4;
+  c->mm_vmax = 1.75;
+  c->mm_km = 27.0;
+  c->epi_w[0] = 18e3;
+  c->epi_w[1] = 957e3;
+  c->epi_w[2] = 25e3;
+  c->epi_q2 = 0.918e3;
+  c->epi_q3 = 0.25e3;
+  c->epi_cl2 = 0.983e3;
   c->dose_interval = 21;
   c->D_K = 1.05e5;
   c->phi_K = 900.0;
@@ -1335,12 +1463,12 @@ int hca_stage(hca_handle* h, uint32_t mask) {
 }
 
 int hca_read_fields(hca_handle* h, int32_t rep, uint32_t mask, void* dst, size_t dst_bytes, int32_t dst_on_device) {
-  if (check_rep(h, rep) || !dst || (mask & ~0xFFu) || !mask) return HCA_ERR_ARG;
+  if (check_rep(h, rep) || !dst || (mask & ~0x1FFu) || !mask) return HCA_ERR_ARG;
   const RepDesc& r = h->reps_h[rep];
   const size_t es = elem_size(h);
   const size_t per = (size_t)r.nx * r.ny * r.nz;
   size_t k = 0;
-  for (uint32_t bit = 1; bit <= 0x80u; bit <<= 1)
+  for (uint32_t bit = 1; bit <= 0x100u; bit <<= 1)
     if (mask & bit) {
       if (!field_ptr(h, bit)) return HCA_ERR_ARG;
       ++k;
@@ -1348,7 +1476,7 @@ int hca_read_fields(hca_handle* h, int32_t rep, uint32_t mask, void* dst, size_t
   if (dst_bytes < k * per * es) return HCA_ERR_ARG;
   (void)dst_on_device;
   size_t slot = 0;
-  for (uint32_t bit = 1; bit <= 0x80u; bit <<= 1) {
+  for (uint32_t bit = 1; bit <= 0x100u; bit <<= 1) {
     if (!(mask & bit)) continue;
     int rc = copy_field(h, rep, field_ptr(h, bit), es, dst, true, slot * per);
     if (rc) return rc;
@@ -1360,12 +1488,12 @@ int hca_read_fields(hca_handle* h, int32_t rep, uint32_t mask, void* dst, size_t
 
 int hca_write_fields(hca_handle* h, int32_t rep, uint32_t mask, const void* src, size_t src_bytes,
                      int32_t src_on_device) {
-  if (check_rep(h, rep) || !src || (mask & ~0xFFu) || !mask) return HCA_ERR_ARG;
+  if (check_rep(h, rep) || !src || (mask & ~0x1FFu) || !mask) return HCA_ERR_ARG;
   const RepDesc& r = h->reps_h[rep];
   const size_t es = elem_size(h);
   const size_t per = (size_t)r.nx * r.ny * r.nz;
   size_t k = 0;
-  for (uint32_t bit = 1; bit <= 0x80u; bit <<= 1)
+  for (uint32_t bit = 1; bit <= 0x100u; bit <<= 1)
     if (mask & bit) {
       if (!field_ptr(h, bit)) return HCA_ERR_ARG;
       ++k;
@@ -1373,12 +1501,13 @@ int hca_write_fields(hca_handle* h, int32_t rep, uint32_t mask, const void* src,
   if (src_bytes < k * per * es) return HCA_ERR_ARG;
   (void)src_on_device;
   size_t slot = 0;
-  for (uint32_t bit = 1; bit <= 0x80u; bit <<= 1) {
+  for (uint32_t bit = 1; bit <= 0x100u; bit <<= 1) {
     if (!(mask & bit)) continue;
     int rc = copy_field(h, rep, field_ptr(h, bit), es, const_cast<void*>(src), false, slot * per);
     if (rc) return rc;
     void* lo = nullptr;
     if (bit == HCA_FIELD_O2) lo = h->ctx.K_lo;
+    if (bit == HCA_FIELD_VEGF) lo = h->ctx.G_lo[hca::VEGF_SLOT];
     for (int d = 0; d < h->n_drugs; ++d)
       if (bit == (HCA_FIELD_DRUG0 << d)) lo = h->ctx.G_lo[d];
     if (lo) {
@@ -1442,6 +1571,10 @@ int hca_get_stats(hca_handle* h, int32_t rep, hca_stats* out) {
     out->drug_rel_residual[d] = st.rel[1 + d];
   }
   out->o2_rel_residual = st.rel[0];
+  out->vegf_iterations = st.iters[hca::WHICH_VEGF];
+  out->vegf_rel_residual = st.rel[hca::WHICH_VEGF];
+  out->vessel_births = st.vessel_births;
+  out->vessel_deaths = st.vessel_deaths;
   out->not_converged = st.not_converged;
   out->committed = st.committed;
   out->kills = st.kills;

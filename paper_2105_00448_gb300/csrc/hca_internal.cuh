@@ -27,6 +27,11 @@ constexpr int VEC = 4;          // sites per thread access
 constexpr int CHUNK_ROWS = 32;  // rows per reduction chunk
 constexpr int NDOT = 3;         // inner products carried per pass
 constexpr int MAX_DRUGS = 3;
+// linear fields solved besides oxygen: the drugs in slots 0..2 and the VEGF
+// field (Eq. vac_v, A = 0) in slot 3, solved as operator `which` = 1 + slot
+constexpr int MAX_FIELDS = 4;
+constexpr int VEGF_SLOT = 3;
+constexpr int WHICH_VEGF = 1 + VEGF_SLOT;
 constexpr int SUPER_CHUNKS = 64;  // chunks per second-level reduction group
 
 // ---------------------------------------------------------------- params --
@@ -49,19 +54,28 @@ struct RepDesc {
   double c_o2;            // D_K / dx^2
   double phi_K, K1, K0, r_K;
   // drugs (Eq. chemo), implicit Euler
-  double c_drug[MAX_DRUGS];   // D_G / dx^2
-  double base_drug[MAX_DRUGS];// 1/dt + psi_G
+  double c_drug[MAX_FIELDS];   // D_G / dx^2 (slot 3: D_V / dx^2)
+  double base_drug[MAX_FIELDS];// mass term + psi_G (slot 3: + psi_V)
   double inv_dt;
   // time discretisation per operator (0 oxygen, 1 + d drug d): the reaction
   // carries the mass term (o2_mass; inside base_drug), the right-hand side is
   // b = bx x0 - (bax ? A x0 : 0) + source, with the oxygen source doubled and
   // the drug source taken at both ends of the sub-step when bax (Crank-Nicolson)
   double o2_mass;
-  double bx[1 + MAX_DRUGS];
-  int bax[1 + MAX_DRUGS];
-  int nsub[1 + MAX_DRUGS];   // sub-steps per CA step
-  double kappa[MAX_DRUGS];
-  double uptake[MAX_DRUGS];
+  double bx[1 + MAX_FIELDS];
+  int bax[1 + MAX_FIELDS];
+  int nsub[1 + MAX_FIELDS];   // sub-steps per CA step
+  double kappa[MAX_FIELDS];   // slot 3: 0 (no vessel exchange)
+  double uptake[MAX_FIELDS];  // slot 3: 0
+  double a_vegf;              // VEGF release per unit Vc at cell sites
+  // plasma pharmacokinetics per drug: 0 exponential, 1 Michaelis-Menten,
+  // 2 three compartments (unit-bolus response sum_i pk_coef e^{pk_lam t})
+  int pk_model[MAX_DRUGS];
+  double mm_vmax, mm_km;
+  double pk_lam[MAX_DRUGS][3], pk_coef[MAX_DRUGS][3];
+  // vascular automaton
+  int vessel_interval;        // steps between updates, 0 = off
+  double V_low, V_high, p_death, beta_birth, V_sprout;
   double dose_peak[MAX_DRUGS];
   double plasma_decay[MAX_DRUGS];
   double dose_interval_min;  // minutes between boluses
@@ -94,12 +108,13 @@ struct RepSolve {
 struct DevStats {
   long long committed, kills, divisions, blocked;
   long long counts[6];
-  int iters[1 + MAX_DRUGS];
-  int sweeps[1 + MAX_DRUGS];
+  int iters[1 + MAX_FIELDS];
+  int sweeps[1 + MAX_FIELDS];
   int not_converged;
-  double rel[1 + MAX_DRUGS];
+  double rel[1 + MAX_FIELDS];
   int nonfinite;
   int pad;
+  long long vessel_births, vessel_deaths;
 };
 
 // Shared state for the last-block finalisation of a pass.
@@ -186,7 +201,7 @@ __host__ __device__ __forceinline__ float site_uniform(unsigned long long seed, 
   return (float)(o.w[0] >> 8) * 5.9604644775390625e-08f;
 }
 
-enum Purpose : uint32_t { PURPOSE_VESSEL = 0, PURPOSE_CANCER = 1, PURPOSE_PHI = 2, PURPOSE_KILL = 3 };
+enum Purpose : uint32_t { PURPOSE_VESSEL = 0, PURPOSE_CANCER = 1, PURPOSE_PHI = 2, PURPOSE_KILL = 3, PURPOSE_VASCULAR = 4 };
 
 // ------------------------------------------------------ row iteration ---
 // Geometry of one row (y, z) of replicate rd.
@@ -269,8 +284,9 @@ struct Ctx {
   uint8_t* state;
   void* K;       // oxygen
   void* K_lo;    // FP32 scheme: low-order words of the solved fields
-  void* G[MAX_DRUGS];
-  void* G_lo[MAX_DRUGS];
+  void* G[MAX_FIELDS];      // drugs, then the VEGF field in slot 3
+  void* G_lo[MAX_FIELDS];
+  unsigned long long* vsum;  // vascular automaton: [rep][2] fixed-point sums
   void* dx;      // FP32 scheme: correction of the inner solve
   void* aux;     // scratch field (previous iterate of the initial oxygen fixed point)
   int sub;          // sub-step of the current solve within the CA step (plasma times)
@@ -502,14 +518,61 @@ __device__ __forceinline__ double plasma_level(double t, double peak, double dec
 
 // Plasma level seen by a drug sub-step: G_{d,0} at its end (t_k), plus at its
 // start (t_{k-1}) under Crank-Nicolson; t_k = (step + (sub + 1) / m) dt.
+// Principal branch of Lambert W for x = e^L > 0, given L: Newton on
+// f(w) = w + ln w - L (w > 0), from w = L - ln L (L > 1) or w = e^L.  Written
+// from the definition w e^w = x; a fixed number of steps (quadratic
+// convergence) keeps the result independent of data-dependent stopping.
+__device__ __forceinline__ double lambert_w_exp(double L) {
+  double w = L > 1.0 ? L - log(L) : exp(L);
+  for (int i = 0; i < 8; ++i) {
+    const double f = w + log(w) - L;
+    w = fmax(w - f * w / (w + 1.0), 0.5 * w);
+  }
+  return w;
+}
+
+// Michaelis-Menten plasma level a time s after the level G_s:
+// G = k_m W((G_s / k_m) exp((G_s - v_max s) / k_m)).
+__device__ __forceinline__ double mm_decay(double G_s, double s, double vmax, double km) {
+  if (G_s <= 0.0) return 0.0;
+  return km * lambert_w_exp(log(G_s / km) + (G_s - vmax * s) / km);
+}
+
+// Plasma level of drug dg at time t under its model (doses of dose_peak at
+// 0, I dt, 2 I dt, ...).
+__device__ __forceinline__ double plasma_at(const RepDesc& rd, int dg, double t) {
+  const double peak = rd.dose_peak[dg], I = rd.dose_interval_min;
+  if (rd.pk_model[dg] == 1) {
+    if (t < 0.0) return 0.0;
+    double G = 0.0, t_prev = 0.0;
+    for (long long n = 0; (double)n * I <= t; ++n) {
+      const double tn = (double)n * I;
+      G = n > 0 ? mm_decay(G, tn - t_prev, rd.mm_vmax, rd.mm_km) + peak : peak;
+      t_prev = tn;
+      if (I <= 0.0) break;
+    }
+    return mm_decay(G, t - t_prev, rd.mm_vmax, rd.mm_km);
+  }
+  if (rd.pk_model[dg] == 2) {
+    if (t < 0.0) return 0.0;
+    double total = 0.0;
+    for (long long n = 0; (double)n * I <= t; ++n) {
+      const double s = t - (double)n * I;
+      for (int i = 0; i < 3; ++i) total += peak * rd.pk_coef[dg][i] * exp(rd.pk_lam[dg][i] * s);
+      if (I <= 0.0) break;
+    }
+    return total;
+  }
+  return plasma_level(t, peak, rd.plasma_decay[dg], I);
+}
+
 __device__ __forceinline__ double substep_plasma(const RepDesc& rd, int which, long long step, int sub) {
+  if (which == WHICH_VEGF) return 0.0;
   const int dg = which - 1;
   const double m = (double)rd.nsub[which];
   const double t_new = ((double)step + (double)(sub + 1) / m) * rd.dt;
-  double g = plasma_level(t_new, rd.dose_peak[dg], rd.plasma_decay[dg], rd.dose_interval_min);
-  if (rd.bax[which])
-    g += plasma_level(((double)step + (double)sub / m) * rd.dt, rd.dose_peak[dg], rd.plasma_decay[dg],
-                      rd.dose_interval_min);
+  double g = plasma_at(rd, dg, t_new);
+  if (rd.bax[which]) g += plasma_at(rd, dg, ((double)step + (double)sub / m) * rd.dt);
   return g;
 }
 

@@ -110,6 +110,10 @@ __global__ void __launch_bounds__(512) k_setup(Ctx c, int which, CondArg cnd) {
         const uchar4 st = ld_state4(c.state + e);
         V4<T> PF = zero4<T>();
         if (KIND == 1) PF = ld4(perf + e);
+        // the VEGF field's source is the cells' release a_V Vc (doubled under Crank-Nicolson)
+        const bool vegf = KIND == 1 && which == WHICH_VEGF;
+        const V4<T> VC = vegf ? ld4((const T*)c.Vc + e) : zero4<T>();
+        const T av = (T)(bax ? 2.0 * rd.a_vegf : rd.a_vegf);
         const V4<T> LG = (KIND == 0 && c.lag) ? ld4((const T*)c.lag + e) : X;
         V4<T> D, Z, B, RR = zero4<T>();
         T g_rho = 0, g_rr = 0, g_bb = 0;
@@ -121,6 +125,7 @@ __global__ void __launch_bounds__(512) k_setup(Ctx c, int which, CondArg cnd) {
           if (xk < rd.nx) {
             dk = diag_site<T, KIND>(rd, which, neighbour_count(rd, geo, xk), s, LG.a[k], PF.a[k]);
             if (KIND == 0) bk = (is_vessel(s) ? bvessel : T(0)) + (o2t ? X.a[k] * bx : T(0));
+            else if (vegf) bk = X.a[k] * bx + (is_consumer(s) ? av * VC.a[k] : T(0));
             else bk = X.a[k] * bx + (is_vessel(s) ? (T)rd.kappa[which - 1] * PF.a[k] * G0 : T(0));
             const T ax = dk * X.a[k] - cpl * nb_sum(X, k, left, right, ym, yp, zm, zp);
             if (bax) bk -= ax;   // Crank-Nicolson: b = (4/h) x0 - A x0 + f^{k-1} + f^k
@@ -634,6 +639,9 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
             const uchar4 st = ld_state4(c.state + e);
             V4<float> PF = zero4<float>();
             if (KIND == 1) PF = ld4(perf + e);
+            const bool vegf = KIND == 1 && which == WHICH_VEGF;
+            const V4<float> VC = vegf ? ld4((const float*)c.Vc + e) : zero4<float>();
+            const float av = (float)(bax ? 2.0 * rd.a_vegf : rd.a_vegf);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
               const int xk = 4 * g + k;
@@ -653,7 +661,8 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
                   SRC.a[k] = is_vessel(s) ? bvessel : 0.f;
                   B.a[k] = SRC.a[k] + (o2t ? (float)(xk64 * bx) : 0.f);
                 } else {
-                  SRC.a[k] = is_vessel(s) ? (float)rd.kappa[which - 1] * PF.a[k] * G0 : 0.f;
+                  if (vegf) SRC.a[k] = is_consumer(s) ? av * VC.a[k] : 0.f;
+                  else SRC.a[k] = is_vessel(s) ? (float)rd.kappa[which - 1] * PF.a[k] * G0 : 0.f;
                   B.a[k] = (float)(xk64 * bx) + SRC.a[k];
                 }
               }

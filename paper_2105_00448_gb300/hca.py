@@ -45,6 +45,7 @@ FIELD_PHI = 1 << 4
 FIELD_P53 = 1 << 5
 FIELD_VEGFC = 1 << 6
 FIELD_PERF = 1 << 7
+FIELD_VEGF = 1 << 8
 FIELD_DRUG = (FIELD_DRUG0, FIELD_DRUG1, FIELD_DRUG2)
 
 STAGE_O2 = 1 << 0
@@ -82,6 +83,12 @@ class hca_config(ctypes.Structure):
         ("threads_per_block", ctypes.c_int32), ("o2_nonlinear", ctypes.c_int32),
         ("drug_scheme", ctypes.c_int32), ("drug_substeps", ctypes.c_int32),
         ("o2_scheme", ctypes.c_int32), ("o2_substeps", ctypes.c_int32), ("ca_mode", ctypes.c_int32),
+        ("vegf", ctypes.c_int32), ("vessel_interval", ctypes.c_int32), ("pk_model", _i3), ("pad3", ctypes.c_int32),
+        ("D_V", ctypes.c_double), ("psi_V", ctypes.c_double), ("a_V", ctypes.c_double),
+        ("V_low", ctypes.c_double), ("V_high", ctypes.c_double),
+        ("p_death", ctypes.c_double), ("beta_birth", ctypes.c_double), ("V_sprout", ctypes.c_double),
+        ("mm_vmax", ctypes.c_double), ("mm_km", ctypes.c_double), ("epi_w", _d3),
+        ("epi_q2", ctypes.c_double), ("epi_q3", ctypes.c_double), ("epi_cl2", ctypes.c_double),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -104,6 +111,9 @@ class hca_stats(ctypes.Structure):
         ("pad1", ctypes.c_int32),
         ("ws_r0_prev", ctypes.c_double),
         ("ws_r0_learned", ctypes.c_double),
+        ("vegf_iterations", ctypes.c_int32), ("pad2", ctypes.c_int32),
+        ("vegf_rel_residual", ctypes.c_double),
+        ("vessel_births", ctypes.c_int64), ("vessel_deaths", ctypes.c_int64),
     ]
 
     def as_dict(self) -> Dict:
@@ -226,7 +236,7 @@ def _check(rc: int, what: str):
 
 
 # ------------------------------------------------------------ config ---
-_ARRAY3 = {"D_G", "psi_G", "kappa_G", "uptake_G", "dose_peak", "plasma_decay", "kill_b"}
+_ARRAY3 = {"D_G", "psi_G", "kappa_G", "uptake_G", "dose_peak", "plasma_decay", "kill_b", "pk_model", "epi_w"}
 
 
 def make_config(nx: int, ny: int, nz: int, precision="f64", stream=None, **params) -> hca_config:

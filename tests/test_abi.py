@@ -68,3 +68,21 @@ def test_make_config_overrides(lib):
     assert list(cfg.kill_b) == [2, 3, 1] and cfg.dt == 30.0
     with pytest.raises(KeyError):
         hca.make_config(5, 5, 5, no_such_field=1)
+
+
+def test_library_defaults_equal_oracle_defaults(lib):
+    """Every parameter the library and the oracle share has the same default
+    (the GPU tests rely on this when they pass only overrides to both)."""
+    from oracle import params as Pm
+
+    cfg = hca.hca_config()
+    assert lib.hca_config_default(ctypes.byref(cfg), 8, 9, 10) == 0
+    ref = Pm.Config(8, 9, 10)
+    skip = {"nx", "ny", "nz", "precision", "seed", "dose_peak"}
+    shared = [f for f, _ in hca.hca_config._fields_ if f in Pm.Config.__dataclass_fields__ and f not in skip]
+    assert len(shared) >= 40
+    for f in shared:
+        got, want = getattr(cfg, f), getattr(ref, f)
+        got = list(got) if hasattr(got, "__len__") else got
+        want = list(want) if isinstance(want, tuple) else want
+        assert got == pytest.approx(want, rel=1e-15), f
