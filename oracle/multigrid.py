@@ -9,12 +9,14 @@ Operator on every level: (A u)_i = c_l S_l(u)_i + a_l,i u_i, with S_l the
 Neumann neighbour-difference sum of laplacian_sum on the level's lattice,
 diagonal d_l = c_l n_l + a_l (n_l = number of in-box face neighbours).
 
-Hierarchy: level l+1 halves every extent (ceil(n/2)); site I of level l+1
-owns the children 2I + {0,1}^3 that exist on level l.  Coefficients:
-c_{l+1} = 2 c_l (the Laplacian rediscretised at twice the spacing and scaled
-by the 8 times larger volume) and a_{l+1,I} = sum of the children's a_l
+Hierarchy: level l+1 halves every extent (ceil(n/2); an extent of 1 stays
+1); site I of level l+1 owns the children 2I + {0,1}^3 that exist on level
+l.  Coefficients: c_{l+1} = c_l 2^k / 4, k the number of extents of level l
+above 1 (the Laplacian rediscretised at twice the spacing in those k
+directions and scaled by the 2^k times larger volume: 2 c_l on a 3-D
+lattice, c_l on a flat one), and a_{l+1,I} = sum of the children's a_l
 (Galerkin for the reaction).  Coarsening stops at the first level with at
-most MIN_SITES sites or with an extent of 1.
+most MIN_SITES sites or with every extent 1.
 Transfers: restriction R = sum over children; prolongation P = R^T (copy to
 children).  Smoother: weighted Jacobi, weight OMEGA.
 
@@ -74,9 +76,10 @@ class Level:
 def hierarchy(c, a):
     """Levels of the operator c S + diag(a) on a's lattice."""
     levels = [Level(c, a)]
-    while levels[-1].a.size > MIN_SITES and min(levels[-1].a.shape) > 1:
+    while levels[-1].a.size > MIN_SITES and max(levels[-1].a.shape) > 1:
         lv = levels[-1]
-        levels.append(Level(2.0 * lv.c, restrict(lv.a)))
+        k = sum(1 for n in lv.a.shape if n > 1)
+        levels.append(Level(lv.c * 2.0 ** k / 4.0, restrict(lv.a)))
     return levels
 
 

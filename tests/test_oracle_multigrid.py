@@ -102,3 +102,39 @@ def test_mg_pcg_needs_far_fewer_iterations_than_jacobi(rng):
     assert i_mg.converged and i_j.converged
     assert i_mg.iterations * 5 < i_j.iterations
     assert np.max(np.abs(x_mg - x_j)) <= 1e-6 * np.max(np.abs(x_j))
+
+
+@pytest.mark.parametrize("shape,children", [((16, 16, 16), 8), ((1, 32, 48), 4), ((1, 1, 600), 2)])
+def test_coarse_coupling_is_consistent_rediscretisation(shape, children):
+    """On a quadratic field u = sum over the lattice's extended directions of
+    x^2 (cell centres), the coarse operator applied to u sampled at the
+    aggregates' centres equals the number of children times the fine
+    operator's value at interior sites (the sum restriction convention):
+    the coarse Laplacian is the rediscretised one, whatever the number of
+    coarsened directions."""
+    c = 3.0
+    levels = MG.hierarchy(c, np.zeros(shape))
+    assert len(levels) >= 2
+    f, cs = levels[0], levels[1]
+    def quad(shp, spacing, offset):
+        grids = np.meshgrid(*[spacing * np.arange(n) + offset for n in shp], indexing="ij")
+        return sum(g ** 2 for g, n in zip(grids, shp) if n > 1)
+    u = quad(shape, 1.0, 0.0)
+    U = quad(cs.a.shape, 2.0, 0.5)                 # aggregate centres in fine cell units
+    fine = f.apply(u)[tuple(slice(1, -1) if n > 2 else slice(None) for n in shape)]
+    coarse = cs.apply(U)[tuple(slice(1, -1) if n > 2 else slice(None) for n in cs.a.shape)]
+    assert np.allclose(fine, fine.flat[0]) and np.allclose(coarse, coarse.flat[0])
+    assert np.isclose(coarse.flat[0], children * fine.flat[0])
+
+
+def test_flat_lattice_mg_pcg(rng):
+    """A 2-D lattice coarsens in-plane; MG-PCG stays far ahead of Jacobi."""
+    shape = (1, 64, 96)
+    c, a, b = _drug_like(shape, rng)
+    assert len(MG.hierarchy(c, a)) >= 3
+    x_mg, i_mg = MG.mg_pcg(c, a, b, np.zeros(shape), 1e-8, 2000)
+    d = S.jacobi_diagonal(shape, c, a)
+    x_j, i_j = PCG.pcg(lambda u: c * S.laplacian_sum(u) + a * u, b, np.zeros(shape), d, 1e-8, 5000)
+    assert i_mg.converged and i_j.converged
+    assert i_mg.iterations * 4 < i_j.iterations
+    assert np.max(np.abs(x_mg - x_j)) <= 1e-6 * np.max(np.abs(x_j))
