@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(512) k_ca_compact(Ctx c) {
   const int2 ch = c.chunks[blockIdx.x];
   const int rep = ch.x;
   const RepDesc& rd = c.reps[rep];
-  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
   const long long base0 = rd.off + (long long)ch.y * rd.nxp;
   const int ngroups = nrows * rd.gpr;
   const int lane = threadIdx.x & 31;
@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(512) k_vessel_sums(Ctx c) {
   if (!vessel_step(c, rd)) return;
   if (threadIdx.x < 2) s_sum[threadIdx.x] = 0ull;
   __syncthreads();
-  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
   const long long base0 = rd.off + (long long)ch.y * rd.nxp;
   const T* V = (const T*)c.G[VEGF_SLOT];
   unsigned long long a1 = 0ull, a2 = 0ull;
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(512) k_vessel_update(Ctx c) {
   if (!vessel_step(c, rd)) return;
   if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0u;
   __syncthreads();
-  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
   const long long base0 = rd.off + (long long)ch.y * rd.nxp;
   const T* V = (const T*)c.G[VEGF_SLOT];
   const double S1 = (double)c.vsum[2 * rep], S2 = (double)c.vsum[2 * rep + 1];

@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(512) k_init(Ctx c, const float* __restrict__ p
   HCA_COUNT_KERNEL(c);
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
-  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
   const long long base0 = rd.off + (long long)ch.y * rd.nxp;
   const int ngroups = nrows * rd.gpr;
   for (int gi = threadIdx.x; gi < ngroups; gi += blockDim.x) {
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(512) k_ode(Ctx c) {
   __shared__ long long s_site[kMaxWarps][128];
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
-  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
   const long long base0 = rd.off + (long long)ch.y * rd.nxp;
   const int ngroups = nrows * rd.gpr;
   const T dt = (T)rd.dt, Tc = (T)rd.T_cycle, Kphi = (T)rd.K_phi;
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(512) k_histogram(Ctx c) {
   __syncthreads();
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
-  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
   const long long base0 = rd.off + (long long)ch.y * rd.nxp;
   unsigned int loc[6] = {0, 0, 0, 0, 0, 0};
   for (int i = threadIdx.x; i < nrows * rd.nx; i += blockDim.x) {

@@ -1013,11 +1013,22 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     off += ((long long)r.nxp * r.ny * r.nz + kFieldAlign - 1) / kFieldAlign * kFieldAlign;
     const int rows = r.ny * r.nz;
     r.chunk_begin = chunk0;
-    r.n_chunks = (rows + hca::CHUNK_ROWS - 1) / hca::CHUNK_ROWS;
+    // rows per chunk: CHUNK_ROWS, halved while the lattice would give fewer
+    // than 1024 chunks and a chunk keeps at least one row per warp of an
+    // 8-warp block (lattices with few rows, e.g. flat ones, get more blocks);
+    // it depends on the lattice's shape only, so results do not depend on the
+    // launch configuration or on the other replicates of a batch
+    {
+      const int min_rows = std::min(hca::CHUNK_ROWS, 8 * (32 / r.lpr));
+      int cr = hca::CHUNK_ROWS;
+      while (cr > min_rows && rows / cr < 1024) cr >>= 1;
+      r.chunk_rows = cr;
+    }
+    r.n_chunks = (rows + r.chunk_rows - 1) / r.chunk_rows;
     r.super_begin = super0;
     r.n_supers = (r.n_chunks + hca::SUPER_CHUNKS - 1) / hca::SUPER_CHUNKS;
     super0 += r.n_supers;
-    for (int k = 0; k < r.n_chunks; ++k) h->chunks_h.push_back(make_int2(i, k * hca::CHUNK_ROWS));
+    for (int k = 0; k < r.n_chunks; ++k) h->chunks_h.push_back(make_int2(i, k * r.chunk_rows));
     chunk0 += r.n_chunks;
     for (int col = 0; col < 27; ++col) {
       const int cap = colour_count(r.nx, col % 3) * colour_count(r.ny, (col / 3) % 3) * colour_count(r.nz, col / 9);
@@ -1102,7 +1113,13 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
         long long nn = (long long)nx * ny * nz;
         int nl = 1;
         start[i + 1] = start[i] + nn;   // level 0 (the lattices)
-        while (nn > hca::MG_MIN_SITES && std::min(nx, std::min(ny, nz)) > 1 && nl < hca::MG_MAXLEV) {
+        double cs = 1.0;
+        // coarsen while the level is large and some extent exceeds 1; the
+        // coupling grows by 2^k / 4 for the k extents above 1 (2 on a 3-D
+        // lattice, 1 on a flat one)
+        while (nn > hca::MG_MIN_SITES && std::max(nx, std::max(ny, nz)) > 1 && nl < hca::MG_MAXLEV) {
+          const int k = (nx > 1) + (ny > 1) + (nz > 1);
+          cs *= std::ldexp(1.0, k - 2);
           nx = (nx + 1) / 2;
           ny = (ny + 1) / 2;
           nz = (nz + 1) / 2;
@@ -1112,7 +1129,7 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
           L.ny = ny;
           L.nz = nz;
           L.n = nn;
-          L.cscale = std::ldexp(1.0, nl);
+          L.cscale = cs;
           nl += 1;
         }
         int small = nl - 1;

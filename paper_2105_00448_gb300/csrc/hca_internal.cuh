@@ -43,6 +43,7 @@ struct RepDesc {
   int lpr;                // lanes per row (power of two, <= 32)
   int chunk_begin;        // first chunk of this replicate in the chunk table
   int n_chunks;
+  int chunk_rows;         // rows per chunk (a power of two <= CHUNK_ROWS, from the lattice's shape)
   int super_begin;        // first group of SUPER_CHUNKS chunks of this replicate
   int n_supers;
   unsigned long long seed;
@@ -434,7 +435,7 @@ __device__ __forceinline__ void warp_epilogue(const Ctx& c, int ndot, int chunk,
   __threadfence();
   const int2 ch = c.chunks[chunk];
   const RepDesc& rd = c.reps[ch.x];
-  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
   for (int k = 0; k < ndot; ++k) {
     double v = lane < nrows ? __ldcg(&c.rowp[((long long)chunk * CHUNK_ROWS + lane) * NDOT + k]) : 0.0;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULLM, v, o);

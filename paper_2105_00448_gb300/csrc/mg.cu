@@ -534,7 +534,7 @@ __global__ void __maxnreg__(96) k_mg_post0(Ctx c, int which, const T* __restrict
   HCA_COUNT_KERNEL(c);
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
-  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
   const T* __restrict__ rr = (const T*)c.r;
   const T* __restrict__ dd = (const T*)c.d;
   const T* __restrict__ ww = (const T*)c.mg_w;
@@ -549,7 +549,7 @@ __global__ void __maxnreg__(96) k_mg_post0(Ctx c, int which, const T* __restrict
     ny1 = L1.ny;
   }
   const RowIter it = row_iter(rd);
-  for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
+  for (int rbase = it.warp * it.rpw; rbase < rd.chunk_rows; rbase += it.nw * it.rpw) {
     const int rl = rbase + it.sub;
     const bool row_ok = rl < nrows;
     const int j = ch.y + (row_ok ? rl : 0);

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(512) k_setup(Ctx c, int which, CondArg cnd) {
   __shared__ double s_G0;
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
-  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
   const T* __restrict__ x = KIND == 0 ? (const T*)c.K : (const T*)c.G[which - 1];
   const T* __restrict__ perf = (const T*)c.perf;
   T* __restrict__ dd = (T*)c.d;
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(512) k_setup(Ctx c, int which, CondArg cnd) {
   const bool o2t = KIND == 0 && rd.bx[0] != 0.0;   // time-dependent oxygen: b depends on x0
   const T bvessel = (T)(bax ? 2.0 * rd.r_K * rd.K0 : rd.r_K * rd.K0);
   const RowIter it = row_iter(rd);
-  for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
+  for (int rbase = it.warp * it.rpw; rbase < rd.chunk_rows; rbase += it.nw * it.rpw) {
     const int rl = rbase + it.sub;
     const bool row_ok = rl < nrows;
     const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
@@ -199,7 +199,7 @@ __global__ void __maxnreg__(REGS) k_pass_a(Ctx c, int which) {
   const RepDesc& rd = c.reps[ch.x];
   const RepSolve sv = c.solve[ch.x];
   if (sv.active) {
-    const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+    const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
     const int gpr = rd.gpr;
     const int par = c.sync->parity;
     const T* __restrict__ pp = (const T*)(par ? c.p_alt : c.p);
@@ -213,7 +213,7 @@ __global__ void __maxnreg__(REGS) k_pass_a(Ctx c, int which) {
     const T zs = (sv.iters == 0 && !c.mg) ? (T)sv.scale : T(1);
     const T cpl = (T)op_coupling(rd, which);
     const RowIter it = row_iter(rd);
-    for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
+    for (int rbase = it.warp * it.rpw; rbase < rd.chunk_rows; rbase += it.nw * it.rpw) {
       const int rl = rbase + it.sub;
       const bool row_ok = rl < nrows;
       const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
@@ -295,7 +295,7 @@ __global__ void __maxnreg__(REGS) k_pass_b(Ctx c, int which, void* xfield, CondA
   const RepDesc& rd = c.reps[ch.x];
   const RepSolve sv = c.solve[ch.x];
   if (sv.active) {
-    const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+    const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
     const int gpr = rd.gpr, nx = rd.nx;
     // Jacobi form: z = r / d is carried; V-cycle form: r itself (already scaled)
     const bool mg = c.mg != 0;
@@ -307,7 +307,7 @@ __global__ void __maxnreg__(REGS) k_pass_b(Ctx c, int which, void* xfield, CondA
     const T zs = (sv.iters == 0 && !mg) ? (T)sv.scale : T(1);
     const T cpl = (T)op_coupling(rd, which);
     const RowIter it = row_iter(rd);
-    for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
+    for (int rbase = it.warp * it.rpw; rbase < rd.chunk_rows; rbase += it.nw * it.rpw) {
       const int rl = rbase + it.sub;
       const bool row_ok = rl < nrows;
       const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
@@ -403,14 +403,14 @@ __global__ void __launch_bounds__(512) k_true_residual(Ctx c, int which, void* x
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
   const RepSolve sv = c.solve[ch.x];
-  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
   T* __restrict__ xx = (T*)xfield;
   const T* __restrict__ dd = (const T*)c.d;
   const T* __restrict__ bb = (const T*)c.b;
   const T cpl = (T)op_coupling(rd, which);
   const T bvessel = (T)(rd.r_K * rd.K0);
   const RowIter it = row_iter(rd);
-  for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
+  for (int rbase = it.warp * it.rpw; rbase < rd.chunk_rows; rbase += it.nw * it.rpw) {
     const int rl = rbase + it.sub;
     const bool row_ok = rl < nrows;
     const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
@@ -476,7 +476,7 @@ __global__ void k_zero_if_b_zero(Ctx c, void* xfield) {
   const int2 ch = c.chunks[blockIdx.x];
   if (!c.solve[ch.x].zero_b) return;
   const RepDesc& rd = c.reps[ch.x];
-  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
   T* xx = (T*)xfield;
   const long long base = rd.off + (long long)ch.y * rd.nxp;
   const long long n = (long long)nrows * rd.nxp;
@@ -493,12 +493,12 @@ __global__ void __launch_bounds__(512) k_apply(Ctx c, int which, int rep, const 
   const int2 ch = c.chunks[blockIdx.x];
   if (ch.x != rep) return;
   const RepDesc& rd = c.reps[ch.x];
-  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
   const T* __restrict__ K = (const T*)c.K;
   const T* __restrict__ perf = (const T*)c.perf;
   const T cpl = (T)op_coupling(rd, which);
   const RowIter it = row_iter(rd);
-  for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
+  for (int rbase = it.warp * it.rpw; rbase < rd.chunk_rows; rbase += it.nw * it.rpw) {
     const int rl = rbase + it.sub;
     const bool row_ok = rl < nrows;
     const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
@@ -541,9 +541,9 @@ __global__ void __launch_bounds__(512) k_diff_norms(Ctx c, const T* __restrict__
   HCA_COUNT_KERNEL(c);
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
-  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
   const RowIter it = row_iter(rd);
-  for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
+  for (int rbase = it.warp * it.rpw; rbase < rd.chunk_rows; rbase += it.nw * it.rpw) {
     const int rl = rbase + it.sub;
     const bool row_ok = rl < nrows;
     const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
@@ -599,7 +599,7 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
     __syncthreads();
   }
   if (live) {
-    const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+    const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
     float* __restrict__ dd = (float*)c.d;
     float* __restrict__ aa = (float*)c.reac;
     float* __restrict__ zz = (float*)c.z;
@@ -614,7 +614,7 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
     const float bvessel = (float)(bax ? 2.0 * rd.r_K * rd.K0 : rd.r_K * rd.K0);
     const RowIter it = row_iter(rd);
     const float cpl32 = (float)cpl;
-    for (int rbase = it.warp * it.rpw; rbase < CHUNK_ROWS; rbase += it.nw * it.rpw) {
+    for (int rbase = it.warp * it.rpw; rbase < rd.chunk_rows; rbase += it.nw * it.rpw) {
       const int rl = rbase + it.sub;
       const bool row_ok = rl < nrows;
       const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
@@ -844,7 +844,7 @@ __global__ void __launch_bounds__(512) k_dc_update(Ctx c, float* __restrict__ x_
   const RepSolve sv = c.solve[ch.x];
   if (!sv.dc_apply && !sv.zero_b) return;
   const RepDesc& rd = c.reps[ch.x];
-  const int nrows = min(CHUNK_ROWS, rd.ny * rd.nz - ch.y);
+  const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
   const long long base0 = rd.off + (long long)ch.y * rd.nxp;
   const int ngroups = nrows * rd.gpr;
   const float* __restrict__ dxv = (const float*)c.dx;

@@ -25,8 +25,9 @@ from paper_2105_00448_gb300 import hca
 pytestmark = pytest.mark.gpu
 
 # (nz, ny, nx): one level (<= 512 sites), two and three levels with the
-# coarse part in the single-block kernel, four levels with a grid-kernel level
-SHAPES = [(5, 7, 13), (16, 16, 16), (32, 32, 32), (24, 40, 56)]
+# coarse part in the single-block kernel, four levels with a grid-kernel level,
+# a flat lattice (in-plane coarsening) and one that becomes flat after a level
+SHAPES = [(5, 7, 13), (16, 16, 16), (32, 32, 32), (24, 40, 56), (1, 48, 70), (2, 40, 60)]
 
 
 def _operator(which, st, K, perf, cfg):
@@ -180,8 +181,8 @@ def test_mg_edge_cases():
     sim.stage(hca.STAGE_O2)
     assert np.all(sim.field(hca.FIELD_O2) == 0.0)
     sim.close()
-    # a flat lattice (extent 1): no coarsening, the lattice is the coarsest level
-    sim, cfg, _ = make_pair((1, 40, 40), "f64", seed=1, n_drugs=0, rtol_o2=1e-10, preconditioner=hca.HCA_PC_MG)
+    # a lattice of at most 512 sites is its own coarsest level
+    sim, cfg, _ = make_pair((1, 20, 25), "f64", seed=1, n_drugs=0, rtol_o2=1e-10, preconditioner=hca.HCA_PC_MG)
     sim.step(1)
     assert sim.stats()["o2_rel_residual"] <= 2e-10
     sim.close()
