@@ -630,17 +630,30 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
         const V4<float> yph = ld4_if(x_hi + e + geo.sy, gok && geo.yp), ypl = ld4_if(x_lo + e + geo.sy, gok && geo.yp);
         const V4<float> zmh = ld4_if(x_hi + e - geo.sz, gok && geo.zm), zml = ld4_if(x_lo + e - geo.sz, gok && geo.zm);
         const V4<float> zph = ld4_if(x_hi + e + geo.sz, gok && geo.zp), zpl = ld4_if(x_lo + e + geo.sz, gok && geo.zp);
+        // every other load of the group is issued here too, before any value
+        // is used, so a group costs one memory round trip: the site after the
+        // group (the segment's last lane), and d, a, b (later sweeps) or the
+        // state, perfusion and Vc (the first sweep)
+        const bool last_lane = it.sl == it.lpr - 1 && gok && g + 1 < rd.gpr;
+        const float rnh = last_lane ? x_hi[e + 4] : 0.f, rnl = last_lane ? x_lo[e + 4] : 0.f;
+        const bool vegf = KIND == 1 && which == WHICH_VEGF;
+        V4<float> D = zero4<float>(), B = zero4<float>(), AR = zero4<float>(), SRC = zero4<float>();
+        V4<float> PF = zero4<float>(), VC = zero4<float>();
+        uchar4 st = make_uchar4(0, 0, 0, 0);
+        if (gok && first) {
+          st = ld_state4(c.state + e);
+          if (KIND == 1) PF = ld4(perf + e);
+          if (vegf) VC = ld4((const float*)c.Vc + e);
+        } else if (gok) {
+          D = ld4(dd + e);
+          AR = ld4(aa + e);
+          B = ld4(bb + e);
+        }
         float lh, rh, ll, rlo;
-        x_neighbours(Xh, g, rd.gpr, it.sl, it.lpr, gok, carry_h, lh, rh, [&] { return x_hi[e + 4]; });
-        x_neighbours(Xl, g, rd.gpr, it.sl, it.lpr, gok, carry_l, ll, rlo, [&] { return x_lo[e + 4]; });
+        x_neighbours(Xh, g, rd.gpr, it.sl, it.lpr, gok, carry_h, lh, rh, [&] { return rnh; });
+        x_neighbours(Xl, g, rd.gpr, it.sl, it.lpr, gok, carry_l, ll, rlo, [&] { return rnl; });
         if (gok) {
-          V4<float> D, B, AR, SRC;
           if (first) {
-            const uchar4 st = ld_state4(c.state + e);
-            V4<float> PF = zero4<float>();
-            if (KIND == 1) PF = ld4(perf + e);
-            const bool vegf = KIND == 1 && which == WHICH_VEGF;
-            const V4<float> VC = vegf ? ld4((const float*)c.Vc + e) : zero4<float>();
             const float av = (float)(bax ? 2.0 * rd.a_vegf : rd.a_vegf);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -669,10 +682,6 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
             }
             st4(dd + e, D);
             st4(aa + e, AR);
-          } else {
-            D = ld4(dd + e);
-            AR = ld4(aa + e);
-            B = ld4(bb + e);
           }
           V4<float> Z, R32 = zero4<float>();
 #pragma unroll
