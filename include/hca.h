@@ -57,6 +57,7 @@ extern "C" {
 #define HCA_ERR_TIMEOUT (-6)       /* a bounded device wait gave up */
 #define HCA_ERR_UNIMPLEMENTED (-7)
 #define HCA_ERR_STATE (-8)         /* call not valid in the handle's current state */
+#define HCA_ERR_IO (-9)            /* a checkpoint file could not be opened, read or written */
 
 /* precision */
 #define HCA_FP64 0
@@ -383,6 +384,29 @@ int hca_get_profile(hca_handle* h, hca_profile* out);
  * result. */
 int hca_o2_residual_noalloc(const hca_config* cfg, const uint8_t* state, const double* K_prev,
                             const double* K, double* rel_out, void* stream);
+
+/* Checkpoint and resume (no counterpart in the paper, which restarts from
+ * patient data).  hca_save writes, to a new file at `path`, everything a
+ * later step reads: the configurations (stream pointers stored as NULL), the
+ * step counter, and per replicate the lattice states and the fields K, G_d,
+ * V (when vegf = 1), phi, P, Vc and perf in the handle's precision, with the
+ * low words of the FP32 defect-correction fields; it synchronises the
+ * handle's stream first.  hca_load creates a handle from such a file on
+ * `stream` (a cudaStream_t, NULL = default) without the initial oxygen
+ * solve; stepping it continues the saved run bit for bit.  A learned
+ * warm-start network is not part of the file (attach it again with
+ * hca_set_warm_start_net).  Format: the 8 bytes "HCACKPT1", int32 version
+ * (1), int32 sizeof(hca_config), int32 replicate count, int32 precision,
+ * int64 step, int32 picard_iterations, int32 0, the configs, the perfusion
+ * map of every replicate, then per replicate the states (nx*ny*nz bytes) and
+ * the fields K [K_lo], G_d [G_lo_d], V [V_lo], phi, P, Vc (nx*ny*nz elements
+ * each, site order x + nx*(y + ny*z); the low words only for HCA_FP32), all
+ * little-endian as in memory.
+ * Errors: HCA_ERR_ARG (null arguments, a file that is not a checkpoint of
+ * this ABI), HCA_ERR_IO (open, read or write failed), and those of
+ * hca_create_batch. */
+int hca_save(hca_handle* h, const char* path);
+int hca_load(const char* path, void* stream, hca_handle** out);
 
 void hca_destroy(hca_handle* h);
 const char* hca_status_string(int32_t status);

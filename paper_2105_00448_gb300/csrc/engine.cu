@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -962,7 +963,7 @@ int picard_oxygen_impl(hca_handle* h) {
 }
 
 int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const float* const* perf,
-                const float* const* p_vessel, int maps_on_device, hca_handle** out) {
+                const float* const* p_vessel, int maps_on_device, hca_handle** out, bool initial_o2 = true) {
   if (!out || n < 1 || !cfgs || !p_cell || !perf || !p_vessel) return HCA_ERR_ARG;
   *out = nullptr;
   for (int i = 0; i < n; ++i) {
@@ -1337,8 +1338,10 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
         if (rc) goto fail;
       }
     }
-    rc = picard_oxygen(h);
-    if (rc) goto fail;
+    if (initial_o2) {
+      rc = picard_oxygen(h);
+      if (rc) goto fail;
+    }
     rc = reset_step_stats(h);
     if (rc) goto fail;
   }
@@ -1370,6 +1373,49 @@ int copy_field(hca_handle* h, int rep, void* field, size_t es, void* host_or_dev
 }
 
 int check_rep(hca_handle* h, int rep) { return (h && rep >= 0 && rep < h->n_reps) ? HCA_OK : HCA_ERR_ARG; }
+
+// ---------------------------------------------------------- checkpoints --
+struct CkptHeader {
+  char magic[8];
+  int32_t version, config_size, n_reps, precision;
+  int64_t step;
+  int32_t picard_iterations, pad;
+};
+constexpr char kCkptMagic[8] = {'H', 'C', 'A', 'C', 'K', 'P', 'T', '1'};
+
+// The device fields of replicate `rep` in checkpoint order (null entries are
+// skipped consistently on save and load).
+std::vector<void*> ckpt_fields(hca_handle* h) {
+  Ctx& c = h->ctx;
+  std::vector<void*> f{c.K, c.K_lo};
+  for (int d = 0; d < h->n_drugs; ++d) {
+    f.push_back(c.G[d]);
+    f.push_back(c.G_lo[d]);
+  }
+  if (h->vegf) {
+    f.push_back(c.G[hca::VEGF_SLOT]);
+    f.push_back(c.G_lo[hca::VEGF_SLOT]);
+  }
+  f.push_back(c.phi);
+  f.push_back(c.P);
+  f.push_back(c.Vc);
+  return f;
+}
+
+// Copy the states of replicate rep between the device and a host buffer.
+int copy_states(hca_handle* h, int rep, uint8_t* host, bool to_host) {
+  const RepDesc& r = h->reps_h[rep];
+  const cudaError_t e =
+      to_host ? cudaMemcpy2DAsync(host, (size_t)r.nx, h->ctx.state + r.off, (size_t)r.nxp, (size_t)r.nx,
+                                  (size_t)r.ny * r.nz, cudaMemcpyDeviceToHost, h->ctx.stream)
+              : cudaMemcpy2DAsync(h->ctx.state + r.off, (size_t)r.nxp, host, (size_t)r.nx, (size_t)r.nx,
+                                  (size_t)r.ny * r.nz, cudaMemcpyHostToDevice, h->ctx.stream);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return HCA_ERR_CUDA;
+  }
+  return HCA_OK;
+}
 
 }  // namespace
 
@@ -1741,6 +1787,139 @@ int hca_get_profile(hca_handle* h, hca_profile* out) {
   return HCA_OK;
 }
 
+int hca_save(hca_handle* h, const char* path) {
+  if (!h || !path) return HCA_ERR_ARG;
+  HCA_TRY(cudaStreamSynchronize(h->ctx.stream));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return HCA_ERR_IO;
+  CkptHeader hd{};
+  std::memcpy(hd.magic, kCkptMagic, 8);
+  hd.version = 1;
+  hd.config_size = (int32_t)sizeof(hca_config);
+  hd.n_reps = h->n_reps;
+  hd.precision = h->fp64 ? HCA_FP64 : HCA_FP32;
+  hd.step = h->step;
+  hd.picard_iterations = h->picard_iterations;
+  bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1;
+  for (int i = 0; i < h->n_reps && ok; ++i) {
+    hca_config cf = h->cfgs[i];
+    cf.stream = nullptr;
+    ok = std::fwrite(&cf, sizeof(cf), 1, f) == 1;
+  }
+  const size_t es = elem_size(h);
+  int rc = HCA_OK;
+  // the perfusion maps of every replicate first (creation needs them), then
+  // per replicate the states and the fields
+  for (int i = 0; i < h->n_reps && ok && !rc; ++i) {
+    const RepDesc& r = h->reps_h[i];
+    const size_t n = (size_t)r.nx * r.ny * r.nz;
+    std::vector<char> buf(n * es);
+    rc = copy_field(h, i, h->ctx.perf, es, buf.data(), true, 0);
+    if (!rc && cudaStreamSynchronize(h->ctx.stream) != cudaSuccess) rc = HCA_ERR_CUDA;
+    if (!rc) ok = std::fwrite(buf.data(), es, n, f) == n;
+  }
+  for (int i = 0; i < h->n_reps && ok && !rc; ++i) {
+    const RepDesc& r = h->reps_h[i];
+    const size_t n = (size_t)r.nx * r.ny * r.nz;
+    std::vector<char> buf(n * es);
+    rc = copy_states(h, i, (uint8_t*)buf.data(), true);
+    if (!rc && cudaStreamSynchronize(h->ctx.stream) != cudaSuccess) rc = HCA_ERR_CUDA;
+    if (!rc) ok = std::fwrite(buf.data(), 1, n, f) == n;
+    for (void* fld : ckpt_fields(h)) {
+      if (!fld || rc || !ok) continue;
+      rc = copy_field(h, i, fld, es, buf.data(), true, 0);
+      if (!rc && cudaStreamSynchronize(h->ctx.stream) != cudaSuccess) rc = HCA_ERR_CUDA;
+      if (!rc) ok = std::fwrite(buf.data(), es, n, f) == n;
+    }
+  }
+  if (std::fclose(f) != 0) ok = false;
+  if (rc) return rc;
+  return ok ? HCA_OK : HCA_ERR_IO;
+}
+
+int hca_load(const char* path, void* stream, hca_handle** out) {
+  if (!path || !out) return HCA_ERR_ARG;
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return HCA_ERR_IO;
+  CkptHeader hd{};
+  int rc = HCA_OK;
+  std::vector<hca_config> cfgs;
+  std::vector<std::vector<float>> perf;
+  hca_handle* h = nullptr;
+  if (std::fread(&hd, sizeof(hd), 1, f) != 1) rc = HCA_ERR_IO;
+  else if (std::memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != 1 ||
+           hd.config_size != (int32_t)sizeof(hca_config) || hd.n_reps < 1 || hd.n_reps > (1 << 20))
+    rc = HCA_ERR_ARG;
+  if (!rc) {
+    cfgs.resize(hd.n_reps);
+    if (std::fread(cfgs.data(), sizeof(hca_config), hd.n_reps, f) != (size_t)hd.n_reps) rc = HCA_ERR_IO;
+  }
+  // validate before any allocation sized from the file
+  for (int i = 0; i < hd.n_reps && !rc; ++i) {
+    cfgs[i].stream = stream;
+    rc = validate(cfgs[i]);
+    if (!rc && cfgs[i].precision != hd.precision) rc = HCA_ERR_ARG;
+  }
+  std::vector<std::vector<char>> perf_raw;
+  if (!rc) {
+    // creation needs maps: zero densities and the saved perfusion (written
+    // back in the handle's precision below); states and fields are then
+    // overwritten, so only perfusion's bounds check matters
+    const size_t es = hd.precision == HCA_FP64 ? 8 : 4;
+    perf.resize(hd.n_reps);
+    perf_raw.resize(hd.n_reps);
+    for (int i = 0; i < hd.n_reps && !rc; ++i) {
+      const size_t n = (size_t)cfgs[i].nx * cfgs[i].ny * cfgs[i].nz;
+      perf_raw[i].resize(n * es);
+      if (std::fread(perf_raw[i].data(), es, n, f) != n) {
+        rc = HCA_ERR_IO;
+        break;
+      }
+      perf[i].resize(n);
+      for (size_t k = 0; k < n; ++k)
+        perf[i][k] = es == 8 ? (float)((const double*)perf_raw[i].data())[k] : ((const float*)perf_raw[i].data())[k];
+    }
+    if (!rc) {
+      std::vector<std::vector<float>> zeros(hd.n_reps);
+      std::vector<const float*> pz(hd.n_reps), pp(hd.n_reps);
+      for (int i = 0; i < hd.n_reps; ++i) {
+        zeros[i].assign(perf[i].size(), 0.f);
+        pz[i] = zeros[i].data();
+        pp[i] = perf[i].data();
+      }
+      rc = create_impl(hd.n_reps, cfgs.data(), pz.data(), pp.data(), pz.data(), 0, &h, false);
+    }
+  }
+  for (int i = 0; h && i < h->n_reps && !rc; ++i) {
+    const RepDesc& r = h->reps_h[i];
+    const size_t n = (size_t)r.nx * r.ny * r.nz, es = elem_size(h);
+    std::vector<char> buf(n * es);
+    // perfusion in the handle's precision exactly as saved (creation rounded it through FP32)
+    rc = copy_field(h, i, h->ctx.perf, es, perf_raw[i].data(), false, 0);
+    if (!rc && std::fread(buf.data(), 1, n, f) != n) rc = HCA_ERR_IO;
+    if (!rc) rc = copy_states(h, i, (uint8_t*)buf.data(), false);
+    if (!rc && cudaStreamSynchronize(h->ctx.stream) != cudaSuccess) rc = HCA_ERR_CUDA;
+    for (void* fld : ckpt_fields(h)) {
+      if (!fld || rc) continue;
+      if (std::fread(buf.data(), es, n, f) != n) rc = HCA_ERR_IO;
+      if (!rc) rc = copy_field(h, i, fld, es, buf.data(), false, 0);
+      if (!rc && cudaStreamSynchronize(h->ctx.stream) != cudaSuccess) rc = HCA_ERR_CUDA;
+    }
+  }
+  std::fclose(f);
+  if (!rc && h) {
+    h->picard_iterations = hd.picard_iterations;
+    rc = hca_set_step(h, hd.step);
+  }
+  if (rc) {
+    if (h) hca_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return HCA_OK;
+}
+
 void hca_destroy(hca_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->ctx.stream);
@@ -1759,6 +1938,7 @@ const char* hca_status_string(int32_t s) {
     case HCA_ERR_TIMEOUT: return "a bounded device wait gave up";
     case HCA_ERR_UNIMPLEMENTED: return "not implemented";
     case HCA_ERR_STATE: return "call not valid in the current state";
+    case HCA_ERR_IO: return "checkpoint file input/output failed";
     default: return "unknown status";
   }
 }

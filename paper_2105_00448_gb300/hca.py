@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import struct
 from typing import Dict, Optional, Sequence
 
 import numpy as np
@@ -26,6 +27,7 @@ HCA_ERR_NOCONV = -5
 HCA_ERR_TIMEOUT = -6
 HCA_ERR_UNIMPLEMENTED = -7
 HCA_ERR_STATE = -8
+HCA_ERR_IO = -9
 
 HCA_FP64 = 0
 HCA_FP32 = 1
@@ -143,7 +145,7 @@ EXPORTS = [
     "hca_set_step", "hca_get_stats", "hca_apply_operator", "hca_apply_preconditioner", "hca_philox_uniforms",
     "hca_get_launch_config",
     "hca_sync", "hca_get_shape", "hca_launch_count", "hca_profile_enable", "hca_get_profile",
-    "hca_o2_residual_noalloc", "hca_destroy", "hca_status_string",
+    "hca_o2_residual_noalloc", "hca_save", "hca_load", "hca_destroy", "hca_status_string",
     "hca_net_param_count", "hca_net_create", "hca_net_set_params", "hca_net_get_params", "hca_net_forward",
     "hca_net_forward_x", "hca_net_read_activation", "hca_net_gradients_x", "hca_net_gradients", "hca_net_adam", "hca_net_train_step", "hca_net_sync",
     "hca_net_destroy", "hca_set_warm_start_net",
@@ -204,6 +206,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "hca_profile_enable": (ctypes.c_int, [P, I32]),
         "hca_get_profile": (ctypes.c_int, [P, ctypes.POINTER(hca_profile)]),
         "hca_o2_residual_noalloc": (ctypes.c_int, [cfgp, P, P, P, ctypes.POINTER(ctypes.c_double), P]),
+        "hca_save": (ctypes.c_int, [P, ctypes.c_char_p]),
+        "hca_load": (ctypes.c_int, [ctypes.c_char_p, P, ctypes.POINTER(P)]),
         "hca_destroy": (None, [P]),
         "hca_status_string": (ctypes.c_char_p, [I32]),
         "hca_net_param_count": (ctypes.c_int, [ctypes.POINTER(I64)]),
@@ -419,6 +423,35 @@ def hca_destroy(h) -> None:
         load().hca_destroy(h)
 
 
+def hca_save(h, path: str) -> None:
+    _check(load().hca_save(h, os.fsencode(path)), "hca_save")
+
+
+def hca_load(path: str, stream=None):
+    h = ctypes.c_void_p()
+    _check(load().hca_load(os.fsencode(path), ctypes.c_void_p(int(stream)) if stream is not None else None,
+                           ctypes.byref(h)), "hca_load")
+    return h
+
+
+def checkpoint_configs(path: str):
+    """The configurations stored in a checkpoint file (its header is read
+    here; see hca_save for the format)."""
+    with open(path, "rb") as f:
+        head = f.read(40)
+        if len(head) != 40 or head[:8] != b"HCACKPT1":
+            raise ValueError("not a checkpoint file")
+        version, csize, n, _prec = struct.unpack("<4i", head[8:24])
+        if version != 1 or csize != ctypes.sizeof(hca_config):
+            raise ValueError("checkpoint of another ABI")
+        cfgs = []
+        for _ in range(n):
+            cfg = hca_config()
+            ctypes.memmove(ctypes.byref(cfg), f.read(csize), csize)
+            cfgs.append(cfg)
+    return cfgs
+
+
 # ------------------------------------------- learned warm start (net) ---
 def _dev(t, what, nbytes=None):
     p, nb, on_dev = _ptr(t)
@@ -615,6 +648,18 @@ class Sim:
 
     def launches(self) -> int:
         return hca_launch_count(self.handle)
+
+    def save(self, path: str) -> None:
+        hca_save(self.handle, path)
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "Sim":
+        sim = cls.__new__(cls)
+        sim.cfgs = checkpoint_configs(path)
+        sim.handle = hca_load(path, stream)
+        sim.fp64 = sim.cfgs[0].precision == HCA_FP64
+        sim.dtype = np.float64 if sim.fp64 else np.float32
+        return sim
 
     def set_warm_start_net(self, net) -> None:
         hca_set_warm_start_net(self.handle, net.handle if isinstance(net, Net) else net)

@@ -46,7 +46,7 @@ def test_config_struct_layout_matches(lib):
 
 
 def test_status_strings(lib):
-    for code in range(0, -9, -1):
+    for code in range(0, -10, -1):
         s = lib.hca_status_string(code)
         assert s and s != b"unknown status"
     assert lib.hca_status_string(-99) == b"unknown status"
@@ -86,3 +86,18 @@ def test_library_defaults_equal_oracle_defaults(lib):
         got = list(got) if hasattr(got, "__len__") else got
         want = list(want) if isinstance(want, tuple) else want
         assert got == pytest.approx(want, rel=1e-15), f
+
+
+def test_checkpoint_errors_without_gpu(lib, tmp_path):
+    """hca_load rejects a missing file and a file that is not a checkpoint
+    before touching the device; hca_save rejects null arguments."""
+    h = ctypes.c_void_p()
+    missing = str(tmp_path / "none.ckpt").encode()
+    assert lib.hca_load(missing, None, ctypes.byref(h)) == hca.HCA_ERR_IO
+    bad = tmp_path / "bad.ckpt"
+    bad.write_bytes(b"NOTACKPT" + bytes(200))
+    assert lib.hca_load(str(bad).encode(), None, ctypes.byref(h)) == hca.HCA_ERR_ARG
+    assert lib.hca_load(None, None, ctypes.byref(h)) == hca.HCA_ERR_ARG
+    assert lib.hca_save(None, b"x") == hca.HCA_ERR_ARG
+    with pytest.raises(ValueError):
+        hca.checkpoint_configs(str(bad))
