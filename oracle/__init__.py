@@ -24,6 +24,11 @@ odes     Cell-cycle clock, p53 and intracellular VEGF (Eqs. cellcycle, odep53, o
 ca       The stochastic cellular automaton update (Sections 2.2.1 and 2.5).
 model    Algorithm 1: initialisation and the time loop.
 convnet  FP64 reference of the learned warm-start network (no paper counterpart).
+ca_sync  The synchronous CA update with Algorithm 2's higher-phi rule.
+vascular The VEGF field's automaton: vessel birth and death (Eq. vascular_module).
+pk       Michaelis-Menten and three-compartment plasma models (Section 2.2.3).
+multigrid The geometric V-cycle preconditioner and MG-PCG.
+api      The library's call names (oracle_create, oracle_step, ...) over model.
 
 Parity status: every function is pinned by tests under ``tests/test_oracle_*``
 except the ones whose docstring says "parity unpinned".

@@ -405,3 +405,28 @@ def test_autotuned_launch_shape_gives_identical_results(precision, monkeypatch):
     (s0, K0, G0, st0), (s1, K1, G1, st1) = runs
     assert np.array_equal(s0, s1) and np.array_equal(K0, K1) and np.array_equal(G0, G1)
     assert st0["o2_iterations"] == st1["o2_iterations"] and st0["drug_iterations"] == st1["drug_iterations"]
+
+
+def test_same_call_sequence_on_library_and_oracle():
+    """The library and the oracle driven through the same call names
+    (hca_* / oracle_*): states bit-exact, fields within 1e-9 (FP64)."""
+    from oracle import api
+
+    n = 12
+    params = dict(n_drugs=2, seed=17, rtol_o2=1e-13, rtol_drug=1e-13, picard_tol=1e-12)
+    m = make_maps(n, n, n, corr_len=3.0, seed=17)
+    h = hca.hca_create(hca.make_config(n, n, n, **params), m.p_cell, m.perf, m.p_vessel)
+    o = api.oracle_create(Pm.Config(n, n, n, **params), m.p_cell, m.perf, m.p_vessel)
+    mask = hca.FIELD_O2 | hca.FIELD_DRUG0 | hca.FIELD_DRUG1 | hca.FIELD_PHI
+    for _ in range(3):
+        assert hca.hca_step(h, 1) == hca.HCA_OK
+        api.oracle_step(o, 1)
+        st = np.empty(n ** 3, dtype=np.uint8)
+        hca.hca_read_states(h, 0, st)
+        assert np.array_equal(st, api.oracle_read_states(o, 0))
+        f = np.empty(4 * n ** 3)
+        hca.hca_read_fields(h, 0, mask, f)
+        ref = api.oracle_read_fields(o, 0, mask)
+        assert np.max(np.abs(f - ref)) <= 1e-9 * np.max(np.abs(ref))
+    hca.hca_destroy(h)
+    api.oracle_destroy(o)
