@@ -201,6 +201,30 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------- GPU ---
+# ----------------------------------------------------------- replicas ---
+# N > 1: every rank advances its own replicate (seed + rank, its own maps);
+# there is no collective on the data path, only the timing barrier and the
+# max over ranks of the timed region.
+def replica_seed(base: int, rank: int) -> int:
+    return base + rank
+
+
+def max_over_ranks(t_ms: float, dist, device: str) -> float:
+    """The job's time: the slowest rank's (all_reduce MAX; identity for one rank)."""
+    if dist is None:
+        return t_ms
+    import torch
+
+    t = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, sites: int, steps: int, t_ms: float) -> float:
+    """Whole-job site-steps/s: every rank's sites over the slowest rank's time."""
+    return world * sites * steps / (t_ms / 1e3)
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -220,7 +244,7 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     n = args.edge
     sites = n ** 3
-    seed = WORKLOAD["seed"] + rank
+    seed = replica_seed(WORKLOAD["seed"], rank)
     params = {**WORKLOAD, "seed": seed}
     maps = make_maps(n, n, n, corr_len=CORR_LEN, seed=seed)
     stream = torch.cuda.Stream()
@@ -248,10 +272,7 @@ def run_gpu(args):
     t_ms = ev0.elapsed_time(ev1)
     launches = sim.launches() - launches0
     stats = sim.stats()
-    if dist:
-        t = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
+    t_ms = max_over_ranks(t_ms, dist, "cuda")
     # Per-kernel device time: the next steps of the same run, driven from the
     # host with CUDA events around every launch on the library's stream.
     hca.hca_profile_enable(sim.handle, True)
@@ -259,7 +280,7 @@ def run_gpu(args):
     prof = hca.hca_get_profile(sim.handle)
     hca.hca_profile_enable(sim.handle, False)
     sim.close()
-    value = world * sites * args.steps / (t_ms / 1e3)
+    value = job_value(world, sites, args.steps, t_ms)
 
     # roofline of the dominant kernel class (by summed device time)
     peak, peak_kind = measured_peak_hbm()
