@@ -1183,6 +1183,14 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
       }
       H.nrowitems = rowstart[n];
       H.launches = hca::vcycle_launches(H, false);
+      {
+        // row-vector coarse kernels for a single replicate whose level rows
+        // are whole 4-site groups (HCA_MG_GENERIC=1 keeps the per-site form)
+        const char* gen = std::getenv("HCA_MG_GENERIC");
+        if (n == 1 && !(gen && gen[0] == '1'))
+          for (int l = 1; l < rep[0].x; ++l)
+            if (lv[l].nx % 4 == 0) H.rows_ok |= 1u << l;
+      }
       ALLOC(c.r, fbytes);
       ALLOC(c.mg_t0, fbytes);
       ALLOC(c.mg_w, fbytes);

@@ -272,6 +272,7 @@ struct MGHost {
   long long nrowitems = 0;         // (level-1 row, lattice 4-site group) items over the replicates
   int launches = 0;              // kernels per V-cycle
   int ni = 0;                    // groups per lane in a row of the lattice (1, 2, 4; 0 = other)
+  unsigned rows_ok = 0;          // bit l: level l's rows are whole 4-site groups (single replicate)
 };
 
 struct Ctx {

@@ -222,13 +222,15 @@ __device__ void restrict_fused_at(const View<T>& F, const View<T>& C, long long 
     const int x = 2 * X + (k & 1), y = 2 * Y + ((k >> 1) & 1), z = 2 * Z + (k >> 2);
     if (x < F.nx && y < F.ny && z < F.nz) {
       const long long e = F.at(x, y, z);
+      // nb += (omega/d) rhs as one fused multiply-add per neighbour (the
+      // row-vector restriction forms the same sums)
       T nb = T(0);
-      if (x > 0) nb += u_first(F, e - 1);
-      if (x < F.nx - 1) nb += u_first(F, e + 1);
-      if (y > 0) nb += u_first(F, e - F.sy);
-      if (y < F.ny - 1) nb += u_first(F, e + F.sy);
-      if (z > 0) nb += u_first(F, e - F.sz);
-      if (z < F.nz - 1) nb += u_first(F, e + F.sz);
+      if (x > 0) nb = fma(F.w[e - 1], F.rhs[e - 1], nb);
+      if (x < F.nx - 1) nb = fma(F.w[e + 1], F.rhs[e + 1], nb);
+      if (y > 0) nb = fma(F.w[e - F.sy], F.rhs[e - F.sy], nb);
+      if (y < F.ny - 1) nb = fma(F.w[e + F.sy], F.rhs[e + F.sy], nb);
+      if (z > 0) nb = fma(F.w[e - F.sz], F.rhs[e - F.sz], nb);
+      if (z < F.nz - 1) nb = fma(F.w[e + F.sz], F.rhs[e + F.sz], nb);
       acc += F.rhs[e] - (F.d[e] * u_first(F, e) - F.c * nb);
     }
   }
@@ -239,7 +241,10 @@ __device__ void restrict_fused_at(const View<T>& F, const View<T>& C, long long 
 // (prolongation fused into the post-smoothing sweep; u is not stored)
 template <typename T>
 __device__ void post_fused_at(const View<T>& F, const View<T>& C, long long s) {
-  auto u = [&](int x, int y, int z) { return u_first(F, F.at(x, y, z)) + C.x[C.at(x >> 1, y >> 1, z >> 1)]; };
+  auto u = [&](int x, int y, int z) {
+    const long long ef = F.at(x, y, z);
+    return fma(F.w[ef], F.rhs[ef], C.x[C.at(x >> 1, y >> 1, z >> 1)]);
+  };
   int X, Y, Z;
   F.coords(s, X, Y, Z);
   const long long e = F.at(X, Y, Z);
@@ -363,6 +368,161 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_post(Ctx c, int which, int l)
     if (k.at(c, which, l, q, true)) skip = l >= c.mg_rep[k.r].y;
     if (skip) continue;
     post_fused_at<T>(k.F, k.C, q - k.lo);
+  }
+}
+
+// Post-smoothing on coarse level l >= 1 of a single replicate in row-vector
+// form (the level's rows a whole number of 4-site groups): one thread per
+// group; every load of the group (rhs and omega/d of its row and the four
+// neighbour rows, the sites left and right of it, d, the level-(l+1)
+// correction under each row) is issued before u = (omega/d) rhs + P x_C is
+// formed.  The same arithmetic, in the same order, as post_fused_at.
+template <typename T>
+__global__ void __launch_bounds__(kMgThreads) k_mg_post_rows(Ctx c, int which, int l) {
+  HCA_COUNT_KERNEL(c);
+  const View<T> F = view<T>(c, which, 0, l), C = view<T>(c, which, 0, l + 1);
+  const int gpr = F.nx >> 2;
+  const long long items = (long long)F.ny * F.nz * gpr;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < items;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(q % gpr);
+    const long long R = q / gpr;
+    const int Y = (int)(R % F.ny), Z = (int)(R / F.ny);
+    const int X0 = 4 * j;
+    const long long e = F.at(X0, Y, Z);
+    const bool rok[5] = {true, Y > 0, Y < F.ny - 1, Z > 0, Z < F.nz - 1};
+    const long long roff[5] = {0, -F.sy, F.sy, -F.sz, F.sz};
+    const int ry[5] = {Y, Y - 1, Y + 1, Y, Y};
+    const int rz[5] = {Z, Z, Z, Z - 1, Z + 1};
+    V4<T> RH[5], WV[5];
+    T C0[5], C1[5];
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+      RH[t] = ld4_if(F.rhs + e + roff[t], rok[t]);
+      WV[t] = ld4_if(F.w + e + roff[t], rok[t]);
+      const long long cb = rok[t] ? C.at(2 * j, ry[t] >> 1, rz[t] >> 1) : 0;
+      C0[t] = rok[t] ? C.x[cb] : T(0);
+      C1[t] = rok[t] ? C.x[cb + 1] : T(0);
+    }
+    const bool has_l = j > 0, has_r = j + 1 < gpr;
+    const T wl = has_l ? F.w[e - 1] : T(0), rl = has_l ? F.rhs[e - 1] : T(0);
+    const T wr = has_r ? F.w[e + 4] : T(0), rr = has_r ? F.rhs[e + 4] : T(0);
+    const long long cy = C.at(0, Y >> 1, Z >> 1);
+    const T cl = has_l ? C.x[cy + 2 * j - 1] : T(0), cr = has_r ? C.x[cy + 2 * j + 2] : T(0);
+    const V4<T> D = ld4(F.d + e);
+    V4<T> U[5];
+#pragma unroll
+    for (int t = 0; t < 5; ++t)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) U[t].a[k] = rok[t] ? fma(WV[t].a[k], RH[t].a[k], k < 2 ? C0[t] : C1[t]) : T(0);
+    const T ul = has_l ? fma(wl, rl, cl) : T(0), ur = has_r ? fma(wr, rr, cr) : T(0);
+    V4<T> Xo;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      T nb = T(0);
+      if (k > 0 || has_l) nb += k > 0 ? U[0].a[k - 1] : ul;
+      if (k < 3 || has_r) nb += k < 3 ? U[0].a[k + 1] : ur;
+      if (rok[1]) nb += U[1].a[k];
+      if (rok[2]) nb += U[2].a[k];
+      if (rok[3]) nb += U[3].a[k];
+      if (rok[4]) nb += U[4].a[k];
+      const T uc = U[0].a[k];
+      Xo.a[k] = uc + WV[0].a[k] * (RH[0].a[k] - (D.a[k] * uc - F.c * nb));
+    }
+    *reinterpret_cast<V4<T>*>(F.x + e) = Xo;
+  }
+}
+
+// Restriction from coarse level l >= 1 to l + 1 of a single replicate in
+// row-vector form (level l's rows whole 4-site groups): one thread per group
+// of the four fine rows (2Y + dy, 2Z + dz) under coarse row (Y, Z), producing
+// coarse sites 2j, 2j + 1; all loads (rhs and omega/d of the 4 own and 8 outer
+// rows, d, the x neighbours) are issued before u = (omega/d) rhs is formed.
+// The same arithmetic, children in the same order, as restrict_fused_at.
+template <typename T>
+__global__ void __launch_bounds__(128) k_mg_restrict_rows(Ctx c, int which, int l) {
+  HCA_COUNT_KERNEL(c);
+  const View<T> F = view<T>(c, which, 0, l), C = view<T>(c, which, 0, l + 1);
+  const int gpr = F.nx >> 2;
+  const long long items = (long long)C.ny * C.nz * gpr;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < items;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(q % gpr);
+    const long long R = q / gpr;
+    const int Y = (int)(R % C.ny), Z = (int)(R / C.ny);
+    const int y0 = 2 * Y, z0 = 2 * Z, x0 = 4 * j;
+    const long long eb = F.at(x0, y0, z0);
+    // rows: own t = 2 dy + dz; outer: y0 - 1, y0 + 2 (for dz = 0, 1), z0 - 1, z0 + 2 (for dy = 0, 1)
+    bool ok[12];
+    long long off[12];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        ok[2 * a + b] = (y0 + a < F.ny) && (z0 + b < F.nz);
+        off[2 * a + b] = F.sy * a + F.sz * b;
+      }
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      ok[4 + b] = y0 > 0 && z0 + b < F.nz;
+      off[4 + b] = -F.sy + F.sz * b;
+      ok[6 + b] = y0 + 2 < F.ny && z0 + b < F.nz;
+      off[6 + b] = 2 * F.sy + F.sz * b;
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      ok[8 + a] = z0 > 0 && y0 + a < F.ny;
+      off[8 + a] = F.sy * a - F.sz;
+      ok[10 + a] = z0 + 2 < F.nz && y0 + a < F.ny;
+      off[10 + a] = F.sy * a + 2 * F.sz;
+    }
+    V4<T> RV[12], WV[12], DV[4];
+#pragma unroll
+    for (int t = 0; t < 12; ++t) {
+      RV[t] = ld4_if(F.rhs + eb + off[t], ok[t]);
+      WV[t] = ld4_if(F.w + eb + off[t], ok[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) DV[t] = ld4_if(F.d + eb + off[t], ok[t]);
+    T lr[4], lw[4], rrr[4], rw[4];
+    const bool hasl = x0 > 0, hasr = x0 + 4 < F.nx;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      lr[t] = (ok[t] && hasl) ? F.rhs[eb + off[t] - 1] : T(0);
+      lw[t] = (ok[t] && hasl) ? F.w[eb + off[t] - 1] : T(0);
+      rrr[t] = (ok[t] && hasr) ? F.rhs[eb + off[t] + 4] : T(0);
+      rw[t] = (ok[t] && hasr) ? F.w[eb + off[t] + 4] : T(0);
+    }
+    V4<T> U[12];
+#pragma unroll
+    for (int t = 0; t < 12; ++t)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) U[t].a[e] = WV[t].a[e] * RV[t].a[e];
+    T acc[2] = {T(0), T(0)};
+    // children in the order of restrict_fused_at: dz outer, dy, dx inner
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int t = 2 * a + b;
+          if (!ok[t]) continue;
+          const int ym = a ? b : 4 + b, yp = a ? 6 + b : 2 + b;          // rows y - 1, y + 1
+          const int zm = b ? 2 * a : 8 + a, zp = b ? 10 + a : 2 * a + 1;  // rows z - 1, z + 1
+          const int x = x0 + e;
+          T nb = T(0);
+          if (x > 0) nb = e == 0 ? fma(lw[t], lr[t], nb) : fma(WV[t].a[e - 1], RV[t].a[e - 1], nb);
+          if (x < F.nx - 1) nb = e == 3 ? fma(rw[t], rrr[t], nb) : fma(WV[t].a[e + 1], RV[t].a[e + 1], nb);
+          if (y0 + a > 0) nb = fma(WV[ym].a[e], RV[ym].a[e], nb);
+          if (y0 + a < F.ny - 1) nb = fma(WV[yp].a[e], RV[yp].a[e], nb);
+          if (z0 + b > 0) nb = fma(WV[zm].a[e], RV[zm].a[e], nb);
+          if (z0 + b < F.nz - 1) nb = fma(WV[zp].a[e], RV[zp].a[e], nb);
+          acc[e >> 1] += RV[t].a[e] - (DV[t].a[e] * U[t].a[e] - F.c * nb);
+        }
+    const long long cb = C.at(2 * j, Y, Z);
+    C.rhs[cb] = acc[0];
+    C.rhs[cb + 1] = acc[1];
   }
 }
 
@@ -690,11 +850,14 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
   if (all || part == 1) {
     for (int l = 1; l < H.small; ++l) {
       if (multi) k_mg_restrict<T, true><<<grid_for(H.ntot[l + 1]), kMgThreads, 0, s>>>(c, which, l);
+      else if (H.rows_ok >> l & 1u)   // 128 threads: ~28 vector loads per thread in flight
+        k_mg_restrict_rows<T><<<(int)std::min((H.ntot[l + 1] / 2 + 127) / 128, 152LL * 16), 128, 0, s>>>(c, which, l);
       else k_mg_restrict<T, false><<<grid_for(H.ntot[l + 1]), kMgThreads, 0, s>>>(c, which, l);
     }
     k_mg_small<T><<<c.n_reps, kSmallThreads, 0, s>>>(c, which);
     for (int l = H.small - 1; l >= 1; --l) {
       if (multi) k_mg_post<T, true><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
+      else if (H.rows_ok >> l & 1u) k_mg_post_rows<T><<<grid_for(H.ntot[l] / 4), kMgThreads, 0, s>>>(c, which, l);
       else k_mg_post<T, false><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
     }
   }

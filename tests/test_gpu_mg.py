@@ -204,3 +204,19 @@ def test_mg_edge_cases():
         sim.apply_preconditioner(0, np.zeros((8, 8, 8)))
     assert e.value.status == hca.HCA_ERR_STATE
     sim.close()
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("shape", [(32, 32, 32), (24, 40, 56), (20, 44, 104), (1, 64, 96)])
+def test_row_coarse_kernels_are_bit_identical(shape, precision, monkeypatch):
+    """The row-vector coarse post-sweep gives the per-site kernel's bits."""
+    out = []
+    for generic in ("1", "0"):
+        monkeypatch.setenv("HCA_MG_GENERIC", generic)
+        sim, _, _ = make_pair(shape, precision, seed=13, n_drugs=2, preconditioner=hca.HCA_PC_MG)
+        sim.step(2)
+        out.append((sim.states(), sim.field(hca.FIELD_O2), sim.field(hca.FIELD_DRUG[1]), sim.stats()))
+        sim.close()
+    (s0, K0, G0, st0), (s1, K1, G1, st1) = out
+    assert np.array_equal(s0, s1) and np.array_equal(K0, K1) and np.array_equal(G0, G1)
+    assert (st0["o2_iterations"], st0["drug_iterations"]) == (st1["o2_iterations"], st1["drug_iterations"])
