@@ -574,6 +574,27 @@ __global__ void __launch_bounds__(512) k_diff_norms(Ctx c, const T* __restrict__
                  });
 }
 
+// A sum of FP32 terms s * 2^ex kept as m * 2^e in FP32 arithmetic (the
+// terms are scaled sums of a few squares, so m stays of order one; terms more
+// than 2^126 below the running sum underflow to zero), converted to FP64 once.
+struct ScaledAcc {
+  float m = 0.f;
+  int e = 0;
+  __device__ __forceinline__ void add(float s, int ex) {
+    if (s == 0.f) return;
+    if (m == 0.f) {
+      m = s;
+      e = ex;
+    } else if (ex > e) {
+      m = scalbnf(m, e - ex) + s;
+      e = ex;
+    } else {
+      m += scalbnf(s, ex - e);
+    }
+  }
+  __device__ __forceinline__ double value() const { return m == 0.f ? 0.0 : ldexp((double)m, e); }
+};
+
 // --------------------------------------------------- defect correction ---
 // FP32 storage scheme.  The solution is kept as two FP32 words, x = x_hi +
 // x_lo.  Each sweep evaluates the residual r = b - A x in FP64 from the
@@ -618,7 +639,7 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
       const int rl = rbase + it.sub;
       const bool row_ok = rl < nrows;
       const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
-      double acc[NDOT] = {0.0, 0.0, 0.0};
+      ScaledAcc la[NDOT];
       float carry_h = 0.f, carry_l = 0.f;
       for (int itn = 0; itn < it.niter; ++itn) {
         const int g = itn * it.lpr + it.sl;
@@ -711,24 +732,25 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
           // the group's |r|^2, r.z and |b|^2: each 4-term sum is taken in
           // FP32 after an exact power-of-two scaling by the group's largest
           // magnitude (a decayed field's residual, ~1e-22, would underflow
-          // when squared unscaled) and enters the FP64 row sums once
-          auto scaled_sum = [](const V4<float>& v, const V4<float>* w) -> double {
+          // when squared unscaled); the lane keeps its groups' sums as a
+          // scaled FP32 pair and enters the FP64 row sums once per row (FP64
+          // arithmetic is a small fraction of FP32's on this GPU)
+          auto scaled_sum = [](const V4<float>& v, ScaledAcc& acc) {
             float m = 0.f;
 #pragma unroll
             for (int k = 0; k < 4; ++k) m = fmaxf(m, fabsf(v.a[k]));
-            if (m == 0.f) return 0.0;
+            if (m == 0.f) return;
             const int ex = ilogbf(m);
             float s2 = 0.f;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
               const float u = scalbnf(v.a[k], -ex);
-              s2 += w ? u * scalbnf(w->a[k], -ex) : u * u;
+              s2 += u * u;
             }
-            return ldexp((double)s2, 2 * ex);
+            acc.add(s2, 2 * ex);
           };
-          const double g_rr = scaled_sum(R32, nullptr);
-          const double g_bb = first ? scaled_sum(B, nullptr) : 0.0;
-          double g_rho = 0.0;
+          scaled_sum(R32, la[0]);
+          if (first) scaled_sum(B, la[1]);
           if (!c.mg) {
             // r.z with z = r / d: scale r and z by the same power (|z| may be
             // far from |r|, so each is scaled by its own group maximum)
@@ -743,17 +765,17 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
               float s = 0.f;
 #pragma unroll
               for (int k = 0; k < 4; ++k) s += scalbnf(R32.a[k], -er) * scalbnf(Z.a[k], -ez);
-              g_rho = ldexp((double)s, er + ez);
+              la[2].add(s, er + ez);
             }
           }
           st4(zz + e, Z);
           if (c.mg) st4((float*)c.r + e, R32);
           st4(dxv + e, zero4<float>());
-          acc[0] += g_rr;
-          acc[1] += g_bb;
-          acc[2] += g_rho;
         }
       }
+      double acc[NDOT];
+#pragma unroll
+      for (int k = 0; k < NDOT; ++k) acc[k] = la[k].value();
       store_row(c, blockIdx.x, rl, row_ok, it.sl, it.lpr, acc, 3);
     }
   }
