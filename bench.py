@@ -200,7 +200,6 @@ def run_reference(args):
     return 0
 
 
-# --------------------------------------------------------------- GPU ---
 # ----------------------------------------------------------- replicas ---
 # N > 1: every rank advances its own replicate (seed + rank, its own maps);
 # there is no collective on the data path, only the timing barrier and the
@@ -225,6 +224,7 @@ def job_value(world: int, sites: int, steps: int, t_ms: float) -> float:
     return world * sites * steps / (t_ms / 1e3)
 
 
+# --------------------------------------------------------------- GPU ---
 def run_gpu(args):
     import numpy as np
     import torch
