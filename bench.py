@@ -40,12 +40,13 @@ WORKLOAD = dict(precision="f32", n_drugs=2, seed=1, rtol_o2=1e-8, rtol_drug=1e-8
                 dose_interval=21, preconditioner=1)     # 1 = HCA_PC_MG
 CORR_LEN = 8.0
 # algorithmic HBM bytes per site of each kernel class (FP32):
-#   pass A reads z, p_old, d and writes p_new; pass B reads p, d, x, r and writes x, r;
+#   pass A reads z, p_old, d and writes p_new and q = A p_new; pass B reads p, q, x, r and
+#   writes x, r;
 #   defect-correction residual (later sweeps) reads x_hi, x_lo, d, a, b and writes z, dx, r;
 #   multigrid on the lattice: the first sweep + restriction reads r, omega/d, d and writes the
 #   1/8-size coarse right-hand side; the prolongation + last sweep reads r, omega/d, d and the
 #   1/8-size coarse correction and writes z; ODE reads state, K and updates phi, P, Vc
-BYTES_PER_SITE = {"pass_a": 16, "pass_b": 24, "setup": 17, "residual": 32, "ode": 29,
+BYTES_PER_SITE = {"pass_a": 20, "pass_b": 24, "setup": 17, "residual": 32, "ode": 29,
                   "mg_restrict0": 12.5, "mg_post0": 16.5}
 
 

@@ -1098,6 +1098,7 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     ALLOC(c.z, fbytes);
     ALLOC(c.p, fbytes);
     ALLOC(c.p_alt, fbytes);
+    ALLOC(c.q, fbytes);
     ALLOC(c.d, fbytes);
     ALLOC(c.b, fbytes);
     ALLOC(c.aux, fbytes);
@@ -1257,7 +1258,7 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
     }
     // zero every device array (padding sites must hold 0)
     void* zero_list[] = {c.K, c.K_lo, c.G[0], c.G[1], c.G[2], c.G[3], c.G_lo[0], c.G_lo[1], c.G_lo[2], c.G_lo[3], c.dx,
-                         c.phi, c.P, c.Vc, c.perf, c.z, c.p, c.p_alt, c.d, c.b, c.aux, c.reac, c.r, c.mg_t0, c.mg_w};
+                         c.phi, c.P, c.Vc, c.perf, c.z, c.p, c.p_alt, c.q, c.d, c.b, c.aux, c.reac, c.r, c.mg_t0, c.mg_w};
     for (void* p : zero_list)
       if (p && cudaMemsetAsync(p, 0, fbytes, s)) {
         rc = HCA_ERR_CUDA;

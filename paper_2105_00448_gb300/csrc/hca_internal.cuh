@@ -313,6 +313,7 @@ struct Ctx {
   void* z;       // preconditioned residual z = r / d
   void* p;       // search direction (two buffers: pass A reads one, writes the other)
   void* p_alt;
+  void* q;           // A p of the current direction (written by pass A, read by pass B)
   void* d;       // operator diagonal
   void* b;       // right-hand side (drugs) / defect (oxygen correction solve)
   double* partial;

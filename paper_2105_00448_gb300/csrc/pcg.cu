@@ -206,6 +206,7 @@ __global__ void __maxnreg__(REGS) k_pass_a(Ctx c, int which) {
     T* __restrict__ p_new = (T*)(par ? c.p : c.p_alt);
     const T* __restrict__ zz = (const T*)c.z;
     const T* __restrict__ dd = (const T*)c.d;
+    T* __restrict__ qq = (T*)c.q;
     const T beta = (T)sv.beta;
     const bool use_p = sv.beta != 0.0;
     // the first iteration of a rescaled inner solve starts from scale * z
@@ -261,12 +262,14 @@ __global__ void __maxnreg__(REGS) k_pass_a(Ctx c, int which) {
         x_neighbours(PN, g, gpr, it.sl, it.lpr, gok, carry, left, right, [&] { return right_next; });
         if (gok) {
           T g_s = 0;
+          V4<T> Q;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            const T q = D.a[k] * PN.a[k] - cpl * nb_sum(PN, k, left, right, ym, yp, zm, zp);
-            g_s += PN.a[k] * q;
+            Q.a[k] = D.a[k] * PN.a[k] - cpl * nb_sum(PN, k, left, right, ym, yp, zm, zp);
+            g_s += PN.a[k] * Q.a[k];
           }
           st4(p_new + e, PN);
+          st4(qq + e, Q);   // pass B reads A p instead of re-forming it from p's neighbours
           acc[0].add(g_s);
         }
       }
@@ -302,17 +305,16 @@ __global__ void __maxnreg__(REGS) k_pass_b(Ctx c, int which, void* xfield, CondA
     T* __restrict__ zz = (T*)(mg ? c.r : c.z);
     const T* __restrict__ pp = (const T*)(c.sync->parity ? c.p : c.p_alt);
     const T* __restrict__ dd = (const T*)c.d;
+    const T* __restrict__ qq = (const T*)c.q;
     T* __restrict__ xx = (T*)xfield;
     const T alpha = (T)sv.alpha;
     const T zs = (sv.iters == 0 && !mg) ? (T)sv.scale : T(1);
-    const T cpl = (T)op_coupling(rd, which);
     const RowIter it = row_iter(rd);
     for (int rbase = it.warp * it.rpw; rbase < rd.chunk_rows; rbase += it.nw * it.rpw) {
       const int rl = rbase + it.sub;
       const bool row_ok = rl < nrows;
       const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
       LaneAcc<T> acc[2];
-      T carry = T(0);
       // groups per lane in a row: a compile-time count (NI > 0) lets the
       // compiler issue the loads of all of them before the first is used
       const int niter = NI > 0 ? NI : it.niter;
@@ -321,25 +323,18 @@ __global__ void __maxnreg__(REGS) k_pass_b(Ctx c, int which, void* xfield, CondA
         const int g = itn * it.lpr + it.sl;
         const bool gok = row_ok && g < gpr;
         const long long e = geo.base + 4LL * g;
-        const bool last_lane = it.sl == it.lpr - 1 && gok && g + 1 < gpr;
-        // issue every load of this group
+        // issue every load of this group (A p comes from pass A)
         const V4<T> P = ld4_if(pp + e, gok);
-        const V4<T> ym = ld4_if(pp + e - geo.sy, gok && geo.ym);
-        const V4<T> yp = ld4_if(pp + e + geo.sy, gok && geo.yp);
-        const V4<T> zm = ld4_if(pp + e - geo.sz, gok && geo.zm);
-        const V4<T> zp = ld4_if(pp + e + geo.sz, gok && geo.zp);
-        const V4<T> D = ld4_if(dd + e, gok);
+        const V4<T> Q = ld4_if(qq + e, gok);
+        const V4<T> D = mg ? zero4<T>() : ld4_if(dd + e, gok);
         V4<T> X = ld4_if(xx + e, gok);
         V4<T> Z = ld4_if(zz + e, gok);
-        const T pr = last_lane ? pp[e + 4] : T(0);
-        T left, right;
-        x_neighbours(P, g, gpr, it.sl, it.lpr, gok, carry, left, right, [&] { return pr; });
         if (gok) {
           T g_rho = 0, g_rr = 0;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             if (4 * g + k < nx) {
-              const T q = D.a[k] * P.a[k] - cpl * nb_sum(P, k, left, right, ym, yp, zm, zp);
+              const T q = Q.a[k];
               X.a[k] += alpha * P.a[k];
               if (mg) {
                 Z.a[k] -= alpha * q;
