@@ -1184,13 +1184,35 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
       }
       H.nrowitems = rowstart[n];
       H.launches = hca::vcycle_launches(H, false);
+      // row-vector coarse kernels: level l qualifies when the level's rows of
+      // every replicate that runs it on the grid (l below its single-block
+      // levels) are whole 4-site groups; item prefix tables per level
+      // (HCA_MG_GENERIC=1 keeps the per-site form)
+      std::vector<long long> post_pre((size_t)hca::MG_MAXLEV * (n + 1), 0), restr_pre(post_pre.size(), 0);
       {
-        // row-vector coarse kernels for a single replicate whose level rows
-        // are whole 4-site groups (HCA_MG_GENERIC=1 keeps the per-site form)
         const char* gen = std::getenv("HCA_MG_GENERIC");
-        if (n == 1 && !(gen && gen[0] == '1'))
-          for (int l = 1; l < rep[0].x; ++l)
-            if (lv[l].nx % 4 == 0) H.rows_ok |= 1u << l;
+        const bool allow = !(gen && gen[0] == '1');
+        for (int l = 1; l < H.small && allow; ++l) {
+          bool ok = true;
+          long long pp = 0, rp = 0;
+          for (int i = 0; i < n; ++i) {
+            post_pre[(size_t)l * (n + 1) + i] = pp;
+            restr_pre[(size_t)l * (n + 1) + i] = rp;
+            if (l >= rep[i].y) continue;   // this replicate runs level l in the single-block kernel
+            const hca::MGLevel& F = lv[(size_t)i * hca::MG_MAXLEV + l];
+            const hca::MGLevel& C = lv[(size_t)i * hca::MG_MAXLEV + l + 1];
+            if (F.nx % 4 != 0) ok = false;
+            pp += (long long)F.ny * F.nz * (F.nx / 4);
+            rp += (long long)C.ny * C.nz * (F.nx / 4);
+          }
+          post_pre[(size_t)l * (n + 1) + n] = pp;
+          restr_pre[(size_t)l * (n + 1) + n] = rp;
+          if (ok) {
+            H.rows_ok |= 1u << l;
+            H.post_items[l] = pp;
+            H.restr_items[l] = rp;
+          }
+        }
       }
       ALLOC(c.r, fbytes);
       ALLOC(c.mg_t0, fbytes);
@@ -1217,6 +1239,20 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
       c.mg_start = start_d;
       c.mg_rep = rep_d;
       c.mg_rowstart = rowstart_d;
+      {
+        long long* pre_d;
+        ALLOC(pre_d, sizeof(long long) * 2 * post_pre.size());
+        if (cudaMemcpyAsync(pre_d, post_pre.data(), sizeof(long long) * post_pre.size(), cudaMemcpyHostToDevice,
+                            c.stream) ||
+            cudaMemcpyAsync(pre_d + post_pre.size(), restr_pre.data(), sizeof(long long) * restr_pre.size(),
+                            cudaMemcpyHostToDevice, c.stream) ||
+            cudaStreamSynchronize(c.stream)) {
+          rc = HCA_ERR_CUDA;
+          goto fail;
+        }
+        c.mg_post_items = pre_d;
+        c.mg_restr_items = pre_d + post_pre.size();
+      }
       c.mg = 1;
     }
     if (h->learned) {

@@ -272,7 +272,9 @@ struct MGHost {
   long long nrowitems = 0;         // (level-1 row, lattice 4-site group) items over the replicates
   int launches = 0;              // kernels per V-cycle
   int ni = 0;                    // groups per lane in a row of the lattice (1, 2, 4; 0 = other)
-  unsigned rows_ok = 0;          // bit l: level l's rows are whole 4-site groups (single replicate)
+  unsigned rows_ok = 0;          // bit l: every replicate's level-l rows are whole 4-site groups
+  long long post_items[MG_MAXLEV] = {};   // row-kernel items per level over the replicates
+  long long restr_items[MG_MAXLEV] = {};
 };
 
 struct Ctx {
@@ -305,6 +307,10 @@ struct Ctx {
   const long long* mg_start;  // [MG_MAXLEV][n_reps + 1] prefix sums of each level's sites over the replicates
   const int2* mg_rep;         // per replicate: (levels, first single-block level)
   const long long* mg_rowstart;  // [n_reps + 1] prefix of level-1 rows x lattice groups per row
+  // row-vector coarse kernels: [MG_MAXLEV][n_reps + 1] prefix sums of the items
+  // (4-site groups) of the post-sweep on level l and of the restriction l -> l + 1
+  const long long* mg_post_items;
+  const long long* mg_restr_items;
   void* reac;    // FP32 scheme: reaction part a of the diagonal d = c n + a
   void* phi;
   void* P;

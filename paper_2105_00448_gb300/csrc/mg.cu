@@ -371,20 +371,43 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_post(Ctx c, int which, int l)
   }
 }
 
-// Post-smoothing on coarse level l >= 1 of a single replicate in row-vector
-// form (the level's rows a whole number of 4-site groups): one thread per
-// group; every load of the group (rhs and omega/d of its row and the four
+// Replicate owning item q of a prefix table (the last r with pre[r] <= q).
+__device__ __forceinline__ int rep_of_items(const long long* pre, int n, long long q) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pre[mid] <= q) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Post-smoothing on coarse level l >= 1 in row-vector form (every
+// replicate's level rows a whole number of 4-site groups; items of a batch
+// found through the level's prefix table): one thread per group; every load of the group (rhs and omega/d of its row and the four
 // neighbour rows, the sites left and right of it, d, the level-(l+1)
 // correction under each row) is issued before u = (omega/d) rhs + P x_C is
 // formed.  The same arithmetic, in the same order, as post_fused_at.
 template <typename T>
 __global__ void __launch_bounds__(kMgThreads) k_mg_post_rows(Ctx c, int which, int l) {
   HCA_COUNT_KERNEL(c);
-  const View<T> F = view<T>(c, which, 0, l), C = view<T>(c, which, 0, l + 1);
-  const int gpr = F.nx >> 2;
-  const long long items = (long long)F.ny * F.nz * gpr;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < items;
-       q += (long long)gridDim.x * blockDim.x) {
+  const long long* pre = c.mg_post_items + (long long)l * (c.n_reps + 1);
+  const long long items = pre[c.n_reps];
+  int r = -1;
+  long long lo = 0, hi = 0;
+  View<T> F, C;
+  int gpr = 1;
+  for (long long qq = blockIdx.x * (long long)blockDim.x + threadIdx.x; qq < items;
+       qq += (long long)gridDim.x * blockDim.x) {
+    if (qq < lo || qq >= hi) {   // the replicate changes rarely along a thread's items
+      r = rep_of_items(pre, c.n_reps, qq);
+      lo = pre[r];
+      hi = pre[r + 1];
+      F = view<T>(c, which, r, l);
+      C = view<T>(c, which, r, l + 1);
+      gpr = F.nx >> 2;
+    }
+    const long long q = qq - lo;
     const int j = (int)(q % gpr);
     const long long R = q / gpr;
     const int Y = (int)(R % F.ny), Z = (int)(R / F.ny);
@@ -433,8 +456,8 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_post_rows(Ctx c, int which, i
   }
 }
 
-// Restriction from coarse level l >= 1 to l + 1 of a single replicate in
-// row-vector form (level l's rows whole 4-site groups): one thread per group
+// Restriction from coarse level l >= 1 to l + 1 in row-vector form (every
+// replicate's level-l rows whole 4-site groups; batches as in k_mg_post_rows): one thread per group
 // of the four fine rows (2Y + dy, 2Z + dz) under coarse row (Y, Z), producing
 // coarse sites 2j, 2j + 1; all loads (rhs and omega/d of the 4 own and 8 outer
 // rows, d, the x neighbours) are issued before u = (omega/d) rhs is formed.
@@ -442,11 +465,23 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_post_rows(Ctx c, int which, i
 template <typename T>
 __global__ void __launch_bounds__(128) k_mg_restrict_rows(Ctx c, int which, int l) {
   HCA_COUNT_KERNEL(c);
-  const View<T> F = view<T>(c, which, 0, l), C = view<T>(c, which, 0, l + 1);
-  const int gpr = F.nx >> 2;
-  const long long items = (long long)C.ny * C.nz * gpr;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < items;
-       q += (long long)gridDim.x * blockDim.x) {
+  const long long* pre = c.mg_restr_items + (long long)l * (c.n_reps + 1);
+  const long long items = pre[c.n_reps];
+  int r = -1;
+  long long lo = 0, hi = 0;
+  View<T> F, C;
+  int gpr = 1;
+  for (long long qq = blockIdx.x * (long long)blockDim.x + threadIdx.x; qq < items;
+       qq += (long long)gridDim.x * blockDim.x) {
+    if (qq < lo || qq >= hi) {
+      r = rep_of_items(pre, c.n_reps, qq);
+      lo = pre[r];
+      hi = pre[r + 1];
+      F = view<T>(c, which, r, l);
+      C = view<T>(c, which, r, l + 1);
+      gpr = F.nx >> 2;
+    }
+    const long long q = qq - lo;
     const int j = (int)(q % gpr);
     const long long R = q / gpr;
     const int Y = (int)(R % C.ny), Z = (int)(R / C.ny);
@@ -849,15 +884,15 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
   }
   if (all || part == 1) {
     for (int l = 1; l < H.small; ++l) {
-      if (multi) k_mg_restrict<T, true><<<grid_for(H.ntot[l + 1]), kMgThreads, 0, s>>>(c, which, l);
-      else if (H.rows_ok >> l & 1u)   // 128 threads: ~28 vector loads per thread in flight
-        k_mg_restrict_rows<T><<<(int)std::min((H.ntot[l + 1] / 2 + 127) / 128, 152LL * 16), 128, 0, s>>>(c, which, l);
+      if (H.rows_ok >> l & 1u)   // 128 threads: ~28 vector loads per thread in flight
+        k_mg_restrict_rows<T><<<(int)std::min((H.restr_items[l] + 127) / 128, 152LL * 16), 128, 0, s>>>(c, which, l);
+      else if (multi) k_mg_restrict<T, true><<<grid_for(H.ntot[l + 1]), kMgThreads, 0, s>>>(c, which, l);
       else k_mg_restrict<T, false><<<grid_for(H.ntot[l + 1]), kMgThreads, 0, s>>>(c, which, l);
     }
     k_mg_small<T><<<c.n_reps, kSmallThreads, 0, s>>>(c, which);
     for (int l = H.small - 1; l >= 1; --l) {
-      if (multi) k_mg_post<T, true><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
-      else if (H.rows_ok >> l & 1u) k_mg_post_rows<T><<<grid_for(H.ntot[l] / 4), kMgThreads, 0, s>>>(c, which, l);
+      if (H.rows_ok >> l & 1u) k_mg_post_rows<T><<<grid_for(H.post_items[l]), kMgThreads, 0, s>>>(c, which, l);
+      else if (multi) k_mg_post<T, true><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
       else k_mg_post<T, false><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
     }
   }

@@ -21,6 +21,7 @@ from oracle import params as Pm
 from oracle import stencil as S
 from oracle.model import plasma_levels
 from paper_2105_00448_gb300 import hca
+from synth import make_maps
 
 pytestmark = pytest.mark.gpu
 
@@ -220,3 +221,25 @@ def test_row_coarse_kernels_are_bit_identical(shape, precision, monkeypatch):
     (s0, K0, G0, st0), (s1, K1, G1, st1) = out
     assert np.array_equal(s0, s1) and np.array_equal(K0, K1) and np.array_equal(G0, G1)
     assert (st0["o2_iterations"], st0["drug_iterations"]) == (st1["o2_iterations"], st1["drug_iterations"])
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_row_coarse_kernels_batch_bit_identical(precision, monkeypatch):
+    """Batches (replicates of several sizes, item prefix tables per level)
+    give the per-site coarse kernels' bits too."""
+    res = []
+    for generic in ("1", "0"):
+        monkeypatch.setenv("HCA_MG_GENERIC", generic)
+        cfgs, maps = [], []
+        for r, n in enumerate((48, 40, 64)):
+            m = make_maps(n, n, n, corr_len=3.0, seed=80 + r)
+            maps.append((m.p_cell, m.perf, m.p_vessel))
+            cfgs.append(hca.make_config(n, n, n, precision=precision, seed=80 + r, n_drugs=1,
+                                        preconditioner=hca.HCA_PC_MG))
+        b = hca.Sim(cfgs, maps, batch=True)
+        b.step(2)
+        res.append([(b.states(r), b.field(hca.FIELD_O2, r), b.field(hca.FIELD_DRUG0, r)) for r in range(3)])
+        b.close()
+    for x, y in zip(*res):
+        for a, c in zip(x, y):
+            assert np.array_equal(a, c)
