@@ -46,8 +46,8 @@ CORR_LEN = 8.0
 #   multigrid on the lattice: the first sweep + restriction reads r, omega/d, d and writes the
 #   1/8-size coarse right-hand side; the prolongation + last sweep reads r, omega/d, d and the
 #   1/8-size coarse correction and writes z; ODE reads state, K and updates phi, P, Vc
-BYTES_PER_SITE = {"pass_a": 20, "pass_b": 24, "setup": 17, "residual": 32, "ode": 29,
-                  "mg_restrict0": 12.5, "mg_post0": 16.5}
+BYTES_PER_SITE = {"pass_a": 20, "pass_b": 24, "setup": 17, "residual": 24, "ode": 29,
+                  "mg_restrict0": 16.5, "mg_post0": 16.5}
 
 
 def workload_config():
@@ -291,7 +291,7 @@ def run_gpu(args):
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
     tr = traffic_record(dom)
     kernel_names = {"pass_a": "k_pass_a<float>", "pass_b": "k_pass_b<float>", "setup": "k_setup<float>",
-                    "residual": "k_dc_residual", "ode": "k_ode<float>", "mg_restrict0": "k_mg_restrict<float> (level 0)",
+                    "residual": "k_dc_residual", "ode": "k_ode<float>", "mg_restrict0": "k_mg_restrict0_rows<float>",
                     "mg_post0": "k_mg_post0<float, true>"}
     roofline = {"bound": "hbm", "kernel": kernel_names[dom], "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,

@@ -566,10 +566,13 @@ __global__ void __launch_bounds__(128) k_mg_restrict_rows(Ctx c, int which, int 
 // producing coarse sites X = 2j, 2j+1.  Every load of the item (the four own
 // rows, their eight outer neighbour rows, the x neighbours at the group's
 // ends) is issued before u = (omega/d) r is formed, so an item costs one
-// memory round trip.  Same arithmetic as restrict_fused_at.
+// memory round trip.  Same arithmetic as restrict_fused_at.  The kernel also
+// stores the pre-smoothed iterate after its residual correction,
+// v = u + (omega/d)(r - A u), into mg_t0 for the post-smoothing kernel.
 template <typename T>
 __global__ void __launch_bounds__(128) k_mg_restrict0_rows(Ctx c, int which) {
   HCA_COUNT_KERNEL(c);
+  T* __restrict__ vv = (T*)c.mg_t0;
   const T* __restrict__ rr = (const T*)c.r;
   const T* __restrict__ ww = (const T*)c.mg_w;
   const T* __restrict__ dd = (const T*)c.d;
@@ -648,6 +651,9 @@ __global__ void __launch_bounds__(128) k_mg_restrict0_rows(Ctx c, int which) {
 #pragma unroll
       for (int e = 0; e < 4; ++e) U[t].a[e] = (x0 + e < rd.nx) ? WV[t].a[e] * RV[t].a[e] : T(0);
     T acc0 = T(0), acc1 = T(0);
+    V4<T> VO[4];   // v = u + (omega/d)(r - A u), zero on padding
+#pragma unroll
+    for (int t = 0; t < 4; ++t) VO[t] = zero4<T>();
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -669,8 +675,12 @@ __global__ void __launch_bounds__(128) k_mg_restrict0_rows(Ctx c, int which) {
           const T res = RV[t].a[e] - (DV[t].a[e] * U[t].a[e] - cpl * nb);
           if (e < 2) acc0 += res;
           else acc1 += res;
+          VO[t].a[e] = fma(WV[t].a[e], res, U[t].a[e]);
         }
       }
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (ok[t]) st4(vv + eb + off[t], VO[t]);
     T* rhs1 = (T*)L1.rhs;
     const long long cb = ((long long)Z * L1.ny + Y) * L1.nx + 2 * j;
     if (2 * j < L1.nx) rhs1[cb] = acc0;
@@ -719,11 +729,17 @@ __global__ void __launch_bounds__(kSmallThreads) k_mg_small(Ctx c, int which) {
 }
 
 // ------------------------------------------ level-0 post-smoothing + rho --
-// z = u + omega (r - A u) / d over the chunk's rows, with u = omega r / d +
-// P x_1 (PROLONG: the first sweep and the coarse correction evaluated where
-// they are needed) or u = src (the lattice is the coarsest level);
-// rho = r.z (fixed-order sums); beta = rho / rho_old (0 on the first
-// application of a solve).
+// z = u + omega (r - A u) / d over the chunk's rows, then rho = r.z
+// (fixed-order sums) and beta = rho / rho_old (0 on the first application of
+// a solve).
+//
+// PROLONG: u = u0 + p with u0 = omega r / d the first sweep and p = P x_1 the
+// coarse correction.  With v = u0 + omega (r - A u0) / d, stored by the
+// restriction kernel, and (omega / d) d = omega,
+//   z = v + p - (omega / d) A p = v + (1 - omega) p + (omega / d) c sum_nb p,
+// so the kernel streams v, r and omega/d and reads p from the coarse level
+// (piecewise constant: three of a site's neighbours share its coarse cell).
+// Otherwise the lattice is the coarsest level and u = src.
 template <typename T, bool PROLONG, int NI>
 __global__ void __maxnreg__(96) k_mg_post0(Ctx c, int which, const T* __restrict__ src) {
   HCA_COUNT_KERNEL(c);
@@ -733,6 +749,7 @@ __global__ void __maxnreg__(96) k_mg_post0(Ctx c, int which, const T* __restrict
   const T* __restrict__ rr = (const T*)c.r;
   const T* __restrict__ dd = (const T*)c.d;
   const T* __restrict__ ww = (const T*)c.mg_w;
+  const T* __restrict__ vv = (const T*)c.mg_t0;
   T* __restrict__ zz = (T*)c.z;
   const T cpl = (T)op_coupling(rd, which);
   const T* __restrict__ x1 = nullptr;
@@ -751,83 +768,91 @@ __global__ void __maxnreg__(96) k_mg_post0(Ctx c, int which, const T* __restrict
     const RowGeo geo = row_geo(rd, j);
     const int y = j % rd.ny, z = j / rd.ny;
     LaneAcc<T> acc[1];
-    T carry = T(0);
     // groups per lane in a row: a compile-time count (NI > 0) lets the
     // compiler issue the loads of all of them before the first is used
     const int niter = NI > 0 ? NI : it.niter;
+    if (PROLONG) {
+      // coarse rows of the site row and of its y and z neighbours outside
+      // its coarse cell; in-cell neighbours (one along y, one along z, where
+      // inside the lattice) carry the site's own p
+      const int yo = (y & 1) ? y + 1 : y - 1, zo = (z & 1) ? z + 1 : z - 1;
+      const bool yout = yo >= 0 && yo < rd.ny, zout = zo >= 0 && zo < rd.nz;
+      const T nin = (T)(int)(((y & 1) || y + 1 < rd.ny) + ((z & 1) || z + 1 < rd.nz));
+      const long long cown = ((long long)(z >> 1) * ny1 + (y >> 1)) * nx1;
+      const long long cy = yout ? ((long long)(z >> 1) * ny1 + (yo >> 1)) * nx1 : cown;
+      const long long cz = zout ? ((long long)(zo >> 1) * ny1 + (y >> 1)) * nx1 : cown;
 #pragma unroll
-    for (int itn = 0; itn < niter; ++itn) {
-      const int g = itn * it.lpr + it.sl;
-      const bool gok = row_ok && g < rd.gpr;
-      const long long e = geo.base + 4LL * g;
-      // u on the group and on the same group of the four neighbour rows.  All
-      // loads of the group are issued (predicated) before any value is used,
-      // so a group costs one memory round trip
-      const bool rok[5] = {gok, gok && geo.ym, gok && geo.yp, gok && geo.zm, gok && geo.zp};
-      const long long roff[5] = {0, -geo.sy, geo.sy, -geo.sz, geo.sz};
-      const int ry[5] = {y, y - 1, y + 1, y, y};
-      const int rz[5] = {z, z, z, z - 1, z + 1};
-      V4<T> RR[5], WW[5];
-      T C0[5], C1[5];
+      for (int itn = 0; itn < niter; ++itn) {
+        const int g = itn * it.lpr + it.sl;
+        const bool gok = row_ok && g < rd.gpr;
+        const long long e = geo.base + 4LL * g;
+        const bool two = 4 * g + 2 < rd.nx;   // the group reaches coarse cell 2g + 1
+        const V4<T> V = ld4_if(vv + e, gok);
+        const V4<T> R = ld4_if(rr + e, gok);
+        const V4<T> W = ld4_if(ww + e, gok);
+        const T C0 = gok ? x1[cown + 2 * g] : T(0);
+        const T C1 = gok && two ? x1[cown + 2 * g + 1] : T(0);
+        const T Cl = gok && g > 0 ? x1[cown + 2 * g - 1] : T(0);
+        const T Cr = gok && 4 * g + 4 < rd.nx ? x1[cown + 2 * g + 2] : T(0);
+        const T Y0 = gok && yout ? x1[cy + 2 * g] : T(0);
+        const T Y1 = gok && yout && two ? x1[cy + 2 * g + 1] : T(0);
+        const T Z0 = gok && zout ? x1[cz + 2 * g] : T(0);
+        const T Z1 = gok && zout && two ? x1[cz + 2 * g + 1] : T(0);
+        if (gok) {
+          V4<T> Zo;
+          T rz = T(0);
 #pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        if (PROLONG) {
-          RR[q] = ld4_if(rr + e + roff[q], rok[q]);
-          WW[q] = ld4_if(ww + e + roff[q], rok[q]);
-          const long long cb = rok[q] ? ((long long)(rz[q] >> 1) * ny1 + (ry[q] >> 1)) * nx1 + 2LL * g : 0;
-          C0[q] = rok[q] ? x1[cb] : T(0);
-          C1[q] = (rok[q] && 4 * g + 2 < rd.nx) ? x1[cb + 1] : T(0);
-        } else {
-          RR[q] = ld4_if(src + e + roff[q], rok[q]);
-        }
-      }
-      const V4<T> D = ld4_if(dd + e, gok);
-      // u at the site after the group, for the segment's last lane
-      const bool last_lane = it.sl == it.lpr - 1 && gok && g + 1 < rd.gpr;
-      T un = T(0);
-      if (PROLONG) {
-        const T wn = last_lane ? ww[e + 4] : T(0);
-        const T rn = last_lane ? rr[e + 4] : T(0);
-        const T cn = last_lane ? x1[((long long)(z >> 1) * ny1 + (y >> 1)) * nx1 + 2LL * g + 2] : T(0);
-        un = wn != T(0) ? wn * rn + cn : T(0);
-      } else {
-        un = last_lane ? src[e + 4] : T(0);
-      }
-      V4<T> UU[5];
-#pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        if (PROLONG) {
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            UU[q].a[k] = (4 * g + k < rd.nx && WW[q].a[k] != T(0)) ? WW[q].a[k] * RR[q].a[k] + (k < 2 ? C0[q] : C1[q])
-                                                                    : T(0);
-        } else {
-          UU[q] = RR[q];
-        }
-      }
-      const V4<T>& U = UU[0];
-      const V4<T>& ym = UU[1];
-      const V4<T>& yp = UU[2];
-      const V4<T>& zm = UU[3];
-      const V4<T>& zp = UU[4];
-      const V4<T> R = PROLONG ? RR[0] : ld4_if(rr + e, gok);
-      const V4<T> W = PROLONG ? WW[0] : ld4_if(ww + e, gok);
-      T left, right;
-      x_neighbours(U, g, rd.gpr, it.sl, it.lpr, gok, carry, left, right, [&] { return un; });
-      if (gok) {
-        V4<T> Zo;
-        T rz = T(0);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          Zo.a[k] = T(0);
-          if (4 * g + k < rd.nx && D.a[k] != T(0)) {
-            const T q = D.a[k] * U.a[k] - cpl * nb_sum(U, k, left, right, ym, yp, zm, zp);
-            Zo.a[k] = U.a[k] + W.a[k] * (R.a[k] - q);
-            rz += R.a[k] * Zo.a[k];
+          for (int k = 0; k < 4; ++k) {
+            Zo.a[k] = T(0);
+            const int x = 4 * g + k;
+            if (x < rd.nx && W.a[k] != T(0)) {
+              const T p = k < 2 ? C0 : C1;
+              const T pl = x > 0 ? (k == 0 ? Cl : k < 3 ? C0 : C1) : T(0);
+              const T pr = x < rd.nx - 1 ? (k == 3 ? Cr : k == 0 ? C0 : C1) : T(0);
+              const T nb = ((pl + pr) + nin * p) + ((k < 2 ? Y0 : Y1) + (k < 2 ? Z0 : Z1));
+              Zo.a[k] = fma(W.a[k], cpl * nb, fma((T)(1.0 - MG_OMEGA), p, V.a[k]));
+              rz += R.a[k] * Zo.a[k];
+            }
           }
+          st4(zz + e, Zo);
+          acc[0].add(rz);   // float-float lane sums for FP32 (r is scaled to O(1))
         }
-        st4(zz + e, Zo);
-        acc[0].add(rz);   // float-float lane sums for FP32 (r is scaled to O(1))
+      }
+    } else {
+      T carry = T(0);
+#pragma unroll
+      for (int itn = 0; itn < niter; ++itn) {
+        const int g = itn * it.lpr + it.sl;
+        const bool gok = row_ok && g < rd.gpr;
+        const long long e = geo.base + 4LL * g;
+        const bool rok[5] = {gok, gok && geo.ym, gok && geo.yp, gok && geo.zm, gok && geo.zp};
+        const long long roff[5] = {0, -geo.sy, geo.sy, -geo.sz, geo.sz};
+        V4<T> UU[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) UU[q] = ld4_if(src + e + roff[q], rok[q]);
+        const V4<T> D = ld4_if(dd + e, gok);
+        const V4<T> R = ld4_if(rr + e, gok);
+        const V4<T> W = ld4_if(ww + e, gok);
+        const bool last_lane = it.sl == it.lpr - 1 && gok && g + 1 < rd.gpr;
+        const T un = last_lane ? src[e + 4] : T(0);
+        const V4<T>& U = UU[0];
+        T left, right;
+        x_neighbours(U, g, rd.gpr, it.sl, it.lpr, gok, carry, left, right, [&] { return un; });
+        if (gok) {
+          V4<T> Zo;
+          T rz = T(0);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            Zo.a[k] = T(0);
+            if (4 * g + k < rd.nx && D.a[k] != T(0)) {
+              const T q = D.a[k] * U.a[k] - cpl * nb_sum(U, k, left, right, UU[1], UU[2], UU[3], UU[4]);
+              Zo.a[k] = U.a[k] + W.a[k] * (R.a[k] - q);
+              rz += R.a[k] * Zo.a[k];
+            }
+          }
+          st4(zz + e, Zo);
+          acc[0].add(rz);
+        }
       }
     }
     store_rows_acc(c, blockIdx.x, rl, row_ok, it.sl, it.lpr, acc, 1);

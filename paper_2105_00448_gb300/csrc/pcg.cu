@@ -599,18 +599,22 @@ struct ScaledAcc {
 // c n ~ 600 for a drug).  It stops the solve when |r| <= rtol |b| (FP64 norms)
 // and otherwise starts an FP32 inner CG on the correction, A32 dx = fl32(r),
 // dx0 = 0, to the inner tolerance, where A32 uses the FP32 diagonal.  The first
-// sweep of a solve also builds and stores a, d (and b for a drug).
-template <int KIND>
+// sweep of a solve (FIRST) also builds and stores a, d (and b for a drug).
+// With the multigrid preconditioner (MG) the kernel stores r for the V-cycle,
+// which forms z itself; otherwise it stores the Jacobi z = r / d and sums r.z.
+// Per site the arithmetic is FP32 and float-float (FP64 runs at a small
+// fraction of the FP32 rate on this GPU).
+template <int KIND, bool FIRST, bool MG>
 __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const float* __restrict__ x_hi,
-                                                     const float* __restrict__ x_lo, int first, CondArg outer,
+                                                     const float* __restrict__ x_lo, CondArg outer,
                                                      CondArg inner) {
   HCA_COUNT_KERNEL(c);
   __shared__ double s_G0;
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
   const RepSolve sv = c.solve[ch.x];
-  const bool live = first || sv.active || sv.dc_apply;
-  if (KIND == 1 && first) {
+  const bool live = FIRST || sv.active || sv.dc_apply;
+  if (KIND == 1 && FIRST) {
     if (threadIdx.x == 0) s_G0 = substep_plasma(rd, which, *c.step, c.sub);
     __syncthreads();
   }
@@ -623,10 +627,12 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
     float* __restrict__ dxv = (float*)c.dx;
     const float* __restrict__ perf = (const float*)c.perf;
     const double cpl = (double)(float)op_coupling(rd, which);
-    const float G0 = KIND == 1 && first ? (float)s_G0 : 0.f;
+    const float G0 = KIND == 1 && FIRST ? (float)s_G0 : 0.f;
     const bool bax = rd.bax[which] != 0;
     const bool o2t = KIND == 0 && rd.bx[0] != 0.0;
     const double bx = rd.bx[which];
+    // bx as an unevaluated float pair (b = bx x0 + ... is formed to ~48 bits)
+    const float bx_hi = (float)bx, bx_lo = (float)(bx - (double)bx_hi);
     const float bvessel = (float)(bax ? 2.0 * rd.r_K * rd.K0 : rd.r_K * rd.K0);
     const RowIter it = row_iter(rd);
     const float cpl32 = (float)cpl;
@@ -656,12 +662,12 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
         V4<float> D = zero4<float>(), B = zero4<float>(), AR = zero4<float>(), SRC = zero4<float>();
         V4<float> PF = zero4<float>(), VC = zero4<float>();
         uchar4 st = make_uchar4(0, 0, 0, 0);
-        if (gok && first) {
+        if (gok && FIRST) {
           st = ld_state4(c.state + e);
           if (KIND == 1) PF = ld4(perf + e);
           if (vegf) VC = ld4((const float*)c.Vc + e);
         } else if (gok) {
-          D = ld4(dd + e);
+          if (!MG) D = ld4(dd + e);
           AR = ld4(aa + e);
           B = ld4(bb + e);
         }
@@ -669,7 +675,7 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
         x_neighbours(Xh, g, rd.gpr, it.sl, it.lpr, gok, carry_h, lh, rh, [&] { return rnh; });
         x_neighbours(Xl, g, rd.gpr, it.sl, it.lpr, gok, carry_l, ll, rlo, [&] { return rnl; });
         if (gok) {
-          if (first) {
+          if (FIRST) {
             const float av = (float)(bax ? 2.0 * rd.a_vegf : rd.a_vegf);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -680,19 +686,21 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
               AR.a[k] = 0.f;
               SRC.a[k] = 0.f;
               if (xk < rd.nx) {
-                const double xk64 = (double)Xh.a[k] + (double)Xl.a[k];
-                const float xk32 = (float)xk64;
+                // x0 bx to ~48 bits, rounded once; x0 rounded to FP32
+                const FF xbx = ff_mul(FF{Xh.a[k], Xl.a[k]}, FF{bx_hi, bx_lo});
+                const float xb32 = __fadd_rn(xbx.hi, xbx.lo);
+                const float xk32 = __fadd_rn(Xh.a[k], Xl.a[k]);
                 // the operator is linearised about K_prev: the start field, or c.lag when the solve starts from another guess
                 const float lag = (KIND == 0 && c.lag) ? ((const float*)c.lag)[e + k] : xk32;
                 AR.a[k] = reaction_site<float, KIND>(rd, which, s, lag, PF.a[k]);
                 D.a[k] = cpl32 * (float)neighbour_count(rd, geo, xk) + AR.a[k];
                 if (KIND == 0) {
                   SRC.a[k] = is_vessel(s) ? bvessel : 0.f;
-                  B.a[k] = SRC.a[k] + (o2t ? (float)(xk64 * bx) : 0.f);
+                  B.a[k] = SRC.a[k] + (o2t ? xb32 : 0.f);
                 } else {
                   if (vegf) SRC.a[k] = is_consumer(s) ? av * VC.a[k] : 0.f;
                   else SRC.a[k] = is_vessel(s) ? (float)rd.kappa[which - 1] * PF.a[k] * G0 : 0.f;
-                  B.a[k] = (float)(xk64 * bx) + SRC.a[k];
+                  B.a[k] = xb32 + SRC.a[k];
                 }
               }
             }
@@ -715,15 +723,17 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
               const FF d = ff_add(ff_two_prod(cpl32, (float)neighbour_count(rd, geo, 4 * g + k)), AR.a[k]);
               const FF t = ff_add(ff_mul(d, xv), ff_neg(ff_mul(nb, cpl32)));
               // Crank-Nicolson: b = (4/h) x0 - A x0 + source, formed once from the start field
-              if (first && bax)
-                B.a[k] = (float)(((double)xv.hi + (double)xv.lo) * bx + (double)SRC.a[k] - ((double)t.hi + (double)t.lo));
+              if (FIRST && bax) {
+                const FF bf = ff_add(ff_add(ff_mul(xv, FF{bx_hi, bx_lo}), SRC.a[k]), ff_neg(t));
+                B.a[k] = __fadd_rn(bf.hi, bf.lo);
+              }
               const FF rf = ff_add(ff_neg(t), B.a[k]);
               const float r32 = __fadd_rn(rf.hi, rf.lo);
-              Z.a[k] = D.a[k] != 0.f ? r32 / D.a[k] : 0.f;
+              if (!MG) Z.a[k] = D.a[k] != 0.f ? r32 / D.a[k] : 0.f;
               R32.a[k] = r32;
             }
           }
-          if (first) st4(bb + e, B);
+          if (FIRST) st4(bb + e, B);
           // the group's |r|^2, r.z and |b|^2: each 4-term sum is taken in
           // FP32 after an exact power-of-two scaling by the group's largest
           // magnitude (a decayed field's residual, ~1e-22, would underflow
@@ -745,8 +755,8 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
             acc.add(s2, 2 * ex);
           };
           scaled_sum(R32, la[0]);
-          if (first) scaled_sum(B, la[1]);
-          if (!c.mg) {
+          if (FIRST) scaled_sum(B, la[1]);
+          if (!MG) {
             // r.z with z = r / d: scale r and z by the same power (|z| may be
             // far from |r|, so each is scaled by its own group maximum)
             float mr = 0.f, mz = 0.f;
@@ -763,8 +773,8 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
               la[2].add(s, er + ez);
             }
           }
-          st4(zz + e, Z);
-          if (c.mg) st4((float*)c.r + e, R32);
+          if (MG) st4((float*)c.r + e, R32);
+          else st4(zz + e, Z);
           st4(dxv + e, zero4<float>());
         }
       }
@@ -779,7 +789,7 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
                    const RepDesc& rr = c.reps[r];
                    RepSolve& s = c.solve[r];
                    DevStats& st = c.stats[r];
-                   if (first) {
+                   if (FIRST) {
                      s.outer = 0;
                      s.zero_b = 0;
                      s.dc_apply = 0;
@@ -792,7 +802,7 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
                    st.iters[which] += s.iters;
                    st.sweeps[which] += 1;
                    // |b|^2 is summed on the first sweep only (b does not change)
-                   if (first) s.bb_outer = s3[1];
+                   if (FIRST) s.bb_outer = s3[1];
                    const double bb = s.bb_outer;
                    if (!isfinite(s3[0]) || !isfinite(bb) || !isfinite(s3[2])) {
                      c.sync->error = 1;
@@ -846,13 +856,13 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
                    s.beta = 0.0;
                    s.dc_apply = 1;
                    // the multigrid form leaves rho to the V-cycle (s3[2] = 0)
-                   s.active = (c.mg ? s3[0] > 0.0 : s3[2] > 0.0) ? 1 : 0;
+                   s.active = (MG ? s3[0] > 0.0 : s3[2] > 0.0) ? 1 : 0;
                    return s.active;
                  },
                  [&](int n_active) {
                    c.sync->parity = 0;
                    c.sync->guard = 0;
-                   const int g = first ? (c.sync->guard_outer = 0) : ++c.sync->guard_outer;
+                   const int g = FIRST ? (c.sync->guard_outer = 0) : ++c.sync->guard_outer;
                    bool go = n_active > 0;
                    if (go && g >= c.sync->guard_outer_limit) {
                      c.sync->error = 2;
@@ -906,14 +916,20 @@ __global__ void __launch_bounds__(512) k_dc_update(Ctx c, float* __restrict__ x_
 }  // namespace
 
 // ------------------------------------------------------------- launchers --
+template <int KIND>
+static void launch_dc_residual_t(const Ctx& c, int which, const float* x_hi, const float* x_lo, bool first,
+                                 CondArg outer, CondArg inner) {
+  const dim3 g(c.n_chunks), b(c.threads);
+  if (first && c.mg) k_dc_residual<KIND, true, true><<<g, b, 0, c.stream>>>(c, which, x_hi, x_lo, outer, inner);
+  else if (first) k_dc_residual<KIND, true, false><<<g, b, 0, c.stream>>>(c, which, x_hi, x_lo, outer, inner);
+  else if (c.mg) k_dc_residual<KIND, false, true><<<g, b, 0, c.stream>>>(c, which, x_hi, x_lo, outer, inner);
+  else k_dc_residual<KIND, false, false><<<g, b, 0, c.stream>>>(c, which, x_hi, x_lo, outer, inner);
+}
+
 void launch_dc_residual(const Ctx& c, int which, const void* x_hi, const void* x_lo, bool first, CondArg outer,
                         CondArg inner) {
-  if (which == 0)
-    k_dc_residual<0><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, (const float*)x_hi, (const float*)x_lo, first,
-                                                              outer, inner);
-  else
-    k_dc_residual<1><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, (const float*)x_hi, (const float*)x_lo, first,
-                                                              outer, inner);
+  if (which == 0) launch_dc_residual_t<0>(c, which, (const float*)x_hi, (const float*)x_lo, first, outer, inner);
+  else launch_dc_residual_t<1>(c, which, (const float*)x_hi, (const float*)x_lo, first, outer, inner);
 }
 
 void launch_dc_update(const Ctx& c, void* x_hi, void* x_lo) {
