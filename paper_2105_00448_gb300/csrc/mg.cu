@@ -741,7 +741,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_mg_small(Ctx c, int which) {
 // (piecewise constant: three of a site's neighbours share its coarse cell).
 // Otherwise the lattice is the coarsest level and u = src.
 template <typename T, bool PROLONG, int NI>
-__global__ void __maxnreg__(96) k_mg_post0(Ctx c, int which, const T* __restrict__ src) {
+__global__ void __maxnreg__(64) k_mg_post0(Ctx c, int which, const T* __restrict__ src) {
   HCA_COUNT_KERNEL(c);
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
