@@ -145,11 +145,24 @@ def traffic_record(kernel: str):
     return rec.get("dram_bytes_per_site")
 
 
-def kernel_source_sha() -> str:
+def code_lines(text: str):
+    """Source lines without // comments, trailing blanks and empty lines
+    (a fingerprint of the code that comment edits leave unchanged; no
+    string literal in these files holds //)."""
+    out = []
+    for line in text.splitlines():
+        code = line.split("//", 1)[0].rstrip()
+        if code:
+            out.append(code)
+    return out
+
+
+def kernel_source_sha(root: str = ROOT) -> str:
+    """Fingerprint of the hot kernels' code, matched against profiles/traffic.json."""
     h = hashlib.sha256()
     for name in ("hca_internal.cuh", "row_ops.cuh", "pcg.cu", "mg.cu"):
-        with open(os.path.join(ROOT, "paper_2105_00448_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(root, "paper_2105_00448_gb300", "csrc", name), encoding="utf-8") as f:
+            h.update("\n".join(code_lines(f.read())).encode())
     return h.hexdigest()[:16]
 
 

@@ -12,8 +12,10 @@
 // smoother is weighted Jacobi (one sweep before and one after the coarse
 // correction, MG_NU_COARSE sweeps on the coarsest level), so M is symmetric.
 //
-// Level 0 is the solver's padded field layout: rhs = r, iterate = mg_t0,
-// diagonal = d; coarser levels are dense arrays, the replicates of a batch
+// Level 0 is the solver's padded field layout: rhs = r, diagonal = d, and
+// mg_t0 the iterate when the lattice is the coarsest level, else the
+// pre-smoothed iterate v that the restriction kernel leaves for the
+// post-smoothing kernel; coarser levels are dense arrays, the replicates of a batch
 // concatenated per level (each replicate has its own hierarchy; a per-level
 // prefix table maps a flattened site index to its replicate).  Levels of at
 // most MG_SMALL_SITES sites run inside one block per replicate (block
