@@ -27,8 +27,11 @@ pytestmark = pytest.mark.gpu
 
 # (nz, ny, nx): one level (<= 512 sites), two and three levels with the
 # coarse part in the single-block kernel, four levels with a grid-kernel level,
-# a flat lattice (in-plane coarsening) and one that becomes flat after a level
-SHAPES = [(5, 7, 13), (16, 16, 16), (32, 32, 32), (24, 40, 56), (1, 48, 70), (2, 40, 60)]
+# a flat lattice (in-plane coarsening), one that becomes flat after a level,
+# and odd extents on every axis (a last fine row or plane alone in its
+# coarse cell) with two and three levels
+SHAPES = [(5, 7, 13), (16, 16, 16), (32, 32, 32), (24, 40, 56), (1, 48, 70), (2, 40, 60), (9, 13, 21),
+          (17, 23, 31)]
 
 
 def _operator(which, st, K, perf, cfg):
