@@ -59,7 +59,7 @@ def workload_config(edge: int = N_EDGE):
     return {"workload": f"{edge}^3 coupled HCA step (O2 quasi-steady CG + 2 implicit-Euler drug CGs + "
                         f"per-cell ODEs + 27-colour stochastic CA)",
             "solver": "CG preconditioned by one geometric-multigrid V-cycle per iteration; FP32 inner solves "
-                      "with FP64-residual defect correction",
+                      "with float-float-residual defect correction (FP64 norms)",
             "lattice": [edge] * 3, "precision": "f32 fields, f64 reductions", "n_drugs": 2,
             "cg_rtol": WORKLOAD["rtol_o2"], "maps": f"seeded GRF, correlation length {CORR_LEN:g} sites",
             "l2": f"working set ~{0.9 * (edge / 256) ** 3:.1f} GB per replicate > 129 MB L2; no flush needed"}

@@ -479,9 +479,10 @@ int solve_plain(hca_handle* h, int which) {
   return h->h_pinned[1] ? HCA_ERR_NONFINITE : HCA_OK;
 }
 
-// FP32 storage with defect correction: FP64 residual of the two-word
-// solution, FP32 inner CG on the correction, two-word update; repeated until
-// the FP64 relative residual meets the tolerance or max_outer sweeps.
+// FP32 storage with defect correction: float-float (~48-bit) residual of the
+// two-word solution, FP32 inner CG on the correction, two-word update;
+// repeated until the relative residual (FP64 norms) meets the tolerance or
+// max_outer sweeps.
 int solve_dc(hca_handle* h, int which) {
   Ctx& c = h->ctx;
   void* xh = which == 0 ? c.K : c.G[which - 1];

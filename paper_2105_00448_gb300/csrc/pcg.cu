@@ -592,9 +592,9 @@ struct ScaledAcc {
 
 // --------------------------------------------------- defect correction ---
 // FP32 storage scheme.  The solution is kept as two FP32 words, x = x_hi +
-// x_lo.  Each sweep evaluates the residual r = b - A x in FP64 from the
-// two-word solution, with the diagonal rebuilt in FP64 as c n + a from the
-// stored FP32 reaction coefficient a (storing d = c n + a itself in FP32 would
+// x_lo.  Each sweep evaluates the residual r = b - A x to about 48 bits
+// (float-float arithmetic) from the two-word solution, with the diagonal
+// rebuilt exactly as c n + a from the stored FP32 reaction coefficient a (storing d = c n + a itself in FP32 would
 // round away most digits of the small reaction part: 1/dt + psi ~ 0.03 next to
 // c n ~ 600 for a drug).  It stops the solve when |r| <= rtol |b| (FP64 norms)
 // and otherwise starts an FP32 inner CG on the correction, A32 dx = fl32(r),

@@ -116,7 +116,7 @@ def test_mg_cuts_drug_iterations(rng):
 
 @pytest.mark.parametrize("shape", [(16, 16, 16), (24, 40, 56)])
 def test_fp32_defect_correction_with_mg(shape, rng):
-    """FP32 storage, FP32 inner MG-PCG, FP64 residuals: the field matches the
+    """FP32 storage, FP32 inner MG-PCG, float-float residuals: the field matches the
     FP64 oracle within the FP32 bound (1e-6 relative)."""
     sim, cfg, _ = make_pair(shape, "f32", seed=6, n_drugs=1, rtol_o2=1e-8, rtol_drug=1e-8, picard_maxit=1,
                             preconditioner=hca.HCA_PC_MG)

@@ -1,5 +1,5 @@
 """Cell counts of the fully coupled run over 32 replicates: the GPU (one
-batched handle; FP64, and FP32 fields with FP64-residual defect correction)
+batched handle; FP64, and FP32 fields with float-float-residual defect correction)
 against the FP64 oracle, 48^3 lattices, one drug, 12 hourly steps, seeds
 0..31, maps with correlation length 4 sites.
 
