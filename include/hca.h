@@ -363,25 +363,28 @@ int hca_get_profile(hca_handle* h, hca_profile* out);
  * running inside another framework's memory pool or a real-time loop that
  * forbids cudaMalloc and its implicit synchronisation).
  *
- * Computes *rel_out = ||b - A K||_2 / ||b||_2 (0 when b = 0) for the oxygen
- * operator of one lattice linearised about K_prev, i.e. the relative
- * residual that hca_get_stats reports for an oxygen solve: A = -D_K Lap_h
- * (7-point, Neumann) + diag(phi_K/(K1 + K_prev)[consumer] + r_K[vessel]),
- * b = r_K K0 [vessel].  Only cfg's nx, ny, nz, dx, D_K, phi_K, K1, K0, r_K
- * are used.  state (uint8 codes), K_prev and K (double) are caller-owned
- * DEVICE arrays of nx*ny*nz elements in site order x + nx*(y + ny*z); they
- * are only read.  Work is queued on `stream` (a cudaStream_t, NULL = the
- * default stream), which is synchronised before the call returns.
+ * Computes *rel_out = ||b - A K||_2 / ||b||_2 (0 when b = 0) for the
+ * quasi-steady oxygen operator of one lattice linearised about K_prev, i.e.
+ * the relative residual that hca_get_stats reports for an oxygen solve with
+ * o2_scheme 0: A = -D_K Lap_h (7-point, Neumann) +
+ * diag(phi_K/(K1 + K_prev)[consumer] + r_K[vessel]), b = r_K K0 [vessel].
+ * Only cfg's nx, ny, nz, dx, D_K, phi_K, K1, K0, r_K and o2_scheme are used;
+ * they are checked as hca_create checks them, and o2_scheme != 0 (whose
+ * right-hand side depends on the previous field) is HCA_ERR_ARG.
+ * state (uint8 codes), K_prev and K (double) are caller-owned DEVICE arrays
+ * of nx*ny*nz elements in site order x + nx*(y + ny*z); they are only read.
  *
  * Nothing is allocated: the reduction scratch is a fixed device array inside
  * the library (about 33 KB per GPU, kept until the process exits), so the
- * lattice is limited to ny*nz <= 65536 rows (HCA_ERR_ARG beyond that).  The
- * first call on a device looks up that array's device address with the
- * device current; make that first call before any stream capture.  Every
- * call shares the array: calls that overlap on the GPU race and must be
- * serialised by the caller.  Returns HCA_ERR_ARG for bad arguments,
- * HCA_ERR_CUDA for a failed CUDA call, HCA_ERR_NONFINITE for a non-finite
- * result. */
+ * lattice is limited to ny*nz <= 65536 rows (HCA_ERR_ARG beyond that).  Each
+ * call looks up that array's device address in the context of the current
+ * device (a host-side lookup that allocates nothing), then queues a memset of
+ * its ticket, one kernel and a copy of the result to host memory on `stream`
+ * (a cudaStream_t, NULL = the default stream), and synchronises `stream`
+ * before it returns.  Every call shares the array: calls that overlap on the
+ * GPU race and must be serialised by the caller.  Returns HCA_ERR_ARG for
+ * bad arguments, HCA_ERR_CUDA for a failed CUDA call, HCA_ERR_NONFINITE for a
+ * non-finite result. */
 int hca_o2_residual_noalloc(const hca_config* cfg, const uint8_t* state, const double* K_prev,
                             const double* K, double* rel_out, void* stream);
 

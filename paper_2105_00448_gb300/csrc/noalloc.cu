@@ -20,6 +20,11 @@
 // until the process exits, and every call shares it.  Calls that overlap on
 // the GPU (two streams, or two host threads) race on it and must be
 // serialised by the caller.
+//
+// The array's device address is looked up on every call, with the caller's
+// device current (cudaGetSymbolAddress is a host-side lookup and allocates
+// nothing).  A cached address could outlive the context it belongs to: after
+// a device reset the module is loaded again and the array may move.
 #include <cuda_runtime.h>
 
 #include "hca_internal.cuh"
@@ -29,7 +34,6 @@ namespace {
 constexpr int kNoAllocMaxChunks = 2048;
 constexpr int kNoAllocRows = 32;       // rows per chunk
 constexpr int kNoAllocThreads = 256;   // fixed: the reduction order depends on it
-constexpr int kMaxDevices = 64;
 
 struct NoAllocScratch {
   double partial[kNoAllocMaxChunks][2];  // per chunk: |r|^2, |b|^2
@@ -39,10 +43,6 @@ struct NoAllocScratch {
 };
 
 static __device__ __align__(256) NoAllocScratch g_noalloc;
-
-// Device address of g_noalloc per device, fetched once with that device
-// current (the host-side symbol is only a stand-in, not a device address).
-NoAllocScratch* g_noalloc_ptr[kMaxDevices] = {};
 
 __global__ void __launch_bounds__(kNoAllocThreads) k_o2_residual_noalloc(
     NoAllocScratch* __restrict__ sc, int nx, int ny, int nz, double c, double phi_K, double K1, double K0,
@@ -138,26 +138,24 @@ extern "C" int hca_o2_residual_noalloc(const hca_config* cfg, const uint8_t* sta
   if (!cfg || !state || !K_prev || !K || !rel_out) return HCA_ERR_ARG;
   if (cfg->struct_size != sizeof(hca_config)) return HCA_ERR_ARG;
   if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1 || !(cfg->dx > 0)) return HCA_ERR_ARG;
+  // the same parameter checks as handle creation, for the fields read here
+  if (!(cfg->D_K > 0) || !(cfg->phi_K >= 0) || !(cfg->K1 > 0) || !(cfg->r_K >= 0) || !(cfg->K0 >= 0))
+    return HCA_ERR_ARG;
+  // only the quasi-steady operator: with a time-dependent oxygen scheme the
+  // handle's right-hand side also depends on the previous field
+  if (cfg->o2_scheme != 0) return HCA_ERR_ARG;
   const long long rows = (long long)cfg->ny * cfg->nz;
   const long long chunks = (rows + kNoAllocRows - 1) / kNoAllocRows;
   if (chunks > kNoAllocMaxChunks) return HCA_ERR_ARG;   // beyond the fixed scratch size
   if ((long long)cfg->nx * rows > 2147483647LL) return HCA_ERR_ARG;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  // device address of the scratch array in the current device's context (the
+  // host-side symbol is only a stand-in, not a device address)
+  void* addr = nullptr;
+  if (cudaGetSymbolAddress(&addr, g_noalloc) != cudaSuccess || !addr) {
     (void)cudaGetLastError();
     return HCA_ERR_CUDA;
   }
-  // set-up, once per device, with that device current
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc);
-    if (e != cudaSuccess || !p) {
-      (void)cudaGetLastError();
-      return HCA_ERR_CUDA;
-    }
-    g_noalloc_ptr[dev] = (NoAllocScratch*)p;
-  }
-  NoAllocScratch* sc = g_noalloc_ptr[dev];
+  NoAllocScratch* sc = (NoAllocScratch*)addr;
   cudaStream_t s = (cudaStream_t)stream;
   // the ticket must start at zero (a previous call that failed mid-way may
   // have left it otherwise); the partials are fully overwritten

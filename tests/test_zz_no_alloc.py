@@ -3,10 +3,15 @@
 Callers that may not allocate device memory (inside another framework's
 memory pool, or in a real-time loop that forbids cudaMalloc) cannot create a
 handle just to check a field; this entry point takes their device arrays and
-uses a fixed scratch array inside the library.  The test compares it with the
-relative residual the existing handle path reports for the same oxygen solve
-(hca_stage + hca_get_stats), on two calls in a row, at the 1e-12 tolerance
-(relative to the size of the operator's terms) used for operator parity.
+uses a fixed scratch array inside the library.  The tests compare it, on two
+calls in a row, with the relative residual the existing handle path reports
+for the same oxygen solve (hca_stage + hca_get_stats) and with the oracle's
+FP64 residual (1e-12 relative, plus 64 units of FP64 rounding of the size of
+the operator's terms for a converged field); they check that device free memory is
+the same before and after the calls, that a lattice with more chunks than one
+block's threads (the last block's strided loop over the partials) and the
+largest accepted lattice (ny*nz = 65536 rows) agree with the oracle, and that
+sizes beyond the scratch array and unsupported configurations are refused.
 This file is collected last on purpose.
 """
 
@@ -15,15 +20,58 @@ import pytest
 
 from gpu_helpers import make_pair, random_states
 from oracle import params as Pm
+from oracle import stencil as S
 from paper_2105_00448_gb300 import hca
 
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("shape", [(9, 17, 30), (24, 40, 64)])
-def test_noalloc_residual_matches_handle_solve(shape):
+def oracle_rel_residual(state, K_prev, K, cfg):
+    """||b - A(K_prev) K|| / ||b|| of the quasi-steady oxygen system, FP64
+    (oracle), and the tolerance a second FP64 evaluation must meet: 1e-12
+    relative, plus 64 units of rounding of the size of the operator's terms
+    (|b| + |a K| + c (n |K| + sum |K_nb|)) relative to ||b||, which is what
+    rounding leaves of a residual that has converged far below its terms."""
+    a = S.o2_reaction(state, K_prev, cfg)
+    b = S.o2_rhs(state, cfg)
+    c = S.o2_coupling(cfg)
+    r = b - S.apply_operator(K, c, a)
+    nb_abs = S.neighbour_count(K.shape) * np.abs(K) - S.laplacian_sum(np.abs(K))
+    terms = np.abs(b) + np.abs(a * K) + c * (S.neighbour_count(K.shape) * np.abs(K) + nb_abs)
+    bn = np.linalg.norm(b)
+    rel = float(np.linalg.norm(r) / bn)
+    return rel, 1e-12 * rel + 64 * np.finfo(np.float64).eps * float(np.linalg.norm(terms) / bn)
+
+
+def device_arrays(st, K_prev, K):
     import torch
 
+    dev = torch.device("cuda", 0)
+    return [torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).to(dev) for a in (st, K_prev, K)]
+
+
+def free_bytes():
+    import torch
+
+    torch.cuda.synchronize()
+    return torch.cuda.mem_get_info(0)[0]
+
+
+def load_module_once():
+    """One call on a tiny lattice before any free-memory measurement: the CUDA
+    runtime loads the library's module (its code and the fixed scratch array)
+    on first use, which is the runtime's one-time cost, not the call's."""
+    import torch
+
+    dev = torch.device("cuda", 0)
+    st = torch.zeros(64, dtype=torch.uint8, device=dev)
+    st[0] = Pm.VESSEL
+    K = torch.ones(64, dtype=torch.float64, device=dev)
+    hca.hca_o2_residual_noalloc(hca.make_config(4, 4, 4), st, K, K)
+
+
+@pytest.mark.parametrize("shape", [(9, 17, 30), (24, 40, 64)])
+def test_noalloc_residual_matches_handle_solve(shape):
     rng = np.random.default_rng(5)
     sim, cfg, _ = make_pair(shape, "f64", seed=3, n_drugs=0, rtol_o2=1e-10, picard_maxit=1)
     st = random_states(shape, rng)
@@ -37,19 +85,45 @@ def test_noalloc_residual_matches_handle_solve(shape):
     sim.close()
     assert 0.0 < rel_handle <= 1e-10
 
-    dev = torch.device("cuda", 0)
-    st_d = torch.from_numpy(st.reshape(-1).copy()).to(dev)
-    Kp_d = torch.from_numpy(K_prev.reshape(-1).copy()).to(dev)
-    K_d = torch.from_numpy(K.reshape(-1).copy()).to(dev)
+    st_d, Kp_d, K_d = device_arrays(st, K_prev, K)
     nz, ny, nx = shape
     c = hca.make_config(nx, ny, nz)
+    load_module_once()
+    free0 = free_bytes()
     first = hca.hca_o2_residual_noalloc(c, st_d, Kp_d, K_d)
     second = hca.hca_o2_residual_noalloc(c, st_d, Kp_d, K_d)
+    assert free_bytes() == free0, "the call changed the device's free memory"
     assert first == second
-    assert abs(first - rel_handle) <= 1e-12
+    rel_oracle, tol = oracle_rel_residual(st, K_prev, K, cfg)
+    assert abs(first - rel_handle) <= tol
+    assert abs(first - rel_oracle) <= tol
     # the starting field is far from the solution: a large residual, same on both calls
     rel0 = hca.hca_o2_residual_noalloc(c, st_d, Kp_d, Kp_d)
     assert rel0 > 1e-3 and rel0 == hca.hca_o2_residual_noalloc(c, st_d, Kp_d, Kp_d)
+    rel0_oracle, tol0 = oracle_rel_residual(st, K_prev, K_prev, cfg)
+    assert abs(rel0 - rel0_oracle) <= tol0
+
+
+@pytest.mark.parametrize("shape", [(16, 640, 8), (256, 256, 4)])
+def test_noalloc_many_chunks_and_largest_lattice_match_oracle(shape):
+    """(16, 640, 8): 320 chunks, more than the 256 threads of the finishing
+    block; (256, 256, 4): ny*nz = 65536 rows, the largest accepted lattice."""
+    rng = np.random.default_rng(11)
+    st = random_states(shape, rng)
+    K_prev = rng.uniform(0.0, 20.0, shape)
+    K = K_prev * rng.uniform(0.9, 1.1, shape)
+    nz, ny, nx = shape
+    cfg = Pm.Config(nx=nx, ny=ny, nz=nz)
+    c = hca.make_config(nx, ny, nz)
+    arrs = device_arrays(st, K_prev, K)
+    load_module_once()
+    free0 = free_bytes()
+    first = hca.hca_o2_residual_noalloc(c, *arrs)
+    second = hca.hca_o2_residual_noalloc(c, *arrs)
+    assert free_bytes() == free0
+    assert first == second
+    rel_oracle, tol = oracle_rel_residual(st, K_prev, K, cfg)
+    assert abs(first - rel_oracle) <= tol
 
 
 def test_noalloc_rejects_lattices_beyond_its_scratch():
@@ -59,6 +133,19 @@ def test_noalloc_rejects_lattices_beyond_its_scratch():
     c = hca.make_config(4, 300, 300)          # 90000 rows > 65536
     st = torch.zeros(4 * 300 * 300, dtype=torch.uint8, device=dev)
     K = torch.zeros(4 * 300 * 300, dtype=torch.float64, device=dev)
+    with pytest.raises(hca.HcaError) as e:
+        hca.hca_o2_residual_noalloc(c, st, K, K)
+    assert e.value.status == hca.HCA_ERR_ARG
+
+
+@pytest.mark.parametrize("override", [{"o2_scheme": 1}, {"D_K": 0.0}, {"phi_K": -1.0}, {"K1": 0.0}])
+def test_noalloc_rejects_unsupported_configs(override):
+    import torch
+
+    dev = torch.device("cuda", 0)
+    c = hca.make_config(8, 8, 8, **override)
+    st = torch.zeros(512, dtype=torch.uint8, device=dev)
+    K = torch.ones(512, dtype=torch.float64, device=dev)
     with pytest.raises(hca.HcaError) as e:
         hca.hca_o2_residual_noalloc(c, st, K, K)
     assert e.value.status == hca.HCA_ERR_ARG
