@@ -36,6 +36,7 @@ void launch_mg_setup(const Ctx& c, int which, bool fp64, const MGHost& H);
 void launch_vcycle(const Ctx& c, int which, bool fp64, const MGHost& H, int part, bool scale);
 int vcycle_launches(const MGHost& H, bool scale);
 int vcycle_part_launches(const MGHost& H, int part, bool scale);
+void mg_coop_config(MGHost& H, bool fp64, int sm_count, long long smem_bytes);
 }  // namespace hca
 
 using hca::Ctx;
@@ -120,6 +121,11 @@ constexpr int kFieldAlign = 64;  // elements; keeps every replicate 256-byte ali
     }                                              \
   } while (0)
 
+
+// Host status of a nonzero PassSync::error code.
+int sync_error_status(int e) {
+  return e == hca::SYNC_ERR_TIMEOUT ? HCA_ERR_TIMEOUT : e == hca::SYNC_ERR_NOCONV ? HCA_ERR_NOCONV : HCA_ERR_NONFINITE;
+}
 
 constexpr size_t kPairs = 4096;
 
@@ -440,7 +446,7 @@ int pcg_iterate(hca_handle* h, int which, void* x, int predict) {
   for (;;) {
     HCA_TRY(cudaMemcpyAsync(h->h_pinned, &c.sync->active_count, 2 * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     HCA_TRY(cudaStreamSynchronize(c.stream));
-    if (h->h_pinned[1]) return HCA_ERR_NONFINITE;
+    if (h->h_pinned[1]) return sync_error_status(h->h_pinned[1]);
     if (h->h_pinned[0] == 0 || done >= h->maxit_all) break;
     const int n = std::min(chunk, h->maxit_all - done);
     for (int k = 0; k < n; ++k) {
@@ -476,7 +482,7 @@ int solve_plain(hca_handle* h, int which) {
   HCA_LAUNCH(h, HCA_KCLASS_RESIDUAL, 2, hca::launch_true_residual(c, which, x, h->fp64));
   HCA_TRY(cudaMemcpyAsync(h->h_pinned, &c.sync->active_count, 2 * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
   HCA_TRY(cudaStreamSynchronize(c.stream));
-  return h->h_pinned[1] ? HCA_ERR_NONFINITE : HCA_OK;
+  return h->h_pinned[1] ? sync_error_status(h->h_pinned[1]) : HCA_OK;
 }
 
 // FP32 storage with defect correction: float-float (~48-bit) residual of the
@@ -497,7 +503,7 @@ int solve_dc(hca_handle* h, int which) {
     }
     HCA_TRY(cudaMemcpyAsync(h->h_pinned, &c.sync->active_count, 2 * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     HCA_TRY(cudaStreamSynchronize(c.stream));
-    if (h->h_pinned[1]) return HCA_ERR_NONFINITE;
+    if (h->h_pinned[1]) return sync_error_status(h->h_pinned[1]);
     if (h->h_pinned[0] == 0) {
       // converged everywhere (or max_outer); zero fields whose right-hand side vanished
       HCA_LAUNCH(h, HCA_KCLASS_OTHER, 1, hca::launch_dc_update(c, xh, xl));
@@ -652,6 +658,7 @@ int cap_stages(hca_handle* h, uint32_t mask, cudaGraph_t G) {
   c.stream = h->cap[0];
   HCA_TRY(cudaMemsetAsync(c.stats, 0, sizeof(hca::DevStats) * h->n_reps, c.stream));
   HCA_TRY(cudaMemsetAsync(&c.sync->error, 0, sizeof(int), c.stream));
+  HCA_TRY(cudaMemsetAsync(&c.sync->bar_count, 0, sizeof(unsigned int), c.stream));
   int rc;
   if (mask & HCA_STAGE_O2) {
     rc = ws_before_o2(h, c.stream);
@@ -762,6 +769,7 @@ int run_graph(hca_handle* h, uint32_t mask, int times) {
 int reset_step_stats(hca_handle* h) {
   HCA_TRY(cudaMemsetAsync(h->ctx.stats, 0, sizeof(hca::DevStats) * h->n_reps, h->ctx.stream));
   HCA_TRY(cudaMemsetAsync(&h->ctx.sync->error, 0, sizeof(int), h->ctx.stream));
+  HCA_TRY(cudaMemsetAsync(&h->ctx.sync->bar_count, 0, sizeof(unsigned int), h->ctx.stream));
   return HCA_OK;
 }
 
@@ -842,8 +850,7 @@ int check_convergence(hca_handle* h) {
   HCA_TRY(cudaMemcpyAsync(h->h_pinned, &h->ctx.sync->active_count, 2 * sizeof(int), cudaMemcpyDeviceToHost,
                           h->ctx.stream));
   HCA_TRY(cudaStreamSynchronize(h->ctx.stream));
-  if (h->h_pinned[1] == 1) return HCA_ERR_NONFINITE;
-  if (h->h_pinned[1] == 2) return HCA_ERR_NOCONV;
+  if (h->h_pinned[1]) return sync_error_status(h->h_pinned[1]);
   for (auto& s : st) {
     if (s.nonfinite) return HCA_ERR_NONFINITE;
   }
@@ -907,6 +914,7 @@ int autotune(hca_handle* h, bool tune_regs) {
   if (rc) return rc;
   // the timed passes may have left solver flags set; the solves reset the rest
   HCA_TRY(cudaMemsetAsync(&c.sync->error, 0, sizeof(int), c.stream));
+  HCA_TRY(cudaMemsetAsync(&c.sync->bar_count, 0, sizeof(unsigned int), c.stream));
   HCA_TRY(cudaStreamSynchronize(c.stream));
   return HCA_OK;
 }
@@ -1214,6 +1222,17 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
             H.restr_items[l] = rp;
           }
         }
+      }
+      {
+        // shared-memory footprint of the single-block levels (x, t, rhs, d, w)
+        long long smem = 0;
+        for (int i = 0; i < n; ++i) {
+          long long s = 0;
+          for (int l = rep[i].y; l < rep[i].x; ++l) s += 5 * lv[(size_t)i * hca::MG_MAXLEV + l].n * (long long)es;
+          smem = std::max(smem, s);
+        }
+        hca::mg_coop_config(H, h->fp64, c.sm_count, smem);
+        H.launches = hca::vcycle_launches(H, false);
       }
       ALLOC(c.r, fbytes);
       ALLOC(c.mg_t0, fbytes);

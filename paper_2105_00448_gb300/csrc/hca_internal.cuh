@@ -128,7 +128,18 @@ struct PassSync {
   int guard_outer;      // defect-correction sweeps since the solve's first sweep
   int guard_limit;      // passes after which a graph loop is forced to stop
   int guard_outer_limit;
+  // grid barrier of the cooperative coarse-level V-cycle kernel: arrivals
+  // since the last release, and the release generation the waiters poll
+  unsigned int bar_count;
+  unsigned int bar_gen;
 };
+
+// PassSync::error codes (read back by the host): 1 a norm became NaN/Inf,
+// 2 a defect-correction solve stopped at its sweep limit, 3 a bounded device
+// wait gave up
+constexpr int SYNC_ERR_NONFINITE = 1;
+constexpr int SYNC_ERR_NOCONV = 2;
+constexpr int SYNC_ERR_TIMEOUT = 3;
 
 // A conditional-node handle of the step graph that a kernel's last block sets
 // (valid = 0 outside graph execution).
@@ -267,6 +278,12 @@ constexpr int MG_MAXLEV = 16;
 // Host summary of the hierarchies of a handle's replicates (launch geometry).
 struct MGHost {
   int nlev = 0;                  // most levels of any replicate
+  // the coarse levels of a V-cycle in one cooperative launch (grid barriers
+  // between levels): blocks of that launch (0 = one launch per level) and
+  // the shared memory of its single-block levels (0 = they stay in global memory)
+  int coop_blocks = 0;
+  int small_smem = 0;
+  int coop_cfg = 0;              // launch shape of the cooperative kernel (threads, register budget)
   int small = 0;                 // 1 + deepest grid-kernel level of any replicate
   long long ntot[MG_MAXLEV] = {};  // sites of level l summed over the replicates
   long long nrowitems = 0;         // (level-1 row, lattice 4-site group) items over the replicates

@@ -23,6 +23,9 @@
 // level 0, also forms rho = r.z with the fixed-order reductions of the CG
 // passes and sets beta, per replicate.
 
+#include <algorithm>
+#include <cstdlib>
+
 #include "hca_internal.cuh"
 #include "row_ops.cuh"
 
@@ -198,6 +201,59 @@ __device__ void restrict_residual_at(const View<T>& F, const View<T>& C, long lo
   C.rhs[C.at(X, Y, Z)] = acc;
 }
 
+// Coordinates of the sites s0, s0 + st, s0 + 2 st, ... of a dense level
+// (s = X + nx (Y + ny Z)), advanced by mixed-radix addition instead of a
+// division per site.
+struct Walk {
+  int X, Y, Z, ax, ay, az, nx, ny;
+  __device__ __forceinline__ Walk(int s0, int st, int nx_, int ny_) : nx(nx_), ny(ny_) {
+    int q = s0 / nx;
+    X = s0 - q * nx;
+    Z = q / ny;
+    Y = q - Z * ny;
+    q = st / nx;
+    ax = st - q * nx;
+    az = q / ny;
+    ay = q - az * ny;
+  }
+  __device__ __forceinline__ void next() {
+    X += ax;
+    int cy = X >= nx;
+    if (cy) X -= nx;
+    Y += ay + cy;
+    cy = Y >= ny;
+    if (cy) Y -= ny;
+    Z += az + cy;
+  }
+};
+
+// The per-site steps on a dense level (element index = site index s) at
+// known coordinates: the same arithmetic, in the same order, as
+// sweep_at / restrict_residual_at / prolong_at.
+template <typename T>
+__device__ __forceinline__ void sweep_xyz(const View<T>& V, const T* src, T* dst, int X, int Y, int Z, int s) {
+  const T r = V.rhs[s] - V.apply(src, X, Y, Z, s);
+  dst[s] = src[s] + V.w[s] * r;
+}
+
+template <typename T>
+__device__ __forceinline__ void restrict_residual_xyz(const View<T>& F, const View<T>& C, int X, int Y, int Z, int S) {
+  T acc = T(0);
+  for (int k = 0; k < 8; ++k) {
+    const int x = 2 * X + (k & 1), y = 2 * Y + ((k >> 1) & 1), z = 2 * Z + (k >> 2);
+    if (x < F.nx && y < F.ny && z < F.nz) {
+      const long long e = x + (long long)F.nx * (y + (long long)F.ny * z);
+      acc += F.rhs[e] - F.apply(F.x, x, y, z, e);
+    }
+  }
+  C.rhs[S] = acc;
+}
+
+template <typename T>
+__device__ __forceinline__ void prolong_xyz(const View<T>& F, const View<T>& C, int X, int Y, int Z, int s) {
+  F.t[s] = F.x[s] + C.x[(X >> 1) + (long long)C.nx * ((Y >> 1) + (long long)C.ny * (Z >> 1))];
+}
+
 // t_F = x_F + P x_C
 template <typename T>
 __device__ void prolong_at(const View<T>& F, const View<T>& C, long long s) {
@@ -265,9 +321,14 @@ __device__ void post_fused_at(const View<T>& F, const View<T>& C, long long s) {
 
 // Grid-stride loop over the flattened sites of level l of every replicate
 // (a per-site lookup of the owning replicate in the level's prefix table).
-#define HCA_MG_FOR_SITES(l)                                                                           \
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;                               \
-       q < c.mg_start[(long long)(l) * (c.n_reps + 1) + c.n_reps]; q += (long long)gridDim.x * blockDim.x)
+#define HCA_MG_FOR_SITES_FROM(l, t0, st)                                                              \
+  for (long long q = (t0); q < c.mg_start[(long long)(l) * (c.n_reps + 1) + c.n_reps]; q += (st))
+#define HCA_MG_FOR_SITES(l) \
+  HCA_MG_FOR_SITES_FROM(l, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x)
+
+// This thread's first item and the stride of a grid-stride loop.
+__device__ __forceinline__ long long grid_t0() { return blockIdx.x * (long long)blockDim.x + threadIdx.x; }
+__device__ __forceinline__ long long grid_st() { return (long long)gridDim.x * blockDim.x; }
 
 // ------------------------------------------------------- grid kernels ---
 template <typename T>
@@ -332,20 +393,19 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_sweep0(Ctx c, int which, cons
 
 // Restriction from level l to l + 1 for the replicates whose level l is
 // swept by grid kernels (l < their first single-block level).  MULTI = false:
-// one replicate, whose views are fixed for the whole kernel (fewer registers).
+// one replicate, whose views are fixed for the whole loop (fewer registers).
+// t0, st: this thread's first item and the loop stride.
 template <typename T, bool MULTI>
-__global__ void __launch_bounds__(kMgThreads) k_mg_restrict(Ctx c, int which, int l) {
-  HCA_COUNT_KERNEL(c);
+__device__ __forceinline__ void restrict_sites(const Ctx& c, int which, int l, long long t0, long long st) {
   if (!MULTI) {
     const View<T> F = view<T>(c, which, 0, l), C = view<T>(c, which, 0, l + 1);
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < C.n(); s += (long long)gridDim.x * blockDim.x)
-      restrict_fused_at<T>(F, C, s);
+    for (long long s = t0; s < C.n(); s += st) restrict_fused_at<T>(F, C, s);
     return;
   }
   RepCursor<T> k;   // cursor on level l + 1 (its F is the coarse view)
   View<T> Ff;
   bool skip = true;
-  HCA_MG_FOR_SITES(l + 1) {
+  HCA_MG_FOR_SITES_FROM(l + 1, t0, st) {
     if (k.at(c, which, l + 1, q, false)) {
       skip = l >= c.mg_rep[k.r].y;
       Ff = view<T>(c, which, k.r, l);
@@ -356,21 +416,31 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_restrict(Ctx c, int which, in
 }
 
 template <typename T, bool MULTI>
-__global__ void __launch_bounds__(kMgThreads) k_mg_post(Ctx c, int which, int l) {
+__global__ void __launch_bounds__(kMgThreads) k_mg_restrict(Ctx c, int which, int l) {
   HCA_COUNT_KERNEL(c);
+  restrict_sites<T, MULTI>(c, which, l, grid_t0(), grid_st());
+}
+
+template <typename T, bool MULTI>
+__device__ __forceinline__ void post_sites(const Ctx& c, int which, int l, long long t0, long long st) {
   if (!MULTI) {
     const View<T> F = view<T>(c, which, 0, l), C = view<T>(c, which, 0, l + 1);
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < F.n(); s += (long long)gridDim.x * blockDim.x)
-      post_fused_at<T>(F, C, s);
+    for (long long s = t0; s < F.n(); s += st) post_fused_at<T>(F, C, s);
     return;
   }
   RepCursor<T> k;
   bool skip = true;
-  HCA_MG_FOR_SITES(l) {
+  HCA_MG_FOR_SITES_FROM(l, t0, st) {
     if (k.at(c, which, l, q, true)) skip = l >= c.mg_rep[k.r].y;
     if (skip) continue;
     post_fused_at<T>(k.F, k.C, q - k.lo);
   }
+}
+
+template <typename T, bool MULTI>
+__global__ void __launch_bounds__(kMgThreads) k_mg_post(Ctx c, int which, int l) {
+  HCA_COUNT_KERNEL(c);
+  post_sites<T, MULTI>(c, which, l, grid_t0(), grid_st());
 }
 
 // Replicate owning item q of a prefix table (the last r with pre[r] <= q).
@@ -391,16 +461,14 @@ __device__ __forceinline__ int rep_of_items(const long long* pre, int n, long lo
 // correction under each row) is issued before u = (omega/d) rhs + P x_C is
 // formed.  The same arithmetic, in the same order, as post_fused_at.
 template <typename T>
-__global__ void __launch_bounds__(kMgThreads) k_mg_post_rows(Ctx c, int which, int l) {
-  HCA_COUNT_KERNEL(c);
+__device__ __forceinline__ void post_rows(const Ctx& c, int which, int l, long long t0, long long st) {
   const long long* pre = c.mg_post_items + (long long)l * (c.n_reps + 1);
   const long long items = pre[c.n_reps];
   int r = -1;
   long long lo = 0, hi = 0;
   View<T> F, C;
   int gpr = 1;
-  for (long long qq = blockIdx.x * (long long)blockDim.x + threadIdx.x; qq < items;
-       qq += (long long)gridDim.x * blockDim.x) {
+  for (long long qq = t0; qq < items; qq += st) {
     if (qq < lo || qq >= hi) {   // the replicate changes rarely along a thread's items
       r = rep_of_items(pre, c.n_reps, qq);
       lo = pre[r];
@@ -458,6 +526,12 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_post_rows(Ctx c, int which, i
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kMgThreads) k_mg_post_rows(Ctx c, int which, int l) {
+  HCA_COUNT_KERNEL(c);
+  post_rows<T>(c, which, l, grid_t0(), grid_st());
+}
+
 // Restriction from coarse level l >= 1 to l + 1 in row-vector form (every
 // replicate's level-l rows whole 4-site groups; batches as in k_mg_post_rows): one thread per group
 // of the four fine rows (2Y + dy, 2Z + dz) under coarse row (Y, Z), producing
@@ -465,16 +539,14 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_post_rows(Ctx c, int which, i
 // rows, d, the x neighbours) are issued before u = (omega/d) rhs is formed.
 // The same arithmetic, children in the same order, as restrict_fused_at.
 template <typename T>
-__global__ void __launch_bounds__(128) k_mg_restrict_rows(Ctx c, int which, int l) {
-  HCA_COUNT_KERNEL(c);
+__device__ __forceinline__ void restrict_rows(const Ctx& c, int which, int l, long long t0, long long st) {
   const long long* pre = c.mg_restr_items + (long long)l * (c.n_reps + 1);
   const long long items = pre[c.n_reps];
   int r = -1;
   long long lo = 0, hi = 0;
   View<T> F, C;
   int gpr = 1;
-  for (long long qq = blockIdx.x * (long long)blockDim.x + threadIdx.x; qq < items;
-       qq += (long long)gridDim.x * blockDim.x) {
+  for (long long qq = t0; qq < items; qq += st) {
     if (qq < lo || qq >= hi) {
       r = rep_of_items(pre, c.n_reps, qq);
       lo = pre[r];
@@ -489,78 +561,68 @@ __global__ void __launch_bounds__(128) k_mg_restrict_rows(Ctx c, int which, int 
     const int Y = (int)(R % C.ny), Z = (int)(R / C.ny);
     const int y0 = 2 * Y, z0 = 2 * Z, x0 = 4 * j;
     const long long eb = F.at(x0, y0, z0);
-    // rows: own t = 2 dy + dz; outer: y0 - 1, y0 + 2 (for dz = 0, 1), z0 - 1, z0 + 2 (for dy = 0, 1)
-    bool ok[12];
-    long long off[12];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        ok[2 * a + b] = (y0 + a < F.ny) && (z0 + b < F.nz);
-        off[2 * a + b] = F.sy * a + F.sz * b;
-      }
+    const bool hasl = x0 > 0, hasr = x0 + 4 < F.nx;
+    const bool y1 = y0 + 1 < F.ny;
+    T acc[2] = {T(0), T(0)};
+    // children in the order of restrict_fused_at (dz outer, dy, dx inner),
+    // one dz half at a time with its eight rows in registers: slots 0, 1 the
+    // half's own rows (y0, y0 + 1), 2, 3 rows y0 - 1 and y0 + 2, 4, 5 the
+    // other half's own rows, 6, 7 the outer z row (z0 - 1 or z0 + 2) under y0, y0 + 1
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
-      ok[4 + b] = y0 > 0 && z0 + b < F.nz;
-      off[4 + b] = -F.sy + F.sz * b;
-      ok[6 + b] = y0 + 2 < F.ny && z0 + b < F.nz;
-      off[6 + b] = 2 * F.sy + F.sz * b;
-    }
+      if (z0 + b >= F.nz) break;
+      const int ob = 1 - b;
+      const bool zo = b ? z0 + 2 < F.nz : z0 > 0;
+      const long long zoff = b ? 2 * F.sz : -F.sz;
+      const bool ok[8] = {true, y1, y0 > 0, y0 + 2 < F.ny, z0 + ob < F.nz, y1 && z0 + ob < F.nz, zo, zo && y1};
+      const long long off[8] = {F.sz * b, F.sy + F.sz * b, -F.sy + F.sz * b, 2 * F.sy + F.sz * b,
+                                F.sz * ob, F.sy + F.sz * ob, zoff, F.sy + zoff};
+      V4<T> RV[8], WV[8], DV[2];
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      ok[8 + a] = z0 > 0 && y0 + a < F.ny;
-      off[8 + a] = F.sy * a - F.sz;
-      ok[10 + a] = z0 + 2 < F.nz && y0 + a < F.ny;
-      off[10 + a] = F.sy * a + 2 * F.sz;
-    }
-    V4<T> RV[12], WV[12], DV[4];
+      for (int t = 0; t < 8; ++t) {
+        RV[t] = ld4_if(F.rhs + eb + off[t], ok[t]);
+        WV[t] = ld4_if(F.w + eb + off[t], ok[t]);
+      }
 #pragma unroll
-    for (int t = 0; t < 12; ++t) {
-      RV[t] = ld4_if(F.rhs + eb + off[t], ok[t]);
-      WV[t] = ld4_if(F.w + eb + off[t], ok[t]);
-    }
+      for (int t = 0; t < 2; ++t) DV[t] = ld4_if(F.d + eb + off[t], ok[t]);
+      T lr[2], lw[2], rrr[2], rw[2];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) DV[t] = ld4_if(F.d + eb + off[t], ok[t]);
-    T lr[4], lw[4], rrr[4], rw[4];
-    const bool hasl = x0 > 0, hasr = x0 + 4 < F.nx;
+      for (int t = 0; t < 2; ++t) {
+        lr[t] = (ok[t] && hasl) ? F.rhs[eb + off[t] - 1] : T(0);
+        lw[t] = (ok[t] && hasl) ? F.w[eb + off[t] - 1] : T(0);
+        rrr[t] = (ok[t] && hasr) ? F.rhs[eb + off[t] + 4] : T(0);
+        rw[t] = (ok[t] && hasr) ? F.w[eb + off[t] + 4] : T(0);
+      }
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      lr[t] = (ok[t] && hasl) ? F.rhs[eb + off[t] - 1] : T(0);
-      lw[t] = (ok[t] && hasl) ? F.w[eb + off[t] - 1] : T(0);
-      rrr[t] = (ok[t] && hasr) ? F.rhs[eb + off[t] + 4] : T(0);
-      rw[t] = (ok[t] && hasr) ? F.w[eb + off[t] + 4] : T(0);
-    }
-    V4<T> U[12];
-#pragma unroll
-    for (int t = 0; t < 12; ++t)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) U[t].a[e] = WV[t].a[e] * RV[t].a[e];
-    T acc[2] = {T(0), T(0)};
-    // children in the order of restrict_fused_at: dz outer, dy, dx inner
-#pragma unroll
-    for (int b = 0; b < 2; ++b)
-#pragma unroll
-      for (int a = 0; a < 2; ++a)
+      for (int a = 0; a < 2; ++a) {
+        if (!ok[a]) continue;
+        const int ym = a ? 0 : 2, yp = a ? 3 : 1;           // rows y - 1, y + 1
+        const int zm = b ? 4 + a : 6 + a, zp = b ? 6 + a : 4 + a;  // rows z - 1, z + 1
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const int t = 2 * a + b;
-          if (!ok[t]) continue;
-          const int ym = a ? b : 4 + b, yp = a ? 6 + b : 2 + b;          // rows y - 1, y + 1
-          const int zm = b ? 2 * a : 8 + a, zp = b ? 10 + a : 2 * a + 1;  // rows z - 1, z + 1
           const int x = x0 + e;
+          const T u = WV[a].a[e] * RV[a].a[e];
           T nb = T(0);
-          if (x > 0) nb = e == 0 ? fma(lw[t], lr[t], nb) : fma(WV[t].a[e - 1], RV[t].a[e - 1], nb);
-          if (x < F.nx - 1) nb = e == 3 ? fma(rw[t], rrr[t], nb) : fma(WV[t].a[e + 1], RV[t].a[e + 1], nb);
+          if (x > 0) nb = e == 0 ? fma(lw[a], lr[a], nb) : fma(WV[a].a[e - 1], RV[a].a[e - 1], nb);
+          if (x < F.nx - 1) nb = e == 3 ? fma(rw[a], rrr[a], nb) : fma(WV[a].a[e + 1], RV[a].a[e + 1], nb);
           if (y0 + a > 0) nb = fma(WV[ym].a[e], RV[ym].a[e], nb);
           if (y0 + a < F.ny - 1) nb = fma(WV[yp].a[e], RV[yp].a[e], nb);
           if (z0 + b > 0) nb = fma(WV[zm].a[e], RV[zm].a[e], nb);
           if (z0 + b < F.nz - 1) nb = fma(WV[zp].a[e], RV[zp].a[e], nb);
-          acc[e >> 1] += RV[t].a[e] - (DV[t].a[e] * U[t].a[e] - F.c * nb);
+          acc[e >> 1] += RV[a].a[e] - (DV[a].a[e] * u - F.c * nb);
         }
+      }
+    }
     const long long cb = C.at(2 * j, Y, Z);
     C.rhs[cb] = acc[0];
     C.rhs[cb + 1] = acc[1];
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_mg_restrict_rows(Ctx c, int which, int l) {
+  HCA_COUNT_KERNEL(c);
+  restrict_rows<T>(c, which, l, grid_t0(), grid_st());
 }
 
 // Restriction from the lattice to level 1 in row-vector form: one thread per
@@ -690,44 +752,238 @@ __global__ void __launch_bounds__(128) k_mg_restrict0_rows(Ctx c, int which) {
   }
 }
 
-// The whole sub-cycle of one replicate's levels small .. nlev-1 in one block
-// (block r = replicate r).
+// The view of single-block level l of replicate r with its arrays in the
+// block's shared memory `sm` (levels l0 .. l packed one after another, five
+// arrays x, t, rhs, d, w of n_l elements each), or in global memory when sm
+// is null.
+template <typename T, bool SMEM>
+__device__ __forceinline__ View<T> small_view(const Ctx& c, int which, int r, int l0, int l, T* sm) {
+  View<T> v = view<T>(c, which, r, l);
+  if (!SMEM) return v;
+  long long o = 0;
+  for (int k = l0; k < l; ++k) o += 5 * ((const MGLevel*)c.mg_lv)[r * MG_MAXLEV + k].n;
+  const long long n = v.n();
+  v.x = sm + o;
+  v.t = sm + o + n;
+  v.rhs = sm + o + 2 * n;
+  v.d = sm + o + 3 * n;
+  v.w = sm + o + 4 * n;
+  return v;
+}
+
+// Asynchronous copies (cp.async) from global to shared memory.
+template <int B>
+__device__ __forceinline__ void cp_async(void* sdst, const void* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sa), "l"(gsrc), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Start copying the diagonals and omega/d of replicate r's single-block
+// levels into shared memory (they do not change during a V-cycle); the copies
+// complete in the background until cp_async_wait_all.
 template <typename T>
-__global__ void __launch_bounds__(kSmallThreads) k_mg_small(Ctx c, int which) {
-  HCA_COUNT_KERNEL(c);
-  const int r = blockIdx.x;
+__device__ void small_prefetch(const Ctx& c, int which, int r, int tid, int nthr, T* sm) {
   const int l0 = c.mg_rep[r].y, last = c.mg_rep[r].x - 1;
-  const long long s0 = threadIdx.x, st = blockDim.x;
-  for (int l = l0; l < last; ++l) {
-    const View<T> V = view<T>(c, which, r, l);
-    for (long long s = s0; s < V.n(); s += st) sweep_first_at<T>(V, s);
+  for (int l = l0; l <= last; ++l) {
+    const View<T> G = view<T>(c, which, r, l), V = small_view<T, true>(c, which, r, l0, l, sm);
+    const int n = (int)V.n();
+    for (int s = tid; s < n; s += nthr) {
+      cp_async<sizeof(T)>(V.d + s, G.d + s);
+      cp_async<sizeof(T)>(V.w + s, G.w + s);
+    }
+  }
+}
+
+// The whole sub-cycle of replicate r's levels small .. nlev-1 by one block
+// (tid, nthr: this thread and the block's threads; block barriers between
+// sweeps).  With sm, the cycle runs in shared memory (the same arithmetic in
+// the same order as in global memory): the diagonals and omega/d of those
+// levels are copied in (already under way when `prefetched`), then the
+// right-hand side of the first level; afterwards the first level's iterate,
+// the only array later kernels read, is written back.
+template <typename T, bool SMEM>
+__device__ void small_cycle(const Ctx& c, int which, int r, int tid, int nthr, T* sm, bool prefetched) {
+  const int l0 = c.mg_rep[r].y, last = c.mg_rep[r].x - 1;
+  if (SMEM) {
+    if (!prefetched) small_prefetch<T>(c, which, r, tid, nthr, sm);
+    const View<T> G = view<T>(c, which, r, l0), V = small_view<T, true>(c, which, r, l0, l0, sm);
+    const int n = (int)V.n();
+    // all loads of a batch before its stores (the copies may not be reordered
+    // across the stores to shared memory otherwise)
+    for (int base = tid; base < n; base += 8 * nthr) {
+      T v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int s = base + k * nthr;
+        v[k] = s < n ? G.rhs[s] : T(0);
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int s = base + k * nthr;
+        if (s < n) V.rhs[s] = v[k];
+      }
+    }
+    cp_async_wait_all();
     __syncthreads();
-    const View<T> C = view<T>(c, which, r, l + 1);
-    for (long long s = s0; s < C.n(); s += st) restrict_residual_at<T>(V, C, s);
+  }
+  for (int l = l0; l < last; ++l) {
+    const View<T> V = small_view<T, SMEM>(c, which, r, l0, l, sm);
+    const int n = (int)V.n();
+    for (int s = tid; s < n; s += nthr) sweep_first_at<T>(V, s);
+    __syncthreads();
+    const View<T> C = small_view<T, SMEM>(c, which, r, l0, l + 1, sm);
+    const int nc = (int)C.n();
+    Walk w(tid, nthr, C.nx, C.ny);
+    for (int s = tid; s < nc; s += nthr, w.next()) restrict_residual_xyz<T>(V, C, w.X, w.Y, w.Z, s);
     __syncthreads();
   }
   {
-    const View<T> V = view<T>(c, which, r, last);
-    for (long long s = s0; s < V.n(); s += st) sweep_first_at<T>(V, s);
+    const View<T> V = small_view<T, SMEM>(c, which, r, l0, last, sm);
+    const int n = (int)V.n();
+    for (int s = tid; s < n; s += nthr) sweep_first_at<T>(V, s);
     __syncthreads();
     for (int k = 1; k < MG_NU_COARSE; ++k) {
       const bool odd = k & 1;
-      for (long long s = s0; s < V.n(); s += st) sweep_at<T>(V, odd ? V.x : V.t, odd ? V.t : V.x, s);
+      Walk w(tid, nthr, V.nx, V.ny);
+      for (int s = tid; s < n; s += nthr, w.next())
+        sweep_xyz<T>(V, odd ? V.x : V.t, odd ? V.t : V.x, w.X, w.Y, w.Z, s);
       __syncthreads();
     }
     if ((MG_NU_COARSE & 1) == 0) {   // the last sweep wrote t
-      for (long long s = s0; s < V.n(); s += st) V.x[s] = V.t[s];
+      for (int s = tid; s < n; s += nthr) V.x[s] = V.t[s];
       __syncthreads();
     }
   }
   for (int l = last - 1; l >= l0; --l) {
-    const View<T> V = view<T>(c, which, r, l);
-    const View<T> C = view<T>(c, which, r, l + 1);
-    for (long long s = s0; s < V.n(); s += st) prolong_at<T>(V, C, s);
+    const View<T> V = small_view<T, SMEM>(c, which, r, l0, l, sm);
+    const View<T> C = small_view<T, SMEM>(c, which, r, l0, l + 1, sm);
+    const int n = (int)V.n();
+    {
+      Walk w(tid, nthr, V.nx, V.ny);
+      for (int s = tid; s < n; s += nthr, w.next()) prolong_xyz<T>(V, C, w.X, w.Y, w.Z, s);
+    }
     __syncthreads();
-    for (long long s = s0; s < V.n(); s += st) sweep_at<T>(V, V.t, V.x, s);
+    {
+      Walk w(tid, nthr, V.nx, V.ny);
+      for (int s = tid; s < n; s += nthr, w.next()) sweep_xyz<T>(V, V.t, V.x, w.X, w.Y, w.Z, s);
+    }
     __syncthreads();
   }
+  if (SMEM) {
+    const View<T> G = view<T>(c, which, r, l0), V = small_view<T, true>(c, which, r, l0, l0, sm);
+    const int n = (int)V.n();
+    for (int s = tid; s < n; s += nthr) G.x[s] = V.x[s];
+  }
+}
+
+// The sub-cycle of the single-block levels, one block per replicate, in
+// global memory.
+template <typename T>
+__global__ void __launch_bounds__(kSmallThreads) k_mg_small(Ctx c, int which) {
+  HCA_COUNT_KERNEL(c);
+  small_cycle<T, false>(c, which, blockIdx.x, threadIdx.x, blockDim.x, nullptr, false);
+}
+
+// ------------------------------------- coarse levels in one cooperative launch --
+// Grid-wide barrier of a cooperative launch (every block is resident).
+// PassSync::bar_count counts the arrivals of the launch: barrier k of the
+// launch opens when it reaches (k + 1) * gridDim.x, and the last block to
+// leave the kernel (grid_exit) sets it back to 0 for the next launch.  A
+// wait gives up after kBarrierTimeoutNs of device time and records
+// SYNC_ERR_TIMEOUT (the host returns HCA_ERR_TIMEOUT and the step sets the
+// counter back to 0), so no kernel waits forever; later barriers and
+// launches then return at once.
+constexpr unsigned long long kBarrierTimeoutNs = 1000000000ull;   // 1 s
+
+__device__ __forceinline__ unsigned long long device_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ bool grid_barrier(PassSync* sy, int k) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (*(volatile int*)&sy->error == SYNC_ERR_TIMEOUT) {
+      ok = 0;
+    } else {
+      const unsigned target = (unsigned)(k + 1) * gridDim.x;
+      __threadfence();   // this block's writes before its arrival
+      atomicAdd(&sy->bar_count, 1u);
+      if (ld_acquire_gpu(&sy->bar_count) < target) {
+        const unsigned long long t0 = device_ns();
+        while (ld_acquire_gpu(&sy->bar_count) < target) {
+          if (device_ns() - t0 > kBarrierTimeoutNs) {
+            atomicExch(&sy->error, SYNC_ERR_TIMEOUT);
+            ok = 0;
+            break;
+          }
+          __nanosleep(20);
+        }
+      }
+      __threadfence();   // the other blocks' writes before this block reads on
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Leave a launch that passed nbar barriers: the last block out resets the
+// arrival counter.
+__device__ __forceinline__ void grid_exit(PassSync* sy, int nbar) {
+  if (threadIdx.x == 0 && atomicAdd(&sy->bar_count, 1u) == (unsigned)(nbar + 1) * gridDim.x - 1u)
+    atomicExch(&sy->bar_count, 0u);
+}
+
+// Levels 1 .. nlev-1 of one V-cycle in one cooperative launch: the
+// restrictions l -> l + 1 for l = 1 .. small-1, the single-block sub-cycle
+// (block b takes replicates b, b + grid, ...; its levels in dynamic shared
+// memory when small_smem > 0), then the post-sweeps l = small-1 .. 1, with a
+// grid barrier between consecutive phases.  Each phase is the loop body of
+// the corresponding per-level kernel over this launch's threads, so the
+// result is bit-identical to the per-level launches.  rows_ok: bit l selects
+// the row-vector form of level l (as for the per-level kernels).
+template <typename T, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_mg_coarse(Ctx c, int which, int small, unsigned rows_ok, int use_smem) {
+  HCA_COUNT_KERNEL(c);
+  extern __shared__ __align__(16) unsigned char mg_smem[];
+  T* sm = (T*)mg_smem;
+  const long long t0 = grid_t0(), st = grid_st();
+  const bool multi = c.n_reps > 1;
+  if (*(volatile int*)&c.sync->error == SYNC_ERR_TIMEOUT) return;
+  // the single-block levels' constant arrays start moving into shared memory
+  // while the restrictions run
+  const bool pre = use_smem && blockIdx.x < c.n_reps;
+  if (pre) small_prefetch<T>(c, which, blockIdx.x, threadIdx.x, blockDim.x, sm);
+  int k = 0;
+  for (int l = 1; l < small; ++l) {
+    if (rows_ok >> l & 1u) restrict_rows<T>(c, which, l, t0, st);
+    else if (multi) restrict_sites<T, true>(c, which, l, t0, st);
+    else restrict_sites<T, false>(c, which, l, t0, st);
+    if (!grid_barrier(c.sync, k++)) return;
+  }
+  for (int r = blockIdx.x; r < c.n_reps; r += gridDim.x) {
+    if (use_smem) small_cycle<T, true>(c, which, r, threadIdx.x, blockDim.x, sm, pre && r == (int)blockIdx.x);
+    else small_cycle<T, false>(c, which, r, threadIdx.x, blockDim.x, nullptr, false);
+    __syncthreads();
+  }
+  if (!grid_barrier(c.sync, k++)) return;
+  for (int l = small - 1; l >= 1; --l) {
+    if (rows_ok >> l & 1u) post_rows<T>(c, which, l, t0, st);
+    else if (multi) post_sites<T, true>(c, which, l, t0, st);
+    else post_sites<T, false>(c, which, l, t0, st);
+    if (l > 1 && !grid_barrier(c.sync, k++)) return;
+  }
+  grid_exit(c.sync, k);
 }
 
 // ------------------------------------------ level-0 post-smoothing + rho --
@@ -873,6 +1129,16 @@ __global__ void __maxnreg__(64) k_mg_post0(Ctx c, int which, const T* __restrict
   });
 }
 
+// Launch shapes of the cooperative coarse-level kernel: 0 = 256 threads with
+// up to 255 registers (one block per SM), 1 = 256 threads, 128 registers (two
+// blocks per SM), 2 = 512 threads, 128 registers (one block per SM).
+template <typename T>
+const void* coarse_fn(int cfg) {
+  return cfg == 1 ? (const void*)k_mg_coarse<T, 256, 2>
+                  : cfg == 2 ? (const void*)k_mg_coarse<T, 512, 1> : (const void*)k_mg_coarse<T, 256, 1>;
+}
+inline int coarse_threads(int cfg) { return cfg == 2 ? 512 : 256; }
+
 int grid_for(long long n) {
   const long long b = (n + kMgThreads - 1) / kMgThreads;
   return (int)std::max(1LL, std::min(b, 152LL * 16));
@@ -909,7 +1175,14 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
     const int nb = (int)std::max(1LL, std::min((H.nrowitems + 127) / 128, 152LL * 16));
     k_mg_restrict0_rows<T><<<nb, 128, 0, s>>>(c, which);
   }
-  if (all || part == 1) {
+  if ((all || part == 1) && H.coop_blocks > 0) {
+    Ctx cc = c;
+    int wh = which, sm = H.small, use = H.small_smem > 0;
+    unsigned rows = H.rows_ok;
+    void* args[] = {&cc, &wh, &sm, &rows, &use};
+    (void)cudaLaunchCooperativeKernel(coarse_fn<T>(H.coop_cfg), dim3(H.coop_blocks), dim3(coarse_threads(H.coop_cfg)),
+                                      args, (size_t)H.small_smem, s);
+  } else if (all || part == 1) {
     for (int l = 1; l < H.small; ++l) {
       if (H.rows_ok >> l & 1u)   // 128 threads: ~28 vector loads per thread in flight
         k_mg_restrict_rows<T><<<(int)std::min((H.restr_items[l] + 127) / 128, 152LL * 16), 128, 0, s>>>(c, which, l);
@@ -939,10 +1212,62 @@ void mg_setup_t(const Ctx& c, int which, const MGHost& H) {
   for (int l = 1; l < H.nlev; ++l) k_mg_diag<T><<<grid_for(H.ntot[l]), kMgThreads, 0, c.stream>>>(c, which, l);
 }
 
+// The launch geometry of the cooperative coarse-level kernel.
+template <typename T>
+int coop_config_t(MGHost& H, int sm_count, long long smem_bytes) {
+  H.coop_blocks = 0;
+  H.small_smem = 0;
+  const char* env = std::getenv("HCA_MG_COOP");
+  if (env && env[0] == '0') return 0;
+  int dev = 0, coop = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || !coop) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  // the single-block levels go to shared memory when they fit in one block's
+  // opt-in maximum; else they stay in global memory
+  const int smem = smem_bytes <= optin ? (int)smem_bytes : 0;
+  // launch shape (HCA_MG_COOP_CFG=0, 1, 2 selects another one)
+  const char* cs = std::getenv("HCA_MG_COOP_CFG");
+  const int cfg = (cs && cs[0] >= '0' && cs[0] <= '2') ? cs[0] - '0' : 0;
+  const void* fn = coarse_fn<T>(cfg);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, coarse_threads(cfg), smem) != cudaSuccess ||
+      per_sm < 1) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  H.coop_blocks = per_sm * sm_count;
+  H.small_smem = smem;
+  H.coop_cfg = cfg;
+  return 0;
+}
+
 }  // namespace
 
 int vcycle_launches(const MGHost& H, bool scale) {
+  if (H.nlev > 1 && H.coop_blocks > 0) return 3 + (scale ? 1 : 0);
   return (H.nlev == 1 ? MG_NU_COARSE : 2 * H.small + 1) + (scale ? 1 : 0);
+}
+
+// Choose the coarse-level launch form of a hierarchy (after H.small and
+// H.rows_ok are known): one cooperative launch when the device supports it
+// (HCA_MG_COOP=0 keeps one launch per level).  smem_bytes: the largest
+// shared-memory footprint of any replicate's single-block levels.
+void mg_coop_config(MGHost& H, bool fp64, int sm_count, long long smem_bytes) {
+  if (H.nlev <= 1) {
+    H.coop_blocks = 0;
+    H.small_smem = 0;
+    return;
+  }
+  if (fp64) coop_config_t<double>(H, sm_count, smem_bytes);
+  else coop_config_t<float>(H, sm_count, smem_bytes);
 }
 // (H.small: the deepest grid-kernel level + 1 over the batch)
 
@@ -958,6 +1283,7 @@ void launch_vcycle(const Ctx& c, int which, bool fp64, const MGHost& H, int part
 
 int vcycle_part_launches(const MGHost& H, int part, bool scale) {
   if (H.nlev == 1) return part == 0 ? MG_NU_COARSE + (scale ? 1 : 0) : 0;
+  if (part == 1 && H.coop_blocks > 0) return 1;
   return part == 0 ? 1 + (scale ? 1 : 0) : part == 1 ? 2 * (H.small - 1) + 1 : 1;
 }
 

@@ -1,0 +1,102 @@
+"""The coarse levels of the V-cycle in one cooperative launch (grid barriers
+between levels, the single-block levels in shared memory) against one launch
+per level (HCA_MG_COOP=0, read at handle creation): both run the same per-site
+arithmetic in the same order, so z = M r, whole solves and coupled steps must
+agree bit for bit, in FP64 and FP32, for single lattices and batches.  The
+V-cycle itself is compared with the oracle in test_gpu_mg.py.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+from gpu_helpers import make_pair, random_states
+from paper_2105_00448_gb300 import hca
+from synth import make_maps
+
+pytestmark = pytest.mark.gpu
+
+# grid-kernel coarse levels (row-vector and per-site forms), a flat lattice,
+# odd extents, and a lattice whose level 1 is already a single-block level
+SHAPES = [(24, 40, 56), (64, 64, 64), (1, 48, 70), (17, 23, 31), (40, 36, 44), (16, 16, 16)]
+
+
+def _with_coop(flag, fn):
+    old = os.environ.get("HCA_MG_COOP")
+    os.environ["HCA_MG_COOP"] = "1" if flag else "0"
+    try:
+        return fn()
+    finally:
+        if old is None:
+            del os.environ["HCA_MG_COOP"]
+        else:
+            os.environ["HCA_MG_COOP"] = old
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("which", [0, 1])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_vcycle_coop_equals_per_level_launches(shape, which, precision):
+    rng = np.random.default_rng(31)
+    st = random_states(shape, rng)
+    K = rng.uniform(0.0, 20.0, shape)
+    r = rng.standard_normal(shape)
+
+    def run():
+        sim, _, _ = make_pair(shape, precision, seed=2, n_drugs=1, preconditioner=hca.HCA_PC_MG, picard_maxit=1)
+        sim.set_states(st)
+        sim.set_field(hca.FIELD_O2, K)
+        z = sim.apply_preconditioner(which, r)
+        sim.close()
+        return z
+
+    z_coop = _with_coop(True, run)
+    z_levels = _with_coop(False, run)
+    assert np.array_equal(z_coop, z_levels)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_coupled_steps_coop_equal_per_level_launches(precision):
+    n = 48
+
+    def run():
+        maps = make_maps(n, n, n, corr_len=4.0, seed=5)
+        sim = hca.Sim.create(n, n, n, maps.p_cell, maps.perf, maps.p_vessel, precision=precision, n_drugs=2,
+                             seed=5, preconditioner=hca.HCA_PC_MG)
+        sim.step(3)
+        out = (sim.states(), sim.field(hca.FIELD_O2), sim.field(hca.FIELD_DRUG0), sim.field(hca.FIELD_DRUG1),
+               sim.stats())
+        sim.close()
+        return out
+
+    a = _with_coop(True, run)
+    b = _with_coop(False, run)
+    assert np.array_equal(a[0], b[0])
+    for k in (1, 2, 3):
+        assert np.array_equal(a[k], b[k])
+    assert a[4]["o2_iterations"] == b[4]["o2_iterations"]
+    assert a[4]["drug_iterations"] == b[4]["drug_iterations"]
+
+
+def test_batch_coop_equals_per_level_launches():
+    sizes = [(20, 24, 28), (33, 17, 40), (48, 48, 48)]
+
+    def run():
+        cfgs, maps = [], []
+        for i, (nz, ny, nx) in enumerate(sizes):
+            m = make_maps(nx, ny, nz, corr_len=3.0, seed=10 + i)
+            maps.append((m.p_cell, m.perf, m.p_vessel))
+            cfgs.append(hca.make_config(nx, ny, nz, precision="f32", n_drugs=1, seed=10 + i,
+                                        preconditioner=hca.HCA_PC_MG))
+        sim = hca.Sim(cfgs, maps, batch=True)
+        sim.step(2)
+        out = [(sim.states(i), sim.field(hca.FIELD_O2, i), sim.field(hca.FIELD_DRUG0, i)) for i in range(len(sizes))]
+        sim.close()
+        return out
+
+    a = _with_coop(True, run)
+    b = _with_coop(False, run)
+    for x, y in zip(a, b):
+        for u, v in zip(x, y):
+            assert np.array_equal(u, v)
