@@ -48,6 +48,17 @@ CORR_LEN = 8.0
 #   1/8-size coarse correction and writes z; ODE reads state, K and updates phi, P, Vc
 BYTES_PER_SITE = {"pass_a": 20, "pass_b": 24, "setup": 17, "residual": 24, "ode": 29,
                   "mg_restrict0": 16.5, "mg_post0": 16.5}
+# the method's minimum per site where this design moves more: CG pass A reads
+# z, d, p_old and writes p (16 B); storing q = A p for pass B adds 4 B
+BYTES_MIN_PER_SITE = {**BYTES_PER_SITE, "pass_a": 16}
+# step-level algorithmic bytes per lattice site (FP32 storage): set-up and
+# solve start-up, ODE and CA 70 B, 13 B per defect-correction residual sweep,
+# 40 B per CG iteration (two-pass minimum), plus per V-cycle the lattice's
+# first sweep + restriction and prolongation + last sweep (33 B) and the
+# coarse levels (33 B per coarse site: restriction reads rhs, omega/d, d and
+# writes the next level's rhs; the post-sweep reads rhs, omega/d, d, the
+# coarser correction and writes x)
+STEP_FIXED_B, STEP_DC_B, STEP_IT_B, VCYCLE_LATTICE_B, VCYCLE_COARSE_B = 70, 13, 40, 33, 33
 
 
 def metric_name(edge: int = N_EDGE) -> str:
@@ -172,7 +183,7 @@ def kernel_source_sha(root: str = ROOT) -> str:
 
 
 # ------------------------------------------------------------ oracle ---
-def oracle_sample(steps: int, edge: int = SAMPLE_EDGE):
+def oracle_sample(steps: int, edge: int = SAMPLE_EDGE, seed: int = WORKLOAD["seed"]):
     """Time `steps` oracle steps on an edge^3 sample of the workload (seconds)."""
     from oracle import params as Pm
     from oracle.model import OracleSim
@@ -181,8 +192,9 @@ def oracle_sample(steps: int, edge: int = SAMPLE_EDGE):
     # the oracle's own solver (Jacobi-preconditioned textbook CG); the
     # library-only settings (preconditioner) have no oracle counterpart
     params = {k: v for k, v in WORKLOAD.items() if k in Pm.Config.__dataclass_fields__}
+    params["seed"] = seed
     cfg = Pm.Config(nx=edge, ny=edge, nz=edge, **params)
-    maps = make_maps(edge, edge, edge, corr_len=CORR_LEN, seed=WORKLOAD["seed"])
+    maps = make_maps(edge, edge, edge, corr_len=CORR_LEN, seed=seed)
     sim = OracleSim(cfg, maps.p_cell, maps.perf, maps.p_vessel)
     times = []
     for _ in range(steps):
@@ -195,6 +207,71 @@ def oracle_sample(steps: int, edge: int = SAMPLE_EDGE):
 def cpu_cores_used() -> int:
     # numpy element-wise kernels and the oracle's Python loops run on one thread
     return 1
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_replicate(args):
+    """One spawned process: `steps` oracle steps of replicate `seed` (seconds)."""
+    steps, edge, seed = args
+    return sum(oracle_sample(steps, edge, seed))
+
+
+def oracle_all_cores(steps: int, edge: int = SAMPLE_EDGE):
+    """The oracle on every host core: one independent replicate (seed + i) per
+    core in spawned processes (a pool forked after CUDA initialisation would
+    hang), timed by the wall clock around the pool.  Returns (site-steps/s,
+    processes, wall seconds)."""
+    import multiprocessing as mp
+
+    n = host_cores()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(n) as pool:
+        pool.map(_oracle_replicate, [(0, 8, 0)] * n)   # start-up (imports) outside the timed region
+        t0 = time.perf_counter()
+        pool.map(_oracle_replicate, [(steps, edge, WORKLOAD["seed"] + i) for i in range(n)])
+        wall = time.perf_counter() - t0
+    return n * edge ** 3 * steps / wall, n, wall
+
+
+def cpu_baseline_record(steps: int):
+    """The oracle timed on one core and on all host cores (64^3 samples)."""
+    times = oracle_sample(steps)
+    one = SAMPLE_EDGE ** 3 * len(times) / sum(times)
+    allv, n, wall = oracle_all_cores(steps)
+    return {"value": one, "unit": "site-steps/s", "cores": cpu_cores_used(), "kind": "oracle",
+            "sample": f"{len(times)} coupled steps of the FP64 oracle (Jacobi-PCG) on a {SAMPLE_EDGE}^3 lattice with "
+                      f"the 256^3 workload's recipe and parameters, one process ({sum(times):.1f} s)",
+            "all_cores": {"value": allv, "unit": "site-steps/s", "cores": n, "kind": "oracle",
+                          "sample": f"{n} independent {SAMPLE_EDGE}^3 replicates (seeds {WORKLOAD['seed']}.."
+                                    f"{WORKLOAD['seed'] + n - 1}), {steps} steps each, one spawned process per host "
+                                    f"core, wall {wall:.1f} s"}}
+
+
+def step_roofline(prof, steps: int, sites: int, ms_per_step: float, level_fraction: float):
+    """Step-level HBM roofline: the method's algorithmic bytes of one step
+    (counts of CG iterations, defect-correction sweeps and V-cycles from the
+    profiled steps) over the measured step time."""
+    peak, peak_kind = measured_peak_hbm()
+    n_it = prof["pass_a"]["launches"] / steps
+    n_dc = prof["residual"]["launches"] / steps
+    n_vc = prof["mg_post0"]["launches"] / steps
+    terms = {"fixed": STEP_FIXED_B, "defect_correction": STEP_DC_B * n_dc, "cg_iterations": STEP_IT_B * n_it,
+             "vcycle_lattice": VCYCLE_LATTICE_B * n_vc, "vcycle_coarse": VCYCLE_COARSE_B * level_fraction * n_vc}
+    per_site = sum(terms.values())
+    achieved = per_site * sites / (ms_per_step * 1e-3) / 1e9
+    cg_only = (terms["fixed"] + terms["defect_correction"] + terms["cg_iterations"]) * sites / (ms_per_step * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+            "frac": achieved / peak, "bytes_per_site": per_site, "terms_bytes_per_site": terms,
+            "counts_per_step": {"cg_iterations": n_it, "dc_sweeps": n_dc, "vcycles": n_vc},
+            "frac_without_vcycle": cg_only / peak,
+            "formula": "70 + 13 n_dc + 40 n_it + n_vc (33 + 33 f_coarse) B/site x sites / step time; f_coarse = "
+                       "coarse-level sites per lattice site"}
 
 
 def run_reference(args):
@@ -211,7 +288,10 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "site-steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(timed),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(),
+            "data": "synthetic",
+            "config": {**workload_config(), "solver": "the FP64 oracle's Jacobi-preconditioned CG (no multigrid)",
+                       "precision": "f64", "sample_lattice": [SAMPLE_EDGE] * 3,
+                       "l2": "CPU run (host cores): no GPU caches involved"},
             "cpu_baseline": {"value": value, "unit": "site-steps/s", "cores": cpu_cores_used(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "site-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -244,6 +324,16 @@ def job_value(world: int, sites: int, steps: int, t_ms: float) -> float:
 
 
 # --------------------------------------------------------------- GPU ---
+def coarse_level_fraction(n: int) -> float:
+    """Sites of the multigrid coarse levels per lattice site (edges halved,
+    rounding up, until a level has at most 512 sites)."""
+    tot, m = 0, n
+    while m ** 3 > 512:
+        m = (m + 1) // 2
+        tot += m ** 3
+    return tot / n ** 3
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -269,6 +359,7 @@ def run_gpu(args):
     stream = torch.cuda.Stream()
     cfg = hca.make_config(n, n, n, stream=stream.cuda_stream, **params)
     sim = hca.Sim(cfg, (maps.p_cell, maps.perf, maps.p_vessel))
+    level_frac = coarse_level_fraction(n)
     if args.warmup:
         sim.step(args.warmup, allow_noconv=True)
     torch.cuda.synchronize()
@@ -305,8 +396,9 @@ def run_gpu(args):
     peak, peak_kind = measured_peak_hbm()
     dom = max(BYTES_PER_SITE, key=lambda k: prof[k]["ms"])
     avg_ms = prof[dom]["ms"] / max(1, prof[dom]["launches"])
-    bytes_per_launch = BYTES_PER_SITE[dom] * sites
+    bytes_per_launch = BYTES_MIN_PER_SITE[dom] * sites
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+    design_bytes = BYTES_PER_SITE[dom] * sites
     tr = traffic_record(dom)
     kernel_names = {"pass_a": "k_pass_a<float>", "pass_b": "k_pass_b<float>", "setup": "k_setup<float>",
                     "residual": "k_dc_residual", "ode": "k_ode<float>", "mg_restrict0": "k_mg_restrict0_rows<float>",
@@ -315,6 +407,8 @@ def run_gpu(args):
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": tr * sites if tr is not None else None,
                 "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
+                "design_bytes_per_launch": design_bytes,
+                "frac_design_bytes": design_bytes / (avg_ms * 1e-3) / 1e9 / peak,
                 "timing": f"CUDA events around each launch over {args.profile_steps} profiled steps "
                           f"following the timed region"}
     # time share of each kernel class over the timed region
@@ -325,17 +419,15 @@ def run_gpu(args):
         e2e = run_e2e(args, hca, make_maps, np, torch) if not args.skip_e2e else None
         cpu = None
         if world == 1 and not args.skip_cpu:
-            times = oracle_sample(args.cpu_steps)
-            cpu_val = SAMPLE_EDGE ** 3 * len(times) / sum(times)
-            cpu = {"value": cpu_val, "unit": "site-steps/s", "cores": cpu_cores_used(), "kind": "oracle",
-                   "sample": f"{len(times)} coupled steps of the FP64 oracle on a {SAMPLE_EDGE}^3 lattice with "
-                             f"the 256^3 workload's recipe and parameters ({sum(times):.1f} s)"}
+            cpu = cpu_baseline_record(args.cpu_steps)
         line = {"metric": metric_name(args.edge), "value": value, "unit": "site-steps/s", "n_gpus": world,
                 "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {**workload_config(args.edge), "parallelism": f"replicas{world}" if world > 1 else "single"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "roofline": roofline,
+                "roofline_step": step_roofline(prof, args.profile_steps, sites, t_ms / args.steps, level_frac),
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clocks,
                 "cg_iterations_per_step": prof["pass_a"]["launches"] / args.profile_steps,
                 "last_step": {"o2_iterations": stats["o2_iterations"], "drug_iterations": stats["drug_iterations"][:2],

@@ -83,6 +83,14 @@ extern "C" {
 #define HCA_FIELD_VEGFC (1u << 6)  /* intracellular VEGF, Vc */
 #define HCA_FIELD_PERF (1u << 7)   /* perfusion map (the vessel-exchange scale) */
 #define HCA_FIELD_VEGF (1u << 8)   /* extracellular VEGF, V (ug/mL; vegf = 1) */
+/* read only, FP32 handles with defect correction: the low-order FP32 words of
+ * the solved fields (the solution is the two-word sum hi + lo, the FP32
+ * field above being hi; Section 2.4.1's rtol-1e-8 solves are met by hi + lo) */
+#define HCA_FIELD_O2_LO (1u << 9)
+#define HCA_FIELD_DRUG0_LO (1u << 10)
+#define HCA_FIELD_DRUG1_LO (1u << 11)
+#define HCA_FIELD_DRUG2_LO (1u << 12)
+#define HCA_FIELD_VEGF_LO (1u << 13)
 
 /* stages for hca_stage; HCA_STAGE_ALL runs one full step (as hca_step(h, 1)) */
 #define HCA_STAGE_O2 (1u << 0)
@@ -281,9 +289,15 @@ int hca_create_batch(int32_t n, const hca_config* cfgs, const float* const* p_ce
                      const float* const* perf, const float* const* p_vessel,
                      int32_t maps_on_device, hca_handle** out);
 
-/* Advance all replicates by n_steps full steps.  Returns HCA_ERR_NOCONV if
- * any solve of the last step hit maxit (its last iterate is kept and the
- * step completed), HCA_ERR_NONFINITE if a residual norm became NaN/Inf. */
+/* Advance all replicates by n_steps full steps.  One step is the loop body
+ * of Algorithm 1: plasma levels (Eq. intrachemo3), the oxygen solve
+ * (Eq. oxygen, Section 2.4.1), the drug solves (Eq. chemo), the cell ODEs
+ * (Eqs. cellcycle, odep53, odevegf; Section 2.4.2) and the CA update
+ * (Sections 2.2.1, 2.5; Eq. 1).  Work is queued on the handle's stream (one
+ * captured graph launch per step).  Returns HCA_ERR_NOCONV if any solve of
+ * the last step hit maxit (its last iterate is kept and the step completed),
+ * HCA_ERR_NONFINITE if a residual norm became NaN/Inf, HCA_ERR_TIMEOUT if a
+ * bounded device wait gave up. */
 int hca_step(hca_handle* h, int32_t n_steps);
 
 /* Run selected stages of one step (HCA_STAGE_* mask) in their fixed order
@@ -293,7 +307,12 @@ int hca_stage(hca_handle* h, uint32_t stage_mask);
 
 /* Copy fields of replicate rep to dst: the selected fields one after another
  * in increasing mask-bit order, each nx*ny*nz elements of the handle's
- * precision.  dst_bytes must be at least that size (else HCA_ERR_ARG). */
+ * precision, x fastest (site x + nx*(y + ny*z)); dst is caller-owned host or
+ * device memory (any pointer cudaMemcpy accepts) and the call synchronises
+ * the handle's stream.  dst_bytes must be at least that size, and every
+ * selected field must exist in the handle (else HCA_ERR_ARG).  These are the
+ * fields Algorithm 1 carries from one step to the next (Eqs. oxygen, chemo,
+ * cellcycle, odep53, odevegf). */
 int hca_read_fields(hca_handle* h, int32_t rep, uint32_t field_mask, void* dst,
                     size_t dst_bytes, int32_t dst_on_device);
 
@@ -302,7 +321,10 @@ int hca_read_fields(hca_handle* h, int32_t rep, uint32_t field_mask, void* dst,
 int hca_write_fields(hca_handle* h, int32_t rep, uint32_t field_mask, const void* src,
                      size_t src_bytes, int32_t src_on_device);
 
-/* Copy / overwrite the uint8 lattice states (HCA_EMPTY .. HCA_STROMA) of rep. */
+/* Copy / overwrite the uint8 lattice states (HCA_EMPTY .. HCA_STROMA) of
+ * rep: the CA lattice of Section 2.2 that Algorithm 1 updates, nx*ny*nz
+ * bytes, x fastest; host or device memory, synchronising the handle's
+ * stream; a short buffer or a bad code is HCA_ERR_ARG. */
 int hca_read_states(hca_handle* h, int32_t rep, uint8_t* dst, size_t dst_bytes,
                     int32_t dst_on_device);
 int hca_write_states(hca_handle* h, int32_t rep, const uint8_t* src, size_t src_bytes,
@@ -311,7 +333,10 @@ int hca_write_states(hca_handle* h, int32_t rep, const uint8_t* src, size_t src_
 /* Set / get the step index n (drives plasma levels and the Philox counter). */
 int hca_set_step(hca_handle* h, int64_t step);
 
-/* Statistics of replicate rep after the last step or stage. */
+/* Statistics of replicate rep after the last step or stage: CG iterations,
+ * defect-correction sweeps and true relative residuals of the Section 2.4.1
+ * solves, cell counts per state, kills and divisions of the CA update
+ * (Section 2.5).  Synchronises the handle's stream. */
 int hca_get_stats(hca_handle* h, int32_t rep, hca_stats* out);
 
 /* out = A u for replicate rep, where A is the operator of the next solve

@@ -396,6 +396,12 @@ void* field_ptr(hca_handle* h, uint32_t bit) {
     case HCA_FIELD_VEGFC: return h->ctx.Vc;
     case HCA_FIELD_PERF: return h->ctx.perf;
     case HCA_FIELD_VEGF: return h->vegf ? h->ctx.G[hca::VEGF_SLOT] : nullptr;
+    // low-order words of the FP32 defect-correction fields (read only)
+    case HCA_FIELD_O2_LO: return h->ctx.K_lo;
+    case HCA_FIELD_DRUG0_LO: return h->n_drugs > 0 ? h->ctx.G_lo[0] : nullptr;
+    case HCA_FIELD_DRUG1_LO: return h->n_drugs > 1 ? h->ctx.G_lo[1] : nullptr;
+    case HCA_FIELD_DRUG2_LO: return h->n_drugs > 2 ? h->ctx.G_lo[2] : nullptr;
+    case HCA_FIELD_VEGF_LO: return h->vegf ? h->ctx.G_lo[hca::VEGF_SLOT] : nullptr;
     default: return nullptr;
   }
 }
@@ -1591,12 +1597,12 @@ int hca_stage(hca_handle* h, uint32_t mask) {
 }
 
 int hca_read_fields(hca_handle* h, int32_t rep, uint32_t mask, void* dst, size_t dst_bytes, int32_t dst_on_device) {
-  if (check_rep(h, rep) || !dst || (mask & ~0x1FFu) || !mask) return HCA_ERR_ARG;
+  if (check_rep(h, rep) || !dst || (mask & ~0x3FFFu) || !mask) return HCA_ERR_ARG;
   const RepDesc& r = h->reps_h[rep];
   const size_t es = elem_size(h);
   const size_t per = (size_t)r.nx * r.ny * r.nz;
   size_t k = 0;
-  for (uint32_t bit = 1; bit <= 0x100u; bit <<= 1)
+  for (uint32_t bit = 1; bit <= 0x2000u; bit <<= 1)
     if (mask & bit) {
       if (!field_ptr(h, bit)) return HCA_ERR_ARG;
       ++k;
@@ -1604,7 +1610,7 @@ int hca_read_fields(hca_handle* h, int32_t rep, uint32_t mask, void* dst, size_t
   if (dst_bytes < k * per * es) return HCA_ERR_ARG;
   (void)dst_on_device;
   size_t slot = 0;
-  for (uint32_t bit = 1; bit <= 0x100u; bit <<= 1) {
+  for (uint32_t bit = 1; bit <= 0x2000u; bit <<= 1) {
     if (!(mask & bit)) continue;
     int rc = copy_field(h, rep, field_ptr(h, bit), es, dst, true, slot * per);
     if (rc) return rc;

@@ -11,11 +11,14 @@
 //
 // CG is carried in the preconditioned residual z = r / d instead of r, so
 // the direction update p = z + beta p needs no division at neighbour sites:
-//   pass A: p = z + beta p;  q = A p (q recomputed, not stored);  sigma = p.q
-//   pass B: q = A p;  x += alpha p;  z -= alpha q / d;  rho = r.z = sum d z^2,
-//           |r|^2 = sum (d z)^2
-// HBM traffic per site and iteration: pass A reads z, p, d and writes p;
-// pass B reads p, d, x, z and writes x, z: 10 values = 40 B (FP32).
+//   pass A: p = z + beta p;  q = A p, stored;  sigma = p.q
+//   pass B: x += alpha p;  z -= alpha q / d;  rho = r.z = sum d z^2,
+//           |r|^2 = sum (d z)^2  (multigrid form: r -= alpha q, |r|^2; the
+//           V-cycle then forms z = M r and rho)
+// HBM traffic per site and iteration: pass A reads z, p, d and writes p and
+// q (20 B, FP32); pass B reads p, q, x, z (+ d, Jacobi form) and writes x, z
+// (24-28 B): 44 B, against the two-pass minimum of 40 B in which pass B
+// re-forms A p from p's neighbour rows instead of streaming q.
 // Neighbour rows are re-read through L1/L2.  Pass A rebuilds the new
 // direction at neighbour sites from the old one, so the old and new
 // directions live in two buffers that swap roles every iteration (an in-place
@@ -28,6 +31,12 @@
 namespace hca {
 namespace {
 
+// a + k p for the drug reaction: in FP32 rounded after the product and after
+// the sum (no fused multiply-add), so the stored FP32 coefficients of the
+// system are the plain IEEE result of these operations.
+__device__ __forceinline__ float add_prod(float a, float k, float p) { return __fadd_rn(a, __fmul_rn(k, p)); }
+__device__ __forceinline__ double add_prod(double a, double k, double p) { return a + k * p; }
+
 // Reaction coefficient a of the operator at one site (d = c n + a).
 template <typename T, int KIND>
 __device__ __forceinline__ T reaction_site(const RepDesc& rd, int which, uint8_t s, T K_prev, T pf) {
@@ -39,7 +48,7 @@ __device__ __forceinline__ T reaction_site(const RepDesc& rd, int which, uint8_t
   } else {
     const int dd = which - 1;
     a = (T)rd.base_drug[dd];
-    if (is_vessel(s)) a += (T)rd.kappa[dd] * pf;
+    if (is_vessel(s)) a = add_prod(a, (T)rd.kappa[dd], pf);
     if (is_cancer(s)) a += (T)rd.uptake[dd];
   }
   return a;
@@ -57,7 +66,7 @@ __device__ __forceinline__ T diag_site(const RepDesc& rd, int which, int n_nb, u
   } else {
     const int dd = which - 1;
     a = (T)rd.base_drug[dd];
-    if (is_vessel(s)) a += (T)rd.kappa[dd] * pf;
+    if (is_vessel(s)) a = add_prod(a, (T)rd.kappa[dd], pf);
     if (is_cancer(s)) a += (T)rd.uptake[dd];
   }
   return cpl * (T)n_nb + a;
@@ -699,8 +708,8 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
                   B.a[k] = SRC.a[k] + (o2t ? xb32 : 0.f);
                 } else {
                   if (vegf) SRC.a[k] = is_consumer(s) ? av * VC.a[k] : 0.f;
-                  else SRC.a[k] = is_vessel(s) ? (float)rd.kappa[which - 1] * PF.a[k] * G0 : 0.f;
-                  B.a[k] = xb32 + SRC.a[k];
+                  else SRC.a[k] = is_vessel(s) ? __fmul_rn(__fmul_rn((float)rd.kappa[which - 1], PF.a[k]), G0) : 0.f;
+                  B.a[k] = __fadd_rn(xb32, SRC.a[k]);
                 }
               }
             }

@@ -48,6 +48,12 @@ FIELD_P53 = 1 << 5
 FIELD_VEGFC = 1 << 6
 FIELD_PERF = 1 << 7
 FIELD_VEGF = 1 << 8
+# low-order words of the FP32 defect-correction fields (read only)
+FIELD_O2_LO = 1 << 9
+FIELD_DRUG0_LO = 1 << 10
+FIELD_DRUG1_LO = 1 << 11
+FIELD_DRUG2_LO = 1 << 12
+FIELD_VEGF_LO = 1 << 13
 FIELD_DRUG = (FIELD_DRUG0, FIELD_DRUG1, FIELD_DRUG2)
 
 STAGE_O2 = 1 << 0

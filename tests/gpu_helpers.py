@@ -37,17 +37,21 @@ def operator_scale(coupling, reaction, u):
     return float(np.max(np.abs(reaction) * np.abs(u)) + coupling * 7.0 * np.max(np.abs(u)))
 
 
-def oracle_counts(args):
-    """One oracle replicate of the coupled run (for a spawn process pool):
-    (seed, edge, steps, corr_len, params) -> (final counts per state code,
-    kills, divisions summed over the steps)."""
+def oracle_trajectory(args):
+    """One oracle replicate of the coupled run, step by step (for a spawn
+    process pool): (seed, edge, steps, corr_len, params) -> int64 array
+    (steps, 8): the count of each state code after every step, then that
+    step's kills and divisions."""
     seed, edge, steps, corr_len, params = args
     from oracle.model import OracleSim
 
     cfg = Pm.Config(nx=edge, ny=edge, nz=edge, seed=seed, **params)
     maps = make_maps(edge, edge, edge, corr_len=corr_len, seed=seed)
     sim = OracleSim(cfg, maps.p_cell, maps.perf, maps.p_vessel)
-    sim.step(steps)
-    kills = sum(h.kills for h in sim.history)
-    divisions = sum(h.divisions for h in sim.history)
-    return np.bincount(sim.state.reshape(-1), minlength=6).astype(np.int64), kills, divisions
+    out = np.zeros((steps, 8), dtype=np.int64)
+    for t in range(steps):
+        sim.step(1)
+        h = sim.history[-1]
+        out[t, :6] = np.bincount(sim.state.reshape(-1), minlength=6)
+        out[t, 6], out[t, 7] = h.kills, h.divisions
+    return out

@@ -60,3 +60,29 @@ def test_labels_follow_the_lattice_edge():
     assert bench.metric_name(512) == "lattice site-steps/s at 512^3 coupled"
     cfg = bench.workload_config(512)
     assert cfg["lattice"] == [512] * 3 and cfg["workload"].startswith("512^3")
+
+
+def test_coarse_level_fraction_counts_the_hierarchy():
+    # 256 -> 128 -> 64 -> 32 -> 16 -> 8 (512 sites: the coarsest level)
+    assert bench.coarse_level_fraction(256) == (128 ** 3 + 64 ** 3 + 32 ** 3 + 16 ** 3 + 8 ** 3) / 256 ** 3
+    # odd extents round up: 9 -> 5 (125 sites)
+    assert bench.coarse_level_fraction(9) == 125 / 729
+    assert bench.coarse_level_fraction(8) == 0.0
+
+
+def test_step_roofline_follows_its_formula():
+    steps, sites, ms = 2, 1000, 4.0
+    prof = {"pass_a": {"launches": 20, "ms": 0.0}, "residual": {"launches": 6, "ms": 0.0},
+            "mg_post0": {"launches": 26, "ms": 0.0}}
+    r = bench.step_roofline(prof, steps, sites, ms, 0.125)
+    per_site = 70 + 13 * 3 + 40 * 10 + 13 * (33 + 33 * 0.125)
+    assert abs(r["bytes_per_site"] - per_site) < 1e-9
+    assert abs(r["achieved"] - per_site * sites / 4e-3 / 1e9) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    assert r["counts_per_step"] == {"cg_iterations": 10, "dc_sweeps": 3, "vcycles": 13}
+    assert r["frac_without_vcycle"] < r["frac"]
+
+
+def test_all_core_oracle_sample_runs_in_spawned_processes():
+    value, n, wall = bench.oracle_all_cores(1, 8)
+    assert n == bench.host_cores() and value > 0 and wall > 0

@@ -1,11 +1,12 @@
 """Pins for the oracle's Philox4x32-10 generator.
 
-Known-answer vectors of the reference Philox distribution are not available
-here, so the generator is pinned by what a counter-based generator must do:
+These CPU tests pin the generator by what a counter-based generator must do:
 uniform, independent outputs across counters, keys and purposes, full
 avalanche of a one-bit counter change, and the exact 24-bit uniform mapping.
-Bit identity with the GPU copy (and with cuRAND's Philox4_32_10) is checked in
-the GPU tests.
+Its output bits are pinned against an independent implementation, cuRAND's
+Philox4_32_10 device generator, in tests/test_gpu_philox_curand.py (needs a
+GPU); bit identity with the library's own copy is checked in the GPU parity
+tests.
 """
 
 import numpy as np
