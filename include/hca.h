@@ -495,6 +495,14 @@ int hca_net_forward_x(hca_net* n, const void* x, float* out);
  * For inspection and per-layer checks. */
 int hca_net_read_activation(hca_net* n, int32_t which, void* dst);
 
+/* Copy the gradient of the last backward pass with respect to one
+ * convolution's output (after its ReLU mask; for enc0..enc2 after the skip
+ * path's gradient is added) into dst (BF16, dense, channels innermost, the
+ * convolution's output lattice): which = 0 enc0, 1 enc1, 2 enc2, 3 enc3,
+ * 4 dec2, 5 dec1, 6 dec0.  Trainable networks only (else HCA_ERR_ARG).  For
+ * per-layer checks. */
+int hca_net_read_gradient(hca_net* n, int32_t which, void* dst);
+
 /* Forward and backward on input x and target t (D*H*W floats): gradients of
  * mean((f - t)^2) into grads (param_count floats, optional) and the loss
  * into *loss (optional); both device pointers.  Needs trainable. */
@@ -521,6 +529,35 @@ int hca_net_gradients(hca_net* n, const hca_config* cfg, const uint8_t* state, c
 int hca_net_train_step(hca_net* n, const hca_config* cfg, const uint8_t* state, const float* perf,
                        const float* K_prev, const float* K_new, double w_mse, double w_res, double lr,
                        float* loss);
+
+/* A training run of the warm-start network in one call (no counterpart in
+ * the paper; the network of this section is trained on fields the solver
+ * itself generates).  The dataset is n_samples oxygen solves, each given by
+ * caller-owned DEVICE arrays of the network's nz*ny*nx lattice: the lattice
+ * states the solve saw (uint8), the perfusion map, K before and K after the
+ * solve (float).  Step t = 0 .. iters-1 draws sample
+ * floor(u_t * n_samples), u_t the 24-bit Philox uniform keyed by
+ * (seed; counter t, 0, 0, 5) (the generator of Section 2.6's streams), and
+ * runs hca_net_train_step on it with learning rate
+ * lr * (lr_final / lr)^(t / (iters - 1)) (geometric decay; lr_final = lr
+ * keeps it constant) and loss w_mse * MSE + w_res * residual loss.  losses
+ * (device, iters floats, optional) receives every step's loss before its
+ * update.  Asynchronous on the network's stream (hca_net_sync waits).
+ * HCA_ERR_ARG for a bad field, an untrainable network or null pointers. */
+typedef struct {
+  uint32_t struct_size;              /* sizeof(hca_train_cfg) */
+  int32_t n_samples;
+  const uint8_t* const* state;       /* host array of n_samples device pointers */
+  const float* const* perf;
+  const float* const* K_prev;
+  const float* const* K_new;
+  int32_t iters;
+  double lr, lr_final;
+  uint64_t seed;
+  double w_mse, w_res;
+  float* losses;
+} hca_train_cfg;
+int hca_train_warmstart(hca_net* n, const hca_config* cfg, const hca_train_cfg* tc);
 
 int hca_net_sync(hca_net* n);
 int hca_net_destroy(hca_net* n);

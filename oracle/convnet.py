@@ -153,40 +153,46 @@ def loss(out, target):
     return float(np.mean((out - target) ** 2))
 
 
-def backward(p, c, gout):
+def backward(p, c, gout, bf16=False, record=None):
     """Gradients of sum(out * gout) with respect to every parameter.
 
-    Uses the (possibly BF16-rounded) weights the forward pass used.
+    Uses the (possibly BF16-rounded) weights the forward pass used.  With
+    bf16=True the gradient with respect to each convolution's output (after
+    the ReLU mask and, on the encoder side, after adding the skip path's
+    gradient) is rounded to BF16 where it is formed: the BF16 network stores
+    these tensors in BF16, as it stores its activations.  record (a dict), if
+    given, receives each convolution's output gradient (as used) and input
+    under the convolution's name, for checks of the weight gradients.
     """
     p = c.get("params", p)
+    r = bf16_round if bf16 else (lambda v: v)
     g = {}
+
+    def wgrad(name, x, gy):
+        if record is not None:
+            record[name] = (x, gy)
+        g[name + ".w"] = conv3_wgrad(x, gy)
+        g[name + ".b"] = gy.sum(axis=(0, 1, 2))
+
     g["head.w"] = c["d0"].reshape(-1, 16).T @ gout.reshape(-1)
     g["head.b"] = np.array([gout.sum()])
-    gd0 = gout[..., None] * p["head.w"]
-    gd0 = gd0 * (c["d0"] > 0)
-    g["dec0.w"] = conv3_wgrad(c["u1"], gd0)
-    g["dec0.b"] = gd0.sum(axis=(0, 1, 2))
+    gd0 = r((gout[..., None] * p["head.w"]) * (c["d0"] > 0))
+    wgrad("dec0", c["u1"], gd0)
     ge0 = gd0.copy()
-    gd1 = up_grad(conv3_dgrad(gd0, p["dec0.w"])) * (c["d1"] > 0)
-    g["dec1.w"] = conv3_wgrad(c["u2"], gd1)
-    g["dec1.b"] = gd1.sum(axis=(0, 1, 2))
+    gd1 = r(up_grad(conv3_dgrad(gd0, p["dec0.w"])) * (c["d1"] > 0))
+    wgrad("dec1", c["u2"], gd1)
     ge1 = gd1.copy()
-    gd2 = up_grad(conv3_dgrad(gd1, p["dec1.w"])) * (c["d2"] > 0)
-    g["dec2.w"] = conv3_wgrad(c["u3"], gd2)
-    g["dec2.b"] = gd2.sum(axis=(0, 1, 2))
+    gd2 = r(up_grad(conv3_dgrad(gd1, p["dec1.w"])) * (c["d2"] > 0))
+    wgrad("dec2", c["u3"], gd2)
     ge2 = gd2.copy()
-    ge3 = up_grad(conv3_dgrad(gd2, p["dec2.w"])) * (c["e3"] > 0)
-    g["enc3.w"] = conv3_wgrad(c["p2"], ge3)
-    g["enc3.b"] = ge3.sum(axis=(0, 1, 2))
-    ge2 = (ge2 + pool_grad(conv3_dgrad(ge3, p["enc3.w"]))) * (c["e2"] > 0)
-    g["enc2.w"] = conv3_wgrad(c["p1"], ge2)
-    g["enc2.b"] = ge2.sum(axis=(0, 1, 2))
-    ge1 = (ge1 + pool_grad(conv3_dgrad(ge2, p["enc2.w"]))) * (c["e1"] > 0)
-    g["enc1.w"] = conv3_wgrad(c["p0"], ge1)
-    g["enc1.b"] = ge1.sum(axis=(0, 1, 2))
-    ge0 = (ge0 + pool_grad(conv3_dgrad(ge1, p["enc1.w"]))) * (c["e0"] > 0)
-    g["enc0.w"] = conv3_wgrad(c["x"], ge0)
-    g["enc0.b"] = ge0.sum(axis=(0, 1, 2))
+    ge3 = r(up_grad(conv3_dgrad(gd2, p["dec2.w"])) * (c["e3"] > 0))
+    wgrad("enc3", c["p2"], ge3)
+    ge2 = r((ge2 + pool_grad(conv3_dgrad(ge3, p["enc3.w"]))) * (c["e2"] > 0))
+    wgrad("enc2", c["p1"], ge2)
+    ge1 = r((ge1 + pool_grad(conv3_dgrad(ge2, p["enc2.w"]))) * (c["e1"] > 0))
+    wgrad("enc1", c["p0"], ge1)
+    ge0 = r((ge0 + pool_grad(conv3_dgrad(ge1, p["enc1.w"]))) * (c["e0"] > 0))
+    wgrad("enc0", c["x"], ge0)
     return g
 
 

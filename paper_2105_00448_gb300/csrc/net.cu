@@ -905,7 +905,11 @@ struct hca_net {
   bf16 *wq = nullptr, *wt = nullptr;
   bf16 *x = nullptr, *e0 = nullptr, *p0 = nullptr, *e1 = nullptr, *p1 = nullptr, *e2 = nullptr, *p2 = nullptr,
        *e3 = nullptr, *d2 = nullptr, *d1 = nullptr, *d0 = nullptr;
+  // gradients with respect to each convolution's output (BF16): g0..g2 the
+  // decoder's (dec0, dec1, dec2), g3 enc3's, ge0..ge2 the encoder's after
+  // the skip path's gradient is added (enc0, enc1, enc2)
   bf16 *g0 = nullptr, *g1 = nullptr, *g2 = nullptr, *g3 = nullptr;
+  bf16 *ge0 = nullptr, *ge1 = nullptr, *ge2 = nullptr;
   float *out = nullptr, *tgt = nullptr, *ru = nullptr, *rg = nullptr, *graw = nullptr, *wpart = nullptr, *bpart = nullptr, *loss = nullptr;
   long long wpart_n = 0;
   int bpart_blocks = 0;
@@ -1103,17 +1107,17 @@ void backward(hca_net* n, cudaStream_t s, const float* target, const float* gbuf
   // enc3: input p2
   wgrad<64, 64, false>(n, s, n->p2, n->g3, D[3], H[3], W[3], n->grads + L.w_off[3]);
   conv<64, 64, 2, false, EPI_RAW>(s, n->g3, Wt(n, 3), nullptr, nullptr, nullptr, n->graw, nullptr, nullptr, D[3], H[3], W[3]);
-  combine<64, 1>(n, s, n->graw, n->e2, n->g2, n->g2, 2, 2);
+  combine<64, 1>(n, s, n->graw, n->e2, n->g2, n->ge2, 2, 2);
   // enc2: input p1
-  wgrad<32, 64, false>(n, s, n->p1, n->g2, D[2], H[2], W[2], n->grads + L.w_off[2]);
-  conv<64, 32, 4, false, EPI_RAW>(s, n->g2, Wt(n, 2), nullptr, nullptr, nullptr, n->graw, nullptr, nullptr, D[2], H[2], W[2]);
-  combine<32, 1>(n, s, n->graw, n->e1, n->g1, n->g1, 1, 1);
+  wgrad<32, 64, false>(n, s, n->p1, n->ge2, D[2], H[2], W[2], n->grads + L.w_off[2]);
+  conv<64, 32, 4, false, EPI_RAW>(s, n->ge2, Wt(n, 2), nullptr, nullptr, nullptr, n->graw, nullptr, nullptr, D[2], H[2], W[2]);
+  combine<32, 1>(n, s, n->graw, n->e1, n->g1, n->ge1, 1, 1);
   // enc1: input p0
-  wgrad<16, 32, false>(n, s, n->p0, n->g1, D[1], H[1], W[1], n->grads + L.w_off[1]);
-  conv<32, 16, 4, false, EPI_RAW>(s, n->g1, Wt(n, 1), nullptr, nullptr, nullptr, n->graw, nullptr, nullptr, D[1], H[1], W[1]);
-  combine<16, 1>(n, s, n->graw, n->e0, n->g0, n->g0, 0, 0);
+  wgrad<16, 32, false>(n, s, n->p0, n->ge1, D[1], H[1], W[1], n->grads + L.w_off[1]);
+  conv<32, 16, 4, false, EPI_RAW>(s, n->ge1, Wt(n, 1), nullptr, nullptr, nullptr, n->graw, nullptr, nullptr, D[1], H[1], W[1]);
+  combine<16, 1>(n, s, n->graw, n->e0, n->g0, n->ge0, 0, 0);
   // enc0: input x
-  wgrad<16, 16, false>(n, s, n->x, n->g0, D[0], H[0], W[0], n->grads + L.w_off[0]);
+  wgrad<16, 16, false>(n, s, n->x, n->ge0, D[0], H[0], W[0], n->grads + L.w_off[0]);
 }
 
 void quantize(hca_net* n, cudaStream_t s) {
@@ -1199,6 +1203,9 @@ int create_impl(int D, int H, int W, int trainable, void* stream, hca_net** out)
     NET_ALLOC(n->g1, Ln[1] * 32 * b2);
     NET_ALLOC(n->g2, Ln[2] * 64 * b2);
     NET_ALLOC(n->g3, Ln[3] * 64 * b2);
+    NET_ALLOC(n->ge0, Ln[0] * 16 * b2);
+    NET_ALLOC(n->ge1, Ln[1] * 32 * b2);
+    NET_ALLOC(n->ge2, Ln[2] * 64 * b2);
     NET_ALLOC(n->graw, std::max({Ln[1] * 32, Ln[2] * 64, Ln[3] * 64}) * sizeof(float));
     n->wpart_n = (long long)2 * n->sm_count * 27 * 16 * 16 + 27LL * 64 * 64 * 32;
     NET_ALLOC(n->wpart, n->wpart_n * sizeof(float));
@@ -1360,6 +1367,18 @@ int hca_net_read_activation(hca_net* n, int32_t which, void* dst) {
   return HCA_OK;
 }
 
+int hca_net_read_gradient(hca_net* n, int32_t which, void* dst) {
+  if (!n || !dst || which < 0 || which > 6 || !n->trainable) return HCA_ERR_ARG;
+  // convolution order enc0, enc1, enc2, enc3, dec2, dec1, dec0
+  bf16* src[7] = {n->ge0, n->ge1, n->ge2, n->g3, n->g2, n->g1, n->g0};
+  const int lvl[7] = {0, 1, 2, 3, 2, 1, 0};
+  const int ch[7] = {16, 32, 64, 64, 64, 32, 16};
+  NET_CUDA(cudaMemcpyAsync(dst, src[which], n->Ln[lvl[which]] * ch[which] * sizeof(bf16), cudaMemcpyDeviceToDevice,
+                           n->stream));
+  NET_CUDA(cudaStreamSynchronize(n->stream));
+  return HCA_OK;
+}
+
 int hca_net_gradients_x(hca_net* n, const void* x, const float* target, float* grads, float* loss) {
   if (!n || !x || !target || !n->trainable) return HCA_ERR_ARG;
   NET_CUDA(cudaMemcpyAsync(n->x, x, n->Ln[0] * 16 * sizeof(bf16), cudaMemcpyDeviceToDevice, n->stream));
@@ -1404,6 +1423,42 @@ int hca_net_train_step(hca_net* n, const hca_config* cfg, const uint8_t* state, 
   const int rc = hca_net_gradients(n, cfg, state, perf, K_prev, K_new, w_mse, w_res, nullptr, loss);
   if (rc) return rc;
   return adam_update(n, lr, 0.9, 0.999, 1e-8);
+}
+
+// The training sample of step t: floor(u * n) for the 24-bit uniform of the
+// Philox4x32-10 output word 0 at counter (t, 0, 0, 5), key (seed lo, seed hi).
+static int train_sample(uint64_t seed, int t, int n) {
+  uint32_t c[4] = {(uint32_t)t, 0u, 0u, 5u};
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long p0 = 0xD2511F53ull * (unsigned long long)c[0];
+    const unsigned long long p1 = 0xCD9E8D57ull * (unsigned long long)c[2];
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0, n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;
+    c[1] = (uint32_t)p1;
+    c[3] = (uint32_t)p0;
+    c[0] = n0;
+    c[2] = n2;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  const double u = (double)(c[0] >> 8) * 5.9604644775390625e-08;
+  return std::min(n - 1, (int)(u * n));
+}
+
+int hca_train_warmstart(hca_net* n, const hca_config* cfg, const hca_train_cfg* tc) {
+  if (!n || !cfg || !tc || tc->struct_size != sizeof(hca_train_cfg) || !n->trainable) return HCA_ERR_ARG;
+  if (tc->n_samples < 1 || tc->iters < 0 || !tc->state || !tc->perf || !tc->K_prev || !tc->K_new) return HCA_ERR_ARG;
+  if (!(tc->lr > 0) || !(tc->lr_final > 0)) return HCA_ERR_ARG;
+  for (int i = 0; i < tc->n_samples; ++i)
+    if (!tc->state[i] || !tc->perf[i] || !tc->K_prev[i] || !tc->K_new[i]) return HCA_ERR_ARG;
+  for (int t = 0; t < tc->iters; ++t) {
+    const int i = train_sample(tc->seed, t, tc->n_samples);
+    const double a = tc->iters > 1 ? tc->lr * std::pow(tc->lr_final / tc->lr, (double)t / (tc->iters - 1)) : tc->lr;
+    const int rc = hca_net_train_step(n, cfg, tc->state[i], tc->perf[i], tc->K_prev[i], tc->K_new[i], tc->w_mse,
+                                      tc->w_res, a, tc->losses ? tc->losses + t : nullptr);
+    if (rc) return rc;
+  }
+  return HCA_OK;
 }
 
 int hca_net_adam(hca_net* n, double lr, double beta1, double beta2, double eps) {

@@ -137,6 +137,15 @@ KCLASS_NAMES = ("setup", "pass_a", "pass_b", "residual", "ode", "ca_compact", "c
                 "mg_restrict0", "mg_post0")
 
 
+class hca_train_cfg(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("n_samples", ctypes.c_int32),
+                ("state", ctypes.POINTER(ctypes.c_void_p)), ("perf", ctypes.POINTER(ctypes.c_void_p)),
+                ("K_prev", ctypes.POINTER(ctypes.c_void_p)), ("K_new", ctypes.POINTER(ctypes.c_void_p)),
+                ("iters", ctypes.c_int32), ("lr", ctypes.c_double), ("lr_final", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("w_mse", ctypes.c_double), ("w_res", ctypes.c_double),
+                ("losses", ctypes.c_void_p)]
+
+
 class hca_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64 * NKCLASS), ("ms", ctypes.c_double * NKCLASS)]
 
@@ -153,7 +162,7 @@ EXPORTS = [
     "hca_sync", "hca_get_shape", "hca_launch_count", "hca_profile_enable", "hca_get_profile",
     "hca_o2_residual_noalloc", "hca_save", "hca_load", "hca_destroy", "hca_status_string",
     "hca_net_param_count", "hca_net_create", "hca_net_set_params", "hca_net_get_params", "hca_net_forward",
-    "hca_net_forward_x", "hca_net_read_activation", "hca_net_gradients_x", "hca_net_gradients", "hca_net_adam", "hca_net_train_step", "hca_net_sync",
+    "hca_net_forward_x", "hca_net_read_activation", "hca_net_read_gradient", "hca_net_gradients_x", "hca_net_gradients", "hca_net_adam", "hca_net_train_step", "hca_train_warmstart", "hca_net_sync",
     "hca_net_destroy", "hca_set_warm_start_net",
 ]
 
@@ -223,11 +232,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "hca_net_forward": (ctypes.c_int, [P, cfgp, P, P, P, P, P]),
         "hca_net_forward_x": (ctypes.c_int, [P, P, P]),
         "hca_net_read_activation": (ctypes.c_int, [P, I32, P]),
+        "hca_net_read_gradient": (ctypes.c_int, [P, I32, P]),
         "hca_net_gradients_x": (ctypes.c_int, [P, P, P, P, P]),
         "hca_net_adam": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
         "hca_net_gradients": (ctypes.c_int, [P, cfgp, P, P, P, P, ctypes.c_double, ctypes.c_double, P, P]),
         "hca_net_train_step": (ctypes.c_int, [P, cfgp, P, P, P, P, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_double, P]),
+        "hca_train_warmstart": (ctypes.c_int, [P, cfgp, ctypes.POINTER(hca_train_cfg)]),
         "hca_net_sync": (ctypes.c_int, [P]),
         "hca_net_destroy": (ctypes.c_int, [P]),
         "hca_set_warm_start_net": (ctypes.c_int, [P, P]),
@@ -517,6 +528,10 @@ def hca_net_read_activation(net, which: int, dst) -> None:
     _check(load().hca_net_read_activation(net, which, _dev(dst, "dst")), "hca_net_read_activation")
 
 
+def hca_net_read_gradient(net, which: int, dst) -> None:
+    _check(load().hca_net_read_gradient(net, which, _dev(dst, "dst")), "hca_net_read_gradient")
+
+
 def hca_net_gradients_x(net, x, target, grads=None, loss=None) -> None:
     _check(load().hca_net_gradients_x(net, _dev(x, "x"), _dev(target, "target"),
                                       _dev(grads, "grads", 4 * hca_net_param_count()) if grads is not None else None,
@@ -542,6 +557,27 @@ def hca_net_train_step(net, cfg: hca_config, state, perf, K_prev, K_new, lr: flo
     _check(load().hca_net_train_step(net, ctypes.byref(cfg), _dev(state, "state", n), _dev(perf, "perf", 4 * n),
                                      _dev(K_prev, "K_prev", 4 * n), _dev(K_new, "K_new", 4 * n), w_mse, w_res, lr,
                                      _dev(loss, "loss", 4) if loss is not None else None), "hca_net_train_step")
+
+
+def hca_train_warmstart(net, cfg: hca_config, states, perfs, K_prevs, K_news, iters: int, lr: float,
+                        lr_final: float, seed: int = 0, w_mse: float = 1.0, w_res: float = 0.0, losses=None) -> None:
+    """The whole training run in one library call (sequences of device tensors,
+    one entry per sample; see include/hca.h)."""
+    n = cfg.nx * cfg.ny * cfg.nz
+    k = len(states)
+    if not (len(perfs) == len(K_prevs) == len(K_news) == k):
+        raise ValueError("one state, perf, K_prev and K_new per sample")
+    arr = lambda ts, name, nb: (ctypes.c_void_p * k)(*[_dev(t, name, nb) for t in ts])
+    tc = hca_train_cfg()
+    tc.struct_size = ctypes.sizeof(hca_train_cfg)
+    tc.n_samples = k
+    keep = [arr(states, "state", n), arr(perfs, "perf", 4 * n), arr(K_prevs, "K_prev", 4 * n),
+            arr(K_news, "K_new", 4 * n)]
+    tc.state, tc.perf, tc.K_prev, tc.K_new = [ctypes.cast(a, ctypes.POINTER(ctypes.c_void_p)) for a in keep]
+    tc.iters, tc.lr, tc.lr_final, tc.seed = iters, lr, lr_final, seed & 0xFFFFFFFFFFFFFFFF
+    tc.w_mse, tc.w_res = w_mse, w_res
+    tc.losses = _dev(losses, "losses", 4 * iters) if losses is not None else None
+    _check(load().hca_train_warmstart(net, ctypes.byref(cfg), ctypes.byref(tc)), "hca_train_warmstart")
 
 
 def hca_net_sync(net) -> None:

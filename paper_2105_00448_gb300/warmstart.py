@@ -1,7 +1,8 @@
 """Training helpers for the learned oxygen warm start (the network of hca.h's
-"learned warm start" section).  Every step runs in libhca's kernels; this
-module only draws the initial parameters, moves solver fields into device
-tensors and loops over training samples.
+"learned warm start" section).  Every step runs in libhca's kernels and the
+training loop itself in one library call (hca_train_warmstart); this module
+only draws the initial parameters and moves solver fields into device
+tensors.
 """
 
 from __future__ import annotations
@@ -87,14 +88,13 @@ def train(net: "hca.Net", cfg: "hca.hca_config", samples: Sequence[Sample], iter
     iterations)."""
     import torch
 
-    rng = np.random.default_rng(seed)
     dev = device if device is not None else samples[0].state.device
-    losses = torch.zeros(iters, dtype=torch.float32, device=dev)
+    losses = torch.zeros(max(1, iters), dtype=torch.float32, device=dev)
     lr_final = lr if lr_final is None else lr_final
-    for it in range(iters):
-        s = samples[int(rng.integers(len(samples)))]
-        a = lr * (lr_final / lr) ** (it / max(1, iters - 1))
-        hca.hca_net_train_step(net.handle, cfg, s.state, s.perf, s.K_prev, s.K_new, a, losses[it:it + 1],
-                               w_mse=w_mse, w_res=w_res)
+    # one library call: the seeded sample order and the learning-rate
+    # schedule run on the host side of libhca, every step in its kernels
+    hca.hca_train_warmstart(net.handle, cfg, [s.state for s in samples], [s.perf for s in samples],
+                            [s.K_prev for s in samples], [s.K_new for s in samples], iters, lr, lr_final,
+                            seed=seed, w_mse=w_mse, w_res=w_res, losses=losses)
     hca.hca_net_sync(net.handle)
-    return losses.cpu().numpy()
+    return losses.cpu().numpy()[:iters]

@@ -4,10 +4,15 @@ training, and its use as the oxygen solve's initial guess.
 
 Tolerances: the GPU stores activations and activation gradients in BF16 and
 accumulates in FP32; the oracle rounds the same activations to BF16
-(forward(bf16=True)) and keeps everything else in FP64.  What remains is
-FP32-vs-FP64 summation order, which now and then moves a stored activation
-by one BF16 unit (2^-8 relative), plus the BF16 storage of the gradients
-(2^-9 relative per element, averaged over the sums of the weight gradient).
+(forward(bf16=True)) and, for the gradient checks, is fed the GPU's own stored
+activations and rounds its activation gradients to BF16 where the GPU stores
+them (backward(bf16=True)).  What remains is FP32-vs-FP64 summation order,
+which now and then moves a stored value by one BF16 unit: every stored
+activation and activation gradient equals the oracle's layer applied to the
+GPU's own inputs or is one unit away, weight and bias gradients from the
+GPU's own stored tensors are within 2^-10 of the sum of their terms' absolute
+values element by element, and the oracle's whole BF16 backward from the
+GPU's activations is within 3e-3 relative L2 per tensor.
 """
 
 import numpy as np
@@ -101,13 +106,13 @@ def test_forward_matches_oracle(shape):
     assert np.max(np.abs(got - ref)) < 5e-2 * np.max(np.abs(ref))
 
 
-def _bf16_close(got, ref):
-    """Elements equal, or (rarely) one BF16 unit apart from a rounding tie the
-    FP32 and FP64 sums resolve differently."""
+def _bf16_close(got, ref, max_frac=5e-3):
+    """Elements equal, or (rarely: at most max_frac of them) one BF16 unit
+    apart from a rounding tie the FP32 and FP64 sums resolve differently."""
     diff = np.abs(got - ref)
     unit = np.maximum(np.abs(ref), np.abs(got)) * 2.0 ** -7 + 1e-30
     frac = np.mean(diff > 0)
-    return bool(np.all(diff <= unit * 1.01 + 1e-6)) and frac < 5e-3, frac, float(np.max(diff / unit))
+    return bool(np.all(diff <= unit * 1.01 + 1e-6)) and frac < max_frac, frac, float(np.max(diff / unit))
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -202,8 +207,96 @@ def test_features_match_oracle():
     assert np.all(np.abs(got[..., 8] - ref[..., 8]) <= ulp(ref[..., 8]) + 2e-3)
 
 
+def _read_activations(net, D, H, W):
+    import torch
+
+    act = {}
+    for i, (name, lvl, ch) in enumerate(hca.NET_ACTIVATIONS):
+        t = torch.empty((D >> lvl) * (H >> lvl) * (W >> lvl) * ch, dtype=torch.bfloat16, device=dev())
+        hca.hca_net_read_activation(net.handle, i, t)
+        act[name] = t.float().cpu().numpy().astype(np.float64).reshape(D >> lvl, H >> lvl, W >> lvl, ch)
+    return act
+
+
+def _cache_from(act, P):
+    """The oracle's forward cache made of the GPU's own stored activations."""
+    c = dict(act)
+    c["u3"], c["u2"], c["u1"] = C.up(act["e3"]), C.up(act["d2"]), C.up(act["d1"])
+    c["params"] = {k: (C.bf16_round(v) if k.endswith(".w") and k != "head.w" else v) for k, v in P.items()}
+    return c
+
+
+def _read_gradients(net, D, H, W):
+    """The GPU's stored output gradient of every convolution (CONVS order)."""
+    import torch
+
+    lvl = {"enc0": 0, "enc1": 1, "enc2": 2, "enc3": 3, "dec2": 2, "dec1": 1, "dec0": 0}
+    out = {}
+    for i, (name, _, co) in enumerate(CONVS):
+        l = lvl[name]
+        t = torch.empty((D >> l) * (H >> l) * (W >> l) * co, dtype=torch.bfloat16, device=dev())
+        hca.hca_net_read_gradient(net.handle, i, t)
+        out[name] = t.float().cpu().numpy().astype(np.float64).reshape(D >> l, H >> l, W >> l, co)
+    return out
+
+
+# Weight gradients per layer from the GPU's own stored BF16 inputs and output
+# gradients: only FP32-vs-FP64 summation order differs, so each element is
+# within 2^-10 of the sum of its terms' absolute values (bias gradients, which
+# the GPU sums before the BF16 storage of their terms: 2^-8).  Each
+# stored output gradient is checked against the oracle's step from the GPU's
+# own downstream gradient: equal, or one BF16 unit apart where the FP32 and
+# FP64 sums fall on different sides of a rounding boundary.
+WGRAD_TOL = 2.0 ** -10
+
+
+def _check_gradients(gg, act, gy, P, gout, label, head_frac=5e-3):
+    """head_frac: the share of dec0's output gradient allowed one unit off;
+    it starts from the loss gradient, which the GPU forms in FP32 (the
+    residual loss applies the operator twice, with cancellation)."""
+    c = _cache_from(act, P)
+    Wb = c["params"]
+    r, up_g, pool_g, dg = C.bf16_round, C.up_grad, C.pool_grad, C.conv3_dgrad
+    steps = {
+        "dec0": r((gout[..., None] * P["head.w"]) * (act["d0"] > 0)),
+        "dec1": r(up_g(dg(gy["dec0"], Wb["dec0.w"])) * (act["d1"] > 0)),
+        "dec2": r(up_g(dg(gy["dec1"], Wb["dec1.w"])) * (act["d2"] > 0)),
+        "enc3": r(up_g(dg(gy["dec2"], Wb["dec2.w"])) * (act["e3"] > 0)),
+        "enc2": r((gy["dec2"] + pool_g(dg(gy["enc3"], Wb["enc3.w"]))) * (act["e2"] > 0)),
+        "enc1": r((gy["dec1"] + pool_g(dg(gy["enc2"], Wb["enc2.w"]))) * (act["e1"] > 0)),
+        "enc0": r((gy["dec0"] + pool_g(dg(gy["enc1"], Wb["enc1.w"]))) * (act["e0"] > 0)),
+    }
+    inputs = {"enc0": c["x"], "enc1": c["p0"], "enc2": c["p1"], "enc3": c["p2"], "dec2": c["u3"], "dec1": c["u2"],
+              "dec0": c["u1"]}
+    for name, _, _ in CONVS:
+        ok, frac, worst = _bf16_close(gy[name], steps[name], head_frac if name == "dec0" else 5e-3)
+        print(f"{label} d{name}: differing {frac:.1e}, worst {worst:.2f} units")
+        assert ok, name
+        x, g = inputs[name], gy[name]
+        # the bias gradient sums the FP32 output gradient before its BF16
+        # storage: each term within half a BF16 unit of the stored one
+        for key, ref, terms, tol in ((name + ".w", C.conv3_wgrad(x, g), C.conv3_wgrad(np.abs(x), np.abs(g)), WGRAD_TOL),
+                                     (name + ".b", g.sum(axis=(0, 1, 2)), np.abs(g).sum(axis=(0, 1, 2)), 2.0 ** -8)):
+            diff = np.abs(gg[key] - ref)
+            print(f"{label} {key}: worst {float(np.max(diff / (terms + 1e-30))):.2e} of the term sum")
+            assert np.all(diff <= tol * terms + 1e-30), key
+    terms_hw = np.abs(act["d0"]).reshape(-1, 16).T @ np.abs(gout).reshape(-1)
+    ref_hw = act["d0"].reshape(-1, 16).T @ gout.reshape(-1)
+    assert np.all(np.abs(gg["head.w"] - ref_hw) <= 1e-5 * terms_hw + 1e-30)
+    assert abs(gg["head.b"][0] - gout.sum()) <= 1e-5 * np.abs(gout).sum() + 1e-30
+    # end to end: the oracle's whole BF16 backward from the same activations
+    ref = C.backward(P, c, gout, bf16=True)
+    for k in ref:
+        e = rel(gg[k], ref[k])
+        print(f"{label} end to end {k}: rel L2 {e:.2e}")
+        assert e < 3e-3, k
+
+
 @pytest.mark.parametrize("shape", [(8, 8, 8), (16, 16, 32)])
 def test_gradients_match_oracle(shape):
+    """Weight and bias gradients element by element, the oracle fed the GPU's
+    own stored BF16 activations and storing its activation gradients in BF16
+    at the same points."""
     import torch
 
     D, H, W = shape
@@ -216,18 +309,18 @@ def test_gradients_match_oracle(shape):
     n = hca.hca_net_param_count()
     g = torch.empty(n, dtype=torch.float32, device=dev())
     loss = torch.empty(1, dtype=torch.float32, device=dev())
+    out = torch.empty(D * H * W, dtype=torch.float32, device=dev())
+    hca.hca_net_forward_x(net.handle, to_bf16_dev(x), out)
+    out_gpu = out.cpu().numpy().astype(np.float64).reshape(D, H, W)
     hca.hca_net_gradients_x(net.handle, to_bf16_dev(x), torch.from_numpy(tgt.reshape(-1)).to(dev()), g, loss)
+    act = _read_activations(net, D, H, W)
+    gy = _read_gradients(net, D, H, W)
     gg = unflatten(g.cpu().numpy())
     net.close()
     P = unflatten(flat)
-    out, cache = C.forward(P, x, bf16=True)
-    L, gout = C.mse_grad(out, tgt.astype(np.float64))
-    ref = C.backward(P, cache, gout)
-    assert abs(float(loss.item()) - L) <= 1e-4 * L
-    for k in ref:
-        e = rel(gg[k], ref[k])
-        print(f"grad {k}: rel {e:.2e}")
-        assert e < 3e-2, k
+    L, gout = C.mse_grad(out_gpu, tgt.astype(np.float64))
+    assert abs(float(loss.item()) - L) <= 1e-5 * L
+    _check_gradients(gg, act, gy, P, gout, f"mse {shape}")
 
 
 def test_combined_loss_gradients_match_oracle():
@@ -254,23 +347,19 @@ def test_combined_loss_gradients_match_oracle():
     c = hca.make_config(W, H, D)
     hca.hca_net_gradients(net.handle, c, tt(st), tt(maps.perf.astype(np.float32)), tt(Kp), tt(Kn),
                           0.5, 0.25, g, loss)
-    xg = torch.empty(D * H * W * 16, dtype=torch.bfloat16, device=dev())
-    hca.hca_net_read_activation(net.handle, 0, xg)
-    x = xg.float().cpu().numpy().astype(np.float64).reshape(D, H, W, 16)
+    act = _read_activations(net, D, H, W)
+    gy = _read_gradients(net, D, H, W)
     gg = unflatten(g.cpu().numpy())
     net.close()
     P = unflatten(flat)
-    out, cache = C.forward(P, x, bf16=True)
+    # the network output from the GPU's own last activation (FP64 head)
+    out = act["d0"] @ P["head.w"] + P["head.b"][0]
     tgt = C.target(Kp.astype(np.float64), Kn.astype(np.float64), cfg)
     Lr, gr = C.residual_loss(out, tgt, st, Kp.astype(np.float64), cfg)
     Lm, gm = C.mse_grad(out, tgt)
     L, gout = 0.5 * Lm + 0.25 * Lr, 0.5 * gm + 0.25 * gr
-    ref = C.backward(P, cache, gout)
     assert abs(float(loss.item()) - L) <= 1e-3 * L
-    for k in ref:
-        e = rel(gg[k], ref[k])
-        print(f"residual-loss grad {k}: rel {e:.2e}")
-        assert e < 3e-2, k
+    _check_gradients(gg, act, gy, P, gout, "mse + residual", head_frac=0.05)
 
 
 def test_adam_step_matches_formula():
@@ -448,3 +537,40 @@ def test_trained_network_cuts_oxygen_iterations_on_held_out_solves():
     net.close()
     print("held-out oxygen CG iterations: previous-step start", it[0], "learned start", it[1])
     assert it[1] <= 0.9 * it[0]
+
+
+def test_train_warmstart_call_equals_its_documented_steps():
+    """hca_train_warmstart is the seeded loop of hca_net_train_step it
+    documents: sample floor(u_t n) with u_t the Philox uniform of counter
+    (t, 0, 0, 5) under the seed (the oracle's generator gives the order
+    here), geometric learning-rate decay; same parameters bit for bit."""
+    import torch
+
+    from oracle.philox import site_uniform
+
+    shape = (16, 16, 16)
+    nz, ny, nx = shape
+    samples, c = _sim_samples(shape, 4, 3)
+    iters, lr, lr_final, seed = 12, 2e-3, 5e-4, (3 << 32) | 77
+    a = hca.Net(*shape, trainable=True)
+    a.set_params(warmstart.init_params(1))
+    la = torch.zeros(iters, dtype=torch.float32, device=dev())
+    hca.hca_train_warmstart(a.handle, c, [s.state for s in samples], [s.perf for s in samples],
+                            [s.K_prev for s in samples], [s.K_new for s in samples], iters, lr, lr_final,
+                            seed=seed, losses=la)
+    hca.hca_net_sync(a.handle)
+    b = hca.Net(*shape, trainable=True)
+    b.set_params(warmstart.init_params(1))
+    lb = torch.zeros(iters, dtype=torch.float32, device=dev())
+    u = site_uniform(seed, np.arange(iters, dtype=np.uint64), 0, 5)
+    order = np.minimum(len(samples) - 1, np.floor(u * len(samples)).astype(int))
+    for t in range(iters):
+        s = samples[order[t]]
+        rate = lr * (lr_final / lr) ** (t / (iters - 1))
+        hca.hca_net_train_step(b.handle, c, s.state, s.perf, s.K_prev, s.K_new, rate, lb[t:t + 1])
+    hca.hca_net_sync(b.handle)
+    assert len(set(order.tolist())) > 1
+    assert np.array_equal(a.params(), b.params())
+    assert torch.equal(la, lb)
+    a.close()
+    b.close()

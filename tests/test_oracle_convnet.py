@@ -174,3 +174,24 @@ def test_residual_loss_gradient_and_special_cases():
     e[1, 1, 1] = 0.5
     L1, _ = C.residual_loss(e, np.zeros_like(e), st1, np.ones_like(e), Pm.Config(3, 3, 3))
     assert L1 == pytest.approx(42 * 0.25 / 27)
+
+
+def test_bf16_backward_rounds_the_activation_gradients_only():
+    """backward(bf16=True): every recorded output gradient is a BF16 value,
+    each weight gradient is the weight-gradient correlation of the recorded
+    tensors, and the result stays within BF16 rounding of the exact backward."""
+    rng = np.random.default_rng(3)
+    p = C.init_params(rng)
+    x = C.bf16_round(rng.standard_normal((8, 8, 8, C.IN_CH)))
+    out, cache = C.forward(p, x, bf16=True)
+    gout = rng.standard_normal(out.shape) / out.size
+    rec = {}
+    g16 = C.backward(p, cache, gout, bf16=True, record=rec)
+    g64 = C.backward(p, cache, gout)
+    for name, _, _ in C.CONVS:
+        xin, gy = rec[name]
+        assert np.array_equal(C.bf16_round(gy), gy), name
+        assert np.allclose(g16[name + ".w"], C.conv3_wgrad(xin, gy), rtol=1e-13, atol=0)
+        e = np.linalg.norm(g16[name + ".w"] - g64[name + ".w"]) / np.linalg.norm(g64[name + ".w"])
+        assert 0 < e < 2 ** -6, (name, e)
+    assert np.array_equal(g16["head.w"], g64["head.w"])
