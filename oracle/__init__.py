@@ -31,5 +31,8 @@ multigrid The geometric V-cycle preconditioner and MG-PCG.
 api      The library's call names (oracle_create, oracle_step, ...) over model.
 
 Parity status: every function is pinned by tests under ``tests/test_oracle_*``
-except the ones whose docstring says "parity unpinned".
+except the ones whose docstring says "parity unpinned"; the output bits of
+``philox.philox4x32_10`` are pinned against cuRAND's Philox4_32_10 device
+generator, an independent implementation, in ``tests/test_gpu_philox_curand.py``
+(it needs a GPU).
 """
