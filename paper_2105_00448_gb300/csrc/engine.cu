@@ -1401,6 +1401,10 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
       }
       c.pass_ni = ni == 1 || ni == 2 || ni == 4 ? ni : 0;
       h->mgh.ni = c.pass_ni;
+      // persistent row kernels for one FP32 lattice with one row per warp
+      // (HCA_PERSIST=0 keeps one block per chunk)
+      const char* pe = std::getenv("HCA_PERSIST");
+      c.persist = (!(pe && pe[0] == '0') && n == 1 && !h->fp64 && h->reps_h[0].lpr == 32 && c.pass_ni > 0) ? 1 : 0;
     }
     if (!cfgs[0].threads_per_block) {
       const char* nt = std::getenv("HCA_NO_TUNE");

@@ -176,6 +176,21 @@ __device__ __forceinline__ uint8_t st_at(const uchar4& s, int k) {
   return k == 0 ? s.x : (k == 1 ? s.y : (k == 2 ? s.z : s.w));
 }
 
+// The CG direction and operator arithmetic of pass A, with its roundings
+// fixed (no contraction left to the compiler) so that every kernel forming
+// them gets the same bits: p = zs z + beta p_old, q = d p - c nb, and the
+// accumulation s += p q.
+__device__ __forceinline__ float cg_dir(float zs, float z, float beta, float p) {
+  return __fmaf_rn(beta, p, __fmul_rn(zs, z));
+}
+__device__ __forceinline__ float cg_apply(float d, float p, float c, float nb) {
+  return __fmaf_rn(d, p, -__fmul_rn(c, nb));
+}
+__device__ __forceinline__ float cg_madd(float a, float b, float s) { return __fmaf_rn(a, b, s); }
+__device__ __forceinline__ double cg_dir(double zs, double z, double beta, double p) { return zs * z + beta * p; }
+__device__ __forceinline__ double cg_apply(double d, double p, double c, double nb) { return d * p - c * nb; }
+__device__ __forceinline__ double cg_madd(double a, double b, double s) { return s + a * b; }
+
 // state classes
 __device__ __forceinline__ bool is_consumer(uint8_t s) {
   return s == HCA_PROLIF || s == HCA_QUIESC || s == HCA_STROMA;
@@ -317,6 +332,7 @@ struct Ctx {
   int pass_regs;    // register cap of the FP32 CG passes (64, 80, 96, 128)
   int pass_ni;      // groups per lane in a row shared by all replicates (1, 2, 4; 0 = differs)
   int mg;           // 0: Jacobi (z = r / d), 1: V-cycle (z = M r)
+  int persist;      // 1: the CG passes and the lattice post-sweep run in persistent row form (one FP32 lattice)
   void* r;
   void* mg_t0;
   void* mg_w;         // omega / d on the lattice (0 where d = 0)
@@ -444,6 +460,11 @@ __device__ __forceinline__ void store_row(const Ctx& c, int chunk, int rl, bool 
 // active replicates goes to sync->active_count and to post(n_active).  The
 // summation order depends on the lattice only, not on the block size, on the
 // other replicates of a batch or on which warp performs it.
+// The rest of warp_epilogue once a chunk's row slots are all written: the
+// calling warp sums the chunk and continues to the group and replicate levels.
+template <class Fin, class Post>
+__device__ __forceinline__ void warp_chunk_done(const Ctx& c, int ndot, int chunk, Fin fin, Post post);
+
 template <class Fin, class Post>
 __device__ __forceinline__ void warp_epilogue(const Ctx& c, int ndot, int chunk, Fin fin, Post post) {
   const unsigned FULLM = 0xffffffffu;
@@ -457,6 +478,14 @@ __device__ __forceinline__ void warp_epilogue(const Ctx& c, int ndot, int chunk,
   }
   t = __shfl_sync(FULLM, t, 0);
   if (t != nw - 1) return;
+  warp_chunk_done(c, ndot, chunk, fin, post);
+}
+
+template <class Fin, class Post>
+__device__ __forceinline__ void warp_chunk_done(const Ctx& c, int ndot, int chunk, Fin fin, Post post) {
+  const unsigned FULLM = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  int t = 0;
   __threadfence();
   const int2 ch = c.chunks[chunk];
   const RepDesc& rd = c.reps[ch.x];

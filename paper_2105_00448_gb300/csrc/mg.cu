@@ -30,6 +30,9 @@
 #include "row_ops.cuh"
 
 namespace hca {
+
+int persist_grid(const void* fn, int threads, int sm_count);
+
 namespace {
 
 constexpr int kMgThreads = 256;
@@ -998,10 +1001,10 @@ __global__ void __launch_bounds__(NT, MINB) k_mg_coarse(Ctx c, int which, int sm
 // so the kernel streams v, r and omega/d and reads p from the coarse level
 // (piecewise constant: three of a site's neighbours share its coarse cell).
 // Otherwise the lattice is the coarsest level and u = src.
-template <typename T, bool PROLONG, int NI>
+template <typename T, bool PROLONG, int NI, bool PERSIST = false>
 __global__ void __maxnreg__(64) k_mg_post0(Ctx c, int which, const T* __restrict__ src) {
   HCA_COUNT_KERNEL(c);
-  const int2 ch = c.chunks[blockIdx.x];
+  const int2 ch = PERSIST ? make_int2(0, 0) : c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
   const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
   const T* __restrict__ rr = (const T*)c.r;
@@ -1019,10 +1022,8 @@ __global__ void __maxnreg__(64) k_mg_post0(Ctx c, int which, const T* __restrict
     ny1 = L1.ny;
   }
   const RowIter it = row_iter(rd);
-  for (int rbase = it.warp * it.rpw; rbase < rd.chunk_rows; rbase += it.nw * it.rpw) {
-    const int rl = rbase + it.sub;
-    const bool row_ok = rl < nrows;
-    const int j = ch.y + (row_ok ? rl : 0);
+  // one row j (chunk slot rl of `chunk`; row_ok false: a padding slot of the last chunk)
+  auto row = [&](int chunk, int rl, bool row_ok, int j) {
     const RowGeo geo = row_geo(rd, j);
     const int y = j % rd.ny, z = j / rd.ny;
     LaneAcc<T> acc[1];
@@ -1113,9 +1114,19 @@ __global__ void __maxnreg__(64) k_mg_post0(Ctx c, int which, const T* __restrict
         }
       }
     }
-    store_rows_acc(c, blockIdx.x, rl, row_ok, it.sl, it.lpr, acc, 1);
+    store_rows_acc(c, chunk, rl, row_ok, it.sl, it.lpr, acc, 1);
+  };
+  if (PERSIST) {
+    const int R = rd.ny * rd.nz, cr = rd.chunk_rows;
+    for (int j = persist_row_begin(R) + it.warp; j < persist_row_end(R); j += it.nw) row(j / cr, j % cr, true, j);
+  } else {
+    for (int rbase = it.warp * it.rpw; rbase < rd.chunk_rows; rbase += it.nw * it.rpw) {
+      const int rl = rbase + it.sub;
+      const bool row_ok = rl < nrows;
+      row(blockIdx.x, rl, row_ok, ch.y + (row_ok ? rl : 0));
+    }
   }
-  warp_epilogue(c, 1, blockIdx.x, [&](int r, const double* s1) -> int {
+  auto fin = [&](int r, const double* s1) -> int {
     RepSolve& s = c.solve[r];
     if (!s.active) return 0;
     if (!(s1[0] > 0.0) || !isfinite(s1[0])) {
@@ -1126,7 +1137,9 @@ __global__ void __maxnreg__(64) k_mg_post0(Ctx c, int which, const T* __restrict
     s.beta = s.iters == 0 ? 0.0 : s1[0] / s.rho;
     s.rho = s1[0];
     return 1;
-  });
+  };
+  if (PERSIST) block_arrivals(c, 1, fin, [](int) {});
+  else warp_epilogue(c, 1, blockIdx.x, fin);
 }
 
 // Launch shapes of the cooperative coarse-level kernel: 0 = 256 threads with
@@ -1196,7 +1209,16 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
       else k_mg_post<T, false><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
     }
   }
-  if (all || part == 2) {
+  if ((all || part == 2) && c.persist && (H.ni == 1 || H.ni == 2 || H.ni == 4)) {
+    const void* fn = H.ni == 1 ? (const void*)k_mg_post0<T, true, 1, true>
+                   : H.ni == 2 ? (const void*)k_mg_post0<T, true, 2, true> : (const void*)k_mg_post0<T, true, 4, true>;
+    const int g = persist_grid(fn, c.threads, c.sm_count);
+    switch (H.ni) {
+      case 1: k_mg_post0<T, true, 1, true><<<g, c.threads, 0, s>>>(c, which, nullptr); break;
+      case 2: k_mg_post0<T, true, 2, true><<<g, c.threads, 0, s>>>(c, which, nullptr); break;
+      default: k_mg_post0<T, true, 4, true><<<g, c.threads, 0, s>>>(c, which, nullptr); break;
+    }
+  } else if (all || part == 2) {
     switch (H.ni) {
       case 1: k_mg_post0<T, true, 1><<<c.n_chunks, c.threads, 0, s>>>(c, which, nullptr); break;
       case 2: k_mg_post0<T, true, 2><<<c.n_chunks, c.threads, 0, s>>>(c, which, nullptr); break;

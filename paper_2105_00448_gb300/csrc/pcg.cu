@@ -25,6 +25,9 @@
 // update would let one block read a neighbour row another block has already
 // overwritten); a parity bit in device memory, flipped by pass B, names the
 // current buffer, so the same two kernels form the body of a graph loop.
+#include <mutex>
+#include <vector>
+
 #include "hca_internal.cuh"
 #include "row_ops.cuh"
 
@@ -201,10 +204,12 @@ __global__ void __launch_bounds__(512) k_setup(Ctx c, int which, CondArg cnd) {
 // ----------------------------------------------------------------- pass A --
 // All loads of a group (own site and the four neighbour rows) are issued
 // before any value is used, so a group costs one memory round trip.
-template <typename T, int REGS, int NI>
+// PERSIST: the persistent row form (one lattice, one row per warp; see
+// block_arrivals), else one block per chunk.
+template <typename T, int REGS, int NI, bool PERSIST>
 __global__ void __maxnreg__(REGS) k_pass_a(Ctx c, int which) {
   HCA_COUNT_KERNEL(c);
-  const int2 ch = c.chunks[blockIdx.x];
+  const int2 ch = PERSIST ? make_int2(0, 0) : c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
   const RepSolve sv = c.solve[ch.x];
   if (sv.active) {
@@ -223,10 +228,9 @@ __global__ void __maxnreg__(REGS) k_pass_a(Ctx c, int which) {
     const T zs = (sv.iters == 0 && !c.mg) ? (T)sv.scale : T(1);
     const T cpl = (T)op_coupling(rd, which);
     const RowIter it = row_iter(rd);
-    for (int rbase = it.warp * it.rpw; rbase < rd.chunk_rows; rbase += it.nw * it.rpw) {
-      const int rl = rbase + it.sub;
-      const bool row_ok = rl < nrows;
-      const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
+    // one row j (chunk slot rl of `chunk`; row_ok false: a padding slot of the last chunk)
+    auto row = [&](int chunk, int rl, bool row_ok, int j) {
+      const RowGeo geo = row_geo(rd, j);
       LaneAcc<T> acc[1];
       T carry = T(0);
       // groups per lane in a row: a compile-time count (NI > 0) lets the
@@ -260,13 +264,13 @@ __global__ void __maxnreg__(REGS) k_pass_a(Ctx c, int which) {
         V4<T> PN, ym, yp, zm, zp;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          PN.a[k] = zs * z0.a[k] + beta * p0.a[k];
-          ym.a[k] = zs * zym.a[k] + beta * pym.a[k];
-          yp.a[k] = zs * zyp.a[k] + beta * pyp.a[k];
-          zm.a[k] = zs * zzm.a[k] + beta * pzm.a[k];
-          zp.a[k] = zs * zzp.a[k] + beta * pzp.a[k];
+          PN.a[k] = cg_dir(zs, z0.a[k], beta, p0.a[k]);
+          ym.a[k] = cg_dir(zs, zym.a[k], beta, pym.a[k]);
+          yp.a[k] = cg_dir(zs, zyp.a[k], beta, pyp.a[k]);
+          zm.a[k] = cg_dir(zs, zzm.a[k], beta, pzm.a[k]);
+          zp.a[k] = cg_dir(zs, zzp.a[k], beta, pzp.a[k]);
         }
-        const T right_next = zs * zr + beta * pr;
+        const T right_next = cg_dir(zs, zr, beta, pr);
         T left, right;
         x_neighbours(PN, g, gpr, it.sl, it.lpr, gok, carry, left, right, [&] { return right_next; });
         if (gok) {
@@ -274,36 +278,47 @@ __global__ void __maxnreg__(REGS) k_pass_a(Ctx c, int which) {
           V4<T> Q;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            Q.a[k] = D.a[k] * PN.a[k] - cpl * nb_sum(PN, k, left, right, ym, yp, zm, zp);
-            g_s += PN.a[k] * Q.a[k];
+            Q.a[k] = cg_apply(D.a[k], PN.a[k], cpl, nb_sum(PN, k, left, right, ym, yp, zm, zp));
+            g_s = cg_madd(PN.a[k], Q.a[k], g_s);
           }
           st4(p_new + e, PN);
           st4(qq + e, Q);   // pass B reads A p instead of re-forming it from p's neighbours
           acc[0].add(g_s);
         }
       }
-      store_rows_acc(c, blockIdx.x, rl, row_ok, it.sl, it.lpr, acc, 1);
+      store_rows_acc(c, chunk, rl, row_ok, it.sl, it.lpr, acc, 1);
+    };
+    if (PERSIST) {
+      const int R = rd.ny * rd.nz, cr = rd.chunk_rows;
+      for (int j = persist_row_begin(R) + it.warp; j < persist_row_end(R); j += it.nw) row(j / cr, j % cr, true, j);
+    } else {
+      for (int rbase = it.warp * it.rpw; rbase < rd.chunk_rows; rbase += it.nw * it.rpw) {
+        const int rl = rbase + it.sub;
+        const bool row_ok = rl < nrows;
+        row(blockIdx.x, rl, row_ok, ch.y + (row_ok ? rl : 0));
+      }
     }
   }
-  warp_epilogue(c, 1, blockIdx.x,
-                 [&](int r, const double* s1) -> int {
-                   RepSolve& s = c.solve[r];
-                   if (!s.active) return 0;
-                   if (!(s1[0] > 0.0) || !isfinite(s1[0])) {
-                     if (!isfinite(s1[0])) c.sync->error = 1;
-                     s.active = 0;
-                     return 0;
-                   }
-                   s.alpha = s.rho / s1[0];
-                   return 1;
-                 });
+  auto fin = [&](int r, const double* s1) -> int {
+    RepSolve& s = c.solve[r];
+    if (!s.active) return 0;
+    if (!(s1[0] > 0.0) || !isfinite(s1[0])) {
+      if (!isfinite(s1[0])) c.sync->error = 1;
+      s.active = 0;
+      return 0;
+    }
+    s.alpha = s.rho / s1[0];
+    return 1;
+  };
+  if (PERSIST) block_arrivals(c, 1, fin, [](int) {});
+  else warp_epilogue(c, 1, blockIdx.x, fin);
 }
 
 // ----------------------------------------------------------------- pass B --
-template <typename T, int REGS, int NI>
+template <typename T, int REGS, int NI, bool PERSIST>
 __global__ void __maxnreg__(REGS) k_pass_b(Ctx c, int which, void* xfield, CondArg cnd) {
   HCA_COUNT_KERNEL(c);
-  const int2 ch = c.chunks[blockIdx.x];
+  const int2 ch = PERSIST ? make_int2(0, 0) : c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
   const RepSolve sv = c.solve[ch.x];
   if (sv.active) {
@@ -319,10 +334,8 @@ __global__ void __maxnreg__(REGS) k_pass_b(Ctx c, int which, void* xfield, CondA
     const T alpha = (T)sv.alpha;
     const T zs = (sv.iters == 0 && !mg) ? (T)sv.scale : T(1);
     const RowIter it = row_iter(rd);
-    for (int rbase = it.warp * it.rpw; rbase < rd.chunk_rows; rbase += it.nw * it.rpw) {
-      const int rl = rbase + it.sub;
-      const bool row_ok = rl < nrows;
-      const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
+    auto row = [&](int chunk, int rl, bool row_ok, int j) {
+      const RowGeo geo = row_geo(rd, j);
       LaneAcc<T> acc[2];
       // groups per lane in a row: a compile-time count (NI > 0) lets the
       // compiler issue the loads of all of them before the first is used
@@ -362,39 +375,50 @@ __global__ void __maxnreg__(REGS) k_pass_b(Ctx c, int which, void* xfield, CondA
           acc[1].add(g_rr);
         }
       }
-      store_rows_acc(c, blockIdx.x, rl, row_ok, it.sl, it.lpr, acc, 2);
+      store_rows_acc(c, chunk, rl, row_ok, it.sl, it.lpr, acc, 2);
+    };
+    if (PERSIST) {
+      const int R = rd.ny * rd.nz, cr = rd.chunk_rows;
+      for (int j = persist_row_begin(R) + it.warp; j < persist_row_end(R); j += it.nw) row(j / cr, j % cr, true, j);
+    } else {
+      for (int rbase = it.warp * it.rpw; rbase < rd.chunk_rows; rbase += it.nw * it.rpw) {
+        const int rl = rbase + it.sub;
+        const bool row_ok = rl < nrows;
+        row(blockIdx.x, rl, row_ok, ch.y + (row_ok ? rl : 0));
+      }
     }
   }
-  warp_epilogue(c, 2, blockIdx.x,
-                 [&](int r, const double* s2) -> int {
-                   RepSolve& s = c.solve[r];
-                   if (!s.active) return 0;
-                   s.iters += 1;
-                   if (!isfinite(s2[0]) || !isfinite(s2[1])) {
-                     c.sync->error = 1;
-                     s.active = 0;
-                     return 0;
-                   }
-                   if (!c.mg) {   // the V-cycle form sets beta and rho after z = M r
-                     s.beta = s2[0] / s.rho;
-                     s.rho = s2[0];
-                   }
-                   s.rnorm2 = s2[1];
-                   const bool conv = sqrt(s2[1]) <= s.rtol * sqrt(s.bnorm2);
-                   if (conv || s.iters >= s.maxit) s.active = 0;
-                   return s.active;
-                 },
-                 [&](int n_active) {
-                   c.sync->parity ^= 1;
-                   const int g = ++c.sync->guard;
-                   bool go = n_active > 0;
-                   if (go && g >= c.sync->guard_limit) {
-                     // every replicate stops at maxit; this only guards the graph loop
-                     c.sync->error = 2;
-                     go = false;
-                   }
-                   set_cond(cnd, go);
-                 });
+  auto fin = [&](int r, const double* s2) -> int {
+    RepSolve& s = c.solve[r];
+    if (!s.active) return 0;
+    s.iters += 1;
+    if (!isfinite(s2[0]) || !isfinite(s2[1])) {
+      c.sync->error = 1;
+      s.active = 0;
+      return 0;
+    }
+    if (!c.mg) {   // the V-cycle form sets beta and rho after z = M r
+      s.beta = s2[0] / s.rho;
+      s.rho = s2[0];
+    }
+    s.rnorm2 = s2[1];
+    const bool conv = sqrt(s2[1]) <= s.rtol * sqrt(s.bnorm2);
+    if (conv || s.iters >= s.maxit) s.active = 0;
+    return s.active;
+  };
+  auto post = [&](int n_active) {
+    c.sync->parity ^= 1;
+    const int g = ++c.sync->guard;
+    bool go = n_active > 0;
+    if (go && g >= c.sync->guard_limit) {
+      // every replicate stops at maxit; this only guards the graph loop
+      c.sync->error = 2;
+      go = false;
+    }
+    set_cond(cnd, go);
+  };
+  if (PERSIST) block_arrivals(c, 2, fin, post);
+  else warp_epilogue(c, 2, blockIdx.x, fin, post);
 }
 
 // ----------------------------------------------------------- true residual --
@@ -961,10 +985,42 @@ void launch_setup(const Ctx& c, int which, bool fp64, CondArg cnd) {
   else launch_setup_t<float>(c, which, cnd);
 }
 
+// Blocks of a persistent row kernel: every block resident at once (its
+// occupancy at `threads` per block times the SM count), cached per kernel.
+int persist_grid(const void* fn, int threads, int sm_count) {
+  struct Entry {
+    const void* fn;
+    int threads, sm, grid;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  for (const Entry& e : cache)
+    if (e.fn == fn && e.threads == threads && e.sm == sm_count) return e.grid;
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, 0) != cudaSuccess || per < 1) {
+    (void)cudaGetLastError();
+    per = 1;
+  }
+  cache.push_back({fn, threads, sm_count, per * sm_count});
+  return per * sm_count;
+}
+
 template <int REGS, int NI>
 static void launch_ab_f32(const Ctx& c, int which, bool a, void* xfield, CondArg cnd) {
-  if (a) k_pass_a<float, REGS, NI><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which);
-  else k_pass_b<float, REGS, NI><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, xfield, cnd);
+  if (NI > 0 && c.persist) {
+    if (a) {
+      const void* fn = (const void*)k_pass_a<float, REGS, NI, true>;
+      k_pass_a<float, REGS, NI, true><<<persist_grid(fn, c.threads, c.sm_count), c.threads, 0, c.stream>>>(c, which);
+    } else {
+      const void* fn = (const void*)k_pass_b<float, REGS, NI, true>;
+      k_pass_b<float, REGS, NI, true>
+          <<<persist_grid(fn, c.threads, c.sm_count), c.threads, 0, c.stream>>>(c, which, xfield, cnd);
+    }
+    return;
+  }
+  if (a) k_pass_a<float, REGS, NI, false><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which);
+  else k_pass_b<float, REGS, NI, false><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, xfield, cnd);
 }
 
 template <int REGS>
@@ -979,8 +1035,8 @@ static void launch_ab_f32_ni(const Ctx& c, int which, bool a, void* xfield, Cond
 
 static void launch_ab(const Ctx& c, int which, bool fp64, bool a, void* xfield, CondArg cnd) {
   if (fp64) {
-    if (a) k_pass_a<double, 128, 0><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which);
-    else k_pass_b<double, 128, 0><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, xfield, cnd);
+    if (a) k_pass_a<double, 128, 0, false><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which);
+    else k_pass_b<double, 128, 0, false><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, xfield, cnd);
     return;
   }
   switch (c.pass_regs) {

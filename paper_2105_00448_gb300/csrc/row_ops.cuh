@@ -82,4 +82,44 @@ __device__ __forceinline__ void store_rows_acc(const Ctx& c, int chunk, int rl, 
   store_row(c, chunk, rl, row_ok, sl, lpr, a, ndot);
 }
 
+// Persistent row kernels (one lattice, one row per warp): block b of the
+// grid updates the rows [R b / G, R (b + 1) / G) of the lattice's R rows, its
+// warps taking them in turn; row sums go to the same chunk slots as in the
+// one-block-per-chunk form.
+__device__ __forceinline__ int persist_row_begin(int R) { return (int)((long long)R * blockIdx.x / gridDim.x); }
+__device__ __forceinline__ int persist_row_end(int R) { return (int)((long long)R * (blockIdx.x + 1) / gridDim.x); }
+
+// Chunk arrivals of a persistent row kernel, once per block after all its
+// rows: each chunk the block touched receives the number of its rows the
+// block wrote (an atomic add); the arrival that completes a chunk hands it to
+// one warp of this block, which sums it in the fixed tree of warp_epilogue and
+// continues to the group and replicate levels.  The same sums, in the same
+// order, as the one-block-per-chunk form; only who finishes differs.
+template <class Fin, class Post>
+__device__ void block_arrivals(const Ctx& c, int ndot, Fin fin, Post post) {
+  const RepDesc& rd = c.reps[0];
+  const int R = rd.ny * rd.nz, cr = rd.chunk_rows;
+  const int jb = persist_row_begin(R), je = persist_row_end(R);
+  __shared__ int s_done[64];
+  __shared__ int s_n;
+  __threadfence();   // this thread's row sums are visible before the arrivals
+  __syncthreads();
+  if (je <= jb) return;
+  const int c0 = jb / cr, c1 = (je - 1) / cr;
+  for (int base = c0; base <= c1; base += 64) {
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    const int ci = base + (int)threadIdx.x;
+    if (threadIdx.x < 64 && ci <= c1) {
+      const int lo = max(jb, ci * cr), hi = min(je, min(R, (ci + 1) * cr));
+      const int n = hi - lo, full = min(cr, R - ci * cr);
+      if (atomicAdd(&c.chunk_cnt[ci], n) + n == full) s_done[atomicAdd(&s_n, 1)] = ci;
+    }
+    __syncthreads();
+    const int nd = s_n;
+    for (int i = (int)(threadIdx.x >> 5); i < nd; i += (int)(blockDim.x >> 5)) warp_chunk_done(c, ndot, s_done[i], fin, post);
+    __syncthreads();
+  }
+}
+
 }  // namespace hca

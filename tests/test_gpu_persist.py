@@ -1,0 +1,53 @@
+"""Persistent row kernels (CG pass A, pass B and the lattice post-sweep of
+the V-cycle for one FP32 lattice with one row per warp) against the
+one-block-per-chunk form (HCA_PERSIST=0, read at handle creation): every row
+is computed by the same code and its sum goes to the same chunk slot, and
+each chunk is summed in the same fixed tree, so solves and coupled steps must
+agree bit for bit.  Lattices: one, two and four groups per lane, chunks of 8
+and 32 rows, ragged rows, both preconditioners.  Their parity with the oracle
+is checked in test_gpu_bench_instances.py and test_gpu_mg.py.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+from gpu_helpers import make_pair
+from paper_2105_00448_gb300 import hca
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(24, 32, 160), (16, 16, 256), (32, 64, 128), (13, 24, 130), (8, 20, 300), (64, 64, 64)]
+
+
+def _with_persist(flag, fn):
+    old = os.environ.get("HCA_PERSIST")
+    os.environ["HCA_PERSIST"] = "1" if flag else "0"
+    try:
+        return fn()
+    finally:
+        if old is None:
+            del os.environ["HCA_PERSIST"]
+        else:
+            os.environ["HCA_PERSIST"] = old
+
+
+@pytest.mark.parametrize("pc", [hca.HCA_PC_MG, hca.HCA_PC_JACOBI], ids=["mg", "jacobi"])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_persistent_rows_equal_block_per_chunk(shape, pc):
+    def run():
+        sim, _, _ = make_pair(shape, "f32", seed=9, n_drugs=2, preconditioner=pc)
+        sim.step(3)
+        out = (sim.states(), sim.field(hca.FIELD_O2), sim.field(hca.FIELD_O2_LO), sim.field(hca.FIELD_DRUG0),
+               sim.field(hca.FIELD_DRUG1), sim.stats())
+        sim.close()
+        return out
+
+    a = _with_persist(True, run)
+    b = _with_persist(False, run)
+    for u, v in zip(a[:5], b[:5]):
+        assert np.array_equal(u, v)
+    assert a[5]["o2_iterations"] == b[5]["o2_iterations"]
+    assert a[5]["drug_iterations"] == b[5]["drug_iterations"]
+    assert a[5]["o2_rel_residual"] == b[5]["o2_rel_residual"]
