@@ -43,22 +43,23 @@ CORR_LEN = 8.0
 #   pass A reads z, p_old, d and writes p_new and q = A p_new; pass B reads p, q, x, r and
 #   writes x, r;
 #   defect-correction residual (later sweeps) reads x_hi, x_lo, d, a, b and writes z, dx, r;
-#   multigrid on the lattice: the first sweep + restriction reads r, omega/d, d and writes the
-#   1/8-size coarse right-hand side; the prolongation + last sweep reads r, omega/d, d and the
-#   1/8-size coarse correction and writes z; ODE reads state, K and updates phi, P, Vc
+#   multigrid on the lattice: the first sweep + restriction reads r, omega/d and writes the
+#   pre-smoothed iterate v and the 1/8-size coarse right-hand side; the prolongation + last sweep
+#   reads v, r, omega/d and the 1/8-size coarse correction and writes z; ODE reads state, K and
+#   updates phi, P, Vc
 BYTES_PER_SITE = {"pass_a": 20, "pass_b": 24, "setup": 17, "residual": 24, "ode": 29,
-                  "mg_restrict0": 16.5, "mg_post0": 16.5}
+                  "mg_restrict0": 12.5, "mg_post0": 16.5}
 # the method's minimum per site where this design moves more: CG pass A reads
 # z, d, p_old and writes p (16 B); storing q = A p for pass B adds 4 B
 BYTES_MIN_PER_SITE = {**BYTES_PER_SITE, "pass_a": 16}
 # step-level algorithmic bytes per lattice site (FP32 storage): set-up and
 # solve start-up, ODE and CA 70 B, 13 B per defect-correction residual sweep,
 # 40 B per CG iteration (two-pass minimum), plus per V-cycle the lattice's
-# first sweep + restriction and prolongation + last sweep (33 B) and the
+# first sweep + restriction and prolongation + last sweep (29 B) and the
 # coarse levels (33 B per coarse site: restriction reads rhs, omega/d, d and
 # writes the next level's rhs; the post-sweep reads rhs, omega/d, d, the
 # coarser correction and writes x)
-STEP_FIXED_B, STEP_DC_B, STEP_IT_B, VCYCLE_LATTICE_B, VCYCLE_COARSE_B = 70, 13, 40, 33, 33
+STEP_FIXED_B, STEP_DC_B, STEP_IT_B, VCYCLE_LATTICE_B, VCYCLE_COARSE_B = 70, 13, 40, 29, 33
 
 
 def metric_name(edge: int = N_EDGE) -> str:
@@ -270,7 +271,7 @@ def step_roofline(prof, steps: int, sites: int, ms_per_step: float, level_fracti
             "frac": achieved / peak, "bytes_per_site": per_site, "terms_bytes_per_site": terms,
             "counts_per_step": {"cg_iterations": n_it, "dc_sweeps": n_dc, "vcycles": n_vc},
             "frac_without_vcycle": cg_only / peak,
-            "formula": "70 + 13 n_dc + 40 n_it + n_vc (33 + 33 f_coarse) B/site x sites / step time; f_coarse = "
+            "formula": "70 + 13 n_dc + 40 n_it + n_vc (29 + 33 f_coarse) B/site x sites / step time; f_coarse = "
                        "coarse-level sites per lattice site"}
 
 

@@ -873,8 +873,8 @@ int check_convergence(hca_handle* h) {
 int autotune(hca_handle* h, bool tune_regs) {
   Ctx& c = h->ctx;
   const int cand_t[3] = {128, 256, 512};
-  const int cand_r[3] = {80, 96, 128};
-  const int nr = (tune_regs && !h->fp64) ? 3 : 1;
+  const int cand_r[4] = {64, 80, 96, 128};
+  const int nr = (tune_regs && !h->fp64) ? 4 : 1;
   constexpr int kIters = 6;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   HCA_TRY(cudaEventCreate(&e0));

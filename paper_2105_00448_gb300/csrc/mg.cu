@@ -633,7 +633,10 @@ __global__ void __launch_bounds__(128) k_mg_restrict_rows(Ctx c, int which, int 
 // producing coarse sites X = 2j, 2j+1.  Every load of the item (the four own
 // rows, their eight outer neighbour rows, the x neighbours at the group's
 // ends) is issued before u = (omega/d) r is formed, so an item costs one
-// memory round trip.  Same arithmetic as restrict_fused_at.  The kernel also
+// memory round trip.  The arithmetic of restrict_fused_at, except that the
+// diagonal term d u = d (omega/d) r is taken as omega r (equal up to the
+// rounding of omega/d; the post-smoothing kernel uses the same identity), so
+// the diagonal is not read: r and omega/d, 8 B per site.  The kernel also
 // stores the pre-smoothed iterate after its residual correction,
 // v = u + (omega/d)(r - A u), into mg_t0 for the post-smoothing kernel.
 template <typename T>
@@ -642,7 +645,6 @@ __global__ void __launch_bounds__(128) k_mg_restrict0_rows(Ctx c, int which) {
   T* __restrict__ vv = (T*)c.mg_t0;
   const T* __restrict__ rr = (const T*)c.r;
   const T* __restrict__ ww = (const T*)c.mg_w;
-  const T* __restrict__ dd = (const T*)c.d;
   const MGLevel* LV = (const MGLevel*)c.mg_lv;
   const long long total = c.mg_rowstart[c.n_reps];
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
@@ -669,85 +671,69 @@ __global__ void __launch_bounds__(128) k_mg_restrict0_rows(Ctx c, int which) {
     const int y0 = 2 * Y, z0 = 2 * Z, x0 = 4 * j;
     const long long eb = rd.off + (long long)x0 + sy * y0 + sz * z0;   // fine (x0, y0, z0)
     const T cpl = (T)op_coupling(rd, which);
-    // rows: own (a, b) = (y0 + a, z0 + b); outer: y0 - 1, y0 + 2 (for b = 0, 1), z0 - 1, z0 + 2 (for a = 0, 1)
-    bool ok[12];
-    long long off[12];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        ok[2 * a + b] = (y0 + a < rd.ny) && (z0 + b < rd.nz);
-        off[2 * a + b] = sy * a + sz * b;
-      }
+    const bool hasl = x0 > 0, hasr = x0 + 4 < rd.nx;
+    const bool y1 = y0 + 1 < rd.ny;
+    T acc0 = T(0), acc1 = T(0);
+    // children in the order of restrict_fused_at (dz outer, dy, dx inner),
+    // one dz half b at a time with its eight rows in registers: slots 0, 1
+    // the half's own rows (y0, y0 + 1), 2, 3 rows y0 - 1 and y0 + 2, 4, 5 the
+    // other half's own rows, 6, 7 the outer z row (z0 - 1 or z0 + 2) under y0, y0 + 1
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
-      ok[4 + b] = y0 > 0 && z0 + b < rd.nz;
-      off[4 + b] = -sy + sz * b;
-      ok[6 + b] = y0 + 2 < rd.ny && z0 + b < rd.nz;
-      off[6 + b] = 2 * sy + sz * b;
-    }
+      if (z0 + b >= rd.nz) break;
+      const int ob = 1 - b;
+      const bool zo = b ? z0 + 2 < rd.nz : z0 > 0;
+      const long long zoff = b ? 2 * sz : -sz;
+      const bool ok[8] = {true, y1, y0 > 0, y0 + 2 < rd.ny, z0 + ob < rd.nz, y1 && z0 + ob < rd.nz, zo, zo && y1};
+      const long long off[8] = {sz * b, sy + sz * b, -sy + sz * b, 2 * sy + sz * b, sz * ob, sy + sz * ob, zoff,
+                                sy + zoff};
+      V4<T> RV[8], WV[8];
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      ok[8 + a] = z0 > 0 && y0 + a < rd.ny;
-      off[8 + a] = sy * a - sz;
-      ok[10 + a] = z0 + 2 < rd.nz && y0 + a < rd.ny;
-      off[10 + a] = sy * a + 2 * sz;
-    }
-    V4<T> RV[12], WV[12], DV[4];
+      for (int t = 0; t < 8; ++t) {
+        RV[t] = ld4_if(rr + eb + off[t], ok[t]);
+        WV[t] = ld4_if(ww + eb + off[t], ok[t]);
+      }
+      // x neighbours of the half's own rows at the group's ends
+      T lr[2], lw[2], rrr[2], rw[2];
 #pragma unroll
-    for (int t = 0; t < 12; ++t) {
-      RV[t] = ld4_if(rr + eb + off[t], ok[t]);
-      WV[t] = ld4_if(ww + eb + off[t], ok[t]);
-    }
+      for (int t = 0; t < 2; ++t) {
+        lr[t] = (ok[t] && hasl) ? rr[eb + off[t] - 1] : T(0);
+        lw[t] = (ok[t] && hasl) ? ww[eb + off[t] - 1] : T(0);
+        rrr[t] = (ok[t] && hasr) ? rr[eb + off[t] + 4] : T(0);
+        rw[t] = (ok[t] && hasr) ? ww[eb + off[t] + 4] : T(0);
+      }
+      // u = (omega/d) r (zero outside the lattice: w = 0 on padding and missing rows)
+      V4<T> U[8];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) DV[t] = ld4_if(dd + eb + off[t], ok[t]);
-    // x neighbours of the own rows at the group's ends
-    T lr[4], lw[4], rrr[4], rw[4];
-    const bool hasl = x0 > 0, hasr = x0 + 4 < rd.nx;
+      for (int t = 0; t < 8; ++t)
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      lr[t] = (ok[t] && hasl) ? rr[eb + off[t] - 1] : T(0);
-      lw[t] = (ok[t] && hasl) ? ww[eb + off[t] - 1] : T(0);
-      rrr[t] = (ok[t] && hasr) ? rr[eb + off[t] + 4] : T(0);
-      rw[t] = (ok[t] && hasr) ? ww[eb + off[t] + 4] : T(0);
-    }
-    // u = (omega/d) r (zero outside the lattice: w = 0 on padding and missing rows)
-    V4<T> U[12];
+        for (int e = 0; e < 4; ++e) U[t].a[e] = (x0 + e < rd.nx) ? WV[t].a[e] * RV[t].a[e] : T(0);
 #pragma unroll
-    for (int t = 0; t < 12; ++t)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) U[t].a[e] = (x0 + e < rd.nx) ? WV[t].a[e] * RV[t].a[e] : T(0);
-    T acc0 = T(0), acc1 = T(0);
-    V4<T> VO[4];   // v = u + (omega/d)(r - A u), zero on padding
-#pragma unroll
-    for (int t = 0; t < 4; ++t) VO[t] = zero4<T>();
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        const int t = 2 * a + b;
-        if (!ok[t]) continue;
-        const V4<T>& ymr = a ? U[b] : U[4 + b];           // row y - 1
-        const V4<T>& ypr = a ? U[6 + b] : U[2 + b];       // row y + 1
-        const V4<T>& zmr = b ? U[2 * a] : U[8 + a];       // row z - 1
-        const V4<T>& zpr = b ? U[10 + a] : U[2 * a + 1];  // row z + 1
-        const T ul = lw[t] * lr[t], ur = rw[t] * rrr[t];
+      for (int a = 0; a < 2; ++a) {
+        if (!ok[a]) continue;
+        const V4<T>& ymr = a ? U[0] : U[2];                 // row y - 1
+        const V4<T>& ypr = a ? U[3] : U[1];                 // row y + 1
+        const V4<T>& zmr = b ? U[4 + a] : U[6 + a];         // row z - 1
+        const V4<T>& zpr = b ? U[6 + a] : U[4 + a];         // row z + 1
+        const T ul = lw[a] * lr[a], ur = rw[a] * rrr[a];
+        V4<T> VO = zero4<T>();   // v = u + (omega/d)(r - A u), zero on padding
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int x = x0 + e;
           if (x >= rd.nx) continue;
-          const T left = e == 0 ? ul : U[t].a[e - 1];
-          const T right = e == 3 ? ur : U[t].a[e + 1];
+          const T left = e == 0 ? ul : U[a].a[e - 1];
+          const T right = e == 3 ? ur : U[a].a[e + 1];
           const T nb = (x > 0 ? left : T(0)) + (x < rd.nx - 1 ? right : T(0)) + ymr.a[e] + ypr.a[e] + zmr.a[e] + zpr.a[e];
-          const T res = RV[t].a[e] - (DV[t].a[e] * U[t].a[e] - cpl * nb);
+          // d u = d (omega/d) r = omega r: the diagonal is not read
+          const T du = WV[a].a[e] != T(0) ? (T)MG_OMEGA * RV[a].a[e] : T(0);
+          const T res = RV[a].a[e] - (du - cpl * nb);
           if (e < 2) acc0 += res;
           else acc1 += res;
-          VO[t].a[e] = fma(WV[t].a[e], res, U[t].a[e]);
+          VO.a[e] = fma(WV[a].a[e], res, U[a].a[e]);
         }
+        st4(vv + eb + off[a], VO);
       }
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-      if (ok[t]) st4(vv + eb + off[t], VO[t]);
+    }
     T* rhs1 = (T*)L1.rhs;
     const long long cb = ((long long)Z * L1.ny + Y) * L1.nx + 2 * j;
     if (2 * j < L1.nx) rhs1[cb] = acc0;

@@ -637,13 +637,21 @@ struct ScaledAcc {
 // which forms z itself; otherwise it stores the Jacobi z = r / d and sums r.z.
 // Per site the arithmetic is FP32 and float-float (FP64 runs at a small
 // fraction of the FP32 rate on this GPU).
-template <int KIND, bool FIRST, bool MG>
+// The epilogue of a row kernel in either form (block per chunk, or
+// persistent rows with block-level chunk arrivals).
+template <bool PERSIST, class Fin, class Post>
+__device__ __forceinline__ void dc_epilogue(const Ctx& c, int ndot, int chunk, Fin fin, Post post) {
+  if (PERSIST) block_arrivals(c, ndot, fin, post);
+  else warp_epilogue(c, ndot, chunk, fin, post);
+}
+
+template <int KIND, bool FIRST, bool MG, bool PERSIST = false>
 __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const float* __restrict__ x_hi,
                                                      const float* __restrict__ x_lo, CondArg outer,
                                                      CondArg inner) {
   HCA_COUNT_KERNEL(c);
   __shared__ double s_G0;
-  const int2 ch = c.chunks[blockIdx.x];
+  const int2 ch = PERSIST ? make_int2(0, 0) : c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
   const RepSolve sv = c.solve[ch.x];
   const bool live = FIRST || sv.active || sv.dc_apply;
@@ -669,10 +677,9 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
     const float bvessel = (float)(bax ? 2.0 * rd.r_K * rd.K0 : rd.r_K * rd.K0);
     const RowIter it = row_iter(rd);
     const float cpl32 = (float)cpl;
-    for (int rbase = it.warp * it.rpw; rbase < rd.chunk_rows; rbase += it.nw * it.rpw) {
-      const int rl = rbase + it.sub;
-      const bool row_ok = rl < nrows;
-      const RowGeo geo = row_geo(rd, ch.y + (row_ok ? rl : 0));
+    // one row j (chunk slot rl of `chunk`; row_ok false: a padding slot of the last chunk)
+    auto row = [&](int chunk, int rl, bool row_ok, int j) {
+      const RowGeo geo = row_geo(rd, j);
       ScaledAcc la[NDOT];
       float carry_h = 0.f, carry_l = 0.f;
       for (int itn = 0; itn < it.niter; ++itn) {
@@ -814,10 +821,20 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
       double acc[NDOT];
 #pragma unroll
       for (int k = 0; k < NDOT; ++k) acc[k] = la[k].value();
-      store_row(c, blockIdx.x, rl, row_ok, it.sl, it.lpr, acc, 3);
+      store_row(c, chunk, rl, row_ok, it.sl, it.lpr, acc, 3);
+    };
+    if (PERSIST) {
+      const int R = rd.ny * rd.nz, cr = rd.chunk_rows;
+      for (int j = persist_row_begin(R) + it.warp; j < persist_row_end(R); j += it.nw) row(j / cr, j % cr, true, j);
+    } else {
+      for (int rbase = it.warp * it.rpw; rbase < rd.chunk_rows; rbase += it.nw * it.rpw) {
+        const int rl = rbase + it.sub;
+        const bool row_ok = rl < nrows;
+        row(blockIdx.x, rl, row_ok, ch.y + (row_ok ? rl : 0));
+      }
     }
   }
-  warp_epilogue(c, 3, blockIdx.x,
+  dc_epilogue<PERSIST>(c, 3, blockIdx.x,
                  [&](int r, const double* s3) -> int {
                    const RepDesc& rr = c.reps[r];
                    RepSolve& s = c.solve[r];
@@ -949,14 +966,26 @@ __global__ void __launch_bounds__(512) k_dc_update(Ctx c, float* __restrict__ x_
 }  // namespace
 
 // ------------------------------------------------------------- launchers --
+int persist_grid(const void* fn, int threads, int sm_count);
+
+template <int KIND, bool FIRST, bool MG>
+static void launch_dc_residual_v(const Ctx& c, int which, const float* x_hi, const float* x_lo, CondArg outer,
+                                 CondArg inner) {
+  if (c.persist) {
+    const int g = persist_grid((const void*)k_dc_residual<KIND, FIRST, MG, true>, c.threads, c.sm_count);
+    k_dc_residual<KIND, FIRST, MG, true><<<g, c.threads, 0, c.stream>>>(c, which, x_hi, x_lo, outer, inner);
+  } else {
+    k_dc_residual<KIND, FIRST, MG, false><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, x_hi, x_lo, outer, inner);
+  }
+}
+
 template <int KIND>
 static void launch_dc_residual_t(const Ctx& c, int which, const float* x_hi, const float* x_lo, bool first,
                                  CondArg outer, CondArg inner) {
-  const dim3 g(c.n_chunks), b(c.threads);
-  if (first && c.mg) k_dc_residual<KIND, true, true><<<g, b, 0, c.stream>>>(c, which, x_hi, x_lo, outer, inner);
-  else if (first) k_dc_residual<KIND, true, false><<<g, b, 0, c.stream>>>(c, which, x_hi, x_lo, outer, inner);
-  else if (c.mg) k_dc_residual<KIND, false, true><<<g, b, 0, c.stream>>>(c, which, x_hi, x_lo, outer, inner);
-  else k_dc_residual<KIND, false, false><<<g, b, 0, c.stream>>>(c, which, x_hi, x_lo, outer, inner);
+  if (first && c.mg) launch_dc_residual_v<KIND, true, true>(c, which, x_hi, x_lo, outer, inner);
+  else if (first) launch_dc_residual_v<KIND, true, false>(c, which, x_hi, x_lo, outer, inner);
+  else if (c.mg) launch_dc_residual_v<KIND, false, true>(c, which, x_hi, x_lo, outer, inner);
+  else launch_dc_residual_v<KIND, false, false>(c, which, x_hi, x_lo, outer, inner);
 }
 
 void launch_dc_residual(const Ctx& c, int which, const void* x_hi, const void* x_lo, bool first, CondArg outer,

@@ -75,7 +75,7 @@ def test_step_roofline_follows_its_formula():
     prof = {"pass_a": {"launches": 20, "ms": 0.0}, "residual": {"launches": 6, "ms": 0.0},
             "mg_post0": {"launches": 26, "ms": 0.0}}
     r = bench.step_roofline(prof, steps, sites, ms, 0.125)
-    per_site = 70 + 13 * 3 + 40 * 10 + 13 * (33 + 33 * 0.125)
+    per_site = 70 + 13 * 3 + 40 * 10 + 13 * (29 + 33 * 0.125)
     assert abs(r["bytes_per_site"] - per_site) < 1e-9
     assert abs(r["achieved"] - per_site * sites / 4e-3 / 1e9) < 1e-9
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
