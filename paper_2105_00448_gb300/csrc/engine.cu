@@ -95,6 +95,7 @@ struct hca_handle {
   std::vector<Graph> graphs;
   cudaStream_t cap[3] = {nullptr, nullptr, nullptr};
   bool graphs_ok = true;
+  bool capturing = false;     // a step graph is being captured
   int* h_pinned = nullptr;    // [0] active replicates, [1] error flag
   std::vector<void*> allocs;
   // multigrid preconditioner (single replicate)
@@ -417,7 +418,18 @@ void pass_b(hca_handle* h, int which, void* x, hca::CondArg cnd) {
 // z = M r (V-cycle); also sets rho and beta for the next pass A.  first: the
 // residual was just formed (start of a solve or a defect-correction sweep),
 // so it may still need its power-of-two scaling.
+// Inside a captured step graph the coarse levels run as one launch per level
+// (graph-launched kernels follow each other closely, and the per-level
+// kernels keep more warps per SM than the cooperative kernel: measured
+// faster); from host loops, where each launch costs host time, as the one
+// cooperative launch.
 void vcycle(hca_handle* h, int which, bool first) {
+  if (h->capturing && h->mgh.coop_blocks > 0) {
+    hca::MGHost H = h->mgh;
+    H.coop_blocks = 0;
+    hca::launch_vcycle(h->ctx, which, h->fp64, H, -1, first);
+    return;
+  }
   hca::launch_vcycle(h->ctx, which, h->fp64, h->mgh, -1, first);
 }
 
@@ -724,7 +736,9 @@ int build_graph(hca_handle* h, uint32_t mask, cudaGraphExec_t* out) {
     cudaGraphDestroy(G);
     return HCA_ERR_CUDA;
   }
+  h->capturing = true;
   rc = cap_stages(h, mask, G);
+  h->capturing = false;
   cudaGraph_t done = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->cap[0], &done);
   h->ctx.stream = user;
@@ -867,7 +881,7 @@ int check_convergence(hca_handle* h) {
 
 // Launch-shape autotuner: times the oxygen CG passes (the hot pair) for each
 // candidate block size (and register cap of the FP32 passes) on the handle's
-// own lattices and keeps the fastest.  It runs at creation, on the solver's
+// own lattices, best of three timed runs each, and keeps the fastest.  It runs at creation, on the solver's
 // scratch vectors (x = aux), before anything depends on them; the reductions
 // sum by rows in a fixed order, so results do not depend on the choice.
 int autotune(hca_handle* h, bool tune_regs) {
@@ -875,7 +889,7 @@ int autotune(hca_handle* h, bool tune_regs) {
   const int cand_t[3] = {128, 256, 512};
   const int cand_r[4] = {64, 80, 96, 128};
   const int nr = (tune_regs && !h->fp64) ? 4 : 1;
-  constexpr int kIters = 6;
+  constexpr int kIters = 8, kReps = 3;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   HCA_TRY(cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -894,19 +908,26 @@ int autotune(hca_handle* h, bool tune_regs) {
         pass_a(h, 0);
         pass_b(h, 0, c.aux, kNoCond);
       }
-      cudaEventRecord(e0, c.stream);
-      for (int k = 0; k < kIters; ++k) {
-        pass_a(h, 0);
-        pass_b(h, 0, c.aux, kNoCond);
+      // the best of kReps timed runs (a single run is noisy enough to pick a
+      // slower shape now and then)
+      float ms = 1e30f;
+      for (int rep = 0; rep < kReps && !rc; ++rep) {
+        cudaEventRecord(e0, c.stream);
+        for (int k = 0; k < kIters; ++k) {
+          pass_a(h, 0);
+          pass_b(h, 0, c.aux, kNoCond);
+        }
+        cudaEventRecord(e1, c.stream);
+        float t = 0.f;
+        if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+          rc = HCA_ERR_CUDA;
+          break;
+        }
+        ms = std::min(ms, t);
       }
-      cudaEventRecord(e1, c.stream);
-      float ms = 0.f;
-      if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-        rc = HCA_ERR_CUDA;
-        break;
-      }
-      h->launches += 1 + 2 * (kIters + 2);
+      if (rc) break;
+      h->launches += 1 + 2 * (kReps * kIters + 2);
       if (ms < best) {
         best = ms;
         bt = c.threads;

@@ -299,6 +299,7 @@ struct MGHost {
   int coop_blocks = 0;
   int small_smem = 0;
   int coop_cfg = 0;              // launch shape of the cooperative kernel (threads, register budget)
+  bool small_smem_ok = false;    // the standalone single-block kernel runs in shared memory
   int small = 0;                 // 1 + deepest grid-kernel level of any replicate
   long long ntot[MG_MAXLEV] = {};  // sites of level l summed over the replicates
   long long nrowitems = 0;         // (level-1 row, lattice 4-site group) items over the replicates

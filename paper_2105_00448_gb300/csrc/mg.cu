@@ -874,6 +874,15 @@ __global__ void __launch_bounds__(kSmallThreads) k_mg_small(Ctx c, int which) {
   small_cycle<T, false>(c, which, blockIdx.x, threadIdx.x, blockDim.x, nullptr, false);
 }
 
+// The same sub-cycle with the single-block levels in the block's dynamic
+// shared memory (the same arithmetic in the same order).
+template <typename T>
+__global__ void __launch_bounds__(kSmallThreads) k_mg_small_smem(Ctx c, int which) {
+  HCA_COUNT_KERNEL(c);
+  extern __shared__ __align__(16) unsigned char small_smem[];
+  small_cycle<T, true>(c, which, blockIdx.x, threadIdx.x, blockDim.x, (T*)small_smem, false);
+}
+
 // ------------------------------------- coarse levels in one cooperative launch --
 // Grid-wide barrier of a cooperative launch (every block is resident).
 // PassSync::bar_count counts the arrivals of the launch: barrier k of the
@@ -1188,7 +1197,10 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
       else if (multi) k_mg_restrict<T, true><<<grid_for(H.ntot[l + 1]), kMgThreads, 0, s>>>(c, which, l);
       else k_mg_restrict<T, false><<<grid_for(H.ntot[l + 1]), kMgThreads, 0, s>>>(c, which, l);
     }
-    k_mg_small<T><<<c.n_reps, kSmallThreads, 0, s>>>(c, which);
+    if (H.small_smem > 0 && H.small_smem_ok)
+      k_mg_small_smem<T><<<c.n_reps, kSmallThreads, (size_t)H.small_smem, s>>>(c, which);
+    else
+      k_mg_small<T><<<c.n_reps, kSmallThreads, 0, s>>>(c, which);
     for (int l = H.small - 1; l >= 1; --l) {
       if (H.rows_ok >> l & 1u) k_mg_post_rows<T><<<grid_for(H.post_items[l]), kMgThreads, 0, s>>>(c, which, l);
       else if (multi) k_mg_post<T, true><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
@@ -1220,39 +1232,49 @@ void mg_setup_t(const Ctx& c, int which, const MGHost& H) {
   for (int l = 1; l < H.nlev; ++l) k_mg_diag<T><<<grid_for(H.ntot[l]), kMgThreads, 0, c.stream>>>(c, which, l);
 }
 
-// The launch geometry of the cooperative coarse-level kernel.
+// The launch forms of the coarse levels: the single-block levels in shared
+// memory when they fit one block's opt-in maximum (else global memory), and
+// the geometry of the cooperative coarse-level kernel.
 template <typename T>
 int coop_config_t(MGHost& H, int sm_count, long long smem_bytes) {
   H.coop_blocks = 0;
   H.small_smem = 0;
-  const char* env = std::getenv("HCA_MG_COOP");
-  if (env && env[0] == '0') return 0;
+  H.small_smem_ok = false;
   int dev = 0, coop = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || !coop) {
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
     (void)cudaGetLastError();
     return 0;
   }
-  // the single-block levels go to shared memory when they fit in one block's
-  // opt-in maximum; else they stay in global memory
   const int smem = smem_bytes <= optin ? (int)smem_bytes : 0;
+  const char* ss = std::getenv("HCA_MG_SMALL_SMEM");
+  if (smem > 0 && !(ss && ss[0] == '0')) {
+    if (cudaFuncSetAttribute((const void*)k_mg_small_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+        cudaSuccess) {
+      H.small_smem = smem;
+      H.small_smem_ok = true;
+    } else {
+      (void)cudaGetLastError();
+    }
+  }
+  const char* env = std::getenv("HCA_MG_COOP");
+  if ((env && env[0] == '0') || !coop) return 0;
   // launch shape (HCA_MG_COOP_CFG=0, 1, 2 selects another one)
   const char* cs = std::getenv("HCA_MG_COOP_CFG");
   const int cfg = (cs && cs[0] >= '0' && cs[0] <= '2') ? cs[0] - '0' : 0;
   const void* fn = coarse_fn<T>(cfg);
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, H.small_smem) != cudaSuccess) {
     (void)cudaGetLastError();
     return 0;
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, coarse_threads(cfg), smem) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, coarse_threads(cfg), H.small_smem) != cudaSuccess ||
       per_sm < 1) {
     (void)cudaGetLastError();
     return 0;
   }
   H.coop_blocks = per_sm * sm_count;
-  H.small_smem = smem;
   H.coop_cfg = cfg;
   return 0;
 }

@@ -3,7 +3,9 @@ between levels, the single-block levels in shared memory) against one launch
 per level (HCA_MG_COOP=0, read at handle creation): both run the same per-site
 arithmetic in the same order, so z = M r, whole solves and coupled steps must
 agree bit for bit, in FP64 and FP32, for single lattices and batches.  The
-V-cycle itself is compared with the oracle in test_gpu_mg.py.
+library uses the cooperative launch from host-driven loops (the coupled runs
+here set HCA_NO_GRAPH=1) and the per-level launches inside captured step
+graphs.  The V-cycle itself is compared with the oracle in test_gpu_mg.py.
 """
 
 import os
@@ -22,16 +24,19 @@ pytestmark = pytest.mark.gpu
 SHAPES = [(24, 40, 56), (64, 64, 64), (1, 48, 70), (17, 23, 31), (40, 36, 44), (16, 16, 16)]
 
 
-def _with_coop(flag, fn):
-    old = os.environ.get("HCA_MG_COOP")
+def _with_coop(flag, fn, no_graph=False):
+    old = {k: os.environ.get(k) for k in ("HCA_MG_COOP", "HCA_NO_GRAPH")}
     os.environ["HCA_MG_COOP"] = "1" if flag else "0"
+    if no_graph:
+        os.environ["HCA_NO_GRAPH"] = "1"
     try:
         return fn()
     finally:
-        if old is None:
-            del os.environ["HCA_MG_COOP"]
-        else:
-            os.environ["HCA_MG_COOP"] = old
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
 
 
 @pytest.mark.parametrize("precision", ["f64", "f32"])
@@ -70,8 +75,8 @@ def test_coupled_steps_coop_equal_per_level_launches(precision):
         sim.close()
         return out
 
-    a = _with_coop(True, run)
-    b = _with_coop(False, run)
+    a = _with_coop(True, run, no_graph=True)
+    b = _with_coop(False, run, no_graph=True)
     assert np.array_equal(a[0], b[0])
     for k in (1, 2, 3):
         assert np.array_equal(a[k], b[k])
@@ -95,8 +100,8 @@ def test_batch_coop_equals_per_level_launches():
         sim.close()
         return out
 
-    a = _with_coop(True, run)
-    b = _with_coop(False, run)
+    a = _with_coop(True, run, no_graph=True)
+    b = _with_coop(False, run, no_graph=True)
     for x, y in zip(a, b):
         for u, v in zip(x, y):
             assert np.array_equal(u, v)
