@@ -518,7 +518,10 @@ def test_trained_network_cuts_oxygen_iterations_on_held_out_solves():
     test_s = collect(1, 3, 4)
     net = hca.Net(*shape, trainable=True)
     net.set_params(warmstart.init_params(0))
-    warmstart.train(net, hca.make_config(nx, ny, nz), train_s, 4000, 3e-3, seed=1, lr_final=1.5e-4,
+    # lr 1e-3 -> 1e-4: at 3e-3 the final loss depends strongly on the sample
+    # order (measured: 7 % to 31 % fewer held-out iterations over three
+    # orders); at 1e-3 every order tried gave 34-39 %
+    warmstart.train(net, hca.make_config(nx, ny, nz), train_s, 4000, 1e-3, seed=1, lr_final=1e-4,
                     w_res=0.03)
     it = {0: 0, 1: 0}
     for s in test_s:
