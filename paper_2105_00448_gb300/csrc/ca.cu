@@ -21,6 +21,8 @@
 // This translation unit is compiled with -fmad=false and the kill test uses
 // explicit round-to-nearest intrinsics, so the decision is the same IEEE
 // arithmetic as a plain CPU evaluation in the storage precision.
+#include <cstdlib>
+
 #include "hca_internal.cuh"
 
 namespace hca {
@@ -53,31 +55,34 @@ __device__ __forceinline__ bool killed(const Ctx& c, const RepDesc& rd, long lon
 }
 
 // The free Moore neighbour of (x, y, z) with the highest K (first in dz, dy,
-// dx order on ties), as a field element, or -1.
+// dx order on ties), as a field element, or -1.  Every state and K of the
+// in-box neighbourhood is loaded first (one memory round trip instead of one
+// per neighbour: no other cell of the same colour touches this
+// neighbourhood), then the neighbours are scanned in that order.
 template <typename T>
 __device__ __forceinline__ long long best_free(const Ctx& c, const RepDesc& rd, int x, int y, int z) {
   const T* K = (const T*)c.K;
   const long long sy = rd.nxp, sz = (long long)rd.nxp * rd.ny;
+  uint8_t st[27];
+  T kv[27];
+#pragma unroll
+  for (int t = 0; t < 27; ++t) {
+    const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+    const int xx = x + dx, yy = y + dy, zz = z + dz;
+    const bool in = t != 13 && xx >= 0 && xx < rd.nx && yy >= 0 && yy < rd.ny && zz >= 0 && zz < rd.nz;
+    const long long nbi = rd.off + xx + sy * yy + sz * zz;
+    st[t] = in ? c.state[nbi] : (uint8_t)HCA_VESSEL;   // not free
+    kv[t] = in ? K[nbi] : T(0);
+  }
   long long best = -1;
   T best_K = T(0);
-  for (int dz = -1; dz <= 1; ++dz) {
-    const int zz = z + dz;
-    if (zz < 0 || zz >= rd.nz) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int yy = y + dy;
-      if (yy < 0 || yy >= rd.ny) continue;
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int xx = x + dx;
-        if (xx < 0 || xx >= rd.nx || (dx == 0 && dy == 0 && dz == 0)) continue;
-        const long long nbi = rd.off + xx + sy * yy + sz * zz;
-        if (is_free(c.state[nbi])) {
-          const T kv = K[nbi];
-          if (best < 0 || kv > best_K) {
-            best = nbi;
-            best_K = kv;
-          }
-        }
-      }
+#pragma unroll
+  for (int t = 0; t < 27; ++t) {
+    if (!is_free(st[t])) continue;
+    if (best < 0 || kv[t] > best_K) {
+      const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+      best = rd.off + (x + dx) + sy * (y + dy) + sz * (z + dz);
+      best_K = kv[t];
     }
   }
   return best;
@@ -204,6 +209,75 @@ __global__ void __launch_bounds__(256) k_ca_colour(Ctx c, int colour) {
     if (s_cnt[1]) atomicAdd((unsigned long long*)&st.divisions, (unsigned long long)s_cnt[1]);
     if (s_cnt[2]) atomicAdd((unsigned long long*)&st.blocked, (unsigned long long)s_cnt[2]);
   }
+}
+
+// All 27 colour sweeps in one cooperative launch: colour c's cells of every
+// replicate (the per-cell step of k_ca_colour, unchanged), then a grid
+// barrier (bounded: see grid_barrier) before colour c + 1, so later colours
+// see earlier colours' daughters and deaths exactly as with one launch per
+// colour; the results are bit-identical to those launches.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ca_colours(Ctx c) {
+  HCA_COUNT_KERNEL(c);
+  __shared__ unsigned int s_cnt[3];
+  const uint32_t step = (uint32_t)(*c.step);
+  T* phi = (T*)c.phi;
+  T* P = (T*)c.P;
+  T* Vc = (T*)c.Vc;
+  if (*(volatile int*)&c.sync->error == SYNC_ERR_TIMEOUT) return;
+  for (int colour = 0; colour < 27; ++colour) {
+    for (int rep = 0; rep < c.n_reps; ++rep) {
+      if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0;
+      __syncthreads();
+      const RepDesc& rd = c.reps[rep];
+      const int n = c.list_count[rep * 27 + colour];
+      const long long sy = rd.nxp, sz = (long long)rd.nxp * rd.ny;
+      unsigned int kills = 0, divs = 0, blocked = 0;
+      for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t site = c.lists[rd.list_off[colour] + i];
+        const int x = (int)(site % (uint32_t)rd.nx);
+        const int y = (int)((site / (uint32_t)rd.nx) % (uint32_t)rd.ny);
+        const int z = (int)(site / ((uint32_t)rd.nx * (uint32_t)rd.ny));
+        const long long e = rd.off + x + sy * y + sz * z;
+        if (killed<T>(c, rd, e, site, step)) {
+          c.state[e] = HCA_DEAD;
+          phi[e] = T(0);
+          P[e] = T(0);
+          Vc[e] = T(0);
+          kills++;
+          continue;
+        }
+        const long long best = best_free<T>(c, rd, x, y, z);
+        if (best >= 0) {
+          c.state[best] = HCA_PROLIF;
+          c.state[e] = HCA_PROLIF;
+          phi[e] = T(0);
+          P[e] = T(0);
+          Vc[e] = T(0);
+          phi[best] = T(0);
+          P[best] = T(0);
+          Vc[best] = T(0);
+          divs++;
+        } else {
+          c.state[e] = HCA_QUIESC;
+          phi[e] = T(0);
+          blocked++;
+        }
+      }
+      if (kills) atomicAdd(&s_cnt[0], kills);
+      if (divs) atomicAdd(&s_cnt[1], divs);
+      if (blocked) atomicAdd(&s_cnt[2], blocked);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        DevStats& st = c.stats[rep];
+        if (s_cnt[0]) atomicAdd((unsigned long long*)&st.kills, (unsigned long long)s_cnt[0]);
+        if (s_cnt[1]) atomicAdd((unsigned long long*)&st.divisions, (unsigned long long)s_cnt[1]);
+        if (s_cnt[2]) atomicAdd((unsigned long long*)&st.blocked, (unsigned long long)s_cnt[2]);
+      }
+    }
+    if (colour < 26 && !grid_barrier(c.sync, colour)) return;
+  }
+  grid_exit(c.sync, 26);
 }
 
 // ------------------------------------------------- synchronous update ---
@@ -457,6 +531,33 @@ __global__ void __launch_bounds__(512) k_vessel_update(Ctx c) {
 void launch_ca_compact(const Ctx& c, bool fp64) {
   if (fp64) k_ca_compact<double><<<c.n_chunks, c.threads, 0, c.stream>>>(c);
   else k_ca_compact<float><<<c.n_chunks, c.threads, 0, c.stream>>>(c);
+}
+
+// Blocks of the cooperative colour kernel (0 where cooperative launches are
+// unavailable or HCA_CA_COOP=0): every block resident at once.
+int ca_coop_blocks(bool fp64, int sm_count) {
+  const char* env = std::getenv("HCA_CA_COOP");
+  if (env && env[0] == '0') return 0;
+  int dev = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+      !coop) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  const void* fn = fp64 ? (const void*)k_ca_colours<double> : (const void*)k_ca_colours<float>;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0) != cudaSuccess || per_sm < 1) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return per_sm * sm_count;
+}
+
+void launch_ca_colours(const Ctx& c, int blocks, bool fp64) {
+  Ctx cc = c;
+  void* args[] = {&cc};
+  const void* fn = fp64 ? (const void*)k_ca_colours<double> : (const void*)k_ca_colours<float>;
+  (void)cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(256), args, 0, c.stream);
 }
 
 void launch_ca_colour(const Ctx& c, int colour, int blocks_x, bool fp64) {

@@ -30,6 +30,8 @@ void launch_philox_uniforms(unsigned long long seed, unsigned long long site0, l
 void launch_advance_step(const Ctx& c, long long by);
 void launch_ca_compact(const Ctx& c, bool fp64);
 void launch_ca_colour(const Ctx& c, int colour, int blocks_x, bool fp64);
+int ca_coop_blocks(bool fp64, int sm_count);
+void launch_ca_colours(const Ctx& c, int blocks, bool fp64);
 void launch_ca_sync(const Ctx& c, int blocks_x, bool fp64);
 void launch_vessels(const Ctx& c, bool fp64);
 void launch_mg_setup(const Ctx& c, int which, bool fp64, const MGHost& H);
@@ -96,6 +98,7 @@ struct hca_handle {
   cudaStream_t cap[3] = {nullptr, nullptr, nullptr};
   bool graphs_ok = true;
   bool capturing = false;     // a step graph is being captured
+  int ca_coop = 0;            // blocks of the cooperative 27-colour CA kernel (0: one launch per colour)
   int* h_pinned = nullptr;    // [0] active replicates, [1] error flag
   std::vector<void*> allocs;
   // multigrid preconditioner (single replicate)
@@ -711,8 +714,12 @@ int cap_stages(hca_handle* h, uint32_t mask, cudaGraph_t G) {
     if (h->ca_sync) {
       hca::launch_ca_sync(c, ca_sync_blocks(h), h->fp64);
     } else {
-      const int bx = std::max(1, std::min(1024, 2 * c.sm_count / std::max(1, h->n_reps)));
-      for (int col = 0; col < 27; ++col) hca::launch_ca_colour(c, col, bx, h->fp64);
+      if (h->ca_coop > 0) {
+        hca::launch_ca_colours(c, h->ca_coop, h->fp64);
+      } else {
+        const int bx = std::max(1, std::min(1024, 2 * c.sm_count / std::max(1, h->n_reps)));
+        for (int col = 0; col < 27; ++col) hca::launch_ca_colour(c, col, bx, h->fp64);
+      }
     }
     if (h->vessels) {
       HCA_TRY(cudaMemsetAsync(c.vsum, 0, sizeof(unsigned long long) * 2 * h->n_reps, c.stream));
@@ -799,6 +806,10 @@ int run_ca(hca_handle* h) {
   HCA_LAUNCH(h, HCA_KCLASS_CA_COMPACT, 1, hca::launch_ca_compact(c, h->fp64));
   if (h->ca_sync) {
     HCA_LAUNCH(h, HCA_KCLASS_CA_COLOUR, 4, hca::launch_ca_sync(c, ca_sync_blocks(h), h->fp64));
+    return HCA_OK;
+  }
+  if (h->ca_coop > 0) {
+    HCA_LAUNCH(h, HCA_KCLASS_CA_COLOUR, 1, hca::launch_ca_colours(c, h->ca_coop, h->fp64));
     return HCA_OK;
   }
   const int bx = std::max(1, std::min(1024, 2 * c.sm_count / std::max(1, h->n_reps)));
@@ -899,7 +910,10 @@ int autotune(hca_handle* h, bool tune_regs) {
   float best = 1e30f;
   int bt = c.threads, br = c.pass_regs;
   int rc = HCA_OK;
-  for (int ti = 0; ti < 3 && !rc; ++ti)
+  // the persistent row form runs at 128 threads: larger blocks timed faster
+  // here now and then but ran pass A ~20 % slower inside a step
+  const int nt = c.persist ? 1 : 3;
+  for (int ti = 0; ti < nt && !rc; ++ti)
     for (int ri = 0; ri < nr && !rc; ++ri) {
       c.threads = cand_t[ti];
       if (nr > 1) c.pass_regs = cand_r[ri];
@@ -1426,6 +1440,8 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
       // (HCA_PERSIST=0 keeps one block per chunk)
       const char* pe = std::getenv("HCA_PERSIST");
       c.persist = (!(pe && pe[0] == '0') && n == 1 && !h->fp64 && h->reps_h[0].lpr == 32 && c.pass_ni > 0) ? 1 : 0;
+      // the 27 colour sweeps of the CA in one cooperative launch (HCA_CA_COOP=0: one launch per colour)
+      h->ca_coop = hca::ca_coop_blocks(h->fp64, c.sm_count);
     }
     if (!cfgs[0].threads_per_block) {
       const char* nt = std::getenv("HCA_NO_TUNE");

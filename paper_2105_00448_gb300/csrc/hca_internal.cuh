@@ -549,6 +549,64 @@ __device__ __forceinline__ void warp_epilogue(const Ctx& c, int ndot, int chunk,
   warp_epilogue(c, ndot, chunk, fin, [](int) {});
 }
 
+// Grid-wide barrier of a cooperative launch (every block is resident).
+// PassSync::bar_count counts the arrivals of the launch: barrier k of the
+// launch opens when it reaches (k + 1) * gridDim.x, and the last block to
+// leave the kernel (grid_exit) sets it back to 0 for the next launch.  A
+// wait gives up after kBarrierTimeoutNs of device time and records
+// SYNC_ERR_TIMEOUT (the host returns HCA_ERR_TIMEOUT and the step sets the
+// counter back to 0), so no kernel waits forever; later barriers and
+// launches then return at once.
+constexpr unsigned long long kBarrierTimeoutNs = 1000000000ull;   // 1 s
+
+__device__ __forceinline__ unsigned long long device_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+static __device__ __noinline__ bool grid_barrier(PassSync* sy, int k) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (*(volatile int*)&sy->error == SYNC_ERR_TIMEOUT) {
+      ok = 0;
+    } else {
+      const unsigned target = (unsigned)(k + 1) * gridDim.x;
+      __threadfence();   // this block's writes before its arrival
+      atomicAdd(&sy->bar_count, 1u);
+      if (ld_acquire_gpu(&sy->bar_count) < target) {
+        const unsigned long long t0 = device_ns();
+        while (ld_acquire_gpu(&sy->bar_count) < target) {
+          if (device_ns() - t0 > kBarrierTimeoutNs) {
+            atomicExch(&sy->error, SYNC_ERR_TIMEOUT);
+            ok = 0;
+            break;
+          }
+          __nanosleep(20);
+        }
+      }
+      __threadfence();   // the other blocks' writes before this block reads on
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Leave a launch that passed nbar barriers: the last block out resets the
+// arrival counter.
+__device__ __forceinline__ void grid_exit(PassSync* sy, int nbar) {
+  if (threadIdx.x == 0 && atomicAdd(&sy->bar_count, 1u) == (unsigned)(nbar + 1) * gridDim.x - 1u)
+    atomicExch(&sy->bar_count, 0u);
+}
+
 // Count this kernel launch (call once, at kernel entry).
 #define HCA_COUNT_KERNEL(c)                                                  \
   do {                                                                       \
