@@ -43,22 +43,25 @@ CORR_LEN = 8.0
 #   pass A reads z, p_old, d and writes p_new and q = A p_new; pass B reads p, q, x, r and
 #   writes x, r;
 #   defect-correction residual (later sweeps) reads x_hi, x_lo, d, a, b and writes z, dx, r;
-#   multigrid on the lattice: the first sweep + restriction reads r, omega/d and writes the
-#   pre-smoothed iterate v and the 1/8-size coarse right-hand side; the prolongation + last sweep
-#   reads v, r, omega/d and the 1/8-size coarse correction and writes z; ODE reads state, K and
+#   multigrid on the lattice, four kernels per V-cycle: the two pre-sweeps read r, 1/d and
+#   write the pre-smoothed iterate v (12 B); the restriction reads v, r, 1/d, d and writes
+#   v' = v + (W2/d)(r - A v) and the 1/8-size coarse right-hand side (20.5 B); the prolongation
+#   + first post-sweep reads v', 1/d and the 1/8-size coarse correction and writes y (12.5 B);
+#   the last post-sweep reads y, r, 1/d, d and writes z (20 B); ODE reads state, K and
 #   updates phi, P, Vc
 BYTES_PER_SITE = {"pass_a": 20, "pass_b": 24, "setup": 17, "residual": 24, "ode": 29,
-                  "mg_restrict0": 12.5, "mg_post0": 16.5}
+                  "mg_pre0": 12, "mg_restrict0": 20.5, "mg_post0": 12.5, "mg_last0": 20}
 # the method's minimum per site where this design moves more: CG pass A reads
 # z, d, p_old and writes p (16 B); storing q = A p for pass B adds 4 B
 BYTES_MIN_PER_SITE = {**BYTES_PER_SITE, "pass_a": 16}
 # step-level algorithmic bytes per lattice site (FP32 storage): set-up and
 # solve start-up, ODE and CA 70 B, 13 B per defect-correction residual sweep,
 # 40 B per CG iteration (two-pass minimum), plus per V-cycle the lattice's
-# first sweep + restriction and prolongation + last sweep (29 B) and the
-# coarse levels (33 B per coarse site: restriction reads rhs, omega/d, d and
-# writes the next level's rhs; the post-sweep reads rhs, omega/d, d, the
-# coarser correction and writes x)
+# smoothing and transfers (29 B: the pre-sweeps and restriction need r and
+# 1/d and leave one iterate and the next level's rhs, the post-sweeps need
+# that iterate, r, 1/d and the coarse correction and write z, whatever the
+# number of sweeps when they are fused) and the coarse levels (33 B per
+# coarse site, by the same count)
 STEP_FIXED_B, STEP_DC_B, STEP_IT_B, VCYCLE_LATTICE_B, VCYCLE_COARSE_B = 70, 13, 40, 29, 33
 
 
@@ -402,8 +405,9 @@ def run_gpu(args):
     design_bytes = BYTES_PER_SITE[dom] * sites
     tr = traffic_record(dom)
     kernel_names = {"pass_a": "k_pass_a<float>", "pass_b": "k_pass_b<float>", "setup": "k_setup<float>",
-                    "residual": "k_dc_residual", "ode": "k_ode<float>", "mg_restrict0": "k_mg_restrict0_rows<float>",
-                    "mg_post0": "k_mg_post0<float, true>"}
+                    "residual": "k_dc_residual", "ode": "k_ode<float>", "mg_pre0": "k_mg_pre0<float>",
+                    "mg_restrict0": "k_mg_restrict0_rows<float>", "mg_post0": "k_mg_post0<float, true>",
+                    "mg_last0": "k_mg_post0<float, false>"}
     roofline = {"bound": "hbm", "kernel": kernel_names[dom], "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": tr * sites if tr is not None else None,

@@ -257,9 +257,11 @@ typedef struct hca_handle hca_handle;
 #define HCA_KCLASS_CA_COLOUR 6  /* CA colour sweeps */
 #define HCA_KCLASS_OTHER 7
 #define HCA_KCLASS_MG 8         /* multigrid: coarse levels, r scaling, level diagonals */
-#define HCA_KCLASS_MG_RESTRICT0 9 /* multigrid: first sweep + restriction on the lattice */
-#define HCA_KCLASS_MG_POST0 10  /* multigrid: prolongation + last sweep on the lattice, r.z */
-#define HCA_NKCLASS 11
+#define HCA_KCLASS_MG_RESTRICT0 9 /* multigrid: restriction of the pre-smoothed residual on the lattice */
+#define HCA_KCLASS_MG_POST0 10  /* multigrid: prolongation + first post-sweep on the lattice */
+#define HCA_KCLASS_MG_PRE0 11   /* multigrid: the two pre-sweeps on the lattice */
+#define HCA_KCLASS_MG_LAST0 12  /* multigrid: last post-sweep on the lattice, r.z */
+#define HCA_NKCLASS 13
 
 typedef struct hca_profile {
   int64_t launches[HCA_NKCLASS];

@@ -444,8 +444,9 @@ int vcycle_host(hca_handle* h, int which, bool first) {
     return HCA_OK;
   }
   const hca::MGHost& H = h->mgh;
-  const int cls[3] = {HCA_KCLASS_MG_RESTRICT0, HCA_KCLASS_MG, HCA_KCLASS_MG_POST0};
-  for (int part = 0; part < 3; ++part) {
+  const int cls[hca::kVcycleParts] = {HCA_KCLASS_MG,      HCA_KCLASS_MG_PRE0,  HCA_KCLASS_MG_RESTRICT0,
+                                       HCA_KCLASS_MG,      HCA_KCLASS_MG_POST0, HCA_KCLASS_MG_LAST0};
+  for (int part = 0; part < hca::kVcycleParts; ++part) {
     const int n = hca::vcycle_part_launches(H, part, first);
     if (n) HCA_LAUNCH(h, cls[part], n, hca::launch_vcycle(h->ctx, which, h->fp64, H, part, first));
   }

@@ -282,13 +282,22 @@ struct MGLevel {
   double cscale;            // coupling of this level / coupling of the lattice (2^level)
 };
 
-// multigrid constants (the FP64 reference uses the same)
-constexpr double MG_OMEGA = 0.8;
+// multigrid constants (the FP64 reference uses the same).  Above the
+// coarsest level a V-cycle smooths with two Jacobi sweeps before the coarse
+// correction, of weights MG_W1 then MG_W2, and two after it, MG_W2 then
+// MG_W1: the reciprocals of the roots 1.25 +- 0.75 cos(pi/4) of the
+// degree-2 Chebyshev polynomial on [0.5, 2] (a Chebyshev polynomial
+// smoother for the spectrum of D^-1 A).  The coarsest level takes
+// MG_NU_COARSE sweeps of weight MG_OMEGA_COARSE.
+constexpr double MG_W1 = 1.0 / (1.25 + 0.75 * 0.70710678118654752440);
+constexpr double MG_W2 = 1.0 / (1.25 - 0.75 * 0.70710678118654752440);
+constexpr double MG_OMEGA_COARSE = 0.8;
 constexpr int MG_NU_COARSE = 16;
 constexpr long long MG_MIN_SITES = 512;     // coarsening stops at or below this size
 constexpr long long MG_SMALL_SITES = 4096;  // levels this small run inside one block
 
 constexpr int MG_MAXLEV = 16;
+constexpr int kVcycleParts = 6;   // launch groups of a V-cycle (see launch_vcycle)
 
 // Host summary of the hierarchies of a handle's replicates (launch geometry).
 struct MGHost {
@@ -336,7 +345,7 @@ struct Ctx {
   int persist;      // 1: the CG passes and the lattice post-sweep run in persistent row form (one FP32 lattice)
   void* r;
   void* mg_t0;
-  void* mg_w;         // omega / d on the lattice (0 where d = 0)
+  void* mg_w;         // 1 / d on the lattice (0 where d = 0)
   const void* mg_lv;  // device MGLevel[n_reps][MG_MAXLEV] (level 0 unused)
   const long long* mg_start;  // [MG_MAXLEV][n_reps + 1] prefix sums of each level's sites over the replicates
   const int2* mg_rep;         // per replicate: (levels, first single-block level)

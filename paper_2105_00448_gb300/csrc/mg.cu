@@ -143,7 +143,7 @@ struct RepCursor {
 };
 
 // ------------------------------------------------------ per-site steps --
-// d_C(I) = c_C n_C(I) + sum over children of max(0, d_F - c_F n_F); w_C = omega / d_C
+// d_C(I) = c_C n_C(I) + sum over children of max(0, d_F - c_F n_F); w_C = 1 / d_C
 template <typename T>
 __device__ void coarse_diag_at(const View<T>& F, const View<T>& C, long long S) {
   int X, Y, Z;
@@ -156,36 +156,56 @@ __device__ void coarse_diag_at(const View<T>& F, const View<T>& C, long long S) 
   }
   const double dc = (double)C.c * C.nbcount(X, Y, Z) + a;
   C.d[C.at(X, Y, Z)] = (T)dc;
-  C.w[C.at(X, Y, Z)] = dc != 0.0 ? (T)(MG_OMEGA / dc) : T(0);
+  C.w[C.at(X, Y, Z)] = dc != 0.0 ? (T)(1.0 / dc) : T(0);
 }
 
-// w = omega / d on the lattice
+// w = 1 / d on the lattice
 template <typename T>
 __device__ void lattice_w_at(const View<T>& V, long long s) {
   int X, Y, Z;
   V.coords(s, X, Y, Z);
   const long long e = V.at(X, Y, Z);
   const T d = V.d[e];
-  V.w[e] = d != T(0) ? (T)MG_OMEGA / d : T(0);
+  V.w[e] = d != T(0) ? T(1) / d : T(0);
 }
 
-// x = omega rhs / d
+// Every sweep of weight om at a site scales by om * w, one rounding: the
+// row-vector and per-site forms below form it the same way.
 template <typename T>
-__device__ void sweep_first_at(const View<T>& V, long long s) {
+__device__ __forceinline__ T wt(double om, T w) {
+  return (T)om * w;
+}
+
+// rhs - (A u) at a site with diagonal d and neighbour sum nb, as
+// rhs - fma(d, u, -(c nb)): one explicit rounding order, so that the
+// per-site and row-vector forms of a step give the same bits whatever the
+// compiler would contract.
+template <typename T>
+__device__ __forceinline__ T resid(T rhs, T d, T u, T c, T nb) {
+  return rhs - fma(d, u, -(c * nb));
+}
+
+// a * b rounded on its own (never contracted into a following sum)
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+// dst = (om / d) rhs: a sweep from zero
+template <typename T>
+__device__ void sweep_first_at(const View<T>& V, T* __restrict__ dst, long long s, double om) {
   int X, Y, Z;
   V.coords(s, X, Y, Z);
   const long long e = V.at(X, Y, Z);
-  V.x[e] = V.w[e] * V.rhs[e];
+  dst[e] = wt(om, V.w[e]) * V.rhs[e];
 }
 
-// dst = src + omega (rhs - A src) / d
+// dst = src + (om / d)(rhs - A src)
 template <typename T>
-__device__ void sweep_at(const View<T>& V, const T* __restrict__ src, T* __restrict__ dst, long long s) {
+__device__ void sweep_at(const View<T>& V, const T* __restrict__ src, T* __restrict__ dst, long long s, double om) {
   int X, Y, Z;
   V.coords(s, X, Y, Z);
   const long long e = V.at(X, Y, Z);
   const T r = V.rhs[e] - V.apply(src, X, Y, Z, e);
-  dst[e] = src[e] + V.w[e] * r;
+  dst[e] = fma(wt(om, V.w[e]), r, src[e]);
 }
 
 // rhs_C(I) = sum over children of (rhs_F - A_F x_F)
@@ -198,7 +218,15 @@ __device__ void restrict_residual_at(const View<T>& F, const View<T>& C, long lo
     const int x = 2 * X + (k & 1), y = 2 * Y + ((k >> 1) & 1), z = 2 * Z + (k >> 2);
     if (x < F.nx && y < F.ny && z < F.nz) {
       const long long e = F.at(x, y, z);
-      acc += F.rhs[e] - F.apply(F.x, x, y, z, e);
+      const T* u = F.x;
+      T nb = T(0);
+      if (x > 0) nb += u[e - 1];
+      if (x < F.nx - 1) nb += u[e + 1];
+      if (y > 0) nb += u[e - F.sy];
+      if (y < F.ny - 1) nb += u[e + F.sy];
+      if (z > 0) nb += u[e - F.sz];
+      if (z < F.nz - 1) nb += u[e + F.sz];
+      acc += resid(F.rhs[e], F.d[e], u[e], F.c, nb);
     }
   }
   C.rhs[C.at(X, Y, Z)] = acc;
@@ -231,12 +259,13 @@ struct Walk {
 };
 
 // The per-site steps on a dense level (element index = site index s) at
-// known coordinates: the same arithmetic, in the same order, as
-// sweep_at / restrict_residual_at / prolong_at.
+// known coordinates: the same arithmetic, in the same order, as sweep_at /
+// restrict_residual_at.
 template <typename T>
-__device__ __forceinline__ void sweep_xyz(const View<T>& V, const T* src, T* dst, int X, int Y, int Z, int s) {
+__device__ __forceinline__ void sweep_xyz(const View<T>& V, const T* src, T* dst, int X, int Y, int Z, int s,
+                                          double om) {
   const T r = V.rhs[s] - V.apply(src, X, Y, Z, s);
-  dst[s] = src[s] + V.w[s] * r;
+  dst[s] = fma(wt(om, V.w[s]), r, src[s]);
 }
 
 template <typename T>
@@ -252,65 +281,33 @@ __device__ __forceinline__ void restrict_residual_xyz(const View<T>& F, const Vi
   C.rhs[S] = acc;
 }
 
+// x_F += P x_C (in place: a site reads only its own x and its coarse cell)
 template <typename T>
 __device__ __forceinline__ void prolong_xyz(const View<T>& F, const View<T>& C, int X, int Y, int Z, int s) {
-  F.t[s] = F.x[s] + C.x[(X >> 1) + (long long)C.nx * ((Y >> 1) + (long long)C.ny * (Z >> 1))];
+  F.x[s] = F.x[s] + C.x[(X >> 1) + (long long)C.nx * ((Y >> 1) + (long long)C.ny * (Z >> 1))];
 }
 
-// t_F = x_F + P x_C
-template <typename T>
-__device__ void prolong_at(const View<T>& F, const View<T>& C, long long s) {
-  int X, Y, Z;
-  F.coords(s, X, Y, Z);
-  const long long e = F.at(X, Y, Z);
-  F.t[e] = F.x[e] + C.x[C.at(X >> 1, Y >> 1, Z >> 1)];
-}
+// The three sweeps of a grid level l >= 1 around its coarse correction, each
+// fused with the step before it (the iterate they start from is formed at
+// the site and its neighbours, not stored):
+//   SM_PRE:  x = u + (W2 / d)(rhs - A u), u = (W1 / d) rhs (both pre-sweeps)
+//   SM_POST: t = u + (W2 / d)(rhs - A u), u = x + P x_C (prolongation, first post-sweep)
+//   SM_LAST: x = t + (W1 / d)(rhs - A t) (second post-sweep)
+// Neighbour sums in the order x - 1, x + 1, y - 1, y + 1, z - 1, z + 1 (the
+// row-vector form smooth_rows forms the same sums).
+enum { SM_PRE = 0, SM_POST = 1, SM_LAST = 2 };
 
-// First sweep from zero, evaluated where it is needed: u = omega rhs / d
-template <typename T>
-__device__ __forceinline__ T u_first(const View<T>& V, long long e) {
-  return V.w[e] * V.rhs[e];
-}
-
-// rhs_C(I) = sum over children of (rhs_F - A_F u), u = omega rhs_F / d_F
-// (the pre-smoothing sweep fused into the restriction; u is not stored)
-template <typename T>
-__device__ void restrict_fused_at(const View<T>& F, const View<T>& C, long long S) {
-  int X, Y, Z;
-  C.coords(S, X, Y, Z);
-  T acc = T(0);
-  for (int k = 0; k < 8; ++k) {
-    const int x = 2 * X + (k & 1), y = 2 * Y + ((k >> 1) & 1), z = 2 * Z + (k >> 2);
-    if (x < F.nx && y < F.ny && z < F.nz) {
-      const long long e = F.at(x, y, z);
-      // nb += (omega/d) rhs as one fused multiply-add per neighbour (the
-      // row-vector restriction forms the same sums)
-      T nb = T(0);
-      if (x > 0) nb = fma(F.w[e - 1], F.rhs[e - 1], nb);
-      if (x < F.nx - 1) nb = fma(F.w[e + 1], F.rhs[e + 1], nb);
-      if (y > 0) nb = fma(F.w[e - F.sy], F.rhs[e - F.sy], nb);
-      if (y < F.ny - 1) nb = fma(F.w[e + F.sy], F.rhs[e + F.sy], nb);
-      if (z > 0) nb = fma(F.w[e - F.sz], F.rhs[e - F.sz], nb);
-      if (z < F.nz - 1) nb = fma(F.w[e + F.sz], F.rhs[e + F.sz], nb);
-      acc += F.rhs[e] - (F.d[e] * u_first(F, e) - F.c * nb);
-    }
-  }
-  C.rhs[C.at(X, Y, Z)] = acc;
-}
-
-// x_F = u + omega (rhs_F - A_F u) / d_F with u = omega rhs_F / d_F + P x_C
-// (prolongation fused into the post-smoothing sweep; u is not stored)
-template <typename T>
-__device__ void post_fused_at(const View<T>& F, const View<T>& C, long long s) {
+template <typename T, int MODE>
+__device__ void smooth_at(const View<T>& F, const View<T>& C, long long s) {
   auto u = [&](int x, int y, int z) {
     const long long ef = F.at(x, y, z);
-    return fma(F.w[ef], F.rhs[ef], C.x[C.at(x >> 1, y >> 1, z >> 1)]);
+    if (MODE == SM_PRE) return mul_rn(wt(MG_W1, F.w[ef]), F.rhs[ef]);
+    if (MODE == SM_POST) return F.x[ef] + C.x[C.at(x >> 1, y >> 1, z >> 1)];
+    return F.t[ef];
   };
   int X, Y, Z;
   F.coords(s, X, Y, Z);
   const long long e = F.at(X, Y, Z);
-  const T d = F.d[e];
-  const T w = F.w[e];
   T nb = T(0);
   if (X > 0) nb += u(X - 1, Y, Z);
   if (X < F.nx - 1) nb += u(X + 1, Y, Z);
@@ -319,7 +316,10 @@ __device__ void post_fused_at(const View<T>& F, const View<T>& C, long long s) {
   if (Z > 0) nb += u(X, Y, Z - 1);
   if (Z < F.nz - 1) nb += u(X, Y, Z + 1);
   const T uc = u(X, Y, Z);
-  F.x[e] = uc + w * (F.rhs[e] - (d * uc - F.c * nb));
+  const T res = resid(F.rhs[e], F.d[e], uc, F.c, nb);
+  const T out = fma(wt(MODE == SM_LAST ? MG_W1 : MG_W2, F.w[e]), res, uc);
+  if (MODE == SM_POST) F.t[e] = out;
+  else F.x[e] = out;
 }
 
 // Grid-stride loop over the flattened sites of level l of every replicate
@@ -377,13 +377,13 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_scale0(Ctx c, int which) {
   }
 }
 
-// The lattice as the coarsest level (single replicate): t0 = omega r / d
+// The lattice as the coarsest level (single replicate): t0 = (omega / d) r
 template <typename T>
 __global__ void __launch_bounds__(kMgThreads) k_mg_first0(Ctx c, int which) {
   HCA_COUNT_KERNEL(c);
   const View<T> V = view<T>(c, which, 0, 0);
   for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < V.n(); s += (long long)gridDim.x * blockDim.x)
-    sweep_first_at<T>(V, s);
+    sweep_first_at<T>(V, V.x, s, MG_OMEGA_COARSE);
 }
 
 template <typename T>
@@ -391,18 +391,19 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_sweep0(Ctx c, int which, cons
   HCA_COUNT_KERNEL(c);
   const View<T> V = view<T>(c, which, 0, 0);
   for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < V.n(); s += (long long)gridDim.x * blockDim.x)
-    sweep_at<T>(V, src, dst, s);
+    sweep_at<T>(V, src, dst, s, MG_OMEGA_COARSE);
 }
 
-// Restriction from level l to l + 1 for the replicates whose level l is
-// swept by grid kernels (l < their first single-block level).  MULTI = false:
-// one replicate, whose views are fixed for the whole loop (fewer registers).
-// t0, st: this thread's first item and the loop stride.
+// Restriction of the pre-smoothed residual from level l to l + 1 for the
+// replicates whose level l is swept by grid kernels (l below their first
+// single-block level).  MULTI = false: one replicate, whose views are fixed
+// for the whole loop (fewer registers).  t0, st: this thread's first item
+// and the loop stride.
 template <typename T, bool MULTI>
 __device__ __forceinline__ void restrict_sites(const Ctx& c, int which, int l, long long t0, long long st) {
   if (!MULTI) {
     const View<T> F = view<T>(c, which, 0, l), C = view<T>(c, which, 0, l + 1);
-    for (long long s = t0; s < C.n(); s += st) restrict_fused_at<T>(F, C, s);
+    for (long long s = t0; s < C.n(); s += st) restrict_residual_at<T>(F, C, s);
     return;
   }
   RepCursor<T> k;   // cursor on level l + 1 (its F is the coarse view)
@@ -414,7 +415,7 @@ __device__ __forceinline__ void restrict_sites(const Ctx& c, int which, int l, l
       Ff = view<T>(c, which, k.r, l);
     }
     if (skip) continue;
-    restrict_fused_at<T>(Ff, k.F, q - k.lo);
+    restrict_residual_at<T>(Ff, k.F, q - k.lo);
   }
 }
 
@@ -424,11 +425,12 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_restrict(Ctx c, int which, in
   restrict_sites<T, MULTI>(c, which, l, grid_t0(), grid_st());
 }
 
-template <typename T, bool MULTI>
-__device__ __forceinline__ void post_sites(const Ctx& c, int which, int l, long long t0, long long st) {
+// One of the sweeps of smooth_at over the sites of grid level l.
+template <typename T, bool MULTI, int MODE>
+__device__ __forceinline__ void smooth_sites(const Ctx& c, int which, int l, long long t0, long long st) {
   if (!MULTI) {
     const View<T> F = view<T>(c, which, 0, l), C = view<T>(c, which, 0, l + 1);
-    for (long long s = t0; s < F.n(); s += st) post_fused_at<T>(F, C, s);
+    for (long long s = t0; s < F.n(); s += st) smooth_at<T, MODE>(F, C, s);
     return;
   }
   RepCursor<T> k;
@@ -436,14 +438,14 @@ __device__ __forceinline__ void post_sites(const Ctx& c, int which, int l, long 
   HCA_MG_FOR_SITES_FROM(l, t0, st) {
     if (k.at(c, which, l, q, true)) skip = l >= c.mg_rep[k.r].y;
     if (skip) continue;
-    post_fused_at<T>(k.F, k.C, q - k.lo);
+    smooth_at<T, MODE>(k.F, k.C, q - k.lo);
   }
 }
 
-template <typename T, bool MULTI>
-__global__ void __launch_bounds__(kMgThreads) k_mg_post(Ctx c, int which, int l) {
+template <typename T, bool MULTI, int MODE>
+__global__ void __launch_bounds__(kMgThreads) k_mg_smooth(Ctx c, int which, int l) {
   HCA_COUNT_KERNEL(c);
-  post_sites<T, MULTI>(c, which, l, grid_t0(), grid_st());
+  smooth_sites<T, MULTI, MODE>(c, which, l, grid_t0(), grid_st());
 }
 
 // Replicate owning item q of a prefix table (the last r with pre[r] <= q).
@@ -457,14 +459,15 @@ __device__ __forceinline__ int rep_of_items(const long long* pre, int n, long lo
   return lo;
 }
 
-// Post-smoothing on coarse level l >= 1 in row-vector form (every
+// The sweeps of smooth_at on grid level l >= 1 in row-vector form (every
 // replicate's level rows a whole number of 4-site groups; items of a batch
-// found through the level's prefix table): one thread per group; every load of the group (rhs and omega/d of its row and the four
-// neighbour rows, the sites left and right of it, d, the level-(l+1)
-// correction under each row) is issued before u = (omega/d) rhs + P x_C is
-// formed.  The same arithmetic, in the same order, as post_fused_at.
-template <typename T>
-__device__ __forceinline__ void post_rows(const Ctx& c, int which, int l, long long t0, long long st) {
+// found through the level's prefix table): one thread per group; every load
+// of the group (the arrays that form u on its row and the four neighbour
+// rows, the sites left and right of it, the row's rhs, 1/d and d, for
+// SM_POST the level-(l+1) correction under each row) is issued before u is
+// formed.  The same arithmetic, in the same order, as smooth_at.
+template <typename T, int MODE>
+__device__ __forceinline__ void smooth_rows(const Ctx& c, int which, int l, long long t0, long long st) {
   const long long* pre = c.mg_post_items + (long long)l * (c.n_reps + 1);
   const long long items = pre[c.n_reps];
   int r = -1;
@@ -488,30 +491,61 @@ __device__ __forceinline__ void post_rows(const Ctx& c, int which, int l, long l
     const long long e = F.at(X0, Y, Z);
     const bool rok[5] = {true, Y > 0, Y < F.ny - 1, Z > 0, Z < F.nz - 1};
     const long long roff[5] = {0, -F.sy, F.sy, -F.sz, F.sz};
-    const int ry[5] = {Y, Y - 1, Y + 1, Y, Y};
-    const int rz[5] = {Z, Z, Z, Z - 1, Z + 1};
-    V4<T> RH[5], WV[5];
-    T C0[5], C1[5];
-#pragma unroll
-    for (int t = 0; t < 5; ++t) {
-      RH[t] = ld4_if(F.rhs + e + roff[t], rok[t]);
-      WV[t] = ld4_if(F.w + e + roff[t], rok[t]);
-      const long long cb = rok[t] ? C.at(2 * j, ry[t] >> 1, rz[t] >> 1) : 0;
-      C0[t] = rok[t] ? C.x[cb] : T(0);
-      C1[t] = rok[t] ? C.x[cb + 1] : T(0);
-    }
     const bool has_l = j > 0, has_r = j + 1 < gpr;
-    const T wl = has_l ? F.w[e - 1] : T(0), rl = has_l ? F.rhs[e - 1] : T(0);
-    const T wr = has_r ? F.w[e + 4] : T(0), rr = has_r ? F.rhs[e + 4] : T(0);
-    const long long cy = C.at(0, Y >> 1, Z >> 1);
-    const T cl = has_l ? C.x[cy + 2 * j - 1] : T(0), cr = has_r ? C.x[cy + 2 * j + 2] : T(0);
+    V4<T> U[5], RH0, W0;
+    T ul, ur;
     const V4<T> D = ld4(F.d + e);
-    V4<T> U[5];
+    if (MODE == SM_PRE) {
+      V4<T> RH[5], WV[5];
 #pragma unroll
-    for (int t = 0; t < 5; ++t)
+      for (int t = 0; t < 5; ++t) {
+        RH[t] = ld4_if(F.rhs + e + roff[t], rok[t]);
+        WV[t] = ld4_if(F.w + e + roff[t], rok[t]);
+      }
+      const T wl = has_l ? F.w[e - 1] : T(0), rl = has_l ? F.rhs[e - 1] : T(0);
+      const T wr = has_r ? F.w[e + 4] : T(0), rr = has_r ? F.rhs[e + 4] : T(0);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) U[t].a[k] = rok[t] ? fma(WV[t].a[k], RH[t].a[k], k < 2 ? C0[t] : C1[t]) : T(0);
-    const T ul = has_l ? fma(wl, rl, cl) : T(0), ur = has_r ? fma(wr, rr, cr) : T(0);
+      for (int t = 0; t < 5; ++t)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) U[t].a[k] = rok[t] ? mul_rn(wt(MG_W1, WV[t].a[k]), RH[t].a[k]) : T(0);
+      ul = has_l ? mul_rn(wt(MG_W1, wl), rl) : T(0);
+      ur = has_r ? mul_rn(wt(MG_W1, wr), rr) : T(0);
+      RH0 = RH[0];
+      W0 = WV[0];
+    } else {
+      const T* src = MODE == SM_POST ? F.x : F.t;
+      const int ry[5] = {Y, Y - 1, Y + 1, Y, Y};
+      const int rz[5] = {Z, Z, Z, Z - 1, Z + 1};
+      V4<T> XV[5];
+      T C0[5], C1[5];
+#pragma unroll
+      for (int t = 0; t < 5; ++t) {
+        XV[t] = ld4_if(src + e + roff[t], rok[t]);
+        if (MODE == SM_POST) {
+          const long long cb = rok[t] ? C.at(2 * j, ry[t] >> 1, rz[t] >> 1) : 0;
+          C0[t] = rok[t] ? C.x[cb] : T(0);
+          C1[t] = rok[t] ? C.x[cb + 1] : T(0);
+        }
+      }
+      RH0 = ld4(F.rhs + e);
+      W0 = ld4(F.w + e);
+      const T xl = has_l ? src[e - 1] : T(0), xr = has_r ? src[e + 4] : T(0);
+      if (MODE == SM_POST) {
+        const long long cy = C.at(0, Y >> 1, Z >> 1);
+        const T cl = has_l ? C.x[cy + 2 * j - 1] : T(0), cr = has_r ? C.x[cy + 2 * j + 2] : T(0);
+#pragma unroll
+        for (int t = 0; t < 5; ++t)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) U[t].a[k] = rok[t] ? XV[t].a[k] + (k < 2 ? C0[t] : C1[t]) : T(0);
+        ul = has_l ? xl + cl : T(0);
+        ur = has_r ? xr + cr : T(0);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 5; ++t) U[t] = rok[t] ? XV[t] : zero4<T>();
+        ul = xl;
+        ur = xr;
+      }
+    }
     V4<T> Xo;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -523,24 +557,27 @@ __device__ __forceinline__ void post_rows(const Ctx& c, int which, int l, long l
       if (rok[3]) nb += U[3].a[k];
       if (rok[4]) nb += U[4].a[k];
       const T uc = U[0].a[k];
-      Xo.a[k] = uc + WV[0].a[k] * (RH[0].a[k] - (D.a[k] * uc - F.c * nb));
+      const T res = resid(RH0.a[k], D.a[k], uc, F.c, nb);
+      Xo.a[k] = fma(wt(MODE == SM_LAST ? MG_W1 : MG_W2, W0.a[k]), res, uc);
     }
-    *reinterpret_cast<V4<T>*>(F.x + e) = Xo;
+    *reinterpret_cast<V4<T>*>((MODE == SM_POST ? F.t : F.x) + e) = Xo;
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kMgThreads) k_mg_post_rows(Ctx c, int which, int l) {
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kMgThreads) k_mg_smooth_rows(Ctx c, int which, int l) {
   HCA_COUNT_KERNEL(c);
-  post_rows<T>(c, which, l, grid_t0(), grid_st());
+  smooth_rows<T, MODE>(c, which, l, grid_t0(), grid_st());
 }
 
-// Restriction from coarse level l >= 1 to l + 1 in row-vector form (every
-// replicate's level-l rows whole 4-site groups; batches as in k_mg_post_rows): one thread per group
-// of the four fine rows (2Y + dy, 2Z + dz) under coarse row (Y, Z), producing
-// coarse sites 2j, 2j + 1; all loads (rhs and omega/d of the 4 own and 8 outer
-// rows, d, the x neighbours) are issued before u = (omega/d) rhs is formed.
-// The same arithmetic, children in the same order, as restrict_fused_at.
+// Restriction of the pre-smoothed residual from grid level l >= 1 to l + 1
+// in row-vector form (every replicate's level-l rows whole 4-site groups;
+// batches as in k_mg_smooth_rows): one thread per group of the four fine rows
+// (2Y + dy, 2Z + dz) under coarse row (Y, Z), producing coarse sites 2j,
+// 2j + 1; all loads of a dz half (x on its 2 own and 6 outer rows, rhs and d
+// on the own rows, the x neighbours at the group's ends) are issued before
+// its residuals are formed.  The same arithmetic, children in the same order,
+// as restrict_residual_at.
 template <typename T>
 __device__ __forceinline__ void restrict_rows(const Ctx& c, int which, int l, long long t0, long long st) {
   const long long* pre = c.mg_restr_items + (long long)l * (c.n_reps + 1);
@@ -567,10 +604,10 @@ __device__ __forceinline__ void restrict_rows(const Ctx& c, int which, int l, lo
     const bool hasl = x0 > 0, hasr = x0 + 4 < F.nx;
     const bool y1 = y0 + 1 < F.ny;
     T acc[2] = {T(0), T(0)};
-    // children in the order of restrict_fused_at (dz outer, dy, dx inner),
-    // one dz half at a time with its eight rows in registers: slots 0, 1 the
-    // half's own rows (y0, y0 + 1), 2, 3 rows y0 - 1 and y0 + 2, 4, 5 the
-    // other half's own rows, 6, 7 the outer z row (z0 - 1 or z0 + 2) under y0, y0 + 1
+    // children in the order of restrict_residual_at (dz outer, dy, dx inner),
+    // one dz half b at a time: slots 0, 1 the half's own rows (y0, y0 + 1),
+    // 2, 3 rows y0 - 1 and y0 + 2, 4, 5 the other half's own rows, 6, 7 the
+    // outer z row (z0 - 1 or z0 + 2) under y0, y0 + 1
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
       if (z0 + b >= F.nz) break;
@@ -580,21 +617,19 @@ __device__ __forceinline__ void restrict_rows(const Ctx& c, int which, int l, lo
       const bool ok[8] = {true, y1, y0 > 0, y0 + 2 < F.ny, z0 + ob < F.nz, y1 && z0 + ob < F.nz, zo, zo && y1};
       const long long off[8] = {F.sz * b, F.sy + F.sz * b, -F.sy + F.sz * b, 2 * F.sy + F.sz * b,
                                 F.sz * ob, F.sy + F.sz * ob, zoff, F.sy + zoff};
-      V4<T> RV[8], WV[8], DV[2];
+      V4<T> XV[8], RV[2], DV[2];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        RV[t] = ld4_if(F.rhs + eb + off[t], ok[t]);
-        WV[t] = ld4_if(F.w + eb + off[t], ok[t]);
-      }
-#pragma unroll
-      for (int t = 0; t < 2; ++t) DV[t] = ld4_if(F.d + eb + off[t], ok[t]);
-      T lr[2], lw[2], rrr[2], rw[2];
+      for (int t = 0; t < 8; ++t) XV[t] = ld4_if(F.x + eb + off[t], ok[t]);
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
-        lr[t] = (ok[t] && hasl) ? F.rhs[eb + off[t] - 1] : T(0);
-        lw[t] = (ok[t] && hasl) ? F.w[eb + off[t] - 1] : T(0);
-        rrr[t] = (ok[t] && hasr) ? F.rhs[eb + off[t] + 4] : T(0);
-        rw[t] = (ok[t] && hasr) ? F.w[eb + off[t] + 4] : T(0);
+        RV[t] = ld4_if(F.rhs + eb + off[t], ok[t]);
+        DV[t] = ld4_if(F.d + eb + off[t], ok[t]);
+      }
+      T xl[2], xr[2];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        xl[t] = (ok[t] && hasl) ? F.x[eb + off[t] - 1] : T(0);
+        xr[t] = (ok[t] && hasr) ? F.x[eb + off[t] + 4] : T(0);
       }
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
@@ -604,15 +639,14 @@ __device__ __forceinline__ void restrict_rows(const Ctx& c, int which, int l, lo
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int x = x0 + e;
-          const T u = WV[a].a[e] * RV[a].a[e];
           T nb = T(0);
-          if (x > 0) nb = e == 0 ? fma(lw[a], lr[a], nb) : fma(WV[a].a[e - 1], RV[a].a[e - 1], nb);
-          if (x < F.nx - 1) nb = e == 3 ? fma(rw[a], rrr[a], nb) : fma(WV[a].a[e + 1], RV[a].a[e + 1], nb);
-          if (y0 + a > 0) nb = fma(WV[ym].a[e], RV[ym].a[e], nb);
-          if (y0 + a < F.ny - 1) nb = fma(WV[yp].a[e], RV[yp].a[e], nb);
-          if (z0 + b > 0) nb = fma(WV[zm].a[e], RV[zm].a[e], nb);
-          if (z0 + b < F.nz - 1) nb = fma(WV[zp].a[e], RV[zp].a[e], nb);
-          acc[e >> 1] += RV[a].a[e] - (DV[a].a[e] * u - F.c * nb);
+          if (x > 0) nb += e == 0 ? xl[a] : XV[a].a[e - 1];
+          if (x < F.nx - 1) nb += e == 3 ? xr[a] : XV[a].a[e + 1];
+          if (y0 + a > 0) nb += XV[ym].a[e];
+          if (y0 + a < F.ny - 1) nb += XV[yp].a[e];
+          if (z0 + b > 0) nb += XV[zm].a[e];
+          if (z0 + b < F.nz - 1) nb += XV[zp].a[e];
+          acc[e >> 1] += resid(RV[a].a[e], DV[a].a[e], XV[a].a[e], F.c, nb);
         }
       }
     }
@@ -628,53 +662,61 @@ __global__ void __launch_bounds__(128) k_mg_restrict_rows(Ctx c, int which, int 
   restrict_rows<T>(c, which, l, grid_t0(), grid_st());
 }
 
-// Restriction from the lattice to level 1 in row-vector form: one thread per
-// 4-site group of the fine rows 2Y, 2Y+1 x 2Z, 2Z+1 under coarse row (Y, Z),
-// producing coarse sites X = 2j, 2j+1.  Every load of the item (the four own
-// rows, their eight outer neighbour rows, the x neighbours at the group's
-// ends) is issued before u = (omega/d) r is formed, so an item costs one
-// memory round trip.  The arithmetic of restrict_fused_at, except that the
-// diagonal term d u = d (omega/d) r is taken as omega r (equal up to the
-// rounding of omega/d; the post-smoothing kernel uses the same identity), so
-// the diagonal is not read: r and omega/d, 8 B per site.  The kernel also
-// stores the pre-smoothed iterate after its residual correction,
-// v = u + (omega/d)(r - A u), into mg_t0 for the post-smoothing kernel.
+// Item q of the lattice's row-vector kernels (one thread per 4-site group of
+// the fine rows 2Y, 2Y + 1 x 2Z, 2Z + 1 under level-1 row (Y, Z), items of a
+// batch through the prefix table mg_rowstart): its replicate, level 1 and
+// fine geometry.
+struct Item0 {
+  int r, j, Y, Z, y0, z0, x0;
+  long long sy, sz, eb;
+};
+__device__ __forceinline__ Item0 item0(const Ctx& c, long long q) {
+  Item0 I;
+  int lo = 0, hi = c.n_reps;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (c.mg_rowstart[mid] <= q) lo = mid;
+    else hi = mid;
+  }
+  I.r = lo;
+  const RepDesc& rd = c.reps[I.r];
+  const MGLevel& L1 = ((const MGLevel*)c.mg_lv)[I.r * MG_MAXLEV + 1];
+  const long long it = q - c.mg_rowstart[I.r];
+  I.j = (int)(it % rd.gpr);
+  const long long R = it / rd.gpr;
+  I.Y = (int)(R % L1.ny);
+  I.Z = (int)(R / L1.ny);
+  I.sy = rd.nxp;
+  I.sz = (long long)rd.nxp * rd.ny;
+  I.y0 = 2 * I.Y;
+  I.z0 = 2 * I.Z;
+  I.x0 = 4 * I.j;
+  I.eb = rd.off + (long long)I.x0 + I.sy * I.y0 + I.sz * I.z0;   // fine (x0, y0, z0)
+  return I;
+}
+
+// Both pre-smoothing sweeps on the lattice in row-vector form:
+// v = u + (W2 / d)(r - A u) with u = (W1 / d) r, stored into dst (the z
+// buffer, free until the last post-sweep).  The diagonal term d u is taken
+// as W1 r (equal up to the rounding of 1/d), so d is not read: r and 1/d,
+// 8 B per site.  Every load of an item (its four own rows, their eight outer
+// neighbour rows, the x neighbours at the group's ends) is issued before u is
+// formed.
 template <typename T>
-__global__ void __launch_bounds__(128) k_mg_restrict0_rows(Ctx c, int which) {
+__global__ void __launch_bounds__(128) k_mg_pre0(Ctx c, int which, T* __restrict__ dst) {
   HCA_COUNT_KERNEL(c);
-  T* __restrict__ vv = (T*)c.mg_t0;
   const T* __restrict__ rr = (const T*)c.r;
   const T* __restrict__ ww = (const T*)c.mg_w;
-  const MGLevel* LV = (const MGLevel*)c.mg_lv;
   const long long total = c.mg_rowstart[c.n_reps];
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
        q += (long long)gridDim.x * blockDim.x) {
-    // replicate of item q (prefix over replicates of coarse rows x groups)
-    int r = 0;
-    {
-      int lo = 0, hi = c.n_reps;
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (c.mg_rowstart[mid] <= q) lo = mid;
-        else hi = mid;
-      }
-      r = lo;
-    }
-    const RepDesc& rd = c.reps[r];
-    const MGLevel& L1 = LV[r * MG_MAXLEV + 1];
-    const long long it = q - c.mg_rowstart[r];
-    const int gpr = rd.gpr;
-    const int j = (int)(it % gpr);
-    const long long R = it / gpr;
-    const int Y = (int)(R % L1.ny), Z = (int)(R / L1.ny);
-    const long long sy = rd.nxp, sz = (long long)rd.nxp * rd.ny;
-    const int y0 = 2 * Y, z0 = 2 * Z, x0 = 4 * j;
-    const long long eb = rd.off + (long long)x0 + sy * y0 + sz * z0;   // fine (x0, y0, z0)
+    const Item0 I = item0(c, q);
+    const RepDesc& rd = c.reps[I.r];
+    const long long sy = I.sy, sz = I.sz, eb = I.eb;
+    const int y0 = I.y0, z0 = I.z0, x0 = I.x0;
     const T cpl = (T)op_coupling(rd, which);
     const bool hasl = x0 > 0, hasr = x0 + 4 < rd.nx;
     const bool y1 = y0 + 1 < rd.ny;
-    T acc0 = T(0), acc1 = T(0);
-    // children in the order of restrict_fused_at (dz outer, dy, dx inner),
     // one dz half b at a time with its eight rows in registers: slots 0, 1
     // the half's own rows (y0, y0 + 1), 2, 3 rows y0 - 1 and y0 + 2, 4, 5 the
     // other half's own rows, 6, 7 the outer z row (z0 - 1 or z0 + 2) under y0, y0 + 1
@@ -693,7 +735,6 @@ __global__ void __launch_bounds__(128) k_mg_restrict0_rows(Ctx c, int which) {
         RV[t] = ld4_if(rr + eb + off[t], ok[t]);
         WV[t] = ld4_if(ww + eb + off[t], ok[t]);
       }
-      // x neighbours of the half's own rows at the group's ends
       T lr[2], lw[2], rrr[2], rw[2];
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
@@ -702,12 +743,12 @@ __global__ void __launch_bounds__(128) k_mg_restrict0_rows(Ctx c, int which) {
         rrr[t] = (ok[t] && hasr) ? rr[eb + off[t] + 4] : T(0);
         rw[t] = (ok[t] && hasr) ? ww[eb + off[t] + 4] : T(0);
       }
-      // u = (omega/d) r (zero outside the lattice: w = 0 on padding and missing rows)
+      // u = (W1 / d) r (zero outside the lattice: w = 0 on padding and missing rows)
       V4<T> U[8];
 #pragma unroll
       for (int t = 0; t < 8; ++t)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) U[t].a[e] = (x0 + e < rd.nx) ? WV[t].a[e] * RV[t].a[e] : T(0);
+        for (int e = 0; e < 4; ++e) U[t].a[e] = (x0 + e < rd.nx) ? wt(MG_W1, WV[t].a[e]) * RV[t].a[e] : T(0);
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
         if (!ok[a]) continue;
@@ -715,8 +756,8 @@ __global__ void __launch_bounds__(128) k_mg_restrict0_rows(Ctx c, int which) {
         const V4<T>& ypr = a ? U[3] : U[1];                 // row y + 1
         const V4<T>& zmr = b ? U[4 + a] : U[6 + a];         // row z - 1
         const V4<T>& zpr = b ? U[6 + a] : U[4 + a];         // row z + 1
-        const T ul = lw[a] * lr[a], ur = rw[a] * rrr[a];
-        V4<T> VO = zero4<T>();   // v = u + (omega/d)(r - A u), zero on padding
+        const T ul = wt(MG_W1, lw[a]) * lr[a], ur = wt(MG_W1, rw[a]) * rrr[a];
+        V4<T> VO = zero4<T>();   // zero on padding
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int x = x0 + e;
@@ -724,20 +765,95 @@ __global__ void __launch_bounds__(128) k_mg_restrict0_rows(Ctx c, int which) {
           const T left = e == 0 ? ul : U[a].a[e - 1];
           const T right = e == 3 ? ur : U[a].a[e + 1];
           const T nb = (x > 0 ? left : T(0)) + (x < rd.nx - 1 ? right : T(0)) + ymr.a[e] + ypr.a[e] + zmr.a[e] + zpr.a[e];
-          // d u = d (omega/d) r = omega r: the diagonal is not read
-          const T du = WV[a].a[e] != T(0) ? (T)MG_OMEGA * RV[a].a[e] : T(0);
+          const T du = WV[a].a[e] != T(0) ? (T)MG_W1 * RV[a].a[e] : T(0);
           const T res = RV[a].a[e] - (du - cpl * nb);
+          VO.a[e] = fma(wt(MG_W2, WV[a].a[e]), res, U[a].a[e]);
+        }
+        st4(dst + eb + off[a], VO);
+      }
+    }
+  }
+}
+
+// Restriction from the lattice to level 1 in row-vector form, from the
+// pre-smoothed iterate v (src, stored by k_mg_pre0): rhs_1 = R (r - A v).  It
+// also stores v' = v + (W2 / d)(r - A v) into mg_t0, the part of the first
+// post-sweep that does not depend on the coarse correction (the post-sweep
+// kernel adds the rest).  Per item and dz half: v on the 2 own and 6 outer
+// rows, r, 1/d and d on the own rows, the x neighbours of v at the group's
+// ends, all loaded before the residuals are formed.  Children in the order
+// of restrict_residual_at.
+template <typename T>
+__global__ void __launch_bounds__(128) k_mg_restrict0_rows(Ctx c, int which, const T* __restrict__ src) {
+  HCA_COUNT_KERNEL(c);
+  T* __restrict__ vo = (T*)c.mg_t0;
+  const T* __restrict__ rr = (const T*)c.r;
+  const T* __restrict__ ww = (const T*)c.mg_w;
+  const T* __restrict__ dd = (const T*)c.d;
+  const MGLevel* LV = (const MGLevel*)c.mg_lv;
+  const long long total = c.mg_rowstart[c.n_reps];
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const Item0 I = item0(c, q);
+    const RepDesc& rd = c.reps[I.r];
+    const MGLevel& L1 = LV[I.r * MG_MAXLEV + 1];
+    const long long sy = I.sy, sz = I.sz, eb = I.eb;
+    const int y0 = I.y0, z0 = I.z0, x0 = I.x0;
+    const T cpl = (T)op_coupling(rd, which);
+    const bool hasl = x0 > 0, hasr = x0 + 4 < rd.nx;
+    const bool y1 = y0 + 1 < rd.ny;
+    T acc0 = T(0), acc1 = T(0);
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      if (z0 + b >= rd.nz) break;
+      const int ob = 1 - b;
+      const bool zo = b ? z0 + 2 < rd.nz : z0 > 0;
+      const long long zoff = b ? 2 * sz : -sz;
+      const bool ok[8] = {true, y1, y0 > 0, y0 + 2 < rd.ny, z0 + ob < rd.nz, y1 && z0 + ob < rd.nz, zo, zo && y1};
+      const long long off[8] = {sz * b, sy + sz * b, -sy + sz * b, 2 * sy + sz * b, sz * ob, sy + sz * ob, zoff,
+                                sy + zoff};
+      V4<T> XV[8], RV[2], WV[2], DV[2];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) XV[t] = ld4_if(src + eb + off[t], ok[t]);
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        RV[t] = ld4_if(rr + eb + off[t], ok[t]);
+        WV[t] = ld4_if(ww + eb + off[t], ok[t]);
+        DV[t] = ld4_if(dd + eb + off[t], ok[t]);
+      }
+      T xl[2], xr[2];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        xl[t] = (ok[t] && hasl) ? src[eb + off[t] - 1] : T(0);
+        xr[t] = (ok[t] && hasr) ? src[eb + off[t] + 4] : T(0);
+      }
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        if (!ok[a]) continue;
+        const V4<T>& ymr = a ? XV[0] : XV[2];                 // row y - 1
+        const V4<T>& ypr = a ? XV[3] : XV[1];                 // row y + 1
+        const V4<T>& zmr = b ? XV[4 + a] : XV[6 + a];         // row z - 1
+        const V4<T>& zpr = b ? XV[6 + a] : XV[4 + a];         // row z + 1
+        V4<T> VO = zero4<T>();   // zero on padding
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int x = x0 + e;
+          if (x >= rd.nx) continue;
+          const T left = e == 0 ? xl[a] : XV[a].a[e - 1];
+          const T right = e == 3 ? xr[a] : XV[a].a[e + 1];
+          const T nb = (x > 0 ? left : T(0)) + (x < rd.nx - 1 ? right : T(0)) + ymr.a[e] + ypr.a[e] + zmr.a[e] + zpr.a[e];
+          const T res = RV[a].a[e] - (DV[a].a[e] * XV[a].a[e] - cpl * nb);
           if (e < 2) acc0 += res;
           else acc1 += res;
-          VO.a[e] = fma(WV[a].a[e], res, U[a].a[e]);
+          VO.a[e] = fma(wt(MG_W2, WV[a].a[e]), res, XV[a].a[e]);
         }
-        st4(vv + eb + off[a], VO);
+        st4(vo + eb + off[a], VO);
       }
     }
     T* rhs1 = (T*)L1.rhs;
-    const long long cb = ((long long)Z * L1.ny + Y) * L1.nx + 2 * j;
-    if (2 * j < L1.nx) rhs1[cb] = acc0;
-    if (2 * j + 1 < L1.nx) rhs1[cb + 1] = acc1;
+    const long long cb = ((long long)I.Z * L1.ny + I.Y) * L1.nx + 2 * I.j;
+    if (2 * I.j < L1.nx) rhs1[cb] = acc0;
+    if (2 * I.j + 1 < L1.nx) rhs1[cb + 1] = acc1;
   }
 }
 
@@ -817,9 +933,15 @@ __device__ void small_cycle(const Ctx& c, int which, int r, int tid, int nthr, T
     __syncthreads();
   }
   for (int l = l0; l < last; ++l) {
+    // pre-smoothing: t = (W1 / d) rhs, x = t + (W2 / d)(rhs - A t); rhs_C = R (rhs - A x)
     const View<T> V = small_view<T, SMEM>(c, which, r, l0, l, sm);
     const int n = (int)V.n();
-    for (int s = tid; s < n; s += nthr) sweep_first_at<T>(V, s);
+    for (int s = tid; s < n; s += nthr) sweep_first_at<T>(V, V.t, s, MG_W1);
+    __syncthreads();
+    {
+      Walk w(tid, nthr, V.nx, V.ny);
+      for (int s = tid; s < n; s += nthr, w.next()) sweep_xyz<T>(V, V.t, V.x, w.X, w.Y, w.Z, s, MG_W2);
+    }
     __syncthreads();
     const View<T> C = small_view<T, SMEM>(c, which, r, l0, l + 1, sm);
     const int nc = (int)C.n();
@@ -830,13 +952,13 @@ __device__ void small_cycle(const Ctx& c, int which, int r, int tid, int nthr, T
   {
     const View<T> V = small_view<T, SMEM>(c, which, r, l0, last, sm);
     const int n = (int)V.n();
-    for (int s = tid; s < n; s += nthr) sweep_first_at<T>(V, s);
+    for (int s = tid; s < n; s += nthr) sweep_first_at<T>(V, V.x, s, MG_OMEGA_COARSE);
     __syncthreads();
     for (int k = 1; k < MG_NU_COARSE; ++k) {
       const bool odd = k & 1;
       Walk w(tid, nthr, V.nx, V.ny);
       for (int s = tid; s < n; s += nthr, w.next())
-        sweep_xyz<T>(V, odd ? V.x : V.t, odd ? V.t : V.x, w.X, w.Y, w.Z, s);
+        sweep_xyz<T>(V, odd ? V.x : V.t, odd ? V.t : V.x, w.X, w.Y, w.Z, s, MG_OMEGA_COARSE);
       __syncthreads();
     }
     if ((MG_NU_COARSE & 1) == 0) {   // the last sweep wrote t
@@ -845,6 +967,7 @@ __device__ void small_cycle(const Ctx& c, int which, int r, int tid, int nthr, T
     }
   }
   for (int l = last - 1; l >= l0; --l) {
+    // x += P x_C, then t = x + (W2 / d)(rhs - A x), x = t + (W1 / d)(rhs - A t)
     const View<T> V = small_view<T, SMEM>(c, which, r, l0, l, sm);
     const View<T> C = small_view<T, SMEM>(c, which, r, l0, l + 1, sm);
     const int n = (int)V.n();
@@ -855,7 +978,12 @@ __device__ void small_cycle(const Ctx& c, int which, int r, int tid, int nthr, T
     __syncthreads();
     {
       Walk w(tid, nthr, V.nx, V.ny);
-      for (int s = tid; s < n; s += nthr, w.next()) sweep_xyz<T>(V, V.t, V.x, w.X, w.Y, w.Z, s);
+      for (int s = tid; s < n; s += nthr, w.next()) sweep_xyz<T>(V, V.x, V.t, w.X, w.Y, w.Z, s, MG_W2);
+    }
+    __syncthreads();
+    {
+      Walk w(tid, nthr, V.nx, V.ny);
+      for (int s = tid; s < n; s += nthr, w.next()) sweep_xyz<T>(V, V.t, V.x, w.X, w.Y, w.Z, s, MG_W1);
     }
     __syncthreads();
   }
@@ -885,10 +1013,11 @@ __global__ void __launch_bounds__(kSmallThreads) k_mg_small_smem(Ctx c, int whic
 
 // ------------------------------------- coarse levels in one cooperative launch --
 // Levels 1 .. nlev-1 of one V-cycle in one cooperative launch: the
-// restrictions l -> l + 1 for l = 1 .. small-1, the single-block sub-cycle
-// (block b takes replicates b, b + grid, ...; its levels in dynamic shared
-// memory when small_smem > 0), then the post-sweeps l = small-1 .. 1, with a
-// grid barrier between consecutive phases.  Each phase is the loop body of
+// pre-sweeps and restrictions l -> l + 1 for l = 1 .. small-1, the
+// single-block sub-cycle (block b takes replicates b, b + grid, ...; its
+// levels in dynamic shared memory when small_smem > 0), then the two
+// post-sweeps of l = small-1 .. 1, with a grid barrier between consecutive
+// phases.  Each phase is the loop body of
 // the corresponding per-level kernel over this launch's threads, so the
 // result is bit-identical to the per-level launches.  rows_ok: bit l selects
 // the row-vector form of level l (as for the per-level kernels).
@@ -906,7 +1035,12 @@ __global__ void __launch_bounds__(NT, MINB) k_mg_coarse(Ctx c, int which, int sm
   if (pre) small_prefetch<T>(c, which, blockIdx.x, threadIdx.x, blockDim.x, sm);
   int k = 0;
   for (int l = 1; l < small; ++l) {
-    if (rows_ok >> l & 1u) restrict_rows<T>(c, which, l, t0, st);
+    const bool rows = rows_ok >> l & 1u;
+    if (rows) smooth_rows<T, SM_PRE>(c, which, l, t0, st);
+    else if (multi) smooth_sites<T, true, SM_PRE>(c, which, l, t0, st);
+    else smooth_sites<T, false, SM_PRE>(c, which, l, t0, st);
+    if (!grid_barrier(c.sync, k++)) return;
+    if (rows) restrict_rows<T>(c, which, l, t0, st);
     else if (multi) restrict_sites<T, true>(c, which, l, t0, st);
     else restrict_sites<T, false>(c, which, l, t0, st);
     if (!grid_barrier(c.sync, k++)) return;
@@ -918,28 +1052,34 @@ __global__ void __launch_bounds__(NT, MINB) k_mg_coarse(Ctx c, int which, int sm
   }
   if (!grid_barrier(c.sync, k++)) return;
   for (int l = small - 1; l >= 1; --l) {
-    if (rows_ok >> l & 1u) post_rows<T>(c, which, l, t0, st);
-    else if (multi) post_sites<T, true>(c, which, l, t0, st);
-    else post_sites<T, false>(c, which, l, t0, st);
+    const bool rows = rows_ok >> l & 1u;
+    if (rows) smooth_rows<T, SM_POST>(c, which, l, t0, st);
+    else if (multi) smooth_sites<T, true, SM_POST>(c, which, l, t0, st);
+    else smooth_sites<T, false, SM_POST>(c, which, l, t0, st);
+    if (!grid_barrier(c.sync, k++)) return;
+    if (rows) smooth_rows<T, SM_LAST>(c, which, l, t0, st);
+    else if (multi) smooth_sites<T, true, SM_LAST>(c, which, l, t0, st);
+    else smooth_sites<T, false, SM_LAST>(c, which, l, t0, st);
     if (l > 1 && !grid_barrier(c.sync, k++)) return;
   }
   grid_exit(c.sync, k);
 }
 
 // ------------------------------------------ level-0 post-smoothing + rho --
-// z = u + omega (r - A u) / d over the chunk's rows, then rho = r.z
-// (fixed-order sums) and beta = rho / rho_old (0 on the first application of
-// a solve).
-//
-// PROLONG: u = u0 + p with u0 = omega r / d the first sweep and p = P x_1 the
-// coarse correction.  With v = u0 + omega (r - A u0) / d, stored by the
-// restriction kernel, and (omega / d) d = omega,
-//   z = v + p - (omega / d) A p = v + (1 - omega) p + (omega / d) c sum_nb p,
-// so the kernel streams v, r and omega/d and reads p from the coarse level
-// (piecewise constant: three of a site's neighbours share its coarse cell).
-// Otherwise the lattice is the coarsest level and u = src.
+// PROLONG: the first post-sweep of u = v + p, p = P x_1 the coarse correction
+// and v the pre-smoothed iterate.  With v' = v + (W2 / d)(r - A v), stored
+// by the restriction kernel in mg_t0, and (1 / d) d = 1,
+//   y = u + (W2 / d)(r - A u) = v' + (1 - W2) p + (W2 / d) c sum_nb p,
+// so the kernel streams v' and 1/d, reads p from the coarse level (piecewise
+// constant: three of a site's neighbours share its coarse cell) and writes y
+// over v' in place (each site reads and writes only its own element).
+// Otherwise: z = u + (om / d)(r - A u) with u = src, into z (the second
+// post-sweep, om = W1, or the last sweep of the coarsest level, om =
+// MG_OMEGA_COARSE, when the lattice is the coarsest level); then rho = r.z with the fixed-order reductions
+// of the CG passes and beta = rho / rho_old (0 on the first application of a
+// solve).
 template <typename T, bool PROLONG, int NI, bool PERSIST = false>
-__global__ void __maxnreg__(64) k_mg_post0(Ctx c, int which, const T* __restrict__ src) {
+__global__ void __maxnreg__(64) k_mg_post0(Ctx c, int which, const T* __restrict__ src, T om) {
   HCA_COUNT_KERNEL(c);
   const int2 ch = PERSIST ? make_int2(0, 0) : c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
@@ -947,7 +1087,7 @@ __global__ void __maxnreg__(64) k_mg_post0(Ctx c, int which, const T* __restrict
   const T* __restrict__ rr = (const T*)c.r;
   const T* __restrict__ dd = (const T*)c.d;
   const T* __restrict__ ww = (const T*)c.mg_w;
-  const T* __restrict__ vv = (const T*)c.mg_t0;
+  T* yy = (T*)c.mg_t0;   // read and written in place by PROLONG
   T* __restrict__ zz = (T*)c.z;
   const T cpl = (T)op_coupling(rd, which);
   const T* __restrict__ x1 = nullptr;
@@ -983,8 +1123,7 @@ __global__ void __maxnreg__(64) k_mg_post0(Ctx c, int which, const T* __restrict
         const bool gok = row_ok && g < rd.gpr;
         const long long e = geo.base + 4LL * g;
         const bool two = 4 * g + 2 < rd.nx;   // the group reaches coarse cell 2g + 1
-        const V4<T> V = ld4_if(vv + e, gok);
-        const V4<T> R = ld4_if(rr + e, gok);
+        const V4<T> V = ld4_if(yy + e, gok);
         const V4<T> W = ld4_if(ww + e, gok);
         const T C0 = gok ? x1[cown + 2 * g] : T(0);
         const T C1 = gok && two ? x1[cown + 2 * g + 1] : T(0);
@@ -995,23 +1134,20 @@ __global__ void __maxnreg__(64) k_mg_post0(Ctx c, int which, const T* __restrict
         const T Z0 = gok && zout ? x1[cz + 2 * g] : T(0);
         const T Z1 = gok && zout && two ? x1[cz + 2 * g + 1] : T(0);
         if (gok) {
-          V4<T> Zo;
-          T rz = T(0);
+          V4<T> Yo;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            Zo.a[k] = T(0);
+            Yo.a[k] = T(0);
             const int x = 4 * g + k;
             if (x < rd.nx && W.a[k] != T(0)) {
               const T p = k < 2 ? C0 : C1;
               const T pl = x > 0 ? (k == 0 ? Cl : k < 3 ? C0 : C1) : T(0);
               const T pr = x < rd.nx - 1 ? (k == 3 ? Cr : k == 0 ? C0 : C1) : T(0);
               const T nb = ((pl + pr) + nin * p) + ((k < 2 ? Y0 : Y1) + (k < 2 ? Z0 : Z1));
-              Zo.a[k] = fma(W.a[k], cpl * nb, fma((T)(1.0 - MG_OMEGA), p, V.a[k]));
-              rz += R.a[k] * Zo.a[k];
+              Yo.a[k] = fma(wt(MG_W2, W.a[k]), cpl * nb, fma((T)(1.0 - MG_W2), p, V.a[k]));
             }
           }
-          st4(zz + e, Zo);
-          acc[0].add(rz);   // float-float lane sums for FP32 (r is scaled to O(1))
+          st4(yy + e, Yo);
         }
       }
     } else {
@@ -1042,16 +1178,16 @@ __global__ void __maxnreg__(64) k_mg_post0(Ctx c, int which, const T* __restrict
             Zo.a[k] = T(0);
             if (4 * g + k < rd.nx && D.a[k] != T(0)) {
               const T q = D.a[k] * U.a[k] - cpl * nb_sum(U, k, left, right, UU[1], UU[2], UU[3], UU[4]);
-              Zo.a[k] = U.a[k] + W.a[k] * (R.a[k] - q);
+              Zo.a[k] = fma(om * W.a[k], R.a[k] - q, U.a[k]);
               rz += R.a[k] * Zo.a[k];
             }
           }
           st4(zz + e, Zo);
-          acc[0].add(rz);
+          acc[0].add(rz);   // float-float lane sums for FP32 (r is scaled to O(1))
         }
       }
     }
-    store_rows_acc(c, chunk, rl, row_ok, it.sl, it.lpr, acc, 1);
+    if (!PROLONG) store_rows_acc(c, chunk, rl, row_ok, it.sl, it.lpr, acc, 1);
   };
   if (PERSIST) {
     const int R = rd.ny * rd.nz, cr = rd.chunk_rows;
@@ -1063,6 +1199,7 @@ __global__ void __maxnreg__(64) k_mg_post0(Ctx c, int which, const T* __restrict
       row(blockIdx.x, rl, row_ok, ch.y + (row_ok ? rl : 0));
     }
   }
+  if (PROLONG) return;
   auto fin = [&](int r, const double* s1) -> int {
     RepSolve& s = c.solve[r];
     if (!s.active) return 0;
@@ -1094,10 +1231,37 @@ int grid_for(long long n) {
   return (int)std::max(1LL, std::min(b, 152LL * 16));
 }
 
-// part: -1 = whole cycle; 0 = r scaling and the lattice's first sweep +
-// restriction; 1 = coarse levels; 2 = the lattice's prolongation + last sweep.
-// scale: launch the r-scaling kernel (needed only right after a residual was
-// formed, i.e. at the start of a solve or a defect-correction sweep).
+// One of the lattice's post-sweep kernels (k_mg_post0), in the persistent
+// row form when the handle uses it.
+template <typename T, bool PROLONG>
+void launch_post0(const Ctx& c, int which, const MGHost& H, const T* src, T om) {
+  cudaStream_t s = c.stream;
+  if (c.persist && (H.ni == 1 || H.ni == 2 || H.ni == 4)) {
+    const void* fn = H.ni == 1   ? (const void*)k_mg_post0<T, PROLONG, 1, true>
+                     : H.ni == 2 ? (const void*)k_mg_post0<T, PROLONG, 2, true>
+                                 : (const void*)k_mg_post0<T, PROLONG, 4, true>;
+    const int g = persist_grid(fn, c.threads, c.sm_count);
+    switch (H.ni) {
+      case 1: k_mg_post0<T, PROLONG, 1, true><<<g, c.threads, 0, s>>>(c, which, src, om); break;
+      case 2: k_mg_post0<T, PROLONG, 2, true><<<g, c.threads, 0, s>>>(c, which, src, om); break;
+      default: k_mg_post0<T, PROLONG, 4, true><<<g, c.threads, 0, s>>>(c, which, src, om); break;
+    }
+    return;
+  }
+  switch (H.ni) {
+    case 1: k_mg_post0<T, PROLONG, 1><<<c.n_chunks, c.threads, 0, s>>>(c, which, src, om); break;
+    case 2: k_mg_post0<T, PROLONG, 2><<<c.n_chunks, c.threads, 0, s>>>(c, which, src, om); break;
+    case 4: k_mg_post0<T, PROLONG, 4><<<c.n_chunks, c.threads, 0, s>>>(c, which, src, om); break;
+    default: k_mg_post0<T, PROLONG, 0><<<c.n_chunks, c.threads, 0, s>>>(c, which, src, om); break;
+  }
+}
+
+// part: -1 = whole cycle; 0 = r scaling (only with `scale`: right after a
+// residual was formed, i.e. at the start of a solve or a defect-correction
+// sweep); 1 = the lattice's pre-sweeps; 2 = its restriction; 3 = the coarse
+// levels; 4 = the lattice's prolongation and first post-sweep; 5 = its last
+// post-sweep with r.z.  A lattice that is the coarsest level runs its sweeps
+// as part 3.
 template <typename T>
 void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
   cudaStream_t s = c.stream;
@@ -1105,67 +1269,64 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
   T* z = (T*)c.z;
   const bool all = part < 0;
   const bool multi = c.n_reps > 1;
+  if (scale && (all || part == 0)) k_mg_scale0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, s>>>(c, which);
   if (H.nlev == 1) {
-    if (!all && part != 0) return;
+    if (!all && part != 3) return;
     // the lattice is the coarsest level (single replicate): MG_NU_COARSE
     // sweeps, the last one in post0
-    if (scale) k_mg_scale0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, s>>>(c, which);
     k_mg_first0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, s>>>(c, which);
     for (int k = 1; k < MG_NU_COARSE - 1; ++k) {
       const bool odd = k & 1;
       k_mg_sweep0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, s>>>(c, which, odd ? t0 : z, odd ? z : t0);
     }
     const T* src = ((MG_NU_COARSE - 2) & 1) ? z : t0;
-    k_mg_post0<T, false, 0><<<c.n_chunks, c.threads, 0, s>>>(c, which, src);
+    k_mg_post0<T, false, 0><<<c.n_chunks, c.threads, 0, s>>>(c, which, src, (T)MG_OMEGA_COARSE);
     return;
   }
-  if (all || part == 0) {
-    if (scale) k_mg_scale0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, s>>>(c, which);
-    // 128 threads: the kernel keeps ~28 vector loads per thread in flight
-    const int nb = (int)std::max(1LL, std::min((H.nrowitems + 127) / 128, 152LL * 16));
-    k_mg_restrict0_rows<T><<<nb, 128, 0, s>>>(c, which);
-  }
-  if ((all || part == 1) && H.coop_blocks > 0) {
+  // 128 threads: the lattice kernels keep ~20-28 vector loads per thread in flight
+  const int nb = (int)std::max(1LL, std::min((H.nrowitems + 127) / 128, 152LL * 16));
+  if (all || part == 1) k_mg_pre0<T><<<nb, 128, 0, s>>>(c, which, z);
+  if (all || part == 2) k_mg_restrict0_rows<T><<<nb, 128, 0, s>>>(c, which, z);
+  if ((all || part == 3) && H.coop_blocks > 0) {
     Ctx cc = c;
     int wh = which, sm = H.small, use = H.small_smem > 0;
     unsigned rows = H.rows_ok;
     void* args[] = {&cc, &wh, &sm, &rows, &use};
     (void)cudaLaunchCooperativeKernel(coarse_fn<T>(H.coop_cfg), dim3(H.coop_blocks), dim3(coarse_threads(H.coop_cfg)),
                                       args, (size_t)H.small_smem, s);
-  } else if (all || part == 1) {
+  } else if (all || part == 3) {
     for (int l = 1; l < H.small; ++l) {
-      if (H.rows_ok >> l & 1u)   // 128 threads: ~28 vector loads per thread in flight
+      if (H.rows_ok >> l & 1u) {
+        k_mg_smooth_rows<T, SM_PRE><<<grid_for(H.post_items[l]), kMgThreads, 0, s>>>(c, which, l);
+        // 128 threads: ~12 vector loads per thread in flight
         k_mg_restrict_rows<T><<<(int)std::min((H.restr_items[l] + 127) / 128, 152LL * 16), 128, 0, s>>>(c, which, l);
-      else if (multi) k_mg_restrict<T, true><<<grid_for(H.ntot[l + 1]), kMgThreads, 0, s>>>(c, which, l);
-      else k_mg_restrict<T, false><<<grid_for(H.ntot[l + 1]), kMgThreads, 0, s>>>(c, which, l);
+      } else if (multi) {
+        k_mg_smooth<T, true, SM_PRE><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
+        k_mg_restrict<T, true><<<grid_for(H.ntot[l + 1]), kMgThreads, 0, s>>>(c, which, l);
+      } else {
+        k_mg_smooth<T, false, SM_PRE><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
+        k_mg_restrict<T, false><<<grid_for(H.ntot[l + 1]), kMgThreads, 0, s>>>(c, which, l);
+      }
     }
     if (H.small_smem > 0 && H.small_smem_ok)
       k_mg_small_smem<T><<<c.n_reps, kSmallThreads, (size_t)H.small_smem, s>>>(c, which);
     else
       k_mg_small<T><<<c.n_reps, kSmallThreads, 0, s>>>(c, which);
     for (int l = H.small - 1; l >= 1; --l) {
-      if (H.rows_ok >> l & 1u) k_mg_post_rows<T><<<grid_for(H.post_items[l]), kMgThreads, 0, s>>>(c, which, l);
-      else if (multi) k_mg_post<T, true><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
-      else k_mg_post<T, false><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
+      if (H.rows_ok >> l & 1u) {
+        k_mg_smooth_rows<T, SM_POST><<<grid_for(H.post_items[l]), kMgThreads, 0, s>>>(c, which, l);
+        k_mg_smooth_rows<T, SM_LAST><<<grid_for(H.post_items[l]), kMgThreads, 0, s>>>(c, which, l);
+      } else if (multi) {
+        k_mg_smooth<T, true, SM_POST><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
+        k_mg_smooth<T, true, SM_LAST><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
+      } else {
+        k_mg_smooth<T, false, SM_POST><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
+        k_mg_smooth<T, false, SM_LAST><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
+      }
     }
   }
-  if ((all || part == 2) && c.persist && (H.ni == 1 || H.ni == 2 || H.ni == 4)) {
-    const void* fn = H.ni == 1 ? (const void*)k_mg_post0<T, true, 1, true>
-                   : H.ni == 2 ? (const void*)k_mg_post0<T, true, 2, true> : (const void*)k_mg_post0<T, true, 4, true>;
-    const int g = persist_grid(fn, c.threads, c.sm_count);
-    switch (H.ni) {
-      case 1: k_mg_post0<T, true, 1, true><<<g, c.threads, 0, s>>>(c, which, nullptr); break;
-      case 2: k_mg_post0<T, true, 2, true><<<g, c.threads, 0, s>>>(c, which, nullptr); break;
-      default: k_mg_post0<T, true, 4, true><<<g, c.threads, 0, s>>>(c, which, nullptr); break;
-    }
-  } else if (all || part == 2) {
-    switch (H.ni) {
-      case 1: k_mg_post0<T, true, 1><<<c.n_chunks, c.threads, 0, s>>>(c, which, nullptr); break;
-      case 2: k_mg_post0<T, true, 2><<<c.n_chunks, c.threads, 0, s>>>(c, which, nullptr); break;
-      case 4: k_mg_post0<T, true, 4><<<c.n_chunks, c.threads, 0, s>>>(c, which, nullptr); break;
-      default: k_mg_post0<T, true, 0><<<c.n_chunks, c.threads, 0, s>>>(c, which, nullptr); break;
-    }
-  }
+  if (all || part == 4) launch_post0<T, true>(c, which, H, nullptr, T(0));
+  if (all || part == 5) launch_post0<T, false>(c, which, H, t0, (T)MG_W1);
 }
 
 template <typename T>
@@ -1223,9 +1384,12 @@ int coop_config_t(MGHost& H, int sm_count, long long smem_bytes) {
 
 }  // namespace
 
+int vcycle_part_launches(const MGHost& H, int part, bool scale);
+
 int vcycle_launches(const MGHost& H, bool scale) {
-  if (H.nlev > 1 && H.coop_blocks > 0) return 3 + (scale ? 1 : 0);
-  return (H.nlev == 1 ? MG_NU_COARSE : 2 * H.small + 1) + (scale ? 1 : 0);
+  int n = 0;
+  for (int part = 0; part < kVcycleParts; ++part) n += vcycle_part_launches(H, part, scale);
+  return n;
 }
 
 // Choose the coarse-level launch form of a hierarchy (after H.small and
@@ -1254,9 +1418,10 @@ void launch_vcycle(const Ctx& c, int which, bool fp64, const MGHost& H, int part
 }
 
 int vcycle_part_launches(const MGHost& H, int part, bool scale) {
-  if (H.nlev == 1) return part == 0 ? MG_NU_COARSE + (scale ? 1 : 0) : 0;
-  if (part == 1 && H.coop_blocks > 0) return 1;
-  return part == 0 ? 1 + (scale ? 1 : 0) : part == 1 ? 2 * (H.small - 1) + 1 : 1;
+  if (part == 0) return scale ? 1 : 0;
+  if (H.nlev == 1) return part == 3 ? MG_NU_COARSE : 0;
+  if (part == 3) return H.coop_blocks > 0 ? 1 : 4 * (H.small - 1) + 1;
+  return 1;
 }
 
 }  // namespace hca

@@ -132,9 +132,9 @@ class hca_stats(ctypes.Structure):
         return d
 
 
-NKCLASS = 11
+NKCLASS = 13
 KCLASS_NAMES = ("setup", "pass_a", "pass_b", "residual", "ode", "ca_compact", "ca_colour", "other", "mg",
-                "mg_restrict0", "mg_post0")
+                "mg_restrict0", "mg_post0", "mg_pre0", "mg_last0")
 
 
 class hca_train_cfg(ctypes.Structure):

@@ -1,7 +1,9 @@
 """Pins of the FP64 multigrid oracle (oracle/multigrid.py): transfer
 adjointness, symmetry and definiteness of the V-cycle, the coarsest-level
 sweeps against their closed-form matrix polynomial, and MG-preconditioned CG
-against a dense direct solve and against Jacobi-preconditioned CG."""
+against a dense direct solve and against Jacobi-preconditioned CG, the
+smoothing weights against the closed form of the Chebyshev polynomial, and a
+two-level V-cycle against its error-propagation matrix."""
 
 import numpy as np
 import pytest
@@ -62,15 +64,72 @@ def test_single_level_is_the_jacobi_polynomial(rng):
     assert len(levels) == 1
     A = dense(levels[0].apply, shape)
     Dinv = np.diag(1.0 / levels[0].d.reshape(-1))
-    G = np.eye(A.shape[0]) - MG.OMEGA * Dinv @ A
+    G = np.eye(A.shape[0]) - MG.OMEGA_COARSE * Dinv @ A
     # M = sum_{k < nu} G^k omega D^-1
     M = np.zeros_like(A)
     Gk = np.eye(A.shape[0])
     for _ in range(MG.NU_COARSE):
-        M += Gk @ (MG.OMEGA * Dinv)
+        M += Gk @ (MG.OMEGA_COARSE * Dinv)
         Gk = Gk @ G
     r = rng.standard_normal(shape)
     assert np.allclose(MG.vcycle(levels, r).reshape(-1), M @ r.reshape(-1), rtol=1e-12, atol=1e-14)
+
+
+def test_smoothing_weights_are_the_chebyshev_polynomial():
+    """(1 - w1 t)(1 - w2 t) = T2(s(t)) / T2(s(0)) with T2(x) = 2 x^2 - 1 and
+    s(t) = (hi + lo - 2 t) / (hi - lo): the two sweeps' error polynomial is
+    the scaled Chebyshev polynomial of the damped interval, bounded there by
+    1 / T2(s(0)) and within [-1, 1] on all of (0, 2]."""
+    lo, hi = MG.CHEB_LO, MG.CHEB_HI
+    w1, w2 = MG.SMOOTH_WEIGHTS
+    assert MG.NU == 2 and w1 < w2
+    t = np.linspace(0.0, 2.0, 2001)
+    s = (hi + lo - 2.0 * t) / (hi - lo)
+    s0 = (hi + lo) / (hi - lo)
+    cheb = (2.0 * s ** 2 - 1.0) / (2.0 * s0 ** 2 - 1.0)
+    poly = (1.0 - w1 * t) * (1.0 - w2 * t)
+    assert np.allclose(poly, cheb, rtol=0, atol=1e-14)
+    on = (t >= lo) & (t <= hi)
+    assert np.max(np.abs(poly[on])) <= 1.0 / (2.0 * s0 ** 2 - 1.0) + 1e-15
+    assert np.max(np.abs(poly[t > 0])) < 1.0
+    # degree 1 is the single sweep of weight 2 / (lo + hi)
+    assert np.isclose(MG.chebyshev_weights(1, lo, hi)[0], 2.0 / (lo + hi))
+
+
+def test_two_level_vcycle_is_its_error_propagation(rng, monkeypatch):
+    """With two levels, I - M A = S (I - P B R A) S, S = (I - w2 D^-1 A)(I - w1 D^-1 A)
+    the smoother's error propagation and B the coarse sweeps' polynomial
+    sum_{k < nu} G_c^k w_c D_c^-1 (G_c = I - w_c D_c^-1 A_c): the recursive
+    V-cycle against the matrix form of the two-grid method."""
+    monkeypatch.setattr(MG, "MIN_SITES", 40)
+    shape = (4, 5, 6)
+    a = rng.uniform(0.01, 2.0, shape)
+    levels = MG.hierarchy(1.7, a)
+    assert len(levels) == 2
+    f, cl = levels
+    A = dense(f.apply, shape)
+    Ac = dense(cl.apply, cl.a.shape)
+    n, nc = A.shape[0], Ac.shape[0]
+    R = np.zeros((nc, n))
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        R[:, i] = MG.restrict(e.reshape(shape)).reshape(-1)
+    P = R.T
+    Dinv = np.diag(1.0 / f.d.reshape(-1))
+    Dcinv = np.diag(1.0 / cl.d.reshape(-1))
+    w1, w2 = MG.SMOOTH_WEIGHTS
+    I = np.eye(n)
+    S = (I - w2 * Dinv @ A) @ (I - w1 * Dinv @ A)
+    Gc = np.eye(nc) - MG.OMEGA_COARSE * Dcinv @ Ac
+    B = np.zeros_like(Ac)
+    Gk = np.eye(nc)
+    for _ in range(MG.NU_COARSE):
+        B += Gk @ (MG.OMEGA_COARSE * Dcinv)
+        Gk = Gk @ Gc
+    E = S @ (I - P @ B @ R @ A) @ S
+    M = dense(lambda r: MG.vcycle(levels, r), shape)
+    assert np.allclose(I - M @ A, E, rtol=0, atol=1e-11)
 
 
 def _drug_like(shape, rng):
