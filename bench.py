@@ -44,13 +44,13 @@ CORR_LEN = 8.0
 #   writes x, r;
 #   defect-correction residual (later sweeps) reads x_hi, x_lo, d, a, b and writes z, dx, r;
 #   multigrid on the lattice, four kernels per V-cycle: the two pre-sweeps read r, 1/d and
-#   write the pre-smoothed iterate v (12 B); the restriction reads v, r, 1/d, d and writes
-#   v' = v + (W2/d)(r - A v) and the 1/8-size coarse right-hand side (20.5 B); the prolongation
+#   write the pre-smoothed iterate v (12 B); the restriction reads v, r, d and writes
+#   v' = v + (W2/d)(r - A v) and the 1/8-size coarse right-hand side (16.5 B); the prolongation
 #   + first post-sweep reads v', 1/d and the 1/8-size coarse correction and writes y (12.5 B);
-#   the last post-sweep reads y, r, 1/d, d and writes z (20 B); ODE reads state, K and
+#   the last post-sweep reads y, r, 1/d and writes z (16 B); ODE reads state, K and
 #   updates phi, P, Vc
 BYTES_PER_SITE = {"pass_a": 20, "pass_b": 24, "setup": 17, "residual": 24, "ode": 29,
-                  "mg_pre0": 12, "mg_restrict0": 20.5, "mg_post0": 12.5, "mg_last0": 20}
+                  "mg_pre0": 12, "mg_restrict0": 16.5, "mg_post0": 12.5, "mg_last0": 16}
 # the method's minimum per site where this design moves more: CG pass A reads
 # z, d, p_old and writes p (16 B); storing q = A p for pass B adds 4 B
 BYTES_MIN_PER_SITE = {**BYTES_PER_SITE, "pass_a": 16}

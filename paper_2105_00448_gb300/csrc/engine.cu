@@ -425,9 +425,14 @@ void pass_b(hca_handle* h, int which, void* x, hca::CondArg cnd) {
 // (graph-launched kernels follow each other closely, and the per-level
 // kernels keep more warps per SM than the cooperative kernel: measured
 // faster); from host loops, where each launch costs host time, as the one
-// cooperative launch.
+// cooperative launch (HCA_MG_COOP_GRAPH=1 captures the cooperative launch
+// too).
 void vcycle(hca_handle* h, int which, bool first) {
-  if (h->capturing && h->mgh.coop_blocks > 0) {
+  static const bool coop_graph = [] {
+    const char* e = std::getenv("HCA_MG_COOP_GRAPH");
+    return e && e[0] == '1';
+  }();
+  if (h->capturing && h->mgh.coop_blocks > 0 && !coop_graph) {
     hca::MGHost H = h->mgh;
     H.coop_blocks = 0;
     hca::launch_vcycle(h->ctx, which, h->fp64, H, -1, first);

@@ -777,18 +777,17 @@ __global__ void __launch_bounds__(128) k_mg_pre0(Ctx c, int which, T* __restrict
 
 // Restriction from the lattice to level 1 in row-vector form, from the
 // pre-smoothed iterate v (src, stored by k_mg_pre0): rhs_1 = R (r - A v).  It
-// also stores v' = v + (W2 / d)(r - A v) into mg_t0, the part of the first
-// post-sweep that does not depend on the coarse correction (the post-sweep
-// kernel adds the rest).  Per item and dz half: v on the 2 own and 6 outer
-// rows, r, 1/d and d on the own rows, the x neighbours of v at the group's
-// ends, all loaded before the residuals are formed.  Children in the order
-// of restrict_residual_at.
+// also stores v' = v + (W2 / d)(r - A v) = (1 - W2) v + W2 (r + c sum_nb v) / d
+// into mg_t0, the part of the first post-sweep that does not depend on the
+// coarse correction (the post-sweep kernel adds the rest).  Per item and dz
+// half: v on the 2 own and 6 outer rows, r and d on the own rows, the x
+// neighbours of v at the group's ends, all loaded before the residuals are
+// formed: 16.5 B per site.  Children in the order of restrict_residual_at.
 template <typename T>
 __global__ void __launch_bounds__(128) k_mg_restrict0_rows(Ctx c, int which, const T* __restrict__ src) {
   HCA_COUNT_KERNEL(c);
   T* __restrict__ vo = (T*)c.mg_t0;
   const T* __restrict__ rr = (const T*)c.r;
-  const T* __restrict__ ww = (const T*)c.mg_w;
   const T* __restrict__ dd = (const T*)c.d;
   const MGLevel* LV = (const MGLevel*)c.mg_lv;
   const long long total = c.mg_rowstart[c.n_reps];
@@ -812,13 +811,12 @@ __global__ void __launch_bounds__(128) k_mg_restrict0_rows(Ctx c, int which, con
       const bool ok[8] = {true, y1, y0 > 0, y0 + 2 < rd.ny, z0 + ob < rd.nz, y1 && z0 + ob < rd.nz, zo, zo && y1};
       const long long off[8] = {sz * b, sy + sz * b, -sy + sz * b, 2 * sy + sz * b, sz * ob, sy + sz * ob, zoff,
                                 sy + zoff};
-      V4<T> XV[8], RV[2], WV[2], DV[2];
+      V4<T> XV[8], RV[2], DV[2];
 #pragma unroll
       for (int t = 0; t < 8; ++t) XV[t] = ld4_if(src + eb + off[t], ok[t]);
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
         RV[t] = ld4_if(rr + eb + off[t], ok[t]);
-        WV[t] = ld4_if(ww + eb + off[t], ok[t]);
         DV[t] = ld4_if(dd + eb + off[t], ok[t]);
       }
       T xl[2], xr[2];
@@ -842,10 +840,12 @@ __global__ void __launch_bounds__(128) k_mg_restrict0_rows(Ctx c, int which, con
           const T left = e == 0 ? xl[a] : XV[a].a[e - 1];
           const T right = e == 3 ? xr[a] : XV[a].a[e + 1];
           const T nb = (x > 0 ? left : T(0)) + (x < rd.nx - 1 ? right : T(0)) + ymr.a[e] + ypr.a[e] + zmr.a[e] + zpr.a[e];
-          const T res = RV[a].a[e] - (DV[a].a[e] * XV[a].a[e] - cpl * nb);
+          const T rn = fma(cpl, nb, RV[a].a[e]);   // r + c sum_nb v
+          const T res = rn - DV[a].a[e] * XV[a].a[e];
           if (e < 2) acc0 += res;
           else acc1 += res;
-          VO.a[e] = fma(wt(MG_W2, WV[a].a[e]), res, XV[a].a[e]);
+          // v + (W2 / d)(r - A v) = (1 - W2) v + W2 (r + c sum_nb v) / d
+          if (DV[a].a[e] != T(0)) VO.a[e] = fma((T)MG_W2, rn / DV[a].a[e], (T)(1.0 - MG_W2) * XV[a].a[e]);
         }
         st4(vo + eb + off[a], VO);
       }
@@ -1073,9 +1073,10 @@ __global__ void __launch_bounds__(NT, MINB) k_mg_coarse(Ctx c, int which, int sm
 // so the kernel streams v' and 1/d, reads p from the coarse level (piecewise
 // constant: three of a site's neighbours share its coarse cell) and writes y
 // over v' in place (each site reads and writes only its own element).
-// Otherwise: z = u + (om / d)(r - A u) with u = src, into z (the second
-// post-sweep, om = W1, or the last sweep of the coarsest level, om =
-// MG_OMEGA_COARSE, when the lattice is the coarsest level); then rho = r.z with the fixed-order reductions
+// Otherwise: z = u + (om / d)(r - A u) = (1 - om) u + (om / d)(r + c sum_nb u)
+// with u = src, into z (the second post-sweep, om = W1, or the last sweep of
+// the coarsest level, om = MG_OMEGA_COARSE, when the lattice is the coarsest
+// level): reads u, r and 1/d, 16 B per site with the write; then rho = r.z with the fixed-order reductions
 // of the CG passes and beta = rho / rho_old (0 on the first application of a
 // solve).
 template <typename T, bool PROLONG, int NI, bool PERSIST = false>
@@ -1085,7 +1086,6 @@ __global__ void __maxnreg__(64) k_mg_post0(Ctx c, int which, const T* __restrict
   const RepDesc& rd = c.reps[ch.x];
   const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
   const T* __restrict__ rr = (const T*)c.r;
-  const T* __restrict__ dd = (const T*)c.d;
   const T* __restrict__ ww = (const T*)c.mg_w;
   T* yy = (T*)c.mg_t0;   // read and written in place by PROLONG
   T* __restrict__ zz = (T*)c.z;
@@ -1152,6 +1152,7 @@ __global__ void __maxnreg__(64) k_mg_post0(Ctx c, int which, const T* __restrict
       }
     } else {
       T carry = T(0);
+      const T om1 = T(1) - om;
 #pragma unroll
       for (int itn = 0; itn < niter; ++itn) {
         const int g = itn * it.lpr + it.sl;
@@ -1162,7 +1163,6 @@ __global__ void __maxnreg__(64) k_mg_post0(Ctx c, int which, const T* __restrict
         V4<T> UU[5];
 #pragma unroll
         for (int q = 0; q < 5; ++q) UU[q] = ld4_if(src + e + roff[q], rok[q]);
-        const V4<T> D = ld4_if(dd + e, gok);
         const V4<T> R = ld4_if(rr + e, gok);
         const V4<T> W = ld4_if(ww + e, gok);
         const bool last_lane = it.sl == it.lpr - 1 && gok && g + 1 < rd.gpr;
@@ -1176,9 +1176,10 @@ __global__ void __maxnreg__(64) k_mg_post0(Ctx c, int which, const T* __restrict
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             Zo.a[k] = T(0);
-            if (4 * g + k < rd.nx && D.a[k] != T(0)) {
-              const T q = D.a[k] * U.a[k] - cpl * nb_sum(U, k, left, right, UU[1], UU[2], UU[3], UU[4]);
-              Zo.a[k] = fma(om * W.a[k], R.a[k] - q, U.a[k]);
+            if (4 * g + k < rd.nx && W.a[k] != T(0)) {
+              // u + (om / d)(r - A u) = (1 - om) u + (om / d)(r + c sum_nb u)
+              const T rn = fma(cpl, nb_sum(U, k, left, right, UU[1], UU[2], UU[3], UU[4]), R.a[k]);
+              Zo.a[k] = fma(om * W.a[k], rn, om1 * U.a[k]);
               rz += R.a[k] * Zo.a[k];
             }
           }
