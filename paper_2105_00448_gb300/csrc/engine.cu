@@ -327,6 +327,7 @@ RepDesc make_desc(const hca_config& c) {
   r.bax[hca::WHICH_VEGF] = c.drug_scheme == 1;
   r.nsub[hca::WHICH_VEGF] = c.drug_substeps;
   r.c_drug[hca::VEGF_SLOT] = c.D_V / dx2;
+  for (int w = 0; w <= hca::MAX_FIELDS; ++w) r.cpl32[w] = (float)(w == 0 ? r.c_o2 : r.c_drug[w - 1]);
   r.base_drug[hca::VEGF_SLOT] = (c.drug_scheme ? 2.0 / hd : 1.0 / hd) + c.psi_V;
   r.kappa[hca::VEGF_SLOT] = 0.0;
   r.uptake[hca::VEGF_SLOT] = 0.0;
@@ -1188,6 +1189,7 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
           L.nz = nz;
           L.n = nn;
           L.cscale = cs;
+          L.cscale32 = (float)cs;
           nl += 1;
         }
         int small = nl - 1;

@@ -56,6 +56,7 @@ struct RepDesc {
   double phi_K, K1, K0, r_K;
   // drugs (Eq. chemo), implicit Euler
   double c_drug[MAX_FIELDS];   // D_G / dx^2 (slot 3: D_V / dx^2)
+  float cpl32[1 + MAX_FIELDS]; // the couplings of operators 0 (c_o2), 1.. (c_drug) rounded to FP32
   double base_drug[MAX_FIELDS];// mass term + psi_G (slot 3: + psi_V)
   double inv_dt;
   // time discretisation per operator (0 oxygen, 1 + d drug d): the reaction
@@ -278,8 +279,9 @@ namespace hca {
 struct MGLevel {
   int nx, ny, nz, pad;
   long long n;
-  void *x, *t, *rhs, *d, *w;   // iterate, second iterate, right-hand side, diagonal, omega / diagonal
+  void *x, *t, *rhs, *d, *w;   // iterate, second iterate, right-hand side, diagonal, 1 / diagonal
   double cscale;            // coupling of this level / coupling of the lattice (2^level)
+  float cscale32;           // the same in FP32 (exact)
 };
 
 // multigrid constants (the FP64 reference uses the same).  Above the
@@ -625,6 +627,18 @@ __device__ __forceinline__ void grid_exit(PassSync* sy, int nbar) {
 // Operator selector: 0 = oxygen, 1 + d = drug d.
 __device__ __forceinline__ double op_coupling(const RepDesc& rd, int which) {
   return which == 0 ? rd.c_o2 : rd.c_drug[which - 1];
+}
+// The coupling in the field precision (FP32: the stored rounding, no
+// conversion on the FP64 pipe).
+template <typename T>
+__device__ __forceinline__ T op_coupling_t(const RepDesc& rd, int which);
+template <>
+__device__ __forceinline__ float op_coupling_t<float>(const RepDesc& rd, int which) {
+  return rd.cpl32[which];
+}
+template <>
+__device__ __forceinline__ double op_coupling_t<double>(const RepDesc& rd, int which) {
+  return op_coupling(rd, which);
 }
 
 // Plasma level G_{d,0}(t) after boluses at 0, I dt, 2 I dt, ... (closed form

@@ -74,7 +74,7 @@ template <typename T>
 __device__ __forceinline__ View<T> view(const Ctx& c, int which, int r, int l) {
   const RepDesc& rd = c.reps[r];
   View<T> v;
-  const T c0 = (T)op_coupling(rd, which);
+  const T c0 = op_coupling_t<T>(rd, which);
   if (l == 0) {
     v.nx = rd.nx;
     v.ny = rd.ny;
@@ -102,7 +102,7 @@ __device__ __forceinline__ View<T> view(const Ctx& c, int which, int r, int l) {
   v.rhs = (T*)L.rhs;
   v.d = (T*)L.d;
   v.w = (T*)L.w;
-  v.c = c0 * (T)L.cscale;
+  v.c = c0 * (sizeof(T) == 4 ? (T)L.cscale32 : (T)L.cscale);
   return v;
 }
 
@@ -714,7 +714,7 @@ __global__ void __launch_bounds__(128) k_mg_pre0(Ctx c, int which, T* __restrict
     const RepDesc& rd = c.reps[I.r];
     const long long sy = I.sy, sz = I.sz, eb = I.eb;
     const int y0 = I.y0, z0 = I.z0, x0 = I.x0;
-    const T cpl = (T)op_coupling(rd, which);
+    const T cpl = op_coupling_t<T>(rd, which);
     const bool hasl = x0 > 0, hasr = x0 + 4 < rd.nx;
     const bool y1 = y0 + 1 < rd.ny;
     // one dz half b at a time with its eight rows in registers: slots 0, 1
@@ -798,7 +798,7 @@ __global__ void __launch_bounds__(128) k_mg_restrict0_rows(Ctx c, int which, con
     const MGLevel& L1 = LV[I.r * MG_MAXLEV + 1];
     const long long sy = I.sy, sz = I.sz, eb = I.eb;
     const int y0 = I.y0, z0 = I.z0, x0 = I.x0;
-    const T cpl = (T)op_coupling(rd, which);
+    const T cpl = op_coupling_t<T>(rd, which);
     const bool hasl = x0 > 0, hasr = x0 + 4 < rd.nx;
     const bool y1 = y0 + 1 < rd.ny;
     T acc0 = T(0), acc1 = T(0);
@@ -1089,7 +1089,7 @@ __global__ void __maxnreg__(64) k_mg_post0(Ctx c, int which, const T* __restrict
   const T* __restrict__ ww = (const T*)c.mg_w;
   T* yy = (T*)c.mg_t0;   // read and written in place by PROLONG
   T* __restrict__ zz = (T*)c.z;
-  const T cpl = (T)op_coupling(rd, which);
+  const T cpl = op_coupling_t<T>(rd, which);
   const T* __restrict__ x1 = nullptr;
   int nx1 = 0, ny1 = 0;
   if (PROLONG) {

@@ -40,39 +40,54 @@ namespace {
 __device__ __forceinline__ float add_prod(float a, float k, float p) { return __fadd_rn(a, __fmul_rn(k, p)); }
 __device__ __forceinline__ double add_prod(double a, double k, double p) { return a + k * p; }
 
-// Reaction coefficient a of the operator at one site (d = c n + a).
+// The coefficients of operator `which` in the field precision, converted
+// from the handle's FP64 parameters once per thread: the conversions run on
+// the FP64 pipe (a small fraction of the FP32 rate on this GPU), and the
+// parameters sit in global memory, where the compiler cannot keep them in
+// registers across the kernel's own stores.
+template <typename T>
+struct Coef {
+  T cpl, phi_K, K1, r_K, o2_mass, base, kappa, uptake;
+};
 template <typename T, int KIND>
-__device__ __forceinline__ T reaction_site(const RepDesc& rd, int which, uint8_t s, T K_prev, T pf) {
-  T a;
+__device__ __forceinline__ Coef<T> coef(const RepDesc& rd, int which) {
+  Coef<T> q;
+  q.cpl = op_coupling_t<T>(rd, which);
+  q.phi_K = q.K1 = q.r_K = q.o2_mass = q.base = q.kappa = q.uptake = T(0);
   if (KIND == 0) {
-    a = is_consumer(s) ? (T)rd.phi_K / ((T)rd.K1 + K_prev) : T(0);
-    if (is_vessel(s)) a += (T)rd.r_K;
-    a += (T)rd.o2_mass;   // 0 for the quasi-steady form
+    q.phi_K = (T)rd.phi_K;
+    q.K1 = (T)rd.K1;
+    q.r_K = (T)rd.r_K;
+    q.o2_mass = (T)rd.o2_mass;
   } else {
     const int dd = which - 1;
-    a = (T)rd.base_drug[dd];
-    if (is_vessel(s)) a = add_prod(a, (T)rd.kappa[dd], pf);
-    if (is_cancer(s)) a += (T)rd.uptake[dd];
+    q.base = (T)rd.base_drug[dd];
+    q.kappa = (T)rd.kappa[dd];
+    q.uptake = (T)rd.uptake[dd];
+  }
+  return q;
+}
+
+// Reaction coefficient a of the operator at one site (d = c n + a).
+template <typename T, int KIND>
+__device__ __forceinline__ T reaction_site(const Coef<T>& q, uint8_t s, T K_prev, T pf) {
+  T a;
+  if (KIND == 0) {
+    a = is_consumer(s) ? q.phi_K / (q.K1 + K_prev) : T(0);
+    if (is_vessel(s)) a += q.r_K;
+    a += q.o2_mass;   // 0 for the quasi-steady form
+  } else {
+    a = q.base;
+    if (is_vessel(s)) a = add_prod(a, q.kappa, pf);
+    if (is_cancer(s)) a += q.uptake;
   }
   return a;
 }
 
 // Diagonal of the operator at one site.
 template <typename T, int KIND>
-__device__ __forceinline__ T diag_site(const RepDesc& rd, int which, int n_nb, uint8_t s, T K_prev, T pf) {
-  const T cpl = (T)op_coupling(rd, which);
-  T a;
-  if (KIND == 0) {
-    a = is_consumer(s) ? (T)rd.phi_K / ((T)rd.K1 + K_prev) : T(0);
-    if (is_vessel(s)) a += (T)rd.r_K;
-    a += (T)rd.o2_mass;
-  } else {
-    const int dd = which - 1;
-    a = (T)rd.base_drug[dd];
-    if (is_vessel(s)) a = add_prod(a, (T)rd.kappa[dd], pf);
-    if (is_cancer(s)) a += (T)rd.uptake[dd];
-  }
-  return cpl * (T)n_nb + a;
+__device__ __forceinline__ T diag_site(const Coef<T>& q, int n_nb, uint8_t s, T K_prev, T pf) {
+  return q.cpl * (T)n_nb + reaction_site<T, KIND>(q, s, K_prev, pf);
 }
 
 // ------------------------------------------------------------------ setup --
@@ -95,11 +110,13 @@ __global__ void __launch_bounds__(512) k_setup(Ctx c, int which, CondArg cnd) {
     __syncthreads();
   }
   const T G0 = KIND == 1 ? (T)s_G0 : T(0);
-  const T cpl = (T)op_coupling(rd, which);
+  const Coef<T> q = coef<T, KIND>(rd, which);
+  const T cpl = q.cpl;
   const T bx = (T)rd.bx[which];
   const bool bax = rd.bax[which] != 0;
   const bool o2t = KIND == 0 && rd.bx[0] != 0.0;   // time-dependent oxygen: b depends on x0
   const T bvessel = (T)(bax ? 2.0 * rd.r_K * rd.K0 : rd.r_K * rd.K0);
+  const T av = (T)(bax ? 2.0 * rd.a_vegf : rd.a_vegf);
   const RowIter it = row_iter(rd);
   for (int rbase = it.warp * it.rpw; rbase < rd.chunk_rows; rbase += it.nw * it.rpw) {
     const int rl = rbase + it.sub;
@@ -125,7 +142,6 @@ __global__ void __launch_bounds__(512) k_setup(Ctx c, int which, CondArg cnd) {
         // the VEGF field's source is the cells' release a_V Vc (doubled under Crank-Nicolson)
         const bool vegf = KIND == 1 && which == WHICH_VEGF;
         const V4<T> VC = vegf ? ld4((const T*)c.Vc + e) : zero4<T>();
-        const T av = (T)(bax ? 2.0 * rd.a_vegf : rd.a_vegf);
         const V4<T> LG = (KIND == 0 && c.lag) ? ld4((const T*)c.lag + e) : X;
         V4<T> D, Z, B, RR = zero4<T>();
         T g_rho = 0, g_rr = 0, g_bb = 0;
@@ -135,10 +151,10 @@ __global__ void __launch_bounds__(512) k_setup(Ctx c, int which, CondArg cnd) {
           const uint8_t s = st_at(st, k);
           T dk = T(0), zk = T(0), bk = T(0);
           if (xk < rd.nx) {
-            dk = diag_site<T, KIND>(rd, which, neighbour_count(rd, geo, xk), s, LG.a[k], PF.a[k]);
+            dk = diag_site<T, KIND>(q, neighbour_count(rd, geo, xk), s, LG.a[k], PF.a[k]);
             if (KIND == 0) bk = (is_vessel(s) ? bvessel : T(0)) + (o2t ? X.a[k] * bx : T(0));
             else if (vegf) bk = X.a[k] * bx + (is_consumer(s) ? av * VC.a[k] : T(0));
-            else bk = X.a[k] * bx + (is_vessel(s) ? (T)rd.kappa[which - 1] * PF.a[k] * G0 : T(0));
+            else bk = X.a[k] * bx + (is_vessel(s) ? q.kappa * PF.a[k] * G0 : T(0));
             const T ax = dk * X.a[k] - cpl * nb_sum(X, k, left, right, ym, yp, zm, zp);
             if (bax) bk -= ax;   // Crank-Nicolson: b = (4/h) x0 - A x0 + f^{k-1} + f^k
             const T r = bk - ax;
@@ -226,7 +242,7 @@ __global__ void __maxnreg__(REGS) k_pass_a(Ctx c, int which) {
     // the first iteration of a rescaled inner solve starts from scale * z
     // (the V-cycle scales r itself before it forms z)
     const T zs = (sv.iters == 0 && !c.mg) ? (T)sv.scale : T(1);
-    const T cpl = (T)op_coupling(rd, which);
+    const T cpl = op_coupling_t<T>(rd, which);
     const RowIter it = row_iter(rd);
     // one row j (chunk slot rl of `chunk`; row_ok false: a padding slot of the last chunk)
     auto row = [&](int chunk, int rl, bool row_ok, int j) {
@@ -435,7 +451,7 @@ __global__ void __launch_bounds__(512) k_true_residual(Ctx c, int which, void* x
   T* __restrict__ xx = (T*)xfield;
   const T* __restrict__ dd = (const T*)c.d;
   const T* __restrict__ bb = (const T*)c.b;
-  const T cpl = (T)op_coupling(rd, which);
+  const T cpl = op_coupling_t<T>(rd, which);
   const T bvessel = (T)(rd.r_K * rd.K0);
   const RowIter it = row_iter(rd);
   for (int rbase = it.warp * it.rpw; rbase < rd.chunk_rows; rbase += it.nw * it.rpw) {
@@ -524,7 +540,8 @@ __global__ void __launch_bounds__(512) k_apply(Ctx c, int which, int rep, const 
   const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
   const T* __restrict__ K = (const T*)c.K;
   const T* __restrict__ perf = (const T*)c.perf;
-  const T cpl = (T)op_coupling(rd, which);
+  const Coef<T> q = coef<T, KIND>(rd, which);
+  const T cpl = q.cpl;
   const RowIter it = row_iter(rd);
   for (int rbase = it.warp * it.rpw; rbase < rd.chunk_rows; rbase += it.nw * it.rpw) {
     const int rl = rbase + it.sub;
@@ -552,7 +569,7 @@ __global__ void __launch_bounds__(512) k_apply(Ctx c, int which, int rep, const 
           const int xk = 4 * g + k;
           O.a[k] = T(0);
           if (xk < rd.nx) {
-            const T dk = diag_site<T, KIND>(rd, which, neighbour_count(rd, geo, xk), st_at(st, k), KK.a[k], PF.a[k]);
+            const T dk = diag_site<T, KIND>(q, neighbour_count(rd, geo, xk), st_at(st, k), KK.a[k], PF.a[k]);
             O.a[k] = dk * U.a[k] - cpl * nb_sum(U, k, left, right, ym, yp, zm, zp);
           }
         }
@@ -620,8 +637,35 @@ struct ScaledAcc {
       m += scalbnf(s, ex - e);
     }
   }
-  __device__ __forceinline__ double value() const { return m == 0.f ? 0.0 : ldexp((double)m, e); }
+  // m 2^e in FP64, exactly: 2^e is built from its bits when it is a normal
+  // double (two FP64-pipe instructions instead of a library ldexp)
+  __device__ __forceinline__ double value() const {
+    if (m == 0.f) return 0.0;
+    if (e < -1022 || e > 1023) return ldexp((double)m, e);
+    return (double)m * __longlong_as_double((long long)(e + 1023) << 52);
+  }
 };
+
+// The sum of a row's lane accumulators (lane segments of lpr lanes, fixed
+// xor tree: partners form the same sum, so every lane of the segment ends
+// with it) in FP32 arithmetic, converted to FP64 once per row.
+__device__ __forceinline__ double row_reduce_scaled(ScaledAcc a, int lpr) {
+  for (int o = lpr >> 1; o > 0; o >>= 1) {
+    const float bm = __shfl_xor_sync(0xffffffffu, a.m, o, 32);
+    const int be = __shfl_xor_sync(0xffffffffu, a.e, o, 32);
+    if (bm != 0.f) {
+      if (a.m == 0.f) {
+        a.m = bm;
+        a.e = be;
+      } else {
+        const int e = max(a.e, be);
+        a.m = scalbnf(a.m, a.e - e) + scalbnf(bm, be - e);
+        a.e = e;
+      }
+    }
+  }
+  return a.value();
+}
 
 // --------------------------------------------------- defect correction ---
 // FP32 storage scheme.  The solution is kept as two FP32 words, x = x_hi +
@@ -667,7 +711,8 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
     float* __restrict__ bb = (float*)c.b;
     float* __restrict__ dxv = (float*)c.dx;
     const float* __restrict__ perf = (const float*)c.perf;
-    const double cpl = (double)(float)op_coupling(rd, which);
+    const Coef<float> q = coef<float, KIND>(rd, which);
+    const double cpl = (double)q.cpl;
     const float G0 = KIND == 1 && FIRST ? (float)s_G0 : 0.f;
     const bool bax = rd.bax[which] != 0;
     const bool o2t = KIND == 0 && rd.bx[0] != 0.0;
@@ -675,6 +720,7 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
     // bx as an unevaluated float pair (b = bx x0 + ... is formed to ~48 bits)
     const float bx_hi = (float)bx, bx_lo = (float)(bx - (double)bx_hi);
     const float bvessel = (float)(bax ? 2.0 * rd.r_K * rd.K0 : rd.r_K * rd.K0);
+    const float av = (float)(bax ? 2.0 * rd.a_vegf : rd.a_vegf);
     const RowIter it = row_iter(rd);
     const float cpl32 = (float)cpl;
     // one row j (chunk slot rl of `chunk`; row_ok false: a padding slot of the last chunk)
@@ -716,7 +762,6 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
         x_neighbours(Xl, g, rd.gpr, it.sl, it.lpr, gok, carry_l, ll, rlo, [&] { return rnl; });
         if (gok) {
           if (FIRST) {
-            const float av = (float)(bax ? 2.0 * rd.a_vegf : rd.a_vegf);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
               const int xk = 4 * g + k;
@@ -732,14 +777,14 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
                 const float xk32 = __fadd_rn(Xh.a[k], Xl.a[k]);
                 // the operator is linearised about K_prev: the start field, or c.lag when the solve starts from another guess
                 const float lag = (KIND == 0 && c.lag) ? ((const float*)c.lag)[e + k] : xk32;
-                AR.a[k] = reaction_site<float, KIND>(rd, which, s, lag, PF.a[k]);
+                AR.a[k] = reaction_site<float, KIND>(q, s, lag, PF.a[k]);
                 D.a[k] = cpl32 * (float)neighbour_count(rd, geo, xk) + AR.a[k];
                 if (KIND == 0) {
                   SRC.a[k] = is_vessel(s) ? bvessel : 0.f;
                   B.a[k] = SRC.a[k] + (o2t ? xb32 : 0.f);
                 } else {
                   if (vegf) SRC.a[k] = is_consumer(s) ? av * VC.a[k] : 0.f;
-                  else SRC.a[k] = is_vessel(s) ? __fmul_rn(__fmul_rn((float)rd.kappa[which - 1], PF.a[k]), G0) : 0.f;
+                  else SRC.a[k] = is_vessel(s) ? __fmul_rn(__fmul_rn(q.kappa, PF.a[k]), G0) : 0.f;
                   B.a[k] = __fadd_rn(xb32, SRC.a[k]);
                 }
               }
@@ -818,10 +863,11 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
           st4(dxv + e, zero4<float>());
         }
       }
-      double acc[NDOT];
 #pragma unroll
-      for (int k = 0; k < NDOT; ++k) acc[k] = la[k].value();
-      store_row(c, chunk, rl, row_ok, it.sl, it.lpr, acc, 3);
+      for (int k = 0; k < NDOT; ++k) {
+        const double v = row_reduce_scaled(la[k], it.lpr);
+        if (row_ok && it.sl == 0) c.rowp[((long long)chunk * CHUNK_ROWS + rl) * NDOT + k] = v;
+      }
     };
     if (PERSIST) {
       const int R = rd.ny * rd.nz, cr = rd.chunk_rows;
