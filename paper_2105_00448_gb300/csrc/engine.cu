@@ -422,20 +422,20 @@ void pass_b(hca_handle* h, int which, void* x, hca::CondArg cnd) {
 // z = M r (V-cycle); also sets rho and beta for the next pass A.  first: the
 // residual was just formed (start of a solve or a defect-correction sweep),
 // so it may still need its power-of-two scaling.
-// Inside a captured step graph the coarse levels run as one launch per level
-// (graph-launched kernels follow each other closely, and the per-level
-// kernels keep more warps per SM than the cooperative kernel: measured
-// faster); from host loops, where each launch costs host time, as the one
-// cooperative launch (HCA_MG_COOP_GRAPH=1 captures the cooperative launch
-// too).
+// Inside a captured step graph the coarse levels run as one launch per
+// kernel (graph-launched kernels follow each other closely, and the
+// per-level kernels keep more warps per SM than the cooperative kernel:
+// measured faster, also against the cooperative launch of only the levels
+// below 2^18 sites); from host loops, where each launch costs host time, as
+// the one cooperative launch.  HCA_MG_COOP_GRAPH=1 captures the cooperative
+// launch from level 1, =2 from the first level below 2^18 sites.
 void vcycle(hca_handle* h, int which, bool first) {
-  static const bool coop_graph = [] {
-    const char* e = std::getenv("HCA_MG_COOP_GRAPH");
-    return e && e[0] == '1';
-  }();
-  if (h->capturing && h->mgh.coop_blocks > 0 && !coop_graph) {
+  if (h->capturing && h->mgh.coop_blocks > 0) {
+    const char* e = std::getenv("HCA_MG_COOP_GRAPH");   // 0 none, 1 all coarse levels, else from coop_lo
+    const int coop_graph = e ? e[0] - '0' : 0;
     hca::MGHost H = h->mgh;
-    H.coop_blocks = 0;
+    if (coop_graph == 0) H.coop_blocks = 0;
+    else H.coop_from = coop_graph == 1 ? 1 : H.coop_lo;
     hca::launch_vcycle(h->ctx, which, h->fp64, H, -1, first);
     return;
   }

@@ -310,6 +310,11 @@ struct MGHost {
   int coop_blocks = 0;
   int small_smem = 0;
   int coop_cfg = 0;              // launch shape of the cooperative kernel (threads, register budget)
+  // first level of the cooperative launch: 1 in host loops; in captured
+  // graphs the first level small enough for it (coop_lo), the levels above
+  // keep their per-level kernels
+  int coop_from = 1;
+  int coop_lo = 1;
   bool small_smem_ok = false;    // the standalone single-block kernel runs in shared memory
   int small = 0;                 // 1 + deepest grid-kernel level of any replicate
   long long ntot[MG_MAXLEV] = {};  // sites of level l summed over the replicates

@@ -143,20 +143,47 @@ struct RepCursor {
 };
 
 // ------------------------------------------------------ per-site steps --
-// d_C(I) = c_C n_C(I) + sum over children of max(0, d_F - c_F n_F); w_C = 1 / d_C
+// d_C(I) = c_C n_C(I) + sum over children of max(0, d_F - c_F n_F); w_C = 1 / d_C.
+// FP64 fields: in FP64.  FP32 fields: in FP32 (FP64 runs at a small fraction
+// of the FP32 rate on this GPU); d_F - c_F n_F is then exact whenever
+// c_F n_F is within a factor two of d_F (Sterbenz), i.e. the recovered
+// reaction carries only the rounding of the stored FP32 diagonal and of c_F n_F.
+__device__ __forceinline__ float nbcount_f(int X, int Y, int Z, int nx, int ny, int nz) {
+  return ((X > 0 ? 1.f : 0.f) + (X < nx - 1 ? 1.f : 0.f)) + ((Y > 0 ? 1.f : 0.f) + (Y < ny - 1 ? 1.f : 0.f)) +
+         ((Z > 0 ? 1.f : 0.f) + (Z < nz - 1 ? 1.f : 0.f));
+}
+
 template <typename T>
-__device__ void coarse_diag_at(const View<T>& F, const View<T>& C, long long S) {
+__device__ void coarse_diag_at(const View<T>& F, const View<T>& C, long long S);
+
+template <>
+__device__ void coarse_diag_at<float>(const View<float>& F, const View<float>& C, long long S) {
+  int X, Y, Z;
+  C.coords(S, X, Y, Z);
+  float a = 0.f;
+  for (int k = 0; k < 8; ++k) {
+    const int x = 2 * X + (k & 1), y = 2 * Y + ((k >> 1) & 1), z = 2 * Z + (k >> 2);
+    if (x < F.nx && y < F.ny && z < F.nz)
+      a += fmaxf(0.f, F.d[F.at(x, y, z)] - F.c * nbcount_f(x, y, z, F.nx, F.ny, F.nz));
+  }
+  const float dc = C.c * nbcount_f(X, Y, Z, C.nx, C.ny, C.nz) + a;
+  C.d[C.at(X, Y, Z)] = dc;
+  C.w[C.at(X, Y, Z)] = dc != 0.f ? 1.f / dc : 0.f;
+}
+
+template <>
+__device__ void coarse_diag_at<double>(const View<double>& F, const View<double>& C, long long S) {
   int X, Y, Z;
   C.coords(S, X, Y, Z);
   double a = 0.0;
   for (int k = 0; k < 8; ++k) {
     const int x = 2 * X + (k & 1), y = 2 * Y + ((k >> 1) & 1), z = 2 * Z + (k >> 2);
     if (x < F.nx && y < F.ny && z < F.nz)
-      a += fmax(0.0, (double)F.d[F.at(x, y, z)] - (double)F.c * F.nbcount(x, y, z));
+      a += fmax(0.0, F.d[F.at(x, y, z)] - F.c * F.nbcount(x, y, z));
   }
-  const double dc = (double)C.c * C.nbcount(X, Y, Z) + a;
-  C.d[C.at(X, Y, Z)] = (T)dc;
-  C.w[C.at(X, Y, Z)] = dc != 0.0 ? (T)(1.0 / dc) : T(0);
+  const double dc = C.c * C.nbcount(X, Y, Z) + a;
+  C.d[C.at(X, Y, Z)] = dc;
+  C.w[C.at(X, Y, Z)] = dc != 0.0 ? 1.0 / dc : 0.0;
 }
 
 // w = 1 / d on the lattice
@@ -1012,17 +1039,18 @@ __global__ void __launch_bounds__(kSmallThreads) k_mg_small_smem(Ctx c, int whic
 }
 
 // ------------------------------------- coarse levels in one cooperative launch --
-// Levels 1 .. nlev-1 of one V-cycle in one cooperative launch: the
-// pre-sweeps and restrictions l -> l + 1 for l = 1 .. small-1, the
+// Levels lo .. nlev-1 of one V-cycle in one cooperative launch: the
+// pre-sweeps and restrictions l -> l + 1 for l = lo .. small-1, the
 // single-block sub-cycle (block b takes replicates b, b + grid, ...; its
 // levels in dynamic shared memory when small_smem > 0), then the two
-// post-sweeps of l = small-1 .. 1, with a grid barrier between consecutive
+// post-sweeps of l = small-1 .. lo, with a grid barrier between consecutive
 // phases.  Each phase is the loop body of
 // the corresponding per-level kernel over this launch's threads, so the
 // result is bit-identical to the per-level launches.  rows_ok: bit l selects
 // the row-vector form of level l (as for the per-level kernels).
 template <typename T, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) k_mg_coarse(Ctx c, int which, int small, unsigned rows_ok, int use_smem) {
+__global__ void __launch_bounds__(NT, MINB) k_mg_coarse(Ctx c, int which, int lo, int small, unsigned rows_ok,
+                                                         int use_smem) {
   HCA_COUNT_KERNEL(c);
   extern __shared__ __align__(16) unsigned char mg_smem[];
   T* sm = (T*)mg_smem;
@@ -1034,7 +1062,7 @@ __global__ void __launch_bounds__(NT, MINB) k_mg_coarse(Ctx c, int which, int sm
   const bool pre = use_smem && blockIdx.x < c.n_reps;
   if (pre) small_prefetch<T>(c, which, blockIdx.x, threadIdx.x, blockDim.x, sm);
   int k = 0;
-  for (int l = 1; l < small; ++l) {
+  for (int l = lo; l < small; ++l) {
     const bool rows = rows_ok >> l & 1u;
     if (rows) smooth_rows<T, SM_PRE>(c, which, l, t0, st);
     else if (multi) smooth_sites<T, true, SM_PRE>(c, which, l, t0, st);
@@ -1051,7 +1079,7 @@ __global__ void __launch_bounds__(NT, MINB) k_mg_coarse(Ctx c, int which, int sm
     __syncthreads();
   }
   if (!grid_barrier(c.sync, k++)) return;
-  for (int l = small - 1; l >= 1; --l) {
+  for (int l = small - 1; l >= lo; --l) {
     const bool rows = rows_ok >> l & 1u;
     if (rows) smooth_rows<T, SM_POST>(c, which, l, t0, st);
     else if (multi) smooth_sites<T, true, SM_POST>(c, which, l, t0, st);
@@ -1060,7 +1088,7 @@ __global__ void __launch_bounds__(NT, MINB) k_mg_coarse(Ctx c, int which, int sm
     if (rows) smooth_rows<T, SM_LAST>(c, which, l, t0, st);
     else if (multi) smooth_sites<T, true, SM_LAST>(c, which, l, t0, st);
     else smooth_sites<T, false, SM_LAST>(c, which, l, t0, st);
-    if (l > 1 && !grid_barrier(c.sync, k++)) return;
+    if (l > lo && !grid_barrier(c.sync, k++)) return;
   }
   grid_exit(c.sync, k);
 }
@@ -1288,15 +1316,13 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
   const int nb = (int)std::max(1LL, std::min((H.nrowitems + 127) / 128, 152LL * 16));
   if (all || part == 1) k_mg_pre0<T><<<nb, 128, 0, s>>>(c, which, z);
   if (all || part == 2) k_mg_restrict0_rows<T><<<nb, 128, 0, s>>>(c, which, z);
-  if ((all || part == 3) && H.coop_blocks > 0) {
-    Ctx cc = c;
-    int wh = which, sm = H.small, use = H.small_smem > 0;
-    unsigned rows = H.rows_ok;
-    void* args[] = {&cc, &wh, &sm, &rows, &use};
-    (void)cudaLaunchCooperativeKernel(coarse_fn<T>(H.coop_cfg), dim3(H.coop_blocks), dim3(coarse_threads(H.coop_cfg)),
-                                      args, (size_t)H.small_smem, s);
-  } else if (all || part == 3) {
-    for (int l = 1; l < H.small; ++l) {
+  if (all || part == 3) {
+    // levels 1 .. lo-1 by per-level kernels, lo .. nlev-1 in the cooperative
+    // launch when there is one (lo = small: no level in it but the
+    // single-block ones, which then run in their own kernel)
+    const bool coop = H.coop_blocks > 0 && H.coop_from < H.small;
+    const int lo = coop ? H.coop_from : H.small;
+    for (int l = 1; l < lo; ++l) {
       if (H.rows_ok >> l & 1u) {
         k_mg_smooth_rows<T, SM_PRE><<<grid_for(H.post_items[l]), kMgThreads, 0, s>>>(c, which, l);
         // 128 threads: ~12 vector loads per thread in flight
@@ -1309,11 +1335,19 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
         k_mg_restrict<T, false><<<grid_for(H.ntot[l + 1]), kMgThreads, 0, s>>>(c, which, l);
       }
     }
-    if (H.small_smem > 0 && H.small_smem_ok)
+    if (coop) {
+      Ctx cc = c;
+      int wh = which, l0 = lo, sm = H.small, use = H.small_smem > 0;
+      unsigned rows = H.rows_ok;
+      void* args[] = {&cc, &wh, &l0, &sm, &rows, &use};
+      (void)cudaLaunchCooperativeKernel(coarse_fn<T>(H.coop_cfg), dim3(H.coop_blocks),
+                                        dim3(coarse_threads(H.coop_cfg)), args, (size_t)H.small_smem, s);
+    } else if (H.small_smem > 0 && H.small_smem_ok) {
       k_mg_small_smem<T><<<c.n_reps, kSmallThreads, (size_t)H.small_smem, s>>>(c, which);
-    else
+    } else {
       k_mg_small<T><<<c.n_reps, kSmallThreads, 0, s>>>(c, which);
-    for (int l = H.small - 1; l >= 1; --l) {
+    }
+    for (int l = lo - 1; l >= 1; --l) {
       if (H.rows_ok >> l & 1u) {
         k_mg_smooth_rows<T, SM_POST><<<grid_for(H.post_items[l]), kMgThreads, 0, s>>>(c, which, l);
         k_mg_smooth_rows<T, SM_LAST><<<grid_for(H.post_items[l]), kMgThreads, 0, s>>>(c, which, l);
@@ -1380,6 +1414,10 @@ int coop_config_t(MGHost& H, int sm_count, long long smem_bytes) {
   }
   H.coop_blocks = per_sm * sm_count;
   H.coop_cfg = cfg;
+  // the first level small enough for the cooperative launch's threads
+  // inside graphs (about one 4-site group per thread and level): 2^18 sites
+  H.coop_lo = 1;
+  while (H.coop_lo < H.small && H.ntot[H.coop_lo] > (1LL << 18)) ++H.coop_lo;
   return 0;
 }
 
@@ -1421,7 +1459,10 @@ void launch_vcycle(const Ctx& c, int which, bool fp64, const MGHost& H, int part
 int vcycle_part_launches(const MGHost& H, int part, bool scale) {
   if (part == 0) return scale ? 1 : 0;
   if (H.nlev == 1) return part == 3 ? MG_NU_COARSE : 0;
-  if (part == 3) return H.coop_blocks > 0 ? 1 : 4 * (H.small - 1) + 1;
+  if (part == 3) {
+    const int lo = H.coop_blocks > 0 && H.coop_from < H.small ? H.coop_from : H.small;
+    return 4 * (lo - 1) + 1;
+  }
   return 1;
 }
 

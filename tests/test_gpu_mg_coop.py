@@ -4,8 +4,10 @@ per level (HCA_MG_COOP=0, read at handle creation): both run the same per-site
 arithmetic in the same order, so z = M r, whole solves and coupled steps must
 agree bit for bit, in FP64 and FP32, for single lattices and batches.  The
 library uses the cooperative launch from host-driven loops (the coupled runs
-here set HCA_NO_GRAPH=1) and the per-level launches inside captured step
-graphs.  The V-cycle itself is compared with the oracle in test_gpu_mg.py.
+here set HCA_NO_GRAPH=1) and per-level launches inside captured step graphs
+(HCA_MG_COOP_GRAPH=2 captures the cooperative launch for the levels below
+2^18 sites).  The V-cycle itself is compared with the oracle in
+test_gpu_mg.py.
 """
 
 import os
@@ -105,3 +107,30 @@ def test_batch_coop_equals_per_level_launches():
     for x, y in zip(a, b):
         for u, v in zip(x, y):
             assert np.array_equal(u, v)
+
+
+@pytest.mark.parametrize("n", [48, 160])
+def test_graph_steps_with_coop_tail_equal_per_level_launches(n):
+    """Captured step graphs with HCA_MG_COOP_GRAPH=2: at 160^3 level 1
+    (80^3 sites) keeps its per-level kernels and the cooperative launch
+    starts at level 2; at 48^3 it starts at level 1.  Both give the
+    per-level launches' bits."""
+
+    def run():
+        maps = make_maps(n, n, n, corr_len=4.0, seed=7)
+        sim = hca.Sim.create(n, n, n, maps.p_cell, maps.perf, maps.p_vessel, precision="f32", n_drugs=2,
+                             seed=7, preconditioner=hca.HCA_PC_MG)
+        sim.step(2)
+        out = (sim.states(), sim.field(hca.FIELD_O2), sim.field(hca.FIELD_DRUG1), sim.stats())
+        sim.close()
+        return out
+
+    os.environ["HCA_MG_COOP_GRAPH"] = "2"
+    try:
+        a = _with_coop(True, run)
+    finally:
+        os.environ.pop("HCA_MG_COOP_GRAPH", None)
+    b = _with_coop(False, run)
+    for k in range(3):
+        assert np.array_equal(a[k], b[k])
+    assert a[3]["drug_iterations"] == b[3]["drug_iterations"]
