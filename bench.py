@@ -439,8 +439,17 @@ def run_gpu(args):
                               "o2_rel_residual": stats["o2_rel_residual"],
                               "drug_rel_residual": stats["drug_rel_residual"][:2], "counts": stats["counts"]},
                 "kernel_time_share": kernel_share, "status": int(rc)}
-        if args.ws_learned and world == 1:
-            line["warm_start_learned"] = run_ws_learned(args, hca, make_maps, np, torch)
+        if not args.skip_ws and world == 1:
+            ws = run_ws_learned(args, hca, make_maps, np, torch)
+            line["warm_start_learned"] = ws
+            prev, lrn = ws["previous_step_start"], ws["learned_start"]
+            line["learned_vs_plain"] = {
+                "workload": ws["workload"],
+                "o2_iterations_per_step": {"plain": prev["o2_iterations_per_step"],
+                                           "learned": lrn["o2_iterations_per_step"]},
+                "ms_per_step": {"plain": prev["ms_per_step"], "learned": lrn["ms_per_step"]},
+                "step_time_ratio": ws["step_time_ratio"], "net_forward_ms": ws["net_forward"]["ms"],
+                "net_tensor_frac": ws["roofline"]["frac"]}
         if args.batch and world == 1:
             line["batched"] = run_batch(args, hca, torch)
         if args.paper_time and world == 1:
@@ -739,8 +748,8 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=2)
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--ws-learned", action="store_true",
-                    help="also train and measure the learned oxygen warm start (about a minute)")
+    ap.add_argument("--skip-ws", action="store_true",
+                    help="skip training and measuring the learned oxygen warm start (about a minute)")
     ap.add_argument("--ws-samples", type=int, default=48)
     ap.add_argument("--ws-iters", type=int, default=4000)
     ap.add_argument("--ws-steps", type=int, default=10)
