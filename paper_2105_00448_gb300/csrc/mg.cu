@@ -730,7 +730,7 @@ __device__ __forceinline__ Item0 item0(const Ctx& c, long long q) {
 // neighbour rows, the x neighbours at the group's ends) is issued before u is
 // formed.
 template <typename T>
-__global__ void __launch_bounds__(128) k_mg_pre0(Ctx c, int which, T* __restrict__ dst) {
+__global__ void __launch_bounds__(128, 5) k_mg_pre0(Ctx c, int which, T* __restrict__ dst) {
   HCA_COUNT_KERNEL(c);
   const T* __restrict__ rr = (const T*)c.r;
   const T* __restrict__ ww = (const T*)c.mg_w;
@@ -811,7 +811,7 @@ __global__ void __launch_bounds__(128) k_mg_pre0(Ctx c, int which, T* __restrict
 // neighbours of v at the group's ends, all loaded before the residuals are
 // formed: 16.5 B per site.  Children in the order of restrict_residual_at.
 template <typename T>
-__global__ void __launch_bounds__(128) k_mg_restrict0_rows(Ctx c, int which, const T* __restrict__ src) {
+__global__ void __launch_bounds__(128, 4) k_mg_restrict0_rows(Ctx c, int which, const T* __restrict__ src) {
   HCA_COUNT_KERNEL(c);
   T* __restrict__ vo = (T*)c.mg_t0;
   const T* __restrict__ rr = (const T*)c.r;
@@ -1171,7 +1171,7 @@ __global__ void __maxnreg__(64) k_mg_post0(Ctx c, int which, const T* __restrict
               const T p = k < 2 ? C0 : C1;
               const T pl = x > 0 ? (k == 0 ? Cl : k < 3 ? C0 : C1) : T(0);
               const T pr = x < rd.nx - 1 ? (k == 3 ? Cr : k == 0 ? C0 : C1) : T(0);
-              const T nb = ((pl + pr) + nin * p) + ((k < 2 ? Y0 : Y1) + (k < 2 ? Z0 : Z1));
+              const T nb = ((pl + pr) + mul_rn(nin, p)) + ((k < 2 ? Y0 : Y1) + (k < 2 ? Z0 : Z1));
               Yo.a[k] = fma(wt(MG_W2, W.a[k]), cpl * nb, fma((T)(1.0 - MG_W2), p, V.a[k]));
             }
           }
@@ -1314,6 +1314,9 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
   }
   // 128 threads: the lattice kernels keep ~20-28 vector loads per thread in flight
   const int nb = (int)std::max(1LL, std::min((H.nrowitems + 127) / 128, 152LL * 16));
+  // register budgets (blocks per SM): 5 for the pre-sweeps (a few spilled
+  // registers; measured 71.4 -> 67.6 us at 256^3), 4 for the restriction
+  // (61.4 us; 65.5 us with 5)
   if (all || part == 1) k_mg_pre0<T><<<nb, 128, 0, s>>>(c, which, z);
   if (all || part == 2) k_mg_restrict0_rows<T><<<nb, 128, 0, s>>>(c, which, z);
   if (all || part == 3) {
