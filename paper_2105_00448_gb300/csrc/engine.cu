@@ -34,7 +34,7 @@ int ca_coop_blocks(bool fp64, int sm_count);
 void launch_ca_colours(const Ctx& c, int blocks, bool fp64);
 void launch_ca_sync(const Ctx& c, int blocks_x, bool fp64);
 void launch_vessels(const Ctx& c, bool fp64);
-void launch_mg_setup(const Ctx& c, int which, bool fp64, const MGHost& H);
+void launch_mg_setup(const Ctx& c, int which, bool fp64, const MGHost& H, bool w_done);
 void launch_vcycle(const Ctx& c, int which, bool fp64, const MGHost& H, int part, bool scale);
 int vcycle_launches(const MGHost& H, bool scale);
 int vcycle_part_launches(const MGHost& H, int part, bool scale);
@@ -460,7 +460,9 @@ int vcycle_host(hca_handle* h, int which, bool first) {
 }
 
 // coarse diagonals of the current operator (after its set-up stored d)
-void mg_setup(hca_handle* h, int which) { hca::launch_mg_setup(h->ctx, which, h->fp64, h->mgh); }
+void mg_setup(hca_handle* h, int which, bool w_done = false) {
+  hca::launch_mg_setup(h->ctx, which, h->fp64, h->mgh, w_done);
+}
 
 // CG iterations (pass A, pass B) on operator `which` for every replicate whose
 // solve is active, updating x, until none is active or maxit is reached.  The
@@ -525,7 +527,7 @@ int solve_dc(hca_handle* h, int which) {
     HCA_LAUNCH(h, HCA_KCLASS_RESIDUAL, 1,
                hca::launch_dc_residual(c, which, xh, xl, outer == 0, kNoCond, kNoCond));
     if (h->mg) {
-      if (outer == 0) HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.nlev, mg_setup(h, which));
+      if (outer == 0) HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.nlev - 1, mg_setup(h, which, true));
       const int rv = vcycle_host(h, which, true);
       if (rv) return rv;
     }
@@ -648,7 +650,7 @@ int cap_solve(hca_handle* h, int which, cudaGraph_t G) {
   c.stream = S;
   hca::launch_dc_residual(c, which, xh, xl, true, co, ci);
   if (h->mg) {
-    mg_setup(h, which);
+    mg_setup(h, which, true);
     vcycle(h, which, true);
   }
   HCA_TRY(cudaGetLastError());

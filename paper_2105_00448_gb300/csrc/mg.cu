@@ -1368,8 +1368,8 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
 }
 
 template <typename T>
-void mg_setup_t(const Ctx& c, int which, const MGHost& H) {
-  k_mg_w0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, c.stream>>>(c, which);
+void mg_setup_t(const Ctx& c, int which, const MGHost& H, bool w_done) {
+  if (!w_done) k_mg_w0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, c.stream>>>(c, which);
   for (int l = 1; l < H.nlev; ++l) k_mg_diag<T><<<grid_for(H.ntot[l]), kMgThreads, 0, c.stream>>>(c, which, l);
 }
 
@@ -1449,9 +1449,11 @@ void mg_coop_config(MGHost& H, bool fp64, int sm_count, long long smem_bytes) {
 }
 // (H.small: the deepest grid-kernel level + 1 over the batch)
 
-void launch_mg_setup(const Ctx& c, int which, bool fp64, const MGHost& H) {
-  if (fp64) mg_setup_t<double>(c, which, H);
-  else mg_setup_t<float>(c, which, H);
+// w_done: the lattice's 1/d is already in place (the first defect-correction
+// residual sweep of an FP32 solve forms it).
+void launch_mg_setup(const Ctx& c, int which, bool fp64, const MGHost& H, bool w_done) {
+  if (fp64) mg_setup_t<double>(c, which, H, w_done);
+  else mg_setup_t<float>(c, which, H, w_done);
 }
 
 void launch_vcycle(const Ctx& c, int which, bool fp64, const MGHost& H, int part, bool scale) {

@@ -28,6 +28,8 @@
 #include <mutex>
 #include <vector>
 
+#include <cstdlib>
+
 #include "hca_internal.cuh"
 #include "row_ops.cuh"
 
@@ -689,8 +691,8 @@ __device__ __forceinline__ void dc_epilogue(const Ctx& c, int ndot, int chunk, F
   else warp_epilogue(c, ndot, chunk, fin, post);
 }
 
-template <int KIND, bool FIRST, bool MG, bool PERSIST = false>
-__global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const float* __restrict__ x_hi,
+template <int KIND, bool FIRST, bool MG, bool PERSIST = false, int REGS = 128>
+__global__ void __launch_bounds__(512) __maxnreg__(REGS) k_dc_residual(Ctx c, int which, const float* __restrict__ x_hi,
                                                      const float* __restrict__ x_lo, CondArg outer,
                                                      CondArg inner) {
   HCA_COUNT_KERNEL(c);
@@ -791,6 +793,12 @@ __global__ void __launch_bounds__(512) k_dc_residual(Ctx c, int which, const flo
             }
             st4(dd + e, D);
             st4(aa + e, AR);
+            if (MG) {   // 1/d for the V-cycle's sweeps (0 where d = 0), as k_mg_w0 forms it
+              V4<float> Wv;
+#pragma unroll
+              for (int k = 0; k < 4; ++k) Wv.a[k] = D.a[k] != 0.f ? 1.f / D.a[k] : 0.f;
+              st4((float*)c.mg_w + e, Wv);
+            }
           }
           V4<float> Z, R32 = zero4<float>();
 #pragma unroll
@@ -1018,8 +1026,9 @@ template <int KIND, bool FIRST, bool MG>
 static void launch_dc_residual_v(const Ctx& c, int which, const float* x_hi, const float* x_lo, CondArg outer,
                                  CondArg inner) {
   if (c.persist) {
-    const int g = persist_grid((const void*)k_dc_residual<KIND, FIRST, MG, true>, c.threads, c.sm_count);
-    k_dc_residual<KIND, FIRST, MG, true><<<g, c.threads, 0, c.stream>>>(c, which, x_hi, x_lo, outer, inner);
+    // a 96-register cap: 16 -> 20 warps per SM (measured 176 -> 170 us per launch at 256^3)
+    const int g = persist_grid((const void*)k_dc_residual<KIND, FIRST, MG, true, 96>, c.threads, c.sm_count);
+    k_dc_residual<KIND, FIRST, MG, true, 96><<<g, c.threads, 0, c.stream>>>(c, which, x_hi, x_lo, outer, inner);
   } else {
     k_dc_residual<KIND, FIRST, MG, false><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, x_hi, x_lo, outer, inner);
   }
