@@ -439,23 +439,38 @@ __device__ __forceinline__ FF ff_mul(FF x, FF y) {
 __device__ __forceinline__ FF ff_neg(FF x) { return FF{-x.hi, -x.lo}; }
 
 // Row sum of float-float lane partials over the row's lane segment (fixed
-// xor tree), as a double.
-__device__ __forceinline__ double row_reduce_ff(FF v, int lpr) {
+// xor tree).
+__device__ __forceinline__ FF row_reduce_ff(FF v, int lpr) {
   for (int o = lpr >> 1; o > 0; o >>= 1) {
     FF w;
     w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o, 32);
     w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o, 32);
     v = ff_add(v, w);
   }
-  return (double)v.hi + (double)v.lo;
+  return v;
 }
 
+// The row slot keeps the float-float pair itself (two FP32 words in the
+// slot's 8 bytes); the chunk reduction converts it to FP64 as hi + lo, one
+// row per lane, instead of every lane of every row (FP64 runs at a small
+// fraction of the FP32 rate on this GPU).  The same FP64 values either way.
 __device__ __forceinline__ void store_row_ff(const Ctx& c, int chunk, int rl, bool row_ok, int sl, int lpr,
                                              const FF* acc, int ndot) {
   for (int k = 0; k < ndot; ++k) {
-    const double v = row_reduce_ff(acc[k], lpr);
-    if (row_ok && sl == 0) c.rowp[((long long)chunk * CHUNK_ROWS + rl) * NDOT + k] = v;
+    const FF v = row_reduce_ff(acc[k], lpr);
+    if (row_ok && sl == 0)
+      *reinterpret_cast<float2*>(&c.rowp[((long long)chunk * CHUNK_ROWS + rl) * NDOT + k]) = make_float2(v.hi, v.lo);
   }
+}
+
+// A row slot's value: an FP64 sum, or (FFROWS) a float-float pair.
+template <bool FFROWS>
+__device__ __forceinline__ double row_slot(const Ctx& c, long long i) {
+  if (FFROWS) {
+    const float2 f = __ldcg(reinterpret_cast<const float2*>(&c.rowp[i]));
+    return (double)f.x + (double)f.y;
+  }
+  return __ldcg(&c.rowp[i]);
 }
 
 // Row sum of a lane-partial over the row's lane segment, written to the
@@ -479,10 +494,10 @@ __device__ __forceinline__ void store_row(const Ctx& c, int chunk, int rl, bool 
 // other replicates of a batch or on which warp performs it.
 // The rest of warp_epilogue once a chunk's row slots are all written: the
 // calling warp sums the chunk and continues to the group and replicate levels.
-template <class Fin, class Post>
+template <bool FFROWS, class Fin, class Post>
 __device__ __forceinline__ void warp_chunk_done(const Ctx& c, int ndot, int chunk, Fin fin, Post post);
 
-template <class Fin, class Post>
+template <bool FFROWS = false, class Fin, class Post>
 __device__ __forceinline__ void warp_epilogue(const Ctx& c, int ndot, int chunk, Fin fin, Post post) {
   const unsigned FULLM = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -495,10 +510,10 @@ __device__ __forceinline__ void warp_epilogue(const Ctx& c, int ndot, int chunk,
   }
   t = __shfl_sync(FULLM, t, 0);
   if (t != nw - 1) return;
-  warp_chunk_done(c, ndot, chunk, fin, post);
+  warp_chunk_done<FFROWS>(c, ndot, chunk, fin, post);
 }
 
-template <class Fin, class Post>
+template <bool FFROWS, class Fin, class Post>
 __device__ __forceinline__ void warp_chunk_done(const Ctx& c, int ndot, int chunk, Fin fin, Post post) {
   const unsigned FULLM = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -508,7 +523,7 @@ __device__ __forceinline__ void warp_chunk_done(const Ctx& c, int ndot, int chun
   const RepDesc& rd = c.reps[ch.x];
   const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
   for (int k = 0; k < ndot; ++k) {
-    double v = lane < nrows ? __ldcg(&c.rowp[((long long)chunk * CHUNK_ROWS + lane) * NDOT + k]) : 0.0;
+    double v = lane < nrows ? row_slot<FFROWS>(c, ((long long)chunk * CHUNK_ROWS + lane) * NDOT + k) : 0.0;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULLM, v, o);
     if (lane == 0) c.partial[(long long)chunk * NDOT + k] = v;
   }
@@ -560,9 +575,9 @@ __device__ __forceinline__ void warp_chunk_done(const Ctx& c, int ndot, int chun
   }
 }
 
-template <class Fin>
+template <bool FFROWS = false, class Fin>
 __device__ __forceinline__ void warp_epilogue(const Ctx& c, int ndot, int chunk, Fin fin) {
-  warp_epilogue(c, ndot, chunk, fin, [](int) {});
+  warp_epilogue<FFROWS>(c, ndot, chunk, fin, [](int) {});
 }
 
 // Grid-wide barrier of a cooperative launch (every block is resident).

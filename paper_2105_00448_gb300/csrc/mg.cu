@@ -1241,8 +1241,9 @@ __global__ void __maxnreg__(64) k_mg_post0(Ctx c, int which, const T* __restrict
     s.rho = s1[0];
     return 1;
   };
-  if (PERSIST) block_arrivals(c, 1, fin, [](int) {});
-  else warp_epilogue(c, 1, blockIdx.x, fin);
+  // float-float row slots for FP32 fields (LaneAcc<float>)
+  if (PERSIST) block_arrivals<sizeof(T) == 4>(c, 1, fin, [](int) {});
+  else warp_epilogue<sizeof(T) == 4>(c, 1, blockIdx.x, fin);
 }
 
 // Launch shapes of the cooperative coarse-level kernel: 0 = 256 threads with

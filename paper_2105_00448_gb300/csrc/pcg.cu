@@ -328,8 +328,9 @@ __global__ void __maxnreg__(REGS) k_pass_a(Ctx c, int which) {
     s.alpha = s.rho / s1[0];
     return 1;
   };
-  if (PERSIST) block_arrivals(c, 1, fin, [](int) {});
-  else warp_epilogue(c, 1, blockIdx.x, fin);
+  // float-float row slots for FP32 fields (LaneAcc<float>)
+  if (PERSIST) block_arrivals<sizeof(T) == 4>(c, 1, fin, [](int) {});
+  else warp_epilogue<sizeof(T) == 4>(c, 1, blockIdx.x, fin);
 }
 
 // ----------------------------------------------------------------- pass B --
@@ -435,8 +436,8 @@ __global__ void __maxnreg__(REGS) k_pass_b(Ctx c, int which, void* xfield, CondA
     }
     set_cond(cnd, go);
   };
-  if (PERSIST) block_arrivals(c, 2, fin, post);
-  else warp_epilogue(c, 2, blockIdx.x, fin, post);
+  if (PERSIST) block_arrivals<sizeof(T) == 4>(c, 2, fin, post);
+  else warp_epilogue<sizeof(T) == 4>(c, 2, blockIdx.x, fin, post);
 }
 
 // ----------------------------------------------------------- true residual --

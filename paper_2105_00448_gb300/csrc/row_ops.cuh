@@ -95,7 +95,7 @@ __device__ __forceinline__ int persist_row_end(int R) { return (int)((long long)
 // one warp of this block, which sums it in the fixed tree of warp_epilogue and
 // continues to the group and replicate levels.  The same sums, in the same
 // order, as the one-block-per-chunk form; only who finishes differs.
-template <class Fin, class Post>
+template <bool FFROWS = false, class Fin, class Post>
 __device__ void block_arrivals(const Ctx& c, int ndot, Fin fin, Post post) {
   const RepDesc& rd = c.reps[0];
   const int R = rd.ny * rd.nz, cr = rd.chunk_rows;
@@ -117,7 +117,7 @@ __device__ void block_arrivals(const Ctx& c, int ndot, Fin fin, Post post) {
     }
     __syncthreads();
     const int nd = s_n;
-    for (int i = (int)(threadIdx.x >> 5); i < nd; i += (int)(blockDim.x >> 5)) warp_chunk_done(c, ndot, s_done[i], fin, post);
+    for (int i = (int)(threadIdx.x >> 5); i < nd; i += (int)(blockDim.x >> 5)) warp_chunk_done<FFROWS>(c, ndot, s_done[i], fin, post);
     __syncthreads();
   }
 }
