@@ -63,6 +63,11 @@ BYTES_MIN_PER_SITE = {**BYTES_PER_SITE, "pass_a": 16}
 # number of sweeps when they are fused) and the coarse levels (33 B per
 # coarse site, by the same count)
 STEP_FIXED_B, STEP_DC_B, STEP_IT_B, VCYCLE_LATTICE_B, VCYCLE_COARSE_B = 70, 13, 40, 29, 33
+# the bytes this design's kernels move per CG iteration (pass A also stores
+# q: 44 B) and per V-cycle (the four lattice kernels: 57 B; per coarse site the
+# four coarse kernels, fused pre-sweeps 16, restriction 12.5, fused first
+# post-sweep 20.5, last sweep 20 B: 69 B)
+STEP_IT_DESIGN_B, VCYCLE_LATTICE_DESIGN_B, VCYCLE_COARSE_DESIGN_B = 44, 57, 69
 
 
 def metric_name(edge: int = N_EDGE) -> str:
@@ -269,13 +274,19 @@ def step_roofline(prof, steps: int, sites: int, ms_per_step: float, level_fracti
              "vcycle_lattice": VCYCLE_LATTICE_B * n_vc, "vcycle_coarse": VCYCLE_COARSE_B * level_fraction * n_vc}
     per_site = sum(terms.values())
     achieved = per_site * sites / (ms_per_step * 1e-3) / 1e9
+    design = (STEP_FIXED_B + STEP_DC_B * n_dc + STEP_IT_DESIGN_B * n_it
+              + n_vc * (VCYCLE_LATTICE_DESIGN_B + VCYCLE_COARSE_DESIGN_B * level_fraction))
     cg_only = (terms["fixed"] + terms["defect_correction"] + terms["cg_iterations"]) * sites / (ms_per_step * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
             "frac": achieved / peak, "bytes_per_site": per_site, "terms_bytes_per_site": terms,
             "counts_per_step": {"cg_iterations": n_it, "dc_sweeps": n_dc, "vcycles": n_vc},
             "frac_without_vcycle": cg_only / peak,
+            "design_bytes_per_site": design,
+            "frac_design_bytes": design * sites / (ms_per_step * 1e-3) / 1e9 / peak,
             "formula": "70 + 13 n_dc + 40 n_it + n_vc (29 + 33 f_coarse) B/site x sites / step time; f_coarse = "
-                       "coarse-level sites per lattice site"}
+                       "coarse-level sites per lattice site; 29 and 33 B are the V-cycle's minimum with its sweeps "
+                       "fused; frac_design_bytes counts what the kernels move (44 B per iteration, "
+                       "57 + 69 f_coarse B per V-cycle)"}
 
 
 def run_reference(args):

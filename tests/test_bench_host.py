@@ -83,6 +83,9 @@ def test_step_roofline_follows_its_formula():
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
     assert r["counts_per_step"] == {"cg_iterations": 10, "dc_sweeps": 3, "vcycles": 13}
     assert r["frac_without_vcycle"] < r["frac"]
+    design = 70 + 13 * 3 + 44 * 10 + 13 * (57 + 69 * 0.125)
+    assert abs(r["design_bytes_per_site"] - design) < 1e-9
+    assert abs(r["frac_design_bytes"] - design * sites / 4e-3 / 1e9 / r["peak"]) < 1e-12
 
 
 def test_all_core_oracle_sample_runs_in_spawned_processes():
