@@ -25,16 +25,19 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
 
 #include "hca.h"
 #include "net_internal.cuh"
+#include "tc.cuh"
 
 namespace hcanet {
 
 using bf16 = __nv_bfloat16;
+namespace tc = hca::tc;
 
 constexpr int kThreads = 128;
 constexpr int kRowX = 16;   // sites per tile row (one m16 MMA tile)
@@ -313,6 +316,173 @@ __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs a) {
       }
     }
   }
+}
+
+// ------------------------------------- forward on the fifth-gen tensor cores --
+// The same convolution (EPI_FWD or EPI_HEAD) as k_conv, on tcgen05.  A tile
+// is TZ planes of 8 (x) by 16 (y) output sites, each plane one M = 128 MMA
+// tile (row r = x + 8 y) with its own FP32 accumulator of CO columns in
+// tensor memory.  The input halo of a tile is staged in shared memory at the
+// output resolution (the decoder's nearest upsampling folded into the
+// staging), 16-byte channel chunks stored chunk-major: the 8 sites of a core
+// matrix (8 consecutive x) are contiguous, the chunk stride is the halo
+// size, the 8-site groups (rows y) are one halo row apart, and a tap's shift
+// moves only the start address.  Persistent blocks: all 27 taps' weights are
+// staged once as (tap, CI chunk, CO) core matrices; the next tile's halo is
+// copied asynchronously (cp.async, zero-filled outside the lattice) into the
+// second of two buffers while one thread per warp issues the current tile's
+// 27 CI/16 MMAs of its planes (K = 16 each; each issuing thread commits to
+// the mbarrier) and the warps read the accumulators back
+// (bias, skip, ReLU, head) once an mbarrier signals their completion
+// (bounded wait: a timeout sets *status and ends the block).  Requires
+// W % 8 == 0 and H % 16 == 0.
+constexpr int kTcX = 8, kTcY = 16;
+
+template <int CI, int TZ>
+constexpr uint32_t tc_halo_bytes() {
+  return (uint32_t)(CI / 8) * (kTcX + 2) * (kTcY + 2) * (TZ + 2) * 16u;
+}
+template <int CI, int CO, int TZ>
+constexpr uint32_t tc_conv_smem_bytes() {
+  return 2u * tc_halo_bytes<CI, TZ>() + 27u * CI * CO * 2u + 16u;
+}
+template <int CO, int TZ>
+constexpr uint32_t tc_cols() {
+  return TZ * CO <= 32 ? 32u : TZ * CO <= 64 ? 64u : TZ * CO <= 128 ? 128u : TZ * CO <= 256 ? 256u : 512u;
+}
+
+// 16-byte copy from global to shared memory; src_bytes = 0 writes zeros
+// (the source is not read).
+__device__ __forceinline__ void cp_async16_zfill(void* sdst, const void* gsrc, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(sdst)), "l"(gsrc), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Start the copies of tile `tile`'s halo into sh (the tile's output origin
+// from its index over (W/8, H/16, ceil(D/TZ))).
+template <int CI, int TZ, bool UP>
+__device__ __forceinline__ void tc_stage_halo(char* sh, const ConvArgs& a, int tile, int tx, int ty) {
+  constexpr int HX = kTcX + 2, HY = kTcY + 2, HZ = TZ + 2, NH = HX * HY * HZ, NCH = CI / 8;
+  const int x0 = (tile % tx) * kTcX, y0 = ((tile / tx) % ty) * kTcY, z0 = (tile / (tx * ty)) * TZ;
+  for (int i = threadIdx.x; i < NH * NCH; i += blockDim.x) {
+    const int h = i % NH, j = i / NH;
+    const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
+    const int gz = z0 - 1 + hz, gy = y0 - 1 + hy, gx = x0 - 1 + hx;
+    const bool in = gz >= 0 && gz < a.D && gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
+    const int iz = UP ? gz >> 1 : gz, iy = UP ? gy >> 1 : gy, ix = UP ? gx >> 1 : gx;
+    const bf16* src = in ? a.in + (((long long)iz * a.Hi + iy) * a.Wi + ix) * CI + 8 * j : a.in;
+    cp_async16_zfill(sh + (uint32_t)j * (NH * 16u) + (uint32_t)h * 16u, src, in ? 16 : 0);
+  }
+}
+
+template <int CI, int CO, int TZ, bool UP, int EPI>
+__global__ void __launch_bounds__(128) k_conv_tc(const ConvArgs a, int* status) {
+  static_assert(CI % 16 == 0 && CO % 16 == 0 && CO <= 256, "tcgen05 conv shapes");
+  static_assert(EPI == EPI_FWD || EPI == EPI_HEAD, "forward epilogues only");
+  constexpr int HX = kTcX + 2, HY = kTcY + 2, NH = HX * HY * (TZ + 2);
+  constexpr int NCH = CI / 8;
+  constexpr uint32_t HALO_B = tc_halo_bytes<CI, TZ>(), TAP_B = CI * CO * 2;
+  constexpr uint32_t NCOL = tc_cols<CO, TZ>();
+  extern __shared__ __align__(128) char smem[];
+  char* shb0 = smem;
+  char* sw = smem + 2 * HALO_B;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sw + 27 * TAP_B);
+  __shared__ uint32_t tmem_holder;
+  const int t = threadIdx.x, warp = t >> 5;
+  const int tx = a.W / kTcX, ty = a.H / kTcY, tz = (a.D + TZ - 1) / TZ;
+  const int ntiles = tx * ty * tz;
+  // weights (27, CO, CI) as core matrices: (tap, CI chunk j, CO group g), once
+  for (int i = t; i < 27 * CO * NCH; i += blockDim.x) {
+    const int j = i % NCH, co = (i / NCH) % CO, tap = i / (NCH * CO);
+    cp_async16_zfill(sw + tap * TAP_B + (uint32_t)j * (CO * 16u) + (uint32_t)(co >> 3) * 128u + (uint32_t)(co & 7) * 16u,
+                     a.w + ((long long)tap * CO + co) * CI + 8 * j, 16);
+  }
+  if ((int)blockIdx.x < ntiles) tc_stage_halo<CI, TZ, UP>(shb0, a, blockIdx.x, tx, ty);
+  cp_async_commit();
+  if (t == 0) tc::mbar_init(mbar, 4);   // one arrival per issuing warp
+  if (warp == 0) tc::alloc(&tmem_holder, NCOL);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_holder;
+  const uint32_t swb = tc::smem_u32(sw);
+  int it = 0;
+  bool alive = true;
+  for (int tile = blockIdx.x; tile < ntiles && alive; tile += gridDim.x, ++it) {
+    char* sh = shb0 + (it & 1) * HALO_B;
+    const int next = tile + gridDim.x;
+    if (next < ntiles) tc_stage_halo<CI, TZ, UP>(shb0 + ((it + 1) & 1) * HALO_B, a, next, tx, ty);
+    cp_async_commit();
+    cp_async_wait<1>();   // everything but the group just committed: this tile's halo (and the weights)
+    tc::fence_async_smem();
+    __syncthreads();
+    const int x0 = (tile % tx) * kTcX, y0 = ((tile / tx) % ty) * kTcY, z0 = (tile / (tx * ty)) * TZ;
+    if ((t & 31) == 0) {
+      // lane 0 of each warp issues the MMAs of planes warp, warp + 4, ...
+      constexpr uint32_t idesc = tc::idesc_bf16(128, CO);
+      const uint32_t shb = tc::smem_u32(sh);
+      for (int p = warp; p < TZ; p += 4)
+        for (int tap = 0; tap < 27; ++tap) {
+          const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+          const uint32_t shift = (uint32_t)(((p + dz + 1) * HY + (dy + 1)) * HX + (dx + 1)) * 16u;
+#pragma unroll
+          for (int kc = 0; kc < CI / 16; ++kc) {
+            const uint64_t ad = tc::smem_desc(shb + shift + 2u * kc * (NH * 16u), NH * 16u, HX * 16u);
+            const uint64_t bd = tc::smem_desc(swb + tap * TAP_B + 2u * kc * (CO * 16u), CO * 16u, 128u);
+            tc::mma_bf16(tmem + (uint32_t)(p * CO), ad, bd, idesc, tap > 0 || kc > 0);
+          }
+        }
+      tc::commit(mbar);
+    }
+    const bool done = tc::mbar_wait(mbar, (uint32_t)(it & 1), 1 << 22);
+    if (!done && (t & 31) == 0) atomicExch(status, 1);
+    alive = __syncthreads_and(done) != 0;   // one decision for the whole block
+    tc::fence_after();
+    if (alive) {
+      const int r = t;   // tile row: x = r % 8, y = r / 8 (TMEM lane r)
+      const int x = x0 + (r & 7), y = y0 + (r >> 3);
+      for (int p = 0; p < TZ; ++p) {
+        const int z = z0 + p;
+        const bool ok = z < a.D;
+        const long long site = ((long long)z * a.H + y) * a.W + x;
+        float head = 0.f;
+#pragma unroll
+        for (int c0 = 0; c0 < CO; c0 += 16) {
+          float v[16];
+          tc::ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(p * CO + c0), v);
+          if (!ok) continue;
+          uint32_t packed[8];
+#pragma unroll
+          for (int k = 0; k < 16; k += 2) {
+            float v0 = v[k] + a.bias[c0 + k], v1 = v[k + 1] + a.bias[c0 + k + 1];
+            if (a.skip) {
+              const __nv_bfloat162 sk = *reinterpret_cast<const __nv_bfloat162*>(a.skip + site * CO + c0 + k);
+              v0 += __low2float(sk);
+              v1 += __high2float(sk);
+            }
+            v0 = fmaxf(v0, 0.f);
+            v1 = fmaxf(v1, 0.f);
+            packed[k / 2] = pack_bf2(v0, v1);
+            if (EPI == EPI_HEAD) head += bfr(v0) * a.head_w[c0 + k] + bfr(v1) * a.head_w[c0 + k + 1];
+          }
+          if (a.out) {
+            uint4* o = reinterpret_cast<uint4*>(a.out + site * CO + c0);
+            o[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            o[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+          }
+        }
+        if (EPI == EPI_HEAD && ok) a.out_f[site] = head + a.head_b[0];
+      }
+    }
+    tc::fence_before();
+    __syncthreads();   // accumulators read and this halo buffer free before the next tile reuses them
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  if (warp == 0) tc::dealloc(tmem, NCOL);
 }
 
 // ------------------------------------------------------------- wgrad ---
@@ -916,6 +1086,11 @@ struct hca_net {
   long long* head_index = nullptr;   // device: destination of the 34 head partials
   long long* bias_index = nullptr;   // device: 7 x 64 destinations of the bias partials
   bool trainable = false;
+  // the full-resolution layers (enc0, dec0 + head) of the forward pass on the
+  // fifth-generation tensor cores (k_conv_tc); tc_status: set by a kernel whose
+  // completion wait timed out
+  bool use_tc = false;
+  int* tc_status = nullptr;
 };
 
 namespace {
@@ -988,6 +1163,49 @@ int set_attributes() {
   if ((rc = wgrad_attr<64, 32, true>())) return rc;
   if ((rc = wgrad_attr<32, 16, true>())) return rc;
   return HCA_OK;
+}
+
+template <int CI, int CO, int TZ, bool UP, int EPI>
+bool conv_tc_attr() {
+  if (cudaFuncSetAttribute(k_conv_tc<CI, CO, TZ, UP, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tc_conv_smem_bytes<CI, CO, TZ>()) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+// One tcgen05 convolution launch; (D, H, W) is the output lattice.
+template <int CI, int CO, int TZ, bool UP, int EPI>
+void conv_tc(cudaStream_t s, int* status, const bf16* in, const bf16* w, const float* bias, const bf16* skip,
+             bf16* out, float* out_f, const float* hw, const float* hb, int D, int H, int W) {
+  ConvArgs a;
+  a.in = in;
+  a.w = w;
+  a.bias = bias;
+  a.skip = skip;
+  a.out = out;
+  a.out_f = out_f;
+  a.head_w = hw;
+  a.head_b = hb;
+  a.D = D;
+  a.H = H;
+  a.W = W;
+  a.Di = UP ? D / 2 : D;
+  a.Hi = UP ? H / 2 : H;
+  a.Wi = UP ? W / 2 : W;
+  const int ntiles = (W / kTcX) * (H / kTcY) * ((D + TZ - 1) / TZ);
+  int per = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv_tc<CI, CO, TZ, UP, EPI>, 128,
+                                                    tc_conv_smem_bytes<CI, CO, TZ>()) != cudaSuccess || per < 1) {
+    cudaGetLastError();
+    per = 1;
+  }
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::min(ntiles, per * sms);
+  k_conv_tc<CI, CO, TZ, UP, EPI><<<grid, 128, tc_conv_smem_bytes<CI, CO, TZ>(), s>>>(a, status);
 }
 
 // One convolution launch; (D, H, W) is the output lattice.
@@ -1064,7 +1282,12 @@ void forward(hca_net* n, cudaStream_t s, bool keep_d0) {
   const int* D = n->Ld;
   const int* H = n->Lh;
   const int* W = n->Lw;
-  conv<16, 16, 4, false, EPI_FWD>(s, n->x, Wq(n, 0), Bias(n, 0), nullptr, n->e0, nullptr, nullptr, nullptr, D[0], H[0], W[0]);
+  if (n->use_tc)
+    conv_tc<16, 16, 4, false, EPI_FWD>(s, n->tc_status, n->x, Wq(n, 0), Bias(n, 0), nullptr, n->e0, nullptr, nullptr,
+                                       nullptr, D[0], H[0], W[0]);
+  else
+    conv<16, 16, 4, false, EPI_FWD>(s, n->x, Wq(n, 0), Bias(n, 0), nullptr, n->e0, nullptr, nullptr, nullptr, D[0],
+                                    H[0], W[0]);
   pool<16>(n, s, n->e0, n->p0, 0);
   conv<16, 32, 4, false, EPI_FWD>(s, n->p0, Wq(n, 1), Bias(n, 1), nullptr, n->e1, nullptr, nullptr, nullptr, D[1], H[1], W[1]);
   pool<32>(n, s, n->e1, n->p1, 1);
@@ -1073,8 +1296,12 @@ void forward(hca_net* n, cudaStream_t s, bool keep_d0) {
   conv<64, 64, 2, false, EPI_FWD>(s, n->p2, Wq(n, 3), Bias(n, 3), nullptr, n->e3, nullptr, nullptr, nullptr, D[3], H[3], W[3]);
   conv<64, 64, 2, true, EPI_FWD>(s, n->e3, Wq(n, 4), Bias(n, 4), n->e2, n->d2, nullptr, nullptr, nullptr, D[2], H[2], W[2]);
   conv<64, 32, 4, true, EPI_FWD>(s, n->d2, Wq(n, 5), Bias(n, 5), n->e1, n->d1, nullptr, nullptr, nullptr, D[1], H[1], W[1]);
-  conv<32, 16, 4, true, EPI_HEAD>(s, n->d1, Wq(n, 6), Bias(n, 6), n->e0, keep_d0 ? n->d0 : nullptr, n->out,
-                                  n->params + n->L.hw_off, n->params + n->L.hb_off, D[0], H[0], W[0]);
+  if (n->use_tc)
+    conv_tc<32, 16, 4, true, EPI_HEAD>(s, n->tc_status, n->d1, Wq(n, 6), Bias(n, 6), n->e0, keep_d0 ? n->d0 : nullptr,
+                                       n->out, n->params + n->L.hw_off, n->params + n->L.hb_off, D[0], H[0], W[0]);
+  else
+    conv<32, 16, 4, true, EPI_HEAD>(s, n->d1, Wq(n, 6), Bias(n, 6), n->e0, keep_d0 ? n->d0 : nullptr, n->out,
+                                    n->params + n->L.hw_off, n->params + n->L.hb_off, D[0], H[0], W[0]);
 }
 
 // Backward pass after forward(keep_d0 = true): the MSE loss against target,
@@ -1179,6 +1406,20 @@ int create_impl(int D, int H, int W, int trainable, void* stream, hca_net** out)
   NET_ALLOC(n->params, n->L.total * sizeof(float));
   NET_ALLOC(n->wq, n->L.wq_total * b2);
   NET_ALLOC(n->wt, n->L.wq_total * b2);
+  NET_ALLOC(n->tc_status, sizeof(int));
+  NET_CUDA(cudaMemset(n->tc_status, 0, sizeof(int)));
+  {
+    // tcgen05 forward for the full-resolution layers with HCA_NET_TC=1
+    // (compute capability 10.x; tiles of 8 x 16 sites).  Off by default: with
+    // 16 output channels every MMA is M128 N16 K16 and the 27 taps' small
+    // instructions, with the upsampled layer's output-resolution halo, cost
+    // more than the mma.sync kernel (256^3 forward 4.99 against 3.81 ms)
+    int major = 0;
+    NET_CUDA(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, n->device));
+    const char* e = std::getenv("HCA_NET_TC");
+    n->use_tc = major == 10 && W % kTcX == 0 && H % kTcY == 0 && (e && e[0] == '1') &&
+                conv_tc_attr<16, 16, 4, false, EPI_FWD>() && conv_tc_attr<32, 16, 4, true, EPI_HEAD>();
+  }
   NET_ALLOC(n->x, Ln[0] * 16 * b2);
   NET_ALLOC(n->e0, Ln[0] * 16 * b2);
   NET_ALLOC(n->p0, Ln[1] * 16 * b2);
