@@ -1450,6 +1450,8 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
       // (HCA_PERSIST=0 keeps one block per chunk)
       const char* pe = std::getenv("HCA_PERSIST");
       c.persist = (!(pe && pe[0] == '0') && n == 1 && !h->fp64 && h->reps_h[0].lpr == 32 && c.pass_ni > 0) ? 1 : 0;
+      const char* pd = std::getenv("HCA_PDL");
+      c.pdl = (pd && pd[0] == '0') ? 0 : 1;
       // the 27 colour sweeps of the CA in one cooperative launch (HCA_CA_COOP=0: one launch per colour)
       h->ca_coop = hca::ca_coop_blocks(h->fp64, c.sm_count);
     }

@@ -16,6 +16,8 @@
 // other replicates of a batch.
 #pragma once
 
+#include <utility>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -349,7 +351,8 @@ struct Ctx {
   int pass_regs;    // register cap of the FP32 CG passes (64, 80, 96, 128)
   int pass_ni;      // groups per lane in a row shared by all replicates (1, 2, 4; 0 = differs)
   int mg;           // 0: Jacobi (z = r / d), 1: V-cycle (z = M r)
-  int persist;      // 1: the CG passes and the lattice post-sweep run in persistent row form (one FP32 lattice)
+  int persist;         // 1: the CG passes and the lattice post-sweep run in persistent row form (one FP32 lattice)
+  int pdl;             // 1: the CG and V-cycle kernels launch with programmatic dependent launch
   void* r;
   void* mg_t0;
   void* mg_w;         // 1 / d on the lattice (0 where d = 0)
@@ -639,10 +642,40 @@ __device__ __forceinline__ void grid_exit(PassSync* sy, int nbar) {
 }
 
 // Count this kernel launch (call once, at kernel entry).
+// At the entry of every kernel: wait until the kernel before it in the
+// stream has completed and its memory is visible (programmatic dependent
+// launch: a kernel launched with the programmatic-serialization attribute may
+// start while its predecessor drains; without it the wait returns at once),
+// then let the next kernel start launching, and count the launch.
 #define HCA_COUNT_KERNEL(c)                                                  \
   do {                                                                       \
+    asm volatile("griddepcontrol.wait;" ::: "memory");                       \
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");          \
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) atomicAdd((c).n_kernels, 1ull); \
   } while (0)
+
+// Launch with programmatic dependent launch when enabled (pdl: the handle's
+// setting; HCA_PDL=0 turns it off): the kernel's blocks may be scheduled
+// while the previous kernel drains, and wait at HCA_COUNT_KERNEL.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                            cudaStream_t s, Args&&... args) {
+  if (!pdl) {
+    kernel<<<grid, block, smem, s>>>(std::forward<Args>(args)...);
+    return cudaSuccess;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Operator selector: 0 = oxygen, 1 + d = drug d.
 __device__ __forceinline__ double op_coupling(const RepDesc& rd, int which) {

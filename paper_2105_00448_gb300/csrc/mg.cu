@@ -1266,23 +1266,25 @@ int grid_for(long long n) {
 template <typename T, bool PROLONG>
 void launch_post0(const Ctx& c, int which, const MGHost& H, const T* src, T om) {
   cudaStream_t s = c.stream;
+  const bool pdl = c.pdl != 0;
   if (c.persist && (H.ni == 1 || H.ni == 2 || H.ni == 4)) {
     const void* fn = H.ni == 1   ? (const void*)k_mg_post0<T, PROLONG, 1, true>
                      : H.ni == 2 ? (const void*)k_mg_post0<T, PROLONG, 2, true>
                                  : (const void*)k_mg_post0<T, PROLONG, 4, true>;
-    const int g = persist_grid(fn, c.threads, c.sm_count);
+    const dim3 g(persist_grid(fn, c.threads, c.sm_count));
     switch (H.ni) {
-      case 1: k_mg_post0<T, PROLONG, 1, true><<<g, c.threads, 0, s>>>(c, which, src, om); break;
-      case 2: k_mg_post0<T, PROLONG, 2, true><<<g, c.threads, 0, s>>>(c, which, src, om); break;
-      default: k_mg_post0<T, PROLONG, 4, true><<<g, c.threads, 0, s>>>(c, which, src, om); break;
+      case 1: launch_k(pdl, k_mg_post0<T, PROLONG, 1, true>, g, dim3(c.threads), 0, s, c, which, src, om); break;
+      case 2: launch_k(pdl, k_mg_post0<T, PROLONG, 2, true>, g, dim3(c.threads), 0, s, c, which, src, om); break;
+      default: launch_k(pdl, k_mg_post0<T, PROLONG, 4, true>, g, dim3(c.threads), 0, s, c, which, src, om); break;
     }
     return;
   }
+  const dim3 g(c.n_chunks);
   switch (H.ni) {
-    case 1: k_mg_post0<T, PROLONG, 1><<<c.n_chunks, c.threads, 0, s>>>(c, which, src, om); break;
-    case 2: k_mg_post0<T, PROLONG, 2><<<c.n_chunks, c.threads, 0, s>>>(c, which, src, om); break;
-    case 4: k_mg_post0<T, PROLONG, 4><<<c.n_chunks, c.threads, 0, s>>>(c, which, src, om); break;
-    default: k_mg_post0<T, PROLONG, 0><<<c.n_chunks, c.threads, 0, s>>>(c, which, src, om); break;
+    case 1: launch_k(pdl, k_mg_post0<T, PROLONG, 1>, g, dim3(c.threads), 0, s, c, which, src, om); break;
+    case 2: launch_k(pdl, k_mg_post0<T, PROLONG, 2>, g, dim3(c.threads), 0, s, c, which, src, om); break;
+    case 4: launch_k(pdl, k_mg_post0<T, PROLONG, 4>, g, dim3(c.threads), 0, s, c, which, src, om); break;
+    default: launch_k(pdl, k_mg_post0<T, PROLONG, 0>, g, dim3(c.threads), 0, s, c, which, src, om); break;
   }
 }
 
@@ -1318,8 +1320,9 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
   // register budgets (blocks per SM): 5 for the pre-sweeps (a few spilled
   // registers; measured 71.4 -> 67.6 us at 256^3), 4 for the restriction
   // (61.4 us; 65.5 us with 5)
-  if (all || part == 1) k_mg_pre0<T><<<nb, 128, 0, s>>>(c, which, z);
-  if (all || part == 2) k_mg_restrict0_rows<T><<<nb, 128, 0, s>>>(c, which, z);
+  const bool pdl = c.pdl != 0;
+  if (all || part == 1) launch_k(pdl, k_mg_pre0<T>, dim3(nb), dim3(128), 0, s, c, which, z);
+  if (all || part == 2) launch_k(pdl, k_mg_restrict0_rows<T>, dim3(nb), dim3(128), 0, s, c, which, (const T*)z);
   if (all || part == 3) {
     // levels 1 .. lo-1 by per-level kernels, lo .. nlev-1 in the cooperative
     // launch when there is one (lo = small: no level in it but the
@@ -1328,15 +1331,16 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
     const int lo = coop ? H.coop_from : H.small;
     for (int l = 1; l < lo; ++l) {
       if (H.rows_ok >> l & 1u) {
-        k_mg_smooth_rows<T, SM_PRE><<<grid_for(H.post_items[l]), kMgThreads, 0, s>>>(c, which, l);
+        launch_k(pdl, k_mg_smooth_rows<T, SM_PRE>, dim3(grid_for(H.post_items[l])), dim3(kMgThreads), 0, s, c, which, l);
         // 128 threads: ~12 vector loads per thread in flight
-        k_mg_restrict_rows<T><<<(int)std::min((H.restr_items[l] + 127) / 128, 152LL * 16), 128, 0, s>>>(c, which, l);
+        launch_k(pdl, k_mg_restrict_rows<T>, dim3((int)std::min((H.restr_items[l] + 127) / 128, 152LL * 16)), dim3(128),
+                 0, s, c, which, l);
       } else if (multi) {
-        k_mg_smooth<T, true, SM_PRE><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
-        k_mg_restrict<T, true><<<grid_for(H.ntot[l + 1]), kMgThreads, 0, s>>>(c, which, l);
+        launch_k(pdl, k_mg_smooth<T, true, SM_PRE>, dim3(grid_for(H.ntot[l])), dim3(kMgThreads), 0, s, c, which, l);
+        launch_k(pdl, k_mg_restrict<T, true>, dim3(grid_for(H.ntot[l + 1])), dim3(kMgThreads), 0, s, c, which, l);
       } else {
-        k_mg_smooth<T, false, SM_PRE><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
-        k_mg_restrict<T, false><<<grid_for(H.ntot[l + 1]), kMgThreads, 0, s>>>(c, which, l);
+        launch_k(pdl, k_mg_smooth<T, false, SM_PRE>, dim3(grid_for(H.ntot[l])), dim3(kMgThreads), 0, s, c, which, l);
+        launch_k(pdl, k_mg_restrict<T, false>, dim3(grid_for(H.ntot[l + 1])), dim3(kMgThreads), 0, s, c, which, l);
       }
     }
     if (coop) {
@@ -1347,20 +1351,20 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
       (void)cudaLaunchCooperativeKernel(coarse_fn<T>(H.coop_cfg), dim3(H.coop_blocks),
                                         dim3(coarse_threads(H.coop_cfg)), args, (size_t)H.small_smem, s);
     } else if (H.small_smem > 0 && H.small_smem_ok) {
-      k_mg_small_smem<T><<<c.n_reps, kSmallThreads, (size_t)H.small_smem, s>>>(c, which);
+      launch_k(pdl, k_mg_small_smem<T>, dim3(c.n_reps), dim3(kSmallThreads), (size_t)H.small_smem, s, c, which);
     } else {
-      k_mg_small<T><<<c.n_reps, kSmallThreads, 0, s>>>(c, which);
+      launch_k(pdl, k_mg_small<T>, dim3(c.n_reps), dim3(kSmallThreads), 0, s, c, which);
     }
     for (int l = lo - 1; l >= 1; --l) {
       if (H.rows_ok >> l & 1u) {
-        k_mg_smooth_rows<T, SM_POST><<<grid_for(H.post_items[l]), kMgThreads, 0, s>>>(c, which, l);
-        k_mg_smooth_rows<T, SM_LAST><<<grid_for(H.post_items[l]), kMgThreads, 0, s>>>(c, which, l);
+        launch_k(pdl, k_mg_smooth_rows<T, SM_POST>, dim3(grid_for(H.post_items[l])), dim3(kMgThreads), 0, s, c, which, l);
+        launch_k(pdl, k_mg_smooth_rows<T, SM_LAST>, dim3(grid_for(H.post_items[l])), dim3(kMgThreads), 0, s, c, which, l);
       } else if (multi) {
-        k_mg_smooth<T, true, SM_POST><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
-        k_mg_smooth<T, true, SM_LAST><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
+        launch_k(pdl, k_mg_smooth<T, true, SM_POST>, dim3(grid_for(H.ntot[l])), dim3(kMgThreads), 0, s, c, which, l);
+        launch_k(pdl, k_mg_smooth<T, true, SM_LAST>, dim3(grid_for(H.ntot[l])), dim3(kMgThreads), 0, s, c, which, l);
       } else {
-        k_mg_smooth<T, false, SM_POST><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
-        k_mg_smooth<T, false, SM_LAST><<<grid_for(H.ntot[l]), kMgThreads, 0, s>>>(c, which, l);
+        launch_k(pdl, k_mg_smooth<T, false, SM_POST>, dim3(grid_for(H.ntot[l])), dim3(kMgThreads), 0, s, c, which, l);
+        launch_k(pdl, k_mg_smooth<T, false, SM_LAST>, dim3(grid_for(H.ntot[l])), dim3(kMgThreads), 0, s, c, which, l);
       }
     }
   }

@@ -1029,9 +1029,11 @@ static void launch_dc_residual_v(const Ctx& c, int which, const float* x_hi, con
   if (c.persist) {
     // a 96-register cap: 16 -> 20 warps per SM (measured 176 -> 170 us per launch at 256^3)
     const int g = persist_grid((const void*)k_dc_residual<KIND, FIRST, MG, true, 96>, c.threads, c.sm_count);
-    k_dc_residual<KIND, FIRST, MG, true, 96><<<g, c.threads, 0, c.stream>>>(c, which, x_hi, x_lo, outer, inner);
+    launch_k(c.pdl != 0, k_dc_residual<KIND, FIRST, MG, true, 96>, dim3(g), dim3(c.threads), 0, c.stream, c, which, x_hi,
+             x_lo, outer, inner);
   } else {
-    k_dc_residual<KIND, FIRST, MG, false><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, x_hi, x_lo, outer, inner);
+    launch_k(c.pdl != 0, k_dc_residual<KIND, FIRST, MG, false>, dim3(c.n_chunks), dim3(c.threads), 0, c.stream, c, which,
+             x_hi, x_lo, outer, inner);
   }
 }
 
@@ -1093,19 +1095,21 @@ int persist_grid(const void* fn, int threads, int sm_count) {
 
 template <int REGS, int NI>
 static void launch_ab_f32(const Ctx& c, int which, bool a, void* xfield, CondArg cnd) {
+  const bool pdl = c.pdl != 0;
   if (NI > 0 && c.persist) {
     if (a) {
       const void* fn = (const void*)k_pass_a<float, REGS, NI, true>;
-      k_pass_a<float, REGS, NI, true><<<persist_grid(fn, c.threads, c.sm_count), c.threads, 0, c.stream>>>(c, which);
+      launch_k(pdl, k_pass_a<float, REGS, NI, true>, dim3(persist_grid(fn, c.threads, c.sm_count)), dim3(c.threads), 0,
+               c.stream, c, which);
     } else {
       const void* fn = (const void*)k_pass_b<float, REGS, NI, true>;
-      k_pass_b<float, REGS, NI, true>
-          <<<persist_grid(fn, c.threads, c.sm_count), c.threads, 0, c.stream>>>(c, which, xfield, cnd);
+      launch_k(pdl, k_pass_b<float, REGS, NI, true>, dim3(persist_grid(fn, c.threads, c.sm_count)), dim3(c.threads), 0,
+               c.stream, c, which, xfield, cnd);
     }
     return;
   }
-  if (a) k_pass_a<float, REGS, NI, false><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which);
-  else k_pass_b<float, REGS, NI, false><<<c.n_chunks, c.threads, 0, c.stream>>>(c, which, xfield, cnd);
+  if (a) launch_k(pdl, k_pass_a<float, REGS, NI, false>, dim3(c.n_chunks), dim3(c.threads), 0, c.stream, c, which);
+  else launch_k(pdl, k_pass_b<float, REGS, NI, false>, dim3(c.n_chunks), dim3(c.threads), 0, c.stream, c, which, xfield, cnd);
 }
 
 template <int REGS>
