@@ -42,7 +42,7 @@ template <typename T>
 struct View {
   int nx, ny, nz;
   long long off, sy, sz;
-  T *x, *t, *rhs, *d, *w;   // w = omega / d (0 where d = 0): the sweeps divide nowhere
+  T *x, *t, *rhs, *d, *w;   // w = 1 / d (0 where d = 0): the sweeps divide nowhere
   T c;
   __device__ __forceinline__ long long n() const { return (long long)nx * ny * nz; }
   __device__ __forceinline__ long long at(int X, int Y, int Z) const { return off + X + sy * Y + sz * Z; }
@@ -911,7 +911,7 @@ __device__ __forceinline__ void cp_async(void* sdst, const void* gsrc) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Start copying the diagonals and omega/d of replicate r's single-block
+// Start copying the diagonals and 1/d of replicate r's single-block
 // levels into shared memory (they do not change during a V-cycle); the copies
 // complete in the background until cp_async_wait_all.
 template <typename T>
@@ -930,7 +930,7 @@ __device__ void small_prefetch(const Ctx& c, int which, int r, int tid, int nthr
 // The whole sub-cycle of replicate r's levels small .. nlev-1 by one block
 // (tid, nthr: this thread and the block's threads; block barriers between
 // sweeps).  With sm, the cycle runs in shared memory (the same arithmetic in
-// the same order as in global memory): the diagonals and omega/d of those
+// the same order as in global memory): the diagonals and 1/d of those
 // levels are copied in (already under way when `prefetched`), then the
 // right-hand side of the first level; afterwards the first level's iterate,
 // the only array later kernels read, is written back.
