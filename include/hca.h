@@ -105,8 +105,11 @@ extern "C" {
  * per iteration (the lattice counterpart of the paper's algebraic-multigrid
  * preconditioned CG, Section 2.4): 2x2x2 agglomeration, coupling doubled per
  * level, reaction summed over the children, sum restriction, copy
- * prolongation, one weighted-Jacobi sweep (weight 0.8) before and after the
- * coarse correction, 16 sweeps on the coarsest level (<= 512 sites). */
+ * prolongation, two Jacobi sweeps before the coarse correction and two after
+ * it with the Chebyshev weights 1 / (1.25 +- 0.75 cos(pi/4)) (the degree-2
+ * Chebyshev polynomial on [0.5, 2] of the spectrum of D^-1 A; before: the
+ * smaller weight first, after: the larger first), 16 sweeps of weight 0.8 on
+ * the coarsest level (<= 512 sites). */
 #define HCA_PC_JACOBI 0
 #define HCA_PC_MG 1
 

@@ -9,19 +9,22 @@
 // volume); reaction a_{l+1} = sum of the children's a_l; diagonal
 // d_l = c_l n_l + a_l with n_l the in-box neighbour count (Neumann).
 // Restriction sums over the children, prolongation copies to them, the
-// smoother is weighted Jacobi (one sweep before and one after the coarse
-// correction, MG_NU_COARSE sweeps on the coarsest level), so M is symmetric.
+// smoother is Jacobi with Chebyshev weights (two sweeps before the coarse
+// correction, MG_W1 then MG_W2, and two after it, MG_W2 then MG_W1;
+// MG_NU_COARSE sweeps of weight MG_OMEGA_COARSE on the coarsest level), so M
+// is symmetric.
 //
-// Level 0 is the solver's padded field layout: rhs = r, diagonal = d, and
-// mg_t0 the iterate when the lattice is the coarsest level, else the
-// pre-smoothed iterate v that the restriction kernel leaves for the
-// post-smoothing kernel; coarser levels are dense arrays, the replicates of a batch
+// Level 0 is the solver's padded field layout: rhs = r, diagonal = d, 1/d in
+// mg_w; z holds the pre-smoothed iterate v between the pre-sweep kernel and
+// the restriction, mg_t0 the part v' of the first post-sweep that the
+// restriction leaves for the post-sweep kernels (or the iterate when the
+// lattice is the coarsest level); coarser levels are dense arrays, the replicates of a batch
 // concatenated per level (each replicate has its own hierarchy; a per-level
 // prefix table maps a flattened site index to its replicate).  Levels of at
 // most MG_SMALL_SITES sites run inside one block per replicate (block
-// barriers between sweeps).  The last kernel, the post-smoothing sweep on
-// level 0, also forms rho = r.z with the fixed-order reductions of the CG
-// passes and sets beta, per replicate.
+// barriers between sweeps).  The last kernel, the last post-sweep on level 0,
+// also forms rho = r.z with the fixed-order reductions of the CG passes and
+// sets beta, per replicate.
 
 #include <algorithm>
 #include <cstdlib>
