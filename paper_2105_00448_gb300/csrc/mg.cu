@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_scale0(Ctx c, int which) {
 // The lattice as the coarsest level (single replicate): t0 = (omega / d) r
 template <typename T>
 __global__ void __launch_bounds__(kMgThreads) k_mg_first0(Ctx c, int which) {
-  HCA_COUNT_KERNEL(c);
+  HCA_VC_ENTRY(c);
   const View<T> V = view<T>(c, which, 0, 0);
   for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < V.n(); s += (long long)gridDim.x * blockDim.x)
     sweep_first_at<T>(V, V.x, s, MG_OMEGA_COARSE);
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_first0(Ctx c, int which) {
 
 template <typename T>
 __global__ void __launch_bounds__(kMgThreads) k_mg_sweep0(Ctx c, int which, const T* src, T* dst) {
-  HCA_COUNT_KERNEL(c);
+  HCA_VC_ENTRY(c);
   const View<T> V = view<T>(c, which, 0, 0);
   for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < V.n(); s += (long long)gridDim.x * blockDim.x)
     sweep_at<T>(V, src, dst, s, MG_OMEGA_COARSE);
@@ -451,7 +451,7 @@ __device__ __forceinline__ void restrict_sites(const Ctx& c, int which, int l, l
 
 template <typename T, bool MULTI>
 __global__ void __launch_bounds__(kMgThreads) k_mg_restrict(Ctx c, int which, int l) {
-  HCA_COUNT_KERNEL(c);
+  HCA_VC_ENTRY(c);
   restrict_sites<T, MULTI>(c, which, l, grid_t0(), grid_st());
 }
 
@@ -474,7 +474,7 @@ __device__ __forceinline__ void smooth_sites(const Ctx& c, int which, int l, lon
 
 template <typename T, bool MULTI, int MODE>
 __global__ void __launch_bounds__(kMgThreads) k_mg_smooth(Ctx c, int which, int l) {
-  HCA_COUNT_KERNEL(c);
+  HCA_VC_ENTRY(c);
   smooth_sites<T, MULTI, MODE>(c, which, l, grid_t0(), grid_st());
 }
 
@@ -596,7 +596,7 @@ __device__ __forceinline__ void smooth_rows(const Ctx& c, int which, int l, long
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kMgThreads) k_mg_smooth_rows(Ctx c, int which, int l) {
-  HCA_COUNT_KERNEL(c);
+  HCA_VC_ENTRY(c);
   smooth_rows<T, MODE>(c, which, l, grid_t0(), grid_st());
 }
 
@@ -688,7 +688,7 @@ __device__ __forceinline__ void restrict_rows(const Ctx& c, int which, int l, lo
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_mg_restrict_rows(Ctx c, int which, int l) {
-  HCA_COUNT_KERNEL(c);
+  HCA_VC_ENTRY(c);
   restrict_rows<T>(c, which, l, grid_t0(), grid_st());
 }
 
@@ -734,7 +734,7 @@ __device__ __forceinline__ Item0 item0(const Ctx& c, long long q) {
 // formed.
 template <typename T>
 __global__ void __launch_bounds__(128, 5) k_mg_pre0(Ctx c, int which, T* __restrict__ dst) {
-  HCA_COUNT_KERNEL(c);
+  HCA_VC_ENTRY(c);
   const T* __restrict__ rr = (const T*)c.r;
   const T* __restrict__ ww = (const T*)c.mg_w;
   const long long total = c.mg_rowstart[c.n_reps];
@@ -815,7 +815,7 @@ __global__ void __launch_bounds__(128, 5) k_mg_pre0(Ctx c, int which, T* __restr
 // formed: 16.5 B per site.  Children in the order of restrict_residual_at.
 template <typename T>
 __global__ void __launch_bounds__(128, 4) k_mg_restrict0_rows(Ctx c, int which, const T* __restrict__ src) {
-  HCA_COUNT_KERNEL(c);
+  HCA_VC_ENTRY(c);
   T* __restrict__ vo = (T*)c.mg_t0;
   const T* __restrict__ rr = (const T*)c.r;
   const T* __restrict__ dd = (const T*)c.d;
@@ -1028,7 +1028,7 @@ __device__ void small_cycle(const Ctx& c, int which, int r, int tid, int nthr, T
 // global memory.
 template <typename T>
 __global__ void __launch_bounds__(kSmallThreads) k_mg_small(Ctx c, int which) {
-  HCA_COUNT_KERNEL(c);
+  HCA_VC_ENTRY(c);
   small_cycle<T, false>(c, which, blockIdx.x, threadIdx.x, blockDim.x, nullptr, false);
 }
 
@@ -1036,7 +1036,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_mg_small(Ctx c, int which) {
 // shared memory (the same arithmetic in the same order).
 template <typename T>
 __global__ void __launch_bounds__(kSmallThreads) k_mg_small_smem(Ctx c, int which) {
-  HCA_COUNT_KERNEL(c);
+  HCA_VC_ENTRY(c);
   extern __shared__ __align__(16) unsigned char small_smem[];
   small_cycle<T, true>(c, which, blockIdx.x, threadIdx.x, blockDim.x, (T*)small_smem, false);
 }
@@ -1054,7 +1054,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_mg_small_smem(Ctx c, int whic
 template <typename T, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_mg_coarse(Ctx c, int which, int lo, int small, unsigned rows_ok,
                                                          int use_smem) {
-  HCA_COUNT_KERNEL(c);
+  HCA_VC_ENTRY(c);
   extern __shared__ __align__(16) unsigned char mg_smem[];
   T* sm = (T*)mg_smem;
   const long long t0 = grid_t0(), st = grid_st();
@@ -1112,7 +1112,7 @@ __global__ void __launch_bounds__(NT, MINB) k_mg_coarse(Ctx c, int which, int lo
 // solve).
 template <typename T, bool PROLONG, int NI, bool PERSIST = false>
 __global__ void __maxnreg__(64) k_mg_post0(Ctx c, int which, const T* __restrict__ src, T om) {
-  HCA_COUNT_KERNEL(c);
+  HCA_VC_ENTRY(c);
   const int2 ch = PERSIST ? make_int2(0, 0) : c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
   const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
@@ -1298,7 +1298,11 @@ void launch_post0(const Ctx& c, int which, const MGHost& H, const T* src, T om) 
 // post-sweep with r.z.  A lattice that is the coarsest level runs its sweeps
 // as part 3.
 template <typename T>
-void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
+void vcycle_t(const Ctx& c0, int which, const MGHost& H, int part, bool scale) {
+  // a V-cycle after pass B (not a solve's first one, which follows its
+  // residual): its kernels skip when pass B ended every replicate's loop
+  Ctx c = c0;
+  c.skip_idle = scale ? 0 : 1;
   cudaStream_t s = c.stream;
   T* t0 = (T*)c.mg_t0;
   T* z = (T*)c.z;
