@@ -622,18 +622,17 @@ int cap_solve(hca_handle* h, int which, cudaGraph_t G) {
     const hca::CondArg cnd{H, 1};
     c.stream = S;
     hca::launch_setup(c, which, h->fp64, cnd);
-    if (h->mg) {
-      mg_setup(h, which);
-      vcycle(h, which, true);
-    }
+    if (h->mg) mg_setup(h, which);
     HCA_TRY(cudaGetLastError());
+    // the V-cycle opens the loop's body, so none runs after the pass B that
+    // ends the loop (the set-up leaves r unscaled: no r scaling either)
     cudaGraph_t body;
     if ((rc = add_while(S, H, &body))) return rc;
     HCA_TRY(cudaStreamBeginCaptureToGraph(S2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     c.stream = S2;
+    if (h->mg) vcycle(h, which, false);
     pass_a(h, which);
     pass_b(h, which, x, cnd);
-    if (h->mg) vcycle(h, which, false);
     HCA_TRY(cudaGetLastError());
     HCA_TRY(cudaStreamEndCapture(S2, &body));
     c.stream = S;
@@ -649,26 +648,31 @@ int cap_solve(hca_handle* h, int which, cudaGraph_t G) {
   const hca::CondArg co{Ho, 1}, ci{Hi, 1};
   c.stream = S;
   hca::launch_dc_residual(c, which, xh, xl, true, co, ci);
-  if (h->mg) {
-    mg_setup(h, which, true);
-    vcycle(h, which, true);
-  }
+  if (h->mg) mg_setup(h, which, true);
   HCA_TRY(cudaGetLastError());
+  // Each loop's body opens with its V-cycle, so none runs after the residual
+  // sweep that ends the outer loop or the pass B that ends an inner loop: the
+  // outer body is the first inner iteration (a residual sweep that continues
+  // the outer loop starts an inner solve) and the inner loop the others.
   cudaGraph_t bo, bi;
   if ((rc = add_while(S, Ho, &bo))) return rc;
   HCA_TRY(cudaStreamBeginCaptureToGraph(S2, bo, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  c.stream = S2;
+  if (h->mg) vcycle(h, which, true);
+  pass_a(h, which);
+  pass_b(h, which, c.dx, ci);
+  HCA_TRY(cudaGetLastError());
   if ((rc = add_while(S2, Hi, &bi))) return rc;
   HCA_TRY(cudaStreamBeginCaptureToGraph(S3, bi, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   c.stream = S3;
+  if (h->mg) vcycle(h, which, false);
   pass_a(h, which);
   pass_b(h, which, c.dx, ci);
-  if (h->mg) vcycle(h, which, false);
   HCA_TRY(cudaGetLastError());
   HCA_TRY(cudaStreamEndCapture(S3, &bi));
   c.stream = S2;
   hca::launch_dc_update(c, xh, xl);
   hca::launch_dc_residual(c, which, xh, xl, false, co, ci);
-  if (h->mg) vcycle(h, which, true);
   HCA_TRY(cudaGetLastError());
   HCA_TRY(cudaStreamEndCapture(S2, &bo));
   c.stream = S;
@@ -1452,6 +1456,9 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
       c.persist = (!(pe && pe[0] == '0') && n == 1 && !h->fp64 && h->reps_h[0].lpr == 32 && c.pass_ni > 0) ? 1 : 0;
       const char* pd = std::getenv("HCA_PDL");
       c.pdl = (pd && pd[0] == '0') ? 0 : 1;
+      // a V-cycle whose z no solve reads (after the pass B, set-up or residual
+      // sweep that ended every replicate's iteration) returns at once
+      c.skip_idle = 1;
       // the 27 colour sweeps of the CA in one cooperative launch (HCA_CA_COOP=0: one launch per colour)
       h->ca_coop = hca::ca_coop_blocks(h->fp64, c.sm_count);
     }
@@ -1807,7 +1814,9 @@ int hca_apply_preconditioner(hca_handle* h, int32_t rep, int32_t which, const vo
   HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.nlev, mg_setup(h, which));
   int rc = copy_field(h, rep, c.r, es, const_cast<void*>(r), false, 0);
   if (rc) return rc;
+  c.skip_idle = 0;   // z is wanted whether or not the set-up found the solve converged
   HCA_LAUNCH(h, HCA_KCLASS_MG, hca::vcycle_launches(h->mgh, true), vcycle(h, which, true));
+  c.skip_idle = 1;
   rc = copy_field(h, rep, c.z, es, z, true, 0);
   if (rc) return rc;
   HCA_TRY(cudaStreamSynchronize(c.stream));

@@ -353,8 +353,8 @@ struct Ctx {
   int mg;           // 0: Jacobi (z = r / d), 1: V-cycle (z = M r)
   int persist;         // 1: the CG passes and the lattice post-sweep run in persistent row form (one FP32 lattice)
   int pdl;             // 1: the CG and V-cycle kernels launch with programmatic dependent launch
-  int skip_idle;       // 1: a V-cycle inside a CG loop (after pass B): its kernels return at once
-                       // when pass B left no replicate active (its z would never be used)
+  int skip_idle;       // 1 (solves): a V-cycle's kernels return at once when the set-up, residual
+                       // sweep or pass B before it left no replicate iterating (nothing reads its z)
   void* r;
   void* mg_t0;
   void* mg_w;         // 1 / d on the lattice (0 where d = 0)
@@ -657,9 +657,10 @@ __device__ __forceinline__ void grid_exit(PassSync* sy, int nbar) {
   } while (0)
 
 // Entry of a V-cycle kernel: HCA_COUNT_KERNEL, then return at once when the
-// V-cycle follows a pass B that left no replicate iterating (the loop ends;
-// nothing reads this V-cycle's z).  Every block reads the same count (no
-// kernel writes it between pass B and the next pass B or residual sweep).
+// set-up, residual sweep or pass B before the V-cycle left no replicate
+// iterating (the solve or its inner loop ends; nothing reads this V-cycle's
+// z).  Every block reads the same count: only those kernels write it, and
+// none of them runs between the V-cycle's first and last kernel.
 #define HCA_VC_ENTRY(c)                                                          \
   HCA_COUNT_KERNEL(c);                                                           \
   if ((c).skip_idle && *(volatile const int*)&(c).sync->active_count == 0) return

@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_diag(Ctx c, int which, int l)
 // replicates past that return at once.
 template <typename T>
 __global__ void __launch_bounds__(kMgThreads) k_mg_scale0(Ctx c, int which) {
-  HCA_COUNT_KERNEL(c);
+  HCA_VC_ENTRY(c);
   RepCursor<T> k;
   bool skip = true;
   T sc = T(1);
@@ -1298,11 +1298,7 @@ void launch_post0(const Ctx& c, int which, const MGHost& H, const T* src, T om) 
 // post-sweep with r.z.  A lattice that is the coarsest level runs its sweeps
 // as part 3.
 template <typename T>
-void vcycle_t(const Ctx& c0, int which, const MGHost& H, int part, bool scale) {
-  // a V-cycle after pass B (not a solve's first one, which follows its
-  // residual): its kernels skip when pass B ended every replicate's loop
-  Ctx c = c0;
-  c.skip_idle = scale ? 0 : 1;
+void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
   cudaStream_t s = c.stream;
   T* t0 = (T*)c.mg_t0;
   T* z = (T*)c.z;
