@@ -265,7 +265,9 @@ def cpu_baseline_record(steps: int):
 def step_roofline(prof, steps: int, sites: int, ms_per_step: float, level_fraction: float):
     """Step-level HBM roofline: the method's algorithmic bytes of one step
     (counts of CG iterations, defect-correction sweeps and V-cycles from the
-    profiled steps) over the measured step time."""
+    profiled steps, whose host loops check for convergence before every
+    iteration and so launch only V-cycles that run) over the measured step
+    time."""
     peak, peak_kind = measured_peak_hbm()
     n_it = prof["pass_a"]["launches"] / steps
     n_dc = prof["residual"]["launches"] / steps

@@ -39,6 +39,7 @@ void launch_vcycle(const Ctx& c, int which, bool fp64, const MGHost& H, int part
 int vcycle_launches(const MGHost& H, bool scale);
 int vcycle_part_launches(const MGHost& H, int part, bool scale);
 void mg_coop_config(MGHost& H, bool fp64, int sm_count, long long smem_bytes);
+void mg_zmarch_config(MGHost& H, const RepDesc& rd, int sm_count, const float* r, const float* w);
 }  // namespace hca
 
 using hca::Ctx;
@@ -464,12 +465,14 @@ void mg_setup(hca_handle* h, int which, bool w_done = false) {
   hca::launch_mg_setup(h->ctx, which, h->fp64, h->mgh, w_done);
 }
 
-// CG iterations (pass A, pass B) on operator `which` for every replicate whose
-// solve is active, updating x, until none is active or maxit is reached.  The
-// first convergence check comes after about as many iterations as the same
-// solve needed last time (`predict`), later ones every 4 iterations; with
-// the profiler on, after every iteration (so no launch runs empty).
-int pcg_iterate(hca_handle* h, int which, void* x, int predict) {
+// CG iterations (V-cycle, pass A, pass B) on operator `which` for every
+// replicate whose solve is active, updating x, until none is active or maxit
+// is reached.  The first convergence check comes after about as many
+// iterations as the same solve needed last time (`predict`), later ones every
+// 4 iterations; with the profiler on, before every iteration (so no launch
+// runs empty).  scale_first: the first V-cycle may scale r (it follows a
+// defect-correction residual sweep).
+int pcg_iterate(hca_handle* h, int which, void* x, int predict, bool scale_first) {
   Ctx& c = h->ctx;
   int done = 0;
   int chunk = h->prof.on ? 1 : std::max(1, predict - 2);
@@ -480,12 +483,12 @@ int pcg_iterate(hca_handle* h, int which, void* x, int predict) {
     if (h->h_pinned[0] == 0 || done >= h->maxit_all) break;
     const int n = std::min(chunk, h->maxit_all - done);
     for (int k = 0; k < n; ++k) {
-      HCA_LAUNCH(h, HCA_KCLASS_PASS_A, 1, pass_a(h, which));
-      HCA_LAUNCH(h, HCA_KCLASS_PASS_B, 1, pass_b(h, which, x, kNoCond));
       if (h->mg) {
-        const int rc = vcycle_host(h, which, false);
+        const int rc = vcycle_host(h, which, scale_first && done + k == 0);
         if (rc) return rc;
       }
+      HCA_LAUNCH(h, HCA_KCLASS_PASS_A, 1, pass_a(h, which));
+      HCA_LAUNCH(h, HCA_KCLASS_PASS_B, 1, pass_b(h, which, x, kNoCond));
     }
     done += n;
     chunk = h->prof.on ? 1 : 4;
@@ -501,12 +504,8 @@ int solve_plain(hca_handle* h, int which) {
   Ctx& c = h->ctx;
   void* x = which == 0 ? c.K : c.G[which - 1];
   HCA_LAUNCH(h, HCA_KCLASS_SETUP, 1, hca::launch_setup(c, which, h->fp64, kNoCond));
-  if (h->mg) {
-    HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.nlev, mg_setup(h, which));
-    const int rv = vcycle_host(h, which, true);
-    if (rv) return rv;
-  }
-  int rc = pcg_iterate(h, which, x, h->prev_inner[which][0]);
+  if (h->mg) HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.nlev, mg_setup(h, which));
+  int rc = pcg_iterate(h, which, x, h->prev_inner[which][0], false);
   if (rc) return rc;
   h->prev_inner[which][0] = h->last_iters;
   HCA_LAUNCH(h, HCA_KCLASS_RESIDUAL, 2, hca::launch_true_residual(c, which, x, h->fp64));
@@ -526,11 +525,7 @@ int solve_dc(hca_handle* h, int which) {
   for (int outer = 0;; ++outer) {
     HCA_LAUNCH(h, HCA_KCLASS_RESIDUAL, 1,
                hca::launch_dc_residual(c, which, xh, xl, outer == 0, kNoCond, kNoCond));
-    if (h->mg) {
-      if (outer == 0) HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.nlev - 1, mg_setup(h, which, true));
-      const int rv = vcycle_host(h, which, true);
-      if (rv) return rv;
-    }
+    if (h->mg && outer == 0) HCA_LAUNCH(h, HCA_KCLASS_MG, h->mgh.nlev - 1, mg_setup(h, which, true));
     HCA_TRY(cudaMemcpyAsync(h->h_pinned, &c.sync->active_count, 2 * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     HCA_TRY(cudaStreamSynchronize(c.stream));
     if (h->h_pinned[1]) return sync_error_status(h->h_pinned[1]);
@@ -540,7 +535,7 @@ int solve_dc(hca_handle* h, int which) {
       break;
     }
     const int slot = std::min(outer, 15);
-    int rc = pcg_iterate(h, which, c.dx, h->prev_inner[which][slot]);
+    int rc = pcg_iterate(h, which, c.dx, h->prev_inner[which][slot], true);
     if (rc) return rc;
     h->prev_inner[which][slot] = h->last_iters;
     HCA_LAUNCH(h, HCA_KCLASS_OTHER, 1, hca::launch_dc_update(c, xh, xl));
@@ -555,8 +550,10 @@ int solve(hca_handle* h, int which) {
 
 // ------------------------------------------------------------ step graph --
 // The whole step (or a subset of its stages) captured once into a CUDA graph.
-// Each CG loop is a WHILE conditional node whose body is [pass A, pass B];
-// the last block of the set-up / pass B / defect-correction residual kernels
+// Each CG loop is a WHILE conditional node whose body is [V-cycle, pass A,
+// pass B] ([pass A, pass B] with the Jacobi preconditioner, whose z comes
+// from pass B); the last block of the set-up / pass B / defect-correction
+// residual kernels
 // sets the loop condition on the device, so a step runs without any host
 // round trip.  Loop exit is guaranteed by maxit / max_outer, with a device
 // guard counter as a second stop.
@@ -1292,6 +1289,8 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
       ALLOC(c.r, fbytes);
       ALLOC(c.mg_t0, fbytes);
       ALLOC(c.mg_w, fbytes);
+      if (n == 1 && !h->fp64)
+        hca::mg_zmarch_config(H, h->reps_h[0], c.sm_count, (const float*)c.r, (const float*)c.mg_w);
       hca::MGLevel* lv_d;
       long long* start_d;
       long long* rowstart_d;

@@ -18,6 +18,7 @@
 
 #include <utility>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -326,6 +327,15 @@ struct MGHost {
   unsigned rows_ok = 0;          // bit l: every replicate's level-l rows are whole 4-site groups
   long long post_items[MG_MAXLEV] = {};   // row-kernel items per level over the replicates
   long long restr_items[MG_MAXLEV] = {};
+  // the lattice's pre-sweeps in plane-marching form (one FP32 lattice; 0 =
+  // row form): slabs along z, planes per slab, tiles along x and y
+  int zm_slabs = 0;
+  int zm_zs = 0;
+  int zm_tx = 0, zm_ty = 0;
+  int zm_mode = 0;               // 1: planes prefetched into registers, 2: TMA-staged planes
+  // TMA tensor maps of r and 1/d over the lattice (x extent nx: the copy
+  // engine fills sites outside the lattice with zeros)
+  CUtensorMap zm_map_r, zm_map_w;
 };
 
 struct Ctx {

@@ -28,9 +28,11 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <type_traits>
 
 #include "hca_internal.cuh"
 #include "row_ops.cuh"
+#include "tc.cuh"
 
 namespace hca {
 
@@ -725,10 +727,25 @@ __device__ __forceinline__ Item0 item0(const Ctx& c, long long q) {
   return I;
 }
 
-// Both pre-smoothing sweeps on the lattice in row-vector form:
-// v = u + (W2 / d)(r - A u) with u = (W1 / d) r, stored into dst (the z
-// buffer, free until the last post-sweep).  The diagonal term d u is taken
-// as W1 r (equal up to the rounding of 1/d), so d is not read: r and 1/d,
+// The two pre-smoothing sweeps from zero at one site, shared by the row and
+// plane-marching forms (every product rounded on its own, so both give the
+// same bits): u = (W1 / d) r at every site; with nb the sum of the six
+// neighbours' u (order x-, x+, y-, y+, z-, z+), v = u + (W2 / d)(r - A u)
+// where the diagonal term d u is taken as W1 r (equal up to the rounding of
+// 1/d), so d is not read.
+template <typename T>
+__device__ __forceinline__ T pre0_u(T r, T w) {
+  return mul_rn(wt(MG_W1, w), r);
+}
+template <typename T>
+__device__ __forceinline__ T pre0_site(T r, T w, T u, T cpl, T nb) {
+  const T du = w != T(0) ? mul_rn((T)MG_W1, r) : T(0);
+  const T res = r - (du - mul_rn(cpl, nb));
+  return fma(wt(MG_W2, w), res, u);
+}
+
+// Both pre-smoothing sweeps on the lattice in row-vector form (pre0_site),
+// stored into dst (the z buffer, free until the last post-sweep): r and 1/d,
 // 8 B per site.  Every load of an item (its four own rows, their eight outer
 // neighbour rows, the x neighbours at the group's ends) is issued before u is
 // formed.
@@ -778,7 +795,7 @@ __global__ void __launch_bounds__(128, 5) k_mg_pre0(Ctx c, int which, T* __restr
 #pragma unroll
       for (int t = 0; t < 8; ++t)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) U[t].a[e] = (x0 + e < rd.nx) ? wt(MG_W1, WV[t].a[e]) * RV[t].a[e] : T(0);
+        for (int e = 0; e < 4; ++e) U[t].a[e] = (x0 + e < rd.nx) ? pre0_u(RV[t].a[e], WV[t].a[e]) : T(0);
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
         if (!ok[a]) continue;
@@ -786,7 +803,7 @@ __global__ void __launch_bounds__(128, 5) k_mg_pre0(Ctx c, int which, T* __restr
         const V4<T>& ypr = a ? U[3] : U[1];                 // row y + 1
         const V4<T>& zmr = b ? U[4 + a] : U[6 + a];         // row z - 1
         const V4<T>& zpr = b ? U[6 + a] : U[4 + a];         // row z + 1
-        const T ul = wt(MG_W1, lw[a]) * lr[a], ur = wt(MG_W1, rw[a]) * rrr[a];
+        const T ul = pre0_u(lr[a], lw[a]), ur = pre0_u(rrr[a], rw[a]);
         V4<T> VO = zero4<T>();   // zero on padding
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -795,14 +812,296 @@ __global__ void __launch_bounds__(128, 5) k_mg_pre0(Ctx c, int which, T* __restr
           const T left = e == 0 ? ul : U[a].a[e - 1];
           const T right = e == 3 ? ur : U[a].a[e + 1];
           const T nb = (x > 0 ? left : T(0)) + (x < rd.nx - 1 ? right : T(0)) + ymr.a[e] + ypr.a[e] + zmr.a[e] + zpr.a[e];
-          const T du = WV[a].a[e] != T(0) ? (T)MG_W1 * RV[a].a[e] : T(0);
-          const T res = RV[a].a[e] - (du - cpl * nb);
-          VO.a[e] = fma(wt(MG_W2, WV[a].a[e]), res, U[a].a[e]);
+          VO.a[e] = pre0_site(RV[a].a[e], WV[a].a[e], U[a].a[e], cpl, nb);
         }
         st4(dst + eb + off[a], VO);
       }
     }
   }
+}
+
+// Plane-marching form of k_mg_pre0 for one FP32 lattice.  A block owns a
+// tile of kZmG four-site groups by kZmY rows and a slab of planes, and walks
+// up z: each thread keeps its group's u on planes z - 1, z and z + 1 in
+// registers, and u on plane z of the tile with a one-site halo goes to
+// shared memory (two buffers, one barrier per plane) for the x and y
+// neighbours.  So r and 1/d are read once per site (the halo's from L2), and
+// the loads of plane z + 2 are in flight during plane z's arithmetic.
+// Threads 0 .. 2 kZmG - 1 also load the two halo rows (groups), the next
+// 2 kZmY threads the halo sites at the tile's x ends.  Per site the
+// arithmetic is k_mg_pre0's (pre0_site, same neighbour order).
+constexpr int kZmG = 8, kZmY = 16, kZmThreads = kZmG * kZmY;
+constexpr int kZmPitch = 4 * kZmG + 8;   // tile row in shared memory: left halo at 3, groups from 4, right halo at 4 + 4 kZmG
+
+__global__ void __launch_bounds__(kZmThreads, 7) k_mg_pre0_z(Ctx c, int which, float* __restrict__ dst, int zs) {
+  HCA_VC_ENTRY(c);
+  __shared__ __align__(16) float ub[2][kZmY + 2][kZmPitch];
+  const RepDesc& rd = c.reps[0];
+  const float* __restrict__ rr = (const float*)c.r;
+  const float* __restrict__ ww = (const float*)c.mg_w;
+  const float cpl = op_coupling_t<float>(rd, which);
+  const int t = threadIdx.x, g = t % kZmG, ty = t / kZmG;
+  const int G = blockIdx.x * kZmG + g, y = blockIdx.y * kZmY + ty;
+  const int x0 = 4 * G;
+  const bool own = G < rd.gpr && y < rd.ny;
+  const long long sy = rd.nxp, sz = (long long)rd.nxp * rd.ny;
+  const long long eo = rd.off + x0 + sy * y;
+  // halo role: 1 a group of halo row y0 - 1 or y0 + kZmY, 2 a site at x0 - 1 or x0 + 4 kZmG
+  int hrole = 0, hrow = 0, hcol = 0, hx = 0;
+  bool hok = false;
+  long long he = 0;
+  if (t < 2 * kZmG) {
+    hrole = 1;
+    const int hy = blockIdx.y * kZmY + (t < kZmG ? -1 : kZmY), hg = blockIdx.x * kZmG + t % kZmG;
+    hok = hy >= 0 && hy < rd.ny && hg < rd.gpr;
+    he = rd.off + 4LL * hg + sy * hy;
+    hx = 4 * hg;
+    hrow = t < kZmG ? 0 : kZmY + 1;
+    hcol = 4 + 4 * (t % kZmG);
+  } else if (t < 2 * kZmG + 2 * kZmY) {
+    hrole = 2;
+    const int k = t - 2 * kZmG, side = k / kZmY, row = k % kZmY;
+    hx = side ? 4 * kZmG * (blockIdx.x + 1) : 4 * kZmG * blockIdx.x - 1;
+    const int hy = blockIdx.y * kZmY + row;
+    hok = hx >= 0 && hx < rd.nx && hy < rd.ny;
+    he = rd.off + hx + sy * hy;
+    hrow = row + 1;
+    hcol = side ? 4 + 4 * kZmG : 3;
+  }
+  const int zb = blockIdx.z * zs, ze = min(rd.nz, zb + zs);
+  auto ld_own = [&](int z, V4<float>& R, V4<float>& W) {
+    const bool ok = own && z >= 0 && z < rd.nz;
+    R = ld4_if(rr + eo + sz * z, ok);
+    W = ld4_if(ww + eo + sz * z, ok);
+  };
+  auto ld_halo = [&](int z, V4<float>& R, V4<float>& W) {
+    const bool ok = hok && z >= 0 && z < rd.nz;
+    if (hrole == 1) {
+      R = ld4_if(rr + he + sz * z, ok);
+      W = ld4_if(ww + he + sz * z, ok);
+    } else {
+      R.a[0] = (hrole == 2 && ok) ? rr[he + sz * z] : 0.f;
+      W.a[0] = (hrole == 2 && ok) ? ww[he + sz * z] : 0.f;
+    }
+  };
+  auto u_of = [&](const V4<float>& R, const V4<float>& W, int xb) {
+    V4<float> U;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) U.a[e] = (xb + e < rd.nx) ? pre0_u(R.a[e], W.a[e]) : 0.f;
+    return U;
+  };
+  // u of plane z (own group and halo role) into buffer z & 1
+  auto put = [&](int z, const V4<float>& U, const V4<float>& HR, const V4<float>& HW) {
+    float* row = &ub[z & 1][ty + 1][4 + 4 * g];
+    *reinterpret_cast<float4*>(row) = make_float4(U.a[0], U.a[1], U.a[2], U.a[3]);
+    if (hrole == 1) {
+      const V4<float> H = u_of(HR, HW, hx);
+      *reinterpret_cast<float4*>(&ub[z & 1][hrow][hcol]) = make_float4(H.a[0], H.a[1], H.a[2], H.a[3]);
+    } else if (hrole == 2) {
+      ub[z & 1][hrow][hcol] = pre0_u(HR.a[0], HW.a[0]);
+    }
+  };
+  V4<float> Rc, Wc, Rn, Wn, HRn, HWn, up, uc;
+  {
+    V4<float> Rp, Wp, HRc, HWc;
+    ld_own(zb - 1, Rp, Wp);
+    ld_own(zb, Rc, Wc);
+    ld_halo(zb, HRc, HWc);
+    ld_own(zb + 1, Rn, Wn);
+    ld_halo(zb + 1 < ze ? zb + 1 : -1, HRn, HWn);
+    up = u_of(Rp, Wp, x0);
+    uc = u_of(Rc, Wc, x0);
+    put(zb, uc, HRc, HWc);
+  }
+  __syncthreads();
+  for (int z = zb; z < ze; ++z) {
+    V4<float> Rnn, Wnn, HRnn, HWnn;
+    ld_own(z + 2 <= ze ? z + 2 : -1, Rnn, Wnn);
+    ld_halo(z + 2 < ze ? z + 2 : -1, HRnn, HWnn);
+    const V4<float> un = u_of(Rn, Wn, x0);   // plane z + 1 (zero above the lattice)
+    if (z + 1 < ze) put(z + 1, un, HRn, HWn);
+    const float* mid = &ub[z & 1][ty + 1][4 + 4 * g];
+    const float4 ym = *reinterpret_cast<const float4*>(mid - kZmPitch);
+    const float4 yp = *reinterpret_cast<const float4*>(mid + kZmPitch);
+    const float lft = mid[-1], rgt = mid[4];
+    if (own) {
+      const float ymv[4] = {ym.x, ym.y, ym.z, ym.w}, ypv[4] = {yp.x, yp.y, yp.z, yp.w};
+      V4<float> VO = zero4<float>();   // zero on padding
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int x = x0 + e;
+        if (x >= rd.nx) continue;
+        const float left = e == 0 ? lft : uc.a[e - 1];
+        const float right = e == 3 ? rgt : uc.a[e + 1];
+        const float nb = (x > 0 ? left : 0.f) + (x < rd.nx - 1 ? right : 0.f) + ymv[e] + ypv[e] + up.a[e] + un.a[e];
+        VO.a[e] = pre0_site(Rc.a[e], Wc.a[e], uc.a[e], cpl, nb);
+      }
+      st4(dst + eo + sz * z, VO);
+    }
+    up = uc;
+    uc = un;
+    Rc = Rn;
+    Wc = Wn;
+    Rn = Rnn;
+    Wn = Wnn;
+    HRn = HRnn;
+    HWn = HWnn;
+    __syncthreads();
+  }
+}
+
+// TMA form of the plane-marching pre-sweeps (same tiles, slabs and
+// per-site arithmetic as k_mg_pre0_z).  One thread issues, per plane, two
+// tensor copies (r and 1/d) of the box x0 - 4 .. x0 + 4 kZmG + 3 by
+// y0 - 1 .. y0 + kZmY into one of kTmStages shared-memory stages, completing
+// on the stage's mbarrier; the copy engine fills sites outside the lattice
+// with zeros, so the halo needs no bounds checks.  A plane is consumed
+// kTmStages - 2 planes after its copy was issued; a stage is refilled after
+// the block barrier that follows its last use.  Waits are bounded: on a
+// timeout the block records SYNC_ERR_TIMEOUT, waits (bounded) for its copies
+// in flight and returns.
+constexpr int kTmW = 4 * kZmG + 8, kTmH = kZmY + 2;
+constexpr int kTmPlane = kTmW * kTmH;                      // floats per array and plane
+constexpr int kTmPlaneF = ((kTmPlane * 4 + 127) / 128) * 32;  // stage slot in floats (128-byte multiple)
+constexpr int kTmStages = 4;
+constexpr int kTmSmem = kTmStages * 2 * kTmPlaneF * 4 + 128;
+constexpr int kTmWaitLimit = 1 << 20;
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(float* sdst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(tc::smem_u32(sdst)),
+      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(tc::smem_u32(bar))
+      : "memory");
+}
+
+__global__ void __launch_bounds__(kZmThreads, 7)
+    k_mg_pre0_t(Ctx c, int which, float* __restrict__ dst, int zs, const __grid_constant__ CUtensorMap tm_r,
+                const __grid_constant__ CUtensorMap tm_w) {
+  HCA_VC_ENTRY(c);
+  extern __shared__ __align__(128) float tsm_raw[];
+  __shared__ __align__(8) uint64_t bar[kTmStages];
+  // stage slots start on a 128-byte boundary (the launch adds 128 bytes)
+  float* tsm = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(tsm_raw) + 127) & ~uintptr_t(127));
+  const RepDesc& rd = c.reps[0];
+  const float cpl = op_coupling_t<float>(rd, which);
+  const int t = threadIdx.x, g = t % kZmG, ty = t / kZmG;
+  const int G = blockIdx.x * kZmG + g, y = blockIdx.y * kZmY + ty;
+  const int x0 = 4 * G;
+  const bool own = G < rd.gpr && y < rd.ny;
+  const long long sy = rd.nxp, sz = (long long)rd.nxp * rd.ny;
+  const long long eo = rd.off + x0 + sy * y;
+  const int zb = blockIdx.z * zs, ze = min(rd.nz, zb + zs);
+  const int bx = 4 * kZmG * blockIdx.x - 4, by = kZmY * blockIdx.y - 1;
+  const int nk = ze - zb + 2;   // planes zb - 1 .. ze, plane p at k = p - zb + 1
+  if (t == 0) {
+    for (int s = 0; s < kTmStages; ++s) tc::mbar_init(&bar[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  auto slot = [&](int k, int a) { return tsm + (2 * (k % kTmStages) + a) * kTmPlaneF; };
+  auto issue = [&](int k) {
+    uint64_t* b = &bar[k % kTmStages];
+    mbar_expect_tx(b, 2 * kTmPlane * 4);
+    tma_load_3d(slot(k, 0), &tm_r, bx, by, zb - 1 + k, b);
+    tma_load_3d(slot(k, 1), &tm_w, bx, by, zb - 1 + k, b);
+  };
+  auto ready = [&](int k) { return tc::mbar_wait(&bar[k % kTmStages], (uint32_t)((k / kTmStages) & 1), kTmWaitLimit); };
+  int issued = min(kTmStages, nk);
+  if (t == 0)
+    for (int k = 0; k < issued; ++k) issue(k);
+  // own group in a box: row ty + 1, columns 4 + 4 g ..
+  const int oc = (ty + 1) * kTmW + 4 + 4 * g;
+  auto own4 = [&](int k, int a) {
+    const float4 v = *reinterpret_cast<const float4*>(slot(k, a) + oc);
+    V4<float> r;
+    r.a[0] = v.x;
+    r.a[1] = v.y;
+    r.a[2] = v.z;
+    r.a[3] = v.w;
+    return r;
+  };
+  auto u_of = [&](const V4<float>& R, const V4<float>& W) {
+    V4<float> U;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) U.a[e] = (x0 + e < rd.nx) ? pre0_u(R.a[e], W.a[e]) : 0.f;
+    return U;
+  };
+  bool ok = ready(0);
+  ok = ready(1) && ok;
+  V4<float> up, uc, Rc, Wc;
+  if (ok) {
+    up = u_of(own4(0, 0), own4(0, 1));
+    Rc = own4(1, 0);
+    Wc = own4(1, 1);
+    uc = u_of(Rc, Wc);
+  }
+  for (int z = zb;; ++z) {
+    const bool more = z < ze;
+    if (more && ok) ok = ready(z - zb + 2);
+    // one decision per block: every thread stops together on a timeout
+    if (__syncthreads_or(!ok)) break;
+    if (!more) break;
+    const int k = z - zb + 1;
+    // every thread is past plane z - 1: its stage takes plane k - 1 + kTmStages
+    if (t == 0 && k - 1 + kTmStages < nk) {
+      issue(k - 1 + kTmStages);
+      issued = k + kTmStages;
+    }
+    const V4<float> Rn = own4(k + 1, 0), Wn = own4(k + 1, 1);
+    const V4<float> un = u_of(Rn, Wn);   // plane z + 1 (zero above the lattice)
+    if (own) {
+      const float* br = slot(k, 0) + oc;
+      const float* bw = slot(k, 1) + oc;
+      const float4 ymr = *reinterpret_cast<const float4*>(br - kTmW), ymw = *reinterpret_cast<const float4*>(bw - kTmW);
+      const float4 ypr = *reinterpret_cast<const float4*>(br + kTmW), ypw = *reinterpret_cast<const float4*>(bw + kTmW);
+      const float ymv[4] = {pre0_u(ymr.x, ymw.x), pre0_u(ymr.y, ymw.y), pre0_u(ymr.z, ymw.z), pre0_u(ymr.w, ymw.w)};
+      const float ypv[4] = {pre0_u(ypr.x, ypw.x), pre0_u(ypr.y, ypw.y), pre0_u(ypr.z, ypw.z), pre0_u(ypr.w, ypw.w)};
+      const float lft = pre0_u(br[-1], bw[-1]), rgt = pre0_u(br[4], bw[4]);
+      V4<float> VO = zero4<float>();   // zero on padding
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int x = x0 + e;
+        if (x >= rd.nx) continue;
+        const float left = e == 0 ? lft : uc.a[e - 1];
+        const float right = e == 3 ? rgt : uc.a[e + 1];
+        const float nb = (x > 0 ? left : 0.f) + (x < rd.nx - 1 ? right : 0.f) + ymv[e] + ypv[e] + up.a[e] + un.a[e];
+        VO.a[e] = pre0_site(Rc.a[e], Wc.a[e], uc.a[e], cpl, nb);
+      }
+      st4(dst + eo + sz * z, VO);
+    }
+    up = uc;
+    uc = un;
+    Rc = Rn;
+    Wc = Wn;
+  }
+  if (!ok) {
+    // a copy did not complete in time: record it, and let this block's
+    // copies in flight land before its shared memory is released
+    if (t == 0) {
+      c.sync->error = SYNC_ERR_TIMEOUT;
+      for (int k = max(0, issued - kTmStages); k < issued; ++k) (void)ready(k);
+    }
+    __syncthreads();
+  }
+}
+
+// One site of the lattice's restriction sweep, shared by the row and
+// plane-marching forms: with rn = r + c sum_nb v, the residual r - A v =
+// rn - d v (one fused multiply-add) and the first post-sweep's part
+// v + (W2 / d)(r - A v) = (1 - W2) v + W2 rn / d (0 where d = 0).
+template <typename T>
+__device__ __forceinline__ T restrict0_res(T rn, T d, T v) {
+  return fma(-d, v, rn);
+}
+template <typename T>
+__device__ __forceinline__ T restrict0_vp(T rn, T d, T v) {
+  return d != T(0) ? fma((T)MG_W2, rn / d, mul_rn((T)(1.0 - MG_W2), v)) : T(0);
 }
 
 // Restriction from the lattice to level 1 in row-vector form, from the
@@ -871,11 +1170,10 @@ __global__ void __launch_bounds__(128, 4) k_mg_restrict0_rows(Ctx c, int which, 
           const T right = e == 3 ? xr[a] : XV[a].a[e + 1];
           const T nb = (x > 0 ? left : T(0)) + (x < rd.nx - 1 ? right : T(0)) + ymr.a[e] + ypr.a[e] + zmr.a[e] + zpr.a[e];
           const T rn = fma(cpl, nb, RV[a].a[e]);   // r + c sum_nb v
-          const T res = rn - DV[a].a[e] * XV[a].a[e];
+          const T res = restrict0_res(rn, DV[a].a[e], XV[a].a[e]);
           if (e < 2) acc0 += res;
           else acc1 += res;
-          // v + (W2 / d)(r - A v) = (1 - W2) v + W2 (r + c sum_nb v) / d
-          if (DV[a].a[e] != T(0)) VO.a[e] = fma((T)MG_W2, rn / DV[a].a[e], (T)(1.0 - MG_W2) * XV[a].a[e]);
+          VO.a[e] = restrict0_vp(rn, DV[a].a[e], XV[a].a[e]);
         }
         st4(vo + eb + off[a], VO);
       }
@@ -1324,7 +1622,20 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
   // registers; measured 71.4 -> 67.6 us at 256^3), 4 for the restriction
   // (61.4 us; 65.5 us with 5)
   const bool pdl = c.pdl != 0;
-  if (all || part == 1) launch_k(pdl, k_mg_pre0<T>, dim3(nb), dim3(128), 0, s, c, which, z);
+  if (all || part == 1) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (H.zm_slabs > 0 && H.zm_mode == 2) {
+        launch_k(pdl, k_mg_pre0_t, dim3(H.zm_tx, H.zm_ty, H.zm_slabs), dim3(kZmThreads), (size_t)kTmSmem, s, c, which,
+                 z, H.zm_zs, H.zm_map_r, H.zm_map_w);
+      } else if (H.zm_slabs > 0) {
+        launch_k(pdl, k_mg_pre0_z, dim3(H.zm_tx, H.zm_ty, H.zm_slabs), dim3(kZmThreads), 0, s, c, which, z, H.zm_zs);
+      } else {
+        launch_k(pdl, k_mg_pre0<T>, dim3(nb), dim3(128), 0, s, c, which, z);
+      }
+    } else {
+      launch_k(pdl, k_mg_pre0<T>, dim3(nb), dim3(128), 0, s, c, which, z);
+    }
+  }
   if (all || part == 2) launch_k(pdl, k_mg_restrict0_rows<T>, dim3(nb), dim3(128), 0, s, c, which, (const T*)z);
   if (all || part == 3) {
     // levels 1 .. lo-1 by per-level kernels, lo .. nlev-1 in the cooperative
@@ -1456,6 +1767,68 @@ void mg_coop_config(MGHost& H, bool fp64, int sm_count, long long smem_bytes) {
   else coop_config_t<float>(H, sm_count, smem_bytes);
 }
 // (H.small: the deepest grid-kernel level + 1 over the batch)
+
+// A 3-D tensor map over one lattice array (x extent nx, rows nxp apart),
+// box kTmW x kTmH x 1, zero fill outside.  False if the driver entry point is
+// missing or the encoding is refused.
+bool lattice_map(CUtensorMap* m, const float* base, const RepDesc& rd) {
+  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Encode enc = nullptr;
+  if (!enc) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      (void)cudaGetLastError();
+      return false;
+    }
+    enc = (Encode)fn;
+  }
+  const float* p = base + rd.off;
+  if ((reinterpret_cast<uintptr_t>(p) & 15u) || (rd.nxp * 4) % 16) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)rd.nx, (cuuint64_t)rd.ny, (cuuint64_t)rd.nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)rd.nxp * 4, (cuuint64_t)rd.nxp * rd.ny * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)kTmW, (cuuint32_t)kTmH, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(p), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Form and geometry of the lattice's pre-sweeps on one FP32 lattice rd
+// (arrays r and w): the plane-marching kernel with register prefetch
+// (default), its TMA-staged form (HCA_MG_ZMARCH=2, measured slower within
+// the step: its 4-stage shared memory makes the SMs switch their shared
+// memory / L1 split around it), or the row form (HCA_MG_ZMARCH=0).  Tiles of
+// kZmG groups by kZmY rows; the planes split into slabs so that the grid is
+// a whole number of waves of resident blocks, at most HCA_MG_ZM_WAVES
+// (default 2, measured best at 256^3).
+void mg_zmarch_config(MGHost& H, const RepDesc& rd, int sm_count, const float* r, const float* w) {
+  H.zm_slabs = 0;
+  const char* e = std::getenv("HCA_MG_ZMARCH");
+  if ((e && e[0] == '0') || H.nlev <= 1) return;
+  H.zm_mode = (e && e[0] == '2') ? 2 : 1;
+  if (H.zm_mode == 2 && !(lattice_map(&H.zm_map_r, r, rd) && lattice_map(&H.zm_map_w, w, rd))) H.zm_mode = 1;
+  const void* fn = H.zm_mode == 2 ? (const void*)k_mg_pre0_t : (const void*)k_mg_pre0_z;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kZmThreads, H.zm_mode == 2 ? kTmSmem : 0) !=
+          cudaSuccess ||
+      per_sm < 1) {
+    (void)cudaGetLastError();
+    return;
+  }
+  const char* wv = std::getenv("HCA_MG_ZM_WAVES");
+  const double waves = wv ? std::max(0.05, std::atof(wv)) : 2.0;
+  H.zm_tx = (rd.gpr + kZmG - 1) / kZmG;
+  H.zm_ty = (rd.ny + kZmY - 1) / kZmY;
+  const double tiles = (double)H.zm_tx * H.zm_ty;
+  const long long want = (long long)(waves * sm_count * per_sm / tiles);   // whole waves at most
+  const int slabs = (int)std::max(1LL, std::min((long long)rd.nz, want));
+  H.zm_zs = (rd.nz + slabs - 1) / slabs;
+  H.zm_slabs = (rd.nz + H.zm_zs - 1) / H.zm_zs;
+}
 
 // w_done: the lattice's 1/d is already in place (the first defect-correction
 // residual sweep of an FP32 solve forms it).

@@ -51,3 +51,37 @@ def test_persistent_rows_equal_block_per_chunk(shape, pc):
     assert a[5]["o2_iterations"] == b[5]["o2_iterations"]
     assert a[5]["drug_iterations"] == b[5]["drug_iterations"]
     assert a[5]["o2_rel_residual"] == b[5]["o2_rel_residual"]
+
+
+ZM_SHAPES = [(24, 32, 160), (13, 24, 130), (8, 20, 300), (64, 64, 64), (5, 17, 36), (3, 40, 260)]
+
+
+@pytest.mark.parametrize("waves", ["1", "8", "0.05"], ids=["wave", "thin-slabs", "one-slab"])
+@pytest.mark.parametrize("mode", ["1", "2"], ids=["registers", "tma"])
+@pytest.mark.parametrize("shape", ZM_SHAPES)
+def test_plane_marching_presweeps_equal_row_form(shape, mode, waves, monkeypatch):
+    """The lattice pre-sweeps in plane-marching form (tiles of 32 x 16 sites,
+    slabs of planes; planes prefetched into registers with the halo in shared
+    memory, or staged in shared memory by TMA tensor copies) give the row
+    form's bits: one V-cycle z = M r on a random r, and two coupled steps.
+    Ragged tiles in x and y, slabs of one plane up to the whole lattice."""
+    rng = np.random.default_rng(21)
+    r = rng.standard_normal(shape).astype(np.float32)
+    out = []
+    for zm in ("0", mode):
+        monkeypatch.setenv("HCA_MG_ZMARCH", zm)
+        monkeypatch.setenv("HCA_MG_ZM_WAVES", waves)
+        sim, _, _ = make_pair(shape, "f32", seed=17, n_drugs=2, preconditioner=hca.HCA_PC_MG)
+        z = [sim.apply_preconditioner(w, r) for w in (0, 1)]
+        sim.step(2)
+        out.append((z, sim.states(), sim.field(hca.FIELD_O2), sim.field(hca.FIELD_O2_LO),
+                    sim.field(hca.FIELD_DRUG0), sim.field(hca.FIELD_DRUG1), sim.stats()))
+        sim.close()
+    a, b = out
+    for u, v in zip(a[0], b[0]):
+        assert np.isfinite(u).all() and np.abs(u).max() > 0
+        assert np.array_equal(u, v)
+    for u, v in zip(a[1:6], b[1:6]):
+        assert np.array_equal(u, v)
+    assert a[6]["o2_iterations"] == b[6]["o2_iterations"]
+    assert a[6]["drug_iterations"] == b[6]["drug_iterations"]
