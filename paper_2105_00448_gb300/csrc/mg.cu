@@ -409,6 +409,29 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_scale0(Ctx c, int which) {
   }
 }
 
+// k_mg_scale0 for one lattice as a stream of four-site groups (row-major,
+// vector loads and stores; padding sites are left as they are).
+template <typename T>
+__global__ void __launch_bounds__(256) k_mg_scale0_rows(Ctx c) {
+  HCA_VC_ENTRY(c);
+  const RepSolve& sv = c.solve[0];
+  if (sv.iters != 0 || sv.scale == 1.0) return;
+  const T sc = (T)sv.scale;
+  const RepDesc& rd = c.reps[0];
+  T* __restrict__ r = (T*)c.r + rd.off;
+  const long long ng = (long long)rd.gpr * rd.ny * rd.nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ng; i += (long long)gridDim.x * blockDim.x) {
+    const long long row = i / rd.gpr;
+    const int x0 = 4 * (int)(i - row * rd.gpr);
+    T* p = r + row * rd.nxp + x0;
+    V4<T> v = ld4(p);
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (x0 + e < rd.nx) v.a[e] *= sc;
+    st4(p, v);
+  }
+}
+
 // The lattice as the coarsest level (single replicate): t0 = (omega / d) r
 template <typename T>
 __global__ void __launch_bounds__(kMgThreads) k_mg_first0(Ctx c, int which) {
@@ -1602,7 +1625,12 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
   T* z = (T*)c.z;
   const bool all = part < 0;
   const bool multi = c.n_reps > 1;
-  if (scale && (all || part == 0)) k_mg_scale0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, s>>>(c, which);
+  if (scale && (all || part == 0)) {
+    if (c.n_reps == 1)
+      k_mg_scale0_rows<T><<<grid_for(H.ntot[0] / 4 + 1), kMgThreads, 0, s>>>(c);
+    else
+      k_mg_scale0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, s>>>(c, which);
+  }
   if (H.nlev == 1) {
     if (!all && part != 3) return;
     // the lattice is the coarsest level (single replicate): MG_NU_COARSE
