@@ -85,15 +85,16 @@ __device__ __forceinline__ T p53_at(T P0, T lam, T s, T k1) {
 }
 
 // Per-cell ODEs over one chunk of rows.  A warp packs the consuming sites of
-// its 32 four-site groups into a shared-memory list and its lanes take the
-// list's entries in turn, so the 60-substep RK4 keeps every lane busy
+// its four-site groups into a shared-memory list and its lanes take the
+// list's entries 32 at a time; a partial last batch waits in the list for
+// the warp's next groups, so the 60-substep RK4 keeps every lane busy
 // whatever the mix of cells and empty sites (each site's arithmetic is
 // unchanged).
 template <typename T>
 __global__ void __launch_bounds__(512) k_ode(Ctx c) {
   HCA_COUNT_KERNEL(c);
   constexpr int kMaxWarps = 16;
-  __shared__ long long s_site[kMaxWarps][128];
+  __shared__ long long s_site[kMaxWarps][128 + 32];
   const int2 ch = c.chunks[blockIdx.x];
   const RepDesc& rd = c.reps[ch.x];
   const int nrows = min(rd.chunk_rows, rd.ny * rd.nz - ch.y);
@@ -111,6 +112,59 @@ __global__ void __launch_bounds__(512) k_ode(Ctx c) {
   T* __restrict__ PHI = (T*)c.phi;
   T* __restrict__ PP = (T*)c.P;
   T* __restrict__ VV = (T*)c.Vc;
+  long long* list = s_site[wid];
+  auto cell = [&](long long q) {
+    const uint8_t s = c.state[q];
+    const T Kk = KK[q];
+    if (is_cancer(s)) PHI[q] = PHI[q] + dt * Kk / (Tc * (Kphi + Kk));
+    const T lam = k1p * Kk / (Kp53 + Kk);
+    const T decay = k2p * Kk / (KV + Kk);
+    const T P0 = PP[q];
+    T v = VV[q];
+    // one classical RK4 substep of Vc with P at the stage times (Pa, Pb, Pc)
+    auto rk4 = [&](T Pa, T Pb, T Pc) {
+      const T f1 = k2 + k2pp * Pa * sat(v, J5 + v) - decay * v;
+      const T v2 = v + half * f1;
+      const T f2 = k2 + k2pp * Pb * sat(v2, J5 + v2) - decay * v2;
+      const T v3 = v + half * f2;
+      const T f3 = k2 + k2pp * Pb * sat(v3, J5 + v3) - decay * v3;
+      const T v4 = v + h * f3;
+      const T f4 = k2 + k2pp * Pc * sat(v4, J5 + v4) - decay * v4;
+      v = v + sixth * (f1 + T(2) * f2 + T(2) * f3 + f4);
+    };
+    T Pa = P0;
+    if (lam != T(0)) {
+      // P(s) = P0 e^{-lam s} + k1 (1 - e^{-lam s}) / lam = P0 + E(s) (P0 - k1 / lam) with
+      // E(s) = expm1(-lam s).  The stage times are multiples of h/2, and
+      // expm1(a + b) = expm1(a) + expm1(b) + expm1(a) expm1(b), so E advances
+      // by one half-step with E <- E + q + E q, q = expm1(-lam h/2): one
+      // transcendental per cell instead of two per substep (the recurrence
+      // adds ~1 ulp of E per half-step)
+      const T A0 = P0 - k1 / lam;
+      const T qh = t_expm1(-lam * half);
+      T E = T(0);
+      for (int m = 0; m < nsub; ++m) {
+        E = E + qh + E * qh;
+        const T Pb = P0 + E * A0;
+        E = E + qh + E * qh;
+        const T Pc = P0 + E * A0;
+        rk4(Pa, Pb, Pc);
+        Pa = Pc;
+      }
+    } else {
+      // no p53 decay (K = 0): P grows linearly, P(s) = P0 + k1 s
+      for (int m = 0; m < nsub; ++m) {
+        const T s0 = (T)m * h;
+        const T Pb = P0 + k1 * (s0 + half);
+        const T Pc = P0 + k1 * (s0 + h);
+        rk4(Pa, Pb, Pc);
+        Pa = Pc;
+      }
+    }
+    VV[q] = v;
+    PP[q] = p53_at(P0, lam, dt, k1);
+  };
+  int n = 0;   // cells waiting in the warp's list (fewer than 32)
   for (int gbase = 0; gbase < ngroups; gbase += blockDim.x) {
     const int gi = gbase + threadIdx.x;
     unsigned live = 0;
@@ -131,53 +185,22 @@ __global__ void __launch_bounds__(512) k_ode(Ctx c) {
       const int v = __shfl_up_sync(0xffffffffu, pre, o);
       if (lane >= o) pre += v;
     }
-    const int total = __shfl_sync(0xffffffffu, pre, 31);
-    pre -= cnt;
+    const int total = n + __shfl_sync(0xffffffffu, pre, 31);
+    pre += n - cnt;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-      if (live >> k & 1u) s_site[wid][pre++] = e + k;
+      if (live >> k & 1u) list[pre++] = e + k;
     __syncwarp();
-    for (int j = lane; j < total; j += 32) {
-      const long long q = s_site[wid][j];
-      const uint8_t s = c.state[q];
-      const T Kk = KK[q];
-      if (is_cancer(s)) PHI[q] = PHI[q] + dt * Kk / (Tc * (Kphi + Kk));
-      const T lam = k1p * Kk / (Kp53 + Kk);
-      const T decay = k2p * Kk / (KV + Kk);
-      const T P0 = PP[q];
-      // P(s) = P0 e^{-lam s} + k1 (1 - e^{-lam s}) / lam = P0 + E(s) (P0 - k1 / lam) with
-      // E(s) = expm1(-lam s).  The stage times are multiples of h/2, and
-      // expm1(a + b) = expm1(a) + expm1(b) + expm1(a) expm1(b), so E advances
-      // by one half-step with E <- E + q + E q, q = expm1(-lam h/2): one
-      // transcendental per cell instead of two per substep (the recurrence
-      // adds ~1 ulp of E per half-step)
-      const bool has_lam = lam != T(0);
-      const T A0 = has_lam ? P0 - k1 / lam : T(0);
-      const T qh = has_lam ? t_expm1(-lam * half) : T(0);
-      T E = T(0);
-      T v = VV[q];
-      T Pa = P0;
-      for (int m = 0; m < nsub; ++m) {
-        const T s0 = (T)m * h;
-        E = E + qh + E * qh;
-        const T Pb = has_lam ? P0 + E * A0 : P0 + k1 * (s0 + half);
-        E = E + qh + E * qh;
-        const T Pc = has_lam ? P0 + E * A0 : P0 + k1 * (s0 + h);
-        const T f1 = k2 + k2pp * Pa * sat(v, J5 + v) - decay * v;
-        const T v2 = v + half * f1;
-        const T f2 = k2 + k2pp * Pb * sat(v2, J5 + v2) - decay * v2;
-        const T v3 = v + half * f2;
-        const T f3 = k2 + k2pp * Pb * sat(v3, J5 + v3) - decay * v3;
-        const T v4 = v + h * f3;
-        const T f4 = k2 + k2pp * Pc * sat(v4, J5 + v4) - decay * v4;
-        v = v + sixth * (f1 + T(2) * f2 + T(2) * f3 + f4);
-        Pa = Pc;
-      }
-      VV[q] = v;
-      PP[q] = p53_at(P0, lam, dt, k1);
-    }
+    const int full = total & ~31;
+    for (int j = 0; j < full; j += 32) cell(list[j + lane]);
+    // the partial batch moves to the front of the list
+    n = total - full;
+    const long long keep = lane < n ? list[full + lane] : 0;
+    __syncwarp();
+    if (lane < n) list[lane] = keep;
     __syncwarp();
   }
+  if (lane < n) cell(list[lane]);
 }
 
 // Sites per state code, per replicate (into stats[rep].counts).
