@@ -247,8 +247,8 @@ void launch_init(const Ctx& c, const float* pc, const float* pf, const float* pv
 }
 
 void launch_ode(const Ctx& c, bool fp64) {
-  if (fp64) k_ode<double><<<c.n_chunks, c.threads, 0, c.stream>>>(c);
-  else k_ode<float><<<c.n_chunks, c.threads, 0, c.stream>>>(c);
+  if (fp64) launch_k(c.pdl != 0, k_ode<double>, dim3(c.n_chunks), dim3(c.threads), 0, c.stream, c);
+  else launch_k(c.pdl != 0, k_ode<float>, dim3(c.n_chunks), dim3(c.threads), 0, c.stream, c);
 }
 
 void launch_histogram(const Ctx& c) { k_histogram<<<c.n_chunks, c.threads, 0, c.stream>>>(c); }

@@ -1627,9 +1627,9 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
   const bool multi = c.n_reps > 1;
   if (scale && (all || part == 0)) {
     if (c.n_reps == 1)
-      k_mg_scale0_rows<T><<<grid_for(H.ntot[0] / 4 + 1), kMgThreads, 0, s>>>(c);
+      launch_k(c.pdl != 0, k_mg_scale0_rows<T>, dim3(grid_for(H.ntot[0] / 4 + 1)), dim3(kMgThreads), 0, s, c);
     else
-      k_mg_scale0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, s>>>(c, which);
+      launch_k(c.pdl != 0, k_mg_scale0<T>, dim3(grid_for(H.ntot[0])), dim3(kMgThreads), 0, s, c, which);
   }
   if (H.nlev == 1) {
     if (!all && part != 3) return;
@@ -1716,8 +1716,10 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
 
 template <typename T>
 void mg_setup_t(const Ctx& c, int which, const MGHost& H, bool w_done) {
-  if (!w_done) k_mg_w0<T><<<grid_for(H.ntot[0]), kMgThreads, 0, c.stream>>>(c, which);
-  for (int l = 1; l < H.nlev; ++l) k_mg_diag<T><<<grid_for(H.ntot[l]), kMgThreads, 0, c.stream>>>(c, which, l);
+  const bool pdl = c.pdl != 0;
+  if (!w_done) launch_k(pdl, k_mg_w0<T>, dim3(grid_for(H.ntot[0])), dim3(kMgThreads), 0, c.stream, c, which);
+  for (int l = 1; l < H.nlev; ++l)
+    launch_k(pdl, k_mg_diag<T>, dim3(grid_for(H.ntot[l])), dim3(kMgThreads), 0, c.stream, c, which, l);
 }
 
 // The launch forms of the coarse levels: the single-block levels in shared

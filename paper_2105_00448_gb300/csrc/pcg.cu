@@ -1053,7 +1053,7 @@ void launch_dc_residual(const Ctx& c, int which, const void* x_hi, const void* x
 }
 
 void launch_dc_update(const Ctx& c, void* x_hi, void* x_lo) {
-  k_dc_update<<<c.n_chunks, c.threads, 0, c.stream>>>(c, (float*)x_hi, (float*)x_lo);
+  launch_k(c.pdl != 0, k_dc_update, dim3(c.n_chunks), dim3(c.threads), 0, c.stream, c, (float*)x_hi, (float*)x_lo);
 }
 
 void launch_diff_norms(const Ctx& c, const void* a, const void* b, bool fp64) {
