@@ -663,7 +663,8 @@ __device__ __forceinline__ void grid_exit(PassSync* sy, int nbar) {
   do {                                                                       \
     asm volatile("griddepcontrol.wait;" ::: "memory");                       \
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");          \
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) atomicAdd((c).n_kernels, 1ull); \
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)           \
+      atomicAdd((c).n_kernels, 1ull);                                        \
   } while (0)
 
 // Entry of a V-cycle kernel: HCA_COUNT_KERNEL, then return at once when the
