@@ -39,7 +39,8 @@ void launch_vcycle(const Ctx& c, int which, bool fp64, const MGHost& H, int part
 int vcycle_launches(const MGHost& H, bool scale);
 int vcycle_part_launches(const MGHost& H, int part, bool scale);
 void mg_coop_config(MGHost& H, bool fp64, int sm_count, long long smem_bytes);
-void mg_zmarch_config(MGHost& H, const RepDesc& rd, int sm_count, const float* r, const float* w);
+void mg_zmarch_config(MGHost& H, const RepDesc& rd, int sm_count, const float* r, const float* w,
+                      const int* lv_dims);
 }  // namespace hca
 
 using hca::Ctx;
@@ -1289,8 +1290,15 @@ int create_impl(int n, const hca_config* cfgs, const float* const* p_cell, const
       ALLOC(c.r, fbytes);
       ALLOC(c.mg_t0, fbytes);
       ALLOC(c.mg_w, fbytes);
-      if (n == 1 && !h->fp64)
-        hca::mg_zmarch_config(H, h->reps_h[0], c.sm_count, (const float*)c.r, (const float*)c.mg_w);
+      if (n == 1 && !h->fp64) {
+        int dims[3 * hca::MG_MAXLEV] = {};
+        for (int l = 0; l < hca::MG_MAXLEV; ++l) {
+          dims[3 * l] = lv[l].nx;
+          dims[3 * l + 1] = lv[l].ny;
+          dims[3 * l + 2] = lv[l].nz;
+        }
+        hca::mg_zmarch_config(H, h->reps_h[0], c.sm_count, (const float*)c.r, (const float*)c.mg_w, dims);
+      }
       hca::MGLevel* lv_d;
       long long* start_d;
       long long* rowstart_d;

@@ -333,6 +333,11 @@ struct MGHost {
   int zm_zs = 0;
   int zm_tx = 0, zm_ty = 0;
   int zm_mode = 0;               // 1: planes prefetched into registers, 2: TMA-staged planes
+  // grid levels' pre-sweeps and last post-sweep in plane-marching form
+  // (0 slabs: row form): slabs, planes per slab, tiles along x and y
+  int zl_slabs[MG_MAXLEV] = {};
+  int zl_zs[MG_MAXLEV] = {};
+  int zl_tx[MG_MAXLEV] = {}, zl_ty[MG_MAXLEV] = {};
   // TMA tensor maps of r and 1/d over the lattice (x extent nx: the copy
   // engine fills sites outside the lattice with zeros)
   CUtensorMap zm_map_r, zm_map_w;

@@ -973,6 +973,124 @@ __global__ void __launch_bounds__(kZmThreads, 7) k_mg_pre0_z(Ctx c, int which, f
   }
 }
 
+// Plane-marching form of k_mg_smooth_rows<float, MODE> on grid level l >= 1
+// of one FP32 lattice, for the fused pre-sweeps (SM_PRE: u = (W1 / d) rhs
+// formed at every site, x = u + (W2 / d)(rhs - A u)) and the last post-sweep
+// (SM_LAST: u = t, x = t + (W1 / d)(rhs - A t)).  The tiles, slabs, halo
+// roles and register prefetch of k_mg_pre0_z; the level's rows are whole
+// four-site groups.  Per site the row form's arithmetic: the neighbours'
+// u summed in the order x - 1, x + 1, y - 1, y + 1, z - 1, z + 1 (only those
+// inside the level), resid and one fused multiply-add.
+template <int MODE>
+__global__ void __launch_bounds__(kZmThreads, 7) k_mg_smooth_z(Ctx c, int which, int l, int zs) {
+  HCA_VC_ENTRY(c);
+  __shared__ __align__(16) float ub[2][kZmY + 2][kZmPitch];
+  const View<float> F = view<float>(c, which, 0, l);
+  const int gpr = F.nx >> 2;
+  const int t = threadIdx.x, g = t % kZmG, ty = t / kZmG;
+  const int G = blockIdx.x * kZmG + g, y = blockIdx.y * kZmY + ty;
+  const int x0 = 4 * G;
+  const bool own = G < gpr && y < F.ny;
+  const long long sy = F.sy, sz = F.sz;
+  const long long eo = x0 + sy * y;
+  const float* __restrict__ ua = MODE == SM_PRE ? F.rhs : F.t;   // u's source
+  int hrole = 0, hrow = 0, hcol = 0;
+  bool hok = false;
+  long long he = 0;
+  if (t < 2 * kZmG) {
+    hrole = 1;
+    const int hy = blockIdx.y * kZmY + (t < kZmG ? -1 : kZmY), hg = blockIdx.x * kZmG + t % kZmG;
+    hok = hy >= 0 && hy < F.ny && hg < gpr;
+    he = 4LL * hg + sy * hy;
+    hrow = t < kZmG ? 0 : kZmY + 1;
+    hcol = 4 + 4 * (t % kZmG);
+  } else if (t < 2 * kZmG + 2 * kZmY) {
+    hrole = 2;
+    const int k = t - 2 * kZmG, side = k / kZmY, row = k % kZmY;
+    const int hx = side ? 4 * kZmG * (blockIdx.x + 1) : 4 * kZmG * blockIdx.x - 1;
+    const int hy = blockIdx.y * kZmY + row;
+    hok = hx >= 0 && hx < F.nx && hy < F.ny;
+    he = hx + sy * hy;
+    hrow = row + 1;
+    hcol = side ? 4 + 4 * kZmG : 3;
+  }
+  const int zb = blockIdx.z * zs, ze = min(F.nz, zb + zs);
+  auto u_of = [&](const V4<float>& A, const V4<float>& W) {
+    if (MODE != SM_PRE) return A;
+    V4<float> U;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) U.a[e] = mul_rn(wt(MG_W1, W.a[e]), A.a[e]);
+    return U;
+  };
+  // u of the own group on plane z (0 outside the level)
+  auto u_own = [&](int z) {
+    const bool ok = own && z >= 0 && z < F.nz;
+    const V4<float> A = ld4_if(ua + eo + sz * z, ok);
+    const V4<float> W = MODE == SM_PRE ? ld4_if(F.w + eo + sz * z, ok) : A;
+    return u_of(A, W);
+  };
+  auto u_halo = [&](int z) {
+    const bool ok = hok && z >= 0 && z < ze;
+    V4<float> A = zero4<float>(), W = zero4<float>();
+    if (hrole == 1) {
+      A = ld4_if(ua + he + sz * z, ok);
+      if (MODE == SM_PRE) W = ld4_if(F.w + he + sz * z, ok);
+    } else if (hrole == 2 && ok) {
+      A.a[0] = ua[he + sz * z];
+      if (MODE == SM_PRE) W.a[0] = F.w[he + sz * z];
+    }
+    return u_of(A, W);
+  };
+  auto put = [&](int z, const V4<float>& U, const V4<float>& H) {
+    *reinterpret_cast<float4*>(&ub[z & 1][ty + 1][4 + 4 * g]) = make_float4(U.a[0], U.a[1], U.a[2], U.a[3]);
+    if (hrole == 1) *reinterpret_cast<float4*>(&ub[z & 1][hrow][hcol]) = make_float4(H.a[0], H.a[1], H.a[2], H.a[3]);
+    else if (hrole == 2) ub[z & 1][hrow][hcol] = H.a[0];
+  };
+  auto ld_site = [&](const float* a, int z) { return ld4_if(a + eo + sz * z, own && z < ze); };
+  V4<float> up = u_own(zb - 1), uc = u_own(zb), un = u_own(zb + 1);
+  V4<float> Rc = ld_site(F.rhs, zb), Dc = ld_site(F.d, zb), Wc = ld_site(F.w, zb);
+  V4<float> Hn = u_halo(zb + 1);
+  put(zb, uc, u_halo(zb));
+  __syncthreads();
+  for (int z = zb; z < ze; ++z) {
+    const V4<float> unn = u_own(z + 2 <= ze ? z + 2 : -1);
+    const V4<float> Hnn = u_halo(z + 2);
+    const V4<float> Rn = ld_site(F.rhs, z + 1), Dn = ld_site(F.d, z + 1), Wn = ld_site(F.w, z + 1);
+    if (z + 1 < ze) put(z + 1, un, Hn);
+    if (own) {
+      const float* mid = &ub[z & 1][ty + 1][4 + 4 * g];
+      const float4 a = *reinterpret_cast<const float4*>(mid - kZmPitch);
+      const float4 b = *reinterpret_cast<const float4*>(mid + kZmPitch);
+      const float ym[4] = {a.x, a.y, a.z, a.w}, yp[4] = {b.x, b.y, b.z, b.w};
+      const float lft = mid[-1], rgt = mid[4];
+      V4<float> Xo;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int x = x0 + k;
+        float nb = 0.f;
+        if (x > 0) nb += k > 0 ? uc.a[k - 1] : lft;
+        if (x < F.nx - 1) nb += k < 3 ? uc.a[k + 1] : rgt;
+        if (y > 0) nb += ym[k];
+        if (y < F.ny - 1) nb += yp[k];
+        if (z > 0) nb += up.a[k];
+        if (z < F.nz - 1) nb += un.a[k];
+        const float u0 = uc.a[k];
+        const float res = resid(Rc.a[k], Dc.a[k], u0, F.c, nb);
+        Xo.a[k] = fmaf(wt(MODE == SM_LAST ? MG_W1 : MG_W2, Wc.a[k]), res, u0);
+      }
+      *reinterpret_cast<V4<float>*>(F.x + eo + sz * z) = Xo;
+    }
+    up = uc;
+    uc = un;
+    un = unn;
+    Rc = Rn;
+    Dc = Dn;
+    Wc = Wn;
+    Hn = Hnn;
+    __syncthreads();
+  }
+}
+
 // TMA form of the plane-marching pre-sweeps (same tiles, slabs and
 // per-site arithmetic as k_mg_pre0_z).  One thread issues, per plane, two
 // tensor copies (r and 1/d) of the box x0 - 4 .. x0 + 4 kZmG + 3 by
@@ -1612,6 +1730,13 @@ void launch_post0(const Ctx& c, int which, const MGHost& H, const T* src, T om) 
   }
 }
 
+// Level l >= 1 sweeps in plane-marching form (one FP32 lattice; configured
+// by mg_zmarch_config).
+template <typename T>
+bool zlevel(const MGHost& H, int l) {
+  return std::is_same<T, float>::value && l < MG_MAXLEV && H.zl_slabs[l] > 0 && (H.rows_ok >> l & 1u);
+}
+
 // part: -1 = whole cycle; 0 = r scaling (only with `scale`: right after a
 // residual was formed, i.e. at the start of a solve or a defect-correction
 // sweep); 1 = the lattice's pre-sweeps; 2 = its restriction; 3 = the coarse
@@ -1672,7 +1797,12 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
     const bool coop = H.coop_blocks > 0 && H.coop_from < H.small;
     const int lo = coop ? H.coop_from : H.small;
     for (int l = 1; l < lo; ++l) {
-      if (H.rows_ok >> l & 1u) {
+      if (zlevel<T>(H, l)) {
+        launch_k(pdl, k_mg_smooth_z<SM_PRE>, dim3(H.zl_tx[l], H.zl_ty[l], H.zl_slabs[l]), dim3(kZmThreads), 0, s, c,
+                 which, l, H.zl_zs[l]);
+        launch_k(pdl, k_mg_restrict_rows<T>, dim3((int)std::min((H.restr_items[l] + 127) / 128, 152LL * 16)), dim3(128),
+                 0, s, c, which, l);
+      } else if (H.rows_ok >> l & 1u) {
         launch_k(pdl, k_mg_smooth_rows<T, SM_PRE>, dim3(grid_for(H.post_items[l])), dim3(kMgThreads), 0, s, c, which, l);
         // 128 threads: ~12 vector loads per thread in flight
         launch_k(pdl, k_mg_restrict_rows<T>, dim3((int)std::min((H.restr_items[l] + 127) / 128, 152LL * 16)), dim3(128),
@@ -1698,7 +1828,11 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
       launch_k(pdl, k_mg_small<T>, dim3(c.n_reps), dim3(kSmallThreads), 0, s, c, which);
     }
     for (int l = lo - 1; l >= 1; --l) {
-      if (H.rows_ok >> l & 1u) {
+      if (zlevel<T>(H, l)) {
+        launch_k(pdl, k_mg_smooth_rows<T, SM_POST>, dim3(grid_for(H.post_items[l])), dim3(kMgThreads), 0, s, c, which, l);
+        launch_k(pdl, k_mg_smooth_z<SM_LAST>, dim3(H.zl_tx[l], H.zl_ty[l], H.zl_slabs[l]), dim3(kZmThreads), 0, s, c,
+                 which, l, H.zl_zs[l]);
+      } else if (H.rows_ok >> l & 1u) {
         launch_k(pdl, k_mg_smooth_rows<T, SM_POST>, dim3(grid_for(H.post_items[l])), dim3(kMgThreads), 0, s, c, which, l);
         launch_k(pdl, k_mg_smooth_rows<T, SM_LAST>, dim3(grid_for(H.post_items[l])), dim3(kMgThreads), 0, s, c, which, l);
       } else if (multi) {
@@ -1835,7 +1969,8 @@ bool lattice_map(CUtensorMap* m, const float* base, const RepDesc& rd) {
 // kZmG groups by kZmY rows; the planes split into slabs so that the grid is
 // a whole number of waves of resident blocks, at most HCA_MG_ZM_WAVES
 // (default 2, measured best at 256^3).
-void mg_zmarch_config(MGHost& H, const RepDesc& rd, int sm_count, const float* r, const float* w) {
+void mg_zmarch_config(MGHost& H, const RepDesc& rd, int sm_count, const float* r, const float* w,
+                      const int* lv_dims) {
   H.zm_slabs = 0;
   const char* e = std::getenv("HCA_MG_ZMARCH");
   if ((e && e[0] == '0') || H.nlev <= 1) return;
@@ -1858,6 +1993,31 @@ void mg_zmarch_config(MGHost& H, const RepDesc& rd, int sm_count, const float* r
   const int slabs = (int)std::max(1LL, std::min((long long)rd.nz, want));
   H.zm_zs = (rd.nz + slabs - 1) / slabs;
   H.zm_slabs = (rd.nz + H.zm_zs - 1) / H.zm_zs;
+  // grid levels with whole-group rows: the same tiles, slabs for at most
+  // HCA_MG_ZL_WAVES waves (default 1); HCA_MG_ZLEVELS=0 keeps their row form
+  const char* zl = std::getenv("HCA_MG_ZLEVELS");
+  if (zl && zl[0] == '0') return;
+  int per_sm_l = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_l, (const void*)k_mg_smooth_z<SM_PRE>, kZmThreads, 0) !=
+          cudaSuccess ||
+      per_sm_l < 1) {
+    (void)cudaGetLastError();
+    return;
+  }
+  const char* lw = std::getenv("HCA_MG_ZL_WAVES");
+  const double lwaves = lw ? std::max(0.05, std::atof(lw)) : 1.0;
+  for (int l = 1; l < std::min(H.small, MG_MAXLEV); ++l) {
+    if (!(H.rows_ok >> l & 1u)) continue;
+    const int nx = lv_dims[3 * l], ny = lv_dims[3 * l + 1], nz = lv_dims[3 * l + 2];
+    if (nx % 4) continue;
+    H.zl_tx[l] = (nx / 4 + kZmG - 1) / kZmG;
+    H.zl_ty[l] = (ny + kZmY - 1) / kZmY;
+    const double tl = (double)H.zl_tx[l] * H.zl_ty[l];
+    const long long wl = (long long)(lwaves * sm_count * per_sm_l / tl);
+    const int sl = (int)std::max(1LL, std::min((long long)nz, wl));
+    H.zl_zs[l] = (nz + sl - 1) / sl;
+    H.zl_slabs[l] = (nz + H.zl_zs[l] - 1) / H.zl_zs[l];
+  }
 }
 
 // w_done: the lattice's 1/d is already in place (the first defect-correction

@@ -85,3 +85,25 @@ def test_plane_marching_presweeps_equal_row_form(shape, mode, waves, monkeypatch
         assert np.array_equal(u, v)
     assert a[6]["o2_iterations"] == b[6]["o2_iterations"]
     assert a[6]["drug_iterations"] == b[6]["drug_iterations"]
+
+
+@pytest.mark.parametrize("waves", ["1", "0.05"], ids=["wave", "one-slab"])
+@pytest.mark.parametrize("shape", [(64, 64, 64), (24, 40, 136), (9, 36, 72)])
+def test_plane_marching_level_sweeps_equal_row_form(shape, waves, monkeypatch):
+    """The grid levels' pre-sweeps and last post-sweep in plane-marching form
+    give the row form's bits (two coupled steps; levels of several sizes,
+    ragged tiles, odd plane counts)."""
+    out = []
+    for zl in ("0", "1"):
+        monkeypatch.setenv("HCA_MG_ZLEVELS", zl)
+        monkeypatch.setenv("HCA_MG_ZL_WAVES", waves)
+        sim, _, _ = make_pair(shape, "f32", seed=23, n_drugs=1, preconditioner=hca.HCA_PC_MG)
+        sim.step(2)
+        out.append((sim.states(), sim.field(hca.FIELD_O2), sim.field(hca.FIELD_O2_LO), sim.field(hca.FIELD_DRUG0),
+                    sim.stats()))
+        sim.close()
+    a, b = out
+    for u, v in zip(a[:4], b[:4]):
+        assert np.array_equal(u, v)
+    assert a[4]["o2_iterations"] == b[4]["o2_iterations"]
+    assert a[4]["drug_iterations"] == b[4]["drug_iterations"]
