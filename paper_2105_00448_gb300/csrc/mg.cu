@@ -974,9 +974,11 @@ __global__ void __launch_bounds__(kZmThreads, 7) k_mg_pre0_z(Ctx c, int which, f
 }
 
 // Plane-marching form of k_mg_smooth_rows<float, MODE> on grid level l >= 1
-// of one FP32 lattice, for the fused pre-sweeps (SM_PRE: u = (W1 / d) rhs
-// formed at every site, x = u + (W2 / d)(rhs - A u)) and the last post-sweep
-// (SM_LAST: u = t, x = t + (W1 / d)(rhs - A t)).  The tiles, slabs, halo
+// of one FP32 lattice: the fused pre-sweeps (SM_PRE: u = (W1 / d) rhs formed
+// at every site, x = u + (W2 / d)(rhs - A u)), the prolongation fused with
+// the first post-sweep (SM_POST: u = x + P x_C formed at every site, t = u +
+// (W2 / d)(rhs - A u)) and the last post-sweep (SM_LAST: u = t, x = t +
+// (W1 / d)(rhs - A t)).  The tiles, slabs, halo
 // roles and register prefetch of k_mg_pre0_z; the level's rows are whole
 // four-site groups.  Per site the row form's arithmetic: the neighbours'
 // u summed in the order x - 1, x + 1, y - 1, y + 1, z - 1, z + 1 (only those
@@ -993,22 +995,30 @@ __global__ void __launch_bounds__(kZmThreads, 7) k_mg_smooth_z(Ctx c, int which,
   const bool own = G < gpr && y < F.ny;
   const long long sy = F.sy, sz = F.sz;
   const long long eo = x0 + sy * y;
-  const float* __restrict__ ua = MODE == SM_PRE ? F.rhs : F.t;   // u's source
-  int hrole = 0, hrow = 0, hcol = 0;
+  // u's source: rhs (with 1/d), x (plus the coarse correction) or t
+  const float* __restrict__ ua = MODE == SM_PRE ? F.rhs : MODE == SM_POST ? F.x : F.t;
+  const View<float> C = view<float>(c, which, 0, MODE == SM_POST ? l + 1 : l);
+  // the coarse correction P x_C at fine (x, y, z): level l + 1's value of its cell
+  auto pxc = [&](int x, int yy, int z) {
+    return C.x[(x >> 1) + (long long)C.nx * ((yy >> 1) + (long long)C.ny * (z >> 1))];
+  };
+  int hrole = 0, hrow = 0, hcol = 0, hx = 0, hy = 0;
   bool hok = false;
   long long he = 0;
   if (t < 2 * kZmG) {
     hrole = 1;
-    const int hy = blockIdx.y * kZmY + (t < kZmG ? -1 : kZmY), hg = blockIdx.x * kZmG + t % kZmG;
+    hy = blockIdx.y * kZmY + (t < kZmG ? -1 : kZmY);
+    const int hg = blockIdx.x * kZmG + t % kZmG;
     hok = hy >= 0 && hy < F.ny && hg < gpr;
+    hx = 4 * hg;
     he = 4LL * hg + sy * hy;
     hrow = t < kZmG ? 0 : kZmY + 1;
     hcol = 4 + 4 * (t % kZmG);
   } else if (t < 2 * kZmG + 2 * kZmY) {
     hrole = 2;
     const int k = t - 2 * kZmG, side = k / kZmY, row = k % kZmY;
-    const int hx = side ? 4 * kZmG * (blockIdx.x + 1) : 4 * kZmG * blockIdx.x - 1;
-    const int hy = blockIdx.y * kZmY + row;
+    hx = side ? 4 * kZmG * (blockIdx.x + 1) : 4 * kZmG * blockIdx.x - 1;
+    hy = blockIdx.y * kZmY + row;
     hok = hx >= 0 && hx < F.nx && hy < F.ny;
     he = hx + sy * hy;
     hrow = row + 1;
@@ -1022,10 +1032,21 @@ __global__ void __launch_bounds__(kZmThreads, 7) k_mg_smooth_z(Ctx c, int which,
     for (int e = 0; e < 4; ++e) U.a[e] = mul_rn(wt(MG_W1, W.a[e]), A.a[e]);
     return U;
   };
+  // u of a group (x0 = 4 G, row yy) with both of its coarse cells
+  auto u_post = [&](const V4<float>& A, int xg, int yy, int z, bool ok) {
+    V4<float> U = zero4<float>();
+    if (ok) {
+      const float c0 = pxc(xg, yy, z), c1 = pxc(xg + 2, yy, z);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) U.a[e] = A.a[e] + (e < 2 ? c0 : c1);
+    }
+    return U;
+  };
   // u of the own group on plane z (0 outside the level)
   auto u_own = [&](int z) {
     const bool ok = own && z >= 0 && z < F.nz;
     const V4<float> A = ld4_if(ua + eo + sz * z, ok);
+    if (MODE == SM_POST) return u_post(A, x0, y, z, ok);
     const V4<float> W = MODE == SM_PRE ? ld4_if(F.w + eo + sz * z, ok) : A;
     return u_of(A, W);
   };
@@ -1034,11 +1055,14 @@ __global__ void __launch_bounds__(kZmThreads, 7) k_mg_smooth_z(Ctx c, int which,
     V4<float> A = zero4<float>(), W = zero4<float>();
     if (hrole == 1) {
       A = ld4_if(ua + he + sz * z, ok);
+      if (MODE == SM_POST) return u_post(A, hx, hy, z, ok);
       if (MODE == SM_PRE) W = ld4_if(F.w + he + sz * z, ok);
     } else if (hrole == 2 && ok) {
       A.a[0] = ua[he + sz * z];
+      if (MODE == SM_POST) A.a[0] = A.a[0] + pxc(hx, hy, z);
       if (MODE == SM_PRE) W.a[0] = F.w[he + sz * z];
     }
+    if (MODE == SM_POST) return A;
     return u_of(A, W);
   };
   auto put = [&](int z, const V4<float>& U, const V4<float>& H) {
@@ -1078,7 +1102,7 @@ __global__ void __launch_bounds__(kZmThreads, 7) k_mg_smooth_z(Ctx c, int which,
         const float res = resid(Rc.a[k], Dc.a[k], u0, F.c, nb);
         Xo.a[k] = fmaf(wt(MODE == SM_LAST ? MG_W1 : MG_W2, Wc.a[k]), res, u0);
       }
-      *reinterpret_cast<V4<float>*>(F.x + eo + sz * z) = Xo;
+      *reinterpret_cast<V4<float>*>((MODE == SM_POST ? F.t : F.x) + eo + sz * z) = Xo;
     }
     up = uc;
     uc = un;
@@ -1829,7 +1853,8 @@ void vcycle_t(const Ctx& c, int which, const MGHost& H, int part, bool scale) {
     }
     for (int l = lo - 1; l >= 1; --l) {
       if (zlevel<T>(H, l)) {
-        launch_k(pdl, k_mg_smooth_rows<T, SM_POST>, dim3(grid_for(H.post_items[l])), dim3(kMgThreads), 0, s, c, which, l);
+        launch_k(pdl, k_mg_smooth_z<SM_POST>, dim3(H.zl_tx[l], H.zl_ty[l], H.zl_slabs[l]), dim3(kZmThreads), 0, s, c,
+                 which, l, H.zl_zs[l]);
         launch_k(pdl, k_mg_smooth_z<SM_LAST>, dim3(H.zl_tx[l], H.zl_ty[l], H.zl_slabs[l]), dim3(kZmThreads), 0, s, c,
                  which, l, H.zl_zs[l]);
       } else if (H.rows_ok >> l & 1u) {
