@@ -1987,19 +1987,19 @@ bool lattice_map(CUtensorMap* m, const float* base, const RepDesc& rd) {
 }
 
 // Form and geometry of the lattice's pre-sweeps on one FP32 lattice rd
-// (arrays r and w): the plane-marching kernel with register prefetch
-// (default), its TMA-staged form (HCA_MG_ZMARCH=2, measured slower within
-// the step: its 4-stage shared memory makes the SMs switch their shared
-// memory / L1 split around it), or the row form (HCA_MG_ZMARCH=0).  Tiles of
-// kZmG groups by kZmY rows; the planes split into slabs so that the grid is
-// a whole number of waves of resident blocks, at most HCA_MG_ZM_WAVES
-// (default 2, measured best at 256^3).
+// (arrays r and w): the plane-marching kernel with its planes staged by TMA
+// tensor copies (default; the register-prefetch form when the tensor maps
+// cannot be made or HCA_MG_ZMARCH=1), or the row form (HCA_MG_ZMARCH=0).
+// Tiles of kZmG groups by kZmY rows; the planes split into slabs so that
+// the grid is a whole number of waves of resident blocks, at most
+// HCA_MG_ZM_WAVES (default 1 for the TMA form, 2 for the register form:
+// measured best at 256^3).
 void mg_zmarch_config(MGHost& H, const RepDesc& rd, int sm_count, const float* r, const float* w,
                       const int* lv_dims) {
   H.zm_slabs = 0;
   const char* e = std::getenv("HCA_MG_ZMARCH");
   if ((e && e[0] == '0') || H.nlev <= 1) return;
-  H.zm_mode = (e && e[0] == '2') ? 2 : 1;
+  H.zm_mode = (e && e[0] == '1') ? 1 : 2;
   if (H.zm_mode == 2 && !(lattice_map(&H.zm_map_r, r, rd) && lattice_map(&H.zm_map_w, w, rd))) H.zm_mode = 1;
   const void* fn = H.zm_mode == 2 ? (const void*)k_mg_pre0_t : (const void*)k_mg_pre0_z;
   int per_sm = 0;
@@ -2010,7 +2010,7 @@ void mg_zmarch_config(MGHost& H, const RepDesc& rd, int sm_count, const float* r
     return;
   }
   const char* wv = std::getenv("HCA_MG_ZM_WAVES");
-  const double waves = wv ? std::max(0.05, std::atof(wv)) : 2.0;
+  const double waves = wv ? std::max(0.05, std::atof(wv)) : (H.zm_mode == 2 ? 1.0 : 2.0);
   H.zm_tx = (rd.gpr + kZmG - 1) / kZmG;
   H.zm_ty = (rd.ny + kZmY - 1) / kZmY;
   const double tiles = (double)H.zm_tx * H.zm_ty;
