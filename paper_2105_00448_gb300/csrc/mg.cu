@@ -1206,11 +1206,15 @@ __global__ void __launch_bounds__(kZmThreads, 7)
     Wc = own4(1, 1);
     uc = u_of(Rc, Wc);
   }
+  bool failed = false;   // the same in every thread of the block
   for (int z = zb;; ++z) {
     const bool more = z < ze;
     if (more && ok) ok = ready(z - zb + 2);
     // one decision per block: every thread stops together on a timeout
-    if (__syncthreads_or(!ok)) break;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
     if (!more) break;
     const int k = z - zb + 1;
     // every thread is past plane z - 1: its stage takes plane k - 1 + kTmStages
@@ -1245,7 +1249,7 @@ __global__ void __launch_bounds__(kZmThreads, 7)
     Rc = Rn;
     Wc = Wn;
   }
-  if (!ok) {
+  if (failed) {
     // a copy did not complete in time: record it, and let this block's
     // copies in flight land before its shared memory is released
     if (t == 0) {
