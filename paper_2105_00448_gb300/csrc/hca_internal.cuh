@@ -332,7 +332,7 @@ struct MGHost {
   int zm_slabs = 0;
   int zm_zs = 0;
   int zm_tx = 0, zm_ty = 0;
-  int zm_mode = 0;               // 1: planes prefetched into registers, 2: TMA-staged planes
+  int zm_mode = 0;               // 2: TMA-staged planes (default), 1: planes prefetched into registers
   // grid levels' pre-sweeps and last post-sweep in plane-marching form
   // (0 slabs: row form): slabs, planes per slab, tiles along x and y
   int zl_slabs[MG_MAXLEV] = {};
