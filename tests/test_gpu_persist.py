@@ -1,11 +1,19 @@
-"""Persistent row kernels (CG pass A, pass B and the lattice post-sweep of
-the V-cycle for one FP32 lattice with one row per warp) against the
-one-block-per-chunk form (HCA_PERSIST=0, read at handle creation): every row
-is computed by the same code and its sum goes to the same chunk slot, and
-each chunk is summed in the same fixed tree, so solves and coupled steps must
-agree bit for bit.  Lattices: one, two and four groups per lane, chunks of 8
-and 32 rows, ragged rows, both preconditioners.  Their parity with the oracle
-is checked in test_gpu_bench_instances.py and test_gpu_mg.py.
+"""Alternative launch forms of one FP32 lattice's kernels against each other,
+bit for bit (the form is read at handle creation):
+
+* persistent row kernels (CG pass A, pass B and the lattice post-sweep of the
+  V-cycle, one row per warp) against the one-block-per-chunk form
+  (HCA_PERSIST=0): every row is computed by the same code and its sum goes to
+  the same chunk slot, and each chunk is summed in the same fixed tree.
+  Lattices: one, two and four groups per lane, chunks of 8 and 32 rows,
+  ragged rows, both preconditioners;
+* the plane-marching multigrid sweeps (lattice pre-sweeps with TMA-staged or
+  register-prefetched planes, HCA_MG_ZMARCH; grid-level sweeps,
+  HCA_MG_ZLEVELS) against the row forms: the same arithmetic per site in the
+  same order.
+
+Their parity with the oracle is checked in test_gpu_bench_instances.py and
+test_gpu_mg.py.
 """
 
 import os
